@@ -1,0 +1,105 @@
+"""Seeded workloads shaped like the paper's channel and pipe cases.
+
+A workload is a mesh (``synthetic.meshes``) plus physics (rho, mu, period T),
+the mode frequencies omega_k = 2 pi k / T (Eq. vaptransform) and the
+Dirichlet data of every mode on every Dirichlet node: zero on walls, c_k times
+the analytic fully developed profile on the inlet.  Boundary data are defined
+so that the physical field is Re sum_k c_k g_k(x) e^{j omega_k t}.
+
+Dirichlet nodes are the nodes tagged WALL or INLET, in ascending node id; the
+outlet is traction-free (natural boundary, zero Neumann data).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import meshes
+from .womersley import channel_profile, pipe_profile
+
+
+def dirichlet_nodes(tag):
+    return np.flatnonzero((tag & (meshes.WALL | meshes.INLET)) != 0).astype(np.int64)
+
+
+def phases(n_modes, seed=0):
+    """c_0 = 1, c_k = k^-2 exp(j phi_k), phi_k ~ U[0, 2 pi) (numpy PCG64, seed)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=n_modes)
+    k = np.arange(n_modes, dtype=np.float64)
+    c = np.empty(n_modes, dtype=np.complex128)
+    c[0] = 1.0
+    c[1:] = k[1:] ** -2.0 * np.exp(1j * phi[1:])
+    return c
+
+
+def _inlet_values(mesh, omegas, coeffs, rho, mu, G):
+    tag = mesh["tag"]
+    xyz = mesh["xyz"]
+    dn = dirichlet_nodes(tag)
+    d = mesh["dim"]
+    g = np.zeros((len(omegas), dn.size, d), dtype=np.complex128)
+    inl = ((tag[dn] & meshes.INLET) != 0) & ((tag[dn] & meshes.WALL) == 0)
+    pts = xyz[dn[inl]]
+    for k, (w, c) in enumerate(zip(omegas, coeffs)):
+        if d == 2:
+            prof = channel_profile(pts[:, 1], w, mesh["half_height"], rho, mu, G)
+        else:
+            r = np.hypot(pts[:, 1], pts[:, 2])
+            prof = pipe_profile(r, w, mesh["radius"], rho, mu, G)
+        g[k, inl, 0] = c * prof
+    return dn, g
+
+
+def channel_workload(nx=32, ny=8, n_modes=8, rho=1.0, mu=0.01, period=1.0, G=1.0):
+    """Womersley channel [0,4]x[-0.5,0.5], c_k = 1 for all modes."""
+    mesh = meshes.channel2d(nx, ny)
+    omegas = 2.0 * np.pi * np.arange(n_modes) / period
+    coeffs = np.ones(n_modes, dtype=np.complex128)
+    dn, g = _inlet_values(mesh, omegas, coeffs, rho, mu, G)
+    return dict(mesh=mesh, rho=rho, mu=mu, period=period, G=G, omegas=omegas,
+                coeffs=coeffs, dir_nodes=dn, g=g, name=f"womersley channel {nx}x{ny}, {n_modes} modes")
+
+
+# viscosity that puts the pipe's Womersley numbers W_k = omega_k R^2 rho/mu at
+# 20 k / 31, i.e. in [0.65, 20] for k = 1..31 with R = rho = T = 1
+PIPE_MU = 2.0 * np.pi * 31.0 / 20.0
+
+
+def pipe_workload(n_c=8, n_r=6, n_x=71, n_modes=32, radius=1.0, length=10.0, rho=1.0,
+                  mu=PIPE_MU, period=1.0, G=1.0, jitter=0.05, seed=0, stenosis=0.0):
+    """Jittered O-grid pipe; c_k = k^-2 exp(j phi_k) with seeded phases."""
+    mesh = meshes.pipe3d(radius=radius, length=length, n_c=n_c, n_r=n_r, n_x=n_x,
+                         jitter=jitter, seed=seed, stenosis=stenosis)
+    omegas = 2.0 * np.pi * np.arange(n_modes) / period
+    coeffs = phases(n_modes, seed)
+    dn, g = _inlet_values(mesh, omegas, coeffs, rho, mu, G)
+    return dict(mesh=mesh, rho=rho, mu=mu, period=period, G=G, omegas=omegas,
+                coeffs=coeffs, dir_nodes=dn, g=g,
+                name=f"womersley pipe N={mesh['xyz'].shape[0]}, {n_modes} modes")
+
+
+def exact_nodal(wl, k):
+    """Analytic (u, p) of mode k at the nodes: velocity [N][d], pressure [P].
+
+    Valid for the straight channel; for the pipe it is the continuum solution
+    (the polygonal wall makes the FE solution differ at O(h^2..h^3))."""
+    mesh = wl["mesh"]
+    xyz = mesh["xyz"]
+    d = mesh["dim"]
+    w, c = wl["omegas"][k], wl["coeffs"][k]
+    u = np.zeros((xyz.shape[0], d), dtype=np.complex128)
+    if d == 2:
+        u[:, 0] = c * channel_profile(xyz[:, 1], w, mesh["half_height"], wl["rho"], wl["mu"], wl["G"])
+    else:
+        r = np.hypot(xyz[:, 1], xyz[:, 2])
+        u[:, 0] = c * pipe_profile(r, w, mesh["radius"], wl["rho"], wl["mu"], wl["G"])
+    P = mesh["n_vertices"]
+    p = c * wl["G"] * (mesh["length"] - xyz[:P, 0]) + 0j
+    return u, p
+
+
+def random_block(n_dofs, n_modes, seed, dtype=np.complex128):
+    """Seeded complex test block [n_dofs][n_modes] with entries ~ U(-1,1)+jU(-1,1)."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-1, 1, size=(n_dofs, n_modes)) + 1j * rng.uniform(-1, 1, size=(n_dofs, n_modes))
+    return x.astype(dtype)
