@@ -1,0 +1,225 @@
+/*
+ * scvs.h - C ABI of a GB300 (sm_103a) solver for the spatio-spectral complex
+ * Stokes method (SCVS) of Meng, Bhattacharjee & Esmaily, arXiv 2009.06725.
+ *
+ * A time-periodic creeping flow is expanded in Fourier modes
+ * u = sum_k u_k e^{j omega_k t} (Eq. vaptransform); every mode k is the
+ * independent complex boundary-value problem
+ *     j omega_k rho u_k = -grad p_k + div(mu grad u_k),  div u_k = 0
+ * (Eq. stokes_complex), discretised with unstabilised P2-P1 Taylor-Hood
+ * Galerkin elements (Sec. 2.3) into
+ *     A(omega_k) X_k = R_k,  A = [I_d (x) (mu K_s + j omega_k rho M_s), D; D^T, 0]
+ * (Eqs. linear_sys, linear_sys_def, LS_construction).  This library builds the
+ * sparsity pattern and the mode-independent real matrices once per mesh,
+ * then solves all modes of a mesh together on one GPU and reconstructs the
+ * time-domain field (Eq. sol_reconstruct).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: SCVS_OK (0) or a negative SCVS_ERR_* code; the message of
+ *    the last failure is returned by scvs_last_error().
+ *  - Host pointers are caller-owned; they are read or written during the call
+ *    only and never retained.  Entry points named *_dev take device pointers
+ *    (caller-owned, on the context's device) and work on the context's stream
+ *    without host<->device copies.
+ *  - Complex values are (re, im) pairs: scvs_c64 on the host, double2 / float2
+ *    on the device.
+ *  - Mesh arrays: xyz double [n_nodes][dim]; conn int32 [n_elem][6 or 10] in
+ *    VTK quadratic-simplex order (vertices, then edge nodes (0,1),(1,2),(2,0)
+ *    [, (0,3),(1,3),(2,3)]); vertex nodes are numbered first, so node ids
+ *    0..n_vertices-1 are the P1 pressure dofs; tag uint8 [n_nodes] with bits
+ *    SCVS_TAG_WALL / _INLET / _OUTLET.  A node tagged WALL or INLET is a
+ *    Dirichlet node (all velocity components prescribed); the remaining
+ *    boundary is traction-free (Eq. steady_stokes with h = 0).
+ *  - Dof ordering of one mode: velocity dof (node*dim + c), then the pressure
+ *    dof of every vertex.  Device vectors hold every mode of a mesh
+ *    interleaved: element (dof, k) at dof*ld + k with ld = scvs_mode_stride().
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef SCVS_H
+#define SCVS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define SCVS_OK 0
+#define SCVS_ERR_ARG (-1)                /* bad argument / size / pointer */
+#define SCVS_ERR_MESH (-2)               /* degenerate or inverted element, bad connectivity */
+#define SCVS_ERR_PRESSURE_NULLSPACE (-3) /* no traction-free boundary: pressure undetermined */
+#define SCVS_ERR_OOM (-4)                /* device allocation failed */
+#define SCVS_ERR_CUDA (-5)               /* a CUDA call failed */
+#define SCVS_ERR_STATE (-6)              /* call out of order (e.g. solve before set_modes) */
+#define SCVS_ERR_TIMEOUT (-7)            /* a bounded device-side wait gave up */
+
+/* ---- node tags --------------------------------------------------------- */
+#define SCVS_TAG_WALL 1
+#define SCVS_TAG_INLET 2
+#define SCVS_TAG_OUTLET 4
+
+/* ---- per-mode solve status (scvs_mode_report.status) -------------------- */
+#define SCVS_CONVERGED 0  /* FP64 ||b - A x|| / ||b|| <= tol */
+#define SCVS_MAX_ITER 1   /* cycle cap reached */
+#define SCVS_STAGNATED 2  /* residual stopped decreasing */
+#define SCVS_NON_FINITE 3 /* NaN/Inf met in this mode; other modes unaffected */
+
+/* ---- options ----------------------------------------------------------- */
+#define SCVS_PREC_MIXED 0 /* FP32 complex GMRES cycles inside FP64 refinement */
+#define SCVS_PREC_FP64 1  /* all-FP64 GMRES */
+
+#define SCVS_PC_BLOCK_CHEB 0   /* block-diagonal: Chebyshev-Jacobi polynomial of mu K + |omega| rho M for the
+                                  velocity, Chebyshev Cahouet-Chabard mu M_p^-1 + j omega rho L_p^-1 for the pressure */
+#define SCVS_PC_BLOCK_DIAG 1   /* block-diagonal, diagonal blocks only */
+
+#define SCVS_GUESS_ZERO 0
+#define SCVS_GUESS_MLP 1
+
+typedef struct scvs_ctx scvs_ctx;
+typedef struct { double re, im; } scvs_c64;
+
+typedef struct {
+  double tol;        /* relative residual target per mode (default 1e-8) */
+  int32_t restart;   /* GMRES restart length m_r (default 30, max 64) */
+  int32_t precision; /* SCVS_PREC_* (default MIXED) */
+  int32_t precond;   /* SCVS_PC_* (default BLOCK_CHEB) */
+  int32_t cheb_u;    /* Chebyshev degree, velocity block (default 8) */
+  int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
+  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 30) */
+  int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
+  int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
+  int32_t verbose;   /* 0 = silent */
+  void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+} scvs_opts;
+
+/* Result of one mode of one mesh after scvs_solve. */
+typedef struct {
+  int32_t status;     /* SCVS_CONVERGED / MAX_ITER / STAGNATED / NON_FINITE */
+  int32_t iterations; /* Arnoldi steps spent on this mode */
+  int32_t cycles;     /* restart cycles (= FP64 refinement steps) */
+  int32_t reserved;
+  double rel_res;     /* final FP64 ||b_F - A_FF x_F - A_FD g|| / ||b_F|| (Eq. ls_error) */
+} scvs_mode_report;
+
+/* Fill *opts with the defaults listed above. */
+void scvs_default_opts(scvs_opts *opts);
+
+/* Create a context on the current CUDA device.  opts may be NULL (defaults).
+ * Owns every device buffer it allocates; released by scvs_destroy. */
+int scvs_create(scvs_ctx **out, const scvs_opts *opts);
+void scvs_destroy(scvs_ctx *ctx);
+const char *scvs_last_error(const scvs_ctx *ctx);
+int scvs_set_opts(scvs_ctx *ctx, const scvs_opts *opts);
+
+/* Add a P2 mesh (Sec. 2.3; conventions above) and build, on the GPU, its CSR
+ * sparsity patterns (S: P2xP2, G: P2xP1, G^T) and the real mode-independent
+ * matrices M_s, K_s, D_c of Eq. LS_construction plus the P1 pressure mass and
+ * Laplacian used by the preconditioner.  Returns the mesh id (>= 0) or an
+ * error (SCVS_ERR_MESH for a non-positive element Jacobian or a node id out
+ * of range, SCVS_ERR_PRESSURE_NULLSPACE if no node is tagged OUTLET). */
+int scvs_set_mesh(scvs_ctx *ctx, int32_t dim, int64_t n_nodes, int64_t n_vertices,
+                  const double *xyz, int64_t n_elem, const int32_t *conn, const uint8_t *tag);
+/* Same, with xyz/conn/tag already in device memory. */
+int scvs_set_mesh_dev(scvs_ctx *ctx, int32_t dim, int64_t n_nodes, int64_t n_vertices,
+                      const double *xyz_dev, int64_t n_elem, const int32_t *conn_dev,
+                      const uint8_t *tag_dev);
+/* Drop every mesh (and its modes) from the context. */
+int scvs_clear_meshes(scvs_ctx *ctx);
+
+/* Physical constants rho, mu of a mesh (Eq. stokes_complex); defaults 1, 1. */
+int scvs_set_physics(scvs_ctx *ctx, int32_t mesh_id, double rho, double mu);
+
+/* Number of Dirichlet nodes of a mesh (nodes tagged WALL or INLET). */
+int scvs_dirichlet_count(scvs_ctx *ctx, int32_t mesh_id, int64_t *n_dir);
+
+/* Modes to solve on a mesh: omega[n_modes] and the prescribed velocity
+ * g[n_modes][n_dir][dim] on the Dirichlet nodes in ascending node id
+ * (Eq. dir_dis).  Builds the lifted right-hand sides (Eq. LS_construction:
+ * B = -K G for the momentum rows and -D^T G for the continuity rows) and the
+ * per-mode preconditioner.  Neumann data are zero (traction-free). */
+int scvs_set_modes(scvs_ctx *ctx, int32_t mesh_id, int32_t n_modes, const double *omega,
+                   const scvs_c64 *g);
+int scvs_set_modes_dev(scvs_ctx *ctx, int32_t mesh_id, int32_t n_modes, const double *omega,
+                       const void *g_dev /* double2 [n_modes][n_dir][dim] */);
+
+/* Solve every mode of every mesh (mesh_id = -1) or of one mesh.  rep (host,
+ * may be NULL) receives one entry per (mesh, mode) in mesh order, rep_len
+ * entries at most.  Returns SCVS_OK even if some modes did not converge;
+ * their status says so. */
+int scvs_solve(scvs_ctx *ctx, int32_t mesh_id, scvs_mode_report *rep, int64_t rep_len);
+
+/* Modal solution of a mesh: u[n_modes][n_nodes][dim], p[n_modes][n_vertices]
+ * (host, either may be NULL). */
+int scvs_get_modal(scvs_ctx *ctx, int32_t mesh_id, scvs_c64 *u, scvs_c64 *p);
+/* Device view of the FP64 modal solution, interleaved [n_dof][ld] double2. */
+int scvs_modal_dev(scvs_ctx *ctx, int32_t mesh_id, const void **x_dev, int64_t *n_dof, int32_t *ld);
+
+/* Time reconstruction (Eq. sol_reconstruct, real fields):
+ * u(x,t_s) = Re sum_k u_k(x) e^{j omega_k t_s}, t_s = s*period/n_t,
+ * u_t[n_t][n_nodes][dim], p_t[n_t][n_vertices] (host; either may be NULL). */
+int scvs_reconstruct(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
+                     double *u_t, double *p_t);
+int scvs_reconstruct_dev(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
+                         double *u_t_dev, double *p_t_dev);
+
+/* ---- parity / inspection ------------------------------------------------ */
+#define SCVS_CSR_S 0  /* P2 x P2 scalar pattern (values M_s, K_s) */
+#define SCVS_CSR_G 1  /* P2 rows x P1 columns (values D_c) */
+#define SCVS_CSR_GT 2 /* P1 rows x P2 columns (values D_c^T) */
+#define SCVS_CSR_Q 3  /* P1 x P1 (values: P1 mass, P1 Laplacian) */
+
+/* Rows and nonzeros of one pattern. */
+int scvs_csr_size(scvs_ctx *ctx, int32_t mesh_id, int32_t which, int64_t *n_rows, int64_t *nnz);
+/* Copy a pattern to the host: rowptr int64[n_rows+1], col int32[nnz]. */
+int scvs_get_csr(scvs_ctx *ctx, int32_t mesh_id, int32_t which, int64_t *rowptr, int32_t *col);
+/* Copy FP64 values to the host, in pattern order: S -> [2][nnz] (M_s, K_s);
+ * G and GT -> [dim][nnz] (D_c resp. D_c^T); Q -> [2][nnz] (P1 mass, P1 Laplacian). */
+int scvs_get_values(scvs_ctx *ctx, int32_t mesh_id, int32_t which, double *vals);
+
+/* Row stride ld of the interleaved mode blocks of a mesh (>= n_modes). */
+int scvs_mode_stride(scvs_ctx *ctx, int32_t mesh_id, int32_t *ld);
+/* Degrees of freedom per mode, dim*n_nodes + n_vertices. */
+int scvs_dof_count(scvs_ctx *ctx, int32_t mesh_id, int64_t *n_dof);
+
+/* y_k = A_hat(omega_k) x_k for every mode k of a mesh, in one all-modes SpMM:
+ * A_hat is A(omega_k) with Dirichlet velocity rows replaced by identity rows
+ * and Dirichlet columns removed (the operator the Krylov solver iterates on).
+ * precision SCVS_PREC_MIXED: x, y float2 [n_dof][ld]; SCVS_PREC_FP64: double2.
+ * Device pointers, caller-owned, on the context's stream. */
+int scvs_apply(scvs_ctx *ctx, int32_t mesh_id, int32_t precision, const void *x_dev, void *y_dev);
+/* Same operator evaluated element by element (matrix-free): gathers each
+ * element's nodal block for all modes and contracts it with the element
+ * matrices; same layouts and precisions as scvs_apply. */
+int scvs_apply_matfree(scvs_ctx *ctx, int32_t mesh_id, int32_t precision, const void *x_dev, void *y_dev);
+/* Lifted right-hand side of every mode, FP64 double2 [n_dof][ld] (device view):
+ * b_F = -A_FD g on free rows, b_D = g on Dirichlet rows. */
+int scvs_rhs_dev(scvs_ctx *ctx, int32_t mesh_id, const void **b_dev);
+/* Apply the block preconditioner P^{-1}(omega_k) of every mode:
+ * z = P^{-1} r, FP32 float2 [n_dof][ld] device arrays. */
+int scvs_apply_precond(scvs_ctx *ctx, int32_t mesh_id, const void *r_dev, void *z_dev);
+
+/* Number of kernel launches issued by this context since creation. */
+int64_t scvs_launch_count(const scvs_ctx *ctx);
+
+/* ---- tracing ------------------------------------------------------------
+ * Optional CUDA-event timers around every kernel launch, recorded on the
+ * context's stream, grouped in classes:
+ *   0 all-modes SpMM FP32, 1 all-modes SpMM FP64 (lift, true residual),
+ *   2 block preconditioner, 3 Arnoldi orthogonalisation + Hessenberg,
+ *   4 elementwise vector kernels, 5 pattern/assembly, 6 reconstruction,
+ *   7 matrix-free apply.
+ * Each class also sums the algorithmic bytes of its launches (the data the
+ * kernel must read and write at minimum: matrix values and indices once,
+ * every vector operand once).  scvs_kernel_timers(ctx, 1) clears and enables,
+ * (ctx, 0) clears and disables.  scvs_kernel_times fills up to n_classes
+ * entries of ms (summed device time), bytes and launches (any may be NULL)
+ * and returns the number of classes. */
+#define SCVS_KC_COUNT 8
+int scvs_kernel_timers(scvs_ctx *ctx, int32_t enable);
+int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *bytes, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCVS_H */

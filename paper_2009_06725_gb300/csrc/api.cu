@@ -1,0 +1,560 @@
+// C ABI of the SCVS library: argument checking, error mapping, host <-> device
+// marshalling.  Every computation runs in the kernels of assembly.cu,
+// operators.cu, krylov.cu and recon.cu.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+#include "scvs_internal.h"
+
+using namespace scvs;
+
+struct scvs_ctx : public Ctx {};
+
+namespace scvs {
+void KTimers::begin(cudaStream_t s) {
+  if (pool.empty()) {
+    cudaEvent_t a, b;
+    SCVS_CUDA(cudaEventCreate(&a));
+    SCVS_CUDA(cudaEventCreate(&b));
+    pool.push_back({a, b});
+  }
+  cur_a = pool.back().first;
+  SCVS_CUDA(cudaEventRecord(cur_a, s));
+}
+void KTimers::end(cudaStream_t s, int cls, double nbytes) {
+  auto pr = pool.back();
+  pool.pop_back();
+  SCVS_CUDA(cudaEventRecord(pr.second, s));
+  pend.push_back({pr.first, pr.second, cls, nbytes});
+  if (pend.size() > 4096) resolve();
+}
+void KTimers::resolve() {
+  for (auto &p : pend) {
+    SCVS_CUDA(cudaEventSynchronize(p.b));
+    float t = 0;
+    SCVS_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+    ms[p.cls] += t;
+    bytes[p.cls] += p.bytes;
+    n[p.cls] += 1;
+    pool.push_back({p.a, p.b});
+  }
+  pend.clear();
+}
+void KTimers::reset() {
+  resolve();
+  for (int i = 0; i < KC_COUNT; ++i) { ms[i] = 0; bytes[i] = 0; n[i] = 0; }
+}
+void KTimers::destroy() {
+  for (auto &p : pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto &p : pool) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+  pend.clear();
+  pool.clear();
+}
+
+int dev_error(Ctx &c) {
+  int e = 0;
+  SCVS_CUDA(cudaMemcpyAsync(&e, c.dev_err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  if (e) SCVS_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), c.stream));
+  return e;
+}
+}  // namespace scvs
+
+namespace {
+
+std::string deverr_text(int bits) {
+  std::string s;
+  if (bits & DEVERR_BAD_NODE) s += "connectivity entry outside [0, n_nodes) or node unused; ";
+  if (bits & DEVERR_BAD_VERTEX) s += "simplex vertex id >= n_vertices or edge node id < n_vertices; ";
+  if (bits & DEVERR_JACOBIAN) s += "element with non-positive Jacobian; ";
+  if (bits & DEVERR_VALENCE) s += "too many elements around one node; ";
+  if (bits & DEVERR_BARRIER) s += "grid barrier timeout; ";
+  if (bits & DEVERR_DUP_NODE) s += "element lists a node twice; ";
+  return s;
+}
+
+template <typename F>
+int guarded(scvs_ctx *c, F &&f) {
+  if (!c) return SCVS_ERR_ARG;
+  try {
+    int r = f();
+    if (r == SCVS_OK || r >= 0) c->err.clear();
+    return r;
+  } catch (const CudaError &e) {
+    c->err = std::string("CUDA error ") + cudaGetErrorString(e.code) + " in " + e.where;
+    (void)cudaGetLastError();
+    return SCVS_ERR_CUDA;
+  } catch (const std::bad_alloc &) {
+    c->err = "device allocation failed";
+    return SCVS_ERR_OOM;
+  } catch (int code) {
+    if (code < 0) {
+      if (c->err.empty()) c->err = "error " + std::to_string(code);
+      return code;
+    }
+    c->err = "invalid mesh: " + deverr_text(code);
+    return (code & DEVERR_BARRIER) ? SCVS_ERR_TIMEOUT : SCVS_ERR_MESH;
+  }
+}
+
+int fail(scvs_ctx *c, int code, const std::string &msg) {
+  c->err = msg;
+  return code;
+}
+
+Mesh *get_mesh(scvs_ctx *c, int id) {
+  if (id < 0 || id >= (int)c->meshes.size() || !c->meshes[id]) return nullptr;
+  return c->meshes[id];
+}
+
+int mode_stride(int m) {
+  int ld = 2;
+  while (ld < m) ld <<= 1;
+  return ld;
+}
+
+int add_mesh(scvs_ctx *c, int dim, int64_t N, int64_t P, const double *xyz, int64_t E, const int32_t *conn,
+             const uint8_t *tag, bool on_device) {
+  if (dim != 2 && dim != 3) return fail(c, SCVS_ERR_ARG, "dim must be 2 or 3");
+  if (N <= 0 || P <= 0 || P > N || E <= 0) return fail(c, SCVS_ERR_ARG, "bad mesh sizes");
+  if (N >= INT32_MAX || E * (dim == 2 ? 6 : 10) >= INT32_MAX) return fail(c, SCVS_ERR_ARG, "mesh too large for int32 ids");
+  if (!xyz || !conn || !tag) return fail(c, SCVS_ERR_ARG, "null mesh array");
+  std::vector<uint8_t> htag(N);
+  SCVS_CUDA(cudaMemcpy(htag.data(), tag, N, on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  std::vector<int64_t> dn;
+  int64_t n_out = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    if (htag[i] & (SCVS_TAG_WALL | SCVS_TAG_INLET)) dn.push_back(i);
+    if (i < P && (htag[i] & SCVS_TAG_OUTLET)) ++n_out;
+  }
+  if (n_out == 0)
+    return fail(c, SCVS_ERR_PRESSURE_NULLSPACE,
+                "no vertex tagged OUTLET: with velocity prescribed on the whole boundary the pressure is undetermined");
+  Mesh *m = new Mesh();
+  m->dim = dim;
+  m->nl = dim == 2 ? 6 : 10;
+  m->nv = dim + 1;
+  m->N = N; m->P = P; m->E = E;
+  m->n_dof = (int64_t)dim * N + P;
+  m->n_dir = (int64_t)dn.size();
+  try {
+    build_mesh(*c, *m, xyz, conn, tag);
+    m->dir_nodes = m->arena.alloc<int64_t>(std::max<int64_t>(1, m->n_dir));
+    if (m->n_dir)
+      SCVS_CUDA(cudaMemcpy(m->dir_nodes, dn.data(), m->n_dir * sizeof(int64_t), cudaMemcpyHostToDevice));
+  } catch (...) {
+    m->arena.release();
+    delete m;
+    throw;
+  }
+  c->meshes.push_back(m);
+  return (int)c->meshes.size() - 1;
+}
+
+int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const void *g, bool on_device) {
+  Mesh *m = get_mesh(c, mesh_id);
+  if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+  if (n_modes < 1 || n_modes > 128) return fail(c, SCVS_ERR_ARG, "n_modes must be in [1, 128]");
+  if (!omega || (!g && m->n_dir > 0)) return fail(c, SCVS_ERR_ARG, "null omega or g");
+  m->mode_arena.release();
+  m->pc = PcTables{};
+  m->solved = false;
+  m->m = n_modes;
+  m->ld = mode_stride(n_modes);
+  m->omega.assign(m->ld, 0.0);
+  for (int k = 0; k < n_modes; ++k) m->omega[k] = omega[k];
+  m->omega_d = m->mode_arena.alloc<double>(m->ld);
+  SCVS_CUDA(cudaMemcpyAsync(m->omega_d, m->omega.data(), m->ld * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const int64_t gcount = (int64_t)n_modes * m->n_dir * m->dim;
+  m->g = m->mode_arena.alloc<double2>(std::max<int64_t>(1, gcount));
+  if (gcount)
+    SCVS_CUDA(cudaMemcpyAsync(m->g, g, gcount * sizeof(double2), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+  const int64_t total = m->n_dof * m->ld;
+  m->b = m->mode_arena.alloc<double2>(total);
+  m->x = m->mode_arena.alloc<double2>(total);
+  SCVS_CUDA(cudaMemsetAsync(m->x, 0, total * sizeof(double2), c->stream));
+  lift_rhs(*c, *m);
+  spectral_bounds(*c, *m);
+  return SCVS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void scvs_default_opts(scvs_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->restart = 30;
+  o->precision = SCVS_PREC_MIXED;
+  o->precond = SCVS_PC_BLOCK_CHEB;
+  o->cheb_u = 8;
+  o->cheb_m = 4;
+  o->cheb_l = 30;
+  o->max_cycles = 400;
+  o->guess = SCVS_GUESS_ZERO;
+  o->verbose = 0;
+  o->stream = nullptr;
+}
+
+int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
+  if (!out) return SCVS_ERR_ARG;
+  *out = nullptr;
+  scvs_ctx *c = new (std::nothrow) scvs_ctx();
+  if (!c) return SCVS_ERR_OOM;
+  if (opts) c->opts = *opts; else scvs_default_opts(&c->opts);
+  int r = guarded(c, [&]() {
+    SCVS_CUDA(cudaGetDevice(&c->device));
+    SCVS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    c->stream = static_cast<cudaStream_t>(c->opts.stream);
+    c->dev_err = c->work.alloc<int>(1);
+    c->gsync = c->work.alloc<GridSync>(1);
+    SCVS_CUDA(cudaMemset(c->dev_err, 0, sizeof(int)));
+    SCVS_CUDA(cudaMemset(c->gsync, 0, sizeof(GridSync)));
+    reference_tables(2, &c->ref2);
+    reference_tables(3, &c->ref3);
+    matfree_tables(*c);
+    return SCVS_OK;
+  });
+  if (r != SCVS_OK) {
+    c->work.release();
+    delete c;
+    return r;
+  }
+  *out = c;
+  return SCVS_OK;
+}
+
+void scvs_destroy(scvs_ctx *c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  for (Mesh *m : c->meshes) {
+    if (!m) continue;
+    m->mode_arena.release();
+    m->arena.release();
+    delete m;
+  }
+  c->timers.destroy();
+  c->work.release();
+  delete c;
+}
+
+const char *scvs_last_error(const scvs_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
+  if (!c || !o) return SCVS_ERR_ARG;
+  if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
+      o->max_cycles < 1)
+    return fail(c, SCVS_ERR_ARG, "invalid options");
+  void *old_stream = c->opts.stream;
+  c->opts = *o;
+  if (o->stream != old_stream) c->stream = static_cast<cudaStream_t>(o->stream);
+  return SCVS_OK;
+}
+
+int scvs_set_mesh(scvs_ctx *c, int32_t dim, int64_t N, int64_t P, const double *xyz, int64_t E, const int32_t *conn,
+                  const uint8_t *tag) {
+  return guarded(c, [&]() { return add_mesh(c, dim, N, P, xyz, E, conn, tag, false); });
+}
+
+int scvs_set_mesh_dev(scvs_ctx *c, int32_t dim, int64_t N, int64_t P, const double *xyz, int64_t E,
+                      const int32_t *conn, const uint8_t *tag) {
+  return guarded(c, [&]() { return add_mesh(c, dim, N, P, xyz, E, conn, tag, true); });
+}
+
+int scvs_clear_meshes(scvs_ctx *c) {
+  return guarded(c, [&]() {
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    for (Mesh *m : c->meshes) {
+      if (!m) continue;
+      m->mode_arena.release();
+      m->arena.release();
+      delete m;
+    }
+    c->meshes.clear();
+    return SCVS_OK;
+  });
+}
+
+int scvs_set_physics(scvs_ctx *c, int32_t mesh_id, double rho, double mu) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    if (!(rho > 0) || !(mu > 0)) return fail(c, SCVS_ERR_ARG, "rho and mu must be positive");
+    m->rho = rho;
+    m->mu = mu;
+    if (m->m > 0) {  // modes already set: rebuild what depends on rho, mu
+      m->pc = PcTables{};
+      m->solved = false;
+      lift_rhs(*c, *m);
+      spectral_bounds(*c, *m);
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_dirichlet_count(scvs_ctx *c, int32_t mesh_id, int64_t *n) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !n) return fail(c, SCVS_ERR_ARG, "bad argument");
+    *n = m->n_dir;
+    return SCVS_OK;
+  });
+}
+
+int scvs_set_modes(scvs_ctx *c, int32_t mesh_id, int32_t n_modes, const double *omega, const scvs_c64 *g) {
+  return guarded(c, [&]() { return set_modes(c, mesh_id, n_modes, omega, g, false); });
+}
+
+int scvs_set_modes_dev(scvs_ctx *c, int32_t mesh_id, int32_t n_modes, const double *omega, const void *g) {
+  return guarded(c, [&]() { return set_modes(c, mesh_id, n_modes, omega, g, true); });
+}
+
+int scvs_solve(scvs_ctx *c, int32_t mesh_id, scvs_mode_report *rep, int64_t rep_len) {
+  return guarded(c, [&]() {
+    std::vector<Mesh *> todo;
+    if (mesh_id < 0) {
+      for (Mesh *m : c->meshes) if (m) todo.push_back(m);
+    } else {
+      Mesh *m = get_mesh(c, mesh_id);
+      if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+      todo.push_back(m);
+    }
+    for (Mesh *m : todo)
+      if (m->m == 0) return fail(c, SCVS_ERR_STATE, "scvs_set_modes must precede scvs_solve");
+    int64_t pos = 0;
+    for (Mesh *m : todo) {
+      int r = solve_mesh(*c, *m);
+      if (r != SCVS_OK) return fail(c, r, r == SCVS_ERR_TIMEOUT ? "a device grid barrier timed out" : "solve failed");
+      m->solved = true;
+      for (int k = 0; k < m->m; ++k, ++pos)
+        if (rep && pos < rep_len) rep[pos] = m->rep[k];
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_get_modal(scvs_ctx *c, int32_t mesh_id, scvs_c64 *u, scvs_c64 *p) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    std::vector<double2> h((size_t)m->n_dof * m->ld);
+    SCVS_CUDA(cudaMemcpyAsync(h.data(), m->x, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t nu = (int64_t)m->dim * m->N;
+    for (int k = 0; k < m->m; ++k) {
+      if (u)
+        for (int64_t d = 0; d < nu; ++d) {
+          double2 v = h[(size_t)d * m->ld + k];
+          u[(size_t)k * nu + d] = scvs_c64{v.x, v.y};
+        }
+      if (p)
+        for (int64_t v = 0; v < m->P; ++v) {
+          double2 z = h[(size_t)(nu + v) * m->ld + k];
+          p[(size_t)k * m->P + v] = scvs_c64{z.x, z.y};
+        }
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_modal_dev(scvs_ctx *c, int32_t mesh_id, const void **x, int64_t *n_dof, int32_t *ld) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    if (x) *x = m->x;
+    if (n_dof) *n_dof = m->n_dof;
+    if (ld) *ld = m->ld;
+    return SCVS_OK;
+  });
+}
+
+int scvs_reconstruct_dev(scvs_ctx *c, int32_t mesh_id, int32_t n_t, double period, double *u_t, double *p_t) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    if (n_t < 1 || !(period > 0)) return fail(c, SCVS_ERR_ARG, "n_t >= 1 and period > 0 required");
+    reconstruct(*c, *m, n_t, period, u_t, p_t);
+    return SCVS_OK;
+  });
+}
+
+int scvs_reconstruct(scvs_ctx *c, int32_t mesh_id, int32_t n_t, double period, double *u_t, double *p_t) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    if (n_t < 1 || !(period > 0)) return fail(c, SCVS_ERR_ARG, "n_t >= 1 and period > 0 required");
+    const int64_t nu = (int64_t)n_t * m->dim * m->N, np = (int64_t)n_t * m->P;
+    double *du = nullptr, *dp = nullptr;
+    if (u_t) SCVS_CUDA(cudaMallocAsync(&du, nu * sizeof(double), c->stream));
+    if (p_t) SCVS_CUDA(cudaMallocAsync(&dp, np * sizeof(double), c->stream));
+    reconstruct(*c, *m, n_t, period, du, dp);
+    if (u_t) SCVS_CUDA(cudaMemcpyAsync(u_t, du, nu * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (p_t) SCVS_CUDA(cudaMemcpyAsync(p_t, dp, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (du) SCVS_CUDA(cudaFreeAsync(du, c->stream));
+    if (dp) SCVS_CUDA(cudaFreeAsync(dp, c->stream));
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    return SCVS_OK;
+  });
+}
+
+int scvs_csr_size(scvs_ctx *c, int32_t mesh_id, int32_t which, int64_t *n_rows, int64_t *nnz) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    int64_t r, z;
+    switch (which) {
+      case SCVS_CSR_S: r = m->N; z = m->s_nnz; break;
+      case SCVS_CSR_G: r = m->N; z = m->g_nnz; break;
+      case SCVS_CSR_GT: r = m->P; z = m->gt_nnz; break;
+      case SCVS_CSR_Q: r = m->P; z = m->q_nnz; break;
+      default: return fail(c, SCVS_ERR_ARG, "bad pattern id");
+    }
+    if (n_rows) *n_rows = r;
+    if (nnz) *nnz = z;
+    return SCVS_OK;
+  });
+}
+
+int scvs_get_csr(scvs_ctx *c, int32_t mesh_id, int32_t which, int64_t *rowptr, int32_t *col) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !rowptr || !col) return fail(c, SCVS_ERR_ARG, "bad argument");
+    std::vector<int64_t> sp(m->N + 1), gp(m->N + 1);
+    std::vector<int32_t> sc(m->s_nnz);
+    SCVS_CUDA(cudaMemcpy(sp.data(), m->s_ptr, sp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    SCVS_CUDA(cudaMemcpy(gp.data(), m->g_ptr, gp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    SCVS_CUDA(cudaMemcpy(sc.data(), m->s_col, sc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    // S rows hold, in this order, the G part (columns < P) and the rest
+    auto emit = [&](int64_t rows, bool g_part) {
+      int64_t pos = 0;
+      for (int64_t r = 0; r < rows; ++r) {
+        rowptr[r] = pos;
+        int64_t len = g_part ? gp[r + 1] - gp[r] : sp[r + 1] - sp[r];
+        std::memcpy(col + pos, sc.data() + sp[r], len * sizeof(int32_t));
+        pos += len;
+      }
+      rowptr[rows] = pos;
+    };
+    switch (which) {
+      case SCVS_CSR_S: emit(m->N, false); break;
+      case SCVS_CSR_G: emit(m->N, true); break;
+      case SCVS_CSR_GT: emit(m->P, false); break;
+      case SCVS_CSR_Q: emit(m->P, true); break;
+      default: return fail(c, SCVS_ERR_ARG, "bad pattern id");
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_get_values(scvs_ctx *c, int32_t mesh_id, int32_t which, double *vals) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !vals) return fail(c, SCVS_ERR_ARG, "bad argument");
+    auto cp = [&](double *dst, const double *src, int64_t n) {
+      SCVS_CUDA(cudaMemcpy(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost));
+    };
+    switch (which) {
+      case SCVS_CSR_S: cp(vals, m->Ms, m->s_nnz); cp(vals + m->s_nnz, m->Ks, m->s_nnz); break;
+      case SCVS_CSR_G: cp(vals, m->Dv, (int64_t)m->dim * m->g_nnz); break;
+      case SCVS_CSR_GT: cp(vals, m->DTv, (int64_t)m->dim * m->gt_nnz); break;
+      case SCVS_CSR_Q: cp(vals, m->Mp, m->q_nnz); cp(vals + m->q_nnz, m->Lp, m->q_nnz); break;
+      default: return fail(c, SCVS_ERR_ARG, "bad pattern id");
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_mode_stride(scvs_ctx *c, int32_t mesh_id, int32_t *ld) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !ld || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    *ld = m->ld;
+    return SCVS_OK;
+  });
+}
+
+int scvs_dof_count(scvs_ctx *c, int32_t mesh_id, int64_t *n) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !n) return fail(c, SCVS_ERR_ARG, "bad argument");
+    *n = m->n_dof;
+    return SCVS_OK;
+  });
+}
+
+int scvs_apply(scvs_ctx *c, int32_t mesh_id, int32_t precision, const void *x, void *y) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0 || !x || !y) return fail(c, SCVS_ERR_ARG, "bad argument");
+    if (precision == SCVS_PREC_FP64)
+      apply_saddle<double>(*c, *m, static_cast<const double2 *>(x), static_cast<double2 *>(y));
+    else if (precision == SCVS_PREC_MIXED)
+      apply_saddle<float>(*c, *m, static_cast<const float2 *>(x), static_cast<float2 *>(y));
+    else
+      return fail(c, SCVS_ERR_ARG, "bad precision");
+    SCVS_CUDA(cudaGetLastError());
+    return SCVS_OK;
+  });
+}
+
+int scvs_apply_matfree(scvs_ctx *c, int32_t mesh_id, int32_t precision, const void *x, void *y) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0 || !x || !y) return fail(c, SCVS_ERR_ARG, "bad argument");
+    if (precision != SCVS_PREC_FP64 && precision != SCVS_PREC_MIXED) return fail(c, SCVS_ERR_ARG, "bad precision");
+    apply_matfree(*c, *m, precision, x, y);
+    SCVS_CUDA(cudaGetLastError());
+    return SCVS_OK;
+  });
+}
+
+int scvs_rhs_dev(scvs_ctx *c, int32_t mesh_id, const void **b) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0 || !b) return fail(c, SCVS_ERR_ARG, "bad argument");
+    *b = m->b;
+    return SCVS_OK;
+  });
+}
+
+int scvs_apply_precond(scvs_ctx *c, int32_t mesh_id, const void *r, void *z) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0 || !r || !z) return fail(c, SCVS_ERR_ARG, "bad argument");
+    float2 *s = nullptr;
+    SCVS_CUDA(cudaMallocAsync(&s, (m->n_dof + 4 * m->P) * m->ld * sizeof(float2), c->stream));
+    apply_precond<float>(*c, *m, static_cast<const float2 *>(r), static_cast<float2 *>(z), s, nullptr);
+    SCVS_CUDA(cudaFreeAsync(s, c->stream));
+    SCVS_CUDA(cudaGetLastError());
+    return SCVS_OK;
+  });
+}
+
+int64_t scvs_launch_count(const scvs_ctx *c) { return c ? c->launches.n : -1; }
+
+int scvs_kernel_timers(scvs_ctx *c, int32_t enable) {
+  return guarded(c, [&]() {
+    c->timers.reset();
+    c->timers.on = enable != 0;
+    return SCVS_OK;
+  });
+}
+
+int scvs_kernel_times(scvs_ctx *c, int32_t n_classes, double *ms, double *bytes, int64_t *launches) {
+  return guarded(c, [&]() {
+    c->timers.resolve();
+    for (int i = 0; i < n_classes && i < KC_COUNT; ++i) {
+      if (ms) ms[i] = c->timers.ms[i];
+      if (bytes) bytes[i] = c->timers.bytes[i];
+      if (launches) launches[i] = c->timers.n[i];
+    }
+    return KC_COUNT;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,518 @@
+// GPU construction of the sparsity patterns and of the mode-independent real
+// matrices of the SCVS saddle-point system (Eqs. linear_sys_def, LS_construction).
+//
+//   1. per element: validation, affine map, det J, J^-1, gamma = det J^-1 J^-T
+//   2. node -> element incidence (count, scan, fill, per-node sort)
+//   3. S pattern, one warp per row: gather the nodes of every incident element,
+//      bitonic sort in shared memory, drop duplicates -> ascending columns
+//      (counted in a first pass, written in a second)
+//   4. values, one warp per row: incident elements in ascending id order, the
+//      lanes take the element's local columns (distinct positions), so every
+//      entry is summed in the same order on every run (deterministic)
+//   5. Dirichlet masking, FP32 copies and diagonals
+#include <algorithm>
+#include <climits>
+#include "scvs_internal.h"
+
+namespace scvs {
+
+__constant__ RefTables c_ref;
+
+// --------------------------------------------------------------- geometry
+__global__ void k_geom(const double *__restrict__ xyz, const int32_t *__restrict__ conn, int64_t E,
+                       int nl, int dim, int64_t N, int64_t P, double *__restrict__ geom, int *err) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t *c = conn + e * nl;
+  int bad = 0;
+  for (int a = 0; a < nl; ++a) {
+    int32_t v = c[a];
+    if (v < 0 || v >= N) bad |= DEVERR_BAD_NODE;
+    if (a <= dim && (v < 0 || v >= P)) bad |= DEVERR_BAD_VERTEX;
+    if (a > dim && v < P) bad |= DEVERR_BAD_VERTEX;
+    for (int b = 0; b < a; ++b)
+      if (c[b] == v) bad |= DEVERR_DUP_NODE;
+  }
+  if (bad) { atomicOr(err, bad); return; }
+  double *g = geom + e * GEOM_STRIDE;
+  double J[3][3] = {{0}};
+  for (int i = 0; i < dim; ++i)
+    for (int r = 0; r < dim; ++r) J[r][i] = xyz[(int64_t)c[i + 1] * dim + r] - xyz[(int64_t)c[0] * dim + r];
+  double det, Ji[3][3] = {{0}};
+  if (dim == 2) {
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    double id = 1.0 / det;
+    Ji[0][0] = J[1][1] * id; Ji[0][1] = -J[0][1] * id;
+    Ji[1][0] = -J[1][0] * id; Ji[1][1] = J[0][0] * id;
+  } else {
+    double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    double id = 1.0 / det;
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  }
+  if (!(det > 0.0)) { atomicOr(err, DEVERR_JACOBIAN); return; }
+  g[0] = det;
+  for (int i = 0; i < dim; ++i)
+    for (int k = 0; k < dim; ++k) g[1 + i * dim + k] = Ji[i][k];
+  int p = 0;
+  for (int i = 0; i < dim; ++i)
+    for (int j = i; j < dim; ++j, ++p) {
+      double s = 0;
+      for (int k = 0; k < dim; ++k) s += Ji[i][k] * Ji[j][k];
+      g[10 + p] = det * s;
+    }
+}
+
+// -------------------------------------------------------------- incidence
+__global__ void k_count_incidence(const int32_t *__restrict__ conn, int64_t total, int32_t *cnt) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < total) atomicAdd(&cnt[conn[t]], 1);
+}
+
+__global__ void k_fill_incidence(const int32_t *__restrict__ conn, int64_t E, int nl,
+                                 const int64_t *__restrict__ ptr, int32_t *fill, int32_t *n2e) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= E * nl) return;
+  int32_t node = conn[t];
+  int pos = atomicAdd(&fill[node], 1);
+  n2e[ptr[node] + pos] = (int32_t)(t / nl);
+}
+
+// insertion sort of every node's (short) element list
+__global__ void k_sort_incidence(const int64_t *__restrict__ ptr, int32_t *n2e, int64_t N, int *err) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  int64_t b = ptr[v], e = ptr[v + 1];
+  if (e == b) atomicOr(err, DEVERR_BAD_NODE);  // a node no element uses
+  for (int64_t i = b + 1; i < e; ++i) {
+    int32_t key = n2e[i];
+    int64_t j = i - 1;
+    while (j >= b && n2e[j] > key) { n2e[j + 1] = n2e[j]; --j; }
+    n2e[j + 1] = key;
+  }
+}
+
+// ---------------------------------------------------------------- pattern
+constexpr int PAT_CAP = 2048;   // candidate slots per warp (incident elements x nl)
+constexpr int PAT_WARPS = 4;
+
+__device__ __forceinline__ int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(PAT_WARPS * 32)
+k_row_pattern(const int64_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
+              const int32_t *__restrict__ conn, int nl, int64_t N, int64_t P,
+              int32_t *__restrict__ s_len, int32_t *__restrict__ g_len,
+              const int64_t *__restrict__ s_ptr, int32_t *__restrict__ s_col, int *err) {
+  __shared__ int sbuf[PAT_WARPS][PAT_CAP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *buf = sbuf[warp];
+  for (int64_t row = (int64_t)blockIdx.x * PAT_WARPS + warp; row < N; row += (int64_t)gridDim.x * PAT_WARPS) {
+    const int64_t e0 = n2e_ptr[row], e1 = n2e_ptr[row + 1];
+    const int count = (int)(e1 - e0) * nl;
+    if (count > PAT_CAP) {
+      if (lane == 0) atomicOr(err, DEVERR_VALENCE);
+      continue;
+    }
+    const int n2 = next_pow2(count > 0 ? count : 1);
+    for (int t = lane; t < n2; t += 32)
+      buf[t] = t < count ? conn[(int64_t)n2e[e0 + t / nl] * nl + t % nl] : INT_MAX;
+    __syncwarp();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < n2; t += 32) {
+          int u = t ^ j;
+          if (u > t) {
+            int a = buf[t], b = buf[u];
+            bool up = (t & k) == 0;
+            if ((a > b) == up) { buf[t] = b; buf[u] = a; }
+          }
+        }
+        __syncwarp();
+      }
+    int running = 0, gcount = 0;
+    const int64_t base_out = WRITE ? s_ptr[row] : 0;
+    for (int base = 0; base < n2; base += 32) {
+      int t = base + lane;
+      int v = t < n2 ? buf[t] : INT_MAX;
+      bool flag = (t < n2) && v != INT_MAX && (t == 0 || buf[t - 1] != v);
+      unsigned bal = __ballot_sync(0xffffffffu, flag);
+      unsigned gbal = __ballot_sync(0xffffffffu, flag && v < P);
+      if (WRITE && flag) s_col[base_out + running + __popc(bal & ((1u << lane) - 1u))] = v;
+      running += __popc(bal);
+      gcount += __popc(gbal);
+    }
+    if (!WRITE && lane == 0) {
+      s_len[row] = running;
+      g_len[row] = gcount;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_max_int(const int32_t *__restrict__ v, int64_t n, int *out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int m = 0;
+  for (; i < n; i += (int64_t)gridDim.x * blockDim.x) m = max(m, v[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// ------------------------------------------------------------------ values
+// Shared-memory row accumulators of one warp: cols[cap] + acc[nacc][cap] doubles.
+constexpr int ASM_WARPS = 2;
+
+__global__ void __launch_bounds__(ASM_WARPS * 32)
+k_assemble_rows(const int64_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
+                const int32_t *__restrict__ conn, const double *__restrict__ geom, int nl, int dim,
+                int64_t N, int64_t P, const int64_t *__restrict__ s_ptr, const int32_t *__restrict__ s_col,
+                const int32_t *__restrict__ g_len, const int64_t *__restrict__ g_ptr, int cap,
+                int64_t g_nnz, int64_t gt_nnz, double *__restrict__ Ms, double *__restrict__ Ks,
+                double *__restrict__ Dv, double *__restrict__ DTv, double *__restrict__ Mp,
+                double *__restrict__ Lp, int *err) {
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per warp: acc[10][cap] doubles, cols[cap] ints
+  const int NACC = 10;  // M, K, D0..2, DT0..2, Mp, Lp
+  double *acc = smem + (size_t)warp * (NACC * cap + cap / 2 + 1);
+  int *cols = reinterpret_cast<int *>(acc + NACC * cap);
+  const int nv = dim + 1;
+  const int npair = dim * (dim + 1) / 2;
+  for (int64_t row = (int64_t)blockIdx.x * ASM_WARPS + warp; row < N; row += (int64_t)gridDim.x * ASM_WARPS) {
+    const int64_t r0 = s_ptr[row];
+    const int len = (int)(s_ptr[row + 1] - r0);
+    const int glen = g_len[row];
+    for (int t = lane; t < len; t += 32) {
+      cols[t] = s_col[r0 + t];
+      for (int q = 0; q < NACC; ++q) acc[q * cap + t] = 0.0;
+    }
+    __syncwarp();
+    const bool is_vertex = row < P;
+    for (int64_t ei = n2e_ptr[row]; ei < n2e_ptr[row + 1]; ++ei) {
+      const int64_t e = n2e[ei];
+      const int32_t myc = lane < nl ? conn[e * nl + lane] : -1;
+      const unsigned hit = __ballot_sync(0xffffffffu, myc == (int32_t)row);
+      const int a = __ffs(hit) - 1;
+      const double *g = geom + e * GEOM_STRIDE;
+      if (a < 0 || (is_vertex && a >= nv)) {  // incidence list inconsistent with conn
+        if (lane == 0) atomicOr(err, DEVERR_BAD_VERTEX);
+        __syncwarp();
+        continue;
+      }
+      if (lane < nl) {
+        const int b = lane;
+        // binary search of the column position
+        int lo = 0, hi = len - 1, pos = -1;
+        while (lo <= hi) {
+          int mid = (lo + hi) >> 1;
+          int cv = cols[mid];
+          if (cv == myc) { pos = mid; break; }
+          if (cv < myc) lo = mid + 1; else hi = mid - 1;
+        }
+        if (pos < 0) {
+          atomicOr(err, DEVERR_BAD_NODE);
+        } else {
+          const double det = g[0];
+          acc[0 * cap + pos] += det * c_ref.mref[a][b];
+          double kv = 0.0;
+          for (int p = 0; p < npair; ++p) kv += g[10 + p] * c_ref.ksym[p][a][b];
+          acc[1 * cap + pos] += kv;
+          if (b < nv) {
+            for (int cc = 0; cc < dim; ++cc) {
+              double s = 0.0;
+              for (int i = 0; i < dim; ++i) s += g[1 + i * dim + cc] * c_ref.eref[i][a][b];
+              acc[(2 + cc) * cap + pos] += -det * s;
+            }
+          }
+          if (is_vertex) {
+            for (int cc = 0; cc < dim; ++cc) {
+              double s = 0.0;
+              for (int i = 0; i < dim; ++i) s += g[1 + i * dim + cc] * c_ref.eref[i][b][a];
+              acc[(5 + cc) * cap + pos] += -det * s;
+            }
+            if (b < nv) {
+              acc[8 * cap + pos] += det * c_ref.m1[a][b];
+              double lv = 0.0;
+              for (int p = 0; p < npair; ++p) lv += g[10 + p] * c_ref.k1sym[p][a][b];
+              acc[9 * cap + pos] += lv;
+            }
+          }
+        }
+      }
+      __syncwarp();
+    }
+    const int64_t gp = g_ptr[row];
+    for (int t = lane; t < len; t += 32) {
+      Ms[r0 + t] = acc[0 * cap + t];
+      Ks[r0 + t] = acc[1 * cap + t];
+      if (t < glen)
+        for (int cc = 0; cc < dim; ++cc) Dv[cc * g_nnz + gp + t] = acc[(2 + cc) * cap + t];
+      if (is_vertex) {
+        for (int cc = 0; cc < dim; ++cc) DTv[cc * gt_nnz + r0 + t] = acc[(5 + cc) * cap + t];
+        if (t < glen) {
+          Mp[gp + t] = acc[8 * cap + t];
+          Lp[gp + t] = acc[9 * cap + t];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------- masks and copies
+__global__ void k_masks(const uint8_t *__restrict__ tag, int64_t N, int64_t P, uint8_t *dirmask, uint8_t *outmask) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  dirmask[i] = (tag[i] & (SCVS_TAG_WALL | SCVS_TAG_INLET)) ? 1 : 0;
+  if (i < P) outmask[i] = (tag[i] & SCVS_TAG_OUTLET) ? 1 : 0;
+}
+
+__global__ void k_mask_values(int64_t N, int64_t P, int dim, const int64_t *__restrict__ s_ptr,
+                              const int32_t *__restrict__ s_col, const int32_t *__restrict__ g_len,
+                              const int64_t *__restrict__ g_ptr, int64_t g_nnz, int64_t gt_nnz,
+                              const uint8_t *__restrict__ dirm, const uint8_t *__restrict__ outm,
+                              const double *Ms, const double *Ks, const double *Dv, const double *DTv,
+                              const double *Mp, const double *Lp, double *Ms_m, double *Ks_m,
+                              double *Dv_m, double *DTv_m, double *Lp_m, float *Ms_f, float *Ks_f,
+                              float *Dv_f, float *DTv_f, float *Mp_f, float *Lp_f, double *ms_diag,
+                              double *ks_diag, double *mp_diag, double *lp_diag) {
+  int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (A >= N) return;
+  const bool dA = dirm[A];
+  const int64_t r0 = s_ptr[A], r1 = s_ptr[A + 1], gp = g_ptr[A];
+  const int glen = g_len[A];
+  for (int64_t t = r0; t < r1; ++t) {
+    const int32_t B = s_col[t];
+    const bool keep = !dA && !dirm[B];
+    double ms = keep ? Ms[t] : 0.0, ks = keep ? Ks[t] : 0.0;
+    Ms_m[t] = ms; Ks_m[t] = ks;
+    Ms_f[t] = (float)ms; Ks_f[t] = (float)ks;
+    if (B == A) { ms_diag[A] = Ms[t]; ks_diag[A] = Ks[t]; }
+    if (A < P)
+      for (int c = 0; c < dim; ++c) {
+        double v = dirm[B] ? 0.0 : DTv[c * gt_nnz + t];
+        DTv_m[c * gt_nnz + t] = v;
+        DTv_f[c * gt_nnz + t] = (float)v;
+      }
+  }
+  for (int t = 0; t < glen; ++t) {
+    const int64_t q = gp + t;
+    for (int c = 0; c < dim; ++c) {
+      double v = dA ? 0.0 : Dv[c * g_nnz + q];
+      Dv_m[c * g_nnz + q] = v;
+      Dv_f[c * g_nnz + q] = (float)v;
+    }
+    if (A < P) {
+      const int32_t B = s_col[r0 + t];
+      const bool oA = outm[A], oB = outm[B];
+      double l = (oA || oB) ? ((A == B) ? 1.0 : 0.0) : Lp[q];
+      Lp_m[q] = l;
+      Lp_f[q] = (float)l;
+      Mp_f[q] = (float)Mp[q];
+      if (B == A) { mp_diag[A] = Mp[q]; lp_diag[A] = l; }
+    }
+  }
+}
+
+// ------------------------------------------------------------------- scan
+// Exclusive scan of int32 counts into int64 offsets with out[n] = total.
+constexpr int SCAN_T = 512, SCAN_ITEMS = 4, SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t warp_sums[SCAN_T / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < SCAN_T / 32 ? warp_sums[lane] : 0;
+    int64_t wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t u = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < SCAN_T / 32) warp_sums[lane] = wi - w;
+    if (lane == SCAN_T / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  int64_t r = inc - v + warp_sums[warp];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_tiles(const int32_t *__restrict__ in, int64_t *out, int64_t n, int64_t *tile_sums) {
+  __shared__ int64_t tot;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS], s = 0;
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0;
+    s += v[i];
+  }
+  int64_t ex = block_exclusive_scan(s, &tot);
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if (base + i <= n) out[base + i] = ex;
+    ex += v[i];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int64_t *sums, int64_t nt) {
+  __shared__ int64_t tot;
+  int64_t carry = 0;
+  for (int64_t b = 0; b < nt; b += SCAN_T) {
+    int64_t i = b + threadIdx.x;
+    int64_t v = i < nt ? sums[i] : 0;
+    int64_t ex = block_exclusive_scan(v, &tot);
+    if (i < nt) sums[i] = ex + carry;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *__restrict__ sums) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i <= n) out[i] += sums[i / SCAN_TILE];
+}
+
+void scan_exclusive(Ctx &c, const int32_t *in, int64_t *out, int64_t n) {
+  const int64_t nt = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+  int64_t *sums = nullptr;
+  SCVS_CUDA(cudaMallocAsync(&sums, nt * sizeof(int64_t), c.stream));
+  k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, c.stream>>>(in, out, n, sums);
+  k_scan_sums<<<1, SCAN_T, 0, c.stream>>>(sums, nt);
+  k_scan_add<<<ceil_div(n + 1, 256), 256, 0, c.stream>>>(out, n, sums);
+  c.launches.n += 3;
+  SCVS_CUDA(cudaFreeAsync(sums, c.stream));
+}
+
+// ------------------------------------------------------------------ driver
+void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, const uint8_t *tag_in) {
+  cudaStream_t s = c.stream;
+  KScope ks(c, KC_ASSEMBLY, 0.0);
+  const int64_t N = m.N, P = m.P, E = m.E;
+  const int nl = m.nl, dim = m.dim;
+  m.xyz = m.arena.alloc<double>(N * dim);
+  m.conn = m.arena.alloc<int32_t>(E * nl);
+  m.tag = m.arena.alloc<uint8_t>(N);
+  SCVS_CUDA(cudaMemcpyAsync(m.xyz, xyz_in, N * dim * sizeof(double), cudaMemcpyDefault, s));
+  SCVS_CUDA(cudaMemcpyAsync(m.conn, conn_in, E * nl * sizeof(int32_t), cudaMemcpyDefault, s));
+  SCVS_CUDA(cudaMemcpyAsync(m.tag, tag_in, N, cudaMemcpyDefault, s));
+  SCVS_CUDA(cudaMemsetAsync(c.dev_err, 0, sizeof(int), s));
+
+  m.geom = m.arena.alloc<double>(E * GEOM_STRIDE);
+  k_geom<<<ceil_div(E, 256), 256, 0, s>>>(m.xyz, m.conn, E, nl, dim, N, P, m.geom, c.dev_err);
+  count_launch(c);
+  int derr = dev_error(c);
+  if (derr) throw derr;
+
+  // node -> element incidence
+  int32_t *cnt = m.arena.alloc<int32_t>(N);
+  SCVS_CUDA(cudaMemsetAsync(cnt, 0, N * sizeof(int32_t), s));
+  k_count_incidence<<<ceil_div(E * nl, 256), 256, 0, s>>>(m.conn, E * nl, cnt);
+  count_launch(c);
+  m.n2e_ptr = m.arena.alloc<int64_t>(N + 1);
+  scan_exclusive(c, cnt, m.n2e_ptr, N);
+  m.n2e = m.arena.alloc<int32_t>(E * nl);
+  SCVS_CUDA(cudaMemsetAsync(cnt, 0, N * sizeof(int32_t), s));
+  k_fill_incidence<<<ceil_div(E * nl, 256), 256, 0, s>>>(m.conn, E, nl, m.n2e_ptr, cnt, m.n2e);
+  k_sort_incidence<<<ceil_div(N, 128), 128, 0, s>>>(m.n2e_ptr, m.n2e, N, c.dev_err);
+  c.launches.n += 2;
+
+  // S pattern: count, scan, write
+  m.s_len = m.arena.alloc<int32_t>(N);
+  m.g_len = m.arena.alloc<int32_t>(N);
+  const unsigned pat_blocks = std::min<int64_t>(ceil_div(N, PAT_WARPS), (int64_t)c.num_sms * 16);
+  k_row_pattern<false><<<pat_blocks, PAT_WARPS * 32, 0, s>>>(m.n2e_ptr, m.n2e, m.conn, nl, N, P, m.s_len,
+                                                              m.g_len, nullptr, nullptr, c.dev_err);
+  count_launch(c);
+  derr = dev_error(c);
+  if (derr) throw derr;
+  m.s_ptr = m.arena.alloc<int64_t>(N + 1);
+  m.g_ptr = m.arena.alloc<int64_t>(N + 1);
+  scan_exclusive(c, m.s_len, m.s_ptr, N);
+  scan_exclusive(c, m.g_len, m.g_ptr, N);
+  SCVS_CUDA(cudaMemcpyAsync(&m.s_nnz, m.s_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCVS_CUDA(cudaMemcpyAsync(&m.g_nnz, m.g_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCVS_CUDA(cudaMemcpyAsync(&m.gt_nnz, m.s_ptr + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  SCVS_CUDA(cudaMemcpyAsync(&m.q_nnz, m.g_ptr + P, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int *dmax = m.arena.alloc<int>(1);
+  SCVS_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+  k_max_int<<<std::min<unsigned>(ceil_div(N, 256), 1024), 256, 0, s>>>(m.s_len, N, dmax);
+  count_launch(c);
+  SCVS_CUDA(cudaMemcpyAsync(&m.max_row, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCVS_CUDA(cudaStreamSynchronize(s));
+  m.s_col = m.arena.alloc<int32_t>(m.s_nnz);
+  k_row_pattern<true><<<pat_blocks, PAT_WARPS * 32, 0, s>>>(m.n2e_ptr, m.n2e, m.conn, nl, N, P, m.s_len,
+                                                             m.g_len, m.s_ptr, m.s_col, c.dev_err);
+  count_launch(c);
+
+  // values
+  m.Ms = m.arena.alloc<double>(m.s_nnz);
+  m.Ks = m.arena.alloc<double>(m.s_nnz);
+  m.Dv = m.arena.alloc<double>(dim * m.g_nnz);
+  m.DTv = m.arena.alloc<double>(dim * m.gt_nnz);
+  m.Mp = m.arena.alloc<double>(m.q_nnz);
+  m.Lp = m.arena.alloc<double>(m.q_nnz);
+  const RefTables &rt = dim == 2 ? c.ref2 : c.ref3;
+  SCVS_CUDA(cudaMemcpyToSymbolAsync(c_ref, &rt, sizeof(RefTables), 0, cudaMemcpyHostToDevice, s));
+  int cap = std::max(32, (m.max_row + 31) / 32 * 32);
+  size_t per_warp = (size_t)10 * cap * sizeof(double) + (cap / 2 + 1) * sizeof(double);
+  size_t smem = per_warp * ASM_WARPS;
+  if (smem > 200 * 1024) throw (int)DEVERR_VALENCE;
+  SCVS_CUDA(cudaFuncSetAttribute(k_assemble_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned asm_blocks = std::min<int64_t>(ceil_div(N, ASM_WARPS), (int64_t)c.num_sms * 32);
+  k_assemble_rows<<<asm_blocks, ASM_WARPS * 32, smem, s>>>(
+      m.n2e_ptr, m.n2e, m.conn, m.geom, nl, dim, N, P, m.s_ptr, m.s_col, m.g_len, m.g_ptr, cap, m.g_nnz,
+      m.gt_nnz, m.Ms, m.Ks, m.Dv, m.DTv, m.Mp, m.Lp, c.dev_err);
+  count_launch(c);
+  derr = dev_error(c);
+  if (derr) throw derr;
+
+  // masks, masked values, FP32 copies, diagonals
+  m.dirmask = m.arena.alloc<uint8_t>(N);
+  m.outmask = m.arena.alloc<uint8_t>(P);
+  k_masks<<<ceil_div(N, 256), 256, 0, s>>>(m.tag, N, P, m.dirmask, m.outmask);
+  count_launch(c);
+  m.Ms_m = m.arena.alloc<double>(m.s_nnz);
+  m.Ks_m = m.arena.alloc<double>(m.s_nnz);
+  m.Dv_m = m.arena.alloc<double>(dim * m.g_nnz);
+  m.DTv_m = m.arena.alloc<double>(dim * m.gt_nnz);
+  m.Lp_m = m.arena.alloc<double>(m.q_nnz);
+  m.Ms_f = m.arena.alloc<float>(m.s_nnz);
+  m.Ks_f = m.arena.alloc<float>(m.s_nnz);
+  m.Dv_f = m.arena.alloc<float>(dim * m.g_nnz);
+  m.DTv_f = m.arena.alloc<float>(dim * m.gt_nnz);
+  m.Mp_f = m.arena.alloc<float>(m.q_nnz);
+  m.Lp_f = m.arena.alloc<float>(m.q_nnz);
+  m.ms_diag = m.arena.alloc<double>(N);
+  m.ks_diag = m.arena.alloc<double>(N);
+  m.mp_diag = m.arena.alloc<double>(P);
+  m.lp_diag = m.arena.alloc<double>(P);
+  k_mask_values<<<ceil_div(N, 128), 128, 0, s>>>(
+      N, P, dim, m.s_ptr, m.s_col, m.g_len, m.g_ptr, m.g_nnz, m.gt_nnz, m.dirmask, m.outmask, m.Ms, m.Ks,
+      m.Dv, m.DTv, m.Mp, m.Lp, m.Ms_m, m.Ks_m, m.Dv_m, m.DTv_m, m.Lp_m, m.Ms_f, m.Ks_f, m.Dv_f, m.DTv_f,
+      m.Mp_f, m.Lp_f, m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag);
+  count_launch(c);
+  SCVS_CUDA(cudaStreamSynchronize(s));
+  SCVS_CUDA(cudaGetLastError());
+}
+
+}  // namespace scvs

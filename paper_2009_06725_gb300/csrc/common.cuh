@@ -1,0 +1,113 @@
+// Shared device/host helpers of the SCVS CUDA library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+namespace scvs {
+
+// ---------------------------------------------------------------- errors
+struct CudaError {
+  cudaError_t code;
+  std::string where;
+};
+
+#define SCVS_CUDA(call)                                                          \
+  do {                                                                           \
+    cudaError_t _e = (call);                                                     \
+    if (_e != cudaSuccess) throw ::scvs::CudaError{_e, std::string(#call) + " @ " \
+                                                       + __FILE__ + ":" + std::to_string(__LINE__)}; \
+  } while (0)
+
+// Device-side error bits written by kernels into a flag word; the host turns
+// them into return codes after the kernel.
+enum DevErr : int {
+  DEVERR_NONE = 0,
+  DEVERR_BAD_NODE = 1,      // connectivity entry outside [0, n_nodes)
+  DEVERR_BAD_VERTEX = 2,    // a simplex vertex id outside [0, n_vertices)
+  DEVERR_JACOBIAN = 4,      // non-positive element Jacobian
+  DEVERR_VALENCE = 8,       // too many elements around one node for the pattern kernel
+  DEVERR_BARRIER = 16,      // a bounded grid barrier gave up
+  DEVERR_DUP_NODE = 32,     // an element lists the same node twice
+};
+
+// --------------------------------------------------------- complex helpers
+template <typename T> struct cpx;
+template <> struct cpx<float> { using t = float2; };
+template <> struct cpx<double> { using t = double2; };
+
+template <typename T> __host__ __device__ __forceinline__ typename cpx<T>::t mk(T r, T i) {
+  typename cpx<T>::t z; z.x = r; z.y = i; return z;
+}
+
+// ----------------------------------------------------------- grid barrier
+// Bounded sense-counting barrier for cooperative launches: every block of the
+// grid must be resident (the host launches with cudaLaunchCooperativeKernel).
+// A block that waits more than SPIN_LIMIT polls sets the error word and
+// returns false; every caller then exits the kernel.
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+
+constexpr long long SPIN_LIMIT = 1ll << 24;  // ~2-4 s with the back-off below
+
+#ifdef __CUDACC__
+__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned int nblocks) {
+  __shared__ int s_ok;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *vgen = &gs->gen;
+    volatile int *verr = &gs->err;
+    unsigned int g = *vgen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(&gs->count, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*verr) { ok = 0; break; }
+        if (++spins > SPIN_LIMIT) { atomicExch(&gs->err, 1); ok = 0; break; }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok && (*verr == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+#endif
+
+// ------------------------------------------------------------- constants
+constexpr int MAX_NL = 10;   // P2 tet
+constexpr int MAX_NV = 4;    // P1 tet
+constexpr int GEOM_STRIDE = 16;  // det, Jinv[3][3], gamma[6] (sym, ij i<=j)
+
+// Exact integrals over the reference simplex (computed on the host, see refmats.cpp):
+//   mref[a][b]        = int phi_a phi_b
+//   ksym[p][a][b]     = int (d_i phi_a d_j phi_b + d_j phi_a d_i phi_b)/(1 + delta_ij),
+//                       p enumerating (i,j), i <= j, in row order
+//   eref[i][a][b]     = int d_i phi_a psi_b          (phi P2, psi P1)
+//   m1[a][b]          = int psi_a psi_b
+//   k1sym[p][a][b]    = as ksym for the P1 basis
+struct RefTables {
+  double mref[MAX_NL][MAX_NL];
+  double ksym[6][MAX_NL][MAX_NL];
+  double eref[3][MAX_NL][MAX_NV];
+  double m1[MAX_NV][MAX_NV];
+  double k1sym[6][MAX_NV][MAX_NV];
+};
+
+void reference_tables(int dim, RefTables *out);  // refmats.cpp
+
+inline unsigned int ceil_div(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
+
+}  // namespace scvs

@@ -1,0 +1,880 @@
+// All-modes operators on mode-interleaved complex blocks.
+//
+// Block layout: element (dof, k) at dof*ld + k; velocity dof = node*dim + c,
+// then the pressure dof of every vertex at dim*N + vertex (Eq. linear_sys_def).
+//
+//  * k_saddle   y_k = A(omega_k) x_k for all modes (Eq. linear_sys_def) with the
+//               pattern of S (velocity rows: M_s, K_s over the whole row, D_c over
+//               the leading P1 columns; pressure rows: D_c^T over the S row of the
+//               vertex).  One row group of L lanes per row; each nonzero is
+//               loaded once by one lane and broadcast by shuffle, so its column
+//               index and values serve every mode of the row; every lane owns
+//               MPL modes and gathers them with one 16-byte load per component.
+//  * lift / residual / per-mode norms
+//  * block preconditioner: Chebyshev-Jacobi polynomials of the velocity block
+//    mu K_s + j omega rho M_s (per mode) and of the P1 pressure mass and
+//    Laplacian (Cahouet-Chabard combination mu M_p^-1 + j omega rho L_p^-1),
+//    or their diagonal versions.
+#include <algorithm>
+#include <cmath>
+#include "scvs_internal.h"
+#include "vecops.cuh"
+
+namespace scvs {
+
+template <typename T> struct SaddleArgs {
+  int64_t N, P;
+  int ld;
+  const int64_t *s_ptr;
+  const int32_t *s_col;
+  const int32_t *g_len;
+  const int64_t *g_ptr;
+  const T *Kv, *Mv, *Dv, *DTv;
+  int64_t g_nnz, gt_nnz;
+  const uint8_t *dirmask;  // null: no identity rows
+  const double *omega;
+  double rho, mu;
+};
+
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256)
+k_saddle(const SaddleArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename cpx<T>::t *__restrict__ y) {
+  using C = typename cpx<T>::t;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  const int ld = a.ld;
+  const int koff = lane * MPL;
+  T wr[MPL];
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) wr[i] = (T)(a.omega[koff + i] * a.rho);
+  const T mu = (T)a.mu;
+  const int64_t rows = a.N + a.P;
+  const C *__restrict__ xp_base = x + (int64_t)DIM * a.N * ld + koff;
+  for (int64_t row = (int64_t)blockIdx.x * gpb + group; row < rows; row += (int64_t)gridDim.x * gpb) {
+    if (row < a.N) {
+      const int64_t A = row;
+      if (a.dirmask && a.dirmask[A]) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          CV<T, MPL> v;
+          ldv<T, MPL>(v, x + (A * DIM + c) * ld + koff);
+          stv<T, MPL>(y + (A * DIM + c) * ld + koff, v);
+        }
+        continue;
+      }
+      CV<T, MPL> aK[DIM], aM[DIM], aD[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) { aK[c].zero(); aM[c].zero(); aD[c].zero(); }
+      const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
+      const int64_t gend = r0 + a.g_len[A];
+      const int64_t goff = a.g_ptr[A] - r0;
+      for (int64_t base = r0; base < r1; base += L) {
+        const int64_t t = base + lane;
+        int32_t col = 0;
+        T kv = 0, mv = 0, dv[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dv[c] = 0;
+        if (t < r1) {
+          col = __ldg(a.s_col + t);
+          kv = __ldg(a.Kv + t);
+          mv = __ldg(a.Mv + t);
+          if (t < gend) {
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) dv[c] = __ldg(a.Dv + c * a.g_nnz + t + goff);
+          }
+        }
+        const int cnt = (int)min((int64_t)L, r1 - base);
+        const int gcnt = (int)max((int64_t)0, min((int64_t)L, gend - base));
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+          const int32_t B = gshfl<L>(gm, col, q);
+          const T kq = gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            CV<T, MPL> xv;
+            ldv<T, MPL>(xv, x + ((int64_t)B * DIM + c) * ld + koff);
+            axpy(aK[c], kq, xv);
+            axpy(aM[c], mq, xv);
+          }
+          if (q < gcnt) {  // uniform across the row group
+            CV<T, MPL> xq;
+            ldv<T, MPL>(xq, xp_base + (int64_t)B * ld);
+#pragma unroll
+            for (int c = 0; c < DIM; ++c) axpy(aD[c], gshfl<L>(gm, dv[c], q), xq);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        CV<T, MPL> o;
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+          o.re[i] = mu * aK[c].re[i] - wr[i] * aM[c].im[i] + aD[c].re[i];
+          o.im[i] = mu * aK[c].im[i] + wr[i] * aM[c].re[i] + aD[c].im[i];
+        }
+        stv<T, MPL>(y + (A * DIM + c) * ld + koff, o);
+      }
+    } else {
+      const int64_t B = row - a.N;
+      CV<T, MPL> acc;
+      acc.zero();
+      const int64_t r0 = a.s_ptr[B], r1 = a.s_ptr[B + 1];
+      for (int64_t base = r0; base < r1; base += L) {
+        const int64_t t = base + lane;
+        int32_t col = 0;
+        T dt[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dt[c] = 0;
+        if (t < r1) {
+          col = __ldg(a.s_col + t);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) dt[c] = __ldg(a.DTv + c * a.gt_nnz + t);
+        }
+        const int cnt = (int)min((int64_t)L, r1 - base);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+          const int32_t Acol = gshfl<L>(gm, col, q);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            CV<T, MPL> xv;
+            ldv<T, MPL>(xv, x + ((int64_t)Acol * DIM + c) * ld + koff);
+            axpy(acc, gshfl<L>(gm, dt[c], q), xv);
+          }
+        }
+      }
+      stv<T, MPL>(y + ((int64_t)DIM * a.N + B) * ld + koff, acc);
+    }
+  }
+}
+
+template <typename T>
+SaddleArgs<T> saddle_args(const Ctx &c, const Mesh &m, bool masked);
+
+template <>
+SaddleArgs<float> saddle_args<float>(const Ctx &, const Mesh &m, bool) {
+  return SaddleArgs<float>{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr, m.Ks_f, m.Ms_f, m.Dv_f,
+                           m.DTv_f, m.g_nnz, m.gt_nnz, m.dirmask, m.omega_d, m.rho, m.mu};
+}
+template <>
+SaddleArgs<double> saddle_args<double>(const Ctx &, const Mesh &m, bool masked) {
+  return SaddleArgs<double>{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr,
+                            masked ? m.Ks_m : m.Ks, masked ? m.Ms_m : m.Ms,
+                            masked ? m.Dv_m : m.Dv, masked ? m.DTv_m : m.DTv,
+                            m.g_nnz, m.gt_nnz, masked ? m.dirmask : nullptr, m.omega_d, m.rho, m.mu};
+}
+
+// Algorithmic bytes of one all-modes SpMM: every index and value array once,
+// x read once, y written once.
+double saddle_bytes(const Mesh &m, int vs) {
+  const double mat = (double)m.s_nnz * (4 + 2 * vs) + (double)m.dim * (m.g_nnz + m.gt_nnz) * vs +
+                     (double)(m.N + 1) * 16 + (double)m.N * 5;
+  return mat + 2.0 * m.n_dof * m.ld * 2 * vs;
+}
+
+static unsigned row_blocks(const Ctx &c, int64_t rows, int groups_per_block) {
+  int64_t need = (rows + groups_per_block - 1) / groups_per_block;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c.num_sms * 32));
+}
+
+template <typename T>
+void launch_saddle(Ctx &c, const Mesh &m, const SaddleArgs<T> &a, const typename cpx<T>::t *x,
+                   typename cpx<T>::t *y) {
+  KScope ks(c, sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM64, saddle_bytes(m, sizeof(T)));
+  SCVS_DISPATCH_LD(T, m.ld, {
+    const int gpb = 256 / L;
+    const unsigned nb = row_blocks(c, m.N + m.P, gpb);
+    if (m.dim == 2)
+      k_saddle<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, x, y);
+    else
+      k_saddle<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, x, y);
+  });
+  count_launch(c);
+}
+
+template <typename T>
+void apply_saddle(Ctx &c, const Mesh &m, const typename cpx<T>::t *x, typename cpx<T>::t *y) {
+  launch_saddle<T>(c, m, saddle_args<T>(c, m, true), x, y);
+}
+template void apply_saddle<float>(Ctx &, const Mesh &, const float2 *, float2 *);
+template void apply_saddle<double>(Ctx &, const Mesh &, const double2 *, double2 *);
+
+// ------------------------------------------------------------------- lift
+__global__ void k_scatter_dirichlet(const double2 *__restrict__ g, const int64_t *__restrict__ dir_nodes,
+                                    int64_t n_dir, int dim, int m, int ld, double2 *__restrict__ gfull) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)m * n_dir * dim;
+  if (t >= total) return;
+  int k = (int)(t / (n_dir * dim));
+  int64_t r = t % (n_dir * dim);
+  int64_t i = r / dim;
+  int c = (int)(r % dim);
+  gfull[(dir_nodes[i] * dim + c) * ld + k] = g[t];
+}
+
+// b = -y on free rows, b = gfull on Dirichlet velocity rows
+__global__ void k_lift_finish(const double2 *__restrict__ y, const double2 *__restrict__ gfull,
+                              const uint8_t *__restrict__ dirm, int64_t N, int dim, int64_t n_dof, int ld,
+                              double2 *__restrict__ b) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= n_dof * ld) return;
+  int64_t dof = f / ld;
+  bool dir = dof < N * dim && dirm[dof / dim];
+  double2 v = y[f];
+  b[f] = dir ? gfull[f] : make_double2(-v.x, -v.y);
+}
+
+// Deterministic per-mode squared norms over the free rows: per-block partials,
+// then one thread per mode sums the partials in block order.
+constexpr int NORM_T = 256;
+__global__ void k_norm_partials(const double2 *__restrict__ v, const uint8_t *__restrict__ dirm, int64_t N, int dim,
+                                int64_t n_dof, int ld, double *__restrict__ part) {
+  __shared__ double s[NORM_T];
+  const int64_t total = n_dof * ld;
+  const int64_t stride = (int64_t)gridDim.x * NORM_T;  // multiple of ld
+  double acc = 0.0;
+  for (int64_t f = blockIdx.x * (int64_t)NORM_T + threadIdx.x; f < total; f += stride) {
+    int64_t dof = f / ld;
+    bool dir = dof < N * dim && dirm[dof / dim];
+    if (!dir) { double2 z = v[f]; acc += z.x * z.x + z.y * z.y; }
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  // threads with equal (tid % ld) hold the same mode
+  for (int w = NORM_T / 2; w >= ld; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < ld) part[(int64_t)blockIdx.x * ld + threadIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_norm_finish(const double *__restrict__ part, int nblocks, int ld, double *__restrict__ out) {
+  int k = threadIdx.x;
+  if (k >= ld) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * ld + k];
+  out[k] = s;
+}
+
+static void mode_norms2(Ctx &c, const Mesh &m, const double2 *v, double *part, double *out) {
+  KScope ks(c, KC_VECTOR, (double)m.n_dof * m.ld * 16);
+  const int nb = (int)std::min<int64_t>(std::max<int64_t>(1, (m.n_dof * m.ld) / (NORM_T * 8)), 4 * c.num_sms);
+  k_norm_partials<<<nb, NORM_T, 0, c.stream>>>(v, m.dirmask, m.N, m.dim, m.n_dof, m.ld, part);
+  k_norm_finish<<<1, 128, 0, c.stream>>>(part, nb, m.ld, out);
+  c.launches.n += 2;
+}
+
+void lift_rhs(Ctx &c, Mesh &m) {
+  const int64_t total = m.n_dof * m.ld;
+  double2 *gfull = nullptr, *y = nullptr;
+  double *part = nullptr, *nrm = nullptr;
+  SCVS_CUDA(cudaMallocAsync(&gfull, total * sizeof(double2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(double2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&part, (size_t)4 * c.num_sms * m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&nrm, m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(gfull, 0, total * sizeof(double2), c.stream));
+  if (m.n_dir > 0 && m.m > 0) {
+    int64_t tt = (int64_t)m.m * m.n_dir * m.dim;
+    k_scatter_dirichlet<<<ceil_div(tt, 256), 256, 0, c.stream>>>(m.g, m.dir_nodes, m.n_dir, m.dim, m.m, m.ld, gfull);
+    count_launch(c);
+  }
+  launch_saddle<double>(c, m, saddle_args<double>(c, m, false), gfull, y);
+  {
+    KScope ks(c, KC_VECTOR, (double)total * 48);
+    k_lift_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(y, gfull, m.dirmask, m.N, m.dim, m.n_dof, m.ld, m.b);
+    count_launch(c);
+  }
+  mode_norms2(c, m, m.b, part, nrm);
+  std::vector<double> h(m.ld);
+  SCVS_CUDA(cudaMemcpyAsync(h.data(), nrm, m.ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(gfull, c.stream));
+  SCVS_CUDA(cudaFreeAsync(y, c.stream));
+  SCVS_CUDA(cudaFreeAsync(part, c.stream));
+  SCVS_CUDA(cudaFreeAsync(nrm, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  m.bnorm.assign(m.ld, 0.0);
+  for (int k = 0; k < m.ld; ++k) m.bnorm[k] = std::sqrt(h[k]);
+}
+
+// --------------------------------------------------------------- residual
+// r = b - A_hat x on every row (zero on Dirichlet rows when x_D = g); writes
+// the FP32 copy (right-hand side of the next FP32 cycle) and, optionally, FP64.
+__global__ void k_residual_finish(const double2 *__restrict__ b, const double2 *__restrict__ ax,
+                                  const uint8_t *__restrict__ dirm, int64_t N, int dim, int64_t total, int ld,
+                                  float2 *__restrict__ r32, double2 *__restrict__ r64) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= total) return;
+  int64_t dof = f / ld;
+  bool dir = dof < N * dim && dirm[dof / dim];
+  double2 bb = b[f], a = ax[f];
+  double2 r = dir ? make_double2(0.0, 0.0) : make_double2(bb.x - a.x, bb.y - a.y);
+  if (r32) r32[f] = make_float2((float)r.x, (float)r.y);
+  if (r64) r64[f] = r;
+}
+
+// ----------------------------------------------------- preconditioner
+struct PcArgs {
+  int64_t N, P;
+  int ld;
+  const int64_t *s_ptr;
+  const int32_t *s_col;
+  const int32_t *g_len;
+  const int64_t *g_ptr;
+  const void *Kv, *Mv;         // masked velocity-block values (T)
+  const void *Mpv, *Lpv;       // P1 mass, Laplacian (outlet rows identity) values (T), Q pattern
+  const double *ms_diag, *ks_diag, *mp_diag, *lp_diag;
+  const uint8_t *dirmask, *outmask;
+  const double *omega;
+  double rho, mu;
+};
+
+// The velocity block of mode k, A_u = mu K_s + j omega rho M_s, is preconditioned
+// through the real SPD shift A_r = mu K_s + |omega| rho M_s: the spectrum of
+// A_r^-1 A_u lies on the arc from j to 1 (|z| >= 1/sqrt 2) for every omega, and
+// A_r has a real positive Jacobi-scaled spectrum on which a Chebyshev
+// polynomial on a real interval is effective.  vel_dinv is 1 / diag(A_r).
+template <typename T>
+__device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, double w) {
+  return (T)(1.0 / (a.mu * a.ks_diag[A] + fabs(w) * a.rho * a.ms_diag[A]));
+}
+
+// Step 0 of every polynomial (elementwise): optionally rescale r by rscale[k]
+// (and write it back); z_u = r / (diag A_r theta_u[k]); pressure: zM = r/(diag M_p theta_M),
+// zL = r/(diag L_p theta_L) with r zeroed at outlet vertices.  Block-diagonal
+// mode: z_u = r / diag A_r, z_p = (mu/diag M_p + j omega rho/diag L_p) r.
+template <typename T, int DIM, bool DIAG>
+__global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *__restrict__ rscale,
+                           const double *__restrict__ inv_theta_u, double inv_theta_m, double inv_theta_l,
+                           typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zM,
+                           typename cpx<T>::t *__restrict__ zL) {
+  using C = typename cpx<T>::t;
+  const int64_t total = ((int64_t)DIM * a.N + a.P) * a.ld;
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= total) return;
+  const int64_t dof = f / a.ld;
+  const int k = (int)(f % a.ld);
+  C v = r[f];
+  if (rscale) {
+    T s = (T)rscale[k];
+    v.x *= s; v.y *= s;
+    r[f] = v;
+  }
+  if (dof < (int64_t)DIM * a.N) {
+    const int64_t A = dof / DIM;
+    if (a.dirmask[A]) { zu[f] = v; return; }
+    const T s = vel_dinv<T>(a, A, a.omega[k]) * (DIAG ? T(1) : (T)inv_theta_u[k]);
+    zu[f] = mk<T>(s * v.x, s * v.y);
+  } else {
+    const int64_t B = dof - (int64_t)DIM * a.N;
+    const int64_t pf = B * a.ld + k;
+    const bool out = a.outmask[B];
+    if (DIAG) {
+      double w = a.omega[k] * a.rho;
+      T cm = (T)(a.mu / a.mp_diag[B]);
+      T cl = out ? T(0) : (T)(w / a.lp_diag[B]);
+      // (cm + j cl) * v
+      zu[f] = mk<T>(cm * v.x - cl * v.y, cm * v.y + cl * v.x);
+    } else {
+      T sm = (T)(inv_theta_m / a.mp_diag[B]);
+      zM[pf] = mk<T>(v.x * sm, v.y * sm);
+      T sl = out ? T(0) : (T)(inv_theta_l / a.lp_diag[B]);
+      zL[pf] = mk<T>(v.x * sl, v.y * sl);
+    }
+  }
+}
+
+// Chebyshev step i >= 1 for the velocity rows (rows [0, N)) and the pressure
+// rows (rows [N, N+P), both polynomials):
+//   z_next = z + alpha (z - z_prev) + beta D^-1 (r - A z)
+// z_prev is overwritten by z_next (each row reads its own z_prev first).
+struct ChebCoef {
+  const double *alpha_u, *beta_u;  // [ld] per mode (velocity)
+  double alpha_m, beta_m, alpha_l, beta_l;
+  int do_u, do_m, do_l;
+  int prev_zero_u, prev_zero_m, prev_zero_l;
+};
+
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256)
+k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restrict__ r,
+          const typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zu_prev,
+          const typename cpx<T>::t *__restrict__ zM, typename cpx<T>::t *__restrict__ zM_prev,
+          const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ zL_prev) {
+  using C = typename cpx<T>::t;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  const int ld = a.ld, koff = lane * MPL;
+  const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv, *Mpv = (const T *)a.Mpv, *Lpv = (const T *)a.Lpv;
+  const int64_t row_lo = cc.do_u ? 0 : a.N;
+  const int64_t row_hi = (cc.do_m || cc.do_l) ? a.N + a.P : a.N;
+  for (int64_t row = row_lo + (int64_t)blockIdx.x * gpb + group; row < row_hi; row += (int64_t)gridDim.x * gpb) {
+    if (row < a.N) {
+      const int64_t A = row;
+      if (a.dirmask[A]) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          CV<T, MPL> v;
+          ldv<T, MPL>(v, r + (A * DIM + c) * ld + koff);
+          stv<T, MPL>(zu_prev + (A * DIM + c) * ld + koff, v);
+        }
+        continue;
+      }
+      CV<T, MPL> aK[DIM], aM[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) { aK[c].zero(); aM[c].zero(); }
+      const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
+      for (int64_t base = r0; base < r1; base += L) {
+        const int64_t t = base + lane;
+        int32_t col = 0;
+        T kv = 0, mv = 0;
+        if (t < r1) { col = __ldg(a.s_col + t); kv = __ldg(Kv + t); mv = __ldg(Mv + t); }
+        const int cnt = (int)min((int64_t)L, r1 - base);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+          const int32_t B = gshfl<L>(gm, col, q);
+          const T kq = gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            CV<T, MPL> xv;
+            ldv<T, MPL>(xv, zu + ((int64_t)B * DIM + c) * ld + koff);
+            axpy(aK[c], kq, xv);
+            axpy(aM[c], mq, xv);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        const int k = koff + i;
+        const double w = a.omega[k];
+        const T dr = vel_dinv<T>(a, A, w);
+        const T al = (T)cc.alpha_u[k], be = (T)cc.beta_u[k], mu = (T)a.mu, wr = (T)(fabs(w) * a.rho);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          const int64_t f = (A * DIM + c) * ld + k;
+          const C rv = r[f], z = zu[f];
+          const C zp = cc.prev_zero_u ? mk<T>(0, 0) : zu_prev[f];
+          const T axr = mu * aK[c].re[i] + wr * aM[c].re[i];  // A_r z
+          const T axi = mu * aK[c].im[i] + wr * aM[c].im[i];
+          const T ur = dr * (rv.x - axr), ui = dr * (rv.y - axi);
+          zu_prev[f] = mk<T>(z.x + al * (z.x - zp.x) + be * ur, z.y + al * (z.y - zp.y) + be * ui);
+        }
+      }
+    } else {
+      const int64_t B = row - a.N;
+      const int64_t r0 = a.g_ptr[B], r1 = a.g_ptr[B + 1];  // Q row = leading part of the S row
+      const int64_t s0 = a.s_ptr[B];
+      CV<T, MPL> aMp, aLp;
+      aMp.zero(); aLp.zero();
+      for (int64_t base = r0; base < r1; base += L) {
+        const int64_t t = base + lane;
+        int32_t col = 0;
+        T mv = 0, lv = 0;
+        if (t < r1) { col = __ldg(a.s_col + s0 + (t - r0)); mv = __ldg(Mpv + t); lv = __ldg(Lpv + t); }
+        const int cnt = (int)min((int64_t)L, r1 - base);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+          const int32_t Bc = gshfl<L>(gm, col, q);
+          const T mq = gshfl<L>(gm, mv, q), lq = gshfl<L>(gm, lv, q);
+          if (cc.do_m) { CV<T, MPL> v; ldv<T, MPL>(v, zM + (int64_t)Bc * ld + koff); axpy(aMp, mq, v); }
+          if (cc.do_l) { CV<T, MPL> v; ldv<T, MPL>(v, zL + (int64_t)Bc * ld + koff); axpy(aLp, lq, v); }
+        }
+      }
+      const int64_t rf = ((int64_t)DIM * a.N + B) * ld;
+      const bool out = a.outmask[B];
+      const T dm = (T)(1.0 / a.mp_diag[B]), dl = (T)(1.0 / a.lp_diag[B]);
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        const int k = koff + i;
+        const int64_t pf = B * ld + k;
+        const C rv = r[rf + k];
+        if (cc.do_m) {
+          const C z = zM[pf];
+          const C zp = cc.prev_zero_m ? mk<T>(0, 0) : zM_prev[pf];
+          const T al = (T)cc.alpha_m, be = (T)cc.beta_m;
+          zM_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dm * (rv.x - aMp.re[i]),
+                              z.y + al * (z.y - zp.y) + be * dm * (rv.y - aMp.im[i]));
+        }
+        if (cc.do_l) {
+          const C z = zL[pf];
+          const C zp = cc.prev_zero_l ? mk<T>(0, 0) : zL_prev[pf];
+          const T al = (T)cc.alpha_l, be = (T)cc.beta_l;
+          const T rr = out ? T(0) : rv.x, ri = out ? T(0) : rv.y;
+          zL_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dl * (rr - aLp.re[i]),
+                              z.y + al * (z.y - zp.y) + be * dl * (ri - aLp.im[i]));
+        }
+      }
+    }
+  }
+}
+
+// z_p = mu zM + j omega rho zL
+template <typename T>
+__global__ void k_pc_combine(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zM,
+                             const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ z) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= a.P * a.ld) return;
+  const int k = (int)(f % a.ld);
+  const T mu = (T)a.mu, wr = (T)(a.omega[k] * a.rho);
+  auto m_ = zM[f];
+  auto l_ = zL[f];
+  z[(int64_t)dim * a.N * a.ld + f] = mk<T>(mu * m_.x - wr * l_.y, mu * m_.y + wr * l_.x);
+}
+
+// Chebyshev recurrence coefficients for the interval [lo, hi] (Saad, Iterative
+// Methods for Sparse Linear Systems, Alg. 12.1): theta = (hi+lo)/2,
+// delta = (hi-lo)/2, sigma = theta/delta, rho_0 = 1/sigma,
+// rho_i = 1/(2 sigma - rho_{i-1}), alpha_i = rho_i rho_{i-1}, beta_i = 2 rho_i/delta.
+struct ChebSeq {
+  double inv_theta;
+  std::vector<double> alpha, beta;
+};
+static ChebSeq cheb_seq(double lo, double hi, int s) {
+  ChebSeq q;
+  double th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sg = th / de;
+  q.inv_theta = 1.0 / th;
+  double rho_prev = 1.0 / sg;
+  q.alpha.assign(std::max(s, 1), 0.0);
+  q.beta.assign(std::max(s, 1), 0.0);
+  for (int i = 1; i < s; ++i) {
+    double rho = 1.0 / (2.0 * sg - rho_prev);
+    q.alpha[i] = rho * rho_prev;
+    q.beta[i] = 2.0 * rho / de;
+    rho_prev = rho;
+  }
+  return q;
+}
+
+constexpr double CHEB_RATIO_U = 30.0, CHEB_RATIO_M = 6.0, CHEB_RATIO_L = 300.0, CHEB_TOP = 1.05;
+
+template <typename T>
+static PcArgs pc_args(const Mesh &m) {
+  const bool f = sizeof(T) == 4;
+  return PcArgs{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr,
+                f ? (const void *)m.Ks_f : (const void *)m.Ks_m, f ? (const void *)m.Ms_f : (const void *)m.Ms_m,
+                f ? (const void *)m.Mp_f : (const void *)m.Mp, f ? (const void *)m.Lp_f : (const void *)m.Lp_m,
+                m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag, m.dirmask, m.outmask, m.omega_d, m.rho, m.mu};
+}
+
+static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
+  const int su = std::max(1, c.opts.cheb_u), sm = std::max(1, c.opts.cheb_m), sl = std::max(1, c.opts.cheb_l);
+  if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl) return;
+  t.s_u = su; t.s_m = sm; t.s_l = sl;
+  std::vector<double> th(m.ld), al((size_t)su * m.ld), be((size_t)su * m.ld);
+  for (int k = 0; k < m.ld; ++k) {
+    double lam = m.lam_u[k] > 0 ? m.lam_u[k] : 2.0;
+    ChebSeq q = cheb_seq(lam / CHEB_RATIO_U, CHEB_TOP * lam, su);
+    th[k] = q.inv_theta;
+    for (int i = 0; i < su; ++i) { al[(size_t)i * m.ld + k] = q.alpha[i]; be[(size_t)i * m.ld + k] = q.beta[i]; }
+  }
+  t.inv_theta_u = m.mode_arena.alloc<double>(m.ld);
+  t.alpha_u = m.mode_arena.alloc<double>(al.size());
+  t.beta_u = m.mode_arena.alloc<double>(be.size());
+  SCVS_CUDA(cudaMemcpyAsync(t.inv_theta_u, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(t.alpha_u, al.data(), al.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(t.beta_u, be.data(), be.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  ChebSeq qm = cheb_seq(m.lam_m / CHEB_RATIO_M, CHEB_TOP * m.lam_m, sm);
+  ChebSeq ql = cheb_seq(m.lam_l / CHEB_RATIO_L, CHEB_TOP * m.lam_l, sl);
+  t.inv_theta_m = qm.inv_theta; t.am = qm.alpha; t.bm = qm.beta;
+  t.inv_theta_l = ql.inv_theta; t.al = ql.alpha; t.bl = ql.beta;
+  t.valid = true;
+}
+
+// z = P^-1 r for all modes.  scratch: a full block plus 4 pressure blocks.
+// rscale (device, [ld], may be null): r is first scaled per mode and written back.
+template <typename T>
+void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx<T>::t *z,
+                   typename cpx<T>::t *scratch, const double *rscale) {
+  using C = typename cpx<T>::t;
+  C *r = const_cast<C *>(r_in);
+  const PcArgs a = pc_args<T>(m);
+  const int64_t total = m.n_dof * m.ld;
+  const unsigned eb = ceil_div(total, 256);
+  const double cs = 2.0 * sizeof(T), blk = (double)total * cs, pb = (double)m.P * m.ld * cs;
+  if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
+    KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
+    if (m.dim == 2)
+      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, 0, 0, z, nullptr, nullptr);
+    else
+      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, 0, 0, z, nullptr, nullptr);
+    count_launch(c);
+    return;
+  }
+  PcTables &t = m.pc;
+  pc_tables(c, m, t);
+  const int64_t pblk = m.P * m.ld;
+  C *zu_other = scratch;                 // velocity part lives in dofs [0, dim N)
+  C *pM[2] = {scratch + total, scratch + total + pblk};
+  C *pL[2] = {scratch + total + 2 * pblk, scratch + total + 3 * pblk};
+  // velocity: final iterate must land in z; z_1 goes to z if s_u is odd.
+  C *uA = (t.s_u % 2 == 1) ? z : zu_other;
+  C *uB = (uA == z) ? zu_other : z;
+  {
+  KScope ks0(c, KC_PRECOND, blk * (rscale ? 3 : 2) + 2 * pb + (double)m.N * 17 + (double)m.P * 17);
+  if (m.dim == 2)
+    k_pc_step0<T, 2, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l, uA,
+                                                      pM[0], pL[0]);
+  else
+    k_pc_step0<T, 3, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l, uA,
+                                                      pM[0], pL[0]);
+  count_launch(c);
+  }
+  // Dirichlet velocity rows of the velocity iterate: identity (written by step 0)
+  const int steps = std::max(t.s_u, std::max(t.s_m, t.s_l));
+  int cu = 0, cm = 0, cl = 0;  // index of the current buffer of each polynomial
+  C *ucur = uA, *uprev = uB;
+  for (int i = 1; i < steps; ++i) {
+    ChebCoef cc{};
+    cc.do_u = i < t.s_u;
+    cc.do_m = i < t.s_m;
+    cc.do_l = i < t.s_l;
+    cc.alpha_u = t.alpha_u + (size_t)(cc.do_u ? i : 0) * m.ld;
+    cc.beta_u = t.beta_u + (size_t)(cc.do_u ? i : 0) * m.ld;
+    cc.alpha_m = cc.do_m ? t.am[i] : 0; cc.beta_m = cc.do_m ? t.bm[i] : 0;
+    cc.alpha_l = cc.do_l ? t.al[i] : 0; cc.beta_l = cc.do_l ? t.bl[i] : 0;
+    cc.prev_zero_u = cc.prev_zero_m = cc.prev_zero_l = (i == 1);
+    const double vb = (double)m.dim * m.N * m.ld * cs;
+    double cb = 0;
+    if (cc.do_u) cb += (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + vb * (i == 1 ? 3 : 4);
+    if (cc.do_m || cc.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb;
+    if (cc.do_m) cb += pb * (i == 1 ? 2 : 3);
+    if (cc.do_l) cb += pb * (i == 1 ? 2 : 3);
+    KScope ksc(c, KC_PRECOND, cb);
+    SCVS_DISPATCH_LD(T, m.ld, {
+      const int gpb = 256 / L;
+      int64_t lo = cc.do_u ? 0 : m.N, hi = (cc.do_m || cc.do_l) ? m.N + m.P : m.N;
+      const unsigned nb = row_blocks(c, hi - lo, gpb);
+      if (m.dim == 2)
+        k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, pM[cm], pM[1 - cm], pL[cl],
+                                                         pL[1 - cl]);
+      else
+        k_pc_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, pM[cm], pM[1 - cm], pL[cl],
+                                                         pL[1 - cl]);
+    });
+    count_launch(c);
+    if (cc.do_u) std::swap(ucur, uprev);
+    if (cc.do_m) cm = 1 - cm;
+    if (cc.do_l) cl = 1 - cl;
+  }
+  {
+    KScope ksk(c, KC_PRECOND, 3 * pb);
+    k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z);
+    count_launch(c);
+  }
+}
+template void apply_precond<float>(Ctx &, Mesh &, const float2 *, float2 *, float2 *, const double *);
+template void apply_precond<double>(Ctx &, Mesh &, const double2 *, double2 *, double2 *, const double *);
+
+// ---------------------------------------------------------- power method
+// y = D^-1 A v for the real-shifted velocity block A_r (per mode) and the two P1 matrices
+// (mode-independent; evaluated on every mode column, read from column 0).
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256)
+k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename cpx<T>::t *__restrict__ y,
+            const typename cpx<T>::t *__restrict__ vM, typename cpx<T>::t *__restrict__ yM,
+            const typename cpx<T>::t *__restrict__ vL, typename cpx<T>::t *__restrict__ yL) {
+  using C = typename cpx<T>::t;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  const int ld = a.ld, koff = lane * MPL;
+  const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv, *Mpv = (const T *)a.Mpv, *Lpv = (const T *)a.Lpv;
+  for (int64_t row = (int64_t)blockIdx.x * gpb + group; row < a.N + a.P; row += (int64_t)gridDim.x * gpb) {
+    if (row < a.N) {
+      const int64_t A = row;
+      CV<T, MPL> aK[DIM], aM[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) { aK[c].zero(); aM[c].zero(); }
+      const bool dir = a.dirmask[A];
+      const int64_t r0 = a.s_ptr[A], r1 = dir ? r0 : a.s_ptr[A + 1];
+      for (int64_t base = r0; base < r1; base += L) {
+        const int64_t t = base + lane;
+        int32_t col = 0;
+        T kv = 0, mv = 0;
+        if (t < r1) { col = a.s_col[t]; kv = Kv[t]; mv = Mv[t]; }
+        const int cnt = (int)min((int64_t)L, r1 - base);
+        for (int q = 0; q < cnt; ++q) {
+          const int32_t B = gshfl<L>(gm, col, q);
+          const T kq = gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) {
+            CV<T, MPL> xv;
+            ldv<T, MPL>(xv, v + ((int64_t)B * DIM + c) * ld + koff);
+            axpy(aK[c], kq, xv);
+            axpy(aM[c], mq, xv);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        const int k = koff + i;
+        const T dr = vel_dinv<T>(a, A, a.omega[k]);
+        const T mu = (T)a.mu, wr = (T)(fabs(a.omega[k]) * a.rho);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          const int64_t f = (A * DIM + c) * ld + k;
+          T xr = mu * aK[c].re[i] + wr * aM[c].re[i], xi = mu * aK[c].im[i] + wr * aM[c].im[i];
+          if (dir) { xr = 0; xi = 0; }
+          y[f] = mk<T>(dr * xr, dr * xi);
+        }
+      }
+    } else {
+      const int64_t B = row - a.N;
+      const int64_t r0 = a.g_ptr[B], r1 = a.g_ptr[B + 1], s0 = a.s_ptr[B];
+      CV<T, MPL> aMp, aLp;
+      aMp.zero(); aLp.zero();
+      for (int64_t base = r0; base < r1; base += L) {
+        const int64_t t = base + lane;
+        int32_t col = 0;
+        T mv = 0, lv = 0;
+        if (t < r1) { col = a.s_col[s0 + (t - r0)]; mv = Mpv[t]; lv = Lpv[t]; }
+        const int cnt = (int)min((int64_t)L, r1 - base);
+        for (int q = 0; q < cnt; ++q) {
+          const int32_t Bc = gshfl<L>(gm, col, q);
+          const T mq = gshfl<L>(gm, mv, q), lq = gshfl<L>(gm, lv, q);
+          CV<T, MPL> x1, x2;
+          ldv<T, MPL>(x1, vM + (int64_t)Bc * ld + koff);
+          ldv<T, MPL>(x2, vL + (int64_t)Bc * ld + koff);
+          axpy(aMp, mq, x1);
+          axpy(aLp, lq, x2);
+        }
+      }
+      const T dm = (T)(1.0 / a.mp_diag[B]), dl = (T)(1.0 / a.lp_diag[B]);
+      CV<T, MPL> o1, o2;
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        o1.re[i] = dm * aMp.re[i]; o1.im[i] = dm * aMp.im[i];
+        o2.re[i] = dl * aLp.re[i]; o2.im[i] = dl * aLp.im[i];
+      }
+      stv<T, MPL>(yM + B * ld + koff, o1);
+      stv<T, MPL>(yL + B * ld + koff, o2);
+    }
+  }
+}
+
+// Per-mode 2-norms of a block of `rows` rows (free rows only where dirm != null,
+// rows indexed as velocity dofs), accumulated in double into out2[ld] (atomic).
+template <typename T>
+__global__ void k_block_norm2(const typename cpx<T>::t *__restrict__ v, int64_t rows, int ld, int dim,
+                              const uint8_t *__restrict__ dirm, double *out2) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  const int64_t total = rows * ld;
+  for (int64_t f = blockIdx.x * 256ll + threadIdx.x; f < total; f += (int64_t)gridDim.x * 256) {
+    if (dirm && dirm[(f / ld) / dim]) continue;
+    auto z = v[f];
+    acc += (double)z.x * z.x + (double)z.y * z.y;
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w >= ld; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < ld) atomicAdd(&out2[threadIdx.x], s[threadIdx.x]);
+}
+
+template <typename T>
+__global__ void k_block_scale(typename cpx<T>::t *v, int64_t rows, int ld, const double *__restrict__ n2) {
+  int64_t f = blockIdx.x * 256ll + threadIdx.x;
+  if (f >= rows * ld) return;
+  double nn = n2[f % ld];
+  T s = nn > 0 ? (T)(1.0 / sqrt(nn)) : T(0);
+  auto z = v[f];
+  v[f] = mk<T>(z.x * s, z.y * s);
+}
+
+__global__ void k_init_random(float2 *v, int64_t n) {
+  int64_t i = blockIdx.x * 256ll + threadIdx.x;
+  if (i >= n) return;
+  // fixed hash of the index: deterministic start vector of the power method
+  uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull;
+  h ^= h >> 31; h *= 0xBF58476D1CE4E5B9ull; h ^= h >> 29;
+  float a = (float)((h >> 40) & 0xFFFFFF) / 16777216.0f - 0.5f;
+  float b = (float)((h >> 16) & 0xFFFFFF) / 16777216.0f - 0.5f;
+  v[i] = make_float2(1.0f + a, b);
+}
+
+// Spectral radius estimates of D^-1 A for the real-shifted velocity block
+// (per mode), the P1 mass and the P1 Laplacian (power method, 40 steps, FP32).
+void spectral_bounds(Ctx &c, Mesh &m) {
+  const int ld = m.ld;
+  const int64_t nu = (int64_t)m.dim * m.N * ld, np = m.P * ld;
+  const int64_t total = m.n_dof * ld;
+  float2 *v = nullptr, *y = nullptr, *vM = nullptr, *yM = nullptr, *vL = nullptr, *yL = nullptr;
+  double *n2 = nullptr;
+  SCVS_CUDA(cudaMallocAsync(&v, total * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&vM, np * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&yM, np * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&vL, np * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&yL, np * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&n2, 3 * ld * sizeof(double), c.stream));
+  k_init_random<<<ceil_div(total, 256), 256, 0, c.stream>>>(v, total);
+  k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vM, np);
+  k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vL, np);
+  c.launches.n += 3;
+  const PcArgs a = pc_args<float>(m);
+  const unsigned nbn = (unsigned)std::min<int64_t>(ceil_div(total, 256), 4 * c.num_sms);
+  std::vector<double> h(3 * ld, 0.0);
+  const int iters = 40;
+  for (int it = 0; it < iters; ++it) {
+    SCVS_DISPATCH_LD(float, ld, {
+      const int gpb = 256 / L;
+      const unsigned nb = row_blocks(c, m.N + m.P, gpb);
+      if (m.dim == 2)
+        k_jacobi_op<float, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL);
+      else
+        k_jacobi_op<float, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL);
+    });
+    SCVS_CUDA(cudaMemsetAsync(n2, 0, 3 * ld * sizeof(double), c.stream));
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, m.dim, m.dirmask, n2);
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yM, m.P, ld, 1, nullptr, n2 + ld);
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yL, m.P, ld, 1, nullptr, n2 + 2 * ld);
+    c.launches.n += 4;
+    if (it == iters - 1) {
+      // the previous iterate had unit norm: ||y|| is the Rayleigh-type estimate
+      SCVS_CUDA(cudaMemcpyAsync(h.data(), n2, 3 * ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      break;
+    }
+    k_block_scale<float><<<ceil_div(nu, 256), 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, n2);
+    k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yM, m.P, ld, n2 + ld);
+    k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yL, m.P, ld, n2 + 2 * ld);
+    c.launches.n += 3;
+    std::swap(v, y);
+    std::swap(vM, yM);
+    std::swap(vL, yL);
+  }
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  m.lam_u.assign(ld, 0.0);
+  for (int k = 0; k < ld; ++k) m.lam_u[k] = std::sqrt(h[k]);
+  // every mode column of the P1 blocks carries the same operator: use column 0
+  m.lam_m = std::sqrt(h[ld + 0]);
+  m.lam_l = std::sqrt(h[2 * ld + 0]);
+  for (float2 *p : {v, y, vM, yM, vL, yL}) SCVS_CUDA(cudaFreeAsync(p, c.stream));
+  SCVS_CUDA(cudaFreeAsync(n2, c.stream));
+}
+
+// Residual of the current FP64 iterate: r = b - A_hat x (FP64 SpMM) and the
+// per-mode squared free-row norms into norm2_out_dev[ld].
+void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev) {
+  const int64_t total = m.n_dof * m.ld;
+  double2 *ax = nullptr;
+  double *part = nullptr;
+  SCVS_CUDA(cudaMallocAsync(&ax, total * sizeof(double2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&part, (size_t)4 * c.num_sms * m.ld * sizeof(double), c.stream));
+  launch_saddle<double>(c, m, saddle_args<double>(c, m, true), m.x, ax);
+  double2 *r = r64 ? r64 : ax;
+  {
+    KScope ks(c, KC_VECTOR, (double)total * (32 + 16 + (r32 ? 8 : 0)));
+    k_residual_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(m.b, ax, m.dirmask, m.N, m.dim, total, m.ld, r32,
+                                                                  r64 ? r64 : ax);
+    count_launch(c);
+  }
+  mode_norms2(c, m, r, part, norm2_out_dev);
+  SCVS_CUDA(cudaFreeAsync(ax, c.stream));
+  SCVS_CUDA(cudaFreeAsync(part, c.stream));
+}
+
+}  // namespace scvs

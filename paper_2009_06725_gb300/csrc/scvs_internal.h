@@ -1,0 +1,165 @@
+// Internal host-side structures of the SCVS library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include "../../include/scvs.h"
+#include "common.cuh"
+
+namespace scvs {
+
+// Device allocations owned by one object, released together.
+struct DevArena {
+  std::vector<void *> ptrs;
+  template <typename T> T *alloc(size_t count) {
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) { (void)cudaGetLastError(); throw std::bad_alloc(); }
+    ptrs.push_back(p);
+    return static_cast<T *>(p);
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// Counts every kernel launch of a context (reported by scvs_launch_count).
+struct Launches { int64_t n = 0; };
+
+// Kernel classes timed by the optional event timers (scvs_kernel_timers).
+enum KClass : int {
+  KC_SPMM32 = 0, KC_SPMM64, KC_PRECOND, KC_ARNOLDI, KC_VECTOR, KC_ASSEMBLY, KC_RECON, KC_MATFREE, KC_COUNT
+};
+
+// CUDA-event timing of kernel launches on the launching stream: a start and a
+// stop event around each timed launch, resolved lazily; also sums the
+// algorithmic bytes of each launch (what the kernel must move at minimum).
+struct KTimers {
+  bool on = false;
+  struct Pend { cudaEvent_t a, b; int cls; double bytes; };
+  std::vector<Pend> pend;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  double ms[KC_COUNT] = {0}, bytes[KC_COUNT] = {0};
+  int64_t n[KC_COUNT] = {0};
+  cudaEvent_t cur_a = nullptr;
+  void begin(cudaStream_t s);
+  void end(cudaStream_t s, int cls, double bytes);
+  void resolve();
+  void reset();
+  void destroy();
+};
+
+// Per-mode Chebyshev coefficients of the block preconditioner of one mesh.
+struct PcTables {
+  double *inv_theta_u = nullptr, *alpha_u = nullptr, *beta_u = nullptr;  // device, [ld], [s_u][ld]
+  std::vector<double> am, bm, al, bl;  // P1 mass / Laplacian recurrences
+  double inv_theta_m = 0, inv_theta_l = 0;
+  int s_u = 0, s_m = 0, s_l = 0;
+  bool valid = false;
+};
+
+// One mesh and the state of its modes.
+//
+// Patterns: S (P2 x P2) is stored once; because vertex nodes carry the
+// smallest ids, the columns < P of an S row are a prefix of it, and that
+// prefix is the G row (P2 x P1); the S rows of the vertices (ids < P) are the
+// G^T rows, and the G rows of the vertices are the Q rows (P1 x P1).
+struct Mesh {
+  int dim = 0, nl = 0, nv = 0;
+  int64_t N = 0, P = 0, E = 0, n_dof = 0, n_dir = 0;
+  DevArena arena;
+  double *xyz = nullptr;
+  int32_t *conn = nullptr;
+  uint8_t *tag = nullptr;
+  double *geom = nullptr;           // [E][GEOM_STRIDE]
+  int64_t *n2e_ptr = nullptr;       // [N+1] node -> incident elements
+  int32_t *n2e = nullptr;           // ascending element ids per node
+  int64_t *s_ptr = nullptr;         // [N+1]
+  int32_t *s_col = nullptr;         // [s_nnz]
+  int32_t *s_len = nullptr;         // [N]
+  int32_t *g_len = nullptr;         // [N] leading columns < P
+  int64_t *g_ptr = nullptr;         // [N+1] G row pointers
+  int64_t s_nnz = 0, g_nnz = 0, gt_nnz = 0, q_nnz = 0;
+  int max_row = 0;
+  // FP64 values, unmasked (pattern order)
+  double *Ms = nullptr, *Ks = nullptr;   // [s_nnz]
+  double *Dv = nullptr;                  // [dim][g_nnz]
+  double *DTv = nullptr;                 // [dim][gt_nnz]
+  double *Mp = nullptr, *Lp = nullptr;   // [q_nnz]
+  // operator values with Dirichlet rows/columns removed
+  double *Ms_m = nullptr, *Ks_m = nullptr, *Dv_m = nullptr, *DTv_m = nullptr, *Lp_m = nullptr;
+  float *Ms_f = nullptr, *Ks_f = nullptr, *Dv_f = nullptr, *DTv_f = nullptr, *Mp_f = nullptr, *Lp_f = nullptr;
+  double *ms_diag = nullptr, *ks_diag = nullptr;  // [N]
+  double *mp_diag = nullptr, *lp_diag = nullptr;  // [P] (lp: outlet rows -> 1)
+  uint8_t *dirmask = nullptr;  // [N]
+  uint8_t *outmask = nullptr;  // [P]
+  int64_t *dir_nodes = nullptr;  // [n_dir] ascending
+  double rho = 1.0, mu = 1.0;
+  // ---- modes
+  int m = 0, ld = 0;
+  DevArena mode_arena;
+  std::vector<double> omega;     // host copy [ld] (padded with 0)
+  double *omega_d = nullptr;     // [ld]
+  double2 *g = nullptr;          // [m][n_dir][dim]
+  double2 *b = nullptr;          // [n_dof][ld] lifted RHS (b_D = g)
+  double2 *x = nullptr;          // [n_dof][ld] FP64 solution
+  std::vector<double> bnorm;     // [ld] ||b_F||
+  std::vector<double> lam_u;     // [ld] spectral radius estimate of D_u^-1 A_u per mode
+  double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
+  PcTables pc;
+  bool solved = false;
+  std::vector<scvs_mode_report> rep;
+};
+
+struct Ctx {
+  scvs_opts opts;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  std::string err;
+  Launches launches;
+  std::vector<Mesh *> meshes;
+  DevArena work;            // Krylov workspace, grown on demand
+  size_t work_bytes = 0;
+  int *dev_err = nullptr;   // device error word (DevErr bits)
+  GridSync *gsync = nullptr;
+  RefTables ref2, ref3;
+  KTimers timers;
+};
+
+// Scoped timing of one launch: KT(c, class, algorithmic bytes) { launch; }
+struct KScope {
+  Ctx &c; int cls; double bytes;
+  KScope(Ctx &c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) { if (c.timers.on) c.timers.begin(c.stream); }
+  ~KScope() { if (c.timers.on) c.timers.end(c.stream, cls, bytes); }
+};
+
+// ---- assembly.cu
+void build_mesh(Ctx &c, Mesh &m, const double *xyz_dev, const int32_t *conn_dev, const uint8_t *tag_dev);
+void scan_exclusive(Ctx &c, const int32_t *in, int64_t *out, int64_t n);
+
+// ---- operators.cu
+template <typename T>
+void apply_saddle(Ctx &c, const Mesh &m, const typename cpx<T>::t *x, typename cpx<T>::t *y);
+void lift_rhs(Ctx &c, Mesh &m);
+double saddle_bytes(const Mesh &m, int value_size);
+void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev);
+void spectral_bounds(Ctx &c, Mesh &m);
+template <typename T>
+void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r, typename cpx<T>::t *z,
+                   typename cpx<T>::t *scratch, const double *rscale);
+void apply_matfree(Ctx &c, const Mesh &m, int precision, const void *x, void *y);
+void matfree_tables(Ctx &c);  // matfree.cu
+
+// ---- krylov.cu
+int solve_mesh(Ctx &c, Mesh &m);
+
+// ---- recon.cu
+void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);
+
+int dev_error(Ctx &c);  // reads and clears the device error word
+inline void count_launch(Ctx &c) { c.launches.n++; }
+
+}  // namespace scvs

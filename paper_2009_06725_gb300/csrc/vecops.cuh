@@ -1,0 +1,113 @@
+// Small vector helpers for mode-interleaved complex blocks.
+//
+// A thread ("lane" of a row group of L threads) owns MPL consecutive modes of
+// a row; a row of a block is ld = L * MPL complex numbers, so a group reads
+// one contiguous row with vector loads.
+#pragma once
+#include "common.cuh"
+
+namespace scvs {
+
+template <typename T, int MPL> struct CV {
+  T re[MPL], im[MPL];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) { re[i] = T(0); im[i] = T(0); }
+  }
+};
+
+template <typename T, int MPL>
+__device__ __forceinline__ void ldv(CV<T, MPL> &v, const typename cpx<T>::t *p) {
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) { auto z = __ldg(p + i); v.re[i] = z.x; v.im[i] = z.y; }
+}
+template <>
+__device__ __forceinline__ void ldv<float, 2>(CV<float, 2> &v, const float2 *p) {
+  float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+  v.re[0] = f.x; v.im[0] = f.y; v.re[1] = f.z; v.im[1] = f.w;
+}
+template <>
+__device__ __forceinline__ void ldv<float, 4>(CV<float, 4> &v, const float2 *p) {
+  float4 f = __ldg(reinterpret_cast<const float4 *>(p));
+  float4 g = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  v.re[0] = f.x; v.im[0] = f.y; v.re[1] = f.z; v.im[1] = f.w;
+  v.re[2] = g.x; v.im[2] = g.y; v.re[3] = g.z; v.im[3] = g.w;
+}
+// plain (coherent) load for buffers written earlier in the same kernel
+template <typename T, int MPL>
+__device__ __forceinline__ void ldv_cg(CV<T, MPL> &v, const typename cpx<T>::t *p) {
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) { auto z = p[i]; v.re[i] = z.x; v.im[i] = z.y; }
+}
+template <>
+__device__ __forceinline__ void ldv_cg<float, 2>(CV<float, 2> &v, const float2 *p) {
+  float4 f = *reinterpret_cast<const float4 *>(p);
+  v.re[0] = f.x; v.im[0] = f.y; v.re[1] = f.z; v.im[1] = f.w;
+}
+
+template <typename T, int MPL>
+__device__ __forceinline__ void stv(typename cpx<T>::t *p, const CV<T, MPL> &v) {
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) p[i] = mk<T>(v.re[i], v.im[i]);
+}
+template <>
+__device__ __forceinline__ void stv<float, 2>(float2 *p, const CV<float, 2> &v) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v.re[0], v.im[0], v.re[1], v.im[1]);
+}
+template <>
+__device__ __forceinline__ void stv<float, 4>(float2 *p, const CV<float, 4> &v) {
+  reinterpret_cast<float4 *>(p)[0] = make_float4(v.re[0], v.im[0], v.re[1], v.im[1]);
+  reinterpret_cast<float4 *>(p)[1] = make_float4(v.re[2], v.im[2], v.re[3], v.im[3]);
+}
+
+// acc += s * v (s real)
+template <typename T, int MPL>
+__device__ __forceinline__ void axpy(CV<T, MPL> &acc, T s, const CV<T, MPL> &v) {
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) { acc.re[i] = fma(s, v.re[i], acc.re[i]); acc.im[i] = fma(s, v.im[i], acc.im[i]); }
+}
+
+// Row-group shuffle: broadcast from lane q of this group of L lanes.
+template <int L, typename V>
+__device__ __forceinline__ V gshfl(unsigned mask, V v, int q) {
+  return __shfl_sync(mask, v, q, L);
+}
+
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+  if (L >= 32) return 0xffffffffu;
+  const unsigned base = (threadIdx.x & 31) / L * L;
+  return ((1u << L) - 1u) << base;
+}
+
+// Dispatch a lambda on (MPL, L) for a row stride ld (power of 2, 2..128).
+// FP32 blocks use 2 modes per lane (16-byte loads), FP64 blocks 1 mode per
+// lane (16-byte loads); strides beyond 32 lanes raise the modes per lane.
+#define SCVS_DISPATCH_LD(T, ld, ...)                                          \
+  do {                                                                         \
+    if constexpr (sizeof(T) == 4) {                                            \
+      switch (ld) {                                                            \
+        case 2: { constexpr int MPL = 2, L = 1; __VA_ARGS__; } break;                 \
+        case 4: { constexpr int MPL = 2, L = 2; __VA_ARGS__; } break;                 \
+        case 8: { constexpr int MPL = 2, L = 4; __VA_ARGS__; } break;                 \
+        case 16: { constexpr int MPL = 2, L = 8; __VA_ARGS__; } break;                \
+        case 32: { constexpr int MPL = 2, L = 16; __VA_ARGS__; } break;               \
+        case 64: { constexpr int MPL = 2, L = 32; __VA_ARGS__; } break;               \
+        case 128: { constexpr int MPL = 4, L = 32; __VA_ARGS__; } break;              \
+        default: throw (int)SCVS_ERR_ARG;                                      \
+      }                                                                        \
+    } else {                                                                   \
+      switch (ld) {                                                            \
+        case 2: { constexpr int MPL = 1, L = 2; __VA_ARGS__; } break;                 \
+        case 4: { constexpr int MPL = 1, L = 4; __VA_ARGS__; } break;                 \
+        case 8: { constexpr int MPL = 1, L = 8; __VA_ARGS__; } break;                 \
+        case 16: { constexpr int MPL = 1, L = 16; __VA_ARGS__; } break;               \
+        case 32: { constexpr int MPL = 1, L = 32; __VA_ARGS__; } break;               \
+        case 64: { constexpr int MPL = 2, L = 32; __VA_ARGS__; } break;               \
+        case 128: { constexpr int MPL = 4, L = 32; __VA_ARGS__; } break;              \
+        default: throw (int)SCVS_ERR_ARG;                                      \
+      }                                                                        \
+    }                                                                          \
+  } while (0)
+
+}  // namespace scvs

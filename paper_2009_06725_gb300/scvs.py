@@ -1,0 +1,306 @@
+"""Thin ctypes binding of the SCVS C ABI (include/scvs.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA kernels
+of ``libscvs.so``.  Functions carry the C names; host arrays are numpy arrays
+(copied in/out by the library), device arrays are passed as integer device
+addresses (for example ``torch.Tensor.data_ptr()``).  There is no fallback:
+if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libscvs.so")
+
+SCVS_OK = 0
+SCVS_ERR_ARG, SCVS_ERR_MESH, SCVS_ERR_PRESSURE_NULLSPACE = -1, -2, -3
+SCVS_ERR_OOM, SCVS_ERR_CUDA, SCVS_ERR_STATE, SCVS_ERR_TIMEOUT = -4, -5, -6, -7
+SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET = 1, 2, 4
+SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
+SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
+SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG = 0, 1
+SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
+SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
+SCVS_KC_COUNT = 8
+STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "stagnated", 3: "non_finite"}
+
+
+class scvs_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("precision", C.c_int32),
+                ("precond", C.c_int32), ("cheb_u", C.c_int32), ("cheb_m", C.c_int32),
+                ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
+                ("verbose", C.c_int32), ("stream", C.c_void_p)]
+
+
+class scvs_mode_report(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("cycles", C.c_int32),
+                ("reserved", C.c_int32), ("rel_res", C.c_double)]
+
+
+class ScvsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"scvs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_P = C.c_void_p
+_I32, _I64, _D = C.c_int32, C.c_int64, C.c_double
+SIGNATURES = {
+    "scvs_default_opts": (None, [C.POINTER(scvs_opts)]),
+    "scvs_create": (_I32, [C.POINTER(_P), C.POINTER(scvs_opts)]),
+    "scvs_destroy": (None, [_P]),
+    "scvs_last_error": (C.c_char_p, [_P]),
+    "scvs_set_opts": (_I32, [_P, C.POINTER(scvs_opts)]),
+    "scvs_set_mesh": (_I32, [_P, _I32, _I64, _I64, _P, _I64, _P, _P]),
+    "scvs_set_mesh_dev": (_I32, [_P, _I32, _I64, _I64, _P, _I64, _P, _P]),
+    "scvs_clear_meshes": (_I32, [_P]),
+    "scvs_set_physics": (_I32, [_P, _I32, _D, _D]),
+    "scvs_dirichlet_count": (_I32, [_P, _I32, C.POINTER(_I64)]),
+    "scvs_set_modes": (_I32, [_P, _I32, _I32, _P, _P]),
+    "scvs_set_modes_dev": (_I32, [_P, _I32, _I32, _P, _P]),
+    "scvs_solve": (_I32, [_P, _I32, C.POINTER(scvs_mode_report), _I64]),
+    "scvs_get_modal": (_I32, [_P, _I32, _P, _P]),
+    "scvs_modal_dev": (_I32, [_P, _I32, C.POINTER(_P), C.POINTER(_I64), C.POINTER(_I32)]),
+    "scvs_reconstruct": (_I32, [_P, _I32, _I32, _D, _P, _P]),
+    "scvs_reconstruct_dev": (_I32, [_P, _I32, _I32, _D, _P, _P]),
+    "scvs_csr_size": (_I32, [_P, _I32, _I32, C.POINTER(_I64), C.POINTER(_I64)]),
+    "scvs_get_csr": (_I32, [_P, _I32, _I32, _P, _P]),
+    "scvs_get_values": (_I32, [_P, _I32, _I32, _P]),
+    "scvs_mode_stride": (_I32, [_P, _I32, C.POINTER(_I32)]),
+    "scvs_dof_count": (_I32, [_P, _I32, C.POINTER(_I64)]),
+    "scvs_apply": (_I32, [_P, _I32, _I32, _P, _P]),
+    "scvs_apply_matfree": (_I32, [_P, _I32, _I32, _P, _P]),
+    "scvs_rhs_dev": (_I32, [_P, _I32, C.POINTER(_P)]),
+    "scvs_apply_precond": (_I32, [_P, _I32, _P, _P]),
+    "scvs_launch_count": (_I64, [_P]),
+    "scvs_kernel_timers": (_I32, [_P, _I32]),
+    "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
+}
+KERNEL_CLASSES = ["spmm_fp32", "spmm_fp64", "precond", "arnoldi", "vector", "assembly", "reconstruct", "matfree"]
+
+
+def lib():
+    """Load libscvs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} not built: run paper_2009_06725_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, rc):
+    if rc < 0:
+        msg = lib().scvs_last_error(ctx)
+        raise ScvsError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def scvs_default_opts(**overrides):
+    o = scvs_opts()
+    lib().scvs_default_opts(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def scvs_create(opts=None):
+    h = C.c_void_p()
+    rc = lib().scvs_create(C.byref(h), C.byref(opts) if opts is not None else None)
+    if rc < 0:
+        raise ScvsError(rc, "scvs_create failed")
+    return h
+
+
+def scvs_destroy(ctx):
+    lib().scvs_destroy(ctx)
+
+
+def scvs_last_error(ctx):
+    return lib().scvs_last_error(ctx).decode()
+
+
+def scvs_set_opts(ctx, opts):
+    return _check(ctx, lib().scvs_set_opts(ctx, C.byref(opts)))
+
+
+def scvs_set_mesh(ctx, mesh):
+    """mesh: dict with dim, xyz float64 [N][d], conn int32 [E][nl], tag uint8 [N], n_vertices."""
+    xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+    conn = np.ascontiguousarray(mesh["conn"], dtype=np.int32)
+    tag = np.ascontiguousarray(mesh["tag"], dtype=np.uint8)
+    return _check(ctx, lib().scvs_set_mesh(ctx, int(mesh["dim"]), xyz.shape[0], int(mesh["n_vertices"]),
+                                           _ptr(xyz), conn.shape[0], _ptr(conn), _ptr(tag)))
+
+
+def scvs_set_mesh_dev(ctx, dim, n_nodes, n_vertices, xyz_dev, n_elem, conn_dev, tag_dev):
+    return _check(ctx, lib().scvs_set_mesh_dev(ctx, dim, n_nodes, n_vertices, xyz_dev, n_elem, conn_dev, tag_dev))
+
+
+def scvs_clear_meshes(ctx):
+    return _check(ctx, lib().scvs_clear_meshes(ctx))
+
+
+def scvs_set_physics(ctx, mesh_id, rho, mu):
+    return _check(ctx, lib().scvs_set_physics(ctx, mesh_id, rho, mu))
+
+
+def scvs_dirichlet_count(ctx, mesh_id):
+    n = C.c_int64()
+    _check(ctx, lib().scvs_dirichlet_count(ctx, mesh_id, C.byref(n)))
+    return n.value
+
+
+def scvs_set_modes(ctx, mesh_id, omega, g):
+    """omega float64 [m]; g complex128 [m][n_dir][dim]."""
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    gg = np.ascontiguousarray(g, dtype=np.complex128)
+    return _check(ctx, lib().scvs_set_modes(ctx, mesh_id, om.size, _ptr(om), _ptr(gg)))
+
+
+def scvs_set_modes_dev(ctx, mesh_id, omega, g_dev):
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    return _check(ctx, lib().scvs_set_modes_dev(ctx, mesh_id, om.size, _ptr(om), g_dev))
+
+
+def scvs_solve(ctx, mesh_id=-1, n_reports=0):
+    """Returns a list of dicts (status, iterations, cycles, rel_res)."""
+    rep = (scvs_mode_report * max(1, n_reports))()
+    _check(ctx, lib().scvs_solve(ctx, mesh_id, rep, n_reports))
+    return [dict(status=r.status, iterations=r.iterations, cycles=r.cycles, rel_res=r.rel_res)
+            for r in rep[:n_reports]]
+
+
+def scvs_get_modal(ctx, mesh_id, n_modes, n_nodes, dim, n_vertices):
+    u = np.empty((n_modes, n_nodes, dim), dtype=np.complex128)
+    p = np.empty((n_modes, n_vertices), dtype=np.complex128)
+    _check(ctx, lib().scvs_get_modal(ctx, mesh_id, _ptr(u), _ptr(p)))
+    return u, p
+
+
+def scvs_modal_dev(ctx, mesh_id):
+    x = C.c_void_p()
+    n = C.c_int64()
+    ld = C.c_int32()
+    _check(ctx, lib().scvs_modal_dev(ctx, mesh_id, C.byref(x), C.byref(n), C.byref(ld)))
+    return x.value, n.value, ld.value
+
+
+def scvs_reconstruct(ctx, mesh_id, n_t, period, n_nodes, dim, n_vertices):
+    u = np.empty((n_t, n_nodes, dim), dtype=np.float64)
+    p = np.empty((n_t, n_vertices), dtype=np.float64)
+    _check(ctx, lib().scvs_reconstruct(ctx, mesh_id, n_t, period, _ptr(u), _ptr(p)))
+    return u, p
+
+
+def scvs_reconstruct_dev(ctx, mesh_id, n_t, period, u_dev, p_dev):
+    return _check(ctx, lib().scvs_reconstruct_dev(ctx, mesh_id, n_t, period, u_dev, p_dev))
+
+
+def scvs_csr_size(ctx, mesh_id, which):
+    r, z = C.c_int64(), C.c_int64()
+    _check(ctx, lib().scvs_csr_size(ctx, mesh_id, which, C.byref(r), C.byref(z)))
+    return r.value, z.value
+
+
+def scvs_get_csr(ctx, mesh_id, which):
+    nr, nnz = scvs_csr_size(ctx, mesh_id, which)
+    rowptr = np.empty(nr + 1, dtype=np.int64)
+    col = np.empty(max(nnz, 1), dtype=np.int32)
+    _check(ctx, lib().scvs_get_csr(ctx, mesh_id, which, _ptr(rowptr), _ptr(col)))
+    return rowptr, col[:nnz]
+
+
+def scvs_get_values(ctx, mesh_id, which, dim):
+    _, nnz = scvs_csr_size(ctx, mesh_id, which)
+    rows = 2 if which in (SCVS_CSR_S, SCVS_CSR_Q) else dim
+    v = np.empty((rows, max(nnz, 1)), dtype=np.float64)
+    _check(ctx, lib().scvs_get_values(ctx, mesh_id, which, _ptr(v)))
+    return v[:, :nnz]
+
+
+def scvs_mode_stride(ctx, mesh_id):
+    ld = C.c_int32()
+    _check(ctx, lib().scvs_mode_stride(ctx, mesh_id, C.byref(ld)))
+    return ld.value
+
+
+def scvs_dof_count(ctx, mesh_id):
+    n = C.c_int64()
+    _check(ctx, lib().scvs_dof_count(ctx, mesh_id, C.byref(n)))
+    return n.value
+
+
+def scvs_apply(ctx, mesh_id, precision, x_dev, y_dev):
+    return _check(ctx, lib().scvs_apply(ctx, mesh_id, precision, x_dev, y_dev))
+
+
+def scvs_apply_matfree(ctx, mesh_id, precision, x_dev, y_dev):
+    return _check(ctx, lib().scvs_apply_matfree(ctx, mesh_id, precision, x_dev, y_dev))
+
+
+def scvs_rhs_dev(ctx, mesh_id):
+    b = C.c_void_p()
+    _check(ctx, lib().scvs_rhs_dev(ctx, mesh_id, C.byref(b)))
+    return b.value
+
+
+def scvs_apply_precond(ctx, mesh_id, r_dev, z_dev):
+    return _check(ctx, lib().scvs_apply_precond(ctx, mesh_id, r_dev, z_dev))
+
+
+def scvs_launch_count(ctx):
+    return lib().scvs_launch_count(ctx)
+
+
+def scvs_kernel_timers(ctx, enable):
+    return _check(ctx, lib().scvs_kernel_timers(ctx, 1 if enable else 0))
+
+
+def scvs_kernel_times(ctx):
+    """{class: (ms, algorithmic bytes, launches)} summed since the timers were enabled."""
+    n = len(KERNEL_CLASSES)
+    ms = np.zeros(n)
+    by = np.zeros(n)
+    ln = np.zeros(n, dtype=np.int64)
+    _check(ctx, lib().scvs_kernel_times(ctx, n, _ptr(ms), _ptr(by), _ptr(ln)))
+    return {k: (float(ms[i]), float(by[i]), int(ln[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+class Solver:
+    """Convenience owner of one context (closes it on exit)."""
+
+    def __init__(self, **opts):
+        self.opts = scvs_default_opts(**opts)
+        self.ctx = scvs_create(self.opts)
+
+    def close(self):
+        if self.ctx is not None:
+            scvs_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        scvs_set_opts(self.ctx, self.opts)

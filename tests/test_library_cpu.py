@@ -1,0 +1,43 @@
+"""The C-ABI library builds, loads and exports every declared entry point
+(no GPU needed; no compute call is made)."""
+import os
+import re
+
+import pytest
+
+from paper_2009_06725_gb300 import build, scvs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "scvs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(scvs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_builds_and_loads():
+    path = build.build()
+    assert os.path.exists(path)
+    assert scvs.lib() is not None
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 25
+    L = scvs.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(scvs.SIGNATURES), set(names) ^ set(scvs.SIGNATURES)
+
+
+def test_default_options():
+    o = scvs.scvs_default_opts()
+    assert o.tol == 1e-8 and o.restart == 30 and o.precision == scvs.SCVS_PREC_MIXED
+    assert o.cheb_u >= 1 and o.max_cycles >= 1
+
+
+def test_header_constants_match_binding():
+    src = open(os.path.join(ROOT, "include", "scvs.h")).read()
+    for name, val in re.findall(r"#define (SCVS_[A-Z0-9_]+) \(?(-?\d+)\)?", src):
+        assert getattr(scvs, name) == int(val), name
