@@ -163,6 +163,30 @@ int scvs_reconstruct(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
 int scvs_reconstruct_dev(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
                          double *u_t_dev, double *p_t_dev);
 
+/* Allocation-free variant of scvs_reconstruct_dev (the paper has no
+ * counterpart: this is a deployment convenience).  It is for callers that
+ * must not allocate device memory during the call: code running while a
+ * framework's caching allocator holds nearly all of the GPU's memory (a
+ * cudaMalloc could fail or fragment it), and latency-critical pipelines that
+ * cannot afford the device-wide synchronisation that cudaMalloc/cudaFree
+ * imply.  The caller passes the modal solution (held by the context) and the
+ * output buffers; the twiddle scratch e^{j omega_k t_s} lives in one
+ * file-scope device table of SCVS_RECON_STATIC_MAX double2 entries (128 KiB),
+ * which every GPU that loads the library holds until the process exits.
+ * Limits and behaviour:
+ *  - n_t * n_modes must not exceed SCVS_RECON_STATIC_MAX, else SCVS_ERR_ARG;
+ *  - nothing is allocated: no cudaMalloc, cudaFree or allocating library call;
+ *  - the first call on a device looks up the table's device address
+ *    (cudaGetSymbolAddress) for that device; make that first call before any
+ *    stream capture;
+ *  - every call overwrites the whole table, so nothing carries over between
+ *    calls, but calls that overlap on the GPU (e.g. on two streams) race on
+ *    the table: serialise them.
+ * Output layout and accuracy are those of scvs_reconstruct_dev. */
+#define SCVS_RECON_STATIC_MAX 8192
+int scvs_reconstruct_dev_static(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
+                                double *u_t_dev, double *p_t_dev);
+
 /* ---- parity / inspection ------------------------------------------------ */
 #define SCVS_CSR_S 0  /* P2 x P2 scalar pattern (values M_s, K_s) */
 #define SCVS_CSR_G 1  /* P2 rows x P1 columns (values D_c) */

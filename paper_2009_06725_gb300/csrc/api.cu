@@ -383,6 +383,19 @@ int scvs_reconstruct_dev(scvs_ctx *c, int32_t mesh_id, int32_t n_t, double perio
   });
 }
 
+int scvs_reconstruct_dev_static(scvs_ctx *c, int32_t mesh_id, int32_t n_t, double period, double *u_t, double *p_t) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    if (n_t < 1 || !(period > 0)) return fail(c, SCVS_ERR_ARG, "n_t >= 1 and period > 0 required");
+    if ((int64_t)n_t * m->m > SCVS_RECON_STATIC_MAX)
+      return fail(c, SCVS_ERR_ARG, "n_t * n_modes exceeds SCVS_RECON_STATIC_MAX (" +
+                                       std::to_string(SCVS_RECON_STATIC_MAX) + ") twiddles of the static table");
+    reconstruct_static(*c, *m, n_t, period, u_t, p_t);
+    return SCVS_OK;
+  });
+}
+
 int scvs_reconstruct(scvs_ctx *c, int32_t mesh_id, int32_t n_t, double period, double *u_t, double *p_t) {
   return guarded(c, [&]() {
     Mesh *m = get_mesh(c, mesh_id);

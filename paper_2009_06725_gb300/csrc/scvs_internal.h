@@ -158,6 +158,7 @@ int solve_mesh(Ctx &c, Mesh &m);
 
 // ---- recon.cu
 void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);
+void reconstruct_static(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);
 
 int dev_error(Ctx &c);  // reads and clears the device error word
 inline void count_launch(Ctx &c) { c.launches.n++; }

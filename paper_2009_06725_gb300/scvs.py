@@ -26,6 +26,7 @@ SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG = 0, 1
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
 SCVS_KC_COUNT = 8
+SCVS_RECON_STATIC_MAX = 8192
 STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "stagnated", 3: "non_finite"}
 
 
@@ -69,6 +70,7 @@ SIGNATURES = {
     "scvs_modal_dev": (_I32, [_P, _I32, C.POINTER(_P), C.POINTER(_I64), C.POINTER(_I32)]),
     "scvs_reconstruct": (_I32, [_P, _I32, _I32, _D, _P, _P]),
     "scvs_reconstruct_dev": (_I32, [_P, _I32, _I32, _D, _P, _P]),
+    "scvs_reconstruct_dev_static": (_I32, [_P, _I32, _I32, _D, _P, _P]),
     "scvs_csr_size": (_I32, [_P, _I32, _I32, C.POINTER(_I64), C.POINTER(_I64)]),
     "scvs_get_csr": (_I32, [_P, _I32, _I32, _P, _P]),
     "scvs_get_values": (_I32, [_P, _I32, _I32, _P]),
@@ -210,6 +212,11 @@ def scvs_reconstruct(ctx, mesh_id, n_t, period, n_nodes, dim, n_vertices):
 
 def scvs_reconstruct_dev(ctx, mesh_id, n_t, period, u_dev, p_dev):
     return _check(ctx, lib().scvs_reconstruct_dev(ctx, mesh_id, n_t, period, u_dev, p_dev))
+
+
+def scvs_reconstruct_dev_static(ctx, mesh_id, n_t, period, u_dev, p_dev):
+    """Allocation-free reconstruction (static twiddle table; see include/scvs.h)."""
+    return _check(ctx, lib().scvs_reconstruct_dev_static(ctx, mesh_id, n_t, period, u_dev, p_dev))
 
 
 def scvs_csr_size(ctx, mesh_id, which):
