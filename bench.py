@@ -304,6 +304,37 @@ def run_gpu(args):
     solver.close()
 
 
+def run_kernel_case(args):
+    """Launch-light sequence on the full-size pipe for profiler captures:
+    assembly, mode set-up, 3 all-modes SpMMs (FP32), 2 preconditioner
+    applications and one GMRES(4) cycle (4 Arnoldi steps)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2009_06725_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2009_06725_gb300 import scvs
+    wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=PIPE["n_x"], n_modes=PIPE["n_modes"],
+                                 length=PIPE["length"])
+    mesh = wl["mesh"]
+    with scvs.Solver(restart=4, max_cycles=1) as s:
+        mid = scvs.scvs_set_mesh(s.ctx, mesh)
+        scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
+        scvs.scvs_set_modes(s.ctx, mid, wl["omegas"], wl["g"])
+        n = scvs.scvs_dof_count(s.ctx, mid)
+        ld = scvs.scvs_mode_stride(s.ctx, mid)
+        x = torch.randn((n, ld), dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            scvs.scvs_apply(s.ctx, mid, scvs.SCVS_PREC_MIXED, x.data_ptr(), y.data_ptr())
+        for _ in range(2):
+            scvs.scvs_apply_precond(s.ctx, mid, x.data_ptr(), y.data_ptr())
+        rep = scvs.scvs_solve(s.ctx, mid, len(wl["omegas"]))
+        torch.cuda.synchronize()
+        log("kernel case done:", scvs.scvs_launch_count(s.ctx), "launches; cycle iterations",
+            [r["iterations"] for r in rep][:4])
+
+
 def step_host(scvs, ctx, wl, m, N, P, d):
     mesh = wl["mesh"]
     scvs.scvs_clear_meshes(ctx)
@@ -341,7 +372,11 @@ def main():
     ap.add_argument("--cheb-u", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")
     args = ap.parse_args()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
     if args.warmup < 3 and args.impl == "gpu":
         log("note: the timing rules ask for >= 3 warm-up steps")
     if args.impl == "reference":

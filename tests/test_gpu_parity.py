@@ -108,7 +108,7 @@ def _device_view(ptr, count):
     import torch
 
     class _View:
-        __cuda_array_interface__ = {"shape": (count,), "typestr": "<c16", "data": (ptr, True), "version": 3}
+        __cuda_array_interface__ = {"shape": (count,), "typestr": "<c16", "data": (ptr, False), "version": 3}
 
     return torch.as_tensor(_View(), device="cuda").cpu().numpy()
 
@@ -207,7 +207,7 @@ def test_invalid_meshes_rejected():
             scvs.scvs_set_mesh(s.ctx, bad)
         assert e.value.code == scvs.SCVS_ERR_MESH
         t = m["tag"]
-        closed = dict(m, tag=np.where(t & 4, (t & ~4) | 1, t).astype(np.uint8))
+        closed = dict(m, tag=np.where(t & 4, (t & np.uint8(0xFB)) | np.uint8(1), t).astype(np.uint8))
         with pytest.raises(scvs.ScvsError) as e:
             scvs.scvs_set_mesh(s.ctx, closed)
         assert e.value.code == scvs.SCVS_ERR_PRESSURE_NULLSPACE
