@@ -72,6 +72,9 @@ extern "C" {
 #define SCVS_PC_BLOCK_CHEB 0   /* block-diagonal: Chebyshev-Jacobi polynomial of mu K + |omega| rho M for the
                                   velocity, Chebyshev Cahouet-Chabard mu M_p^-1 + j omega rho L_p^-1 for the pressure */
 #define SCVS_PC_BLOCK_DIAG 1   /* block-diagonal, diagonal blocks only */
+#define SCVS_PC_BLOCK_PMG 2    /* block-diagonal; velocity block by a two-level p-multigrid cycle: Chebyshev
+                                  smoothing of mu K + |omega| rho M on P2 and a Chebyshev solve of the same
+                                  operator on the nested P1 (vertex) space; pressure as BLOCK_CHEB (default) */
 
 #define SCVS_GUESS_ZERO 0
 #define SCVS_GUESS_MLP 1
@@ -83,13 +86,15 @@ typedef struct {
   double tol;        /* relative residual target per mode (default 1e-8) */
   int32_t restart;   /* GMRES restart length m_r (default 30, max 64) */
   int32_t precision; /* SCVS_PREC_* (default MIXED) */
-  int32_t precond;   /* SCVS_PC_* (default BLOCK_CHEB) */
-  int32_t cheb_u;    /* Chebyshev degree, velocity block (default 8) */
+  int32_t precond;   /* SCVS_PC_* (default BLOCK_PMG) */
+  int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with BLOCK_PMG the degree of each
+                        of the pre- and post-smoothers (default 4) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
   int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 30) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
+  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of BLOCK_PMG (default 20) */
   void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
 } scvs_opts;
 

@@ -191,8 +191,9 @@ void scvs_default_opts(scvs_opts *o) {
   o->tol = 1e-8;
   o->restart = 30;
   o->precision = SCVS_PREC_MIXED;
-  o->precond = SCVS_PC_BLOCK_CHEB;
-  o->cheb_u = 8;
+  o->precond = SCVS_PC_BLOCK_PMG;
+  o->cheb_u = 4;
+  o->cheb_c = 20;
   o->cheb_m = 4;
   o->cheb_l = 30;
   o->max_cycles = 400;
@@ -207,6 +208,7 @@ int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
   scvs_ctx *c = new (std::nothrow) scvs_ctx();
   if (!c) return SCVS_ERR_OOM;
   if (opts) c->opts = *opts; else scvs_default_opts(&c->opts);
+  if (c->opts.cheb_c < 1) c->opts.cheb_c = 20;
   int r = guarded(c, [&]() {
     SCVS_CUDA(cudaGetDevice(&c->device));
     SCVS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -248,7 +250,7 @@ const char *scvs_last_error(const scvs_ctx *c) { return c ? c->err.c_str() : "nu
 int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
   if (!c || !o) return SCVS_ERR_ARG;
   if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
-      o->max_cycles < 1)
+      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > 2)
     return fail(c, SCVS_ERR_ARG, "invalid options");
   void *old_stream = c->opts.stream;
   c->opts = *o;
@@ -540,7 +542,7 @@ int scvs_apply_precond(scvs_ctx *c, int32_t mesh_id, const void *r, void *z) {
     Mesh *m = get_mesh(c, mesh_id);
     if (!m || m->m == 0 || !r || !z) return fail(c, SCVS_ERR_ARG, "bad argument");
     float2 *s = nullptr;
-    SCVS_CUDA(cudaMallocAsync(&s, (m->n_dof + 4 * m->P) * m->ld * sizeof(float2), c->stream));
+    SCVS_CUDA(cudaMallocAsync(&s, precond_scratch_elems(*m) * sizeof(float2), c->stream));
     apply_precond<float>(*c, *m, static_cast<const float2 *>(r), static_cast<float2 *>(z), s, nullptr);
     SCVS_CUDA(cudaFreeAsync(s, c->stream));
     SCVS_CUDA(cudaGetLastError());

@@ -289,7 +289,8 @@ __global__ void k_mask_values(int64_t N, int64_t P, int dim, const int64_t *__re
                               const double *Mp, const double *Lp, double *Ms_m, double *Ks_m,
                               double *Dv_m, double *DTv_m, double *Lp_m, float *Ms_f, float *Ks_f,
                               float *Dv_f, float *DTv_f, float *Mp_f, float *Lp_f, double *ms_diag,
-                              double *ks_diag, double *mp_diag, double *lp_diag) {
+                              double *ks_diag, double *mp_diag, double *lp_diag, float *Kc_f, float *Mc_f,
+                              double *k1_diag, double *Kc_m, double *Mc_m) {
   int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (A >= N) return;
   const bool dA = dirm[A];
@@ -323,8 +324,47 @@ __global__ void k_mask_values(int64_t N, int64_t P, int dim, const int64_t *__re
       Lp_m[q] = l;
       Lp_f[q] = (float)l;
       Mp_f[q] = (float)Mp[q];
-      if (B == A) { mp_diag[A] = Mp[q]; lp_diag[A] = l; }
+      const bool keep = !dA && !dirm[B];
+      Kc_m[q] = keep ? Lp[q] : 0.0;
+      Mc_m[q] = keep ? Mp[q] : 0.0;
+      Kc_f[q] = (float)Kc_m[q];
+      Mc_f[q] = (float)Mc_m[q];
+      if (B == A) { mp_diag[A] = Mp[q]; lp_diag[A] = l; k1_diag[A] = Lp[q]; }
     }
+  }
+}
+
+// ------------------------------------------- nested P1 space (coarse level)
+__constant__ int c_edge_pairs[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
+
+// end vertices of every edge node (the same from every element sharing the edge)
+__global__ void k_edge_ends(const int32_t *__restrict__ conn, int64_t E, int nl, int dim, int64_t P, int32_t *ends) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int nv = dim + 1;
+  const int32_t *c = conn + e * nl;
+  for (int k = 0; k < nl - nv; ++k) {
+    const int64_t i = (int64_t)c[nv + k] - P;
+    ends[2 * i] = c[c_edge_pairs[k][0]];
+    ends[2 * i + 1] = c[c_edge_pairs[k][1]];
+  }
+}
+
+__global__ void k_count_v2e(const int32_t *__restrict__ ends, int64_t ne, int32_t *cnt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  atomicAdd(&cnt[ends[2 * i]], 1);
+  atomicAdd(&cnt[ends[2 * i + 1]], 1);
+}
+
+__global__ void k_fill_v2e(const int32_t *__restrict__ ends, int64_t ne, int64_t P, const int64_t *__restrict__ ptr,
+                           int32_t *fill, int32_t *v2e) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  for (int s = 0; s < 2; ++s) {
+    const int32_t v = ends[2 * i + s];
+    const int pos = atomicAdd(&fill[v], 1);
+    v2e[ptr[v] + pos] = (int32_t)(P + i);
   }
 }
 
@@ -506,11 +546,31 @@ void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, c
   m.ks_diag = m.arena.alloc<double>(N);
   m.mp_diag = m.arena.alloc<double>(P);
   m.lp_diag = m.arena.alloc<double>(P);
+  m.Kc_f = m.arena.alloc<float>(m.q_nnz);
+  m.Mc_f = m.arena.alloc<float>(m.q_nnz);
+  m.Kc_m = m.arena.alloc<double>(m.q_nnz);
+  m.Mc_m = m.arena.alloc<double>(m.q_nnz);
+  m.k1_diag = m.arena.alloc<double>(P);
   k_mask_values<<<ceil_div(N, 128), 128, 0, s>>>(
       N, P, dim, m.s_ptr, m.s_col, m.g_len, m.g_ptr, m.g_nnz, m.gt_nnz, m.dirmask, m.outmask, m.Ms, m.Ks,
       m.Dv, m.DTv, m.Mp, m.Lp, m.Ms_m, m.Ks_m, m.Dv_m, m.DTv_m, m.Lp_m, m.Ms_f, m.Ks_f, m.Dv_f, m.DTv_f,
-      m.Mp_f, m.Lp_f, m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag);
+      m.Mp_f, m.Lp_f, m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag, m.Kc_f, m.Mc_f, m.k1_diag, m.Kc_m, m.Mc_m);
   count_launch(c);
+
+  // nested P1 space: edge ends and vertex -> incident edge nodes (sorted)
+  const int64_t ne = N - P;
+  m.edge_ends = m.arena.alloc<int32_t>(2 * std::max<int64_t>(ne, 1));
+  m.v2e_ptr = m.arena.alloc<int64_t>(P + 1);
+  m.v2e = m.arena.alloc<int32_t>(2 * std::max<int64_t>(ne, 1));
+  k_edge_ends<<<ceil_div(E, 256), 256, 0, s>>>(m.conn, E, nl, dim, P, m.edge_ends);
+  int32_t *vc = m.arena.alloc<int32_t>(P);
+  SCVS_CUDA(cudaMemsetAsync(vc, 0, P * sizeof(int32_t), s));
+  if (ne > 0) k_count_v2e<<<ceil_div(ne, 256), 256, 0, s>>>(m.edge_ends, ne, vc);
+  scan_exclusive(c, vc, m.v2e_ptr, P);
+  SCVS_CUDA(cudaMemsetAsync(vc, 0, P * sizeof(int32_t), s));
+  if (ne > 0) k_fill_v2e<<<ceil_div(ne, 256), 256, 0, s>>>(m.edge_ends, ne, P, m.v2e_ptr, vc, m.v2e);
+  k_sort_incidence<<<ceil_div(P, 128), 128, 0, s>>>(m.v2e_ptr, m.v2e, P, c.dev_err);
+  c.launches.n += 4;
   SCVS_CUDA(cudaStreamSynchronize(s));
   SCVS_CUDA(cudaGetLastError());
 }

@@ -426,7 +426,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   wk.V = wk.template get<C>((size_t)(m_r + 1) * total);
   wk.Z = wk.template get<C>(total);
   wk.W = wk.template get<C>(total);
-  wk.S = wk.template get<C>(total + 4 * m.P * ld);
+  wk.S = wk.template get<C>(precond_scratch_elems(m));
   int grid, block;
   size_t smem;
   arnoldi_config<T>(c, ld, m_r, grid, block, smem);

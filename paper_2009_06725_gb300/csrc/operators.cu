@@ -63,9 +63,11 @@ k_saddle(const SaddleArgs<T> a, const typename cpx<T>::t *__restrict__ x, typena
         }
         continue;
       }
-      CV<T, MPL> aK[DIM], aM[DIM], aD[DIM];
+      // y = sum_B (mu K + j omega rho M)_AB x_B + sum_B D_AB x_p,B: one complex
+      // coefficient per nonzero and mode, one accumulator per component
+      CV<T, MPL> acc[DIM];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) { aK[c].zero(); aM[c].zero(); aD[c].zero(); }
+      for (int c = 0; c < DIM; ++c) acc[c].zero();
       const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
       const int64_t gend = r0 + a.g_len[A];
       const int64_t goff = a.g_ptr[A] - r0;
@@ -77,7 +79,7 @@ k_saddle(const SaddleArgs<T> a, const typename cpx<T>::t *__restrict__ x, typena
         for (int c = 0; c < DIM; ++c) dv[c] = 0;
         if (t < r1) {
           col = __ldg(a.s_col + t);
-          kv = __ldg(a.Kv + t);
+          kv = mu * __ldg(a.Kv + t);
           mv = __ldg(a.Mv + t);
           if (t < gend) {
 #pragma unroll
@@ -89,32 +91,30 @@ k_saddle(const SaddleArgs<T> a, const typename cpx<T>::t *__restrict__ x, typena
 #pragma unroll 4
         for (int q = 0; q < cnt; ++q) {
           const int32_t B = gshfl<L>(gm, col, q);
-          const T kq = gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+          const T cr = gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+          T ci[MPL];
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) ci[i] = wr[i] * mq;
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {
             CV<T, MPL> xv;
             ldv<T, MPL>(xv, x + ((int64_t)B * DIM + c) * ld + koff);
-            axpy(aK[c], kq, xv);
-            axpy(aM[c], mq, xv);
+#pragma unroll
+            for (int i = 0; i < MPL; ++i) {
+              acc[c].re[i] = fma(cr, xv.re[i], fma(-ci[i], xv.im[i], acc[c].re[i]));
+              acc[c].im[i] = fma(cr, xv.im[i], fma(ci[i], xv.re[i], acc[c].im[i]));
+            }
           }
           if (q < gcnt) {  // uniform across the row group
             CV<T, MPL> xq;
             ldv<T, MPL>(xq, xp_base + (int64_t)B * ld);
 #pragma unroll
-            for (int c = 0; c < DIM; ++c) axpy(aD[c], gshfl<L>(gm, dv[c], q), xq);
+            for (int c = 0; c < DIM; ++c) axpy(acc[c], gshfl<L>(gm, dv[c], q), xq);
           }
         }
       }
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        CV<T, MPL> o;
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) {
-          o.re[i] = mu * aK[c].re[i] - wr[i] * aM[c].im[i] + aD[c].re[i];
-          o.im[i] = mu * aK[c].im[i] + wr[i] * aM[c].re[i] + aD[c].im[i];
-        }
-        stv<T, MPL>(y + (A * DIM + c) * ld + koff, o);
-      }
+      for (int c = 0; c < DIM; ++c) stv<T, MPL>(y + (A * DIM + c) * ld + koff, acc[c]);
     } else {
       const int64_t B = row - a.N;
       CV<T, MPL> acc;
@@ -326,6 +326,12 @@ struct PcArgs {
   const uint8_t *dirmask, *outmask;
   const double *omega;
   double rho, mu;
+  // coarse (P1) velocity level
+  const void *Kcv, *Mcv;       // masked P1 stiffness / mass (T), Q pattern
+  const double *k1_diag;
+  const int32_t *edge_ends;
+  const int64_t *v2e_ptr;
+  const int32_t *v2e;
 };
 
 // The velocity block of mode k, A_u = mu K_s + j omega rho M_s, is preconditioned
@@ -420,15 +426,19 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
         }
         continue;
       }
-      CV<T, MPL> aK[DIM], aM[DIM];
+      CV<T, MPL> acc[DIM];  // A_r z with the real per-mode coefficient mu K + |omega| rho M
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) { aK[c].zero(); aM[c].zero(); }
+      for (int c = 0; c < DIM; ++c) acc[c].zero();
+      T cw[MPL];
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) cw[i] = (T)(fabs(a.omega[koff + i]) * a.rho);
+      const T muT = (T)a.mu;
       const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
       for (int64_t base = r0; base < r1; base += L) {
         const int64_t t = base + lane;
         int32_t col = 0;
         T kv = 0, mv = 0;
-        if (t < r1) { col = __ldg(a.s_col + t); kv = __ldg(Kv + t); mv = __ldg(Mv + t); }
+        if (t < r1) { col = __ldg(a.s_col + t); kv = muT * __ldg(Kv + t); mv = __ldg(Mv + t); }
         const int cnt = (int)min((int64_t)L, r1 - base);
 #pragma unroll 4
         for (int q = 0; q < cnt; ++q) {
@@ -438,8 +448,12 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
           for (int c = 0; c < DIM; ++c) {
             CV<T, MPL> xv;
             ldv<T, MPL>(xv, zu + ((int64_t)B * DIM + c) * ld + koff);
-            axpy(aK[c], kq, xv);
-            axpy(aM[c], mq, xv);
+#pragma unroll
+            for (int i = 0; i < MPL; ++i) {
+              const T cf = fma(cw[i], mq, kq);
+              acc[c].re[i] = fma(cf, xv.re[i], acc[c].re[i]);
+              acc[c].im[i] = fma(cf, xv.im[i], acc[c].im[i]);
+            }
           }
         }
       }
@@ -448,15 +462,13 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
         const int k = koff + i;
         const double w = a.omega[k];
         const T dr = vel_dinv<T>(a, A, w);
-        const T al = (T)cc.alpha_u[k], be = (T)cc.beta_u[k], mu = (T)a.mu, wr = (T)(fabs(w) * a.rho);
+        const T al = (T)cc.alpha_u[k], be = (T)cc.beta_u[k];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
           const int64_t f = (A * DIM + c) * ld + k;
           const C rv = r[f], z = zu[f];
           const C zp = cc.prev_zero_u ? mk<T>(0, 0) : zu_prev[f];
-          const T axr = mu * aK[c].re[i] + wr * aM[c].re[i];  // A_r z
-          const T axi = mu * aK[c].im[i] + wr * aM[c].im[i];
-          const T ur = dr * (rv.x - axr), ui = dr * (rv.y - axi);
+          const T ur = dr * (rv.x - acc[c].re[i]), ui = dr * (rv.y - acc[c].im[i]);
           zu_prev[f] = mk<T>(z.x + al * (z.x - zp.x) + be * ur, z.y + al * (z.y - zp.y) + be * ui);
         }
       }
@@ -508,6 +520,203 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
   }
 }
 
+
+// ---------------------------------------------------- two-level velocity cycle
+// rr = r - A_r z on the velocity rows (zero on Dirichlet rows).
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256)
+k_vel_residual(const PcArgs a, const typename cpx<T>::t *__restrict__ r, const typename cpx<T>::t *__restrict__ z,
+               typename cpx<T>::t *__restrict__ rr) {
+  using C = typename cpx<T>::t;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  const int ld = a.ld, koff = lane * MPL;
+  const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv;
+  for (int64_t A = (int64_t)blockIdx.x * gpb + group; A < a.N; A += (int64_t)gridDim.x * gpb) {
+    if (a.dirmask[A]) {
+      CV<T, MPL> zz;
+      zz.zero();
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) stv<T, MPL>(rr + (A * DIM + c) * ld + koff, zz);
+      continue;
+    }
+    CV<T, MPL> acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c].zero();
+    T cr[MPL];
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) cr[i] = (T)(fabs(a.omega[koff + i]) * a.rho);
+    const T mu = (T)a.mu;
+    const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
+    for (int64_t base = r0; base < r1; base += L) {
+      const int64_t t = base + lane;
+      int32_t col = 0;
+      T kv = 0, mv = 0;
+      if (t < r1) { col = __ldg(a.s_col + t); kv = __ldg(Kv + t); mv = __ldg(Mv + t); }
+      const int cnt = (int)min((int64_t)L, r1 - base);
+#pragma unroll 4
+      for (int q = 0; q < cnt; ++q) {
+        const int32_t B = gshfl<L>(gm, col, q);
+        const T kq = mu * gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          CV<T, MPL> xv;
+          ldv<T, MPL>(xv, z + ((int64_t)B * DIM + c) * ld + koff);
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) {
+            const T cf = kq + cr[i] * mq;  // real coefficient of A_r
+            acc[c].re[i] = fma(cf, xv.re[i], acc[c].re[i]);
+            acc[c].im[i] = fma(cf, xv.im[i], acc[c].im[i]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      CV<T, MPL> rv, o;
+      ldv<T, MPL>(rv, r + (A * DIM + c) * ld + koff);
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) { o.re[i] = rv.re[i] - acc[c].re[i]; o.im[i] = rv.im[i] - acc[c].im[i]; }
+      stv<T, MPL>(rr + (A * DIM + c) * ld + koff, o);
+    }
+  }
+}
+
+// rc = P^T rr on the vertices: own value plus half of every incident edge
+// node (the transpose of P2 interpolation of a P1 field); zero on Dirichlet vertices.
+template <typename T>
+__global__ void k_restrict(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ rr,
+                           typename cpx<T>::t *__restrict__ rc) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)dim * a.ld;
+  if (f >= a.P * per) return;
+  const int64_t v = f / per, rem = f % per;
+  if (a.dirmask[v]) { rc[f] = mk<T>(0, 0); return; }
+  auto s = rr[v * per + rem];
+  T xr = s.x, xi = s.y;
+  for (int64_t i = a.v2e_ptr[v]; i < a.v2e_ptr[v + 1]; ++i) {
+    const auto e = rr[(int64_t)a.v2e[i] * per + rem];
+    xr += T(0.5) * e.x;
+    xi += T(0.5) * e.y;
+  }
+  rc[f] = mk<T>(xr, xi);
+}
+
+// z += P zc on the free velocity nodes (vertices copy, edge nodes average their ends).
+template <typename T>
+__global__ void k_prolong(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zc,
+                          typename cpx<T>::t *__restrict__ z) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)dim * a.ld;
+  if (f >= a.N * per) return;
+  const int64_t n = f / per, rem = f % per;
+  if (a.dirmask[n]) return;
+  T cr, ci;
+  if (n < a.P) {
+    const auto c0 = zc[n * per + rem];
+    cr = c0.x; ci = c0.y;
+  } else {
+    const int64_t i = n - a.P;
+    const auto c0 = zc[(int64_t)a.edge_ends[2 * i] * per + rem];
+    const auto c1 = zc[(int64_t)a.edge_ends[2 * i + 1] * per + rem];
+    cr = T(0.5) * (c0.x + c1.x);
+    ci = T(0.5) * (c0.y + c1.y);
+  }
+  auto o = z[f];
+  z[f] = mk<T>(o.x + cr, o.y + ci);
+}
+
+// Coarse operator A_c = mu K_1 + |omega| rho M_1 (P1, Dirichlet vertices removed);
+// step 0: zc = rc / (diag A_c theta_c[k]).
+template <typename T>
+__device__ __forceinline__ T coarse_dinv(const PcArgs &a, int64_t v, double w) {
+  return (T)(1.0 / (a.mu * a.k1_diag[v] + fabs(w) * a.rho * a.mp_diag[v]));
+}
+
+template <typename T>
+__global__ void k_coarse_step0(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ rc,
+                               const double *__restrict__ inv_theta, typename cpx<T>::t *__restrict__ zc) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)dim * a.ld;
+  if (f >= a.P * per) return;
+  const int64_t v = f / per;
+  const int k = (int)(f % a.ld);
+  if (a.dirmask[v]) { zc[f] = mk<T>(0, 0); return; }
+  const T s = coarse_dinv<T>(a, v, a.omega[k]) * (T)inv_theta[k];
+  const auto r = rc[f];
+  zc[f] = mk<T>(s * r.x, s * r.y);
+}
+
+// Coarse Chebyshev step: zc_next = zc + alpha (zc - zc_prev) + beta D_c^-1 (rc - A_c zc),
+// written over zc_prev.
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256)
+k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__restrict__ beta, int prev_zero,
+              const typename cpx<T>::t *__restrict__ rc, const typename cpx<T>::t *__restrict__ zc,
+              typename cpx<T>::t *__restrict__ zc_prev) {
+  using C = typename cpx<T>::t;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  const int ld = a.ld, koff = lane * MPL;
+  const T *Kc = (const T *)a.Kcv, *Mc = (const T *)a.Mcv;
+  T cr[MPL];
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) cr[i] = (T)(fabs(a.omega[koff + i]) * a.rho);
+  const T mu = (T)a.mu;
+  for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < a.P; v += (int64_t)gridDim.x * gpb) {
+    if (a.dirmask[v]) {
+      CV<T, MPL> zz;
+      zz.zero();
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) stv<T, MPL>(zc_prev + (v * DIM + c) * ld + koff, zz);
+      continue;
+    }
+    CV<T, MPL> acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c].zero();
+    const int64_t r0 = a.g_ptr[v], r1 = a.g_ptr[v + 1], s0 = a.s_ptr[v];
+    for (int64_t base = r0; base < r1; base += L) {
+      const int64_t t = base + lane;
+      int32_t col = 0;
+      T kv = 0, mv = 0;
+      if (t < r1) { col = __ldg(a.s_col + s0 + (t - r0)); kv = __ldg(Kc + t); mv = __ldg(Mc + t); }
+      const int cnt = (int)min((int64_t)L, r1 - base);
+#pragma unroll 4
+      for (int q = 0; q < cnt; ++q) {
+        const int32_t B = gshfl<L>(gm, col, q);
+        const T kq = mu * gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          CV<T, MPL> xv;
+          ldv<T, MPL>(xv, zc + ((int64_t)B * DIM + c) * ld + koff);
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) {
+            const T cf = kq + cr[i] * mq;
+            acc[c].re[i] = fma(cf, xv.re[i], acc[c].re[i]);
+            acc[c].im[i] = fma(cf, xv.im[i], acc[c].im[i]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) {
+      const int k = koff + i;
+      const T d = coarse_dinv<T>(a, v, a.omega[k]);
+      const T al = (T)alpha[k], be = (T)beta[k];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const int64_t f = (v * DIM + c) * ld + k;
+        const C rv = rc[f], zv = zc[f];
+        const C zp = prev_zero ? mk<T>(0, 0) : zc_prev[f];
+        zc_prev[f] = mk<T>(zv.x + al * (zv.x - zp.x) + be * d * (rv.x - acc[c].re[i]),
+                           zv.y + al * (zv.y - zp.y) + be * d * (rv.y - acc[c].im[i]));
+      }
+    }
+  }
+}
+
 // z_p = mu zM + j omega rho zL
 template <typename T>
 __global__ void k_pc_combine(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zM,
@@ -545,7 +754,12 @@ static ChebSeq cheb_seq(double lo, double hi, int s) {
   return q;
 }
 
-constexpr double CHEB_RATIO_U = 30.0, CHEB_RATIO_M = 6.0, CHEB_RATIO_L = 300.0, CHEB_TOP = 1.05;
+// Interval ratios lambda_max / lambda_low of the Chebyshev polynomials:
+// velocity polynomial used alone (BLOCK_CHEB), velocity smoother of the
+// two-level cycle (damps the upper part of the spectrum only), coarse
+// velocity solve, P1 mass and P1 Laplacian.
+constexpr double CHEB_RATIO_U = 30.0, CHEB_RATIO_SMOOTH = 12.0, CHEB_RATIO_C = 300.0, CHEB_RATIO_M = 6.0,
+                 CHEB_RATIO_L = 300.0, CHEB_TOP = 1.05;
 
 template <typename T>
 static PcArgs pc_args(const Mesh &m) {
@@ -553,27 +767,41 @@ static PcArgs pc_args(const Mesh &m) {
   return PcArgs{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr,
                 f ? (const void *)m.Ks_f : (const void *)m.Ks_m, f ? (const void *)m.Ms_f : (const void *)m.Ms_m,
                 f ? (const void *)m.Mp_f : (const void *)m.Mp, f ? (const void *)m.Lp_f : (const void *)m.Lp_m,
-                m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag, m.dirmask, m.outmask, m.omega_d, m.rho, m.mu};
+                m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag, m.dirmask, m.outmask, m.omega_d, m.rho, m.mu,
+                f ? (const void *)m.Kc_f : (const void *)m.Kc_m, f ? (const void *)m.Mc_f : (const void *)m.Mc_m,
+                m.k1_diag, m.edge_ends, m.v2e_ptr, m.v2e};
+}
+
+// Per-mode Chebyshev sequences on [lam_k / ratio, 1.05 lam_k] uploaded as
+// inv_theta[ld], alpha[s][ld], beta[s][ld].
+static void per_mode_seq(Ctx &c, Mesh &m, const std::vector<double> &lam, double ratio, int s, double **inv_theta,
+                         double **alpha, double **beta) {
+  std::vector<double> th(m.ld), al((size_t)s * m.ld), be((size_t)s * m.ld);
+  for (int k = 0; k < m.ld; ++k) {
+    const double l = lam[k] > 0 ? lam[k] : 2.0;
+    ChebSeq q = cheb_seq(l / ratio, CHEB_TOP * l, s);
+    th[k] = q.inv_theta;
+    for (int i = 0; i < s; ++i) { al[(size_t)i * m.ld + k] = q.alpha[i]; be[(size_t)i * m.ld + k] = q.beta[i]; }
+  }
+  *inv_theta = m.mode_arena.alloc<double>(m.ld);
+  *alpha = m.mode_arena.alloc<double>(al.size());
+  *beta = m.mode_arena.alloc<double>(be.size());
+  SCVS_CUDA(cudaMemcpyAsync(*inv_theta, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(*alpha, al.data(), al.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(*beta, be.data(), be.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   const int su = std::max(1, c.opts.cheb_u), sm = std::max(1, c.opts.cheb_m), sl = std::max(1, c.opts.cheb_l);
-  if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl) return;
-  t.s_u = su; t.s_m = sm; t.s_l = sl;
-  std::vector<double> th(m.ld), al((size_t)su * m.ld), be((size_t)su * m.ld);
-  for (int k = 0; k < m.ld; ++k) {
-    double lam = m.lam_u[k] > 0 ? m.lam_u[k] : 2.0;
-    ChebSeq q = cheb_seq(lam / CHEB_RATIO_U, CHEB_TOP * lam, su);
-    th[k] = q.inv_theta;
-    for (int i = 0; i < su; ++i) { al[(size_t)i * m.ld + k] = q.alpha[i]; be[(size_t)i * m.ld + k] = q.beta[i]; }
-  }
-  t.inv_theta_u = m.mode_arena.alloc<double>(m.ld);
-  t.alpha_u = m.mode_arena.alloc<double>(al.size());
-  t.beta_u = m.mode_arena.alloc<double>(be.size());
-  SCVS_CUDA(cudaMemcpyAsync(t.inv_theta_u, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  SCVS_CUDA(cudaMemcpyAsync(t.alpha_u, al.data(), al.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  SCVS_CUDA(cudaMemcpyAsync(t.beta_u, be.data(), be.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  const int sc = std::max(1, c.opts.cheb_c), kind = c.opts.precond;
+  if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl && t.s_c == sc && t.kind == kind) return;
+  t.s_u = su; t.s_m = sm; t.s_l = sl; t.s_c = sc; t.kind = kind;
+  const bool pmg = kind == SCVS_PC_BLOCK_PMG;
+  per_mode_seq(c, m, m.lam_u, pmg ? CHEB_RATIO_SMOOTH : CHEB_RATIO_U, su, &t.inv_theta_u, &t.alpha_u, &t.beta_u);
+  if (pmg) per_mode_seq(c, m, m.lam_c, CHEB_RATIO_C, sc, &t.inv_theta_c, &t.alpha_c, &t.beta_c);
+  t.zeros = m.mode_arena.alloc<double>(m.ld);
+  SCVS_CUDA(cudaMemsetAsync(t.zeros, 0, m.ld * sizeof(double), c.stream));
   ChebSeq qm = cheb_seq(m.lam_m / CHEB_RATIO_M, CHEB_TOP * m.lam_m, sm);
   ChebSeq ql = cheb_seq(m.lam_l / CHEB_RATIO_L, CHEB_TOP * m.lam_l, sl);
   t.inv_theta_m = qm.inv_theta; t.am = qm.alpha; t.bm = qm.beta;
@@ -581,8 +809,36 @@ static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   t.valid = true;
 }
 
-// z = P^-1 r for all modes.  scratch: a full block plus 4 pressure blocks.
-// rscale (device, [ld], may be null): r is first scaled per mode and written back.
+int64_t precond_scratch_elems(const Mesh &m) { return (m.n_dof + (4 + 3 * (int64_t)m.dim) * m.P) * m.ld; }
+
+// One Chebyshev step launch over velocity rows and/or pressure rows.
+template <typename T>
+static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &cc, int i,
+                        const typename cpx<T>::t *r, const typename cpx<T>::t *ucur, typename cpx<T>::t *uprev,
+                        const typename cpx<T>::t *mcur, typename cpx<T>::t *mprev, const typename cpx<T>::t *lcur,
+                        typename cpx<T>::t *lprev) {
+  const double cs = 2.0 * sizeof(T), pb = (double)m.P * m.ld * cs, vb = (double)m.dim * m.N * m.ld * cs;
+  double cb = 0;
+  if (cc.do_u) cb += (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + vb * (cc.prev_zero_u ? 3 : 4);
+  if (cc.do_m || cc.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb;
+  if (cc.do_m) cb += pb * (cc.prev_zero_m ? 2 : 3);
+  if (cc.do_l) cb += pb * (cc.prev_zero_l ? 2 : 3);
+  KScope ksc(c, KC_PRECOND, cb);
+  SCVS_DISPATCH_LD(T, m.ld, {
+    const int gpb = 256 / L;
+    int64_t lo = cc.do_u ? 0 : m.N, hi = (cc.do_m || cc.do_l) ? m.N + m.P : m.N;
+    const unsigned nb = row_blocks(c, hi - lo, gpb);
+    if (m.dim == 2)
+      k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
+    else
+      k_pc_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
+  });
+  count_launch(c);
+}
+
+// z = P^-1 r for all modes (right block preconditioner).  scratch holds
+// precond_scratch_elems(m) elements.  rscale (device, [ld], may be null): r is
+// first scaled per mode and written back (lazy normalisation of v_j).
 template <typename T>
 void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx<T>::t *z,
                    typename cpx<T>::t *scratch, const double *rscale) {
@@ -592,6 +848,7 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   const int64_t total = m.n_dof * m.ld;
   const unsigned eb = ceil_div(total, 256);
   const double cs = 2.0 * sizeof(T), blk = (double)total * cs, pb = (double)m.P * m.ld * cs;
+  const double vb = (double)m.dim * m.N * m.ld * cs, cbk = (double)m.dim * m.P * m.ld * cs;
   if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
     KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
     if (m.dim == 2)
@@ -603,60 +860,110 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   }
   PcTables &t = m.pc;
   pc_tables(c, m, t);
-  const int64_t pblk = m.P * m.ld;
-  C *zu_other = scratch;                 // velocity part lives in dofs [0, dim N)
+  const bool pmg = c.opts.precond == SCVS_PC_BLOCK_PMG;
+  const int64_t pblk = m.P * m.ld, cblk = (int64_t)m.dim * m.P * m.ld;
+  C *other = scratch;  // velocity part lives in dofs [0, dim N)
   C *pM[2] = {scratch + total, scratch + total + pblk};
   C *pL[2] = {scratch + total + 2 * pblk, scratch + total + 3 * pblk};
-  // velocity: final iterate must land in z; z_1 goes to z if s_u is odd.
-  C *uA = (t.s_u % 2 == 1) ? z : zu_other;
-  C *uB = (uA == z) ? zu_other : z;
+  C *rc = scratch + total + 4 * pblk;
+  C *zc[2] = {rc + cblk, rc + 2 * cblk};
+  // the velocity iterate ping-pongs between z and `other`; every Chebyshev
+  // step moves it once, so the first iterate goes where the last one lands on z
+  const int moves = pmg ? (t.s_u - 1) + t.s_u : (t.s_u - 1);
+  C *uA = (moves % 2 == 0) ? z : other;
+  C *uB = (uA == z) ? other : z;
   {
-  KScope ks0(c, KC_PRECOND, blk * (rscale ? 3 : 2) + 2 * pb + (double)m.N * 17 + (double)m.P * 17);
-  if (m.dim == 2)
-    k_pc_step0<T, 2, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l, uA,
-                                                      pM[0], pL[0]);
-  else
-    k_pc_step0<T, 3, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l, uA,
-                                                      pM[0], pL[0]);
-  count_launch(c);
-  }
-  // Dirichlet velocity rows of the velocity iterate: identity (written by step 0)
-  const int steps = std::max(t.s_u, std::max(t.s_m, t.s_l));
-  int cu = 0, cm = 0, cl = 0;  // index of the current buffer of each polynomial
-  C *ucur = uA, *uprev = uB;
-  for (int i = 1; i < steps; ++i) {
-    ChebCoef cc{};
-    cc.do_u = i < t.s_u;
-    cc.do_m = i < t.s_m;
-    cc.do_l = i < t.s_l;
-    cc.alpha_u = t.alpha_u + (size_t)(cc.do_u ? i : 0) * m.ld;
-    cc.beta_u = t.beta_u + (size_t)(cc.do_u ? i : 0) * m.ld;
-    cc.alpha_m = cc.do_m ? t.am[i] : 0; cc.beta_m = cc.do_m ? t.bm[i] : 0;
-    cc.alpha_l = cc.do_l ? t.al[i] : 0; cc.beta_l = cc.do_l ? t.bl[i] : 0;
-    cc.prev_zero_u = cc.prev_zero_m = cc.prev_zero_l = (i == 1);
-    const double vb = (double)m.dim * m.N * m.ld * cs;
-    double cb = 0;
-    if (cc.do_u) cb += (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + vb * (i == 1 ? 3 : 4);
-    if (cc.do_m || cc.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb;
-    if (cc.do_m) cb += pb * (i == 1 ? 2 : 3);
-    if (cc.do_l) cb += pb * (i == 1 ? 2 : 3);
-    KScope ksc(c, KC_PRECOND, cb);
-    SCVS_DISPATCH_LD(T, m.ld, {
-      const int gpb = 256 / L;
-      int64_t lo = cc.do_u ? 0 : m.N, hi = (cc.do_m || cc.do_l) ? m.N + m.P : m.N;
-      const unsigned nb = row_blocks(c, hi - lo, gpb);
-      if (m.dim == 2)
-        k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, pM[cm], pM[1 - cm], pL[cl],
-                                                         pL[1 - cl]);
-      else
-        k_pc_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, pM[cm], pM[1 - cm], pL[cl],
-                                                         pL[1 - cl]);
-    });
+    KScope ks0(c, KC_PRECOND, blk * (rscale ? 3 : 2) + 2 * pb + (double)m.N * 17 + (double)m.P * 17);
+    if (m.dim == 2)
+      k_pc_step0<T, 2, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
+                                                        uA, pM[0], pL[0]);
+    else
+      k_pc_step0<T, 3, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
+                                                        uA, pM[0], pL[0]);
     count_launch(c);
+  }
+  int cm = 0, cl = 0;  // current buffer of each pressure polynomial
+  C *ucur = uA, *uprev = uB;
+  int ip = 1;          // next pressure step
+  auto coef = [&](bool du, int iu, const double *al_u, const double *be_u, bool prev0_u) {
+    ChebCoef cc{};
+    cc.do_u = du;
+    cc.do_m = ip < t.s_m;
+    cc.do_l = ip < t.s_l;
+    cc.alpha_u = al_u;
+    cc.beta_u = be_u;
+    cc.alpha_m = cc.do_m ? t.am[ip] : 0; cc.beta_m = cc.do_m ? t.bm[ip] : 0;
+    cc.alpha_l = cc.do_l ? t.al[ip] : 0; cc.beta_l = cc.do_l ? t.bl[ip] : 0;
+    cc.prev_zero_u = prev0_u;
+    cc.prev_zero_m = cc.prev_zero_l = (ip == 1);
+    (void)iu;
+    return cc;
+  };
+  auto step = [&](ChebCoef cc) {
+    cheb_launch<T>(c, m, a, cc, 0, r, ucur, uprev, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
     if (cc.do_u) std::swap(ucur, uprev);
     if (cc.do_m) cm = 1 - cm;
     if (cc.do_l) cl = 1 - cl;
+    if (cc.do_m || cc.do_l) ++ip;
+  };
+  // (pre-)smoothing / velocity polynomial, pressure polynomials alongside
+  for (int i = 1; i < t.s_u; ++i)
+    step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, i == 1));
+  if (pmg) {
+    // fine residual, restriction, coarse Chebyshev solve, prolongation
+    SCVS_DISPATCH_LD(T, m.ld, {
+      const int gpb = 256 / L;
+      const unsigned nb = row_blocks(c, m.N, gpb);
+      KScope ks(c, KC_PRECOND, (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + 3 * vb);
+      if (m.dim == 2)
+        k_vel_residual<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
+      else
+        k_vel_residual<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
+    });
+    count_launch(c);
+    {
+      KScope ks(c, KC_PRECOND, cbk + (double)(m.N - m.P) * m.dim * m.ld * cs + (double)(m.P + 1) * 8 +
+                                   (double)(m.N - m.P) * 8 + cbk);
+      k_restrict<T><<<ceil_div(cblk, 256), 256, 0, c.stream>>>(a, m.dim, uprev, rc);
+      count_launch(c);
+    }
+    {
+      KScope ks(c, KC_PRECOND, 2 * cbk + (double)m.P * 17);
+      k_coarse_step0<T><<<ceil_div(cblk, 256), 256, 0, c.stream>>>(a, m.dim, rc, t.inv_theta_c, zc[0]);
+      count_launch(c);
+    }
+    int cc_i = 0;
+    for (int i = 1; i < t.s_c; ++i) {
+      KScope ks(c, KC_PRECOND, (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 16 + m.P +
+                                   cbk * (i == 1 ? 3 : 4));
+      SCVS_DISPATCH_LD(T, m.ld, {
+        const int gpb = 256 / L;
+        const unsigned nb = row_blocks(c, m.P, gpb);
+        if (m.dim == 2)
+          k_coarse_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, t.alpha_c + (size_t)i * m.ld,
+                                                               t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i],
+                                                               zc[1 - cc_i]);
+        else
+          k_coarse_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, t.alpha_c + (size_t)i * m.ld,
+                                                               t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i],
+                                                               zc[1 - cc_i]);
+      });
+      count_launch(c);
+      cc_i = 1 - cc_i;
+    }
+    {
+      KScope ks(c, KC_PRECOND, 2 * vb + cbk + (double)(m.N - m.P) * 8 + m.N);
+      k_prolong<T><<<ceil_div((int64_t)m.dim * m.N * m.ld, 256), 256, 0, c.stream>>>(a, m.dim, zc[cc_i], ucur);
+      count_launch(c);
+    }
+    // post-smoothing from the corrected iterate: first step z1 = z0 + D^-1 (r - A z0)/theta
+    step(coef(true, 0, t.zeros, t.inv_theta_u, true));
+    for (int i = 1; i < t.s_u; ++i)
+      step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, false));
   }
+  // remaining pressure steps
+  while (ip < t.s_m || ip < t.s_l) step(coef(false, 0, t.zeros, t.zeros, false));
+  if (ucur != z) throw (int)SCVS_ERR_STATE;  // buffer bookkeeping invariant
   {
     KScope ksk(c, KC_PRECOND, 3 * pb);
     k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z);
@@ -673,7 +980,8 @@ template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
 k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename cpx<T>::t *__restrict__ y,
             const typename cpx<T>::t *__restrict__ vM, typename cpx<T>::t *__restrict__ yM,
-            const typename cpx<T>::t *__restrict__ vL, typename cpx<T>::t *__restrict__ yL) {
+            const typename cpx<T>::t *__restrict__ vL, typename cpx<T>::t *__restrict__ yL,
+            const typename cpx<T>::t *__restrict__ vC, typename cpx<T>::t *__restrict__ yC) {
   using C = typename cpx<T>::t;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
@@ -722,23 +1030,41 @@ k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename c
     } else {
       const int64_t B = row - a.N;
       const int64_t r0 = a.g_ptr[B], r1 = a.g_ptr[B + 1], s0 = a.s_ptr[B];
-      CV<T, MPL> aMp, aLp;
-      aMp.zero(); aLp.zero();
+      CV<T, MPL> aMp, aLp, aKc, aMc;
+      aMp.zero(); aLp.zero(); aKc.zero(); aMc.zero();
+      const T *Kc = (const T *)a.Kcv, *Mc = (const T *)a.Mcv;
       for (int64_t base = r0; base < r1; base += L) {
         const int64_t t = base + lane;
         int32_t col = 0;
-        T mv = 0, lv = 0;
-        if (t < r1) { col = a.s_col[s0 + (t - r0)]; mv = Mpv[t]; lv = Lpv[t]; }
+        T mv = 0, lv = 0, kc = 0, mc = 0;
+        if (t < r1) { col = a.s_col[s0 + (t - r0)]; mv = Mpv[t]; lv = Lpv[t]; kc = Kc[t]; mc = Mc[t]; }
         const int cnt = (int)min((int64_t)L, r1 - base);
         for (int q = 0; q < cnt; ++q) {
           const int32_t Bc = gshfl<L>(gm, col, q);
           const T mq = gshfl<L>(gm, mv, q), lq = gshfl<L>(gm, lv, q);
-          CV<T, MPL> x1, x2;
+          const T kcq = gshfl<L>(gm, kc, q), mcq = gshfl<L>(gm, mc, q);
+          CV<T, MPL> x1, x2, x3;
           ldv<T, MPL>(x1, vM + (int64_t)Bc * ld + koff);
           ldv<T, MPL>(x2, vL + (int64_t)Bc * ld + koff);
+          ldv<T, MPL>(x3, vC + (int64_t)Bc * ld + koff);
           axpy(aMp, mq, x1);
           axpy(aLp, lq, x2);
+          axpy(aKc, kcq, x3);
+          axpy(aMc, mcq, x3);
         }
+      }
+      {
+        CV<T, MPL> o3;
+        const bool dir = a.dirmask[B];
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+          const double w = a.omega[koff + i];
+          const T d = dir ? T(0) : (T)(1.0 / (a.mu * a.k1_diag[B] + fabs(w) * a.rho * a.mp_diag[B]));
+          const T cr = (T)(fabs(w) * a.rho), mu = (T)a.mu;
+          o3.re[i] = d * (mu * aKc.re[i] + cr * aMc.re[i]);
+          o3.im[i] = d * (mu * aKc.im[i] + cr * aMc.im[i]);
+        }
+        stv<T, MPL>(yC + B * ld + koff, o3);
       }
       const T dm = (T)(1.0 / a.mp_diag[B]), dl = (T)(1.0 / a.lp_diag[B]);
       CV<T, MPL> o1, o2;
@@ -803,6 +1129,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   const int64_t nu = (int64_t)m.dim * m.N * ld, np = m.P * ld;
   const int64_t total = m.n_dof * ld;
   float2 *v = nullptr, *y = nullptr, *vM = nullptr, *yM = nullptr, *vL = nullptr, *yL = nullptr;
+  float2 *vC = nullptr, *yC = nullptr;
   double *n2 = nullptr;
   SCVS_CUDA(cudaMallocAsync(&v, total * sizeof(float2), c.stream));
   SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(float2), c.stream));
@@ -810,41 +1137,47 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   SCVS_CUDA(cudaMallocAsync(&yM, np * sizeof(float2), c.stream));
   SCVS_CUDA(cudaMallocAsync(&vL, np * sizeof(float2), c.stream));
   SCVS_CUDA(cudaMallocAsync(&yL, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&n2, 3 * ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&vC, np * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&yC, np * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&n2, 4 * ld * sizeof(double), c.stream));
+  k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vC, np);
   k_init_random<<<ceil_div(total, 256), 256, 0, c.stream>>>(v, total);
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vM, np);
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vL, np);
   c.launches.n += 3;
   const PcArgs a = pc_args<float>(m);
   const unsigned nbn = (unsigned)std::min<int64_t>(ceil_div(total, 256), 4 * c.num_sms);
-  std::vector<double> h(3 * ld, 0.0);
+  std::vector<double> h(4 * ld, 0.0);
   const int iters = 40;
   for (int it = 0; it < iters; ++it) {
     SCVS_DISPATCH_LD(float, ld, {
       const int gpb = 256 / L;
       const unsigned nb = row_blocks(c, m.N + m.P, gpb);
       if (m.dim == 2)
-        k_jacobi_op<float, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL);
+        k_jacobi_op<float, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC);
       else
-        k_jacobi_op<float, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL);
+        k_jacobi_op<float, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC);
     });
-    SCVS_CUDA(cudaMemsetAsync(n2, 0, 3 * ld * sizeof(double), c.stream));
+    SCVS_CUDA(cudaMemsetAsync(n2, 0, 4 * ld * sizeof(double), c.stream));
     k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, m.dim, m.dirmask, n2);
     k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yM, m.P, ld, 1, nullptr, n2 + ld);
     k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yL, m.P, ld, 1, nullptr, n2 + 2 * ld);
-    c.launches.n += 4;
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yC, m.P, ld, 1, nullptr, n2 + 3 * ld);
+    c.launches.n += 5;
     if (it == iters - 1) {
       // the previous iterate had unit norm: ||y|| is the Rayleigh-type estimate
-      SCVS_CUDA(cudaMemcpyAsync(h.data(), n2, 3 * ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      SCVS_CUDA(cudaMemcpyAsync(h.data(), n2, 4 * ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
       break;
     }
     k_block_scale<float><<<ceil_div(nu, 256), 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, n2);
     k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yM, m.P, ld, n2 + ld);
     k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yL, m.P, ld, n2 + 2 * ld);
-    c.launches.n += 3;
+    k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yC, m.P, ld, n2 + 3 * ld);
+    c.launches.n += 4;
     std::swap(v, y);
     std::swap(vM, yM);
     std::swap(vL, yL);
+    std::swap(vC, yC);
   }
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
   m.lam_u.assign(ld, 0.0);
@@ -852,7 +1185,9 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   // every mode column of the P1 blocks carries the same operator: use column 0
   m.lam_m = std::sqrt(h[ld + 0]);
   m.lam_l = std::sqrt(h[2 * ld + 0]);
-  for (float2 *p : {v, y, vM, yM, vL, yL}) SCVS_CUDA(cudaFreeAsync(p, c.stream));
+  m.lam_c.assign(ld, 0.0);
+  for (int k = 0; k < ld; ++k) m.lam_c[k] = std::sqrt(h[3 * ld + k]);
+  for (float2 *p : {v, y, vM, yM, vL, yL, vC, yC}) SCVS_CUDA(cudaFreeAsync(p, c.stream));
   SCVS_CUDA(cudaFreeAsync(n2, c.stream));
 }
 

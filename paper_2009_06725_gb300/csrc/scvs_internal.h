@@ -55,6 +55,9 @@ struct KTimers {
 // Per-mode Chebyshev coefficients of the block preconditioner of one mesh.
 struct PcTables {
   double *inv_theta_u = nullptr, *alpha_u = nullptr, *beta_u = nullptr;  // device, [ld], [s_u][ld]
+  double *inv_theta_c = nullptr, *alpha_c = nullptr, *beta_c = nullptr;  // coarse level, [ld], [s_c][ld]
+  double *zeros = nullptr;                                                // [ld]
+  int s_c = 0, kind = -1;
   std::vector<double> am, bm, al, bl;  // P1 mass / Laplacian recurrences
   double inv_theta_m = 0, inv_theta_l = 0;
   int s_u = 0, s_m = 0, s_l = 0;
@@ -94,6 +97,13 @@ struct Mesh {
   float *Ms_f = nullptr, *Ks_f = nullptr, *Dv_f = nullptr, *DTv_f = nullptr, *Mp_f = nullptr, *Lp_f = nullptr;
   double *ms_diag = nullptr, *ks_diag = nullptr;  // [N]
   double *mp_diag = nullptr, *lp_diag = nullptr;  // [P] (lp: outlet rows -> 1)
+  // two-level velocity preconditioner: P1 (vertex) coarse space nested in P2
+  int32_t *edge_ends = nullptr;   // [N-P][2] end vertices of every edge node
+  int64_t *v2e_ptr = nullptr;     // [P+1] vertex -> incident edge nodes
+  int32_t *v2e = nullptr;         // ascending edge-node ids
+  float *Kc_f = nullptr, *Mc_f = nullptr;  // [q_nnz] P1 stiffness / mass, Dirichlet vertices removed
+  double *Kc_m = nullptr, *Mc_m = nullptr; // same in FP64
+  double *k1_diag = nullptr;      // [P] unmasked P1 stiffness diagonal
   uint8_t *dirmask = nullptr;  // [N]
   uint8_t *outmask = nullptr;  // [P]
   int64_t *dir_nodes = nullptr;  // [n_dir] ascending
@@ -107,7 +117,8 @@ struct Mesh {
   double2 *b = nullptr;          // [n_dof][ld] lifted RHS (b_D = g)
   double2 *x = nullptr;          // [n_dof][ld] FP64 solution
   std::vector<double> bnorm;     // [ld] ||b_F||
-  std::vector<double> lam_u;     // [ld] spectral radius estimate of D_u^-1 A_u per mode
+  std::vector<double> lam_u;     // [ld] spectral radius estimate of D_r^-1 A_r per mode (velocity)
+  std::vector<double> lam_c;     // [ld] same for the P1 coarse velocity operator
   double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
   PcTables pc;
   bool solved = false;
@@ -145,6 +156,7 @@ template <typename T>
 void apply_saddle(Ctx &c, const Mesh &m, const typename cpx<T>::t *x, typename cpx<T>::t *y);
 void lift_rhs(Ctx &c, Mesh &m);
 double saddle_bytes(const Mesh &m, int value_size);
+int64_t precond_scratch_elems(const Mesh &m);
 void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev);
 void spectral_bounds(Ctx &c, Mesh &m);
 template <typename T>

@@ -22,7 +22,7 @@ SCVS_ERR_OOM, SCVS_ERR_CUDA, SCVS_ERR_STATE, SCVS_ERR_TIMEOUT = -4, -5, -6, -7
 SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET = 1, 2, 4
 SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
-SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG = 0, 1
+SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG = 0, 1, 2
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
 SCVS_KC_COUNT = 8
@@ -34,7 +34,7 @@ class scvs_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("cheb_u", C.c_int32), ("cheb_m", C.c_int32),
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
-                ("verbose", C.c_int32), ("stream", C.c_void_p)]
+                ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("stream", C.c_void_p)]
 
 
 class scvs_mode_report(C.Structure):
