@@ -183,8 +183,11 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     opts = dict(stream=stream.cuda_stream, precision=scvs.SCVS_PREC_FP64 if args.precision == "fp64"
                 else scvs.SCVS_PREC_MIXED)
-    if args.cheb_u:
-        opts["cheb_u"] = args.cheb_u
+    for k in ("cheb_u", "cheb_m", "cheb_l", "cheb_c", "restart"):
+        if getattr(args, k):
+            opts[k] = getattr(args, k)
+    if args.precond is not None:
+        opts["precond"] = args.precond
     solver = scvs.Solver(**opts)
     ctx = solver.ctx
     # device-resident inputs
@@ -370,6 +373,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cheb-u", type=int, default=0)
+    ap.add_argument("--cheb-m", type=int, default=0)
+    ap.add_argument("--cheb-l", type=int, default=0)
+    ap.add_argument("--cheb-c", type=int, default=0)
+    ap.add_argument("--restart", type=int, default=0)
+    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")

@@ -2,6 +2,7 @@
 // marshalling.  Every computation runs in the kernels of assembly.cu,
 // operators.cu, krylov.cu and recon.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -153,6 +154,23 @@ int add_mesh(scvs_ctx *c, int dim, int64_t N, int64_t P, const double *xyz, int6
   return (int)c->meshes.size() - 1;
 }
 
+// |omega_k| rho and omega_k rho per mode, FP64 and FP32 (depend on rho)
+void update_mode_scalars(Ctx &c, Mesh &m) {
+  std::vector<double> wa(m.ld), wr(m.ld);
+  std::vector<float> waf(m.ld), wrf(m.ld);
+  for (int k = 0; k < m.ld; ++k) {
+    wa[k] = std::fabs(m.omega[k]) * m.rho;
+    wr[k] = m.omega[k] * m.rho;
+    waf[k] = (float)wa[k];
+    wrf[k] = (float)wr[k];
+  }
+  SCVS_CUDA(cudaMemcpyAsync(m.wabs_d, wa.data(), m.ld * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(m.wrho_d, wr.data(), m.ld * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(m.wabs_f, waf.data(), m.ld * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(m.wrho_f, wrf.data(), m.ld * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+}
+
 int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const void *g, bool on_device) {
   Mesh *m = get_mesh(c, mesh_id);
   if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
@@ -167,6 +185,11 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
   for (int k = 0; k < n_modes; ++k) m->omega[k] = omega[k];
   m->omega_d = m->mode_arena.alloc<double>(m->ld);
   SCVS_CUDA(cudaMemcpyAsync(m->omega_d, m->omega.data(), m->ld * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  m->wabs_d = m->mode_arena.alloc<double>(m->ld);
+  m->wrho_d = m->mode_arena.alloc<double>(m->ld);
+  m->wabs_f = m->mode_arena.alloc<float>(m->ld);
+  m->wrho_f = m->mode_arena.alloc<float>(m->ld);
+  update_mode_scalars(*c, *m);
   const int64_t gcount = (int64_t)n_modes * m->n_dir * m->dim;
   m->g = m->mode_arena.alloc<double2>(std::max<int64_t>(1, gcount));
   if (gcount)
@@ -290,6 +313,7 @@ int scvs_set_physics(scvs_ctx *c, int32_t mesh_id, double rho, double mu) {
     m->rho = rho;
     m->mu = mu;
     if (m->m > 0) {  // modes already set: rebuild what depends on rho, mu
+      update_mode_scalars(*c, *m);
       m->pc = PcTables{};
       m->solved = false;
       lift_rhs(*c, *m);

@@ -338,6 +338,11 @@ __global__ void k_mask_values(int64_t N, int64_t P, int dim, const int64_t *__re
 __constant__ int c_edge_pairs[6][2] = {{0, 1}, {1, 2}, {2, 0}, {0, 3}, {1, 3}, {2, 3}};
 
 // end vertices of every edge node (the same from every element sharing the edge)
+__global__ void k_diag_f32(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
 __global__ void k_edge_ends(const int32_t *__restrict__ conn, int64_t E, int nl, int dim, int64_t P, int32_t *ends) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -556,6 +561,18 @@ void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, c
       m.Dv, m.DTv, m.Mp, m.Lp, m.Ms_m, m.Ks_m, m.Dv_m, m.DTv_m, m.Lp_m, m.Ms_f, m.Ks_f, m.Dv_f, m.DTv_f,
       m.Mp_f, m.Lp_f, m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag, m.Kc_f, m.Mc_f, m.k1_diag, m.Kc_m, m.Mc_m);
   count_launch(c);
+
+  m.ms_df = m.arena.alloc<float>(N);
+  m.ks_df = m.arena.alloc<float>(N);
+  m.mp_df = m.arena.alloc<float>(P);
+  m.lp_df = m.arena.alloc<float>(P);
+  m.k1_df = m.arena.alloc<float>(P);
+  k_diag_f32<<<ceil_div(N, 256), 256, 0, s>>>(m.ms_diag, m.ms_df, N);
+  k_diag_f32<<<ceil_div(N, 256), 256, 0, s>>>(m.ks_diag, m.ks_df, N);
+  k_diag_f32<<<ceil_div(P, 256), 256, 0, s>>>(m.mp_diag, m.mp_df, P);
+  k_diag_f32<<<ceil_div(P, 256), 256, 0, s>>>(m.lp_diag, m.lp_df, P);
+  k_diag_f32<<<ceil_div(P, 256), 256, 0, s>>>(m.k1_diag, m.k1_df, P);
+  c.launches.n += 5;
 
   // nested P1 space: edge ends and vertex -> incident edge nodes (sorted)
   const int64_t ne = N - P;

@@ -58,7 +58,7 @@ __device__ __forceinline__ T warp_rows_sum(T v) {
 }
 
 template <typename T, int MPL, int TPR>
-__global__ void __launch_bounds__(256) k_arnoldi(const ArnArgs<T> a, const int j) {
+__global__ void __launch_bounds__(256, 3) k_arnoldi(const ArnArgs<T> a, const int j) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *acc = reinterpret_cast<T *>(smem_raw);
@@ -97,30 +97,47 @@ __global__ void __launch_bounds__(256) k_arnoldi(const ArnArgs<T> a, const int j
 #pragma unroll
         for (int i = 0; i < MPL; ++i) myacc[(j + 1) * sstride + 2 * (koff + i)] += s[i];
     }
-    for (int vi = 0; vi < nvec; ++vi) {
-      const C *Vi = a.V + (int64_t)vi * a.vstride;
-      T sr[MPL], si[MPL];
-#pragma unroll
-      for (int i = 0; i < MPL; ++i) { sr[i] = 0; si[i] = 0; }
+    // Krylov vectors in pairs: 2 x ARN_RPT independent loads in flight per thread
+    for (int vi = 0; vi < nvec; vi += 2) {
+      const bool two = vi + 1 < nvec;
+      const C *V0 = a.V + (int64_t)vi * a.vstride;
+      const C *V1 = a.V + (int64_t)(two ? vi + 1 : vi) * a.vstride;
+      CV<T, MPL> v0[ARN_RPT], v1[ARN_RPT];
 #pragma unroll
       for (int q = 0; q < ARN_RPT; ++q) {
         if (rr[q] < a.rows) {
-          CV<T, MPL> v;
-          ldv<T, MPL>(v, Vi + rr[q] * ld + koff);
-#pragma unroll
-          for (int i = 0; i < MPL; ++i) {  // conj(v) * w
-            sr[i] += v.re[i] * wv[q].re[i] + v.im[i] * wv[q].im[i];
-            si[i] += v.re[i] * wv[q].im[i] - v.im[i] * wv[q].re[i];
-          }
+          ldv<T, MPL>(v0[q], V0 + rr[q] * ld + koff);
+          if (two) ldv<T, MPL>(v1[q], V1 + rr[q] * ld + koff); else v1[q].zero();
+        } else {
+          v0[q].zero();
+          v1[q].zero();
         }
       }
+      T sr0[MPL], si0[MPL], sr1[MPL], si1[MPL];
 #pragma unroll
-      for (int i = 0; i < MPL; ++i) { sr[i] = warp_rows_sum<T, TPR>(sr[i]); si[i] = warp_rows_sum<T, TPR>(si[i]); }
+      for (int i = 0; i < MPL; ++i) {
+        sr0[i] = si0[i] = sr1[i] = si1[i] = 0;
+#pragma unroll
+        for (int q = 0; q < ARN_RPT; ++q) {  // conj(v) * w
+          sr0[i] += v0[q].re[i] * wv[q].re[i] + v0[q].im[i] * wv[q].im[i];
+          si0[i] += v0[q].re[i] * wv[q].im[i] - v0[q].im[i] * wv[q].re[i];
+          sr1[i] += v1[q].re[i] * wv[q].re[i] + v1[q].im[i] * wv[q].im[i];
+          si1[i] += v1[q].re[i] * wv[q].im[i] - v1[q].im[i] * wv[q].re[i];
+        }
+        sr0[i] = warp_rows_sum<T, TPR>(sr0[i]);
+        si0[i] = warp_rows_sum<T, TPR>(si0[i]);
+        sr1[i] = warp_rows_sum<T, TPR>(sr1[i]);
+        si1[i] = warp_rows_sum<T, TPR>(si1[i]);
+      }
       if (row_leader)
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
-          myacc[vi * sstride + 2 * (koff + i)] += sr[i];
-          myacc[vi * sstride + 2 * (koff + i) + 1] += si[i];
+          myacc[vi * sstride + 2 * (koff + i)] += sr0[i];
+          myacc[vi * sstride + 2 * (koff + i) + 1] += si0[i];
+          if (two) {
+            myacc[(vi + 1) * sstride + 2 * (koff + i)] += sr1[i];
+            myacc[(vi + 1) * sstride + 2 * (koff + i) + 1] += si1[i];
+          }
         }
     }
   }
@@ -177,23 +194,36 @@ __global__ void __launch_bounds__(256) k_arnoldi(const ArnArgs<T> a, const int j
       rr[q] = tile * TR + roff + (int64_t)q * RPB;
       if (rr[q] < a.rows) ldv<T, MPL>(wv[q], a.w + rr[q] * ld + koff); else wv[q].zero();
     }
-    for (int vi = 0; vi < nvec; ++vi) {
-      const C *Vi = a.V + (int64_t)vi * a.vstride;
-      T hr[MPL], hi[MPL];
+    for (int vi = 0; vi < nvec; vi += 2) {
+      const bool two = vi + 1 < nvec;
+      const C *V0 = a.V + (int64_t)vi * a.vstride;
+      const C *V1 = a.V + (int64_t)(two ? vi + 1 : vi) * a.vstride;
+      T hr0[MPL], hi0[MPL], hr1[MPL], hi1[MPL];
 #pragma unroll
-      for (int i = 0; i < MPL; ++i) { hr[i] = hs[vi * sstride + 2 * (koff + i)]; hi[i] = hs[vi * sstride + 2 * (koff + i) + 1]; }
+      for (int i = 0; i < MPL; ++i) {
+        hr0[i] = hs[vi * sstride + 2 * (koff + i)];
+        hi0[i] = hs[vi * sstride + 2 * (koff + i) + 1];
+        hr1[i] = two ? hs[(vi + 1) * sstride + 2 * (koff + i)] : T(0);
+        hi1[i] = two ? hs[(vi + 1) * sstride + 2 * (koff + i) + 1] : T(0);
+      }
+      CV<T, MPL> v0[ARN_RPT], v1[ARN_RPT];
 #pragma unroll
       for (int q = 0; q < ARN_RPT; ++q) {
         if (rr[q] < a.rows) {
-          CV<T, MPL> v;
-          ldv<T, MPL>(v, Vi + rr[q] * ld + koff);
-#pragma unroll
-          for (int i = 0; i < MPL; ++i) {  // w -= h * v
-            wv[q].re[i] -= hr[i] * v.re[i] - hi[i] * v.im[i];
-            wv[q].im[i] -= hr[i] * v.im[i] + hi[i] * v.re[i];
-          }
+          ldv<T, MPL>(v0[q], V0 + rr[q] * ld + koff);
+          if (two) ldv<T, MPL>(v1[q], V1 + rr[q] * ld + koff); else v1[q].zero();
+        } else {
+          v0[q].zero();
+          v1[q].zero();
         }
       }
+#pragma unroll
+      for (int q = 0; q < ARN_RPT; ++q)
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {  // w -= h0 v0 + h1 v1
+          wv[q].re[i] -= hr0[i] * v0[q].re[i] - hi0[i] * v0[q].im[i] + hr1[i] * v1[q].re[i] - hi1[i] * v1[q].im[i];
+          wv[q].im[i] -= hr0[i] * v0[q].im[i] + hi0[i] * v0[q].re[i] + hr1[i] * v1[q].im[i] + hi1[i] * v1[q].re[i];
+        }
     }
     T s[MPL];
 #pragma unroll
@@ -530,14 +560,20 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       ++steps;
       SCVS_CUDA(cudaMemcpyAsync(h_active, wk.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
       SCVS_CUDA(cudaStreamSynchronize(c.stream));
+      if (*h_active == 0) break;
+    }
+    // a grid barrier that gave up makes every block leave the kernel: the
+    // cycle's results are void, report the timeout
+    {
       int gerr = 0;
-      SCVS_CUDA(cudaMemcpy(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost));
+      SCVS_CUDA(cudaMemcpyAsync(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+      SCVS_CUDA(cudaStreamSynchronize(c.stream));
       if (gerr) {
-        SCVS_CUDA(cudaMemset(c.gsync, 0, sizeof(GridSync)));
+        SCVS_CUDA(cudaMemsetAsync(c.gsync, 0, sizeof(GridSync), c.stream));
+        SCVS_CUDA(cudaStreamSynchronize(c.stream));
         cudaFreeHost(h_active);
         return SCVS_ERR_TIMEOUT;
       }
-      if (*h_active == 0) break;
     }
     // 4. least squares, correction, update
     k_lsq<<<ceil_div(ld, 64), 64, 0, c.stream>>>(wk.H, wk.gv, wk.kdim, ld, m_r, wk.y);

@@ -332,6 +332,9 @@ struct PcArgs {
   const int32_t *edge_ends;
   const int64_t *v2e_ptr;
   const int32_t *v2e;
+  // diagonals and per-mode scalars in the kernel's precision T
+  const void *ksd, *msd, *mpd, *lpd, *k1d;
+  const void *wabs, *wrho;   // [ld] |omega_k| rho, omega_k rho
 };
 
 // The velocity block of mode k, A_u = mu K_s + j omega rho M_s, is preconditioned
@@ -340,8 +343,8 @@ struct PcArgs {
 // A_r has a real positive Jacobi-scaled spectrum on which a Chebyshev
 // polynomial on a real interval is effective.  vel_dinv is 1 / diag(A_r).
 template <typename T>
-__device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, double w) {
-  return (T)(1.0 / (a.mu * a.ks_diag[A] + fabs(w) * a.rho * a.ms_diag[A]));
+__device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, int k) {
+  return T(1) / ((T)a.mu * ((const T *)a.ksd)[A] + ((const T *)a.wabs)[k] * ((const T *)a.msd)[A]);
 }
 
 // Step 0 of every polynomial (elementwise): optionally rescale r by rscale[k]
@@ -368,7 +371,7 @@ __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *
   if (dof < (int64_t)DIM * a.N) {
     const int64_t A = dof / DIM;
     if (a.dirmask[A]) { zu[f] = v; return; }
-    const T s = vel_dinv<T>(a, A, a.omega[k]) * (DIAG ? T(1) : (T)inv_theta_u[k]);
+    const T s = vel_dinv<T>(a, A, k) * (DIAG ? T(1) : (T)inv_theta_u[k]);
     zu[f] = mk<T>(s * v.x, s * v.y);
   } else {
     const int64_t B = dof - (int64_t)DIM * a.N;
@@ -381,9 +384,9 @@ __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *
       // (cm + j cl) * v
       zu[f] = mk<T>(cm * v.x - cl * v.y, cm * v.y + cl * v.x);
     } else {
-      T sm = (T)(inv_theta_m / a.mp_diag[B]);
+      T sm = (T)inv_theta_m / ((const T *)a.mpd)[B];
       zM[pf] = mk<T>(v.x * sm, v.y * sm);
-      T sl = out ? T(0) : (T)(inv_theta_l / a.lp_diag[B]);
+      T sl = out ? T(0) : (T)inv_theta_l / ((const T *)a.lpd)[B];
       zL[pf] = mk<T>(v.x * sl, v.y * sl);
     }
   }
@@ -399,6 +402,63 @@ struct ChebCoef {
   int do_u, do_m, do_l;
   int prev_zero_u, prev_zero_m, prev_zero_l;
 };
+
+// One Chebyshev step of both pressure polynomials (P1 mass, P1 Laplacian with
+// p = 0 on the outlet) on pressure row B, for the lane's modes.
+template <typename T, int MPL, int L, int DIM>
+__device__ __forceinline__ void pressure_row_step(const PcArgs &a, const ChebCoef &cc, const int64_t B,
+                                                  const typename cpx<T>::t *__restrict__ r,
+                                                  const typename cpx<T>::t *__restrict__ zM,
+                                                  typename cpx<T>::t *__restrict__ zM_prev,
+                                                  const typename cpx<T>::t *__restrict__ zL,
+                                                  typename cpx<T>::t *__restrict__ zL_prev, const int lane,
+                                                  const unsigned gm) {
+  using C = typename cpx<T>::t;
+  const int ld = a.ld, koff = lane * MPL;
+  const T *Mpv = (const T *)a.Mpv, *Lpv = (const T *)a.Lpv;
+  const int64_t r0 = a.g_ptr[B], r1 = a.g_ptr[B + 1];  // Q row = leading part of the S row
+  const int64_t s0 = a.s_ptr[B];
+  CV<T, MPL> aMp, aLp;
+  aMp.zero(); aLp.zero();
+  for (int64_t base = r0; base < r1; base += L) {
+    const int64_t t = base + lane;
+    int32_t col = 0;
+    T mv = 0, lv = 0;
+    if (t < r1) { col = __ldg(a.s_col + s0 + (t - r0)); mv = __ldg(Mpv + t); lv = __ldg(Lpv + t); }
+    const int cnt = (int)min((int64_t)L, r1 - base);
+#pragma unroll 4
+    for (int q = 0; q < cnt; ++q) {
+      const int32_t Bc = gshfl<L>(gm, col, q);
+      const T mq = gshfl<L>(gm, mv, q), lq = gshfl<L>(gm, lv, q);
+      if (cc.do_m) { CV<T, MPL> v; ldv<T, MPL>(v, zM + (int64_t)Bc * ld + koff); axpy(aMp, mq, v); }
+      if (cc.do_l) { CV<T, MPL> v; ldv<T, MPL>(v, zL + (int64_t)Bc * ld + koff); axpy(aLp, lq, v); }
+    }
+  }
+  const int64_t rf = ((int64_t)DIM * a.N + B) * ld;
+  const bool out = a.outmask[B];
+  const T dm = T(1) / ((const T *)a.mpd)[B], dl = T(1) / ((const T *)a.lpd)[B];
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) {
+    const int k = koff + i;
+    const int64_t pf = B * ld + k;
+    const C rv = r[rf + k];
+    if (cc.do_m) {
+      const C z = zM[pf];
+      const C zp = cc.prev_zero_m ? mk<T>(0, 0) : zM_prev[pf];
+      const T al = (T)cc.alpha_m, be = (T)cc.beta_m;
+      zM_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dm * (rv.x - aMp.re[i]),
+                          z.y + al * (z.y - zp.y) + be * dm * (rv.y - aMp.im[i]));
+    }
+    if (cc.do_l) {
+      const C z = zL[pf];
+      const C zp = cc.prev_zero_l ? mk<T>(0, 0) : zL_prev[pf];
+      const T al = (T)cc.alpha_l, be = (T)cc.beta_l;
+      const T rr = out ? T(0) : rv.x, ri = out ? T(0) : rv.y;
+      zL_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dl * (rr - aLp.re[i]),
+                          z.y + al * (z.y - zp.y) + be * dl * (ri - aLp.im[i]));
+    }
+  }
+}
 
 template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
@@ -431,7 +491,7 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
       for (int c = 0; c < DIM; ++c) acc[c].zero();
       T cw[MPL];
 #pragma unroll
-      for (int i = 0; i < MPL; ++i) cw[i] = (T)(fabs(a.omega[koff + i]) * a.rho);
+      for (int i = 0; i < MPL; ++i) cw[i] = ((const T *)a.wabs)[koff + i];
       const T muT = (T)a.mu;
       const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
       for (int64_t base = r0; base < r1; base += L) {
@@ -460,8 +520,7 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
 #pragma unroll
       for (int i = 0; i < MPL; ++i) {
         const int k = koff + i;
-        const double w = a.omega[k];
-        const T dr = vel_dinv<T>(a, A, w);
+        const T dr = vel_dinv<T>(a, A, k);
         const T al = (T)cc.alpha_u[k], be = (T)cc.beta_u[k];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
@@ -473,49 +532,7 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
         }
       }
     } else {
-      const int64_t B = row - a.N;
-      const int64_t r0 = a.g_ptr[B], r1 = a.g_ptr[B + 1];  // Q row = leading part of the S row
-      const int64_t s0 = a.s_ptr[B];
-      CV<T, MPL> aMp, aLp;
-      aMp.zero(); aLp.zero();
-      for (int64_t base = r0; base < r1; base += L) {
-        const int64_t t = base + lane;
-        int32_t col = 0;
-        T mv = 0, lv = 0;
-        if (t < r1) { col = __ldg(a.s_col + s0 + (t - r0)); mv = __ldg(Mpv + t); lv = __ldg(Lpv + t); }
-        const int cnt = (int)min((int64_t)L, r1 - base);
-#pragma unroll 4
-        for (int q = 0; q < cnt; ++q) {
-          const int32_t Bc = gshfl<L>(gm, col, q);
-          const T mq = gshfl<L>(gm, mv, q), lq = gshfl<L>(gm, lv, q);
-          if (cc.do_m) { CV<T, MPL> v; ldv<T, MPL>(v, zM + (int64_t)Bc * ld + koff); axpy(aMp, mq, v); }
-          if (cc.do_l) { CV<T, MPL> v; ldv<T, MPL>(v, zL + (int64_t)Bc * ld + koff); axpy(aLp, lq, v); }
-        }
-      }
-      const int64_t rf = ((int64_t)DIM * a.N + B) * ld;
-      const bool out = a.outmask[B];
-      const T dm = (T)(1.0 / a.mp_diag[B]), dl = (T)(1.0 / a.lp_diag[B]);
-#pragma unroll
-      for (int i = 0; i < MPL; ++i) {
-        const int k = koff + i;
-        const int64_t pf = B * ld + k;
-        const C rv = r[rf + k];
-        if (cc.do_m) {
-          const C z = zM[pf];
-          const C zp = cc.prev_zero_m ? mk<T>(0, 0) : zM_prev[pf];
-          const T al = (T)cc.alpha_m, be = (T)cc.beta_m;
-          zM_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dm * (rv.x - aMp.re[i]),
-                              z.y + al * (z.y - zp.y) + be * dm * (rv.y - aMp.im[i]));
-        }
-        if (cc.do_l) {
-          const C z = zL[pf];
-          const C zp = cc.prev_zero_l ? mk<T>(0, 0) : zL_prev[pf];
-          const T al = (T)cc.alpha_l, be = (T)cc.beta_l;
-          const T rr = out ? T(0) : rv.x, ri = out ? T(0) : rv.y;
-          zL_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dl * (rr - aLp.re[i]),
-                              z.y + al * (z.y - zp.y) + be * dl * (ri - aLp.im[i]));
-        }
-      }
+      pressure_row_step<T, MPL, L, DIM>(a, cc, row - a.N, r, zM, zM_prev, zL, zL_prev, lane, gm);
     }
   }
 }
@@ -546,7 +563,7 @@ k_vel_residual(const PcArgs a, const typename cpx<T>::t *__restrict__ r, const t
     for (int c = 0; c < DIM; ++c) acc[c].zero();
     T cr[MPL];
 #pragma unroll
-    for (int i = 0; i < MPL; ++i) cr[i] = (T)(fabs(a.omega[koff + i]) * a.rho);
+    for (int i = 0; i < MPL; ++i) cr[i] = ((const T *)a.wabs)[koff + i];
     const T mu = (T)a.mu;
     const int64_t r0 = a.s_ptr[A], r1 = a.s_ptr[A + 1];
     for (int64_t base = r0; base < r1; base += L) {
@@ -630,8 +647,8 @@ __global__ void k_prolong(const PcArgs a, int dim, const typename cpx<T>::t *__r
 // Coarse operator A_c = mu K_1 + |omega| rho M_1 (P1, Dirichlet vertices removed);
 // step 0: zc = rc / (diag A_c theta_c[k]).
 template <typename T>
-__device__ __forceinline__ T coarse_dinv(const PcArgs &a, int64_t v, double w) {
-  return (T)(1.0 / (a.mu * a.k1_diag[v] + fabs(w) * a.rho * a.mp_diag[v]));
+__device__ __forceinline__ T coarse_dinv(const PcArgs &a, int64_t v, int k) {
+  return T(1) / ((T)a.mu * ((const T *)a.k1d)[v] + ((const T *)a.wabs)[k] * ((const T *)a.mpd)[v]);
 }
 
 template <typename T>
@@ -643,7 +660,7 @@ __global__ void k_coarse_step0(const PcArgs a, int dim, const typename cpx<T>::t
   const int64_t v = f / per;
   const int k = (int)(f % a.ld);
   if (a.dirmask[v]) { zc[f] = mk<T>(0, 0); return; }
-  const T s = coarse_dinv<T>(a, v, a.omega[k]) * (T)inv_theta[k];
+  const T s = coarse_dinv<T>(a, v, k) * (T)inv_theta[k];
   const auto r = rc[f];
   zc[f] = mk<T>(s * r.x, s * r.y);
 }
@@ -654,7 +671,9 @@ template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
 k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__restrict__ beta, int prev_zero,
               const typename cpx<T>::t *__restrict__ rc, const typename cpx<T>::t *__restrict__ zc,
-              typename cpx<T>::t *__restrict__ zc_prev) {
+              typename cpx<T>::t *__restrict__ zc_prev, const ChebCoef pc, const typename cpx<T>::t *__restrict__ r,
+              const typename cpx<T>::t *__restrict__ zM, typename cpx<T>::t *__restrict__ zM_prev,
+              const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ zL_prev) {
   using C = typename cpx<T>::t;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
@@ -663,9 +682,15 @@ k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__
   const T *Kc = (const T *)a.Kcv, *Mc = (const T *)a.Mcv;
   T cr[MPL];
 #pragma unroll
-  for (int i = 0; i < MPL; ++i) cr[i] = (T)(fabs(a.omega[koff + i]) * a.rho);
+  for (int i = 0; i < MPL; ++i) cr[i] = ((const T *)a.wabs)[koff + i];
   const T mu = (T)a.mu;
-  for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < a.P; v += (int64_t)gridDim.x * gpb) {
+  // rows [0, P): coarse velocity step; rows [P, 2P): a pressure step when requested
+  const int64_t rows = (pc.do_m || pc.do_l) ? 2 * a.P : a.P;
+  for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < rows; v += (int64_t)gridDim.x * gpb) {
+    if (v >= a.P) {
+      pressure_row_step<T, MPL, L, DIM>(a, pc, v - a.P, r, zM, zM_prev, zL, zL_prev, lane, gm);
+      continue;
+    }
     if (a.dirmask[v]) {
       CV<T, MPL> zz;
       zz.zero();
@@ -703,7 +728,7 @@ k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__
 #pragma unroll
     for (int i = 0; i < MPL; ++i) {
       const int k = koff + i;
-      const T d = coarse_dinv<T>(a, v, a.omega[k]);
+      const T d = coarse_dinv<T>(a, v, k);
       const T al = (T)alpha[k], be = (T)beta[k];
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
@@ -724,7 +749,7 @@ __global__ void k_pc_combine(const PcArgs a, int dim, const typename cpx<T>::t *
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.P * a.ld) return;
   const int k = (int)(f % a.ld);
-  const T mu = (T)a.mu, wr = (T)(a.omega[k] * a.rho);
+  const T mu = (T)a.mu, wr = ((const T *)a.wrho)[k];
   auto m_ = zM[f];
   auto l_ = zL[f];
   z[(int64_t)dim * a.N * a.ld + f] = mk<T>(mu * m_.x - wr * l_.y, mu * m_.y + wr * l_.x);
@@ -769,7 +794,11 @@ static PcArgs pc_args(const Mesh &m) {
                 f ? (const void *)m.Mp_f : (const void *)m.Mp, f ? (const void *)m.Lp_f : (const void *)m.Lp_m,
                 m.ms_diag, m.ks_diag, m.mp_diag, m.lp_diag, m.dirmask, m.outmask, m.omega_d, m.rho, m.mu,
                 f ? (const void *)m.Kc_f : (const void *)m.Kc_m, f ? (const void *)m.Mc_f : (const void *)m.Mc_m,
-                m.k1_diag, m.edge_ends, m.v2e_ptr, m.v2e};
+                m.k1_diag, m.edge_ends, m.v2e_ptr, m.v2e,
+                f ? (const void *)m.ks_df : (const void *)m.ks_diag, f ? (const void *)m.ms_df : (const void *)m.ms_diag,
+                f ? (const void *)m.mp_df : (const void *)m.mp_diag, f ? (const void *)m.lp_df : (const void *)m.lp_diag,
+                f ? (const void *)m.k1_df : (const void *)m.k1_diag,
+                f ? (const void *)m.wabs_f : (const void *)m.wabs_d, f ? (const void *)m.wrho_f : (const void *)m.wrho_d};
 }
 
 // Per-mode Chebyshev sequences on [lam_k / ratio, 1.05 lam_k] uploaded as
@@ -934,22 +963,27 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     }
     int cc_i = 0;
     for (int i = 1; i < t.s_c; ++i) {
-      KScope ks(c, KC_PRECOND, (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 16 + m.P +
-                                   cbk * (i == 1 ? 3 : 4));
+      ChebCoef pcf = coef(false, 0, t.zeros, t.zeros, false);  // pending pressure step, if any
+      double cb = (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 16 + m.P + cbk * (i == 1 ? 3 : 4);
+      if (pcf.do_m || pcf.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb * (1 + (pcf.do_m ? 3 : 0) + (pcf.do_l ? 3 : 0));
+      KScope ks(c, KC_PRECOND, cb);
       SCVS_DISPATCH_LD(T, m.ld, {
         const int gpb = 256 / L;
-        const unsigned nb = row_blocks(c, m.P, gpb);
+        const unsigned nb = row_blocks(c, (pcf.do_m || pcf.do_l) ? 2 * m.P : m.P, gpb);
         if (m.dim == 2)
-          k_coarse_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, t.alpha_c + (size_t)i * m.ld,
-                                                               t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i],
-                                                               zc[1 - cc_i]);
+          k_coarse_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(
+              a, t.alpha_c + (size_t)i * m.ld, t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i], zc[1 - cc_i], pcf,
+              r, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
         else
-          k_coarse_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, t.alpha_c + (size_t)i * m.ld,
-                                                               t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i],
-                                                               zc[1 - cc_i]);
+          k_coarse_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(
+              a, t.alpha_c + (size_t)i * m.ld, t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i], zc[1 - cc_i], pcf,
+              r, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
       });
       count_launch(c);
       cc_i = 1 - cc_i;
+      if (pcf.do_m) cm = 1 - cm;
+      if (pcf.do_l) cl = 1 - cl;
+      if (pcf.do_m || pcf.do_l) ++ip;
     }
     {
       KScope ks(c, KC_PRECOND, 2 * vb + cbk + (double)(m.N - m.P) * 8 + m.N);
@@ -1017,7 +1051,7 @@ k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename c
 #pragma unroll
       for (int i = 0; i < MPL; ++i) {
         const int k = koff + i;
-        const T dr = vel_dinv<T>(a, A, a.omega[k]);
+        const T dr = vel_dinv<T>(a, A, k);
         const T mu = (T)a.mu, wr = (T)(fabs(a.omega[k]) * a.rho);
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {

@@ -96,6 +96,9 @@ struct Mesh {
   double *Ms_m = nullptr, *Ks_m = nullptr, *Dv_m = nullptr, *DTv_m = nullptr, *Lp_m = nullptr;
   float *Ms_f = nullptr, *Ks_f = nullptr, *Dv_f = nullptr, *DTv_f = nullptr, *Mp_f = nullptr, *Lp_f = nullptr;
   double *ms_diag = nullptr, *ks_diag = nullptr;  // [N]
+  // FP32 copies of the diagonals used by the FP32 preconditioner kernels
+  float *ms_df = nullptr, *ks_df = nullptr;       // [N]
+  float *mp_df = nullptr, *lp_df = nullptr, *k1_df = nullptr;  // [P]
   double *mp_diag = nullptr, *lp_diag = nullptr;  // [P] (lp: outlet rows -> 1)
   // two-level velocity preconditioner: P1 (vertex) coarse space nested in P2
   int32_t *edge_ends = nullptr;   // [N-P][2] end vertices of every edge node
@@ -113,6 +116,8 @@ struct Mesh {
   DevArena mode_arena;
   std::vector<double> omega;     // host copy [ld] (padded with 0)
   double *omega_d = nullptr;     // [ld]
+  double *wabs_d = nullptr, *wrho_d = nullptr;  // [ld] |omega_k| rho, omega_k rho
+  float *wabs_f = nullptr, *wrho_f = nullptr;
   double2 *g = nullptr;          // [m][n_dir][dim]
   double2 *b = nullptr;          // [n_dof][ld] lifted RHS (b_D = g)
   double2 *x = nullptr;          // [n_dof][ld] FP64 solution
