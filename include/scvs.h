@@ -98,12 +98,24 @@ typedef struct {
   void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
 } scvs_opts;
 
+/* Options of scvs_train_guess (learned initial guess). */
+typedef struct {
+  int32_t n_pod;             /* POD vectors per field block (velocity, pressure); default 32 */
+  int32_t hidden;            /* width of the 3 hidden MLP layers; default 256 */
+  int32_t steps;             /* Adam steps; default 3000 */
+  int32_t batch;             /* minibatch size; default 256 */
+  double lr;                 /* Adam learning rate; default 1e-3 (x0.3 after 1/2, x0.1 after 3/4 of the steps) */
+  uint64_t seed;             /* weight initialisation and minibatch order; default 0 */
+  int32_t max_pod_snapshots; /* snapshots entering the POD Gram matrix; default 512 */
+  int32_t reserved;
+} scvs_train_opts;
+
 /* Result of one mode of one mesh after scvs_solve. */
 typedef struct {
   int32_t status;     /* SCVS_CONVERGED / MAX_ITER / STAGNATED / NON_FINITE */
   int32_t iterations; /* Arnoldi steps spent on this mode */
   int32_t cycles;     /* restart cycles (= FP64 refinement steps) */
-  int32_t reserved;
+  int32_t guess_used; /* 1 if the learned initial guess was kept (its residual was below ||b||) */
   double rel_res;     /* final FP64 ||b_F - A_FF x_F - A_FD g|| / ||b_F|| (Eq. ls_error) */
 } scvs_mode_report;
 
@@ -230,6 +242,44 @@ int scvs_apply_precond(scvs_ctx *ctx, int32_t mesh_id, const void *r_dev, void *
 
 /* Number of kernel launches issued by this context since creation. */
 int64_t scvs_launch_count(const scvs_ctx *ctx);
+
+/* ---- learned initial guess ----------------------------------------------
+ * The modes of one geometry family share a node set; a converged mode x_k
+ * divided by its boundary coefficient c_k (the problem is linear in c_k) is a
+ * snapshot.  Training builds a POD basis of the snapshots per field block
+ * (method of snapshots) and fits an MLP  f = (omega_k, Re c_k, Im c_k, R, s)
+ * -> POD coefficients  (3 hidden GELU layers, BF16 weights, FP32 accumulate,
+ * Adam, hand-written kernels).  With opts.guess = SCVS_GUESS_MLP and features
+ * set for a mesh, scvs_solve starts every mode from x0 = c_k Phi a(f) (and g
+ * on the Dirichlet rows); a mode whose x0 has a residual >= ||b|| starts from
+ * zero instead.  The paper solves every mode from scratch; this is an
+ * addition. features: host double [n_modes][5]. */
+void scvs_default_train_opts(scvs_train_opts *opts);
+/* Append the converged modes of a solved mesh to the training set. */
+int scvs_guess_add_snapshots(scvs_ctx *ctx, int32_t mesh_id, const double *features);
+/* POD + MLP training on the GPU; *final_loss (may be NULL) = last minibatch MSE (standardised units). */
+int scvs_train_guess(scvs_ctx *ctx, const scvs_train_opts *opts, double *final_loss);
+/* Features of the modes set on a mesh (used by the next scvs_solve). */
+int scvs_guess_set_features(scvs_ctx *ctx, int32_t mesh_id, const double *features);
+/* Training-set size, POD rank, 1 if a model is trained. */
+int scvs_guess_info(scvs_ctx *ctx, int64_t *n_snapshots, int32_t *n_pod, int32_t *trained);
+/* Drop snapshots and model. */
+int scvs_guess_reset(scvs_ctx *ctx);
+
+/* Raw MLP (no feature/target scaling), for gradient checks and checkpoints.
+ * Parameters are one flat FP32 array: for layer l = 0..3, W_l [in][out]
+ * row-major then b_l [out], sizes n_in -> hidden -> hidden -> hidden -> n_out.
+ * The kernels use the BF16 rounding of W and b and accumulate in FP32. */
+int scvs_mlp_init(scvs_ctx *ctx, int32_t n_in, int32_t hidden, int32_t n_out, const float *params);
+int scvs_mlp_num_params(scvs_ctx *ctx, int64_t *n);
+int scvs_mlp_get_params(scvs_ctx *ctx, float *params);
+/* y_dev[B][n_out] = MLP(x_dev[B][n_in]) (device pointers). */
+int scvs_mlp_forward_dev(scvs_ctx *ctx, const float *x_dev, int64_t batch, float *y_dev);
+/* Gradient of L = sum (y - t)^2 / (B n_out) into grad (host, flat layout); *loss = L. */
+int scvs_mlp_gradient_dev(scvs_ctx *ctx, const float *x_dev, const float *t_dev, int64_t batch, float *grad,
+                          double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+int scvs_mlp_adam_step(scvs_ctx *ctx, double lr);
 
 /* ---- tracing ------------------------------------------------------------
  * Optional CUDA-event timers around every kernel launch, recorded on the

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
-SOURCES = ["api.cu", "assembly.cu", "operators.cu", "krylov.cu", "recon.cu", "matfree.cu", "refmats.cpp"]
+SOURCES = ["api.cu", "assembly.cu", "operators.cu", "krylov.cu", "recon.cu", "matfree.cu", "guess.cu",
+           "refmats.cpp"]
 
 
 def nvcc():
@@ -62,7 +63,7 @@ def build(force=False, verbose_ptxas=False, jobs=None):
             objs.append(o)
             logs.append(log)
     tmp = OUT + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-lcublas"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -264,6 +264,7 @@ void scvs_destroy(scvs_ctx *c) {
     delete m;
   }
   c->timers.destroy();
+  c->guess.release();
   c->work.release();
   delete c;
 }
@@ -575,6 +576,126 @@ int scvs_apply_precond(scvs_ctx *c, int32_t mesh_id, const void *r, void *z) {
 }
 
 int64_t scvs_launch_count(const scvs_ctx *c) { return c ? c->launches.n : -1; }
+
+void scvs_default_train_opts(scvs_train_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_pod = 32;
+  o->hidden = 256;
+  o->steps = 3000;
+  o->batch = 256;
+  o->lr = 1e-3;
+  o->seed = 0;
+  o->max_pod_snapshots = 512;
+}
+
+int scvs_guess_add_snapshots(scvs_ctx *c, int32_t mesh_id, const double *features) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !features) return fail(c, SCVS_ERR_ARG, "bad argument");
+    if (!m->solved) return fail(c, SCVS_ERR_STATE, "solve the mesh before adding its modes as snapshots");
+    guess_add_snapshots(*c, *m, features);
+    return SCVS_OK;
+  });
+}
+
+int scvs_train_guess(scvs_ctx *c, const scvs_train_opts *o, double *loss) {
+  return guarded(c, [&]() {
+    scvs_train_opts d;
+    scvs_default_train_opts(&d);
+    const scvs_train_opts &oo = o ? *o : d;
+    if (oo.n_pod < 1 || oo.hidden < 1 || oo.hidden > 1024 || oo.steps < 0 || oo.batch < 1 || !(oo.lr > 0) ||
+        oo.max_pod_snapshots < 2)
+      return fail(c, SCVS_ERR_ARG, "invalid training options");
+    if (c->guess.n_snap < 4) return fail(c, SCVS_ERR_STATE, "fewer than 4 snapshots");
+    const double l = guess_train(*c, oo);
+    if (loss) *loss = l;
+    return SCVS_OK;
+  });
+}
+
+int scvs_guess_set_features(scvs_ctx *c, int32_t mesh_id, const double *features) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !features || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id, features, or no modes");
+    m->feat.assign(features, features + 5 * m->m);
+    return SCVS_OK;
+  });
+}
+
+int scvs_guess_info(scvs_ctx *c, int64_t *n_snap, int32_t *n_pod, int32_t *trained) {
+  return guarded(c, [&]() {
+    if (n_snap) *n_snap = c->guess.n_snap;
+    if (n_pod) *n_pod = c->guess.n_pod;
+    if (trained) *trained = c->guess.trained ? 1 : 0;
+    return SCVS_OK;
+  });
+}
+
+int scvs_guess_reset(scvs_ctx *c) {
+  return guarded(c, [&]() {
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    c->guess.release();
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_init(scvs_ctx *c, int32_t n_in, int32_t hidden, int32_t n_out, const float *params) {
+  return guarded(c, [&]() {
+    if (n_in < 1 || hidden < 1 || hidden > 1024 || n_out < 1 || !params) return fail(c, SCVS_ERR_ARG, "bad MLP sizes");
+    GuessModel &g = c->guess;
+    mlp_alloc(g, n_in, hidden, n_out);
+    SCVS_CUDA(cudaMemcpy(g.Wf, params, g.n_params * sizeof(float), cudaMemcpyHostToDevice));
+    mlp_refresh_bf16(*c, g);
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_num_params(scvs_ctx *c, int64_t *n) {
+  return guarded(c, [&]() {
+    if (!n) return fail(c, SCVS_ERR_ARG, "null");
+    *n = c->guess.n_params;
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_get_params(scvs_ctx *c, float *params) {
+  return guarded(c, [&]() {
+    if (!params || c->guess.n_params == 0) return fail(c, SCVS_ERR_STATE, "no MLP");
+    SCVS_CUDA(cudaMemcpy(params, c->guess.Wf, c->guess.n_params * sizeof(float), cudaMemcpyDeviceToHost));
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_forward_dev(scvs_ctx *c, const float *x, int64_t B, float *y) {
+  return guarded(c, [&]() {
+    if (!x || !y || B < 1 || c->guess.n_params == 0) return fail(c, SCVS_ERR_ARG, "bad argument or no MLP");
+    mlp_forward(*c, c->guess, x, B, y);
+    SCVS_CUDA(cudaGetLastError());
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_gradient_dev(scvs_ctx *c, const float *x, const float *t, int64_t B, float *grad, double *loss) {
+  return guarded(c, [&]() {
+    if (!x || !t || B < 1 || c->guess.n_params == 0) return fail(c, SCVS_ERR_ARG, "bad argument or no MLP");
+    const float l = mlp_gradient(*c, c->guess, x, t, B);
+    if (grad)
+      SCVS_CUDA(cudaMemcpy(grad, c->guess.grad, c->guess.n_params * sizeof(float), cudaMemcpyDeviceToHost));
+    if (loss) *loss = l;
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_adam_step(scvs_ctx *c, double lr) {
+  return guarded(c, [&]() {
+    if (c->guess.n_params == 0 || !(lr > 0)) return fail(c, SCVS_ERR_ARG, "no MLP or bad lr");
+    mlp_adam(*c, c->guess, (float)lr);
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    return SCVS_OK;
+  });
+}
 
 int scvs_kernel_timers(scvs_ctx *c, int32_t enable) {
   return guarded(c, [&]() {

@@ -384,11 +384,13 @@ __global__ void k_add_to_x(const typename cpx<T>::t *__restrict__ z, const int *
   x[f] = v;
 }
 
-// x = b on Dirichlet rows (= g), 0 elsewhere.
+// x = b on Dirichlet rows (= g), 0 elsewhere (only the modes with reset[k] != 0
+// when `reset` is given).
 __global__ void k_init_x(const double2 *__restrict__ b, const uint8_t *__restrict__ dirm, int64_t N, int dim,
-                         int64_t total, int ld, double2 *__restrict__ x) {
+                         int64_t total, int ld, double2 *__restrict__ x, const int *__restrict__ reset) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= total) return;
+  if (reset && !reset[f % ld]) return;
   const int64_t dof = f / ld;
   const bool dir = dof < N * dim && dirm[dof / dim];
   x[f] = dir ? b[f] : make_double2(0.0, 0.0);
@@ -501,8 +503,12 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   }
 
   const int64_t eb = ceil_div(total, 256);
-  k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x);
-  count_launch(c);
+  bool guess_on = c.opts.guess == SCVS_GUESS_MLP && guess_initial(c, m);
+  if (!guess_on) {
+    k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, nullptr);
+    count_launch(c);
+  }
+  for (int k = 0; k < m.m; ++k) m.rep[k].guess_used = guess_on ? 1 : 0;
 
   int *h_active = nullptr;
   SCVS_CUDA(cudaMallocHost(&h_active, sizeof(int)));
@@ -517,6 +523,24 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       residual_fp64(c, m, nullptr, wk.V, wk.norm2);
     SCVS_CUDA(cudaMemcpyAsync(n2.data(), wk.norm2, ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     SCVS_CUDA(cudaStreamSynchronize(c.stream));
+    if (cyc == 0 && guess_on) {
+      // a guess no better than zero is dropped for that mode (zero-start fallback)
+      std::vector<int> reset(ld, 0);
+      int n_reset = 0;
+      for (int k = 0; k < m.m; ++k) {
+        if (done[k]) continue;
+        const double r = std::sqrt(std::max(n2[k], 0.0));
+        if (!(r < m.bnorm[k])) { reset[k] = 1; ++n_reset; m.rep[k].guess_used = 0; }
+      }
+      guess_on = false;
+      if (n_reset > 0) {
+        SCVS_CUDA(cudaMemcpyAsync(wk.upd, reset.data(), ld * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+        k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, wk.upd);
+        count_launch(c);
+        --cyc;
+        continue;
+      }
+    }
     int n_act = 0;
     for (int k = 0; k < m.m; ++k) {
       if (done[k]) continue;

@@ -6,6 +6,7 @@
 #include <vector>
 #include "../../include/scvs.h"
 #include "common.cuh"
+#include <cuda_bf16.h>
 
 namespace scvs {
 
@@ -126,8 +127,55 @@ struct Mesh {
   std::vector<double> lam_c;     // [ld] same for the P1 coarse velocity operator
   double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
   PcTables pc;
+  std::vector<double> feat;      // [m][5] features of the modes (learned guess)
   bool solved = false;
   std::vector<scvs_mode_report> rep;
+};
+
+// Learned initial guess: snapshots, POD bases, MLP (see guess.cu).
+struct GuessModel {
+  int64_t n_dof = 0, n_u = 0, n_snap = 0, snap_cap = 0;
+  float2 *snap = nullptr;           // [n_snap][n_dof] solutions divided by c_k
+  std::vector<double> feat;         // [n_snap][5]
+  int n_pod = 0;
+  float2 *Phi_u = nullptr, *Phi_p = nullptr;  // [n_u][n_pod], [n_p][n_pod]
+  std::vector<double> fmean, fstd, tmean, tstd;
+  int hidden = 0, n_out = 0, dims[5] = {0, 0, 0, 0, 0};
+  int64_t woff[4] = {0}, boff[4] = {0}, n_params = 0;
+  float *Wf = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr, *scal = nullptr;
+  __nv_bfloat16 *Wb = nullptr, *Wt = nullptr;
+  int64_t adam_t = 0;
+  bool trained = false;
+  float *acts = nullptr;
+  int64_t act_cap = 0;
+  int64_t per_sample() const { return 6 * (int64_t)hidden + 2 * (int64_t)n_out + 2 * (int64_t)std::max(hidden, n_out); }
+  void ensure(int64_t B) {
+    if (act_cap >= B && acts) return;
+    if (acts) cudaFree(acts);
+    act_cap = std::max<int64_t>(B, 64);
+    if (cudaMalloc(&acts, (size_t)act_cap * per_sample() * sizeof(float)) != cudaSuccess) throw std::bad_alloc();
+  }
+  float *zbuf(int l) { return l < 3 ? acts + (int64_t)l * act_cap * hidden : acts + 6 * act_cap * hidden; }
+  float *abuf(int l) { return acts + (int64_t)(3 + l) * act_cap * hidden; }
+  float *ybuf() { return acts + 6 * act_cap * hidden + act_cap * n_out; }
+  float *dbuf(int i) { return acts + 6 * act_cap * hidden + 2 * act_cap * n_out + (int64_t)i * act_cap * std::max(hidden, n_out); }
+  void release_mlp() {
+    for (void *p : {(void *)Wf, (void *)grad, (void *)am, (void *)av, (void *)scal, (void *)Wb, (void *)Wt, (void *)acts})
+      if (p) cudaFree(p);
+    Wf = grad = am = av = scal = acts = nullptr;
+    Wb = Wt = nullptr;
+    act_cap = 0;
+    n_params = 0;
+    trained = false;
+  }
+  void release() {
+    release_mlp();
+    for (void *p : {(void *)snap, (void *)Phi_u, (void *)Phi_p})
+      if (p) cudaFree(p);
+    snap = nullptr; Phi_u = Phi_p = nullptr;
+    n_snap = snap_cap = n_dof = n_u = 0;
+    feat.clear();
+  }
 };
 
 struct Ctx {
@@ -143,6 +191,7 @@ struct Ctx {
   GridSync *gsync = nullptr;
   RefTables ref2, ref3;
   KTimers timers;
+  GuessModel guess;
 };
 
 // Scoped timing of one launch: KT(c, class, algorithmic bytes) { launch; }
@@ -172,6 +221,16 @@ void matfree_tables(Ctx &c);  // matfree.cu
 
 // ---- krylov.cu
 int solve_mesh(Ctx &c, Mesh &m);
+
+// ---- guess.cu
+void guess_add_snapshots(Ctx &c, Mesh &m, const double *features);
+double guess_train(Ctx &c, const scvs_train_opts &o);
+bool guess_initial(Ctx &c, Mesh &m);
+void mlp_alloc(GuessModel &g, int n_in, int hidden, int n_out);
+void mlp_refresh_bf16(Ctx &c, GuessModel &g);
+void mlp_forward(Ctx &c, GuessModel &g, const float *x, int64_t B, float *y);
+float mlp_gradient(Ctx &c, GuessModel &g, const float *x, const float *t, int64_t B);
+void mlp_adam(Ctx &c, GuessModel &g, float lr);
 
 // ---- recon.cu
 void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);

@@ -39,7 +39,13 @@ class scvs_opts(C.Structure):
 
 class scvs_mode_report(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("cycles", C.c_int32),
-                ("reserved", C.c_int32), ("rel_res", C.c_double)]
+                ("guess_used", C.c_int32), ("rel_res", C.c_double)]
+
+
+class scvs_train_opts(C.Structure):
+    _fields_ = [("n_pod", C.c_int32), ("hidden", C.c_int32), ("steps", C.c_int32), ("batch", C.c_int32),
+                ("lr", C.c_double), ("seed", C.c_uint64), ("max_pod_snapshots", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ScvsError(RuntimeError):
@@ -81,6 +87,18 @@ SIGNATURES = {
     "scvs_rhs_dev": (_I32, [_P, _I32, C.POINTER(_P)]),
     "scvs_apply_precond": (_I32, [_P, _I32, _P, _P]),
     "scvs_launch_count": (_I64, [_P]),
+    "scvs_default_train_opts": (None, [C.POINTER(scvs_train_opts)]),
+    "scvs_guess_add_snapshots": (_I32, [_P, _I32, _P]),
+    "scvs_train_guess": (_I32, [_P, C.POINTER(scvs_train_opts), C.POINTER(_D)]),
+    "scvs_guess_set_features": (_I32, [_P, _I32, _P]),
+    "scvs_guess_info": (_I32, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32)]),
+    "scvs_guess_reset": (_I32, [_P]),
+    "scvs_mlp_init": (_I32, [_P, _I32, _I32, _I32, _P]),
+    "scvs_mlp_num_params": (_I32, [_P, C.POINTER(_I64)]),
+    "scvs_mlp_get_params": (_I32, [_P, _P]),
+    "scvs_mlp_forward_dev": (_I32, [_P, _P, _I64, _P]),
+    "scvs_mlp_gradient_dev": (_I32, [_P, _P, _P, _I64, _P, C.POINTER(_D)]),
+    "scvs_mlp_adam_step": (_I32, [_P, _D]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
 }
@@ -184,8 +202,8 @@ def scvs_solve(ctx, mesh_id=-1, n_reports=0):
     """Returns a list of dicts (status, iterations, cycles, rel_res)."""
     rep = (scvs_mode_report * max(1, n_reports))()
     _check(ctx, lib().scvs_solve(ctx, mesh_id, rep, n_reports))
-    return [dict(status=r.status, iterations=r.iterations, cycles=r.cycles, rel_res=r.rel_res)
-            for r in rep[:n_reports]]
+    return [dict(status=r.status, iterations=r.iterations, cycles=r.cycles, rel_res=r.rel_res,
+                 guess_used=r.guess_used) for r in rep[:n_reports]]
 
 
 def scvs_get_modal(ctx, mesh_id, n_modes, n_nodes, dim, n_vertices):
@@ -273,6 +291,72 @@ def scvs_apply_precond(ctx, mesh_id, r_dev, z_dev):
 
 def scvs_launch_count(ctx):
     return lib().scvs_launch_count(ctx)
+
+
+def scvs_default_train_opts(**overrides):
+    o = scvs_train_opts()
+    lib().scvs_default_train_opts(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def scvs_guess_add_snapshots(ctx, mesh_id, features):
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    return _check(ctx, lib().scvs_guess_add_snapshots(ctx, mesh_id, _ptr(f)))
+
+
+def scvs_train_guess(ctx, opts=None):
+    loss = C.c_double()
+    _check(ctx, lib().scvs_train_guess(ctx, C.byref(opts) if opts is not None else None, C.byref(loss)))
+    return loss.value
+
+
+def scvs_guess_set_features(ctx, mesh_id, features):
+    f = np.ascontiguousarray(features, dtype=np.float64)
+    return _check(ctx, lib().scvs_guess_set_features(ctx, mesh_id, _ptr(f)))
+
+
+def scvs_guess_info(ctx):
+    n, r, t = C.c_int64(), C.c_int32(), C.c_int32()
+    _check(ctx, lib().scvs_guess_info(ctx, C.byref(n), C.byref(r), C.byref(t)))
+    return dict(n_snapshots=n.value, n_pod=r.value, trained=bool(t.value))
+
+
+def scvs_guess_reset(ctx):
+    return _check(ctx, lib().scvs_guess_reset(ctx))
+
+
+def scvs_mlp_init(ctx, n_in, hidden, n_out, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(ctx, lib().scvs_mlp_init(ctx, n_in, hidden, n_out, _ptr(p)))
+
+
+def scvs_mlp_num_params(ctx):
+    n = C.c_int64()
+    _check(ctx, lib().scvs_mlp_num_params(ctx, C.byref(n)))
+    return n.value
+
+
+def scvs_mlp_get_params(ctx):
+    out = np.empty(scvs_mlp_num_params(ctx), dtype=np.float32)
+    _check(ctx, lib().scvs_mlp_get_params(ctx, _ptr(out)))
+    return out
+
+
+def scvs_mlp_forward_dev(ctx, x_dev, batch, y_dev):
+    return _check(ctx, lib().scvs_mlp_forward_dev(ctx, x_dev, batch, y_dev))
+
+
+def scvs_mlp_gradient_dev(ctx, x_dev, t_dev, batch):
+    g = np.empty(scvs_mlp_num_params(ctx), dtype=np.float32)
+    loss = C.c_double()
+    _check(ctx, lib().scvs_mlp_gradient_dev(ctx, x_dev, t_dev, batch, _ptr(g), C.byref(loss)))
+    return g, loss.value
+
+
+def scvs_mlp_adam_step(ctx, lr):
+    return _check(ctx, lib().scvs_mlp_adam_step(ctx, lr))
 
 
 def scvs_kernel_timers(ctx, enable):
