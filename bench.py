@@ -236,6 +236,7 @@ def run_gpu(args):
     ktimes = scvs.scvs_kernel_times(ctx)
     scvs.scvs_kernel_timers(ctx, False)
     conv = sum(1 for rr in reps for r in rr if r["status"] == scvs.SCVS_CONVERGED)
+    tuned = scvs.scvs_tuned_shapes(ctx, 0)
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([elapsed], device=dev)
@@ -280,7 +281,10 @@ def run_gpu(args):
     ms, by, nl = ktimes[dom]
     achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     traffic = traffic_from_profiles(dom)
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+    kernel_names = {"cheb_fine": "k_pc_cheb (velocity rows) + k_vel_residual", "arnoldi": "k_arnoldi",
+                    "spmm_fp32": "k_saddle<float>", "precond": "k_coarse_cheb/k_pc_cheb (pressure)/k_pc_step0/...",
+                    "spmm_fp64": "k_saddle<double>"}
+    roof = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind,
             "launches": nl, "avg_launch_us": ms / max(nl, 1) * 1e3,
             "algorithmic_bytes_per_launch": by / max(nl, 1)}
@@ -295,7 +299,7 @@ def run_gpu(args):
            "dtype": "c128" if args.precision == "fp64" else "c64+f64", "data": "synthetic",
            "config": workload_config(), "roofline": roof, "spmm": spmm,
            "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
-           "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb,
+           "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb, "autotune": tuned,
            "solve": {"converged": conv, "modes_per_step": m,
                      "iterations_max": max(r["iterations"] for r in last),
                      "iterations_mean": float(np.mean([r["iterations"] for r in last])),
@@ -336,6 +340,141 @@ def run_kernel_case(args):
         torch.cuda.synchronize()
         log("kernel case done:", scvs.scvs_launch_count(s.ctx), "launches; cycle iterations",
             [r["iterations"] for r in rep][:4])
+
+
+def run_batch(args):
+    """Uneven batch: 48 stenosed pipes (20k-400k P2 nodes, log-uniform), 16
+    modes each = 768 independent systems, solved as one mesh of independent
+    components (one launch per kernel for all meshes)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2009_06725_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2009_06725_gb300 import scvs
+    parts = workloads.uneven_pipes(n_meshes=args.batch_meshes, n_modes=16, seed=0, scale=args.batch_scale)
+    U = workloads.union_workload(parts)
+    mesh = U["mesh"]
+    N, P, E, d = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["conn"].shape[0], 3
+    m = len(U["omegas"])
+    stream = torch.cuda.current_stream(dev)
+    solver = scvs.Solver(stream=stream.cuda_stream)
+    ctx = solver.ctx
+    xyz_d = torch.from_numpy(mesh["xyz"]).to(dev)
+    conn_d = torch.from_numpy(mesh["conn"]).to(dev)
+    tag_d = torch.from_numpy(mesh["tag"]).to(dev)
+    g_d = torch.from_numpy(np.ascontiguousarray(U["g"])).to(dev)
+    u_t = torch.empty((N_T, N, d), dtype=torch.float64, device=dev)
+    p_t = torch.empty((N_T, P), dtype=torch.float64, device=dev)
+
+    def step():
+        scvs.scvs_clear_meshes(ctx)
+        mid = scvs.scvs_set_mesh_dev(ctx, d, N, P, xyz_d.data_ptr(), E, conn_d.data_ptr(), tag_d.data_ptr())
+        scvs.scvs_set_components(ctx, mid, U["n_comp"], U["node_comp"])
+        scvs.scvs_set_physics(ctx, mid, U["rho"], U["mu"])
+        scvs.scvs_set_modes_dev(ctx, mid, U["omegas"], g_d.data_ptr())
+        rep = scvs.scvs_solve(ctx, mid, U["n_comp"] * m)
+        scvs.scvs_reconstruct_dev(ctx, mid, N_T, U["period"], u_t.data_ptr(), p_t.data_ptr())
+        return rep
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    scvs.scvs_kernel_timers(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    el = ev0.elapsed_time(ev1) / 1e3
+    kt = scvs.scvs_kernel_times(ctx)
+    conv = sum(1 for rr in reps for r in rr if r["status"] == scvs.SCVS_CONVERGED)
+    sizes = [p["mesh"]["xyz"].shape[0] for p in parts]
+    out = {"metric": "converged mode-solves/s at 1e-8 rel. residual", "value": conv / el, "unit": "mode-solves/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+           "impl": "batch",
+           "config": {"workload": (f"uneven batch: {len(parts)} stenosed pipes (R 0.5-1.5, L 5-20, s 0-0.5), "
+                                   f"{min(sizes)}-{max(sizes)} P2 nodes (total {N}), 16 modes each = "
+                                   f"{len(parts) * 16} systems, one mesh of independent components"),
+                      "systems": len(parts) * 16, "nodes_total": N},
+           "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
+           "solve": {"converged": conv, "systems_per_step": len(parts) * 16,
+                     "iterations_max": max(r["iterations"] for r in reps[-1]),
+                     "iterations_mean": float(np.mean([r["iterations"] for r in reps[-1]])),
+                     "rel_res_max": max(r["rel_res"] for r in reps[-1])}}
+    print(json.dumps(out), flush=True)
+    solver.close()
+
+
+def run_guess(args):
+    """Learned initial guess on the benchmark pipe family: train on morphs
+    (R ~ U[0.5, 1.5], s ~ U[0, 0.5]) of the 151k-node pipe, then solve
+    held-out morphs with and without the guess."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2009_06725_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2009_06725_gb300 import scvs
+    rng = np.random.default_rng(0)
+
+    def morph(i):
+        R, st = rng.uniform(0.5, 1.5), rng.uniform(0.0, 0.5)
+        wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=PIPE["n_x"], n_modes=PIPE["n_modes"],
+                                     length=PIPE["length"], radius=R, stenosis=st, seed=0)
+        c = workloads.phases(PIPE["n_modes"], seed=100 + i)
+        wl = dict(wl, coeffs=c, g=wl["g"] / wl["coeffs"][:, None, None] * c[:, None, None])
+        f = np.stack([wl["omegas"], c.real, c.imag, np.full(len(c), R), np.full(len(c), st)], axis=1)
+        return wl, f
+
+    def solve(s, wl, f):
+        scvs.scvs_clear_meshes(s.ctx)
+        mid = scvs.scvs_set_mesh(s.ctx, wl["mesh"])
+        scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
+        scvs.scvs_set_modes(s.ctx, mid, wl["omegas"], wl["g"])
+        scvs.scvs_guess_set_features(s.ctx, mid, f)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rep = scvs.scvs_solve(s.ctx, mid, len(f))
+        return mid, rep, time.perf_counter() - t
+
+    with scvs.Solver() as s:
+        t0 = time.perf_counter()
+        for i in range(args.guess_train):
+            wl, f = morph(i)
+            mid, rep, _ = solve(s, wl, f)
+            scvs.scvs_guess_add_snapshots(s.ctx, mid, f)
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        loss = scvs.scvs_train_guess(s.ctx, scvs.scvs_default_train_opts(steps=args.guess_steps))
+        t_train = time.perf_counter() - t0
+        rows = []
+        for i in range(args.guess_test):
+            wl, f = morph(10_000 + i)
+            res = {}
+            for gmode in (scvs.SCVS_GUESS_ZERO, scvs.SCVS_GUESS_MLP):
+                s.set_opts(guess=gmode)
+                _, rep, dt = solve(s, wl, f)
+                res[gmode] = (rep, dt)
+            rows.append(res)
+        info = scvs.scvs_guess_info(s.ctx)
+    it0 = [r["iterations"] for res in rows for r in res[scvs.SCVS_GUESS_ZERO][0]]
+    it1 = [r["iterations"] for res in rows for r in res[scvs.SCVS_GUESS_MLP][0]]
+    t0s = sum(res[scvs.SCVS_GUESS_ZERO][1] for res in rows)
+    t1s = sum(res[scvs.SCVS_GUESS_MLP][1] for res in rows)
+    n = len(it0)
+    conv1 = sum(1 for res in rows for r in res[scvs.SCVS_GUESS_MLP][0] if r["status"] == scvs.SCVS_CONVERGED)
+    out = {"metric": "converged mode-solves/s at 1e-8 rel. residual", "value": conv1 / t1s, "unit": "mode-solves/s",
+           "n_gpus": 1, "higher_is_better": True, "impl": "learned-guess", "data": "synthetic", "dtype": "c64+f64",
+           "config": {"workload": (f"learned initial guess: {args.guess_train} training morphs x 32 modes of the "
+                                   f"151k-node pipe (R 0.5-1.5, s 0-0.5), {args.guess_test} held-out morphs"),
+                      "snapshots": info["n_snapshots"], "n_pod": info["n_pod"], "mlp": "5-256-256-256-128 GELU BF16"},
+           "without_guess": {"value": n / t0s, "iterations_mean": float(np.mean(it0)), "iterations_max": int(max(it0)),
+                             "solve_s": t0s},
+           "with_guess": {"value": conv1 / t1s, "iterations_mean": float(np.mean(it1)), "iterations_max": int(max(it1)),
+                          "solve_s": t1s},
+           "training": {"data_s": t_data, "train_s": t_train, "final_loss": loss}}
+    print(json.dumps(out), flush=True)
 
 
 def step_host(scvs, ctx, wl, m, N, P, d):
@@ -381,9 +520,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")
+    ap.add_argument("--workload", default="pipe", choices=["pipe", "batch", "guess"])
+    ap.add_argument("--batch-meshes", type=int, default=48)
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's node counts")
+    ap.add_argument("--guess-train", type=int, default=16, help="training morphs (x 32 modes)")
+    ap.add_argument("--guess-test", type=int, default=3)
+    ap.add_argument("--guess-steps", type=int, default=3000)
     args = ap.parse_args()
     if args.kernel_case:
         run_kernel_case(args)
+        return
+    if args.workload == "batch" and args.impl == "gpu":
+        run_batch(args)
+        return
+    if args.workload == "guess" and args.impl == "gpu":
+        run_guess(args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         log("note: the timing rules ask for >= 3 warm-up steps")

@@ -90,11 +90,13 @@ typedef struct {
   int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with BLOCK_PMG the degree of each
                         of the pre- and post-smoothers (default 4) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
-  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 30) */
+  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 45) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
   int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of BLOCK_PMG (default 20) */
+  int32_t autotune;  /* 1 (default): time the row-group shapes of the FP32 SpMM and Chebyshev kernels on each
+                        mesh at scvs_set_modes and keep the fastest; 0: default shapes */
   void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
 } scvs_opts;
 
@@ -144,6 +146,17 @@ int scvs_set_mesh_dev(scvs_ctx *ctx, int32_t dim, int64_t n_nodes, int64_t n_ver
 /* Drop every mesh (and its modes) from the context. */
 int scvs_clear_meshes(scvs_ctx *ctx);
 
+/* Declare a mesh as the disjoint union of n_comp independent components
+ * (node_comp[n_nodes] in [0, n_comp), host; no element may span two
+ * components).  Every (component, mode) pair is then solved as its own
+ * linear system (own Krylov space, convergence test and report entry) while
+ * every kernel launch covers all components at once: this is how many meshes
+ * of uneven size are batched.  Components share rho, mu and the mode list.
+ * scvs_solve reports n_comp * n_modes entries for the mesh, component-major.
+ * The learned guess is not applied to multi-component meshes.
+ * Returns SCVS_ERR_MESH if an element couples two components. */
+int scvs_set_components(scvs_ctx *ctx, int32_t mesh_id, int32_t n_comp, const int32_t *node_comp);
+
 /* Physical constants rho, mu of a mesh (Eq. stokes_complex); defaults 1, 1. */
 int scvs_set_physics(scvs_ctx *ctx, int32_t mesh_id, double rho, double mu);
 
@@ -161,8 +174,8 @@ int scvs_set_modes_dev(scvs_ctx *ctx, int32_t mesh_id, int32_t n_modes, const do
                        const void *g_dev /* double2 [n_modes][n_dir][dim] */);
 
 /* Solve every mode of every mesh (mesh_id = -1) or of one mesh.  rep (host,
- * may be NULL) receives one entry per (mesh, mode) in mesh order, rep_len
- * entries at most.  Returns SCVS_OK even if some modes did not converge;
+ * may be NULL) receives one entry per (mesh, component, mode) in mesh order,
+ * rep_len entries at most.  Returns SCVS_OK even if some modes did not converge;
  * their status says so. */
 int scvs_solve(scvs_ctx *ctx, int32_t mesh_id, scvs_mode_report *rep, int64_t rep_len);
 
@@ -285,18 +298,25 @@ int scvs_mlp_adam_step(scvs_ctx *ctx, double lr);
  * Optional CUDA-event timers around every kernel launch, recorded on the
  * context's stream, grouped in classes:
  *   0 all-modes SpMM FP32, 1 all-modes SpMM FP64 (lift, true residual),
- *   2 block preconditioner, 3 Arnoldi orthogonalisation + Hessenberg,
- *   4 elementwise vector kernels, 5 pattern/assembly, 6 reconstruction,
- *   7 matrix-free apply.
+ *   2 block preconditioner except its fine velocity sweeps, 3 Arnoldi
+ *   orthogonalisation + Hessenberg, 4 elementwise vector kernels,
+ *   5 pattern/assembly, 6 reconstruction, 7 matrix-free apply,
+ *   8 fine velocity Chebyshev sweeps and residual of the preconditioner.
  * Each class also sums the algorithmic bytes of its launches (the data the
  * kernel must read and write at minimum: matrix values and indices once,
  * every vector operand once).  scvs_kernel_timers(ctx, 1) clears and enables,
  * (ctx, 0) clears and disables.  scvs_kernel_times fills up to n_classes
  * entries of ms (summed device time), bytes and launches (any may be NULL)
  * and returns the number of classes. */
-#define SCVS_KC_COUNT 8
+#define SCVS_KC_COUNT 9
 int scvs_kernel_timers(scvs_ctx *ctx, int32_t enable);
 int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *bytes, int64_t *launches);
+
+/* Row-group shapes chosen by the autotuner for a mesh (modes per lane of the
+ * FP32 SpMM and of the fine Chebyshev sweep; 0 = not tuned) and the measured
+ * candidate times in microseconds (us[6]: SpMM for 1, 2, 4 modes per lane,
+ * then Chebyshev sweep; 0 = candidate not valid for the mode stride). */
+int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *mpl_spmm, int32_t *mpl_cheb, float *us);
 
 #ifdef __cplusplus
 }

@@ -142,6 +142,7 @@ int add_mesh(scvs_ctx *c, int dim, int64_t N, int64_t P, const double *xyz, int6
   m->n_dir = (int64_t)dn.size();
   try {
     build_mesh(*c, *m, xyz, conn, tag);
+    set_chunks(*c, *m, nullptr, 1);
     m->dir_nodes = m->arena.alloc<int64_t>(std::max<int64_t>(1, m->n_dir));
     if (m->n_dir)
       SCVS_CUDA(cudaMemcpy(m->dir_nodes, dn.data(), m->n_dir * sizeof(int64_t), cudaMemcpyHostToDevice));
@@ -178,6 +179,7 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
   if (!omega || (!g && m->n_dir > 0)) return fail(c, SCVS_ERR_ARG, "null omega or g");
   m->mode_arena.release();
   m->pc = PcTables{};
+  m->mpl_spmm = m->mpl_cheb = 0;
   m->solved = false;
   m->m = n_modes;
   m->ld = mode_stride(n_modes);
@@ -201,6 +203,7 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
   SCVS_CUDA(cudaMemsetAsync(m->x, 0, total * sizeof(double2), c->stream));
   lift_rhs(*c, *m);
   spectral_bounds(*c, *m);
+  if (c->opts.autotune) autotune_shapes(*c, *m);
   return SCVS_OK;
 }
 
@@ -217,8 +220,9 @@ void scvs_default_opts(scvs_opts *o) {
   o->precond = SCVS_PC_BLOCK_PMG;
   o->cheb_u = 4;
   o->cheb_c = 20;
+  o->autotune = 1;
   o->cheb_m = 4;
-  o->cheb_l = 30;
+  o->cheb_l = 45;
   o->max_cycles = 400;
   o->guess = SCVS_GUESS_ZERO;
   o->verbose = 0;
@@ -306,6 +310,34 @@ int scvs_clear_meshes(scvs_ctx *c) {
   });
 }
 
+int scvs_set_components(scvs_ctx *c, int32_t mesh_id, int32_t n_comp, const int32_t *node_comp) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    if (n_comp < 1 || n_comp > 65536 || (n_comp > 1 && !node_comp))
+      return fail(c, SCVS_ERR_ARG, "n_comp must be in [1, 65536] with a node_comp array");
+    if (node_comp)
+      for (int64_t i = 0; i < m->N; ++i)
+        if (node_comp[i] < 0 || node_comp[i] >= n_comp) return fail(c, SCVS_ERR_ARG, "node_comp out of range");
+    // no matrix entry may couple two components
+    if (node_comp && n_comp > 1) {
+      std::vector<int64_t> sp(m->N + 1);
+      std::vector<int32_t> sc(m->s_nnz);
+      SCVS_CUDA(cudaMemcpy(sp.data(), m->s_ptr, sp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+      SCVS_CUDA(cudaMemcpy(sc.data(), m->s_col, sc.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      for (int64_t r = 0; r < m->N; ++r)
+        for (int64_t t = sp[r]; t < sp[r + 1]; ++t)
+          if (node_comp[sc[t]] != node_comp[r]) return fail(c, SCVS_ERR_MESH, "an element spans two components");
+    }
+    set_chunks(*c, *m, n_comp > 1 ? node_comp : nullptr, n_comp);
+    if (m->m > 0) {  // modes already set: per-system norms of the right-hand sides
+      lift_rhs(*c, *m);
+      m->solved = false;
+    }
+    return SCVS_OK;
+  });
+}
+
 int scvs_set_physics(scvs_ctx *c, int32_t mesh_id, double rho, double mu) {
   return guarded(c, [&]() {
     Mesh *m = get_mesh(c, mesh_id);
@@ -358,7 +390,7 @@ int scvs_solve(scvs_ctx *c, int32_t mesh_id, scvs_mode_report *rep, int64_t rep_
       int r = solve_mesh(*c, *m);
       if (r != SCVS_OK) return fail(c, r, r == SCVS_ERR_TIMEOUT ? "a device grid barrier timed out" : "solve failed");
       m->solved = true;
-      for (int k = 0; k < m->m; ++k, ++pos)
+      for (size_t k = 0; k < m->rep.size(); ++k, ++pos)
         if (rep && pos < rep_len) rep[pos] = m->rep[k];
     }
     return SCVS_OK;
@@ -693,6 +725,18 @@ int scvs_mlp_adam_step(scvs_ctx *c, double lr) {
     if (c->guess.n_params == 0 || !(lr > 0)) return fail(c, SCVS_ERR_ARG, "no MLP or bad lr");
     mlp_adam(*c, c->guess, (float)lr);
     SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    return SCVS_OK;
+  });
+}
+
+int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *ms, int32_t *mc, float *us) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    if (ms) *ms = m->mpl_spmm;
+    if (mc) *mc = m->mpl_cheb;
+    if (us)
+      for (int i = 0; i < 6; ++i) us[i] = i < (int)m->tune_us.size() ? m->tune_us[i] : 0.0f;
     return SCVS_OK;
   });
 }

@@ -28,22 +28,28 @@ namespace scvs {
 
 template <typename T> struct ArnArgs {
   int64_t rows;
-  int ld, m_r;
+  int ld, m_r, n_comp;
   typename cpx<T>::t *V;        // [(m_r+1)][rows][ld]
   const typename cpx<T>::t *w;  // A_hat z
   int64_t vstride;              // rows * ld
-  double2 *part;                // [gridDim][m_r+2][ld]
-  double2 *h;                   // [m_r+2][ld]
-  double2 *H;                   // [ld][m_r+1][m_r]   rotated Hessenberg (R factor)
-  double *cs;                   // [ld][m_r]
-  double2 *sn;                  // [ld][m_r]
-  double2 *gv;                  // [ld][m_r+1]        rotated residual vector
-  int *state;                   // [ld] 1 = Arnoldi running for this mode
-  int *kdim;                    // [ld] accepted steps in this cycle
-  const double *target;         // [ld] residual-estimate target
-  double *rscale;               // [ld] 1/||v_{j+1}|| for the next preconditioner step
-  double *est;                  // [ld] |g_{j+1}|
-  int *n_active;                // [1]
+  // row chunks (never straddling components), grouped by component
+  int64_t n_chunk;
+  const int64_t *chunk_row0;
+  const int32_t *chunk_rows, *chunk_comp, *comp_chunk;
+  const uint8_t *comp_active;   // chunks of inactive components are skipped
+  double2 *part;                // [n_chunk][m_r+2][ld] chunk partials
+  double2 *h;                   // [n_comp][m_r+2][ld] reduced products (slot j+1: ||w||^2)
+  // per system s = comp * ld + k
+  double2 *H;                   // [S][m_r+1][m_r]   rotated Hessenberg (R factor)
+  double *cs;                   // [S][m_r]
+  double2 *sn;                  // [S][m_r]
+  double2 *gv;                  // [S][m_r+1]        rotated residual vector
+  int *state;                   // [S] 1 = Arnoldi running for this system
+  int *kdim;                    // [S] accepted steps in this cycle
+  const double *target;         // [S] residual-estimate target
+  double *rscale;               // [S] 1/||v_{j+1}|| for the next preconditioner step
+  double *est;                  // [S] |g_{j+1}|
+  int *n_active;                // [1] zeroed before the launch
   GridSync *gs;
   double breakdown;             // relative size of h_{j+1,j} treated as breakdown
 };
@@ -57,6 +63,13 @@ __device__ __forceinline__ T warp_rows_sum(T v) {
   return v;
 }
 
+// One Arnoldi step j for every system in one cooperative launch:
+//   phase 1  chunk partials of <v_i, w> (i <= j) and ||w||^2
+//   phase 2  per (component, slot, mode) sums over the component's chunks
+//   phase 3  w' = w - sum_i h_i v_i -> v_{j+1}, chunk partials of ||w'||^2
+//   phase 4  per system: sigma = ||w'||, Hessenberg column, complex Givens
+//            rotations and residual estimate in FP64
+// separated by bounded grid barriers.
 template <typename T, int MPL, int TPR>
 __global__ void __launch_bounds__(256, 3) k_arnoldi(const ArnArgs<T> a, const int j) {
   using C = typename cpx<T>::t;
@@ -69,218 +82,223 @@ __global__ void __launch_bounds__(256, 3) k_arnoldi(const ArnArgs<T> a, const in
   const int nvec = j + 1, nslots = j + 2;
   const int sstride = 2 * ld;                  // one slot: ld complex as (re, im)
   const int wstride = (a.m_r + 2) * sstride;   // one warp's slots
-  const int64_t ntiles = (a.rows + TR - 1) / TR;
   const bool row_leader = lane32 < TPR;        // holds the warp's row-reduced sums
+  const int64_t pstride = (int64_t)(a.m_r + 2) * ld;
 
-  // ---------------- phase 1: partial Hermitian products <v_i, w> and ||w||^2
+  // ---------------- phase 1: chunk partials of <v_i, w> and ||w||^2
   T *myacc = acc + warp * wstride;
-  for (int t = lane32; t < nslots * sstride; t += 32) myacc[t] = T(0);
-  __syncwarp();
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    CV<T, MPL> wv[ARN_RPT];
-    int64_t rr[ARN_RPT];
-#pragma unroll
-    for (int q = 0; q < ARN_RPT; ++q) {
-      rr[q] = tile * TR + roff + (int64_t)q * RPB;
-      if (rr[q] < a.rows) ldv<T, MPL>(wv[q], a.w + rr[q] * ld + koff); else wv[q].zero();
-    }
-    {
-      T s[MPL];
-#pragma unroll
-      for (int i = 0; i < MPL; ++i) {
-        s[i] = 0;
-#pragma unroll
-        for (int q = 0; q < ARN_RPT; ++q) s[i] += wv[q].re[i] * wv[q].re[i] + wv[q].im[i] * wv[q].im[i];
-        s[i] = warp_rows_sum<T, TPR>(s[i]);
-      }
-      if (row_leader)
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) myacc[(j + 1) * sstride + 2 * (koff + i)] += s[i];
-    }
-    // Krylov vectors in pairs: 2 x ARN_RPT independent loads in flight per thread
-    for (int vi = 0; vi < nvec; vi += 2) {
-      const bool two = vi + 1 < nvec;
-      const C *V0 = a.V + (int64_t)vi * a.vstride;
-      const C *V1 = a.V + (int64_t)(two ? vi + 1 : vi) * a.vstride;
-      CV<T, MPL> v0[ARN_RPT], v1[ARN_RPT];
+  for (int64_t ch = blockIdx.x; ch < a.n_chunk; ch += gridDim.x) {
+    if (!a.comp_active[a.chunk_comp[ch]]) continue;  // block-uniform
+    for (int t = lane32; t < nslots * sstride; t += 32) myacc[t] = T(0);
+    __syncwarp();
+    const int64_t r0 = a.chunk_row0[ch], r1 = r0 + a.chunk_rows[ch];
+    for (int64_t tb = r0; tb < r1; tb += TR) {
+      CV<T, MPL> wv[ARN_RPT];
+      int64_t rr[ARN_RPT];
 #pragma unroll
       for (int q = 0; q < ARN_RPT; ++q) {
-        if (rr[q] < a.rows) {
-          ldv<T, MPL>(v0[q], V0 + rr[q] * ld + koff);
-          if (two) ldv<T, MPL>(v1[q], V1 + rr[q] * ld + koff); else v1[q].zero();
-        } else {
-          v0[q].zero();
-          v1[q].zero();
-        }
+        rr[q] = tb + roff + (int64_t)q * RPB;
+        if (rr[q] < r1) ldv<T, MPL>(wv[q], a.w + rr[q] * ld + koff); else wv[q].zero();
       }
-      T sr0[MPL], si0[MPL], sr1[MPL], si1[MPL];
-#pragma unroll
-      for (int i = 0; i < MPL; ++i) {
-        sr0[i] = si0[i] = sr1[i] = si1[i] = 0;
-#pragma unroll
-        for (int q = 0; q < ARN_RPT; ++q) {  // conj(v) * w
-          sr0[i] += v0[q].re[i] * wv[q].re[i] + v0[q].im[i] * wv[q].im[i];
-          si0[i] += v0[q].re[i] * wv[q].im[i] - v0[q].im[i] * wv[q].re[i];
-          sr1[i] += v1[q].re[i] * wv[q].re[i] + v1[q].im[i] * wv[q].im[i];
-          si1[i] += v1[q].re[i] * wv[q].im[i] - v1[q].im[i] * wv[q].re[i];
-        }
-        sr0[i] = warp_rows_sum<T, TPR>(sr0[i]);
-        si0[i] = warp_rows_sum<T, TPR>(si0[i]);
-        sr1[i] = warp_rows_sum<T, TPR>(sr1[i]);
-        si1[i] = warp_rows_sum<T, TPR>(si1[i]);
-      }
-      if (row_leader)
+      {
+        T s[MPL];
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
-          myacc[vi * sstride + 2 * (koff + i)] += sr0[i];
-          myacc[vi * sstride + 2 * (koff + i) + 1] += si0[i];
-          if (two) {
-            myacc[(vi + 1) * sstride + 2 * (koff + i)] += sr1[i];
-            myacc[(vi + 1) * sstride + 2 * (koff + i) + 1] += si1[i];
+          s[i] = 0;
+#pragma unroll
+          for (int q = 0; q < ARN_RPT; ++q) s[i] += wv[q].re[i] * wv[q].re[i] + wv[q].im[i] * wv[q].im[i];
+          s[i] = warp_rows_sum<T, TPR>(s[i]);
+        }
+        if (row_leader)
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) myacc[(j + 1) * sstride + 2 * (koff + i)] += s[i];
+      }
+      // Krylov vectors in pairs: 2 x ARN_RPT independent loads in flight per thread
+      for (int vi = 0; vi < nvec; vi += 2) {
+        const bool two = vi + 1 < nvec;
+        const C *V0 = a.V + (int64_t)vi * a.vstride;
+        const C *V1 = a.V + (int64_t)(two ? vi + 1 : vi) * a.vstride;
+        CV<T, MPL> v0[ARN_RPT], v1[ARN_RPT];
+#pragma unroll
+        for (int q = 0; q < ARN_RPT; ++q) {
+          if (rr[q] < r1) {
+            ldv<T, MPL>(v0[q], V0 + rr[q] * ld + koff);
+            if (two) ldv<T, MPL>(v1[q], V1 + rr[q] * ld + koff); else v1[q].zero();
+          } else {
+            v0[q].zero();
+            v1[q].zero();
           }
         }
+        T sr0[MPL], si0[MPL], sr1[MPL], si1[MPL];
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+          sr0[i] = si0[i] = sr1[i] = si1[i] = 0;
+#pragma unroll
+          for (int q = 0; q < ARN_RPT; ++q) {  // conj(v) * w
+            sr0[i] += v0[q].re[i] * wv[q].re[i] + v0[q].im[i] * wv[q].im[i];
+            si0[i] += v0[q].re[i] * wv[q].im[i] - v0[q].im[i] * wv[q].re[i];
+            sr1[i] += v1[q].re[i] * wv[q].re[i] + v1[q].im[i] * wv[q].im[i];
+            si1[i] += v1[q].re[i] * wv[q].im[i] - v1[q].im[i] * wv[q].re[i];
+          }
+          sr0[i] = warp_rows_sum<T, TPR>(sr0[i]);
+          si0[i] = warp_rows_sum<T, TPR>(si0[i]);
+          sr1[i] = warp_rows_sum<T, TPR>(sr1[i]);
+          si1[i] = warp_rows_sum<T, TPR>(si1[i]);
+        }
+        if (row_leader)
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) {
+            myacc[vi * sstride + 2 * (koff + i)] += sr0[i];
+            myacc[vi * sstride + 2 * (koff + i) + 1] += si0[i];
+            if (two) {
+              myacc[(vi + 1) * sstride + 2 * (koff + i)] += sr1[i];
+              myacc[(vi + 1) * sstride + 2 * (koff + i) + 1] += si1[i];
+            }
+          }
+      }
     }
-  }
-  __syncthreads();
-  // block partials (warps summed in fixed order) -> global, FP64
-  for (int e = threadIdx.x; e < nslots * ld; e += blockDim.x) {
-    double re = 0, im = 0;
-    for (int w = 0; w < nwarps; ++w) {
-      re += (double)acc[w * wstride + 2 * e];
-      im += (double)acc[w * wstride + 2 * e + 1];
+    __syncthreads();
+    // chunk partial (warps summed in fixed order) -> global, FP64
+    for (int e = threadIdx.x; e < nslots * ld; e += blockDim.x) {
+      double re = 0, im = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        re += (double)acc[w * wstride + 2 * e];
+        im += (double)acc[w * wstride + 2 * e + 1];
+      }
+      a.part[ch * pstride + e] = make_double2(re, im);
     }
-    a.part[((int64_t)blockIdx.x * (a.m_r + 2)) * ld + e] = make_double2(re, im);
+    __syncthreads();
   }
   if (!grid_sync(a.gs, gridDim.x)) return;
 
-  // ---------------- phase 2: grid reduction, one warp per (slot, mode)
+  // ---------------- phase 2: per (component, slot, mode) sums, one warp per item
   {
-    const int items = nslots * ld;
+    const int items = a.n_comp * nslots * ld;
     for (int it = blockIdx.x * nwarps + warp; it < items; it += gridDim.x * nwarps) {
+      const int comp = it / (nslots * ld), e = it % (nslots * ld);
       double re = 0, im = 0;
-      for (int b = lane32; b < (int)gridDim.x; b += 32) {
-        double2 p = a.part[((int64_t)b * (a.m_r + 2)) * ld + it];
+      for (int ch = a.comp_chunk[comp] + lane32; ch < a.comp_chunk[comp + 1]; ch += 32) {
+        const double2 p = a.part[(int64_t)ch * pstride + e];
         re += p.x; im += p.y;
       }
       for (int o = 16; o > 0; o >>= 1) {
         re += __shfl_xor_sync(0xffffffffu, re, o);
         im += __shfl_xor_sync(0xffffffffu, im, o);
       }
-      if (lane32 == 0) a.h[it] = make_double2(re, im);
+      if (lane32 == 0) a.h[(int64_t)comp * pstride + e] = make_double2(re, im);
     }
   }
   if (!grid_sync(a.gs, gridDim.x)) return;
 
-  // ---------------- phase 3: w' = w - sum_i h_i v_i -> V_{j+1}; ||w'||^2 partials
-  T *hs = acc;                       // [nvec][ld] complex
+  // ---------------- phase 3: w' = w - sum_i h_i v_i -> V_{j+1}; chunk partials of ||w'||^2
+  T *hs = acc;                       // [nvec][ld] complex, for the current chunk's component
   T *nacc = acc + nvec * sstride;    // [nwarps][ld] (re only used)
-  for (int e = threadIdx.x; e < nvec * ld; e += blockDim.x) {
-    const int k = e % ld;
-    double2 hv = a.state[k] ? a.h[e] : make_double2(0.0, 0.0);
-    hs[2 * e] = (T)hv.x;
-    hs[2 * e + 1] = (T)hv.y;
-  }
-  for (int e = threadIdx.x; e < nwarps * ld; e += blockDim.x) nacc[2 * e] = T(0);
-  __syncthreads();
-  bool act[MPL];
-#pragma unroll
-  for (int i = 0; i < MPL; ++i) act[i] = a.state[koff + i] != 0;
   C *Vn = a.V + (int64_t)(j + 1) * a.vstride;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    CV<T, MPL> wv[ARN_RPT];
-    int64_t rr[ARN_RPT];
-#pragma unroll
-    for (int q = 0; q < ARN_RPT; ++q) {
-      rr[q] = tile * TR + roff + (int64_t)q * RPB;
-      if (rr[q] < a.rows) ldv<T, MPL>(wv[q], a.w + rr[q] * ld + koff); else wv[q].zero();
+  for (int64_t ch = blockIdx.x; ch < a.n_chunk; ch += gridDim.x) {
+    const int comp = a.chunk_comp[ch];
+    if (!a.comp_active[comp]) continue;  // block-uniform
+    for (int e = threadIdx.x; e < nvec * ld; e += blockDim.x) {
+      const int k = e % ld;
+      const double2 hv = a.state[comp * ld + k] ? a.h[(int64_t)comp * pstride + e] : make_double2(0.0, 0.0);
+      hs[2 * e] = (T)hv.x;
+      hs[2 * e + 1] = (T)hv.y;
     }
-    for (int vi = 0; vi < nvec; vi += 2) {
-      const bool two = vi + 1 < nvec;
-      const C *V0 = a.V + (int64_t)vi * a.vstride;
-      const C *V1 = a.V + (int64_t)(two ? vi + 1 : vi) * a.vstride;
-      T hr0[MPL], hi0[MPL], hr1[MPL], hi1[MPL];
+    for (int e = threadIdx.x; e < nwarps * ld; e += blockDim.x) nacc[2 * e] = T(0);
+    __syncthreads();
+    bool act[MPL];
 #pragma unroll
-      for (int i = 0; i < MPL; ++i) {
-        hr0[i] = hs[vi * sstride + 2 * (koff + i)];
-        hi0[i] = hs[vi * sstride + 2 * (koff + i) + 1];
-        hr1[i] = two ? hs[(vi + 1) * sstride + 2 * (koff + i)] : T(0);
-        hi1[i] = two ? hs[(vi + 1) * sstride + 2 * (koff + i) + 1] : T(0);
-      }
-      CV<T, MPL> v0[ARN_RPT], v1[ARN_RPT];
+    for (int i = 0; i < MPL; ++i) act[i] = a.state[comp * ld + koff + i] != 0;
+    const int64_t r0 = a.chunk_row0[ch], r1 = r0 + a.chunk_rows[ch];
+    for (int64_t tb = r0; tb < r1; tb += TR) {
+      CV<T, MPL> wv[ARN_RPT];
+      int64_t rr[ARN_RPT];
 #pragma unroll
       for (int q = 0; q < ARN_RPT; ++q) {
-        if (rr[q] < a.rows) {
-          ldv<T, MPL>(v0[q], V0 + rr[q] * ld + koff);
-          if (two) ldv<T, MPL>(v1[q], V1 + rr[q] * ld + koff); else v1[q].zero();
-        } else {
-          v0[q].zero();
-          v1[q].zero();
-        }
+        rr[q] = tb + roff + (int64_t)q * RPB;
+        if (rr[q] < r1) ldv<T, MPL>(wv[q], a.w + rr[q] * ld + koff); else wv[q].zero();
       }
-#pragma unroll
-      for (int q = 0; q < ARN_RPT; ++q)
-#pragma unroll
-        for (int i = 0; i < MPL; ++i) {  // w -= h0 v0 + h1 v1
-          wv[q].re[i] -= hr0[i] * v0[q].re[i] - hi0[i] * v0[q].im[i] + hr1[i] * v1[q].re[i] - hi1[i] * v1[q].im[i];
-          wv[q].im[i] -= hr0[i] * v0[q].im[i] + hi0[i] * v0[q].re[i] + hr1[i] * v1[q].im[i] + hi1[i] * v1[q].re[i];
-        }
-    }
-    T s[MPL];
-#pragma unroll
-    for (int i = 0; i < MPL; ++i) s[i] = 0;
-#pragma unroll
-    for (int q = 0; q < ARN_RPT; ++q) {
-      if (rr[q] < a.rows) {
+      for (int vi = 0; vi < nvec; vi += 2) {
+        const bool two = vi + 1 < nvec;
+        const C *V0 = a.V + (int64_t)vi * a.vstride;
+        const C *V1 = a.V + (int64_t)(two ? vi + 1 : vi) * a.vstride;
+        T hr0[MPL], hi0[MPL], hr1[MPL], hi1[MPL];
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
-          if (!act[i]) { wv[q].re[i] = 0; wv[q].im[i] = 0; }
-          s[i] += wv[q].re[i] * wv[q].re[i] + wv[q].im[i] * wv[q].im[i];
+          hr0[i] = hs[vi * sstride + 2 * (koff + i)];
+          hi0[i] = hs[vi * sstride + 2 * (koff + i) + 1];
+          hr1[i] = two ? hs[(vi + 1) * sstride + 2 * (koff + i)] : T(0);
+          hi1[i] = two ? hs[(vi + 1) * sstride + 2 * (koff + i) + 1] : T(0);
         }
-        stv<T, MPL>(Vn + rr[q] * ld + koff, wv[q]);
+        CV<T, MPL> v0[ARN_RPT], v1[ARN_RPT];
+#pragma unroll
+        for (int q = 0; q < ARN_RPT; ++q) {
+          if (rr[q] < r1) {
+            ldv<T, MPL>(v0[q], V0 + rr[q] * ld + koff);
+            if (two) ldv<T, MPL>(v1[q], V1 + rr[q] * ld + koff); else v1[q].zero();
+          } else {
+            v0[q].zero();
+            v1[q].zero();
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < ARN_RPT; ++q)
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) {  // w -= h0 v0 + h1 v1
+            wv[q].re[i] -= hr0[i] * v0[q].re[i] - hi0[i] * v0[q].im[i] + hr1[i] * v1[q].re[i] - hi1[i] * v1[q].im[i];
+            wv[q].im[i] -= hr0[i] * v0[q].im[i] + hi0[i] * v0[q].re[i] + hr1[i] * v1[q].im[i] + hi1[i] * v1[q].re[i];
+          }
       }
+      T s[MPL];
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) s[i] = 0;
+#pragma unroll
+      for (int q = 0; q < ARN_RPT; ++q) {
+        if (rr[q] < r1) {
+#pragma unroll
+          for (int i = 0; i < MPL; ++i) {
+            if (!act[i]) { wv[q].re[i] = 0; wv[q].im[i] = 0; }
+            s[i] += wv[q].re[i] * wv[q].re[i] + wv[q].im[i] * wv[q].im[i];
+          }
+          stv<T, MPL>(Vn + rr[q] * ld + koff, wv[q]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) s[i] = warp_rows_sum<T, TPR>(s[i]);
+      if (row_leader)
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) nacc[2 * (warp * ld + koff + i)] += s[i];
     }
-#pragma unroll
-    for (int i = 0; i < MPL; ++i) s[i] = warp_rows_sum<T, TPR>(s[i]);
-    if (row_leader)
-#pragma unroll
-      for (int i = 0; i < MPL; ++i) nacc[2 * (warp * ld + koff + i)] += s[i];
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < ld; k += blockDim.x) {
-    double s = 0;
-    for (int w = 0; w < nwarps; ++w) s += (double)nacc[2 * (w * ld + k)];
-    a.part[((int64_t)blockIdx.x * (a.m_r + 2)) * ld + k] = make_double2(s, 0.0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+      double sm = 0;
+      for (int w = 0; w < nwarps; ++w) sm += (double)nacc[2 * (w * ld + k)];
+      a.part[ch * pstride + k] = make_double2(sm, 0.0);
+    }
+    __syncthreads();
   }
   if (!grid_sync(a.gs, gridDim.x)) return;
 
-  // ---------------- phase 4 (block 0): norms, Hessenberg column, Givens, estimate
-  if (blockIdx.x != 0) return;
-  double *sig2 = reinterpret_cast<double *>(smem_raw);  // [ld]
-  __syncthreads();
-  for (int k = warp; k < ld; k += nwarps) {
-    double s = 0;
-    for (int b = lane32; b < (int)gridDim.x; b += 32) s += a.part[((int64_t)b * (a.m_r + 2)) * ld + k].x;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane32 == 0) sig2[k] = s;
-  }
-  __syncthreads();
-  __shared__ int s_active;
-  if (threadIdx.x == 0) s_active = 0;
-  __syncthreads();
-  for (int k = threadIdx.x; k < ld; k += blockDim.x) {
-    if (!a.state[k]) { a.rscale[k] = 0.0; continue; }
+  // ---------------- phase 4: one warp per system: norm, Hessenberg column, Givens, estimate
+  const int S = a.n_comp * ld;
+  for (int sys = blockIdx.x * nwarps + warp; sys < S; sys += gridDim.x * nwarps) {
+    const int comp = sys / ld, k = sys % ld;
+    double s2 = 0;
+    for (int ch = a.comp_chunk[comp] + lane32; ch < a.comp_chunk[comp + 1]; ch += 32) s2 += a.part[(int64_t)ch * pstride + k].x;
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if (lane32 != 0) continue;
+    if (!a.state[sys]) { a.rscale[sys] = 0.0; continue; }
     const int m_r = a.m_r;
-    double2 *Hk = a.H + (int64_t)k * (m_r + 1) * m_r;
-    double *csk = a.cs + (int64_t)k * m_r;
-    double2 *snk = a.sn + (int64_t)k * m_r;
-    double2 *gk = a.gv + (int64_t)k * (m_r + 1);
-    const double sigma = sqrt(fmax(sig2[k], 0.0));
-    const double wn = sqrt(fmax(a.h[(j + 1) * ld + k].x, 0.0));
-    double2 col[2];
+    const double2 *hc = a.h + (int64_t)comp * pstride;  // column: hc[i * ld + k]
+    double2 *Hk = a.H + (int64_t)sys * (m_r + 1) * m_r;
+    double *csk = a.cs + (int64_t)sys * m_r;
+    double2 *snk = a.sn + (int64_t)sys * m_r;
+    double2 *gk = a.gv + (int64_t)sys * (m_r + 1);
+    const double sigma = sqrt(fmax(s2, 0.0));
+    const double wn = sqrt(fmax(hc[(j + 1) * ld + k].x, 0.0));
     // apply the previous rotations to the new column, top-down
-    double2 hprev = a.h[0 * ld + k];
+    double2 hprev = hc[0 * ld + k];
     for (int i = 0; i < j; ++i) {
-      const double2 hnext = a.h[(i + 1) * ld + k];
+      const double2 hnext = hc[(i + 1) * ld + k];
       const double c = csk[i];
       const double2 s = snk[i];
       // t = c h_i + s h_{i+1};  h_{i+1}' = -conj(s) h_i + c h_{i+1}
@@ -289,10 +307,8 @@ __global__ void __launch_bounds__(256, 3) k_arnoldi(const ArnArgs<T> a, const in
       Hk[(int64_t)i * m_r + j] = t;
       hprev = u;
     }
-    col[0] = hprev;
-    col[1] = make_double2(sigma, 0.0);
-    // new rotation zeroing col[1]
-    const double aa = sqrt(col[0].x * col[0].x + col[0].y * col[0].y);
+    // new rotation zeroing sigma below the diagonal
+    const double aa = sqrt(hprev.x * hprev.x + hprev.y * hprev.y);
     const double r = sqrt(aa * aa + sigma * sigma);
     double c;
     double2 s;
@@ -302,37 +318,35 @@ __global__ void __launch_bounds__(256, 3) k_arnoldi(const ArnArgs<T> a, const in
       c = 0.0; s = make_double2(1.0, 0.0);  // conj(b)/|b| with b = sigma > 0
     } else {
       c = aa / r;
-      const double2 ph = make_double2(col[0].x / aa, col[0].y / aa);  // a/|a|
-      s = make_double2(ph.x * sigma / r, ph.y * sigma / r);           // (a/|a|) conj(b)/r, b real
+      const double2 ph = make_double2(hprev.x / aa, hprev.y / aa);  // a/|a|
+      s = make_double2(ph.x * sigma / r, ph.y * sigma / r);         // (a/|a|) conj(b)/r, b real
     }
     csk[j] = c;
     snk[j] = s;
-    const double2 rr = (aa == 0.0) ? make_double2(r, 0.0) : make_double2(col[0].x * r / aa, col[0].y * r / aa);
-    Hk[(int64_t)j * m_r + j] = rr;
+    Hk[(int64_t)j * m_r + j] = (aa == 0.0) ? make_double2(r, 0.0) : make_double2(hprev.x * r / aa, hprev.y * r / aa);
     const double2 gj = gk[j];
     gk[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
     gk[j] = make_double2(c * gj.x, c * gj.y);
     const double e = sqrt(gk[j + 1].x * gk[j + 1].x + gk[j + 1].y * gk[j + 1].y);
-    a.est[k] = e;
-    a.kdim[k] = j + 1;
+    a.est[sys] = e;
+    a.kdim[sys] = j + 1;
     const bool broke = !(sigma > a.breakdown * wn);
     const bool nonfinite = !isfinite(e) || !isfinite(sigma);
-    if (nonfinite) { a.kdim[k] = j; }
-    if (e <= a.target[k] || broke || nonfinite || j + 1 >= m_r) {
-      a.state[k] = 0;
-      a.rscale[k] = 0.0;
+    if (nonfinite) a.kdim[sys] = j;
+    if (e <= a.target[sys] || broke || nonfinite || j + 1 >= m_r) {
+      a.state[sys] = 0;
+      a.rscale[sys] = 0.0;
     } else {
-      a.rscale[k] = 1.0 / sigma;
-      atomicAdd(&s_active, 1);
+      a.rscale[sys] = 1.0 / sigma;
+      atomicAdd(a.n_active, 1);
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *a.n_active = s_active;
 }
 
 // Back substitution R y = g for every mode (FP64); y[i][k], zero past kdim.
 __global__ void k_lsq(const double2 *__restrict__ H, const double2 *__restrict__ gv, const int *__restrict__ kdim,
                       int ld, int m_r, double2 *__restrict__ y) {
+  // ld here is the number of systems S (y[i][s])
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ld) return;
   const double2 *Hk = H + (int64_t)k * (m_r + 1) * m_r;
@@ -357,13 +371,15 @@ __global__ void k_lsq(const double2 *__restrict__ H, const double2 *__restrict__
 // u = sum_{i<nv} y_i v_i (per mode)
 template <typename T>
 __global__ void k_combine(const typename cpx<T>::t *__restrict__ V, int64_t vstride, const double2 *__restrict__ y,
-                          int nv, int ld, int64_t total, typename cpx<T>::t *__restrict__ u) {
+                          int nv, int ld, int S, const int32_t *__restrict__ dof_comp, const int *__restrict__ upd,
+                          int64_t total, typename cpx<T>::t *__restrict__ u) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= total) return;
-  const int k = (int)(f % ld);
+  const int sys = (dof_comp ? dof_comp[f / ld] * ld : 0) + (int)(f % ld);
+  if (!upd[sys]) return;  // system not updated in this cycle
   T re = 0, im = 0;
   for (int i = 0; i < nv; ++i) {
-    const double2 yy = y[(int64_t)i * ld + k];
+    const double2 yy = y[(int64_t)i * S + sys];
     const auto v = V[(int64_t)i * vstride + f];
     re += (T)yy.x * v.x - (T)yy.y * v.y;
     im += (T)yy.x * v.y + (T)yy.y * v.x;
@@ -372,11 +388,11 @@ __global__ void k_combine(const typename cpx<T>::t *__restrict__ V, int64_t vstr
 }
 
 template <typename T>
-__global__ void k_add_to_x(const typename cpx<T>::t *__restrict__ z, const int *__restrict__ upd, int ld, int64_t total,
-                           double2 *__restrict__ x) {
+__global__ void k_add_to_x(const typename cpx<T>::t *__restrict__ z, const int *__restrict__ upd, int ld,
+                           const int32_t *__restrict__ dof_comp, int64_t total, double2 *__restrict__ x) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= total) return;
-  if (!upd[f % ld]) return;
+  if (!upd[(dof_comp ? dof_comp[f / ld] * ld : 0) + f % ld]) return;
   const auto d = z[f];
   double2 v = x[f];
   v.x += (double)d.x;
@@ -387,10 +403,11 @@ __global__ void k_add_to_x(const typename cpx<T>::t *__restrict__ z, const int *
 // x = b on Dirichlet rows (= g), 0 elsewhere (only the modes with reset[k] != 0
 // when `reset` is given).
 __global__ void k_init_x(const double2 *__restrict__ b, const uint8_t *__restrict__ dirm, int64_t N, int dim,
-                         int64_t total, int ld, double2 *__restrict__ x, const int *__restrict__ reset) {
+                         int64_t total, int ld, double2 *__restrict__ x, const int *__restrict__ reset,
+                         const int32_t *__restrict__ dof_comp) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= total) return;
-  if (reset && !reset[f % ld]) return;
+  if (reset && !reset[(dof_comp ? dof_comp[f / ld] * ld : 0) + f % ld]) return;
   const int64_t dof = f / ld;
   const bool dir = dof < N * dim && dirm[dof / dim];
   x[f] = dir ? b[f] : make_double2(0.0, 0.0);
@@ -452,6 +469,7 @@ template <typename T>
 static int solve_mesh_t(Ctx &c, Mesh &m) {
   using C = typename cpx<T>::t;
   const int ld = m.ld, m_r = std::max(1, std::min(64, c.opts.restart));
+  const int S = m.n_sys(), nm = m.m;
   const int64_t total = m.n_dof * ld;
   Work<T> wk;
   wk.s = c.stream;
@@ -462,58 +480,63 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   int grid, block;
   size_t smem;
   arnoldi_config<T>(c, ld, m_r, grid, block, smem);
-  wk.part = wk.template get<double2>((size_t)grid * (m_r + 2) * ld);
-  wk.h = wk.template get<double2>((size_t)(m_r + 2) * ld);
-  wk.H = wk.template get<double2>((size_t)ld * (m_r + 1) * m_r);
-  wk.sn = wk.template get<double2>((size_t)ld * m_r);
-  wk.gv = wk.template get<double2>((size_t)ld * (m_r + 1));
-  wk.y = wk.template get<double2>((size_t)ld * m_r);
-  wk.cs = wk.template get<double>((size_t)ld * m_r);
-  wk.target = wk.template get<double>(ld);
-  wk.rscale = wk.template get<double>(ld);
-  wk.est = wk.template get<double>(ld);
-  wk.norm2 = wk.template get<double>(ld);
-  wk.state = wk.template get<int>(ld);
-  wk.kdim = wk.template get<int>(ld);
-  wk.upd = wk.template get<int>(ld);
+  wk.part = wk.template get<double2>((size_t)m.n_chunk * (m_r + 2) * ld);
+  wk.h = wk.template get<double2>((size_t)m.n_comp * (m_r + 2) * ld);
+  wk.H = wk.template get<double2>((size_t)S * (m_r + 1) * m_r);
+  wk.sn = wk.template get<double2>((size_t)S * m_r);
+  wk.gv = wk.template get<double2>((size_t)S * (m_r + 1));
+  wk.y = wk.template get<double2>((size_t)S * m_r);
+  wk.cs = wk.template get<double>((size_t)S * m_r);
+  wk.target = wk.template get<double>(S);
+  wk.rscale = wk.template get<double>(S);
+  wk.est = wk.template get<double>(S);
+  wk.norm2 = wk.template get<double>(S);
+  wk.state = wk.template get<int>(S);
+  wk.kdim = wk.template get<int>(S);
+  wk.upd = wk.template get<int>(S);
   wk.n_active = wk.template get<int>(1);
 
   ArnArgs<T> aa{};
-  aa.rows = m.n_dof; aa.ld = ld; aa.m_r = m_r; aa.V = wk.V; aa.w = wk.W; aa.vstride = total;
+  aa.rows = m.n_dof; aa.ld = ld; aa.m_r = m_r; aa.n_comp = m.n_comp; aa.V = wk.V; aa.w = wk.W; aa.vstride = total;
+  aa.n_chunk = m.n_chunk; aa.chunk_row0 = m.chunk_row0; aa.chunk_rows = m.chunk_rows; aa.chunk_comp = m.chunk_comp;
+  aa.comp_chunk = m.comp_chunk;
+  aa.comp_active = m.comp_active;
   aa.part = wk.part; aa.h = wk.h; aa.H = wk.H; aa.cs = wk.cs; aa.sn = wk.sn; aa.gv = wk.gv;
   aa.state = wk.state; aa.kdim = wk.kdim; aa.target = wk.target; aa.rscale = wk.rscale; aa.est = wk.est;
   aa.n_active = wk.n_active; aa.gs = c.gsync;
   aa.breakdown = sizeof(T) == 4 ? 1e-6 : 1e-13;
 
+  // systems s = comp * ld + k; reports are per (comp, mode): comp * m + k
   const double tol = c.opts.tol;
-  m.rep.assign(m.m, scvs_mode_report{SCVS_MAX_ITER, 0, 0, 0, 0.0});
-  std::vector<int> done(ld, 0);
-  std::vector<double> rel(ld, 0.0), best(ld, 1e300);
-  std::vector<int> since_best(ld, 0);
-  for (int k = m.m; k < ld; ++k) done[k] = 1;  // padding columns
-  for (int k = 0; k < m.m; ++k) {
-    if (!std::isfinite(m.bnorm[k])) {  // non-finite boundary data: this mode only
-      done[k] = 1;
-      m.rep[k].status = SCVS_NON_FINITE;
-      m.rep[k].rel_res = m.bnorm[k];
-    } else if (m.bnorm[k] == 0.0) {  // zero data: x = 0 (the Dirichlet lift is zero too) is exact
-      done[k] = 1;
-      m.rep[k].status = SCVS_CONVERGED;
+  m.rep.assign((size_t)m.n_comp * nm, scvs_mode_report{SCVS_MAX_ITER, 0, 0, 0, 0.0});
+  auto rep = [&](int s) -> scvs_mode_report & { return m.rep[(size_t)(s / ld) * nm + (s % ld)]; };
+  std::vector<int> done(S, 0);
+  std::vector<double> rel(S, 0.0), best(S, 1e300);
+  std::vector<int> since_best(S, 0);
+  for (int s = 0; s < S; ++s) {
+    if (s % ld >= nm) { done[s] = 1; continue; }  // padding columns
+    if (!std::isfinite(m.bnorm[s])) {  // non-finite boundary data: this system only
+      done[s] = 1;
+      rep(s).status = SCVS_NON_FINITE;
+      rep(s).rel_res = m.bnorm[s];
+    } else if (m.bnorm[s] == 0.0) {  // zero data: x = 0 (the Dirichlet lift is zero too) is exact
+      done[s] = 1;
+      rep(s).status = SCVS_CONVERGED;
     }
   }
 
   const int64_t eb = ceil_div(total, 256);
-  bool guess_on = c.opts.guess == SCVS_GUESS_MLP && guess_initial(c, m);
+  bool guess_on = c.opts.guess == SCVS_GUESS_MLP && m.n_comp == 1 && guess_initial(c, m);
   if (!guess_on) {
-    k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, nullptr);
+    k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, nullptr, m.dof_comp);
     count_launch(c);
   }
-  for (int k = 0; k < m.m; ++k) m.rep[k].guess_used = guess_on ? 1 : 0;
+  for (auto &r : m.rep) r.guess_used = guess_on ? 1 : 0;
 
   int *h_active = nullptr;
   SCVS_CUDA(cudaMallocHost(&h_active, sizeof(int)));
-  std::vector<double> n2(ld), hbuf(ld);
-  std::vector<int> state(ld), kd(ld);
+  std::vector<double> n2(S);
+  std::vector<int> state(S), kd(S);
   const int max_cycles = std::max(1, c.opts.max_cycles);
   for (int cyc = 0; cyc <= max_cycles; ++cyc) {
     // 1. FP64 true residual; r goes to V_0 (unnormalized)
@@ -521,67 +544,71 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       residual_fp64(c, m, wk.V, nullptr, wk.norm2);
     else
       residual_fp64(c, m, nullptr, wk.V, wk.norm2);
-    SCVS_CUDA(cudaMemcpyAsync(n2.data(), wk.norm2, ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    SCVS_CUDA(cudaMemcpyAsync(n2.data(), wk.norm2, S * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     SCVS_CUDA(cudaStreamSynchronize(c.stream));
     if (cyc == 0 && guess_on) {
       // a guess no better than zero is dropped for that mode (zero-start fallback)
-      std::vector<int> reset(ld, 0);
+      std::vector<int> reset(S, 0);
       int n_reset = 0;
-      for (int k = 0; k < m.m; ++k) {
-        if (done[k]) continue;
-        const double r = std::sqrt(std::max(n2[k], 0.0));
-        if (!(r < m.bnorm[k])) { reset[k] = 1; ++n_reset; m.rep[k].guess_used = 0; }
+      for (int s = 0; s < S; ++s) {
+        if (done[s]) continue;
+        const double r = std::sqrt(std::max(n2[s], 0.0));
+        if (!(r < m.bnorm[s])) { reset[s] = 1; ++n_reset; rep(s).guess_used = 0; }
       }
       guess_on = false;
       if (n_reset > 0) {
-        SCVS_CUDA(cudaMemcpyAsync(wk.upd, reset.data(), ld * sizeof(int), cudaMemcpyHostToDevice, c.stream));
-        k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, wk.upd);
+        SCVS_CUDA(cudaMemcpyAsync(wk.upd, reset.data(), S * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+        k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, wk.upd, m.dof_comp);
         count_launch(c);
         --cyc;
         continue;
       }
     }
     int n_act = 0;
-    for (int k = 0; k < m.m; ++k) {
-      if (done[k]) continue;
-      const double r = std::sqrt(std::max(n2[k], 0.0));
-      rel[k] = r / m.bnorm[k];
-      m.rep[k].rel_res = rel[k];
-      if (!std::isfinite(rel[k])) { done[k] = 1; m.rep[k].status = SCVS_NON_FINITE; continue; }
-      if (rel[k] <= tol) { done[k] = 1; m.rep[k].status = SCVS_CONVERGED; continue; }
+    for (int s = 0; s < S; ++s) {
+      if (done[s]) continue;
+      const double r = std::sqrt(std::max(n2[s], 0.0));
+      rel[s] = r / m.bnorm[s];
+      rep(s).rel_res = rel[s];
+      if (!std::isfinite(rel[s])) { done[s] = 1; rep(s).status = SCVS_NON_FINITE; continue; }
+      if (rel[s] <= tol) { done[s] = 1; rep(s).status = SCVS_CONVERGED; continue; }
       // stagnation: 12 cycles without a 1% gain on the best residual so far
-      if (rel[k] < 0.99 * best[k]) { best[k] = rel[k]; since_best[k] = 0; }
-      else if (++since_best[k] >= 12) { done[k] = 1; m.rep[k].status = SCVS_STAGNATED; continue; }
-      if (cyc == max_cycles) { done[k] = 1; m.rep[k].status = SCVS_MAX_ITER; continue; }
-      done[k] = 0;
+      if (rel[s] < 0.99 * best[s]) { best[s] = rel[s]; since_best[s] = 0; }
+      else if (++since_best[s] >= 12) { done[s] = 1; rep(s).status = SCVS_STAGNATED; continue; }
+      if (cyc == max_cycles) { done[s] = 1; rep(s).status = SCVS_MAX_ITER; continue; }
       ++n_act;
     }
     if (n_act == 0) break;
-    // 2. cycle set-up: active modes, targets, first scale, Hessenberg reset
-    std::vector<double> tgt(ld, 0.0), rs(ld, 0.0);
-    std::vector<double2> g0((size_t)ld * (m_r + 1), make_double2(0, 0));
-    for (int k = 0; k < ld; ++k) {
-      state[k] = done[k] ? 0 : 1;
-      if (!state[k]) continue;
-      const double beta = std::sqrt(n2[k]);
-      rs[k] = 1.0 / beta;
-      tgt[k] = 0.5 * tol * m.bnorm[k];
-      g0[(size_t)k * (m_r + 1)] = make_double2(beta, 0.0);
+    if (m.n_comp > 1) {  // components whose systems are all done drop out of every kernel
+      std::vector<uint8_t> ca(m.n_comp, 0);
+      for (int s = 0; s < S; ++s)
+        if (!done[s]) ca[s / ld] = 1;
+      SCVS_CUDA(cudaMemcpyAsync(m.comp_active, ca.data(), m.n_comp, cudaMemcpyHostToDevice, c.stream));
     }
-    SCVS_CUDA(cudaMemcpyAsync(wk.state, state.data(), ld * sizeof(int), cudaMemcpyHostToDevice, c.stream));
-    SCVS_CUDA(cudaMemcpyAsync(wk.upd, state.data(), ld * sizeof(int), cudaMemcpyHostToDevice, c.stream));
-    SCVS_CUDA(cudaMemcpyAsync(wk.target, tgt.data(), ld * sizeof(double), cudaMemcpyHostToDevice, c.stream));
-    SCVS_CUDA(cudaMemcpyAsync(wk.rscale, rs.data(), ld * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    // 2. cycle set-up: active systems, targets, first scale, Hessenberg reset
+    std::vector<double> tgt(S, 0.0), rs(S, 0.0);
+    std::vector<double2> g0((size_t)S * (m_r + 1), make_double2(0, 0));
+    for (int s = 0; s < S; ++s) {
+      state[s] = done[s] ? 0 : 1;
+      if (!state[s]) continue;
+      const double beta = std::sqrt(n2[s]);
+      rs[s] = 1.0 / beta;
+      tgt[s] = 0.5 * tol * m.bnorm[s];
+      g0[(size_t)s * (m_r + 1)] = make_double2(beta, 0.0);
+    }
+    SCVS_CUDA(cudaMemcpyAsync(wk.state, state.data(), S * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+    SCVS_CUDA(cudaMemcpyAsync(wk.upd, state.data(), S * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+    SCVS_CUDA(cudaMemcpyAsync(wk.target, tgt.data(), S * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    SCVS_CUDA(cudaMemcpyAsync(wk.rscale, rs.data(), S * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     SCVS_CUDA(cudaMemcpyAsync(wk.gv, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
-    SCVS_CUDA(cudaMemsetAsync(wk.kdim, 0, ld * sizeof(int), c.stream));
+    SCVS_CUDA(cudaMemsetAsync(wk.kdim, 0, S * sizeof(int), c.stream));
     // 3. Arnoldi steps
-    int steps = 0;
     for (int j = 0; j < m_r; ++j) {
       C *Vj = wk.V + (int64_t)j * total;
       apply_precond<T>(c, m, Vj, wk.Z, wk.S, wk.rscale);  // normalizes v_j in place
       apply_saddle<T>(c, m, wk.Z, wk.W);
+      SCVS_CUDA(cudaMemsetAsync(wk.n_active, 0, sizeof(int), c.stream));
       launch_arnoldi<T>(c, aa, j, grid, block, smem);
-      ++steps;
       SCVS_CUDA(cudaMemcpyAsync(h_active, wk.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
       SCVS_CUDA(cudaStreamSynchronize(c.stream));
       if (*h_active == 0) break;
@@ -600,33 +627,34 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       }
     }
     // 4. least squares, correction, update
-    k_lsq<<<ceil_div(ld, 64), 64, 0, c.stream>>>(wk.H, wk.gv, wk.kdim, ld, m_r, wk.y);
+    k_lsq<<<ceil_div(S, 64), 64, 0, c.stream>>>(wk.H, wk.gv, wk.kdim, S, m_r, wk.y);
     count_launch(c);
-    SCVS_CUDA(cudaMemcpyAsync(kd.data(), wk.kdim, ld * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    SCVS_CUDA(cudaMemcpyAsync(kd.data(), wk.kdim, S * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     SCVS_CUDA(cudaStreamSynchronize(c.stream));
     int nvmax = 0;
-    for (int k = 0; k < m.m; ++k) {
-      if (done[k]) continue;
-      nvmax = std::max(nvmax, kd[k]);
-      m.rep[k].iterations += kd[k];
-      m.rep[k].cycles += 1;
+    for (int s = 0; s < S; ++s) {
+      if (done[s]) continue;
+      nvmax = std::max(nvmax, kd[s]);
+      rep(s).iterations += kd[s];
+      rep(s).cycles += 1;
     }
     if (nvmax > 0) {
       {
         KScope ks(c, KC_VECTOR, (double)(nvmax + 1) * total * 2 * sizeof(T));
-        k_combine<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.V, total, wk.y, nvmax, ld, total, wk.W);
+        k_combine<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.V, total, wk.y, nvmax, ld, S, m.dof_comp, wk.upd, total,
+                                                         wk.W);
         count_launch(c);
       }
       apply_precond<T>(c, m, wk.W, wk.Z, wk.S, nullptr);
       {
         KScope ks(c, KC_VECTOR, (double)total * (32 + 2 * sizeof(T)));
-        k_add_to_x<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.Z, wk.upd, ld, total, m.x);
+        k_add_to_x<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.Z, wk.upd, ld, m.dof_comp, total, m.x);
         count_launch(c);
       }
     }
-    (void)steps;
   }
   cudaFreeHost(h_active);
+  if (m.n_comp > 1) SCVS_CUDA(cudaMemsetAsync(m.comp_active, 1, m.n_comp, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
   return SCVS_OK;
 }

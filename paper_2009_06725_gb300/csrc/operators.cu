@@ -17,6 +17,7 @@
 //    or their diagonal versions.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include "scvs_internal.h"
 #include "vecops.cuh"
 
@@ -34,7 +35,14 @@ template <typename T> struct SaddleArgs {
   const uint8_t *dirmask;  // null: no identity rows
   const double *omega;
   double rho, mu;
+  const int32_t *dof_comp;      // null: one component
+  const uint8_t *comp_active;   // rows of inactive components are skipped
 };
+
+// true if the row's component has no active system (multi-component meshes)
+__device__ __forceinline__ bool row_idle(const int32_t *dof_comp, const uint8_t *comp_active, int64_t dof) {
+  return dof_comp && !comp_active[dof_comp[dof]];
+}
 
 template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
@@ -52,6 +60,7 @@ k_saddle(const SaddleArgs<T> a, const typename cpx<T>::t *__restrict__ x, typena
   const int64_t rows = a.N + a.P;
   const C *__restrict__ xp_base = x + (int64_t)DIM * a.N * ld + koff;
   for (int64_t row = (int64_t)blockIdx.x * gpb + group; row < rows; row += (int64_t)gridDim.x * gpb) {
+    if (row_idle(a.dof_comp, a.comp_active, row < a.N ? row * DIM : (int64_t)DIM * a.N + (row - a.N))) continue;
     if (row < a.N) {
       const int64_t A = row;
       if (a.dirmask && a.dirmask[A]) {
@@ -154,14 +163,15 @@ SaddleArgs<T> saddle_args(const Ctx &c, const Mesh &m, bool masked);
 template <>
 SaddleArgs<float> saddle_args<float>(const Ctx &, const Mesh &m, bool) {
   return SaddleArgs<float>{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr, m.Ks_f, m.Ms_f, m.Dv_f,
-                           m.DTv_f, m.g_nnz, m.gt_nnz, m.dirmask, m.omega_d, m.rho, m.mu};
+                           m.DTv_f, m.g_nnz, m.gt_nnz, m.dirmask, m.omega_d, m.rho, m.mu, m.dof_comp, m.comp_active};
 }
 template <>
 SaddleArgs<double> saddle_args<double>(const Ctx &, const Mesh &m, bool masked) {
   return SaddleArgs<double>{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr,
                             masked ? m.Ks_m : m.Ks, masked ? m.Ms_m : m.Ms,
                             masked ? m.Dv_m : m.Dv, masked ? m.DTv_m : m.DTv,
-                            m.g_nnz, m.gt_nnz, masked ? m.dirmask : nullptr, m.omega_d, m.rho, m.mu};
+                            m.g_nnz, m.gt_nnz, masked ? m.dirmask : nullptr, m.omega_d, m.rho, m.mu,
+                            masked ? m.dof_comp : nullptr, m.comp_active};
 }
 
 // Algorithmic bytes of one all-modes SpMM: every index and value array once,
@@ -181,14 +191,26 @@ template <typename T>
 void launch_saddle(Ctx &c, const Mesh &m, const SaddleArgs<T> &a, const typename cpx<T>::t *x,
                    typename cpx<T>::t *y) {
   KScope ks(c, sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM64, saddle_bytes(m, sizeof(T)));
-  SCVS_DISPATCH_LD(T, m.ld, {
-    const int gpb = 256 / L;
-    const unsigned nb = row_blocks(c, m.N + m.P, gpb);
-    if (m.dim == 2)
-      k_saddle<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, x, y);
-    else
-      k_saddle<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, x, y);
-  });
+  if constexpr (sizeof(T) == 4) {
+    const int mpl = m.mpl_spmm ? m.mpl_spmm : default_mpl<T>(m.ld);
+    SCVS_DISPATCH_SHAPE(m.ld, mpl, {
+      const int gpb = 256 / L;
+      const unsigned nb = row_blocks(c, m.N + m.P, gpb);
+      if (m.dim == 2)
+        k_saddle<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, x, y);
+      else
+        k_saddle<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, x, y);
+    });
+  } else {
+    SCVS_DISPATCH_LD(T, m.ld, {
+      const int gpb = 256 / L;
+      const unsigned nb = row_blocks(c, m.N + m.P, gpb);
+      if (m.dim == 2)
+        k_saddle<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, x, y);
+      else
+        k_saddle<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, x, y);
+    });
+  }
   count_launch(c);
 }
 
@@ -224,54 +246,111 @@ __global__ void k_lift_finish(const double2 *__restrict__ y, const double2 *__re
   b[f] = dir ? gfull[f] : make_double2(-v.x, -v.y);
 }
 
-// Deterministic per-mode squared norms over the free rows: per-block partials,
-// then one thread per mode sums the partials in block order.
+// Deterministic per-system squared norms over the free rows: one block per
+// row chunk writes its partial per mode, then one thread per system sums the
+// partials of its component's chunks in chunk order.
 constexpr int NORM_T = 256;
-__global__ void k_norm_partials(const double2 *__restrict__ v, const uint8_t *__restrict__ dirm, int64_t N, int dim,
-                                int64_t n_dof, int ld, double *__restrict__ part) {
+__global__ void k_chunk_norm2(const double2 *__restrict__ v, const uint8_t *__restrict__ dirm, int64_t N, int dim,
+                              int ld, int64_t n_chunk, const int64_t *__restrict__ row0,
+                              const int32_t *__restrict__ rows, const int32_t *__restrict__ chunk_comp,
+                              const uint8_t *__restrict__ comp_active, double *__restrict__ part) {
   __shared__ double s[NORM_T];
-  const int64_t total = n_dof * ld;
-  const int64_t stride = (int64_t)gridDim.x * NORM_T;  // multiple of ld
-  double acc = 0.0;
-  for (int64_t f = blockIdx.x * (int64_t)NORM_T + threadIdx.x; f < total; f += stride) {
-    int64_t dof = f / ld;
-    bool dir = dof < N * dim && dirm[dof / dim];
-    if (!dir) { double2 z = v[f]; acc += z.x * z.x + z.y * z.y; }
-  }
-  s[threadIdx.x] = acc;
-  __syncthreads();
-  // threads with equal (tid % ld) hold the same mode
-  for (int w = NORM_T / 2; w >= ld; w >>= 1) {
-    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+  for (int64_t ch = blockIdx.x; ch < n_chunk; ch += gridDim.x) {
+    if (!comp_active[chunk_comp[ch]]) continue;  // block-uniform
+    const int64_t f0 = row0[ch] * ld, f1 = (row0[ch] + rows[ch]) * ld;
+    double acc = 0.0;
+    for (int64_t f = f0 + threadIdx.x; f < f1; f += NORM_T) {  // stride is a multiple of ld
+      const int64_t dof = f / ld;
+      const bool dir = dof < N * dim && dirm[dof / dim];
+      if (!dir) { const double2 z = v[f]; acc += z.x * z.x + z.y * z.y; }
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = NORM_T / 2; w >= ld; w >>= 1) {
+      if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+      __syncthreads();
+    }
+    // thread t < ld holds mode (f0 + t) % ld = t (f0 is a multiple of ld)
+    if (threadIdx.x < ld) part[ch * ld + threadIdx.x] = s[threadIdx.x];
     __syncthreads();
   }
-  if (threadIdx.x < ld) part[(int64_t)blockIdx.x * ld + threadIdx.x] = s[threadIdx.x];
 }
 
-__global__ void k_norm_finish(const double *__restrict__ part, int nblocks, int ld, double *__restrict__ out) {
-  int k = threadIdx.x;
-  if (k >= ld) return;
+__global__ void k_comp_reduce(const double *__restrict__ part, const int32_t *__restrict__ comp_chunk, int n_comp,
+                              int ld, double *__restrict__ out) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= n_comp * ld) return;
+  const int comp = sys / ld, k = sys % ld;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * ld + k];
-  out[k] = s;
+  for (int ch = comp_chunk[comp]; ch < comp_chunk[comp + 1]; ++ch) s += part[(int64_t)ch * ld + k];
+  out[sys] = s;
 }
 
-static void mode_norms2(Ctx &c, const Mesh &m, const double2 *v, double *part, double *out) {
+void norms2_sys(Ctx &c, const Mesh &m, const double2 *v, double *out) {
   KScope ks(c, KC_VECTOR, (double)m.n_dof * m.ld * 16);
-  const int nb = (int)std::min<int64_t>(std::max<int64_t>(1, (m.n_dof * m.ld) / (NORM_T * 8)), 4 * c.num_sms);
-  k_norm_partials<<<nb, NORM_T, 0, c.stream>>>(v, m.dirmask, m.N, m.dim, m.n_dof, m.ld, part);
-  k_norm_finish<<<1, 128, 0, c.stream>>>(part, nb, m.ld, out);
+  double *part = nullptr;
+  SCVS_CUDA(cudaMallocAsync(&part, (size_t)m.n_chunk * m.ld * sizeof(double), c.stream));
+  const unsigned nb = (unsigned)std::min<int64_t>(m.n_chunk, 8 * c.num_sms);
+  k_chunk_norm2<<<nb, NORM_T, 0, c.stream>>>(v, m.dirmask, m.N, m.dim, m.ld, m.n_chunk, m.chunk_row0, m.chunk_rows,
+                                             m.chunk_comp, m.comp_active, part);
+  k_comp_reduce<<<ceil_div(m.n_sys(), 128), 128, 0, c.stream>>>(part, m.comp_chunk, m.n_comp, m.ld, out);
   c.launches.n += 2;
+  SCVS_CUDA(cudaFreeAsync(part, c.stream));
+}
+
+// Row chunks of a mesh: dof rows split where the component changes and every
+// CHUNK_ROWS rows, then grouped by component (stable).  node_comp null: one
+// component.
+void set_chunks(Ctx &c, Mesh &m, const int32_t *node_comp, int n_comp) {
+  std::vector<int32_t> dc(m.n_dof, 0);
+  if (node_comp) {
+    for (int64_t nd = 0; nd < m.N; ++nd)
+      for (int q = 0; q < m.dim; ++q) dc[nd * m.dim + q] = node_comp[nd];
+    for (int64_t v = 0; v < m.P; ++v) dc[(int64_t)m.dim * m.N + v] = node_comp[v];
+  }
+  std::vector<std::vector<std::pair<int64_t, int32_t>>> per(n_comp);
+  int64_t r = 0;
+  while (r < m.n_dof) {
+    const int32_t cc = dc[r];
+    int64_t e = r + 1;
+    while (e < m.n_dof && e - r < CHUNK_ROWS && dc[e] == cc) ++e;
+    per[cc].push_back({r, (int32_t)(e - r)});
+    r = e;
+  }
+  std::vector<int64_t> r0;
+  std::vector<int32_t> rows, comp, cptr(n_comp + 1, 0);
+  for (int q = 0; q < n_comp; ++q) {
+    cptr[q] = (int32_t)r0.size();
+    for (auto &pr : per[q]) { r0.push_back(pr.first); rows.push_back(pr.second); comp.push_back(q); }
+  }
+  cptr[n_comp] = (int32_t)r0.size();
+  m.n_comp = n_comp;
+  m.n_chunk = (int64_t)r0.size();
+  m.chunk_row0 = m.arena.alloc<int64_t>(m.n_chunk);
+  m.chunk_rows = m.arena.alloc<int32_t>(m.n_chunk);
+  m.chunk_comp = m.arena.alloc<int32_t>(m.n_chunk);
+  m.comp_chunk = m.arena.alloc<int32_t>(n_comp + 1);
+  SCVS_CUDA(cudaMemcpy(m.chunk_row0, r0.data(), r0.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  SCVS_CUDA(cudaMemcpy(m.chunk_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  SCVS_CUDA(cudaMemcpy(m.chunk_comp, comp.data(), comp.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  SCVS_CUDA(cudaMemcpy(m.comp_chunk, cptr.data(), cptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  m.comp_active = m.arena.alloc<uint8_t>(n_comp);
+  SCVS_CUDA(cudaMemset(m.comp_active, 1, n_comp));
+  if (n_comp > 1) {
+    m.dof_comp = m.arena.alloc<int32_t>(m.n_dof);
+    SCVS_CUDA(cudaMemcpy(m.dof_comp, dc.data(), dc.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  } else {
+    m.dof_comp = nullptr;
+  }
 }
 
 void lift_rhs(Ctx &c, Mesh &m) {
   const int64_t total = m.n_dof * m.ld;
   double2 *gfull = nullptr, *y = nullptr;
-  double *part = nullptr, *nrm = nullptr;
+  double *nrm = nullptr;
   SCVS_CUDA(cudaMallocAsync(&gfull, total * sizeof(double2), c.stream));
   SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(double2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&part, (size_t)4 * c.num_sms * m.ld * sizeof(double), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&nrm, m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&nrm, m.n_sys() * sizeof(double), c.stream));
   SCVS_CUDA(cudaMemsetAsync(gfull, 0, total * sizeof(double2), c.stream));
   if (m.n_dir > 0 && m.m > 0) {
     int64_t tt = (int64_t)m.m * m.n_dir * m.dim;
@@ -284,16 +363,15 @@ void lift_rhs(Ctx &c, Mesh &m) {
     k_lift_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(y, gfull, m.dirmask, m.N, m.dim, m.n_dof, m.ld, m.b);
     count_launch(c);
   }
-  mode_norms2(c, m, m.b, part, nrm);
-  std::vector<double> h(m.ld);
-  SCVS_CUDA(cudaMemcpyAsync(h.data(), nrm, m.ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  norms2_sys(c, m, m.b, nrm);
+  std::vector<double> h(m.n_sys());
+  SCVS_CUDA(cudaMemcpyAsync(h.data(), nrm, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   SCVS_CUDA(cudaFreeAsync(gfull, c.stream));
   SCVS_CUDA(cudaFreeAsync(y, c.stream));
-  SCVS_CUDA(cudaFreeAsync(part, c.stream));
   SCVS_CUDA(cudaFreeAsync(nrm, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
-  m.bnorm.assign(m.ld, 0.0);
-  for (int k = 0; k < m.ld; ++k) m.bnorm[k] = std::sqrt(h[k]);
+  m.bnorm.assign(m.n_sys(), 0.0);
+  for (int s = 0; s < m.n_sys(); ++s) m.bnorm[s] = std::sqrt(h[s]);
 }
 
 // --------------------------------------------------------------- residual
@@ -301,10 +379,12 @@ void lift_rhs(Ctx &c, Mesh &m) {
 // the FP32 copy (right-hand side of the next FP32 cycle) and, optionally, FP64.
 __global__ void k_residual_finish(const double2 *__restrict__ b, const double2 *__restrict__ ax,
                                   const uint8_t *__restrict__ dirm, int64_t N, int dim, int64_t total, int ld,
-                                  float2 *__restrict__ r32, double2 *__restrict__ r64) {
+                                  float2 *__restrict__ r32, double2 *__restrict__ r64,
+                                  const int32_t *__restrict__ dof_comp, const uint8_t *__restrict__ comp_active) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= total) return;
   int64_t dof = f / ld;
+  if (row_idle(dof_comp, comp_active, dof)) return;
   bool dir = dof < N * dim && dirm[dof / dim];
   double2 bb = b[f], a = ax[f];
   double2 r = dir ? make_double2(0.0, 0.0) : make_double2(bb.x - a.x, bb.y - a.y);
@@ -335,6 +415,8 @@ struct PcArgs {
   // diagonals and per-mode scalars in the kernel's precision T
   const void *ksd, *msd, *mpd, *lpd, *k1d;
   const void *wabs, *wrho;   // [ld] |omega_k| rho, omega_k rho
+  const int32_t *dof_comp;   // null: one component
+  const uint8_t *comp_active;
 };
 
 // The velocity block of mode k, A_u = mu K_s + j omega rho M_s, is preconditioned
@@ -353,6 +435,7 @@ __device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, int k) {
 // mode: z_u = r / diag A_r, z_p = (mu/diag M_p + j omega rho/diag L_p) r.
 template <typename T, int DIM, bool DIAG>
 __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *__restrict__ rscale,
+                           const int32_t *__restrict__ dof_comp,
                            const double *__restrict__ inv_theta_u, double inv_theta_m, double inv_theta_l,
                            typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zM,
                            typename cpx<T>::t *__restrict__ zL) {
@@ -362,9 +445,10 @@ __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *
   if (f >= total) return;
   const int64_t dof = f / a.ld;
   const int k = (int)(f % a.ld);
+  if (row_idle(a.dof_comp, a.comp_active, dof)) return;
   C v = r[f];
   if (rscale) {
-    T s = (T)rscale[k];
+    T s = (T)rscale[(dof_comp ? dof_comp[dof] * a.ld : 0) + k];
     v.x *= s; v.y *= s;
     r[f] = v;
   }
@@ -475,6 +559,7 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
   const int64_t row_lo = cc.do_u ? 0 : a.N;
   const int64_t row_hi = (cc.do_m || cc.do_l) ? a.N + a.P : a.N;
   for (int64_t row = row_lo + (int64_t)blockIdx.x * gpb + group; row < row_hi; row += (int64_t)gridDim.x * gpb) {
+    if (row_idle(a.dof_comp, a.comp_active, row < a.N ? row * DIM : (int64_t)DIM * a.N + (row - a.N))) continue;
     if (row < a.N) {
       const int64_t A = row;
       if (a.dirmask[A]) {
@@ -517,19 +602,27 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
           }
         }
       }
+      T dr[MPL], al[MPL], be[MPL];
 #pragma unroll
       for (int i = 0; i < MPL; ++i) {
-        const int k = koff + i;
-        const T dr = vel_dinv<T>(a, A, k);
-        const T al = (T)cc.alpha_u[k], be = (T)cc.beta_u[k];
+        dr[i] = vel_dinv<T>(a, A, koff + i);
+        al[i] = (T)cc.alpha_u[koff + i];
+        be[i] = (T)cc.beta_u[koff + i];
+      }
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-          const int64_t f = (A * DIM + c) * ld + k;
-          const C rv = r[f], z = zu[f];
-          const C zp = cc.prev_zero_u ? mk<T>(0, 0) : zu_prev[f];
-          const T ur = dr * (rv.x - acc[c].re[i]), ui = dr * (rv.y - acc[c].im[i]);
-          zu_prev[f] = mk<T>(z.x + al * (z.x - zp.x) + be * ur, z.y + al * (z.y - zp.y) + be * ui);
+      for (int c = 0; c < DIM; ++c) {
+        const int64_t f0 = (A * DIM + c) * ld + koff;
+        CV<T, MPL> rv, z, zp, o;
+        ldv<T, MPL>(rv, r + f0);
+        ldv<T, MPL>(z, zu + f0);
+        if (cc.prev_zero_u) zp.zero(); else ldv_cg<T, MPL>(zp, zu_prev + f0);
+#pragma unroll
+        for (int i = 0; i < MPL; ++i) {
+          const T ur = dr[i] * (rv.re[i] - acc[c].re[i]), ui = dr[i] * (rv.im[i] - acc[c].im[i]);
+          o.re[i] = z.re[i] + al[i] * (z.re[i] - zp.re[i]) + be[i] * ur;
+          o.im[i] = z.im[i] + al[i] * (z.im[i] - zp.im[i]) + be[i] * ui;
         }
+        stv<T, MPL>(zu_prev + f0, o);
       }
     } else {
       pressure_row_step<T, MPL, L, DIM>(a, cc, row - a.N, r, zM, zM_prev, zL, zL_prev, lane, gm);
@@ -551,6 +644,7 @@ k_vel_residual(const PcArgs a, const typename cpx<T>::t *__restrict__ r, const t
   const int ld = a.ld, koff = lane * MPL;
   const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv;
   for (int64_t A = (int64_t)blockIdx.x * gpb + group; A < a.N; A += (int64_t)gridDim.x * gpb) {
+    if (row_idle(a.dof_comp, a.comp_active, A * DIM)) continue;
     if (a.dirmask[A]) {
       CV<T, MPL> zz;
       zz.zero();
@@ -609,6 +703,7 @@ __global__ void k_restrict(const PcArgs a, int dim, const typename cpx<T>::t *__
   const int64_t per = (int64_t)dim * a.ld;
   if (f >= a.P * per) return;
   const int64_t v = f / per, rem = f % per;
+  if (row_idle(a.dof_comp, a.comp_active, v * dim)) return;
   if (a.dirmask[v]) { rc[f] = mk<T>(0, 0); return; }
   auto s = rr[v * per + rem];
   T xr = s.x, xi = s.y;
@@ -628,7 +723,7 @@ __global__ void k_prolong(const PcArgs a, int dim, const typename cpx<T>::t *__r
   const int64_t per = (int64_t)dim * a.ld;
   if (f >= a.N * per) return;
   const int64_t n = f / per, rem = f % per;
-  if (a.dirmask[n]) return;
+  if (a.dirmask[n] || row_idle(a.dof_comp, a.comp_active, n * dim)) return;
   T cr, ci;
   if (n < a.P) {
     const auto c0 = zc[n * per + rem];
@@ -659,6 +754,7 @@ __global__ void k_coarse_step0(const PcArgs a, int dim, const typename cpx<T>::t
   if (f >= a.P * per) return;
   const int64_t v = f / per;
   const int k = (int)(f % a.ld);
+  if (row_idle(a.dof_comp, a.comp_active, v * dim)) return;
   if (a.dirmask[v]) { zc[f] = mk<T>(0, 0); return; }
   const T s = coarse_dinv<T>(a, v, k) * (T)inv_theta[k];
   const auto r = rc[f];
@@ -687,6 +783,7 @@ k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__
   // rows [0, P): coarse velocity step; rows [P, 2P): a pressure step when requested
   const int64_t rows = (pc.do_m || pc.do_l) ? 2 * a.P : a.P;
   for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < rows; v += (int64_t)gridDim.x * gpb) {
+    if (row_idle(a.dof_comp, a.comp_active, v < a.P ? v * DIM : (int64_t)DIM * a.N + (v - a.P))) continue;
     if (v >= a.P) {
       pressure_row_step<T, MPL, L, DIM>(a, pc, v - a.P, r, zM, zM_prev, zL, zL_prev, lane, gm);
       continue;
@@ -749,6 +846,7 @@ __global__ void k_pc_combine(const PcArgs a, int dim, const typename cpx<T>::t *
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.P * a.ld) return;
   const int k = (int)(f % a.ld);
+  if (row_idle(a.dof_comp, a.comp_active, (int64_t)dim * a.N + f / a.ld)) return;
   const T mu = (T)a.mu, wr = ((const T *)a.wrho)[k];
   auto m_ = zM[f];
   auto l_ = zL[f];
@@ -798,7 +896,8 @@ static PcArgs pc_args(const Mesh &m) {
                 f ? (const void *)m.ks_df : (const void *)m.ks_diag, f ? (const void *)m.ms_df : (const void *)m.ms_diag,
                 f ? (const void *)m.mp_df : (const void *)m.mp_diag, f ? (const void *)m.lp_df : (const void *)m.lp_diag,
                 f ? (const void *)m.k1_df : (const void *)m.k1_diag,
-                f ? (const void *)m.wabs_f : (const void *)m.wabs_d, f ? (const void *)m.wrho_f : (const void *)m.wrho_d};
+                f ? (const void *)m.wabs_f : (const void *)m.wabs_d, f ? (const void *)m.wrho_f : (const void *)m.wrho_d,
+                m.dof_comp, m.comp_active};
 }
 
 // Per-mode Chebyshev sequences on [lam_k / ratio, 1.05 lam_k] uploaded as
@@ -852,8 +951,9 @@ static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &
   if (cc.do_m || cc.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb;
   if (cc.do_m) cb += pb * (cc.prev_zero_m ? 2 : 3);
   if (cc.do_l) cb += pb * (cc.prev_zero_l ? 2 : 3);
-  KScope ksc(c, KC_PRECOND, cb);
-  SCVS_DISPATCH_LD(T, m.ld, {
+  KScope ksc(c, cc.do_u ? KC_CHEB_FINE : KC_PRECOND, cb);
+  auto body = [&](auto mpl_c, auto l_c) {
+    constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
     const int gpb = 256 / L;
     int64_t lo = cc.do_u ? 0 : m.N, hi = (cc.do_m || cc.do_l) ? m.N + m.P : m.N;
     const unsigned nb = row_blocks(c, hi - lo, gpb);
@@ -861,7 +961,13 @@ static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &
       k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
     else
       k_pc_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
-  });
+  };
+  if constexpr (sizeof(T) == 4) {
+    const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
+    SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+  } else {
+    SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+  }
   count_launch(c);
 }
 
@@ -881,9 +987,9 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
     KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, 0, 0, z, nullptr, nullptr);
+      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr);
     else
-      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, 0, 0, z, nullptr, nullptr);
+      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr);
     count_launch(c);
     return;
   }
@@ -904,10 +1010,10 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   {
     KScope ks0(c, KC_PRECOND, blk * (rscale ? 3 : 2) + 2 * pb + (double)m.N * 17 + (double)m.P * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
+      k_pc_step0<T, 2, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
                                                         uA, pM[0], pL[0]);
     else
-      k_pc_step0<T, 3, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
+      k_pc_step0<T, 3, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
                                                         uA, pM[0], pL[0]);
     count_launch(c);
   }
@@ -940,16 +1046,25 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, i == 1));
   if (pmg) {
     // fine residual, restriction, coarse Chebyshev solve, prolongation
-    SCVS_DISPATCH_LD(T, m.ld, {
-      const int gpb = 256 / L;
-      const unsigned nb = row_blocks(c, m.N, gpb);
-      KScope ks(c, KC_PRECOND, (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + 3 * vb);
-      if (m.dim == 2)
-        k_vel_residual<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
-      else
-        k_vel_residual<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
-    });
-    count_launch(c);
+    {
+      KScope ks(c, KC_CHEB_FINE, (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + 3 * vb);
+      auto body = [&](auto mpl_c, auto l_c) {
+        constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
+        const int gpb = 256 / L;
+        const unsigned nb = row_blocks(c, m.N, gpb);
+        if (m.dim == 2)
+          k_vel_residual<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
+        else
+          k_vel_residual<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
+      };
+      if constexpr (sizeof(T) == 4) {
+        const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
+        SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+      } else {
+        SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+      }
+      count_launch(c);
+    }
     {
       KScope ks(c, KC_PRECOND, cbk + (double)(m.N - m.P) * m.dim * m.ld * cs + (double)(m.P + 1) * 8 +
                                    (double)(m.N - m.P) * 8 + cbk);
@@ -1230,20 +1345,80 @@ void spectral_bounds(Ctx &c, Mesh &m) {
 void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev) {
   const int64_t total = m.n_dof * m.ld;
   double2 *ax = nullptr;
-  double *part = nullptr;
   SCVS_CUDA(cudaMallocAsync(&ax, total * sizeof(double2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&part, (size_t)4 * c.num_sms * m.ld * sizeof(double), c.stream));
   launch_saddle<double>(c, m, saddle_args<double>(c, m, true), m.x, ax);
   double2 *r = r64 ? r64 : ax;
   {
     KScope ks(c, KC_VECTOR, (double)total * (32 + 16 + (r32 ? 8 : 0)));
     k_residual_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(m.b, ax, m.dirmask, m.N, m.dim, total, m.ld, r32,
-                                                                  r64 ? r64 : ax);
+                                                                  r64 ? r64 : ax, m.dof_comp, m.comp_active);
     count_launch(c);
   }
-  mode_norms2(c, m, r, part, norm2_out_dev);
+  norms2_sys(c, m, r, norm2_out_dev);
   SCVS_CUDA(cudaFreeAsync(ax, c.stream));
-  SCVS_CUDA(cudaFreeAsync(part, c.stream));
+}
+
+// ------------------------------------------------------------- autotuner
+// Row-group shape (modes per lane) of the all-modes SpMM and of the fine
+// Chebyshev step, chosen per mesh and mode stride by timing every valid
+// candidate on this mesh with CUDA events (median of 3 launches after one
+// warm-up) and kept in the mesh.
+void autotune_shapes(Ctx &c, Mesh &m) {
+  const int64_t total = m.n_dof * m.ld;
+  float2 *x = nullptr, *y = nullptr;
+  double *zeros = nullptr;
+  SCVS_CUDA(cudaMallocAsync(&x, total * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(float2), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&zeros, m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(zeros, 0, m.ld * sizeof(double), c.stream));
+  k_init_random<<<ceil_div(total, 256), 256, 0, c.stream>>>(x, total);
+  count_launch(c);
+  cudaEvent_t e0, e1;
+  SCVS_CUDA(cudaEventCreate(&e0));
+  SCVS_CUDA(cudaEventCreate(&e1));
+  const bool timers_on = c.timers.on;
+  c.timers.on = false;
+  m.tune_us.assign(6, 0.0f);
+  auto time_it = [&](auto &&launch) {
+    launch();
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      SCVS_CUDA(cudaEventRecord(e0, c.stream));
+      launch();
+      SCVS_CUDA(cudaEventRecord(e1, c.stream));
+      SCVS_CUDA(cudaEventSynchronize(e1));
+      float t = 0;
+      SCVS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      best = std::min(best, t);
+    }
+    return best * 1e3f;
+  };
+  const PcArgs pa = pc_args<float>(m);
+  ChebCoef cc{};
+  cc.do_u = 1;
+  cc.alpha_u = zeros;
+  cc.beta_u = zeros;
+  cc.prev_zero_u = 1;
+  int best_s = 0, best_c = 0;
+  float tb_s = 1e30f, tb_c = 1e30f;
+  for (int mpl : {1, 2, 4}) {
+    if (!shape_valid(m.ld, mpl)) continue;
+    m.mpl_spmm = mpl;
+    const float ts = time_it([&]() { apply_saddle<float>(c, m, x, y); });
+    m.mpl_cheb = mpl;
+    const float tc = time_it([&]() { cheb_launch<float>(c, m, pa, cc, 1, x, x, y, nullptr, nullptr, nullptr, nullptr); });
+    m.tune_us[mpl == 4 ? 2 : mpl - 1] = ts;
+    m.tune_us[3 + (mpl == 4 ? 2 : mpl - 1)] = tc;
+    if (ts < tb_s) { tb_s = ts; best_s = mpl; }
+    if (tc < tb_c) { tb_c = tc; best_c = mpl; }
+  }
+  m.mpl_spmm = best_s;
+  m.mpl_cheb = best_c;
+  c.timers.on = timers_on;
+  SCVS_CUDA(cudaEventDestroy(e0));
+  SCVS_CUDA(cudaEventDestroy(e1));
+  for (void *p : {(void *)x, (void *)y, (void *)zeros}) SCVS_CUDA(cudaFreeAsync(p, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
 }
 
 }  // namespace scvs

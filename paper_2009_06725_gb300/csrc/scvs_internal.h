@@ -27,12 +27,15 @@ struct DevArena {
   }
 };
 
+constexpr int CHUNK_ROWS = 2048;
+
 // Counts every kernel launch of a context (reported by scvs_launch_count).
 struct Launches { int64_t n = 0; };
 
 // Kernel classes timed by the optional event timers (scvs_kernel_timers).
 enum KClass : int {
-  KC_SPMM32 = 0, KC_SPMM64, KC_PRECOND, KC_ARNOLDI, KC_VECTOR, KC_ASSEMBLY, KC_RECON, KC_MATFREE, KC_COUNT
+  KC_SPMM32 = 0, KC_SPMM64, KC_PRECOND, KC_ARNOLDI, KC_VECTOR, KC_ASSEMBLY, KC_RECON, KC_MATFREE, KC_CHEB_FINE,
+  KC_COUNT
 };
 
 // CUDA-event timing of kernel launches on the launching stream: a start and a
@@ -111,6 +114,19 @@ struct Mesh {
   uint8_t *dirmask = nullptr;  // [N]
   uint8_t *outmask = nullptr;  // [P]
   int64_t *dir_nodes = nullptr;  // [n_dir] ascending
+  // Independent components: the mesh may be the disjoint union of several
+  // meshes; every (component, mode) pair is then its own linear system
+  // ("system" s = comp * ld + k) with its own Krylov space and convergence.
+  int n_comp = 1;
+  int32_t *dof_comp = nullptr;   // [n_dof] component of every dof row (null: all 0)
+  // Row chunks of at most CHUNK_ROWS rows that never straddle two
+  // components, grouped by component: reductions are segmented by chunk.
+  int64_t n_chunk = 0;
+  int64_t *chunk_row0 = nullptr;
+  int32_t *chunk_rows = nullptr, *chunk_comp = nullptr;
+  int32_t *comp_chunk = nullptr;  // [n_comp+1] chunk range of every component
+  uint8_t *comp_active = nullptr; // [n_comp] 0: every system of the component is done (kernels skip it)
+  int n_sys() const { return n_comp * ld; }
   double rho = 1.0, mu = 1.0;
   // ---- modes
   int m = 0, ld = 0;
@@ -122,11 +138,13 @@ struct Mesh {
   double2 *g = nullptr;          // [m][n_dir][dim]
   double2 *b = nullptr;          // [n_dof][ld] lifted RHS (b_D = g)
   double2 *x = nullptr;          // [n_dof][ld] FP64 solution
-  std::vector<double> bnorm;     // [ld] ||b_F||
+  std::vector<double> bnorm;     // [n_comp * ld] ||b_F|| per system
   std::vector<double> lam_u;     // [ld] spectral radius estimate of D_r^-1 A_r per mode (velocity)
   std::vector<double> lam_c;     // [ld] same for the P1 coarse velocity operator
   double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
   PcTables pc;
+  int mpl_spmm = 0, mpl_cheb = 0;       // autotuned row-group shapes (0: default)
+  std::vector<float> tune_us;            // measured candidates: [spmm mpl=1,2,4, cheb mpl=1,2,4] (us, 0 = n/a)
   std::vector<double> feat;      // [m][5] features of the modes (learned guess)
   bool solved = false;
   std::vector<scvs_mode_report> rep;
@@ -211,7 +229,10 @@ void apply_saddle(Ctx &c, const Mesh &m, const typename cpx<T>::t *x, typename c
 void lift_rhs(Ctx &c, Mesh &m);
 double saddle_bytes(const Mesh &m, int value_size);
 int64_t precond_scratch_elems(const Mesh &m);
+void autotune_shapes(Ctx &c, Mesh &m);
 void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev);
+void norms2_sys(Ctx &c, const Mesh &m, const double2 *v, double *out_dev);  // [n_sys] free-row squared norms
+void set_chunks(Ctx &c, Mesh &m, const int32_t *node_comp_host, int n_comp);
 void spectral_bounds(Ctx &c, Mesh &m);
 template <typename T>
 void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r, typename cpx<T>::t *z,

@@ -80,31 +80,63 @@ __device__ __forceinline__ unsigned group_mask() {
   return ((1u << L) - 1u) << base;
 }
 
-// Dispatch a lambda on (MPL, L) for a row stride ld (power of 2, 2..128).
-// FP32 blocks use 2 modes per lane (16-byte loads), FP64 blocks 1 mode per
-// lane (16-byte loads); strides beyond 32 lanes raise the modes per lane.
-#define SCVS_DISPATCH_LD(T, ld, ...)                                          \
+#define SCVS_SHAPE_KEY(LDV, MPLV) ((LDV) * 8 + (MPLV))
+// Row-group shapes: a row of ld modes is split over L = ld / MPL lanes with
+// MPL modes each.  SCVS_DISPATCH_SHAPE instantiates every valid (ld, MPL)
+// pair (ld a power of two in [2, 128], MPL in {1, 2, 4}, L <= 32);
+// SCVS_DISPATCH_LD picks the default shape (16-byte loads per lane).
+#define SCVS_SHAPE_CASE(LDV, MPLV, ...)                  \
+  case SCVS_SHAPE_KEY(LDV, MPLV): {                      \
+    constexpr int MPL = MPLV, L = (LDV) / (MPLV);        \
+    __VA_ARGS__;                                         \
+  } break;
+
+#define SCVS_DISPATCH_SHAPE(ld, mpl, ...)                                                       \
+  do {                                                                                          \
+    switch (SCVS_SHAPE_KEY(ld, mpl)) {                                                                 \
+      SCVS_SHAPE_CASE(2, 1, __VA_ARGS__) SCVS_SHAPE_CASE(2, 2, __VA_ARGS__)                      \
+      SCVS_SHAPE_CASE(4, 1, __VA_ARGS__) SCVS_SHAPE_CASE(4, 2, __VA_ARGS__)                      \
+      SCVS_SHAPE_CASE(4, 4, __VA_ARGS__) SCVS_SHAPE_CASE(8, 1, __VA_ARGS__)                      \
+      SCVS_SHAPE_CASE(8, 2, __VA_ARGS__) SCVS_SHAPE_CASE(8, 4, __VA_ARGS__)                      \
+      SCVS_SHAPE_CASE(16, 1, __VA_ARGS__) SCVS_SHAPE_CASE(16, 2, __VA_ARGS__)                    \
+      SCVS_SHAPE_CASE(16, 4, __VA_ARGS__) SCVS_SHAPE_CASE(32, 1, __VA_ARGS__)                    \
+      SCVS_SHAPE_CASE(32, 2, __VA_ARGS__) SCVS_SHAPE_CASE(32, 4, __VA_ARGS__)                    \
+      SCVS_SHAPE_CASE(64, 2, __VA_ARGS__) SCVS_SHAPE_CASE(64, 4, __VA_ARGS__)                    \
+      SCVS_SHAPE_CASE(128, 4, __VA_ARGS__)                                                      \
+      default: throw (int)SCVS_ERR_ARG;                                                         \
+    }                                                                                           \
+  } while (0)
+
+template <typename T>
+inline int default_mpl(int ld) {
+  if (sizeof(T) == 4) return ld >= 128 ? 4 : 2;
+  return ld >= 128 ? 4 : (ld >= 64 ? 2 : 1);
+}
+inline bool shape_valid(int ld, int mpl) { return mpl >= 1 && mpl <= 4 && ld % mpl == 0 && ld / mpl <= 32 && !(ld == 2 && mpl == 4); }
+
+#define SCVS_LD_CASE(LDV, MPLV, ...)                     \
+  case (LDV): {                                          \
+    constexpr int MPL = MPLV, L = (LDV) / (MPLV);        \
+    __VA_ARGS__;                                         \
+  } break;
+
+// default shape only (kernels that are not autotuned)
+#define SCVS_DISPATCH_LD(T, ld, ...)                                           \
   do {                                                                         \
     if constexpr (sizeof(T) == 4) {                                            \
       switch (ld) {                                                            \
-        case 2: { constexpr int MPL = 2, L = 1; __VA_ARGS__; } break;                 \
-        case 4: { constexpr int MPL = 2, L = 2; __VA_ARGS__; } break;                 \
-        case 8: { constexpr int MPL = 2, L = 4; __VA_ARGS__; } break;                 \
-        case 16: { constexpr int MPL = 2, L = 8; __VA_ARGS__; } break;                \
-        case 32: { constexpr int MPL = 2, L = 16; __VA_ARGS__; } break;               \
-        case 64: { constexpr int MPL = 2, L = 32; __VA_ARGS__; } break;               \
-        case 128: { constexpr int MPL = 4, L = 32; __VA_ARGS__; } break;              \
+        SCVS_LD_CASE(2, 2, __VA_ARGS__) SCVS_LD_CASE(4, 2, __VA_ARGS__)   \
+        SCVS_LD_CASE(8, 2, __VA_ARGS__) SCVS_LD_CASE(16, 2, __VA_ARGS__)  \
+        SCVS_LD_CASE(32, 2, __VA_ARGS__) SCVS_LD_CASE(64, 2, __VA_ARGS__) \
+        SCVS_LD_CASE(128, 4, __VA_ARGS__)                                   \
         default: throw (int)SCVS_ERR_ARG;                                      \
       }                                                                        \
     } else {                                                                   \
       switch (ld) {                                                            \
-        case 2: { constexpr int MPL = 1, L = 2; __VA_ARGS__; } break;                 \
-        case 4: { constexpr int MPL = 1, L = 4; __VA_ARGS__; } break;                 \
-        case 8: { constexpr int MPL = 1, L = 8; __VA_ARGS__; } break;                 \
-        case 16: { constexpr int MPL = 1, L = 16; __VA_ARGS__; } break;               \
-        case 32: { constexpr int MPL = 1, L = 32; __VA_ARGS__; } break;               \
-        case 64: { constexpr int MPL = 2, L = 32; __VA_ARGS__; } break;               \
-        case 128: { constexpr int MPL = 4, L = 32; __VA_ARGS__; } break;              \
+        SCVS_LD_CASE(2, 1, __VA_ARGS__) SCVS_LD_CASE(4, 1, __VA_ARGS__)   \
+        SCVS_LD_CASE(8, 1, __VA_ARGS__) SCVS_LD_CASE(16, 1, __VA_ARGS__)  \
+        SCVS_LD_CASE(32, 1, __VA_ARGS__) SCVS_LD_CASE(64, 2, __VA_ARGS__) \
+        SCVS_LD_CASE(128, 4, __VA_ARGS__)                                   \
         default: throw (int)SCVS_ERR_ARG;                                      \
       }                                                                        \
     }                                                                          \

@@ -25,7 +25,7 @@ SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
 SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG = 0, 1, 2
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
-SCVS_KC_COUNT = 8
+SCVS_KC_COUNT = 9
 SCVS_RECON_STATIC_MAX = 8192
 STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "stagnated", 3: "non_finite"}
 
@@ -34,7 +34,7 @@ class scvs_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("cheb_u", C.c_int32), ("cheb_m", C.c_int32),
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
-                ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("stream", C.c_void_p)]
+                ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p)]
 
 
 class scvs_mode_report(C.Structure):
@@ -68,6 +68,7 @@ SIGNATURES = {
     "scvs_set_mesh_dev": (_I32, [_P, _I32, _I64, _I64, _P, _I64, _P, _P]),
     "scvs_clear_meshes": (_I32, [_P]),
     "scvs_set_physics": (_I32, [_P, _I32, _D, _D]),
+    "scvs_set_components": (_I32, [_P, _I32, _I32, _P]),
     "scvs_dirichlet_count": (_I32, [_P, _I32, C.POINTER(_I64)]),
     "scvs_set_modes": (_I32, [_P, _I32, _I32, _P, _P]),
     "scvs_set_modes_dev": (_I32, [_P, _I32, _I32, _P, _P]),
@@ -99,10 +100,12 @@ SIGNATURES = {
     "scvs_mlp_forward_dev": (_I32, [_P, _P, _I64, _P]),
     "scvs_mlp_gradient_dev": (_I32, [_P, _P, _P, _I64, _P, C.POINTER(_D)]),
     "scvs_mlp_adam_step": (_I32, [_P, _D]),
+    "scvs_tuned_shapes": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
 }
-KERNEL_CLASSES = ["spmm_fp32", "spmm_fp64", "precond", "arnoldi", "vector", "assembly", "reconstruct", "matfree"]
+KERNEL_CLASSES = ["spmm_fp32", "spmm_fp64", "precond", "arnoldi", "vector", "assembly", "reconstruct", "matfree",
+                  "cheb_fine"]
 
 
 def lib():
@@ -174,6 +177,11 @@ def scvs_set_mesh_dev(ctx, dim, n_nodes, n_vertices, xyz_dev, n_elem, conn_dev, 
 
 def scvs_clear_meshes(ctx):
     return _check(ctx, lib().scvs_clear_meshes(ctx))
+
+
+def scvs_set_components(ctx, mesh_id, n_comp, node_comp):
+    nc = np.ascontiguousarray(node_comp, dtype=np.int32)
+    return _check(ctx, lib().scvs_set_components(ctx, mesh_id, n_comp, _ptr(nc)))
 
 
 def scvs_set_physics(ctx, mesh_id, rho, mu):
@@ -357,6 +365,13 @@ def scvs_mlp_gradient_dev(ctx, x_dev, t_dev, batch):
 
 def scvs_mlp_adam_step(ctx, lr):
     return _check(ctx, lib().scvs_mlp_adam_step(ctx, lr))
+
+
+def scvs_tuned_shapes(ctx, mesh_id):
+    a, b = C.c_int32(), C.c_int32()
+    us = np.zeros(6, dtype=np.float32)
+    _check(ctx, lib().scvs_tuned_shapes(ctx, mesh_id, C.byref(a), C.byref(b), _ptr(us)))
+    return dict(mpl_spmm=a.value, mpl_cheb=b.value, spmm_us=us[:3].tolist(), cheb_us=us[3:].tolist())
 
 
 def scvs_kernel_timers(ctx, enable):

@@ -276,3 +276,34 @@ def pipe_for_nodes(target_nodes, radius=1.0, length=10.0, **kw):
             best = (N, n_c, n_r, n_x)
     _, n_c, n_r, n_x = best
     return pipe3d(radius=radius, length=length, n_c=n_c, n_r=n_r, n_x=n_x, **kw)
+
+
+def union(mesh_list):
+    """Disjoint union of P2 meshes of one dimension as one mesh.
+
+    Vertices of every component come first (component order), then the edge
+    nodes (component order), so the union keeps the vertex-first numbering.
+    Returns (mesh, node_comp, maps) with maps[i][v] = union id of node v of
+    component i."""
+    dim = mesh_list[0]["dim"]
+    Ps = [m["n_vertices"] for m in mesh_list]
+    Ns = [m["xyz"].shape[0] for m in mesh_list]
+    Ptot = sum(Ps)
+    vbase = np.cumsum([0] + Ps[:-1])
+    ebase = np.cumsum([0] + [n - p for n, p in zip(Ns, Ps)][:-1])
+    Ntot = sum(Ns)
+    xyz = np.zeros((Ntot, dim))
+    tag = np.zeros(Ntot, dtype=np.uint8)
+    node_comp = np.zeros(Ntot, dtype=np.int32)
+    conns, maps = [], []
+    for i, m in enumerate(mesh_list):
+        v = np.arange(Ns[i])
+        mp = np.where(v < Ps[i], vbase[i] + v, Ptot + ebase[i] + (v - Ps[i]))
+        xyz[mp] = m["xyz"]
+        tag[mp] = m["tag"]
+        node_comp[mp] = i
+        conns.append(mp[m["conn"]].astype(np.int32))
+        maps.append(mp)
+    mesh = dict(dim=dim, xyz=xyz, conn=np.concatenate(conns, axis=0), tag=tag, n_vertices=Ptot,
+                name=f"union of {len(mesh_list)} meshes")
+    return mesh, node_comp, maps

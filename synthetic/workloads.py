@@ -103,3 +103,49 @@ def random_block(n_dofs, n_modes, seed, dtype=np.complex128):
     rng = np.random.default_rng(seed)
     x = rng.uniform(-1, 1, size=(n_dofs, n_modes)) + 1j * rng.uniform(-1, 1, size=(n_dofs, n_modes))
     return x.astype(dtype)
+
+
+def union_workload(wls):
+    """Batch of workloads with equal physics and mode lists as one mesh of
+    independent components: the union mesh, node->component map, and the
+    union's Dirichlet data (ascending union node id)."""
+    from .meshes import union
+    mesh, node_comp, maps = union([w["mesh"] for w in wls])
+    dn = dirichlet_nodes(mesh["tag"])
+    pos = {int(n): i for i, n in enumerate(dn)}
+    m = len(wls[0]["omegas"])
+    d = mesh["dim"]
+    g = np.zeros((m, dn.size, d), dtype=np.complex128)
+    for w, mp in zip(wls, maps):
+        idx = np.array([pos[int(mp[n])] for n in w["dir_nodes"]], dtype=np.int64)
+        g[:, idx, :] = w["g"]
+    return dict(mesh=mesh, node_comp=node_comp, n_comp=len(wls), maps=maps, parts=wls, rho=wls[0]["rho"],
+                mu=wls[0]["mu"], period=wls[0]["period"], omegas=wls[0]["omegas"], dir_nodes=dn, g=g,
+                name=f"batch of {len(wls)} pipes")
+
+
+def uneven_pipes(n_meshes=48, n_modes=16, seed=0, n_min=20_000, n_max=400_000, scale=1.0):
+    """Seeded batch of stenosed pipes of uneven size: R ~ U[0.5, 1.5],
+    L ~ U[5, 20], s ~ U[0, 0.5], target P2 node count log-uniform in
+    [n_min, n_max] (times `scale`); phases of c_k drawn per mesh."""
+    from .meshes import pipe_size
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_meshes):
+        R = rng.uniform(0.5, 1.5)
+        L = rng.uniform(5.0, 20.0)
+        s = rng.uniform(0.0, 0.5)
+        target = np.exp(rng.uniform(np.log(n_min), np.log(n_max))) * scale
+        best = None
+        for n_c in range(2, 40):
+            n_r = max(1, int(round(0.75 * n_c)))
+            hc = 2 * 0.5 * R / n_c
+            n_x = max(2, int(round(L / (1.1 * hc))))
+            N, _ = pipe_size(n_c, n_r, n_x)
+            if best is None or abs(np.log(N / target)) < abs(np.log(best[0] / target)):
+                best = (N, n_c, n_r, n_x)
+        _, n_c, n_r, n_x = best
+        wl = pipe_workload(n_c=n_c, n_r=n_r, n_x=n_x, n_modes=n_modes, radius=R, length=L, stenosis=s,
+                           seed=seed + 1 + i)
+        out.append(wl)
+    return out
