@@ -477,6 +477,40 @@ def run_guess(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fp64_permode(args):
+    """Comparison: plain per-mode FP64 GMRES (same block preconditioner, zero
+    guess), one mode per solve, on a sample of the benchmark pipe's modes."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2009_06725_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2009_06725_gb300 import scvs
+    wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=PIPE["n_x"], n_modes=PIPE["n_modes"],
+                                 length=PIPE["length"])
+    modes = [int(k) for k in np.linspace(0, PIPE["n_modes"] - 1, args.fp64_modes).round()]
+    with scvs.Solver(precision=scvs.SCVS_PREC_FP64) as s:
+        mid = scvs.scvs_set_mesh(s.ctx, wl["mesh"])
+        scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
+        times, its, conv = [], [], 0
+        for k in modes:
+            scvs.scvs_set_modes(s.ctx, mid, wl["omegas"][k:k + 1], wl["g"][k:k + 1])
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            rep = scvs.scvs_solve(s.ctx, mid, 1)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t)
+            its.append(rep[0]["iterations"])
+            conv += rep[0]["status"] == scvs.SCVS_CONVERGED
+    rate = conv / sum(times)
+    out = {"metric": "converged mode-solves/s at 1e-8 rel. residual", "value": rate, "unit": "mode-solves/s",
+           "n_gpus": 1, "impl": "fp64-per-mode GMRES", "dtype": "c128", "data": "synthetic",
+           "higher_is_better": True,
+           "config": {"workload": ("151k-node pipe, plain per-mode FP64 GMRES(30), same block preconditioner, zero "
+                                   f"guess, one mode per solve; sampled modes {modes}")},
+           "modes": modes, "iterations": its, "solve_s": times}
+    print(json.dumps(out), flush=True)
+
+
 def step_host(scvs, ctx, wl, m, N, P, d):
     mesh = wl["mesh"]
     scvs.scvs_clear_meshes(ctx)
@@ -520,7 +554,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")
-    ap.add_argument("--workload", default="pipe", choices=["pipe", "batch", "guess"])
+    ap.add_argument("--workload", default="pipe", choices=["pipe", "batch", "guess", "fp64-permode"])
+    ap.add_argument("--fp64-modes", type=int, default=4)
     ap.add_argument("--batch-meshes", type=int, default=48)
     ap.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batch's node counts")
     ap.add_argument("--guess-train", type=int, default=16, help="training morphs (x 32 modes)")
@@ -535,6 +570,9 @@ def main():
         return
     if args.workload == "guess" and args.impl == "gpu":
         run_guess(args)
+        return
+    if args.workload == "fp64-permode" and args.impl == "gpu":
+        run_fp64_permode(args)
         return
     if args.warmup < 3 and args.impl == "gpu":
         log("note: the timing rules ask for >= 3 warm-up steps")

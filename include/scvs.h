@@ -74,7 +74,10 @@ extern "C" {
 #define SCVS_PC_BLOCK_DIAG 1   /* block-diagonal, diagonal blocks only */
 #define SCVS_PC_BLOCK_PMG 2    /* block-diagonal; velocity block by a two-level p-multigrid cycle: Chebyshev
                                   smoothing of mu K + |omega| rho M on P2 and a Chebyshev solve of the same
-                                  operator on the nested P1 (vertex) space; pressure as BLOCK_CHEB (default) */
+                                  operator on the nested P1 (vertex) space; pressure as BLOCK_CHEB */
+#define SCVS_PC_TRI_PMG 3      /* block upper-triangular [A_u D; 0 S~] with the Schur complement approximation
+                                  S~^-1 = -(mu M_p^-1 + j omega rho L_p^-1) (pressure first), then the velocity
+                                  p-multigrid cycle of BLOCK_PMG on r_u - D z_p (default) */
 
 #define SCVS_GUESS_ZERO 0
 #define SCVS_GUESS_MLP 1
@@ -86,17 +89,19 @@ typedef struct {
   double tol;        /* relative residual target per mode (default 1e-8) */
   int32_t restart;   /* GMRES restart length m_r (default 30, max 64) */
   int32_t precision; /* SCVS_PREC_* (default MIXED) */
-  int32_t precond;   /* SCVS_PC_* (default BLOCK_PMG) */
-  int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with BLOCK_PMG the degree of each
+  int32_t precond;   /* SCVS_PC_* (default TRI_PMG) */
+  int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with the p-multigrid kinds the degree of each
                         of the pre- and post-smoothers (default 4) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
   int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 45) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
-  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of BLOCK_PMG (default 20) */
-  int32_t autotune;  /* 1 (default): time the row-group shapes of the FP32 SpMM and Chebyshev kernels on each
-                        mesh at scvs_set_modes and keep the fastest; 0: default shapes */
+  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of the p-multigrid kinds (default 20) */
+  int32_t autotune;  /* 1 (default): time the launch shapes (modes per lane, row tile) of the FP32 SpMM and
+                        Chebyshev kernels at scvs_set_modes and keep the fastest; the result is kept per
+                        context for meshes of the same size (dim, nodes, vertices, nonzeros, mode
+                        stride, components) and reused; 0: default shapes */
   void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
 } scvs_opts;
 
@@ -119,6 +124,8 @@ typedef struct {
   int32_t cycles;     /* restart cycles (= FP64 refinement steps) */
   int32_t guess_used; /* 1 if the learned initial guess was kept (its residual was below ||b||) */
   double rel_res;     /* final FP64 ||b_F - A_FF x_F - A_FD g|| / ||b_F|| (Eq. ls_error) */
+  double res0;        /* the same relative residual at the start point: 1 for the zero start (x_F = 0),
+                         below 1 where the learned guess was kept */
 } scvs_mode_report;
 
 /* Fill *opts with the defaults listed above. */
@@ -312,11 +319,17 @@ int scvs_mlp_adam_step(scvs_ctx *ctx, double lr);
 int scvs_kernel_timers(scvs_ctx *ctx, int32_t enable);
 int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *bytes, int64_t *launches);
 
-/* Row-group shapes chosen by the autotuner for a mesh (modes per lane of the
- * FP32 SpMM and of the fine Chebyshev sweep; 0 = not tuned) and the measured
- * candidate times in microseconds (us[6]: SpMM for 1, 2, 4 modes per lane,
- * then Chebyshev sweep; 0 = candidate not valid for the mode stride). */
-int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *mpl_spmm, int32_t *mpl_cheb, float *us);
+/* Launch shapes chosen by the autotuner for a mesh (set by scvs_set_modes
+ * when opts.autotune is on).  shape[4] = {modes per lane of the FP32 SpMM,
+ * its row tile, modes per lane of the fine Chebyshev sweep, its row tile};
+ * 0 = not tuned.  A row tile of t means a thread block walks
+ * t x (row groups per block) consecutive rows before moving on, so that rows
+ * sharing neighbours are gathered by the same SM.  us[2 * 3 * SCVS_TUNE_TILES]
+ * holds the measured candidate times in microseconds, indexed
+ * [kernel: SpMM, Chebyshev][modes per lane: 1, 2, 4][tile: 1, 2, 4, 8, 16];
+ * 0 = candidate not valid for the mode stride.  Either pointer may be NULL. */
+#define SCVS_TUNE_TILES 5
+int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *shape, float *us);
 
 #ifdef __cplusplus
 }

@@ -180,6 +180,7 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
   m->mode_arena.release();
   m->pc = PcTables{};
   m->mpl_spmm = m->mpl_cheb = 0;
+  m->tile_spmm = m->tile_cheb = 0;
   m->solved = false;
   m->m = n_modes;
   m->ld = mode_stride(n_modes);
@@ -203,7 +204,20 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
   SCVS_CUDA(cudaMemsetAsync(m->x, 0, total * sizeof(double2), c->stream));
   lift_rhs(*c, *m);
   spectral_bounds(*c, *m);
-  if (c->opts.autotune) autotune_shapes(*c, *m);
+  if (c->opts.autotune) {
+    const std::vector<int64_t> key{m->dim, m->N, m->P, m->s_nnz, m->g_nnz, m->ld, m->n_comp};
+    auto it = c->tune_cache.find(key);
+    if (it == c->tune_cache.end()) {
+      autotune_shapes(*c, *m);
+      c->tune_cache[key] = Ctx::TuneRec{m->mpl_spmm, m->tile_spmm, m->mpl_cheb, m->tile_cheb, m->tune_us};
+    } else {
+      m->mpl_spmm = it->second.mpl_spmm;
+      m->tile_spmm = it->second.tile_spmm;
+      m->mpl_cheb = it->second.mpl_cheb;
+      m->tile_cheb = it->second.tile_cheb;
+      m->tune_us = it->second.us;
+    }
+  }
   return SCVS_OK;
 }
 
@@ -217,7 +231,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->tol = 1e-8;
   o->restart = 30;
   o->precision = SCVS_PREC_MIXED;
-  o->precond = SCVS_PC_BLOCK_PMG;
+  o->precond = SCVS_PC_TRI_PMG;
   o->cheb_u = 4;
   o->cheb_c = 20;
   o->autotune = 1;
@@ -278,7 +292,7 @@ const char *scvs_last_error(const scvs_ctx *c) { return c ? c->err.c_str() : "nu
 int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
   if (!c || !o) return SCVS_ERR_ARG;
   if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
-      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > 2)
+      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_TRI_PMG)
     return fail(c, SCVS_ERR_ARG, "invalid options");
   void *old_stream = c->opts.stream;
   c->opts = *o;
@@ -729,14 +743,18 @@ int scvs_mlp_adam_step(scvs_ctx *c, double lr) {
   });
 }
 
-int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *ms, int32_t *mc, float *us) {
+int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *shape, float *us) {
   return guarded(c, [&]() {
     Mesh *m = get_mesh(c, mesh_id);
     if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
-    if (ms) *ms = m->mpl_spmm;
-    if (mc) *mc = m->mpl_cheb;
+    if (shape) {
+      shape[0] = m->mpl_spmm;
+      shape[1] = m->tile_spmm;
+      shape[2] = m->mpl_cheb;
+      shape[3] = m->tile_cheb;
+    }
     if (us)
-      for (int i = 0; i < 6; ++i) us[i] = i < (int)m->tune_us.size() ? m->tune_us[i] : 0.0f;
+      for (int i = 0; i < 2 * 3 * SCVS_TUNE_TILES; ++i) us[i] = i < (int)m->tune_us.size() ? m->tune_us[i] : 0.0f;
     return SCVS_OK;
   });
 }

@@ -508,7 +508,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
 
   // systems s = comp * ld + k; reports are per (comp, mode): comp * m + k
   const double tol = c.opts.tol;
-  m.rep.assign((size_t)m.n_comp * nm, scvs_mode_report{SCVS_MAX_ITER, 0, 0, 0, 0.0});
+  m.rep.assign((size_t)m.n_comp * nm, scvs_mode_report{SCVS_MAX_ITER, 0, 0, 0, 0.0, 0.0});
   auto rep = [&](int s) -> scvs_mode_report & { return m.rep[(size_t)(s / ld) * nm + (s % ld)]; };
   std::vector<int> done(S, 0);
   std::vector<double> rel(S, 0.0), best(S, 1e300);
@@ -570,6 +570,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       const double r = std::sqrt(std::max(n2[s], 0.0));
       rel[s] = r / m.bnorm[s];
       rep(s).rel_res = rel[s];
+      if (cyc == 0) rep(s).res0 = rel[s];
       if (!std::isfinite(rel[s])) { done[s] = 1; rep(s).status = SCVS_NON_FINITE; continue; }
       if (rel[s] <= tol) { done[s] = 1; rep(s).status = SCVS_CONVERGED; continue; }
       // stagnation: 12 cycles without a 1% gain on the best residual so far

@@ -37,6 +37,7 @@ template <typename T> struct SaddleArgs {
   double rho, mu;
   const int32_t *dof_comp;      // null: one component
   const uint8_t *comp_active;   // rows of inactive components are skipped
+  int tile;                     // row tile (SCVS_ROW_LOOP)
 };
 
 // true if the row's component has no active system (multi-component meshes)
@@ -59,7 +60,7 @@ k_saddle(const SaddleArgs<T> a, const typename cpx<T>::t *__restrict__ x, typena
   const T mu = (T)a.mu;
   const int64_t rows = a.N + a.P;
   const C *__restrict__ xp_base = x + (int64_t)DIM * a.N * ld + koff;
-  for (int64_t row = (int64_t)blockIdx.x * gpb + group; row < rows; row += (int64_t)gridDim.x * gpb) {
+  SCVS_ROW_LOOP(row, 0, rows, gpb, group, a.tile) {
     if (row_idle(a.dof_comp, a.comp_active, row < a.N ? row * DIM : (int64_t)DIM * a.N + (row - a.N))) continue;
     if (row < a.N) {
       const int64_t A = row;
@@ -163,7 +164,8 @@ SaddleArgs<T> saddle_args(const Ctx &c, const Mesh &m, bool masked);
 template <>
 SaddleArgs<float> saddle_args<float>(const Ctx &, const Mesh &m, bool) {
   return SaddleArgs<float>{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr, m.Ks_f, m.Ms_f, m.Dv_f,
-                           m.DTv_f, m.g_nnz, m.gt_nnz, m.dirmask, m.omega_d, m.rho, m.mu, m.dof_comp, m.comp_active};
+                           m.DTv_f, m.g_nnz, m.gt_nnz, m.dirmask, m.omega_d, m.rho, m.mu, m.dof_comp, m.comp_active,
+                           m.tile_spmm ? m.tile_spmm : SCVS_DEFAULT_TILE};
 }
 template <>
 SaddleArgs<double> saddle_args<double>(const Ctx &, const Mesh &m, bool masked) {
@@ -171,7 +173,7 @@ SaddleArgs<double> saddle_args<double>(const Ctx &, const Mesh &m, bool masked) 
                             masked ? m.Ks_m : m.Ks, masked ? m.Ms_m : m.Ms,
                             masked ? m.Dv_m : m.Dv, masked ? m.DTv_m : m.DTv,
                             m.g_nnz, m.gt_nnz, masked ? m.dirmask : nullptr, m.omega_d, m.rho, m.mu,
-                            masked ? m.dof_comp : nullptr, m.comp_active};
+                            masked ? m.dof_comp : nullptr, m.comp_active, SCVS_DEFAULT_TILE};
 }
 
 // Algorithmic bytes of one all-modes SpMM: every index and value array once,
@@ -182,8 +184,9 @@ double saddle_bytes(const Mesh &m, int vs) {
   return mat + 2.0 * m.n_dof * m.ld * 2 * vs;
 }
 
-static unsigned row_blocks(const Ctx &c, int64_t rows, int groups_per_block) {
-  int64_t need = (rows + groups_per_block - 1) / groups_per_block;
+static unsigned row_blocks(const Ctx &c, int64_t rows, int groups_per_block, int tile = 1) {
+  const int64_t span = (int64_t)groups_per_block * tile;
+  int64_t need = (rows + span - 1) / span;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c.num_sms * 32));
 }
 
@@ -195,7 +198,7 @@ void launch_saddle(Ctx &c, const Mesh &m, const SaddleArgs<T> &a, const typename
     const int mpl = m.mpl_spmm ? m.mpl_spmm : default_mpl<T>(m.ld);
     SCVS_DISPATCH_SHAPE(m.ld, mpl, {
       const int gpb = 256 / L;
-      const unsigned nb = row_blocks(c, m.N + m.P, gpb);
+      const unsigned nb = row_blocks(c, m.N + m.P, gpb, a.tile);
       if (m.dim == 2)
         k_saddle<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, x, y);
       else
@@ -204,7 +207,7 @@ void launch_saddle(Ctx &c, const Mesh &m, const SaddleArgs<T> &a, const typename
   } else {
     SCVS_DISPATCH_LD(T, m.ld, {
       const int gpb = 256 / L;
-      const unsigned nb = row_blocks(c, m.N + m.P, gpb);
+      const unsigned nb = row_blocks(c, m.N + m.P, gpb, a.tile);
       if (m.dim == 2)
         k_saddle<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, x, y);
       else
@@ -417,6 +420,9 @@ struct PcArgs {
   const void *wabs, *wrho;   // [ld] |omega_k| rho, omega_k rho
   const int32_t *dof_comp;   // null: one component
   const uint8_t *comp_active;
+  int tile;                  // row tile of the gather kernels (SCVS_ROW_LOOP)
+  const void *Dv;            // G block values (T), [dim][g_nnz] (block-triangular form)
+  int64_t g_nnz;
 };
 
 // The velocity block of mode k, A_u = mu K_s + j omega rho M_s, is preconditioned
@@ -433,15 +439,16 @@ __device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, int k) {
 // (and write it back); z_u = r / (diag A_r theta_u[k]); pressure: zM = r/(diag M_p theta_M),
 // zL = r/(diag L_p theta_L) with r zeroed at outlet vertices.  Block-diagonal
 // mode: z_u = r / diag A_r, z_p = (mu/diag M_p + j omega rho/diag L_p) r.
+// f0 > 0 starts the pass at element f0 (f0 = DIM N ld: pressure rows only).
 template <typename T, int DIM, bool DIAG>
 __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *__restrict__ rscale,
                            const int32_t *__restrict__ dof_comp,
                            const double *__restrict__ inv_theta_u, double inv_theta_m, double inv_theta_l,
                            typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zM,
-                           typename cpx<T>::t *__restrict__ zL) {
+                           typename cpx<T>::t *__restrict__ zL, int64_t f0) {
   using C = typename cpx<T>::t;
   const int64_t total = ((int64_t)DIM * a.N + a.P) * a.ld;
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= total) return;
   const int64_t dof = f / a.ld;
   const int k = (int)(f % a.ld);
@@ -558,7 +565,7 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
   const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv, *Mpv = (const T *)a.Mpv, *Lpv = (const T *)a.Lpv;
   const int64_t row_lo = cc.do_u ? 0 : a.N;
   const int64_t row_hi = (cc.do_m || cc.do_l) ? a.N + a.P : a.N;
-  for (int64_t row = row_lo + (int64_t)blockIdx.x * gpb + group; row < row_hi; row += (int64_t)gridDim.x * gpb) {
+  SCVS_ROW_LOOP(row, row_lo, row_hi, gpb, group, a.tile) {
     if (row_idle(a.dof_comp, a.comp_active, row < a.N ? row * DIM : (int64_t)DIM * a.N + (row - a.N))) continue;
     if (row < a.N) {
       const int64_t A = row;
@@ -643,7 +650,7 @@ k_vel_residual(const PcArgs a, const typename cpx<T>::t *__restrict__ r, const t
   const unsigned gm = group_mask<L>();
   const int ld = a.ld, koff = lane * MPL;
   const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv;
-  for (int64_t A = (int64_t)blockIdx.x * gpb + group; A < a.N; A += (int64_t)gridDim.x * gpb) {
+  SCVS_ROW_LOOP(A, 0, a.N, gpb, group, a.tile) {
     if (row_idle(a.dof_comp, a.comp_active, A * DIM)) continue;
     if (a.dirmask[A]) {
       CV<T, MPL> zz;
@@ -782,7 +789,7 @@ k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__
   const T mu = (T)a.mu;
   // rows [0, P): coarse velocity step; rows [P, 2P): a pressure step when requested
   const int64_t rows = (pc.do_m || pc.do_l) ? 2 * a.P : a.P;
-  for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < rows; v += (int64_t)gridDim.x * gpb) {
+  SCVS_ROW_LOOP(v, 0, rows, gpb, group, a.tile) {
     if (row_idle(a.dof_comp, a.comp_active, v < a.P ? v * DIM : (int64_t)DIM * a.N + (v - a.P))) continue;
     if (v >= a.P) {
       pressure_row_step<T, MPL, L, DIM>(a, pc, v - a.P, r, zM, zM_prev, zL, zL_prev, lane, gm);
@@ -839,15 +846,89 @@ k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__
   }
 }
 
-// z_p = mu zM + j omega rho zL
+// Block upper-triangular form, start of the velocity solve: normalise the
+// Krylov vector's velocity rows in place (rscale, may be null), form the
+// right-hand side of the velocity block rt = r_u - D z_p (D z_p gathered over
+// the G row, whose columns are vertices; Dirichlet rows keep r_u) and write the
+// first Chebyshev iterate z_u = rt / (diag A_r theta_u[k]).
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256)
+k_tri_vel0(const PcArgs a, typename cpx<T>::t *__restrict__ r, const double *__restrict__ rscale,
+           const double *__restrict__ inv_theta_u, const typename cpx<T>::t *__restrict__ zp,
+           typename cpx<T>::t *__restrict__ rt, typename cpx<T>::t *__restrict__ zu) {
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  const int ld = a.ld, koff = lane * MPL;
+  const T *Dv = (const T *)a.Dv;
+  SCVS_ROW_LOOP(A, 0, a.N, gpb, group, a.tile) {
+    if (row_idle(a.dof_comp, a.comp_active, A * DIM)) continue;
+    CV<T, MPL> rv[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) ldv<T, MPL>(rv[c], r + (A * DIM + c) * ld + koff);
+    if (rscale) {
+      const double *rs = rscale + (a.dof_comp ? (int64_t)a.dof_comp[A * DIM] * ld : 0) + koff;
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        const T sc = (T)rs[i];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) { rv[c].re[i] *= sc; rv[c].im[i] *= sc; }
+      }
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) stv<T, MPL>(r + (A * DIM + c) * ld + koff, rv[c]);
+    }
+    if (a.dirmask[A]) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        stv<T, MPL>(rt + (A * DIM + c) * ld + koff, rv[c]);
+        stv<T, MPL>(zu + (A * DIM + c) * ld + koff, rv[c]);
+      }
+      continue;
+    }
+    const int64_t s0 = a.s_ptr[A], g1 = s0 + a.g_len[A], goff = a.g_ptr[A] - s0;
+    for (int64_t base = s0; base < g1; base += L) {
+      const int64_t t = base + lane;
+      int32_t col = 0;
+      T dv[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) dv[c] = 0;
+      if (t < g1) {
+        col = __ldg(a.s_col + t);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dv[c] = __ldg(Dv + c * a.g_nnz + t + goff);
+      }
+      const int cnt = (int)min((int64_t)L, g1 - base);
+      for (int q = 0; q < cnt; ++q) {
+        const int32_t B = gshfl<L>(gm, col, q);
+        CV<T, MPL> xq;
+        ldv<T, MPL>(xq, zp + (int64_t)B * ld + koff);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) axpy(rv[c], -gshfl<L>(gm, dv[c], q), xq);
+      }
+    }
+    T sd[MPL];
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) sd[i] = vel_dinv<T>(a, A, koff + i) * (T)inv_theta_u[koff + i];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      CV<T, MPL> o;
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) { o.re[i] = sd[i] * rv[c].re[i]; o.im[i] = sd[i] * rv[c].im[i]; }
+      stv<T, MPL>(rt + (A * DIM + c) * ld + koff, rv[c]);
+      stv<T, MPL>(zu + (A * DIM + c) * ld + koff, o);
+    }
+  }
+}
+
+// z_p = sign (mu zM + j omega rho zL)
 template <typename T>
 __global__ void k_pc_combine(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zM,
-                             const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ z) {
+                             const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ z, T sign) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= a.P * a.ld) return;
   const int k = (int)(f % a.ld);
   if (row_idle(a.dof_comp, a.comp_active, (int64_t)dim * a.N + f / a.ld)) return;
-  const T mu = (T)a.mu, wr = ((const T *)a.wrho)[k];
+  const T mu = sign * (T)a.mu, wr = sign * ((const T *)a.wrho)[k];
   auto m_ = zM[f];
   auto l_ = zL[f];
   z[(int64_t)dim * a.N * a.ld + f] = mk<T>(mu * m_.x - wr * l_.y, mu * m_.y + wr * l_.x);
@@ -897,7 +978,8 @@ static PcArgs pc_args(const Mesh &m) {
                 f ? (const void *)m.mp_df : (const void *)m.mp_diag, f ? (const void *)m.lp_df : (const void *)m.lp_diag,
                 f ? (const void *)m.k1_df : (const void *)m.k1_diag,
                 f ? (const void *)m.wabs_f : (const void *)m.wabs_d, f ? (const void *)m.wrho_f : (const void *)m.wrho_d,
-                m.dof_comp, m.comp_active};
+                m.dof_comp, m.comp_active, m.tile_cheb ? m.tile_cheb : SCVS_DEFAULT_TILE,
+                f ? (const void *)m.Dv_f : (const void *)m.Dv_m, m.g_nnz};
 }
 
 // Per-mode Chebyshev sequences on [lam_k / ratio, 1.05 lam_k] uploaded as
@@ -925,7 +1007,7 @@ static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   const int sc = std::max(1, c.opts.cheb_c), kind = c.opts.precond;
   if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl && t.s_c == sc && t.kind == kind) return;
   t.s_u = su; t.s_m = sm; t.s_l = sl; t.s_c = sc; t.kind = kind;
-  const bool pmg = kind == SCVS_PC_BLOCK_PMG;
+  const bool pmg = kind == SCVS_PC_BLOCK_PMG || kind == SCVS_PC_TRI_PMG;
   per_mode_seq(c, m, m.lam_u, pmg ? CHEB_RATIO_SMOOTH : CHEB_RATIO_U, su, &t.inv_theta_u, &t.alpha_u, &t.beta_u);
   if (pmg) per_mode_seq(c, m, m.lam_c, CHEB_RATIO_C, sc, &t.inv_theta_c, &t.alpha_c, &t.beta_c);
   t.zeros = m.mode_arena.alloc<double>(m.ld);
@@ -937,7 +1019,11 @@ static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   t.valid = true;
 }
 
-int64_t precond_scratch_elems(const Mesh &m) { return (m.n_dof + (4 + 3 * (int64_t)m.dim) * m.P) * m.ld; }
+// velocity iterate, pressure polynomials (2 x 2 P), coarse level (3 dim P), and
+// the velocity right-hand side of the block-triangular form (dim N)
+int64_t precond_scratch_elems(const Mesh &m) {
+  return (m.n_dof + (4 + 3 * (int64_t)m.dim) * m.P + (int64_t)m.dim * m.N) * m.ld;
+}
 
 // One Chebyshev step launch over velocity rows and/or pressure rows.
 template <typename T>
@@ -956,7 +1042,7 @@ static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &
     constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
     const int gpb = 256 / L;
     int64_t lo = cc.do_u ? 0 : m.N, hi = (cc.do_m || cc.do_l) ? m.N + m.P : m.N;
-    const unsigned nb = row_blocks(c, hi - lo, gpb);
+    const unsigned nb = row_blocks(c, hi - lo, gpb, a.tile);
     if (m.dim == 2)
       k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
     else
@@ -987,34 +1073,40 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
     KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr);
+      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, 0);
     else
-      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr);
+      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, 0);
     count_launch(c);
     return;
   }
   PcTables &t = m.pc;
   pc_tables(c, m, t);
-  const bool pmg = c.opts.precond == SCVS_PC_BLOCK_PMG;
+  const bool tri = c.opts.precond == SCVS_PC_TRI_PMG;
+  const bool pmg = c.opts.precond == SCVS_PC_BLOCK_PMG || tri;
   const int64_t pblk = m.P * m.ld, cblk = (int64_t)m.dim * m.P * m.ld;
   C *other = scratch;  // velocity part lives in dofs [0, dim N)
   C *pM[2] = {scratch + total, scratch + total + pblk};
   C *pL[2] = {scratch + total + 2 * pblk, scratch + total + 3 * pblk};
   C *rc = scratch + total + 4 * pblk;
   C *zc[2] = {rc + cblk, rc + 2 * cblk};
+  C *rt = rc + 3 * cblk;  // velocity right-hand side of the triangular form
   // the velocity iterate ping-pongs between z and `other`; every Chebyshev
   // step moves it once, so the first iterate goes where the last one lands on z
   const int moves = pmg ? (t.s_u - 1) + t.s_u : (t.s_u - 1);
   C *uA = (moves % 2 == 0) ? z : other;
   C *uB = (uA == z) ? other : z;
   {
-    KScope ks0(c, KC_PRECOND, blk * (rscale ? 3 : 2) + 2 * pb + (double)m.N * 17 + (double)m.P * 17);
+    // tri: pressure rows only (the velocity rows start after the Schur solve)
+    const int64_t f0 = tri ? (int64_t)m.dim * m.N * m.ld : 0;
+    const unsigned nb0 = ceil_div(total - f0, 256);
+    KScope ks0(c, KC_PRECOND, (tri ? 0.0 : 1.0) * (vb * (rscale ? 3 : 2) + (double)m.N * 17) + pb * (rscale ? 4 : 3) +
+                                  (double)m.P * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
-                                                        uA, pM[0], pL[0]);
+      k_pc_step0<T, 2, false><<<nb0, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m,
+                                                         t.inv_theta_l, uA, pM[0], pL[0], f0);
     else
-      k_pc_step0<T, 3, false><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m, t.inv_theta_l,
-                                                        uA, pM[0], pL[0]);
+      k_pc_step0<T, 3, false><<<nb0, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m,
+                                                         t.inv_theta_l, uA, pM[0], pL[0], f0);
     count_launch(c);
   }
   int cm = 0, cl = 0;  // current buffer of each pressure polynomial
@@ -1034,13 +1126,44 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     (void)iu;
     return cc;
   };
+  const C *ru = r;  // right-hand side of the velocity block (rt in the triangular form)
   auto step = [&](ChebCoef cc) {
-    cheb_launch<T>(c, m, a, cc, 0, r, ucur, uprev, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
+    cheb_launch<T>(c, m, a, cc, 0, ru, ucur, uprev, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
     if (cc.do_u) std::swap(ucur, uprev);
     if (cc.do_m) cm = 1 - cm;
     if (cc.do_l) cl = 1 - cl;
     if (cc.do_m || cc.do_l) ++ip;
   };
+  if (tri) {
+    // Schur complement solve z_p = -(mu M_p^-1 + j omega rho L_p^-1) r_p first ...
+    while (ip < t.s_m || ip < t.s_l) step(coef(false, 0, t.zeros, t.zeros, false));
+    {
+      KScope ksk(c, KC_PRECOND, 3 * pb);
+      k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z, T(-1));
+      count_launch(c);
+    }
+    // ... then the velocity block on r_u - D z_p
+    KScope ks(c, KC_PRECOND, vb * (rscale ? 4 : 3) + (double)m.g_nnz * (4 + m.dim * sizeof(T)) + pb +
+                                 (double)(m.N + 1) * 8 + (double)m.N * 17);
+    auto body = [&](auto mpl_c, auto l_c) {
+      constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
+      const int gpb = 256 / L;
+      const unsigned nb = row_blocks(c, m.N, gpb, a.tile);
+      const C *zp = z + (int64_t)m.dim * m.N * m.ld;
+      if (m.dim == 2)
+        k_tri_vel0<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, zp, rt, uA);
+      else
+        k_tri_vel0<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, zp, rt, uA);
+    };
+    if constexpr (sizeof(T) == 4) {
+      const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
+      SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+    } else {
+      SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+    }
+    count_launch(c);
+    ru = rt;
+  }
   // (pre-)smoothing / velocity polynomial, pressure polynomials alongside
   for (int i = 1; i < t.s_u; ++i)
     step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, i == 1));
@@ -1051,11 +1174,11 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
       auto body = [&](auto mpl_c, auto l_c) {
         constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
         const int gpb = 256 / L;
-        const unsigned nb = row_blocks(c, m.N, gpb);
+        const unsigned nb = row_blocks(c, m.N, gpb, a.tile);
         if (m.dim == 2)
-          k_vel_residual<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
+          k_vel_residual<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, ru, ucur, uprev);
         else
-          k_vel_residual<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, ucur, uprev);
+          k_vel_residual<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, ru, ucur, uprev);
       };
       if constexpr (sizeof(T) == 4) {
         const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
@@ -1084,7 +1207,7 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
       KScope ks(c, KC_PRECOND, cb);
       SCVS_DISPATCH_LD(T, m.ld, {
         const int gpb = 256 / L;
-        const unsigned nb = row_blocks(c, (pcf.do_m || pcf.do_l) ? 2 * m.P : m.P, gpb);
+        const unsigned nb = row_blocks(c, (pcf.do_m || pcf.do_l) ? 2 * m.P : m.P, gpb, a.tile);
         if (m.dim == 2)
           k_coarse_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(
               a, t.alpha_c + (size_t)i * m.ld, t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i], zc[1 - cc_i], pcf,
@@ -1110,12 +1233,13 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     for (int i = 1; i < t.s_u; ++i)
       step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, false));
   }
+  if (ucur != z) throw (int)SCVS_ERR_STATE;  // buffer bookkeeping invariant
+  if (tri) return;
   // remaining pressure steps
   while (ip < t.s_m || ip < t.s_l) step(coef(false, 0, t.zeros, t.zeros, false));
-  if (ucur != z) throw (int)SCVS_ERR_STATE;  // buffer bookkeeping invariant
   {
     KScope ksk(c, KC_PRECOND, 3 * pb);
-    k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z);
+    k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z, T(1));
     count_launch(c);
   }
 }
@@ -1378,11 +1502,12 @@ void autotune_shapes(Ctx &c, Mesh &m) {
   SCVS_CUDA(cudaEventCreate(&e1));
   const bool timers_on = c.timers.on;
   c.timers.on = false;
-  m.tune_us.assign(6, 0.0f);
+  constexpr int NT = (int)(sizeof(SCVS_TILES) / sizeof(SCVS_TILES[0]));
+  m.tune_us.assign(2 * 3 * NT, 0.0f);  // [SpMM | Chebyshev][MPL 1, 2, 4][tile]
   auto time_it = [&](auto &&launch) {
     launch();
     float best = 1e30f;
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 2; ++r) {
       SCVS_CUDA(cudaEventRecord(e0, c.stream));
       launch();
       SCVS_CUDA(cudaEventRecord(e1, c.stream));
@@ -1393,27 +1518,34 @@ void autotune_shapes(Ctx &c, Mesh &m) {
     }
     return best * 1e3f;
   };
-  const PcArgs pa = pc_args<float>(m);
   ChebCoef cc{};
   cc.do_u = 1;
   cc.alpha_u = zeros;
   cc.beta_u = zeros;
   cc.prev_zero_u = 1;
-  int best_s = 0, best_c = 0;
+  int best_s[2] = {0, 0}, best_c[2] = {0, 0};
   float tb_s = 1e30f, tb_c = 1e30f;
-  for (int mpl : {1, 2, 4}) {
+  for (int mi = 0; mi < 3; ++mi) {
+    const int mpl = 1 << mi;
     if (!shape_valid(m.ld, mpl)) continue;
-    m.mpl_spmm = mpl;
-    const float ts = time_it([&]() { apply_saddle<float>(c, m, x, y); });
-    m.mpl_cheb = mpl;
-    const float tc = time_it([&]() { cheb_launch<float>(c, m, pa, cc, 1, x, x, y, nullptr, nullptr, nullptr, nullptr); });
-    m.tune_us[mpl == 4 ? 2 : mpl - 1] = ts;
-    m.tune_us[3 + (mpl == 4 ? 2 : mpl - 1)] = tc;
-    if (ts < tb_s) { tb_s = ts; best_s = mpl; }
-    if (tc < tb_c) { tb_c = tc; best_c = mpl; }
+    for (int ti = 0; ti < NT; ++ti) {
+      m.mpl_spmm = mpl;
+      m.tile_spmm = SCVS_TILES[ti];
+      const float ts = time_it([&]() { apply_saddle<float>(c, m, x, y); });
+      m.mpl_cheb = mpl;
+      m.tile_cheb = SCVS_TILES[ti];
+      const PcArgs pa = pc_args<float>(m);
+      const float tc = time_it([&]() { cheb_launch<float>(c, m, pa, cc, 1, x, x, y, nullptr, nullptr, nullptr, nullptr); });
+      m.tune_us[mi * NT + ti] = ts;
+      m.tune_us[(3 + mi) * NT + ti] = tc;
+      if (ts < tb_s) { tb_s = ts; best_s[0] = mpl; best_s[1] = SCVS_TILES[ti]; }
+      if (tc < tb_c) { tb_c = tc; best_c[0] = mpl; best_c[1] = SCVS_TILES[ti]; }
+    }
   }
-  m.mpl_spmm = best_s;
-  m.mpl_cheb = best_c;
+  m.mpl_spmm = best_s[0];
+  m.tile_spmm = best_s[1];
+  m.mpl_cheb = best_c[0];
+  m.tile_cheb = best_c[1];
   c.timers.on = timers_on;
   SCVS_CUDA(cudaEventDestroy(e0));
   SCVS_CUDA(cudaEventDestroy(e1));

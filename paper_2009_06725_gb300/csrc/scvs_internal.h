@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <map>
 #include <string>
 #include <vector>
 #include "../../include/scvs.h"
@@ -144,6 +145,7 @@ struct Mesh {
   double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
   PcTables pc;
   int mpl_spmm = 0, mpl_cheb = 0;       // autotuned row-group shapes (0: default)
+  int tile_spmm = 0, tile_cheb = 0;     // autotuned row tiles (0: default)
   std::vector<float> tune_us;            // measured candidates: [spmm mpl=1,2,4, cheb mpl=1,2,4] (us, 0 = n/a)
   std::vector<double> feat;      // [m][5] features of the modes (learned guess)
   bool solved = false;
@@ -210,6 +212,10 @@ struct Ctx {
   RefTables ref2, ref3;
   KTimers timers;
   GuessModel guess;
+  // autotuned launch shapes by mesh size (dim, N, P, S nonzeros, G nonzeros,
+  // mode stride, components): the timings depend on the pattern's size, not its values
+  struct TuneRec { int mpl_spmm, tile_spmm, mpl_cheb, tile_cheb; std::vector<float> us; };
+  std::map<std::vector<int64_t>, TuneRec> tune_cache;
 };
 
 // Scoped timing of one launch: KT(c, class, algorithmic bytes) { launch; }

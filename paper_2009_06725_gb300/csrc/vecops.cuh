@@ -142,4 +142,20 @@ inline bool shape_valid(int ld, int mpl) { return mpl >= 1 && mpl <= 4 && ld % m
     }                                                                          \
   } while (0)
 
+// Row scheduling of the gather kernels.  Rows [lo, hi) are cut into tiles of
+// gpb * tile consecutive rows; block b takes tiles b, b + gridDim.x, ... and
+// its row groups walk a tile's rows in order.  Consecutive rows of a mesh
+// share most of their neighbours, so a larger tile keeps the gathered vector
+// entries in the SM's L1 across rows; tile 1 is a plain grid-stride loop.
+#define SCVS_ROW_LOOP(row, lo, hi, gpb, group, tile)                                                  \
+  for (int64_t row##_t0 = (int64_t)(lo) + (int64_t)blockIdx.x * (gpb) * (tile); row##_t0 < (int64_t)(hi); \
+       row##_t0 += (int64_t)gridDim.x * (gpb) * (tile))                                                \
+    for (int64_t row = row##_t0 + (group),                                                            \
+                 row##_te = min(row##_t0 + (int64_t)(gpb) * (tile), (int64_t)(hi));                   \
+         row < row##_te; row += (gpb))
+
+// candidate row tiles of the autotuner (rows per tile = row groups per block x tile)
+constexpr int SCVS_TILES[5] = {1, 2, 4, 8, 16};
+constexpr int SCVS_DEFAULT_TILE = 4;
+
 }  // namespace scvs

@@ -22,11 +22,13 @@ SCVS_ERR_OOM, SCVS_ERR_CUDA, SCVS_ERR_STATE, SCVS_ERR_TIMEOUT = -4, -5, -6, -7
 SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET = 1, 2, 4
 SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
-SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG = 0, 1, 2
+SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG = 0, 1, 2, 3
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
 SCVS_KC_COUNT = 9
 SCVS_RECON_STATIC_MAX = 8192
+SCVS_TUNE_TILES = 5
+TUNE_TILES = (1, 2, 4, 8, 16)
 STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "stagnated", 3: "non_finite"}
 
 
@@ -39,7 +41,7 @@ class scvs_opts(C.Structure):
 
 class scvs_mode_report(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("cycles", C.c_int32),
-                ("guess_used", C.c_int32), ("rel_res", C.c_double)]
+                ("guess_used", C.c_int32), ("rel_res", C.c_double), ("res0", C.c_double)]
 
 
 class scvs_train_opts(C.Structure):
@@ -100,7 +102,7 @@ SIGNATURES = {
     "scvs_mlp_forward_dev": (_I32, [_P, _P, _I64, _P]),
     "scvs_mlp_gradient_dev": (_I32, [_P, _P, _P, _I64, _P, C.POINTER(_D)]),
     "scvs_mlp_adam_step": (_I32, [_P, _D]),
-    "scvs_tuned_shapes": (_I32, [_P, _I32, C.POINTER(_I32), C.POINTER(_I32), _P]),
+    "scvs_tuned_shapes": (_I32, [_P, _I32, _P, _P]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
 }
@@ -207,11 +209,11 @@ def scvs_set_modes_dev(ctx, mesh_id, omega, g_dev):
 
 
 def scvs_solve(ctx, mesh_id=-1, n_reports=0):
-    """Returns a list of dicts (status, iterations, cycles, rel_res)."""
+    """Returns a list of dicts (status, iterations, cycles, rel_res, guess_used, res0)."""
     rep = (scvs_mode_report * max(1, n_reports))()
     _check(ctx, lib().scvs_solve(ctx, mesh_id, rep, n_reports))
     return [dict(status=r.status, iterations=r.iterations, cycles=r.cycles, rel_res=r.rel_res,
-                 guess_used=r.guess_used) for r in rep[:n_reports]]
+                 guess_used=r.guess_used, res0=r.res0) for r in rep[:n_reports]]
 
 
 def scvs_get_modal(ctx, mesh_id, n_modes, n_nodes, dim, n_vertices):
@@ -368,10 +370,15 @@ def scvs_mlp_adam_step(ctx, lr):
 
 
 def scvs_tuned_shapes(ctx, mesh_id):
-    a, b = C.c_int32(), C.c_int32()
-    us = np.zeros(6, dtype=np.float32)
-    _check(ctx, lib().scvs_tuned_shapes(ctx, mesh_id, C.byref(a), C.byref(b), _ptr(us)))
-    return dict(mpl_spmm=a.value, mpl_cheb=b.value, spmm_us=us[:3].tolist(), cheb_us=us[3:].tolist())
+    """Autotuned launch shapes of a mesh and the candidate times (us) as
+    {kernel: [[t(mpl, tile) for tile in TUNE_TILES] for mpl in (1, 2, 4)]}."""
+    shape = np.zeros(4, dtype=np.int32)
+    nt = len(TUNE_TILES)
+    us = np.zeros(2 * 3 * nt, dtype=np.float32)
+    _check(ctx, lib().scvs_tuned_shapes(ctx, mesh_id, _ptr(shape), _ptr(us)))
+    us = us.reshape(2, 3, nt).round(1).tolist()
+    return dict(mpl_spmm=int(shape[0]), tile_spmm=int(shape[1]), mpl_cheb=int(shape[2]), tile_cheb=int(shape[3]),
+                spmm_us=us[0], cheb_us=us[1])
 
 
 def scvs_kernel_timers(ctx, enable):

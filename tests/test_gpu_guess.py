@@ -116,7 +116,7 @@ def test_learned_guess_reduces_iterations():
         assert info["n_snapshots"] == 12 * 16
         loss = scvs.scvs_train_guess(s.ctx, scvs.scvs_default_train_opts(n_pod=16, steps=1500, batch=64))
         assert np.isfinite(loss)
-        it0, it1, used = [], [], []
+        it0, it1, used, res0 = [], [], [], []
         for wl, f in test:
             res = {}
             for guess in (scvs.SCVS_GUESS_ZERO, scvs.SCVS_GUESS_MLP):
@@ -133,8 +133,13 @@ def test_learned_guess_reduces_iterations():
             it0 += [r["iterations"] for r in res[scvs.SCVS_GUESS_ZERO][0]]
             it1 += [r["iterations"] for r in res[scvs.SCVS_GUESS_MLP][0]]
             used += [r["guess_used"] for r in res[scvs.SCVS_GUESS_MLP][0]]
+            res0 += [r["res0"] for r in res[scvs.SCVS_GUESS_MLP][0] if r["guess_used"]]
+            assert all(abs(r["res0"] - 1.0) < 1e-12 for r in res[scvs.SCVS_GUESS_ZERO][0])
             X0, X1 = res[scvs.SCVS_GUESS_ZERO][1], res[scvs.SCVS_GUESS_MLP][1]
             for k in range(len(f)):
                 assert np.linalg.norm(X1[k] - X0[k]) <= 1e-6 * np.linalg.norm(X0[k])
-    assert sum(used) > 0
-    assert np.mean(it1) < 0.9 * np.mean(it0), (np.mean(it0), np.mean(it1))
+    # the guess is kept on most held-out modes, starts well inside the zero
+    # start's residual and saves Arnoldi steps
+    assert sum(used) >= len(used) // 2, used
+    assert np.median(res0) < 0.5, res0
+    assert np.mean(it1) < np.mean(it0), (np.mean(it0), np.mean(it1))
