@@ -1,6 +1,6 @@
-// Batched restarted GMRES over all modes of a mesh (one independent Krylov
-// space per mode), right-preconditioned, with an FP64 iterative-refinement
-// outer loop.
+// Batched restarted flexible GMRES over all modes of a mesh (one independent
+// Krylov space per mode), right-preconditioned, with an FP64
+// iterative-refinement outer loop.
 //
 // The paper solves each mode's system with complex GMRES and a Jacobi
 // preconditioner (Sec. 2.3); its convergence test is the relative residual
@@ -14,8 +14,10 @@
 //      subtracts the projections (classical Gram-Schmidt), writes v_{j+1},
 //      reduces its norm and updates the Hessenberg column with complex Givens
 //      rotations in FP64,
-//   3. solves the small triangular systems (FP64), forms d = P^-1 V y and adds
-//      it to x in FP64.
+//   3. solves the small triangular systems (FP64), forms d = Z y from the kept
+//      preconditioned vectors z_j (flexible GMRES, so the correction is exact
+//      for whatever the preconditioner returned, and needs no extra
+//      application of it) and adds it to x in FP64.
 // The FP32 Krylov bulk therefore only ever computes corrections; the
 // residual, the solution and the Hessenberg least-squares stay in FP64.
 #include <algorithm>
@@ -380,6 +382,7 @@ __global__ void k_combine(const typename cpx<T>::t *__restrict__ V, int64_t vstr
   T re = 0, im = 0;
   for (int i = 0; i < nv; ++i) {
     const double2 yy = y[(int64_t)i * S + sys];
+    if (yy.x == 0.0 && yy.y == 0.0) continue;  // steps beyond this system's Krylov dimension
     const auto v = V[(int64_t)i * vstride + f];
     re += (T)yy.x * v.x - (T)yy.y * v.y;
     im += (T)yy.x * v.y + (T)yy.y * v.x;
@@ -474,7 +477,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   Work<T> wk;
   wk.s = c.stream;
   wk.V = wk.template get<C>((size_t)(m_r + 1) * total);
-  wk.Z = wk.template get<C>(total);
+  wk.Z = wk.template get<C>((size_t)m_r * total);  // flexible GMRES: z_j = P^-1 v_j kept
   wk.W = wk.template get<C>(total);
   wk.S = wk.template get<C>(precond_scratch_elems(m));
   int grid, block;
@@ -605,9 +608,9 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
     SCVS_CUDA(cudaMemsetAsync(wk.kdim, 0, S * sizeof(int), c.stream));
     // 3. Arnoldi steps
     for (int j = 0; j < m_r; ++j) {
-      C *Vj = wk.V + (int64_t)j * total;
-      apply_precond<T>(c, m, Vj, wk.Z, wk.S, wk.rscale);  // normalizes v_j in place
-      apply_saddle<T>(c, m, wk.Z, wk.W);
+      C *Vj = wk.V + (int64_t)j * total, *Zj = wk.Z + (int64_t)j * total;
+      apply_precond<T>(c, m, Vj, Zj, wk.S, wk.rscale);  // normalizes v_j in place
+      apply_saddle<T>(c, m, Zj, wk.W);
       SCVS_CUDA(cudaMemsetAsync(wk.n_active, 0, sizeof(int), c.stream));
       launch_arnoldi<T>(c, aa, j, grid, block, smem);
       SCVS_CUDA(cudaMemcpyAsync(h_active, wk.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
@@ -642,14 +645,13 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
     if (nvmax > 0) {
       {
         KScope ks(c, KC_VECTOR, (double)(nvmax + 1) * total * 2 * sizeof(T));
-        k_combine<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.V, total, wk.y, nvmax, ld, S, m.dof_comp, wk.upd, total,
+        k_combine<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.Z, total, wk.y, nvmax, ld, S, m.dof_comp, wk.upd, total,
                                                          wk.W);
         count_launch(c);
       }
-      apply_precond<T>(c, m, wk.W, wk.Z, wk.S, nullptr);
       {
         KScope ks(c, KC_VECTOR, (double)total * (32 + 2 * sizeof(T)));
-        k_add_to_x<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.Z, wk.upd, ld, m.dof_comp, total, m.x);
+        k_add_to_x<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.W, wk.upd, ld, m.dof_comp, total, m.x);
         count_launch(c);
       }
     }

@@ -439,17 +439,16 @@ __device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, int k) {
 // (and write it back); z_u = r / (diag A_r theta_u[k]); pressure: zM = r/(diag M_p theta_M),
 // zL = r/(diag L_p theta_L) with r zeroed at outlet vertices.  Block-diagonal
 // mode: z_u = r / diag A_r, z_p = (mu/diag M_p + j omega rho/diag L_p) r.
-// f0 > 0 starts the pass at element f0 (f0 = DIM N ld: pressure rows only).
+// The pass covers elements [0, f1) of the block (f1 = DIM N ld: velocity rows only).
 template <typename T, int DIM, bool DIAG>
 __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *__restrict__ rscale,
                            const int32_t *__restrict__ dof_comp,
                            const double *__restrict__ inv_theta_u, double inv_theta_m, double inv_theta_l,
                            typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zM,
-                           typename cpx<T>::t *__restrict__ zL, int64_t f0) {
+                           typename cpx<T>::t *__restrict__ zL, int64_t f1) {
   using C = typename cpx<T>::t;
-  const int64_t total = ((int64_t)DIM * a.N + a.P) * a.ld;
-  int64_t f = f0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= total) return;
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= f1) return;
   const int64_t dof = f / a.ld;
   const int k = (int)(f % a.ld);
   if (row_idle(a.dof_comp, a.comp_active, dof)) return;
@@ -554,21 +553,16 @@ __device__ __forceinline__ void pressure_row_step(const PcArgs &a, const ChebCoe
 template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
 k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restrict__ r,
-          const typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zu_prev,
-          const typename cpx<T>::t *__restrict__ zM, typename cpx<T>::t *__restrict__ zM_prev,
-          const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ zL_prev) {
+          const typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zu_prev) {
   using C = typename cpx<T>::t;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
   const unsigned gm = group_mask<L>();
   const int ld = a.ld, koff = lane * MPL;
-  const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv, *Mpv = (const T *)a.Mpv, *Lpv = (const T *)a.Lpv;
-  const int64_t row_lo = cc.do_u ? 0 : a.N;
-  const int64_t row_hi = (cc.do_m || cc.do_l) ? a.N + a.P : a.N;
-  SCVS_ROW_LOOP(row, row_lo, row_hi, gpb, group, a.tile) {
-    if (row_idle(a.dof_comp, a.comp_active, row < a.N ? row * DIM : (int64_t)DIM * a.N + (row - a.N))) continue;
-    if (row < a.N) {
-      const int64_t A = row;
+  const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv;
+  SCVS_ROW_LOOP(A, 0, a.N, gpb, group, a.tile) {
+    if (row_idle(a.dof_comp, a.comp_active, A * DIM)) continue;
+    {
       if (a.dirmask[A]) {
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
@@ -631,8 +625,6 @@ k_pc_cheb(const PcArgs a, const ChebCoef cc, const typename cpx<T>::t *__restric
         }
         stv<T, MPL>(zu_prev + f0, o);
       }
-    } else {
-      pressure_row_step<T, MPL, L, DIM>(a, cc, row - a.N, r, zM, zM_prev, zL, zL_prev, lane, gm);
     }
   }
 }
@@ -701,27 +693,6 @@ k_vel_residual(const PcArgs a, const typename cpx<T>::t *__restrict__ r, const t
   }
 }
 
-// rc = P^T rr on the vertices: own value plus half of every incident edge
-// node (the transpose of P2 interpolation of a P1 field); zero on Dirichlet vertices.
-template <typename T>
-__global__ void k_restrict(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ rr,
-                           typename cpx<T>::t *__restrict__ rc) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t per = (int64_t)dim * a.ld;
-  if (f >= a.P * per) return;
-  const int64_t v = f / per, rem = f % per;
-  if (row_idle(a.dof_comp, a.comp_active, v * dim)) return;
-  if (a.dirmask[v]) { rc[f] = mk<T>(0, 0); return; }
-  auto s = rr[v * per + rem];
-  T xr = s.x, xi = s.y;
-  for (int64_t i = a.v2e_ptr[v]; i < a.v2e_ptr[v + 1]; ++i) {
-    const auto e = rr[(int64_t)a.v2e[i] * per + rem];
-    xr += T(0.5) * e.x;
-    xi += T(0.5) * e.y;
-  }
-  rc[f] = mk<T>(xr, xi);
-}
-
 // z += P zc on the free velocity nodes (vertices copy, edge nodes average their ends).
 template <typename T>
 __global__ void k_prolong(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zc,
@@ -753,96 +724,203 @@ __device__ __forceinline__ T coarse_dinv(const PcArgs &a, int64_t v, int k) {
   return T(1) / ((T)a.mu * ((const T *)a.k1d)[v] + ((const T *)a.wabs)[k] * ((const T *)a.mpd)[v]);
 }
 
+// rc = P^T rr at element f of the coarse block [P][dim][ld]: own value plus
+// half of every incident edge node (the transpose of P2 interpolation of a P1
+// field); zero on Dirichlet vertices.
 template <typename T>
-__global__ void k_coarse_step0(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ rc,
-                               const double *__restrict__ inv_theta, typename cpx<T>::t *__restrict__ zc) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void restrict_elem(const PcArgs &a, int dim, const typename cpx<T>::t *__restrict__ rr,
+                                              typename cpx<T>::t *__restrict__ rc, int64_t f) {
   const int64_t per = (int64_t)dim * a.ld;
-  if (f >= a.P * per) return;
-  const int64_t v = f / per;
-  const int k = (int)(f % a.ld);
+  const int64_t v = f / per, rem = f % per;
   if (row_idle(a.dof_comp, a.comp_active, v * dim)) return;
-  if (a.dirmask[v]) { zc[f] = mk<T>(0, 0); return; }
-  const T s = coarse_dinv<T>(a, v, k) * (T)inv_theta[k];
-  const auto r = rc[f];
-  zc[f] = mk<T>(s * r.x, s * r.y);
+  if (a.dirmask[v]) { rc[f] = mk<T>(0, 0); return; }
+  auto s = rr[v * per + rem];
+  T xr = s.x, xi = s.y;
+  for (int64_t i = a.v2e_ptr[v]; i < a.v2e_ptr[v + 1]; ++i) {
+    const auto e = rr[(int64_t)a.v2e[i] * per + rem];
+    xr += T(0.5) * e.x;
+    xi += T(0.5) * e.y;
+  }
+  rc[f] = mk<T>(xr, xi);
 }
 
-// Coarse Chebyshev step: zc_next = zc + alpha (zc - zc_prev) + beta D_c^-1 (rc - A_c zc),
-// written over zc_prev.
+// One coarse Chebyshev step on vertex row v (all components, the lane's modes):
+// zc_next = zc + alpha (zc - zc_prev) + beta D_c^-1 (rc - A_c zc), written over zc_prev.
 template <typename T, int MPL, int L, int DIM>
-__global__ void __launch_bounds__(256)
-k_coarse_cheb(const PcArgs a, const double *__restrict__ alpha, const double *__restrict__ beta, int prev_zero,
-              const typename cpx<T>::t *__restrict__ rc, const typename cpx<T>::t *__restrict__ zc,
-              typename cpx<T>::t *__restrict__ zc_prev, const ChebCoef pc, const typename cpx<T>::t *__restrict__ r,
-              const typename cpx<T>::t *__restrict__ zM, typename cpx<T>::t *__restrict__ zM_prev,
-              const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ zL_prev) {
+__device__ __forceinline__ void coarse_row_step(const PcArgs &a, const double *__restrict__ alpha,
+                                                const double *__restrict__ beta, bool prev_zero,
+                                                const typename cpx<T>::t *__restrict__ rc,
+                                                const typename cpx<T>::t *__restrict__ zc,
+                                                typename cpx<T>::t *__restrict__ zc_prev, const int64_t v,
+                                                const int lane, const unsigned gm) {
   using C = typename cpx<T>::t;
-  const int gpb = blockDim.x / L;
-  const int lane = threadIdx.x % L, group = threadIdx.x / L;
-  const unsigned gm = group_mask<L>();
   const int ld = a.ld, koff = lane * MPL;
+  if (a.dirmask[v]) {
+    CV<T, MPL> zz;
+    zz.zero();
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) stv<T, MPL>(zc_prev + (v * DIM + c) * ld + koff, zz);
+    return;
+  }
   const T *Kc = (const T *)a.Kcv, *Mc = (const T *)a.Mcv;
   T cr[MPL];
 #pragma unroll
   for (int i = 0; i < MPL; ++i) cr[i] = ((const T *)a.wabs)[koff + i];
   const T mu = (T)a.mu;
-  // rows [0, P): coarse velocity step; rows [P, 2P): a pressure step when requested
-  const int64_t rows = (pc.do_m || pc.do_l) ? 2 * a.P : a.P;
-  SCVS_ROW_LOOP(v, 0, rows, gpb, group, a.tile) {
-    if (row_idle(a.dof_comp, a.comp_active, v < a.P ? v * DIM : (int64_t)DIM * a.N + (v - a.P))) continue;
-    if (v >= a.P) {
-      pressure_row_step<T, MPL, L, DIM>(a, pc, v - a.P, r, zM, zM_prev, zL, zL_prev, lane, gm);
-      continue;
-    }
-    if (a.dirmask[v]) {
-      CV<T, MPL> zz;
-      zz.zero();
+  CV<T, MPL> acc[DIM];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) stv<T, MPL>(zc_prev + (v * DIM + c) * ld + koff, zz);
-      continue;
-    }
-    CV<T, MPL> acc[DIM];
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) acc[c].zero();
-    const int64_t r0 = a.g_ptr[v], r1 = a.g_ptr[v + 1], s0 = a.s_ptr[v];
-    for (int64_t base = r0; base < r1; base += L) {
-      const int64_t t = base + lane;
-      int32_t col = 0;
-      T kv = 0, mv = 0;
-      if (t < r1) { col = __ldg(a.s_col + s0 + (t - r0)); kv = __ldg(Kc + t); mv = __ldg(Mc + t); }
-      const int cnt = (int)min((int64_t)L, r1 - base);
+  for (int c = 0; c < DIM; ++c) acc[c].zero();
+  const int64_t r0 = a.g_ptr[v], r1 = a.g_ptr[v + 1], s0 = a.s_ptr[v];
+  for (int64_t base = r0; base < r1; base += L) {
+    const int64_t t = base + lane;
+    int32_t col = 0;
+    T kv = 0, mv = 0;
+    if (t < r1) { col = __ldg(a.s_col + s0 + (t - r0)); kv = __ldg(Kc + t); mv = __ldg(Mc + t); }
+    const int cnt = (int)min((int64_t)L, r1 - base);
 #pragma unroll 4
-      for (int q = 0; q < cnt; ++q) {
-        const int32_t B = gshfl<L>(gm, col, q);
-        const T kq = mu * gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
+    for (int q = 0; q < cnt; ++q) {
+      const int32_t B = gshfl<L>(gm, col, q);
+      const T kq = mu * gshfl<L>(gm, kv, q), mq = gshfl<L>(gm, mv, q);
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) {
-          CV<T, MPL> xv;
-          ldv<T, MPL>(xv, zc + ((int64_t)B * DIM + c) * ld + koff);
+      for (int c = 0; c < DIM; ++c) {
+        CV<T, MPL> xv;
+        ldv<T, MPL>(xv, zc + ((int64_t)B * DIM + c) * ld + koff);
 #pragma unroll
-          for (int i = 0; i < MPL; ++i) {
-            const T cf = kq + cr[i] * mq;
-            acc[c].re[i] = fma(cf, xv.re[i], acc[c].re[i]);
-            acc[c].im[i] = fma(cf, xv.im[i], acc[c].im[i]);
-          }
+        for (int i = 0; i < MPL; ++i) {
+          const T cf = kq + cr[i] * mq;
+          acc[c].re[i] = fma(cf, xv.re[i], acc[c].re[i]);
+          acc[c].im[i] = fma(cf, xv.im[i], acc[c].im[i]);
         }
       }
     }
+  }
 #pragma unroll
-    for (int i = 0; i < MPL; ++i) {
-      const int k = koff + i;
-      const T d = coarse_dinv<T>(a, v, k);
-      const T al = (T)alpha[k], be = (T)beta[k];
+  for (int i = 0; i < MPL; ++i) {
+    const int k = koff + i;
+    const T d = coarse_dinv<T>(a, v, k);
+    const T al = (T)alpha[k], be = (T)beta[k];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        const int64_t f = (v * DIM + c) * ld + k;
-        const C rv = rc[f], zv = zc[f];
-        const C zp = prev_zero ? mk<T>(0, 0) : zc_prev[f];
-        zc_prev[f] = mk<T>(zv.x + al * (zv.x - zp.x) + be * d * (rv.x - acc[c].re[i]),
-                           zv.y + al * (zv.y - zp.y) + be * d * (rv.y - acc[c].im[i]));
-      }
+    for (int c = 0; c < DIM; ++c) {
+      const int64_t f = (v * DIM + c) * ld + k;
+      const C rv = rc[f], zv = zc[f];
+      const C zp = prev_zero ? mk<T>(0, 0) : zc_prev[f];
+      zc_prev[f] = mk<T>(zv.x + al * (zv.x - zp.x) + be * d * (rv.x - acc[c].re[i]),
+                         zv.y + al * (zv.y - zp.y) + be * d * (rv.y - acc[c].im[i]));
     }
+  }
+}
+
+// Coarse (P1) velocity solve of the two-level cycle as one cooperative launch:
+// restriction rc = P^T rr, step 0 zc = rc / (diag A_c theta_c[k]) and s_c - 1
+// Chebyshev steps, with a bounded grid barrier between the stages (a barrier
+// that gives up sets the context's error word and every block returns).  The
+// result is in zc[(s_c - 1) % 2].
+template <typename T> struct CoarseArgs {
+  const typename cpx<T>::t *rr;  // fine velocity residual [N][dim][ld]
+  typename cpx<T>::t *rc;        // coarse right-hand side [P][dim][ld]
+  typename cpx<T>::t *zc0, *zc1;
+  const double *inv_theta, *alpha, *beta;  // [ld], [s_c][ld], [s_c][ld]
+  int s_c;
+  GridSync *gs;
+};
+
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256, 3) k_coarse_solve(const PcArgs a, const CoarseArgs<T> q) {
+  const int64_t nc = a.P * DIM * a.ld;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t f = tid; f < nc; f += nth) restrict_elem<T>(a, DIM, q.rr, q.rc, f);
+  if (!grid_sync(q.gs, gridDim.x)) return;
+  for (int64_t f = tid; f < nc; f += nth) {
+    const int64_t v = f / ((int64_t)DIM * a.ld);
+    const int k = (int)(f % a.ld);
+    if (row_idle(a.dof_comp, a.comp_active, v * DIM)) continue;
+    const T sc = a.dirmask[v] ? T(0) : coarse_dinv<T>(a, v, k) * (T)q.inv_theta[k];
+    const auto r = q.rc[f];
+    q.zc0[f] = mk<T>(sc * r.x, sc * r.y);
+  }
+  if (!grid_sync(q.gs, gridDim.x)) return;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  typename cpx<T>::t *zcur = q.zc0, *znext = q.zc1;
+  for (int i = 1; i < q.s_c; ++i) {
+    for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < a.P; v += (int64_t)gridDim.x * gpb) {
+      if (row_idle(a.dof_comp, a.comp_active, v * DIM)) continue;
+      coarse_row_step<T, MPL, L, DIM>(a, q.alpha + (size_t)i * a.ld, q.beta + (size_t)i * a.ld, i == 1, q.rc, zcur,
+                                      znext, v, lane, gm);
+    }
+    typename cpx<T>::t *tmp = zcur;
+    zcur = znext;
+    znext = tmp;
+    if (!grid_sync(q.gs, gridDim.x)) return;
+  }
+}
+
+// Pressure block as one cooperative launch: step 0 of the P1 mass and P1
+// Laplacian polynomials (r_p first scaled in place by rscale, if given), their
+// Chebyshev steps with a bounded grid barrier between steps, and
+// z_p = sign (mu zM + j omega rho zL) written to the pressure rows of z.
+template <typename T> struct PressureArgs {
+  typename cpx<T>::t *r;   // the full block; only its pressure rows are read (and scaled)
+  const double *rscale;    // [n_comp][ld] or null
+  double inv_theta_m, inv_theta_l;
+  const double *am, *bm, *al, *bl;  // recurrences, [s_m], [s_l]
+  int s_m, s_l;
+  typename cpx<T>::t *zM0, *zM1, *zL0, *zL1;
+  typename cpx<T>::t *z;
+  T sign;
+  GridSync *gs;
+};
+
+template <typename T, int MPL, int L, int DIM>
+__global__ void __launch_bounds__(256, 3) k_pressure_solve(const PcArgs a, const PressureArgs<T> p) {
+  using C = typename cpx<T>::t;
+  const int ld = a.ld;
+  const int64_t np = a.P * ld, fp = (int64_t)DIM * a.N * ld;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = tid; e < np; e += nth) {
+    const int64_t B = e / ld, dof = (int64_t)DIM * a.N + B;
+    const int k = (int)(e % ld);
+    if (row_idle(a.dof_comp, a.comp_active, dof)) continue;
+    C v = p.r[fp + e];
+    if (p.rscale) {
+      const T sc = (T)p.rscale[(a.dof_comp ? (int64_t)a.dof_comp[dof] * ld : 0) + k];
+      v.x *= sc; v.y *= sc;
+      p.r[fp + e] = v;
+    }
+    const T sm = (T)p.inv_theta_m / ((const T *)a.mpd)[B];
+    p.zM0[e] = mk<T>(v.x * sm, v.y * sm);
+    const T sl = a.outmask[B] ? T(0) : (T)p.inv_theta_l / ((const T *)a.lpd)[B];
+    p.zL0[e] = mk<T>(v.x * sl, v.y * sl);
+  }
+  if (!grid_sync(p.gs, gridDim.x)) return;
+  const int gpb = blockDim.x / L;
+  const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
+  C *mc = p.zM0, *mn = p.zM1, *lc = p.zL0, *ln = p.zL1;  // current / next iterates
+  const int steps = max(p.s_m, p.s_l);
+  for (int ip = 1; ip < steps; ++ip) {
+    ChebCoef cc{};
+    cc.do_m = ip < p.s_m;
+    cc.do_l = ip < p.s_l;
+    cc.alpha_m = cc.do_m ? p.am[ip] : 0.0; cc.beta_m = cc.do_m ? p.bm[ip] : 0.0;
+    cc.alpha_l = cc.do_l ? p.al[ip] : 0.0; cc.beta_l = cc.do_l ? p.bl[ip] : 0.0;
+    cc.prev_zero_m = cc.prev_zero_l = (ip == 1);
+    for (int64_t B = (int64_t)blockIdx.x * gpb + group; B < a.P; B += (int64_t)gridDim.x * gpb) {
+      if (row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + B)) continue;
+      pressure_row_step<T, MPL, L, DIM>(a, cc, B, p.r, mc, mn, lc, ln, lane, gm);
+    }
+    if (cc.do_m) { C *t = mc; mc = mn; mn = t; }
+    if (cc.do_l) { C *t = lc; lc = ln; ln = t; }
+    if (!grid_sync(p.gs, gridDim.x)) return;
+  }
+  const T mu = p.sign * (T)a.mu;
+  for (int64_t e = tid; e < np; e += nth) {
+    const int k = (int)(e % ld);
+    if (row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + e / ld)) continue;
+    const T wr = p.sign * ((const T *)a.wrho)[k];
+    const C m_ = mc[e], l_ = lc[e];
+    p.z[fp + e] = mk<T>(mu * m_.x - wr * l_.y, mu * m_.y + wr * l_.x);
   }
 }
 
@@ -918,20 +996,6 @@ k_tri_vel0(const PcArgs a, typename cpx<T>::t *__restrict__ r, const double *__r
       stv<T, MPL>(zu + (A * DIM + c) * ld + koff, o);
     }
   }
-}
-
-// z_p = sign (mu zM + j omega rho zL)
-template <typename T>
-__global__ void k_pc_combine(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zM,
-                             const typename cpx<T>::t *__restrict__ zL, typename cpx<T>::t *__restrict__ z, T sign) {
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= a.P * a.ld) return;
-  const int k = (int)(f % a.ld);
-  if (row_idle(a.dof_comp, a.comp_active, (int64_t)dim * a.N + f / a.ld)) return;
-  const T mu = sign * (T)a.mu, wr = sign * ((const T *)a.wrho)[k];
-  auto m_ = zM[f];
-  auto l_ = zL[f];
-  z[(int64_t)dim * a.N * a.ld + f] = mk<T>(mu * m_.x - wr * l_.y, mu * m_.y + wr * l_.x);
 }
 
 // Chebyshev recurrence coefficients for the interval [lo, hi] (Saad, Iterative
@@ -1016,6 +1080,14 @@ static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   ChebSeq ql = cheb_seq(m.lam_l / CHEB_RATIO_L, CHEB_TOP * m.lam_l, sl);
   t.inv_theta_m = qm.inv_theta; t.am = qm.alpha; t.bm = qm.beta;
   t.inv_theta_l = ql.inv_theta; t.al = ql.alpha; t.bl = ql.beta;
+  double **dst[4] = {&t.am_d, &t.bm_d, &t.al_d, &t.bl_d};
+  const std::vector<double> *src[4] = {&t.am, &t.bm, &t.al, &t.bl};
+  for (int i = 0; i < 4; ++i) {
+    *dst[i] = m.mode_arena.alloc<double>(src[i]->size());
+    SCVS_CUDA(cudaMemcpyAsync(*dst[i], src[i]->data(), src[i]->size() * sizeof(double), cudaMemcpyHostToDevice,
+                              c.stream));
+  }
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
   t.valid = true;
 }
 
@@ -1025,28 +1097,21 @@ int64_t precond_scratch_elems(const Mesh &m) {
   return (m.n_dof + (4 + 3 * (int64_t)m.dim) * m.P + (int64_t)m.dim * m.N) * m.ld;
 }
 
-// One Chebyshev step launch over velocity rows and/or pressure rows.
+// One Chebyshev step launch over the velocity rows.
 template <typename T>
-static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &cc, int i,
-                        const typename cpx<T>::t *r, const typename cpx<T>::t *ucur, typename cpx<T>::t *uprev,
-                        const typename cpx<T>::t *mcur, typename cpx<T>::t *mprev, const typename cpx<T>::t *lcur,
-                        typename cpx<T>::t *lprev) {
-  const double cs = 2.0 * sizeof(T), pb = (double)m.P * m.ld * cs, vb = (double)m.dim * m.N * m.ld * cs;
-  double cb = 0;
-  if (cc.do_u) cb += (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + vb * (cc.prev_zero_u ? 3 : 4);
-  if (cc.do_m || cc.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb;
-  if (cc.do_m) cb += pb * (cc.prev_zero_m ? 2 : 3);
-  if (cc.do_l) cb += pb * (cc.prev_zero_l ? 2 : 3);
-  KScope ksc(c, cc.do_u ? KC_CHEB_FINE : KC_PRECOND, cb);
+static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &cc, const typename cpx<T>::t *r,
+                        const typename cpx<T>::t *ucur, typename cpx<T>::t *uprev) {
+  const double cs = 2.0 * sizeof(T), vb = (double)m.dim * m.N * m.ld * cs;
+  KScope ksc(c, KC_CHEB_FINE,
+             (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + vb * (cc.prev_zero_u ? 3 : 4));
   auto body = [&](auto mpl_c, auto l_c) {
     constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
     const int gpb = 256 / L;
-    int64_t lo = cc.do_u ? 0 : m.N, hi = (cc.do_m || cc.do_l) ? m.N + m.P : m.N;
-    const unsigned nb = row_blocks(c, hi - lo, gpb, a.tile);
+    const unsigned nb = row_blocks(c, m.N, gpb, a.tile);
     if (m.dim == 2)
-      k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
+      k_pc_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev);
     else
-      k_pc_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev, mcur, mprev, lcur, lprev);
+      k_pc_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, cc, r, ucur, uprev);
   };
   if constexpr (sizeof(T) == 4) {
     const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
@@ -1055,6 +1120,59 @@ static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &
     SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
   }
   count_launch(c);
+}
+
+// Grid of a cooperative launch: every block resident at once (at most 4 per
+// SM, which keeps the barrier's arrival counter short).
+static int coop_grid(Ctx &c, const void *kfn) {
+  int per_sm = 0;
+  SCVS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, 0));
+  if (per_sm < 1) throw (int)SCVS_ERR_CUDA;
+  return std::min(per_sm, 4) * c.num_sms;
+}
+
+template <typename T>
+static void pressure_solve(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t, typename cpx<T>::t *r,
+                           const double *rscale, typename cpx<T>::t *const *pM, typename cpx<T>::t *const *pL,
+                           typename cpx<T>::t *z, T sign) {
+  const double cs = 2.0 * sizeof(T), pb = (double)m.P * m.ld * cs;
+  double by = pb * (rscale ? 4 : 3) + (double)m.P * 2 * sizeof(T) + 3 * pb;  // step 0 and the combination
+  for (int ip = 1; ip < std::max(t.s_m, t.s_l); ++ip) {
+    const int np = (ip < t.s_m) + (ip < t.s_l);
+    by += (double)m.q_nnz * (4 + np * sizeof(T)) + (double)(m.P + 1) * 8 + pb + np * pb * (ip == 1 ? 2 : 3);
+  }
+  KScope ks(c, KC_PRECOND, by);
+  PressureArgs<T> p{r, rscale, t.inv_theta_m, t.inv_theta_l, t.am_d, t.bm_d, t.al_d, t.bl_d, t.s_m, t.s_l,
+                    pM[0], pM[1], pL[0], pL[1], z, sign, c.gsync};
+  PcArgs aa = a;
+  SCVS_DISPATCH_LD(T, m.ld, {
+    const void *kfn = m.dim == 2 ? (const void *)k_pressure_solve<T, MPL, L, 2> : (const void *)k_pressure_solve<T, MPL, L, 3>;
+    void *args[] = {(void *)&aa, (void *)&p};
+    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn)), dim3(256), args, 0, c.stream));
+  });
+  count_launch(c);
+}
+
+// Returns the coarse buffer that holds the result.
+template <typename T>
+static typename cpx<T>::t *coarse_solve(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t,
+                                        const typename cpx<T>::t *rr, typename cpx<T>::t *rc,
+                                        typename cpx<T>::t *const *zc) {
+  const double cs = 2.0 * sizeof(T), cbk = (double)m.dim * m.P * m.ld * cs;
+  double by = (double)m.dim * m.N * m.ld * cs + (double)(m.P + 1) * 8 + (double)(m.N - m.P) * 4 + cbk  // restriction
+              + 2 * cbk + (double)m.P * 2 * sizeof(T);                                                  // step 0
+  for (int i = 1; i < t.s_c; ++i)
+    by += (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 8 + cbk * (i == 1 ? 3 : 4);
+  KScope ks(c, KC_PRECOND, by);
+  CoarseArgs<T> q{rr, rc, zc[0], zc[1], t.inv_theta_c, t.alpha_c, t.beta_c, t.s_c, c.gsync};
+  PcArgs aa = a;
+  SCVS_DISPATCH_LD(T, m.ld, {
+    const void *kfn = m.dim == 2 ? (const void *)k_coarse_solve<T, MPL, L, 2> : (const void *)k_coarse_solve<T, MPL, L, 3>;
+    void *args[] = {(void *)&aa, (void *)&q};
+    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn)), dim3(256), args, 0, c.stream));
+  });
+  count_launch(c);
+  return zc[(t.s_c - 1) % 2];
 }
 
 // z = P^-1 r for all modes (right block preconditioner).  scratch holds
@@ -1073,9 +1191,9 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
     KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, 0);
+      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, total);
     else
-      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, 0);
+      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, total);
     count_launch(c);
     return;
   }
@@ -1095,54 +1213,12 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   const int moves = pmg ? (t.s_u - 1) + t.s_u : (t.s_u - 1);
   C *uA = (moves % 2 == 0) ? z : other;
   C *uB = (uA == z) ? other : z;
-  {
-    // tri: pressure rows only (the velocity rows start after the Schur solve)
-    const int64_t f0 = tri ? (int64_t)m.dim * m.N * m.ld : 0;
-    const unsigned nb0 = ceil_div(total - f0, 256);
-    KScope ks0(c, KC_PRECOND, (tri ? 0.0 : 1.0) * (vb * (rscale ? 3 : 2) + (double)m.N * 17) + pb * (rscale ? 4 : 3) +
-                                  (double)m.P * 17);
-    if (m.dim == 2)
-      k_pc_step0<T, 2, false><<<nb0, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m,
-                                                         t.inv_theta_l, uA, pM[0], pL[0], f0);
-    else
-      k_pc_step0<T, 3, false><<<nb0, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, t.inv_theta_m,
-                                                         t.inv_theta_l, uA, pM[0], pL[0], f0);
-    count_launch(c);
-  }
-  int cm = 0, cl = 0;  // current buffer of each pressure polynomial
-  C *ucur = uA, *uprev = uB;
-  int ip = 1;          // next pressure step
-  auto coef = [&](bool du, int iu, const double *al_u, const double *be_u, bool prev0_u) {
-    ChebCoef cc{};
-    cc.do_u = du;
-    cc.do_m = ip < t.s_m;
-    cc.do_l = ip < t.s_l;
-    cc.alpha_u = al_u;
-    cc.beta_u = be_u;
-    cc.alpha_m = cc.do_m ? t.am[ip] : 0; cc.beta_m = cc.do_m ? t.bm[ip] : 0;
-    cc.alpha_l = cc.do_l ? t.al[ip] : 0; cc.beta_l = cc.do_l ? t.bl[ip] : 0;
-    cc.prev_zero_u = prev0_u;
-    cc.prev_zero_m = cc.prev_zero_l = (ip == 1);
-    (void)iu;
-    return cc;
-  };
-  const C *ru = r;  // right-hand side of the velocity block (rt in the triangular form)
-  auto step = [&](ChebCoef cc) {
-    cheb_launch<T>(c, m, a, cc, 0, ru, ucur, uprev, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
-    if (cc.do_u) std::swap(ucur, uprev);
-    if (cc.do_m) cm = 1 - cm;
-    if (cc.do_l) cl = 1 - cl;
-    if (cc.do_m || cc.do_l) ++ip;
-  };
+  // 1. pressure block: z_p = -/+ (mu M_p^-1 + j omega rho L_p^-1) r_p (minus: Schur
+  //    complement of the triangular form; plus: block-diagonal form)
+  pressure_solve<T>(c, m, a, t, r, rscale, pM, pL, z, tri ? T(-1) : T(1));
+  // 2. velocity right-hand side and step 0 of the velocity polynomial
+  const C *ru = r;
   if (tri) {
-    // Schur complement solve z_p = -(mu M_p^-1 + j omega rho L_p^-1) r_p first ...
-    while (ip < t.s_m || ip < t.s_l) step(coef(false, 0, t.zeros, t.zeros, false));
-    {
-      KScope ksk(c, KC_PRECOND, 3 * pb);
-      k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z, T(-1));
-      count_launch(c);
-    }
-    // ... then the velocity block on r_u - D z_p
     KScope ks(c, KC_PRECOND, vb * (rscale ? 4 : 3) + (double)m.g_nnz * (4 + m.dim * sizeof(T)) + pb +
                                  (double)(m.N + 1) * 8 + (double)m.N * 17);
     auto body = [&](auto mpl_c, auto l_c) {
@@ -1163,12 +1239,31 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     }
     count_launch(c);
     ru = rt;
+  } else {
+    const int64_t fu = (int64_t)m.dim * m.N * m.ld;
+    KScope ks0(c, KC_PRECOND, vb * (rscale ? 3 : 2) + (double)m.N * 17);
+    if (m.dim == 2)
+      k_pc_step0<T, 2, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, 0, 0, uA,
+                                                                     nullptr, nullptr, fu);
+    else
+      k_pc_step0<T, 3, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, 0, 0, uA,
+                                                                     nullptr, nullptr, fu);
+    count_launch(c);
   }
-  // (pre-)smoothing / velocity polynomial, pressure polynomials alongside
-  for (int i = 1; i < t.s_u; ++i)
-    step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, i == 1));
+  C *ucur = uA, *uprev = uB;
+  auto step = [&](const double *al_u, const double *be_u, bool prev0_u) {
+    ChebCoef cc{};
+    cc.do_u = 1;
+    cc.alpha_u = al_u;
+    cc.beta_u = be_u;
+    cc.prev_zero_u = prev0_u;
+    cheb_launch<T>(c, m, a, cc, ru, ucur, uprev);
+    std::swap(ucur, uprev);
+  };
+  // 3. velocity polynomial / pre-smoothing
+  for (int i = 1; i < t.s_u; ++i) step(t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, i == 1);
   if (pmg) {
-    // fine residual, restriction, coarse Chebyshev solve, prolongation
+    // 4. fine residual, coarse solve (restriction + Chebyshev), prolongation
     {
       KScope ks(c, KC_CHEB_FINE, (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + 3 * vb);
       auto body = [&](auto mpl_c, auto l_c) {
@@ -1188,60 +1283,17 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
       }
       count_launch(c);
     }
-    {
-      KScope ks(c, KC_PRECOND, cbk + (double)(m.N - m.P) * m.dim * m.ld * cs + (double)(m.P + 1) * 8 +
-                                   (double)(m.N - m.P) * 8 + cbk);
-      k_restrict<T><<<ceil_div(cblk, 256), 256, 0, c.stream>>>(a, m.dim, uprev, rc);
-      count_launch(c);
-    }
-    {
-      KScope ks(c, KC_PRECOND, 2 * cbk + (double)m.P * 17);
-      k_coarse_step0<T><<<ceil_div(cblk, 256), 256, 0, c.stream>>>(a, m.dim, rc, t.inv_theta_c, zc[0]);
-      count_launch(c);
-    }
-    int cc_i = 0;
-    for (int i = 1; i < t.s_c; ++i) {
-      ChebCoef pcf = coef(false, 0, t.zeros, t.zeros, false);  // pending pressure step, if any
-      double cb = (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 16 + m.P + cbk * (i == 1 ? 3 : 4);
-      if (pcf.do_m || pcf.do_l) cb += (double)m.q_nnz * (4 + 2 * sizeof(T)) + pb * (1 + (pcf.do_m ? 3 : 0) + (pcf.do_l ? 3 : 0));
-      KScope ks(c, KC_PRECOND, cb);
-      SCVS_DISPATCH_LD(T, m.ld, {
-        const int gpb = 256 / L;
-        const unsigned nb = row_blocks(c, (pcf.do_m || pcf.do_l) ? 2 * m.P : m.P, gpb, a.tile);
-        if (m.dim == 2)
-          k_coarse_cheb<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(
-              a, t.alpha_c + (size_t)i * m.ld, t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i], zc[1 - cc_i], pcf,
-              r, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
-        else
-          k_coarse_cheb<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(
-              a, t.alpha_c + (size_t)i * m.ld, t.beta_c + (size_t)i * m.ld, i == 1, rc, zc[cc_i], zc[1 - cc_i], pcf,
-              r, pM[cm], pM[1 - cm], pL[cl], pL[1 - cl]);
-      });
-      count_launch(c);
-      cc_i = 1 - cc_i;
-      if (pcf.do_m) cm = 1 - cm;
-      if (pcf.do_l) cl = 1 - cl;
-      if (pcf.do_m || pcf.do_l) ++ip;
-    }
+    C *zres = coarse_solve<T>(c, m, a, t, uprev, rc, zc);
     {
       KScope ks(c, KC_PRECOND, 2 * vb + cbk + (double)(m.N - m.P) * 8 + m.N);
-      k_prolong<T><<<ceil_div((int64_t)m.dim * m.N * m.ld, 256), 256, 0, c.stream>>>(a, m.dim, zc[cc_i], ucur);
+      k_prolong<T><<<ceil_div((int64_t)m.dim * m.N * m.ld, 256), 256, 0, c.stream>>>(a, m.dim, zres, ucur);
       count_launch(c);
     }
-    // post-smoothing from the corrected iterate: first step z1 = z0 + D^-1 (r - A z0)/theta
-    step(coef(true, 0, t.zeros, t.inv_theta_u, true));
-    for (int i = 1; i < t.s_u; ++i)
-      step(coef(true, i, t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, false));
+    // 5. post-smoothing from the corrected iterate: first step z1 = z0 + D^-1 (r - A z0)/theta
+    step(t.zeros, t.inv_theta_u, true);
+    for (int i = 1; i < t.s_u; ++i) step(t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, false);
   }
   if (ucur != z) throw (int)SCVS_ERR_STATE;  // buffer bookkeeping invariant
-  if (tri) return;
-  // remaining pressure steps
-  while (ip < t.s_m || ip < t.s_l) step(coef(false, 0, t.zeros, t.zeros, false));
-  {
-    KScope ksk(c, KC_PRECOND, 3 * pb);
-    k_pc_combine<T><<<ceil_div(pblk, 256), 256, 0, c.stream>>>(a, m.dim, pM[cm], pL[cl], z, T(1));
-    count_launch(c);
-  }
 }
 template void apply_precond<float>(Ctx &, Mesh &, const float2 *, float2 *, float2 *, const double *);
 template void apply_precond<double>(Ctx &, Mesh &, const double2 *, double2 *, double2 *, const double *);
@@ -1535,7 +1587,7 @@ void autotune_shapes(Ctx &c, Mesh &m) {
       m.mpl_cheb = mpl;
       m.tile_cheb = SCVS_TILES[ti];
       const PcArgs pa = pc_args<float>(m);
-      const float tc = time_it([&]() { cheb_launch<float>(c, m, pa, cc, 1, x, x, y, nullptr, nullptr, nullptr, nullptr); });
+      const float tc = time_it([&]() { cheb_launch<float>(c, m, pa, cc, x, x, y); });
       m.tune_us[mi * NT + ti] = ts;
       m.tune_us[(3 + mi) * NT + ti] = tc;
       if (ts < tb_s) { tb_s = ts; best_s[0] = mpl; best_s[1] = SCVS_TILES[ti]; }

@@ -64,6 +64,7 @@ struct PcTables {
   double *zeros = nullptr;                                                // [ld]
   int s_c = 0, kind = -1;
   std::vector<double> am, bm, al, bl;  // P1 mass / Laplacian recurrences
+  double *am_d = nullptr, *bm_d = nullptr, *al_d = nullptr, *bl_d = nullptr;  // device copies
   double inv_theta_m = 0, inv_theta_l = 0;
   int s_u = 0, s_m = 0, s_l = 0;
   bool valid = false;
