@@ -282,7 +282,7 @@ def run_gpu(args):
     achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     traffic = traffic_from_profiles(dom)
     kernel_names = {"cheb_fine": "k_pc_cheb (velocity rows) + k_vel_residual", "arnoldi": "k_arnoldi",
-                    "spmm_fp32": "k_saddle<float>", "precond": "k_coarse_cheb/k_pc_cheb (pressure)/k_pc_step0/...",
+                    "spmm_fp32": "k_saddle<float>", "precond": "k_pressure_solve + k_coarse_solve + k_tri_vel0 + k_prolong",
                     "spmm_fp64": "k_saddle<double>"}
     roof = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind,
@@ -550,7 +550,7 @@ def main():
     ap.add_argument("--cheb-l", type=int, default=0)
     ap.add_argument("--cheb-c", type=int, default=0)
     ap.add_argument("--restart", type=int, default=0)
-    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG")
+    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG, 3 TRI_PMG (default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")
