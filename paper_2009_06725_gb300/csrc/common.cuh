@@ -75,7 +75,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned int nblocks) {
       while (*vgen == g) {
         if (*verr) { ok = 0; break; }
         if (++spins > SPIN_LIMIT) { atomicExch(&gs->err, 1); ok = 0; break; }
-        __nanosleep(100);
+        if (spins > 4096) __nanosleep(100);  // poll tightly first: most waits are a few microseconds
       }
     }
     __threadfence();

@@ -379,15 +379,36 @@ __global__ void k_combine(const typename cpx<T>::t *__restrict__ V, int64_t vstr
   if (f >= total) return;
   const int sys = (dof_comp ? dof_comp[f / ld] * ld : 0) + (int)(f % ld);
   if (!upd[sys]) return;  // system not updated in this cycle
-  T re = 0, im = 0;
-  for (int i = 0; i < nv; ++i) {
-    const double2 yy = y[(int64_t)i * S + sys];
-    if (yy.x == 0.0 && yy.y == 0.0) continue;  // steps beyond this system's Krylov dimension
-    const auto v = V[(int64_t)i * vstride + f];
-    re += (T)yy.x * v.x - (T)yy.y * v.y;
-    im += (T)yy.x * v.y + (T)yy.y * v.x;
+  // steps beyond this system's Krylov dimension have y = 0; their term is
+  // selected away (not multiplied by 0) so stale vectors never propagate.
+  // Four independent accumulators keep several basis loads in flight.
+  T re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+  int i = 0;
+  for (; i + 4 <= nv; i += 4) {
+    typename cpx<T>::t v[4];
+    double2 yy[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      yy[u] = y[(int64_t)(i + u) * S + sys];
+      v[u] = V[(int64_t)(i + u) * vstride + f];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool z = yy[u].x == 0.0 && yy[u].y == 0.0;
+      const T a = (T)yy[u].x, b = (T)yy[u].y;
+      re[u] += z ? T(0) : a * v[u].x - b * v[u].y;
+      im[u] += z ? T(0) : a * v[u].y + b * v[u].x;
+    }
   }
-  u[f] = mk<T>(re, im);
+  for (; i < nv; ++i) {
+    const double2 yy = y[(int64_t)i * S + sys];
+    const auto v = V[(int64_t)i * vstride + f];
+    const bool z = yy.x == 0.0 && yy.y == 0.0;
+    re[0] += z ? T(0) : (T)yy.x * v.x - (T)yy.y * v.y;
+    im[0] += z ? T(0) : (T)yy.x * v.y + (T)yy.y * v.x;
+  }
+  const T rs = (re[0] + re[1]) + (re[2] + re[3]), is = (im[0] + im[1]) + (im[2] + im[3]);
+  u[f] = mk<T>(rs, is);
 }
 
 template <typename T>

@@ -810,6 +810,182 @@ __device__ __forceinline__ void coarse_row_step(const PcArgs &a, const double *_
   }
 }
 
+// Row cache of the persistent P1 solves.  A row group owns the same rows in
+// every Chebyshev step of a launch, so the first P1_KMAX of them keep their
+// nonzeros in shared memory: entry (col, a, b, 0) with the row's two real
+// matrices (M_p and L_p, or K_1 and M_1), plus one meta entry per row.  A
+// cached step then reads no index or value from L2: it issues the own-row
+// loads and the neighbour gathers back to back.  Rows longer than P1_CAP,
+// beyond P1_KMAX, or of the FP64 path take the uncached step.
+constexpr int P1_CAP = 32, P1_KMAX_P = 3, P1_KMAX_C = 3;
+constexpr size_t P1_SMEM_MAX = 48 * 1024;  // dynamic shared memory without an opt-in
+// rows cached per group so that the cache of gpb groups fits P1_SMEM_MAX
+inline int p1_kmax(int gpb, int kmax) {
+  return std::min<int>(kmax, (int)(P1_SMEM_MAX / ((size_t)gpb * (P1_CAP + 1) * sizeof(float4))));
+}
+
+template <typename T>
+__device__ __forceinline__ void p1_cache_row(const PcArgs &a, const void *va, const void *vb, int64_t v, float4 *ent,
+                                             float4 *meta, float m0, float m1, float m2, int lane, int L) {
+  const int64_t r0 = a.g_ptr[v], r1 = a.g_ptr[v + 1], s0 = a.s_ptr[v];
+  const int n = (int)(r1 - r0);
+  const bool fits = n <= P1_CAP;
+  if (fits)
+    for (int t = lane; t < n; t += L)
+      ent[t] = make_float4(__int_as_float(a.s_col[s0 + t]), ((const float *)va)[r0 + t], ((const float *)vb)[r0 + t], 0.f);
+  if (lane == 0) *meta = make_float4(m0, m1, m2, __int_as_float(fits ? n : -1));
+}
+
+// Cached pressure step on row B (see pressure_row_step): meta = (1/diag M_p,
+// 1/diag L_p, outlet flag, length).  DO_M / DO_L select the active
+// polynomials (uniform per step), so the gathers of four nonzeros are issued
+// together instead of one dependent round trip per nonzero.
+template <typename T, int MPL, int DIM, bool DO_M, bool DO_L>
+__device__ __forceinline__ void pressure_row_cached(const PcArgs &a, const ChebCoef &cc, const int64_t B,
+                                                    const float4 *__restrict__ ent, const float4 mt,
+                                                    const typename cpx<T>::t *__restrict__ r,
+                                                    const typename cpx<T>::t *__restrict__ zM,
+                                                    typename cpx<T>::t *__restrict__ zM_prev,
+                                                    const typename cpx<T>::t *__restrict__ zL,
+                                                    typename cpx<T>::t *__restrict__ zL_prev, const int lane) {
+  const int ld = a.ld, koff = lane * MPL, len = __float_as_int(mt.w);
+  const int64_t pf = B * ld + koff;
+  CV<T, MPL> aM, aL;
+  aM.zero();
+  aL.zero();
+  int q = 0;
+  for (; q + 4 <= len; q += 4) {
+    float4 e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) e[u] = ent[q + u];
+    if constexpr (DO_M) {
+      CV<T, MPL> x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ldv<T, MPL>(x[u], zM + (int64_t)__float_as_int(e[u].x) * ld + koff);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) axpy(aM, (T)e[u].y, x[u]);
+    }
+    if constexpr (DO_L) {
+      CV<T, MPL> x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ldv<T, MPL>(x[u], zL + (int64_t)__float_as_int(e[u].x) * ld + koff);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) axpy(aL, (T)e[u].z, x[u]);
+    }
+  }
+  for (; q < len; ++q) {
+    const float4 e = ent[q];
+    const int64_t Bc = __float_as_int(e.x);
+    if constexpr (DO_M) { CV<T, MPL> x; ldv<T, MPL>(x, zM + Bc * ld + koff); axpy(aM, (T)e.y, x); }
+    if constexpr (DO_L) { CV<T, MPL> x; ldv<T, MPL>(x, zL + Bc * ld + koff); axpy(aL, (T)e.z, x); }
+  }
+  CV<T, MPL> rv;
+  ldv<T, MPL>(rv, r + ((int64_t)DIM * a.N + B) * ld + koff);
+  if constexpr (DO_M) {
+    CV<T, MPL> z, zp, o;
+    ldv<T, MPL>(z, zM + pf);
+    if (cc.prev_zero_m) zp.zero(); else ldv<T, MPL>(zp, zM_prev + pf);
+    const T al = (T)cc.alpha_m, be = (T)cc.beta_m, dm = (T)mt.x;
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) {
+      o.re[i] = z.re[i] + al * (z.re[i] - zp.re[i]) + be * dm * (rv.re[i] - aM.re[i]);
+      o.im[i] = z.im[i] + al * (z.im[i] - zp.im[i]) + be * dm * (rv.im[i] - aM.im[i]);
+    }
+    stv<T, MPL>(zM_prev + pf, o);
+  }
+  if constexpr (DO_L) {
+    CV<T, MPL> z, zp, o;
+    ldv<T, MPL>(z, zL + pf);
+    if (cc.prev_zero_l) zp.zero(); else ldv<T, MPL>(zp, zL_prev + pf);
+    const T al = (T)cc.alpha_l, be = (T)cc.beta_l, dl = (T)mt.y;
+    const bool out = mt.z != 0.f;
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) {
+      const T rr = out ? T(0) : rv.re[i], ri = out ? T(0) : rv.im[i];
+      o.re[i] = z.re[i] + al * (z.re[i] - zp.re[i]) + be * dl * (rr - aL.re[i]);
+      o.im[i] = z.im[i] + al * (z.im[i] - zp.im[i]) + be * dl * (ri - aL.im[i]);
+    }
+    stv<T, MPL>(zL_prev + pf, o);
+  }
+}
+
+// Cached coarse step on vertex row v (see coarse_row_step): meta = (diag K_1,
+// diag M_1, Dirichlet flag, length).  The gathers of two nonzeros (all
+// components) are issued together.
+template <typename T, int MPL, int DIM>
+__device__ __forceinline__ void coarse_row_cached(const PcArgs &a, const double *__restrict__ alpha,
+                                                  const double *__restrict__ beta, bool prev_zero,
+                                                  const float4 *__restrict__ ent, const float4 mt,
+                                                  const typename cpx<T>::t *__restrict__ rc,
+                                                  const typename cpx<T>::t *__restrict__ zc,
+                                                  typename cpx<T>::t *__restrict__ zc_prev, const int64_t v,
+                                                  const int lane) {
+  const int ld = a.ld, koff = lane * MPL, len = __float_as_int(mt.w);
+  if (mt.z != 0.f) {  // Dirichlet vertex
+    CV<T, MPL> zz;
+    zz.zero();
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) stv<T, MPL>(zc_prev + (v * DIM + c) * ld + koff, zz);
+    return;
+  }
+  T cr[MPL];
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) cr[i] = ((const T *)a.wabs)[koff + i];
+  const T mu = (T)a.mu;
+  CV<T, MPL> acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c].zero();
+  auto fma_row = [&](const float4 e, const CV<T, MPL> *x) {
+    const T kq = mu * (T)e.y, mq = (T)e.z;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        const T cf = kq + cr[i] * mq;
+        acc[c].re[i] = fma(cf, x[c].re[i], acc[c].re[i]);
+        acc[c].im[i] = fma(cf, x[c].im[i], acc[c].im[i]);
+      }
+  };
+  int q = 0;
+  for (; q + 2 <= len; q += 2) {
+    const float4 e0 = ent[q], e1 = ent[q + 1];
+    CV<T, MPL> x0[DIM], x1[DIM];
+    const int64_t b0 = (int64_t)__float_as_int(e0.x) * DIM, b1 = (int64_t)__float_as_int(e1.x) * DIM;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      ldv<T, MPL>(x0[c], zc + (b0 + c) * ld + koff);
+      ldv<T, MPL>(x1[c], zc + (b1 + c) * ld + koff);
+    }
+    fma_row(e0, x0);
+    fma_row(e1, x1);
+  }
+  if (q < len) {
+    const float4 e0 = ent[q];
+    CV<T, MPL> x0[DIM];
+    const int64_t b0 = (int64_t)__float_as_int(e0.x) * DIM;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) ldv<T, MPL>(x0[c], zc + (b0 + c) * ld + koff);
+    fma_row(e0, x0);
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    const int64_t f = (v * DIM + c) * ld + koff;
+    CV<T, MPL> rv, zv, zp, o;
+    ldv<T, MPL>(rv, rc + f);
+    ldv<T, MPL>(zv, zc + f);
+    if (prev_zero) zp.zero(); else ldv<T, MPL>(zp, zc_prev + f);
+#pragma unroll
+    for (int i = 0; i < MPL; ++i) {
+      const int k = koff + i;
+      const T d = T(1) / (mu * (T)mt.x + cr[i] * (T)mt.y);
+      const T al = (T)alpha[k], be = (T)beta[k];
+      o.re[i] = zv.re[i] + al * (zv.re[i] - zp.re[i]) + be * d * (rv.re[i] - acc[c].re[i]);
+      o.im[i] = zv.im[i] + al * (zv.im[i] - zp.im[i]) + be * d * (rv.im[i] - acc[c].im[i]);
+    }
+    stv<T, MPL>(zc_prev + f, o);
+  }
+}
+
 // Coarse (P1) velocity solve of the two-level cycle as one cooperative launch:
 // restriction rc = P^T rr, step 0 zc = rc / (diag A_c theta_c[k]) and s_c - 1
 // Chebyshev steps, with a bounded grid barrier between the stages (a barrier
@@ -821,6 +997,7 @@ template <typename T> struct CoarseArgs {
   typename cpx<T>::t *zc0, *zc1;
   const double *inv_theta, *alpha, *beta;  // [ld], [s_c][ld], [s_c][ld]
   int s_c;
+  int kmax;  // rows cached per row group (the dynamic shared memory holds gpb * kmax rows)
   GridSync *gs;
 };
 
@@ -838,14 +1015,36 @@ __global__ void __launch_bounds__(256, 3) k_coarse_solve(const PcArgs a, const C
     const auto r = q.rc[f];
     q.zc0[f] = mk<T>(sc * r.x, sc * r.y);
   }
-  if (!grid_sync(q.gs, gridDim.x)) return;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
   const unsigned gm = group_mask<L>();
+  const int64_t G = (int64_t)gridDim.x * gpb, g = (int64_t)blockIdx.x * gpb + group;
+  extern __shared__ float4 p1_smem[];
+  const int kmax = sizeof(T) == 4 ? q.kmax : 0;
+  float4 *ent = p1_smem + (size_t)group * kmax * P1_CAP;
+  float4 *meta = p1_smem + (size_t)gpb * kmax * P1_CAP + group * kmax;
+  if constexpr (sizeof(T) == 4) {
+    for (int kk = 0; kk < kmax; ++kk) {
+      const int64_t v = g + kk * G;
+      if (v < a.P)
+        p1_cache_row<T>(a, a.Kcv, a.Mcv, v, ent + kk * P1_CAP, meta + kk, ((const float *)a.k1d)[v],
+                        ((const float *)a.mpd)[v], a.dirmask[v] ? 1.f : 0.f, lane, L);
+    }
+  }
+  if (!grid_sync(q.gs, gridDim.x)) return;  // also orders the cache fill before its use
   typename cpx<T>::t *zcur = q.zc0, *znext = q.zc1;
   for (int i = 1; i < q.s_c; ++i) {
-    for (int64_t v = (int64_t)blockIdx.x * gpb + group; v < a.P; v += (int64_t)gridDim.x * gpb) {
+    int kk = 0;
+    for (int64_t v = g; v < a.P; v += G, ++kk) {
       if (row_idle(a.dof_comp, a.comp_active, v * DIM)) continue;
+      if (kk < kmax) {
+        const float4 mt = meta[kk];
+        if (__float_as_int(mt.w) >= 0) {
+          coarse_row_cached<T, MPL, DIM>(a, q.alpha + (size_t)i * a.ld, q.beta + (size_t)i * a.ld, i == 1,
+                                         ent + kk * P1_CAP, mt, q.rc, zcur, znext, v, lane);
+          continue;
+        }
+      }
       coarse_row_step<T, MPL, L, DIM>(a, q.alpha + (size_t)i * a.ld, q.beta + (size_t)i * a.ld, i == 1, q.rc, zcur,
                                       znext, v, lane, gm);
     }
@@ -869,6 +1068,7 @@ template <typename T> struct PressureArgs {
   typename cpx<T>::t *zM0, *zM1, *zL0, *zL1;
   typename cpx<T>::t *z;
   T sign;
+  int kmax;  // rows cached per row group (the dynamic shared memory holds gpb * kmax rows)
   GridSync *gs;
 };
 
@@ -893,10 +1093,23 @@ __global__ void __launch_bounds__(256, 3) k_pressure_solve(const PcArgs a, const
     const T sl = a.outmask[B] ? T(0) : (T)p.inv_theta_l / ((const T *)a.lpd)[B];
     p.zL0[e] = mk<T>(v.x * sl, v.y * sl);
   }
-  if (!grid_sync(p.gs, gridDim.x)) return;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
   const unsigned gm = group_mask<L>();
+  const int64_t G = (int64_t)gridDim.x * gpb, g = (int64_t)blockIdx.x * gpb + group;
+  extern __shared__ float4 p1_smem[];
+  const int kmax = sizeof(T) == 4 ? p.kmax : 0;
+  float4 *ent = p1_smem + (size_t)group * kmax * P1_CAP;
+  float4 *meta = p1_smem + (size_t)gpb * kmax * P1_CAP + group * kmax;
+  if constexpr (sizeof(T) == 4) {
+    for (int kk = 0; kk < kmax; ++kk) {
+      const int64_t B = g + kk * G;
+      if (B < a.P)
+        p1_cache_row<T>(a, a.Mpv, a.Lpv, B, ent + kk * P1_CAP, meta + kk, 1.f / ((const float *)a.mpd)[B],
+                        1.f / ((const float *)a.lpd)[B], a.outmask[B] ? 1.f : 0.f, lane, L);
+    }
+  }
+  if (!grid_sync(p.gs, gridDim.x)) return;  // also orders the cache fill before its use
   C *mc = p.zM0, *mn = p.zM1, *lc = p.zL0, *ln = p.zL1;  // current / next iterates
   const int steps = max(p.s_m, p.s_l);
   for (int ip = 1; ip < steps; ++ip) {
@@ -906,8 +1119,21 @@ __global__ void __launch_bounds__(256, 3) k_pressure_solve(const PcArgs a, const
     cc.alpha_m = cc.do_m ? p.am[ip] : 0.0; cc.beta_m = cc.do_m ? p.bm[ip] : 0.0;
     cc.alpha_l = cc.do_l ? p.al[ip] : 0.0; cc.beta_l = cc.do_l ? p.bl[ip] : 0.0;
     cc.prev_zero_m = cc.prev_zero_l = (ip == 1);
-    for (int64_t B = (int64_t)blockIdx.x * gpb + group; B < a.P; B += (int64_t)gridDim.x * gpb) {
+    int kk = 0;
+    for (int64_t B = g; B < a.P; B += G, ++kk) {
       if (row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + B)) continue;
+      if (kk < kmax) {
+        const float4 mt = meta[kk];
+        if (__float_as_int(mt.w) >= 0) {
+          if (cc.do_m && cc.do_l)
+            pressure_row_cached<T, MPL, DIM, true, true>(a, cc, B, ent + kk * P1_CAP, mt, p.r, mc, mn, lc, ln, lane);
+          else if (cc.do_l)
+            pressure_row_cached<T, MPL, DIM, false, true>(a, cc, B, ent + kk * P1_CAP, mt, p.r, mc, mn, lc, ln, lane);
+          else
+            pressure_row_cached<T, MPL, DIM, true, false>(a, cc, B, ent + kk * P1_CAP, mt, p.r, mc, mn, lc, ln, lane);
+          continue;
+        }
+      }
       pressure_row_step<T, MPL, L, DIM>(a, cc, B, p.r, mc, mn, lc, ln, lane, gm);
     }
     if (cc.do_m) { C *t = mc; mc = mn; mn = t; }
@@ -1124,9 +1350,9 @@ static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &
 
 // Grid of a cooperative launch: every block resident at once (at most 4 per
 // SM, which keeps the barrier's arrival counter short).
-static int coop_grid(Ctx &c, const void *kfn) {
+static int coop_grid(Ctx &c, const void *kfn, size_t smem) {
   int per_sm = 0;
-  SCVS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, 0));
+  SCVS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
   if (per_sm < 1) throw (int)SCVS_ERR_CUDA;
   return std::min(per_sm, 4) * c.num_sms;
 }
@@ -1143,12 +1369,14 @@ static void pressure_solve(Ctx &c, const Mesh &m, const PcArgs &a, const PcTable
   }
   KScope ks(c, KC_PRECOND, by);
   PressureArgs<T> p{r, rscale, t.inv_theta_m, t.inv_theta_l, t.am_d, t.bm_d, t.al_d, t.bl_d, t.s_m, t.s_l,
-                    pM[0], pM[1], pL[0], pL[1], z, sign, c.gsync};
+                    pM[0], pM[1], pL[0], pL[1], z, sign, 0, c.gsync};
   PcArgs aa = a;
   SCVS_DISPATCH_LD(T, m.ld, {
     const void *kfn = m.dim == 2 ? (const void *)k_pressure_solve<T, MPL, L, 2> : (const void *)k_pressure_solve<T, MPL, L, 3>;
+    p.kmax = sizeof(T) == 4 ? p1_kmax(256 / L, P1_KMAX_P) : 0;
+    const size_t smem = (size_t)(256 / L) * p.kmax * (P1_CAP + 1) * sizeof(float4);
     void *args[] = {(void *)&aa, (void *)&p};
-    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn)), dim3(256), args, 0, c.stream));
+    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn, smem)), dim3(256), args, smem, c.stream));
   });
   count_launch(c);
 }
@@ -1164,12 +1392,14 @@ static typename cpx<T>::t *coarse_solve(Ctx &c, const Mesh &m, const PcArgs &a, 
   for (int i = 1; i < t.s_c; ++i)
     by += (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 8 + cbk * (i == 1 ? 3 : 4);
   KScope ks(c, KC_PRECOND, by);
-  CoarseArgs<T> q{rr, rc, zc[0], zc[1], t.inv_theta_c, t.alpha_c, t.beta_c, t.s_c, c.gsync};
+  CoarseArgs<T> q{rr, rc, zc[0], zc[1], t.inv_theta_c, t.alpha_c, t.beta_c, t.s_c, 0, c.gsync};
   PcArgs aa = a;
   SCVS_DISPATCH_LD(T, m.ld, {
     const void *kfn = m.dim == 2 ? (const void *)k_coarse_solve<T, MPL, L, 2> : (const void *)k_coarse_solve<T, MPL, L, 3>;
+    q.kmax = sizeof(T) == 4 ? p1_kmax(256 / L, P1_KMAX_C) : 0;
+    const size_t smem = (size_t)(256 / L) * q.kmax * (P1_CAP + 1) * sizeof(float4);
     void *args[] = {(void *)&aa, (void *)&q};
-    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn)), dim3(256), args, 0, c.stream));
+    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn, smem)), dim3(256), args, smem, c.stream));
   });
   count_launch(c);
   return zc[(t.s_c - 1) % 2];
@@ -1306,13 +1536,22 @@ __global__ void __launch_bounds__(256)
 k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename cpx<T>::t *__restrict__ y,
             const typename cpx<T>::t *__restrict__ vM, typename cpx<T>::t *__restrict__ yM,
             const typename cpx<T>::t *__restrict__ vL, typename cpx<T>::t *__restrict__ yL,
-            const typename cpx<T>::t *__restrict__ vC, typename cpx<T>::t *__restrict__ yC) {
+            const typename cpx<T>::t *__restrict__ vC, typename cpx<T>::t *__restrict__ yC,
+            const double *__restrict__ vn2) {
   using C = typename cpx<T>::t;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
   const unsigned gm = group_mask<L>();
   const int ld = a.ld, koff = lane * MPL;
   const T *Kv = (const T *)a.Kv, *Mv = (const T *)a.Mv, *Mpv = (const T *)a.Mpv, *Lpv = (const T *)a.Lpv;
+  // vn2 (may be null): squared norms of the four input blocks per mode column,
+  // [velocity | M_p | L_p | coarse][ld]; the outputs are divided by the norms,
+  // which normalises the power iterate without a separate pass
+  auto inv_norm = [&](int blk, int k) -> T {
+    if (!vn2) return T(1);
+    const double nn = vn2[blk * ld + k];
+    return nn > 0 ? (T)(1.0 / sqrt(nn)) : T(0);
+  };
   for (int64_t row = (int64_t)blockIdx.x * gpb + group; row < a.N + a.P; row += (int64_t)gridDim.x * gpb) {
     if (row < a.N) {
       const int64_t A = row;
@@ -1342,7 +1581,7 @@ k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename c
 #pragma unroll
       for (int i = 0; i < MPL; ++i) {
         const int k = koff + i;
-        const T dr = vel_dinv<T>(a, A, k);
+        const T dr = vel_dinv<T>(a, A, k) * inv_norm(0, k);
         const T mu = (T)a.mu, wr = (T)(fabs(a.omega[k]) * a.rho);
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
@@ -1384,7 +1623,7 @@ k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename c
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
           const double w = a.omega[koff + i];
-          const T d = dir ? T(0) : (T)(1.0 / (a.mu * a.k1_diag[B] + fabs(w) * a.rho * a.mp_diag[B]));
+          const T d = dir ? T(0) : (T)(1.0 / (a.mu * a.k1_diag[B] + fabs(w) * a.rho * a.mp_diag[B])) * inv_norm(3, koff + i);
           const T cr = (T)(fabs(w) * a.rho), mu = (T)a.mu;
           o3.re[i] = d * (mu * aKc.re[i] + cr * aMc.re[i]);
           o3.im[i] = d * (mu * aKc.im[i] + cr * aMc.im[i]);
@@ -1395,8 +1634,9 @@ k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename c
       CV<T, MPL> o1, o2;
 #pragma unroll
       for (int i = 0; i < MPL; ++i) {
-        o1.re[i] = dm * aMp.re[i]; o1.im[i] = dm * aMp.im[i];
-        o2.re[i] = dl * aLp.re[i]; o2.im[i] = dl * aLp.im[i];
+        const T sm = dm * inv_norm(1, koff + i), sl = dl * inv_norm(2, koff + i);
+        o1.re[i] = sm * aMp.re[i]; o1.im[i] = sm * aMp.im[i];
+        o2.re[i] = sl * aLp.re[i]; o2.im[i] = sl * aLp.im[i];
       }
       stv<T, MPL>(yM + B * ld + koff, o1);
       stv<T, MPL>(yL + B * ld + koff, o2);
@@ -1424,16 +1664,6 @@ __global__ void k_block_norm2(const typename cpx<T>::t *__restrict__ v, int64_t 
     __syncthreads();
   }
   if (threadIdx.x < ld) atomicAdd(&out2[threadIdx.x], s[threadIdx.x]);
-}
-
-template <typename T>
-__global__ void k_block_scale(typename cpx<T>::t *v, int64_t rows, int ld, const double *__restrict__ n2) {
-  int64_t f = blockIdx.x * 256ll + threadIdx.x;
-  if (f >= rows * ld) return;
-  double nn = n2[f % ld];
-  T s = nn > 0 ? (T)(1.0 / sqrt(nn)) : T(0);
-  auto z = v[f];
-  v[f] = mk<T>(z.x * s, z.y * s);
 }
 
 __global__ void k_init_random(float2 *v, int64_t n) {
@@ -1464,41 +1694,39 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   SCVS_CUDA(cudaMallocAsync(&yL, np * sizeof(float2), c.stream));
   SCVS_CUDA(cudaMallocAsync(&vC, np * sizeof(float2), c.stream));
   SCVS_CUDA(cudaMallocAsync(&yC, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&n2, 4 * ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMallocAsync(&n2, 8 * ld * sizeof(double), c.stream));  // two alternating norm sets
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vC, np);
   k_init_random<<<ceil_div(total, 256), 256, 0, c.stream>>>(v, total);
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vM, np);
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vL, np);
-  c.launches.n += 3;
+  c.launches.n += 4;
   const PcArgs a = pc_args<float>(m);
   const unsigned nbn = (unsigned)std::min<int64_t>(ceil_div(total, 256), 4 * c.num_sms);
   std::vector<double> h(4 * ld, 0.0);
   const int iters = 40;
   for (int it = 0; it < iters; ++it) {
+    // y = D^-1 A (v / ||v||) with ||v|| from the previous step (the start vector is used as is)
+    const double *vn2 = it == 0 ? nullptr : n2 + ((it - 1) % 2) * 4 * ld;
+    double *yn2 = n2 + (it % 2) * 4 * ld;
     SCVS_DISPATCH_LD(float, ld, {
       const int gpb = 256 / L;
       const unsigned nb = row_blocks(c, m.N + m.P, gpb);
       if (m.dim == 2)
-        k_jacobi_op<float, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC);
+        k_jacobi_op<float, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC, vn2);
       else
-        k_jacobi_op<float, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC);
+        k_jacobi_op<float, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC, vn2);
     });
-    SCVS_CUDA(cudaMemsetAsync(n2, 0, 4 * ld * sizeof(double), c.stream));
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, m.dim, m.dirmask, n2);
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yM, m.P, ld, 1, nullptr, n2 + ld);
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yL, m.P, ld, 1, nullptr, n2 + 2 * ld);
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yC, m.P, ld, 1, nullptr, n2 + 3 * ld);
+    SCVS_CUDA(cudaMemsetAsync(yn2, 0, 4 * ld * sizeof(double), c.stream));
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, m.dim, m.dirmask, yn2);
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yM, m.P, ld, 1, nullptr, yn2 + ld);
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yL, m.P, ld, 1, nullptr, yn2 + 2 * ld);
+    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yC, m.P, ld, 1, nullptr, yn2 + 3 * ld);
     c.launches.n += 5;
     if (it == iters - 1) {
-      // the previous iterate had unit norm: ||y|| is the Rayleigh-type estimate
-      SCVS_CUDA(cudaMemcpyAsync(h.data(), n2, 4 * ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+      // the input had unit norm: ||y|| is the Rayleigh-type estimate
+      SCVS_CUDA(cudaMemcpyAsync(h.data(), yn2, 4 * ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
       break;
     }
-    k_block_scale<float><<<ceil_div(nu, 256), 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, n2);
-    k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yM, m.P, ld, n2 + ld);
-    k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yL, m.P, ld, n2 + 2 * ld);
-    k_block_scale<float><<<ceil_div(np, 256), 256, 0, c.stream>>>(yC, m.P, ld, n2 + 3 * ld);
-    c.launches.n += 4;
     std::swap(v, y);
     std::swap(vM, yM);
     std::swap(vL, yL);

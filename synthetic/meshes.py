@@ -307,3 +307,131 @@ def union(mesh_list):
     mesh = dict(dim=dim, xyz=xyz, conn=np.concatenate(conns, axis=0), tag=tag, n_vertices=Ptot,
                 name=f"union of {len(mesh_list)} meshes")
     return mesh, node_comp, maps
+
+
+# Kuhn split of the unit cube: one tet per axis permutation, all sharing the
+# main diagonal v000-v111; on every face the split diagonal joins the face's
+# lowest and highest corner, so neighbouring cubes split shared faces alike.
+_KUHN_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def bifurcation_inside(p, parent_len, stenosis, daughter_radius, daughter_len, angle_deg, radius=1.0):
+    """Inside test of the bifurcation: stenosed parent x in [0, L_p] (cosine
+    stenosis centred at L_p/2, extent 4R), a ball of radius R at the branch
+    point (L_p, 0, 0), and two daughters of radius R_d and length L_d whose
+    axes leave the branch point at +-angle in the x-y plane.  Returns
+    (inside, (t+, r+), (t-, r-)) with the daughters' axial and radial
+    coordinates."""
+    x, y, z = p[..., 0], p[..., 1], p[..., 2]
+    rp = np.hypot(y, z)
+    inside = (x >= 0) & (x <= parent_len) & (rp <= stenosis_radius(x, radius, stenosis, 0.5 * parent_len,
+                                                                  4.0 * radius))
+    q = p - np.array([parent_len, 0.0, 0.0])
+    inside |= np.einsum("...i,...i->...", q, q) <= radius * radius
+    a = np.deg2rad(angle_deg)
+    coords = []
+    for sgn in (1.0, -1.0):
+        d = np.array([np.cos(a), sgn * np.sin(a), 0.0])
+        t = q @ d
+        r = np.linalg.norm(q - t[..., None] * d, axis=-1)
+        inside |= (t >= 0) & (t <= daughter_len) & (r <= daughter_radius)
+        coords.append((t, r))
+    return inside, coords[0], coords[1]
+
+
+def bifurcation3d(h=0.2, parent_len=8.0, stenosis=0.5, daughter_radius=0.7, daughter_len=6.0, angle_deg=45.0,
+                  radius=1.0):
+    """Stenosed bifurcation on a voxel grid of spacing h: every cell whose
+    centre is inside (``bifurcation_inside``) is kept and cut into the 6 Kuhn
+    tets (conforming).  Boundary faces of kept cells are tagged from the
+    cell beyond them: INLET if it lies at x < 0, OUTLET if it lies past the
+    end of a daughter (axial t > L_d, radial r <= R_d), WALL otherwise.  A
+    node carries the tags of every boundary face it lies on (vertices: the 4
+    corners; edge nodes: the 4 sides and the split diagonal).  The wall is a
+    staircase at resolution h.  About 7.6 P2 nodes per vertex; h = 0.038
+    gives ~6M P2 nodes."""
+    a = np.deg2rad(angle_deg)
+    L_d = daughter_len
+    tip = np.array([parent_len, 0.0, 0.0]) + (L_d + daughter_radius) * np.array([np.cos(a), np.sin(a), 0.0])
+    hi = np.array([tip[0] + daughter_radius, max(tip[1] + daughter_radius, radius), radius])
+    lo = np.array([0.0, -hi[1], -radius])
+    n = np.ceil((hi - lo) / h).astype(np.int64) + 1
+    lo[1] = -0.5 * n[1] * h   # symmetric in y and z about the axis
+    lo[2] = -0.5 * n[2] * h
+    ci = [lo[d] + (np.arange(n[d]) + 0.5) * h for d in range(3)]
+    cx, cy, cz = np.meshgrid(ci[0], ci[1], ci[2], indexing="ij")
+    cen = np.stack([cx, cy, cz], axis=-1)
+    keep, _, _ = bifurcation_inside(cen, parent_len, stenosis, daughter_radius, L_d, angle_deg, radius)
+    # vertices of kept cells, numbered x-major (streamwise), then y, then z
+    vused = np.zeros(n + 1, dtype=bool)
+    for o in np.ndindex(2, 2, 2):
+        vused[o[0]:o[0] + n[0], o[1]:o[1] + n[1], o[2]:o[2] + n[2]] |= keep
+    vid = -np.ones(n + 1, dtype=np.int64)
+    vid[vused] = np.arange(int(vused.sum()))
+    gi = np.argwhere(vused)
+    vxyz = lo + gi * h
+    cells = np.argwhere(keep)
+    corner = lambda off: vid[cells[:, 0] + off[0], cells[:, 1] + off[1], cells[:, 2] + off[2]]
+    tets = []
+    for perm in _KUHN_PERMS:
+        off = np.zeros(3, dtype=np.int64)
+        ids = [corner(off)]
+        for ax in perm:
+            off = off.copy()
+            off[ax] = 1
+            ids.append(corner(off))
+        tets.append(np.stack(ids, axis=1))
+    simp = _orient_positive(vxyz, np.concatenate(tets, axis=0))
+
+    def key(lo_, hi_, mid):
+        return (lo_, hi_)
+
+    xyz, conn, ends = _add_p2_nodes(vxyz, simp, key)
+    P = vxyz.shape[0]
+    N = xyz.shape[0]
+    ekey = ends[:, 0] * P + ends[:, 1]
+    eorder = np.argsort(ekey)
+    tag = np.zeros(N, dtype=np.uint8)
+    for ax in range(3):
+        for side in (0, 1):
+            # kept cells whose neighbour across the face (ax, side) is not kept
+            nb = np.zeros_like(keep)
+            sl_dst = [slice(None)] * 3
+            sl_src = [slice(None)] * 3
+            if side == 1:
+                sl_dst[ax] = slice(0, n[ax] - 1)
+                sl_src[ax] = slice(1, n[ax])
+            else:
+                sl_dst[ax] = slice(1, n[ax])
+                sl_src[ax] = slice(0, n[ax] - 1)
+            nb[tuple(sl_dst)] = keep[tuple(sl_src)]
+            fc = np.argwhere(keep & ~nb)
+            if fc.size == 0:
+                continue
+            outc = lo + (fc + 0.5) * h
+            outc[:, ax] += (h if side == 1 else -h)
+            _, (tp, rp_), (tm, rm) = bifurcation_inside(outc, parent_len, stenosis, daughter_radius, L_d,
+                                                       angle_deg, radius)
+            ftag = np.full(fc.shape[0], WALL, dtype=np.uint8)
+            ftag[((tp > L_d) & (rp_ <= daughter_radius)) | ((tm > L_d) & (rm <= daughter_radius))] = OUTLET
+            ftag[outc[:, 0] < 0] = INLET
+            b, c = [d for d in range(3) if d != ax]
+            cv = {}
+            for ob in (0, 1):
+                for oc in (0, 1):
+                    off = np.zeros(3, dtype=np.int64)
+                    off[ax] = side
+                    off[b] = ob
+                    off[c] = oc
+                    cv[ob, oc] = vid[fc[:, 0] + off[0], fc[:, 1] + off[1], fc[:, 2] + off[2]]
+            for v in cv.values():
+                np.bitwise_or.at(tag, v, ftag)
+            for (p0, p1) in (((0, 0), (1, 0)), ((1, 0), (1, 1)), ((1, 1), (0, 1)), ((0, 1), (0, 0)),
+                             ((0, 0), (1, 1))):
+                u, w = cv[p0], cv[p1]
+                k = np.minimum(u, w) * P + np.maximum(u, w)
+                pos = eorder[np.searchsorted(ekey, k, sorter=eorder)]
+                np.bitwise_or.at(tag, P + pos, ftag)
+    return dict(dim=3, xyz=xyz, conn=conn, tag=tag, n_vertices=P,
+                name=f"bifurcation h={h} Lp={parent_len} s={stenosis} Rd={daughter_radius} Ld={L_d}",
+                radius=radius, length=parent_len, stenosis=stenosis)

@@ -78,6 +78,26 @@ def pipe_workload(n_c=8, n_r=6, n_x=71, n_modes=32, radius=1.0, length=10.0, rho
                 name=f"womersley pipe N={mesh['xyz'].shape[0]}, {n_modes} modes")
 
 
+def bifurcation_workload(h=0.2, n_modes=16, rho=1.0, mu=PIPE_MU, period=1.0, G=1.0, seed=0, **geom):
+    """Stenosed bifurcation (``meshes.bifurcation3d``) with the pipe's physics:
+    Womersley inlet profile of the unit-radius parent (node radius clipped to
+    the parent radius), c_k = k^-2 exp(j phi_k) with seeded phases, no-slip
+    walls, traction-free daughter outlets."""
+    mesh = meshes.bifurcation3d(h=h, **geom)
+    omegas = 2.0 * np.pi * np.arange(n_modes) / period
+    coeffs = phases(n_modes, seed)
+    tag = mesh["tag"]
+    dn = dirichlet_nodes(tag)
+    g = np.zeros((n_modes, dn.size, 3), dtype=np.complex128)
+    inl = ((tag[dn] & meshes.INLET) != 0) & ((tag[dn] & meshes.WALL) == 0)
+    pts = mesh["xyz"][dn[inl]]
+    r = np.minimum(np.hypot(pts[:, 1], pts[:, 2]), mesh["radius"])
+    for k, (w, c) in enumerate(zip(omegas, coeffs)):
+        g[k, inl, 0] = c * pipe_profile(r, w, mesh["radius"], rho, mu, G)
+    return dict(mesh=mesh, rho=rho, mu=mu, period=period, G=G, omegas=omegas, coeffs=coeffs, dir_nodes=dn, g=g,
+                name=f"stenosed bifurcation N={mesh['xyz'].shape[0]}, {n_modes} modes")
+
+
 def exact_nodal(wl, k):
     """Analytic (u, p) of mode k at the nodes: velocity [N][d], pressure [P].
 

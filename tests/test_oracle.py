@@ -347,3 +347,36 @@ def test_pipe_generator_is_conforming():
         if cnt == 1:
             common = tag[f[0]] & tag[f[1]] & tag[f[2]]
             assert common != 0
+
+
+def test_bifurcation_generator_is_conforming_and_tagged():
+    """Voxel bifurcation: every interior face is shared by exactly two tets;
+    the nodes of every boundary triangle (vertices and edge nodes) carry a
+    common tag, interior nodes carry none; inlet, outlet and wall all exist
+    and some outlet nodes are not wall nodes (a natural outflow boundary)."""
+    m = meshes.bifurcation3d(h=0.4)
+    conn = m["conn"]
+    tets = conn[:, :4].astype(np.int64)
+    P = m["n_vertices"]
+    local = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+    f = np.sort(np.concatenate([tets[:, list(t)] for t in local], axis=0), axis=1)
+    keys = (f[:, 0] * P + f[:, 1]) * P + f[:, 2]
+    uk, idx, cnt = np.unique(keys, return_index=True, return_counts=True)
+    assert cnt.max() == 2
+    tag = m["tag"]
+    bf = f[idx[cnt == 1]]
+    assert np.all((tag[bf[:, 0]] & tag[bf[:, 1]] & tag[bf[:, 2]]) != 0)
+    # boundary nodes: vertices of boundary faces and the edge nodes of their edges
+    on_b = np.zeros(tag.size, dtype=bool)
+    on_b[bf.ravel()] = True
+    edges = {(min(int(a), int(b)), max(int(a), int(b))) for tri in bf for a, b in ((tri[0], tri[1]), (tri[1], tri[2]),
+                                                                                      (tri[0], tri[2]))}
+    pairs = ((0, 1), (1, 2), (2, 0), (0, 3), (1, 3), (2, 3))
+    for e in range(conn.shape[0]):
+        for j, (a, b) in enumerate(pairs):
+            u, w = int(conn[e, a]), int(conn[e, b])
+            if (min(u, w), max(u, w)) in edges:
+                on_b[conn[e, 4 + j]] = True
+    assert np.array_equal(on_b, tag != 0)
+    assert (tag & meshes.INLET).any() and (tag & meshes.WALL).any()
+    assert ((tag & meshes.OUTLET) != 0).sum() > 0 and (((tag & meshes.OUTLET) != 0) & ((tag & meshes.WALL) == 0)).any()
