@@ -301,6 +301,7 @@ def run_gpu(args):
            "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
            "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb, "autotune": tuned,
            "solve": {"converged": conv, "modes_per_step": m,
+                     "iterations_by_mode": [r["iterations"] for r in last],
                      "iterations_max": max(r["iterations"] for r in last),
                      "iterations_mean": float(np.mean([r["iterations"] for r in last])),
                      "cycles_max": max(r["cycles"] for r in last),

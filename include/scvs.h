@@ -91,13 +91,13 @@ typedef struct {
   int32_t precision; /* SCVS_PREC_* (default MIXED) */
   int32_t precond;   /* SCVS_PC_* (default TRI_PMG) */
   int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with the p-multigrid kinds the degree of each
-                        of the pre- and post-smoothers (default 4) */
+                        of the pre- and post-smoothers (default 3) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
-  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 45) */
+  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 75) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
-  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of the p-multigrid kinds (default 20) */
+  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of the p-multigrid kinds (default 30) */
   int32_t autotune;  /* 1 (default): time the launch shapes (modes per lane, row tile) of the FP32 SpMM and
                         Chebyshev kernels at scvs_set_modes and keep the fastest; the result is kept per
                         context for meshes of the same size (dim, nodes, vertices, nonzeros, mode

@@ -232,11 +232,11 @@ void scvs_default_opts(scvs_opts *o) {
   o->restart = 30;
   o->precision = SCVS_PREC_MIXED;
   o->precond = SCVS_PC_TRI_PMG;
-  o->cheb_u = 4;
-  o->cheb_c = 20;
+  o->cheb_u = 3;
+  o->cheb_c = 30;
   o->autotune = 1;
   o->cheb_m = 4;
-  o->cheb_l = 45;
+  o->cheb_l = 75;
   o->max_cycles = 400;
   o->guess = SCVS_GUESS_ZERO;
   o->verbose = 0;
