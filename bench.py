@@ -207,6 +207,28 @@ def run_gpu(args):
         scvs.scvs_reconstruct_dev(ctx, mid, N_T, wl["period"], u_t.data_ptr(), p_t.data_ptr())
         return rep
 
+    def phases():
+        """Host wall time of each call of one step, synchronised after every call
+        (a diagnostic step outside the timed region)."""
+        out = {}
+
+        def t(name, fn):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            out[name] = round((time.perf_counter() - t0) * 1e3, 2)
+            return r
+        t("clear_meshes", lambda: scvs.scvs_clear_meshes(ctx))
+        mid = t("set_mesh_dev", lambda: scvs.scvs_set_mesh_dev(ctx, d, N, P, xyz_d.data_ptr(), E, conn_d.data_ptr(),
+                                                                tag_d.data_ptr()))
+        t("set_physics", lambda: scvs.scvs_set_physics(ctx, mid, wl["rho"], wl["mu"]))
+        t("set_modes_dev", lambda: scvs.scvs_set_modes_dev(ctx, mid, wl["omegas"], g_d.data_ptr()))
+        t("solve", lambda: scvs.scvs_solve(ctx, mid, m))
+        t("reconstruct_dev", lambda: scvs.scvs_reconstruct_dev(ctx, mid, N_T, wl["period"], u_t.data_ptr(),
+                                                               p_t.data_ptr()))
+        return out
+
     def barrier():
         if world > 1:
             import torch.distributed as dist
@@ -237,6 +259,7 @@ def run_gpu(args):
     scvs.scvs_kernel_timers(ctx, False)
     conv = sum(1 for rr in reps for r in rr if r["status"] == scvs.SCVS_CONVERGED)
     tuned = scvs.scvs_tuned_shapes(ctx, 0)
+    phase_ms = phases()
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([elapsed], device=dev)
@@ -300,6 +323,7 @@ def run_gpu(args):
            "config": workload_config(), "roofline": roof, "spmm": spmm,
            "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
            "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb, "autotune": tuned,
+           "phase_ms": phase_ms,
            "solve": {"converged": conv, "modes_per_step": m,
                      "iterations_by_mode": [r["iterations"] for r in last],
                      "iterations_max": max(r["iterations"] for r in last),

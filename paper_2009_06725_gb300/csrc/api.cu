@@ -134,6 +134,8 @@ int add_mesh(scvs_ctx *c, int dim, int64_t N, int64_t P, const double *xyz, int6
     return fail(c, SCVS_ERR_PRESSURE_NULLSPACE,
                 "no vertex tagged OUTLET: with velocity prescribed on the whole boundary the pressure is undetermined");
   Mesh *m = new Mesh();
+  m->arena.pool = m->mode_arena.pool = c->pool;
+  m->arena.stream = m->mode_arena.stream = c->stream;
   m->dim = dim;
   m->nl = dim == 2 ? 6 : 10;
   m->nv = dim + 1;
@@ -144,8 +146,11 @@ int add_mesh(scvs_ctx *c, int dim, int64_t N, int64_t P, const double *xyz, int6
     build_mesh(*c, *m, xyz, conn, tag);
     set_chunks(*c, *m, nullptr, 1);
     m->dir_nodes = m->arena.alloc<int64_t>(std::max<int64_t>(1, m->n_dir));
-    if (m->n_dir)
-      SCVS_CUDA(cudaMemcpy(m->dir_nodes, dn.data(), m->n_dir * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (m->n_dir) {
+      SCVS_CUDA(cudaMemcpyAsync(m->dir_nodes, dn.data(), m->n_dir * sizeof(int64_t), cudaMemcpyHostToDevice,
+                                c->stream));
+      SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    }
   } catch (...) {
     m->arena.release();
     delete m;
@@ -254,6 +259,15 @@ int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
     SCVS_CUDA(cudaGetDevice(&c->device));
     SCVS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
     c->stream = static_cast<cudaStream_t>(c->opts.stream);
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    SCVS_CUDA(cudaMemPoolCreate(&c->pool, &props));
+    uint64_t keep = UINT64_MAX;  // never hand freed memory back: re-used by the next mesh / solve
+    SCVS_CUDA(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    c->work.pool = c->pool;
+    c->work.stream = c->stream;
     c->dev_err = c->work.alloc<int>(1);
     c->gsync = c->work.alloc<GridSync>(1);
     SCVS_CUDA(cudaMemset(c->dev_err, 0, sizeof(int)));
@@ -265,6 +279,10 @@ int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
   });
   if (r != SCVS_OK) {
     c->work.release();
+    if (c->pool) {
+      if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+      cudaMemPoolDestroy(c->pool);
+    }
     delete c;
     return r;
   }
@@ -284,6 +302,10 @@ void scvs_destroy(scvs_ctx *c) {
   c->timers.destroy();
   c->guess.release();
   c->work.release();
+  if (c->pool) {
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    cudaMemPoolDestroy(c->pool);
+  }
   delete c;
 }
 
@@ -295,8 +317,15 @@ int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
       o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_TRI_PMG)
     return fail(c, SCVS_ERR_ARG, "invalid options");
   void *old_stream = c->opts.stream;
+  if (o->stream != old_stream) {
+    // work queued on the old stream finishes before the arenas follow the new one
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    c->stream = static_cast<cudaStream_t>(o->stream);
+    c->work.stream = c->stream;
+    for (Mesh *m : c->meshes)
+      if (m) { m->arena.stream = c->stream; m->mode_arena.stream = c->stream; }
+  }
   c->opts = *o;
-  if (o->stream != old_stream) c->stream = static_cast<cudaStream_t>(o->stream);
   return SCVS_OK;
 }
 
@@ -476,8 +505,8 @@ int scvs_reconstruct(scvs_ctx *c, int32_t mesh_id, int32_t n_t, double period, d
     if (n_t < 1 || !(period > 0)) return fail(c, SCVS_ERR_ARG, "n_t >= 1 and period > 0 required");
     const int64_t nu = (int64_t)n_t * m->dim * m->N, np = (int64_t)n_t * m->P;
     double *du = nullptr, *dp = nullptr;
-    if (u_t) SCVS_CUDA(cudaMallocAsync(&du, nu * sizeof(double), c->stream));
-    if (p_t) SCVS_CUDA(cudaMallocAsync(&dp, np * sizeof(double), c->stream));
+    if (u_t) SCVS_CUDA(ctx_malloc(*c, &du, nu * sizeof(double), c->stream));
+    if (p_t) SCVS_CUDA(ctx_malloc(*c, &dp, np * sizeof(double), c->stream));
     reconstruct(*c, *m, n_t, period, du, dp);
     if (u_t) SCVS_CUDA(cudaMemcpyAsync(u_t, du, nu * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (p_t) SCVS_CUDA(cudaMemcpyAsync(p_t, dp, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -613,7 +642,7 @@ int scvs_apply_precond(scvs_ctx *c, int32_t mesh_id, const void *r, void *z) {
     Mesh *m = get_mesh(c, mesh_id);
     if (!m || m->m == 0 || !r || !z) return fail(c, SCVS_ERR_ARG, "bad argument");
     float2 *s = nullptr;
-    SCVS_CUDA(cudaMallocAsync(&s, precond_scratch_elems(*m) * sizeof(float2), c->stream));
+    SCVS_CUDA(ctx_malloc(*c, &s, precond_scratch_elems(*m) * sizeof(float2), c->stream));
     apply_precond<float>(*c, *m, static_cast<const float2 *>(r), static_cast<float2 *>(z), s, nullptr);
     SCVS_CUDA(cudaFreeAsync(s, c->stream));
     SCVS_CUDA(cudaGetLastError());

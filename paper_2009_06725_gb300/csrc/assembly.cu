@@ -440,7 +440,7 @@ __global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *__restrict__ 
 void scan_exclusive(Ctx &c, const int32_t *in, int64_t *out, int64_t n) {
   const int64_t nt = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
   int64_t *sums = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&sums, nt * sizeof(int64_t), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &sums, nt * sizeof(int64_t), c.stream));
   k_scan_tiles<<<(unsigned)nt, SCAN_T, 0, c.stream>>>(in, out, n, sums);
   k_scan_sums<<<1, SCAN_T, 0, c.stream>>>(sums, nt);
   k_scan_add<<<ceil_div(n + 1, 256), 256, 0, c.stream>>>(out, n, sums);

@@ -590,8 +590,8 @@ bool guess_initial(Ctx &c, Mesh &m) {
   for (int k = 0; k < m.m; ++k)
     for (int q = 0; q < 5; ++q) F[(size_t)k * 5 + q] = (float)((m.feat[(size_t)k * 5 + q] - g.fmean[q]) / g.fstd[q]);
   float *Xd = nullptr, *Yd = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&Xd, F.size() * sizeof(float), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&Yd, (size_t)m.m * n_out * sizeof(float), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &Xd, F.size() * sizeof(float), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &Yd, (size_t)m.m * n_out * sizeof(float), c.stream));
   SCVS_CUDA(cudaMemcpyAsync(Xd, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice, c.stream));
   mlp_forward(c, g, Xd, m.m, Yd);
   std::vector<float> Y((size_t)m.m * n_out);
@@ -609,9 +609,9 @@ bool guess_initial(Ctx &c, Mesh &m) {
   }
   float2 *aud = nullptr, *apd = nullptr;
   double2 *ckd = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&aud, au.size() * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&apd, ap.size() * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&ckd, ck.size() * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &aud, au.size() * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &apd, ap.size() * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &ckd, ck.size() * sizeof(double2), c.stream));
   SCVS_CUDA(cudaMemcpyAsync(aud, au.data(), au.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream));
   SCVS_CUDA(cudaMemcpyAsync(apd, ap.data(), ap.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream));
   SCVS_CUDA(cudaMemcpyAsync(ckd, ck.data(), ck.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));

@@ -446,9 +446,10 @@ struct Work {
   int *state = nullptr, *kdim = nullptr, *n_active = nullptr, *upd = nullptr;
   std::vector<void *> owned;
   cudaStream_t s = nullptr;
+  cudaMemPool_t pool = nullptr;
   template <typename U> U *get(size_t n) {
     void *p = nullptr;
-    SCVS_CUDA(cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(U), s));
+    SCVS_CUDA(cudaMallocFromPoolAsync(&p, std::max<size_t>(n, 1) * sizeof(U), pool, s));
     owned.push_back(p);
     return static_cast<U *>(p);
   }
@@ -497,6 +498,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   const int64_t total = m.n_dof * ld;
   Work<T> wk;
   wk.s = c.stream;
+  wk.pool = c.pool;
   wk.V = wk.template get<C>((size_t)(m_r + 1) * total);
   wk.Z = wk.template get<C>((size_t)m_r * total);  // flexible GMRES: z_j = P^-1 v_j kept
   wk.W = wk.template get<C>(total);

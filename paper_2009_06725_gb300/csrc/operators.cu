@@ -292,7 +292,7 @@ __global__ void k_comp_reduce(const double *__restrict__ part, const int32_t *__
 void norms2_sys(Ctx &c, const Mesh &m, const double2 *v, double *out) {
   KScope ks(c, KC_VECTOR, (double)m.n_dof * m.ld * 16);
   double *part = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&part, (size_t)m.n_chunk * m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &part, (size_t)m.n_chunk * m.ld * sizeof(double), c.stream));
   const unsigned nb = (unsigned)std::min<int64_t>(m.n_chunk, 8 * c.num_sms);
   k_chunk_norm2<<<nb, NORM_T, 0, c.stream>>>(v, m.dirmask, m.N, m.dim, m.ld, m.n_chunk, m.chunk_row0, m.chunk_rows,
                                              m.chunk_comp, m.comp_active, part);
@@ -351,9 +351,9 @@ void lift_rhs(Ctx &c, Mesh &m) {
   const int64_t total = m.n_dof * m.ld;
   double2 *gfull = nullptr, *y = nullptr;
   double *nrm = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&gfull, total * sizeof(double2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(double2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&nrm, m.n_sys() * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &gfull, total * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &y, total * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &nrm, m.n_sys() * sizeof(double), c.stream));
   SCVS_CUDA(cudaMemsetAsync(gfull, 0, total * sizeof(double2), c.stream));
   if (m.n_dir > 0 && m.m > 0) {
     int64_t tt = (int64_t)m.m * m.n_dir * m.dim;
@@ -1688,15 +1688,15 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   float2 *v = nullptr, *y = nullptr, *vM = nullptr, *yM = nullptr, *vL = nullptr, *yL = nullptr;
   float2 *vC = nullptr, *yC = nullptr;
   double *n2 = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&v, total * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&vM, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&yM, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&vL, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&yL, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&vC, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&yC, np * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&n2, 8 * ld * sizeof(double), c.stream));  // two alternating norm sets
+  SCVS_CUDA(ctx_malloc(c, &v, total * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &y, total * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &vM, np * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &yM, np * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &vL, np * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &yL, np * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &vC, np * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &yC, np * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &n2, 8 * ld * sizeof(double), c.stream));  // two alternating norm sets
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vC, np);
   k_init_random<<<ceil_div(total, 256), 256, 0, c.stream>>>(v, total);
   k_init_random<<<ceil_div(np, 256), 256, 0, c.stream>>>(vM, np);
@@ -1751,7 +1751,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
 void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev) {
   const int64_t total = m.n_dof * m.ld;
   double2 *ax = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&ax, total * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &ax, total * sizeof(double2), c.stream));
   launch_saddle<double>(c, m, saddle_args<double>(c, m, true), m.x, ax);
   double2 *r = r64 ? r64 : ax;
   {
@@ -1773,9 +1773,9 @@ void autotune_shapes(Ctx &c, Mesh &m) {
   const int64_t total = m.n_dof * m.ld;
   float2 *x = nullptr, *y = nullptr;
   double *zeros = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&x, total * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&y, total * sizeof(float2), c.stream));
-  SCVS_CUDA(cudaMallocAsync(&zeros, m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &x, total * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &y, total * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &zeros, m.ld * sizeof(double), c.stream));
   SCVS_CUDA(cudaMemsetAsync(zeros, 0, m.ld * sizeof(double), c.stream));
   k_init_random<<<ceil_div(total, 256), 256, 0, c.stream>>>(x, total);
   count_launch(c);

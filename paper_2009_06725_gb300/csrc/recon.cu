@@ -111,7 +111,7 @@ void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p
     }
   }
   double2 *twd = nullptr;
-  SCVS_CUDA(cudaMallocAsync(&twd, tw.size() * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &twd, tw.size() * sizeof(double2), c.stream));
   SCVS_CUDA(cudaMemcpyAsync(twd, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
   int td = 128;
   while (td > 32 && (size_t)td * m.m * sizeof(double2) > 96 * 1024) td >>= 1;

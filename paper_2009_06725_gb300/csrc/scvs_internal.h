@@ -12,18 +12,27 @@
 namespace scvs {
 
 // Device allocations owned by one object, released together.
+// Device allocations of one owner (a mesh, its mode set, the context), taken
+// stream-ordered from the context's memory pool, which keeps freed memory
+// cached: re-creating a mesh or a Krylov workspace of the same size costs no
+// new mapping and no device-wide synchronisation.
 struct DevArena {
   std::vector<void *> ptrs;
+  cudaMemPool_t pool = nullptr;  // null: plain cudaMalloc / cudaFree
+  cudaStream_t stream = nullptr;
   template <typename T> T *alloc(size_t count) {
     void *p = nullptr;
     if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, count * sizeof(T), pool, stream)
+                         : cudaMalloc(&p, count * sizeof(T));
     if (e != cudaSuccess) { (void)cudaGetLastError(); throw std::bad_alloc(); }
     ptrs.push_back(p);
     return static_cast<T *>(p);
   }
   void release() {
-    for (void *p : ptrs) cudaFree(p);
+    for (void *p : ptrs) {
+      if (pool) cudaFreeAsync(p, stream); else cudaFree(p);
+    }
     ptrs.clear();
   }
 };
@@ -217,7 +226,13 @@ struct Ctx {
   // mode stride, components): the timings depend on the pattern's size, not its values
   struct TuneRec { int mpl_spmm, tile_spmm, mpl_cheb, tile_cheb; std::vector<float> us; };
   std::map<std::vector<int64_t>, TuneRec> tune_cache;
+  cudaMemPool_t pool = nullptr;  // every stream-ordered allocation of the context
 };
+
+// Stream-ordered allocation from the context's pool.
+template <typename P> inline cudaError_t ctx_malloc(const Ctx &c, P **p, size_t bytes, cudaStream_t s) {
+  return cudaMallocFromPoolAsync(reinterpret_cast<void **>(p), bytes, c.pool, s);
+}
 
 // Scoped timing of one launch: KT(c, class, algorithmic bytes) { launch; }
 struct KScope {
