@@ -274,15 +274,16 @@ def run_gpu(args):
     # ---- end to end through the host-pointer entry points
     e2e = None
     if not args.no_e2e:
+        hb = pinned_host_buffers(torch, wl, m, N, P, d)
         for _ in range(1):
-            step_host(scvs, ctx, wl, m, N, P, d)
+            step_host(scvs, ctx, wl, m, N, P, d, hb)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         ev0.record(stream)
         conv_e = 0
         for _ in range(args.steps):
-            rr, nb_in, nb_out = step_host(scvs, ctx, wl, m, N, P, d)
+            rr, nb_in, nb_out = step_host(scvs, ctx, wl, m, N, P, d, hb)
             conv_e += sum(1 for r in rr if r["status"] == scvs.SCVS_CONVERGED)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -305,7 +306,8 @@ def run_gpu(args):
     achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
     traffic = traffic_from_profiles(dom)
     kernel_names = {"cheb_fine": "k_pc_cheb (velocity rows) + k_vel_residual", "arnoldi": "k_arnoldi",
-                    "spmm_fp32": "k_saddle<float>", "precond": "k_pressure_solve + k_coarse_solve + k_tri_vel0 + k_prolong",
+                    "spmm_fp32": "k_saddle<float>", "precond": "k_tri_vel0 + k_prolong + k_pc_step0",
+                    "pressure": "k_pressure_solve", "coarse": "k_coarse_solve",
                     "spmm_fp64": "k_saddle<double>"}
     roof = {"bound": "hbm", "kernel": kernel_names.get(dom, dom), "kernel_class": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind,
@@ -603,17 +605,43 @@ def run_fp64_permode(args):
     print(json.dumps(out), flush=True)
 
 
-def step_host(scvs, ctx, wl, m, N, P, d):
+def pinned_host_buffers(torch, wl, m, N, P, d):
+    """Inputs copied once into page-locked host memory and page-locked output
+    arrays, so the end-to-end step moves its bytes by DMA (set up outside the
+    timed region)."""
+    def pin(a):
+        t = torch.empty(a.shape, dtype=getattr(torch, a.dtype.name), pin_memory=True)
+        v = t.numpy()
+        v[...] = a
+        return t, v
+
     mesh = wl["mesh"]
+    keep, arrs = [], {}
+    for k, a in (("xyz", mesh["xyz"]), ("conn", mesh["conn"]), ("tag", mesh["tag"]), ("g", wl["g"])):
+        t, v = pin(np.ascontiguousarray(a))
+        keep.append(t)
+        arrs[k] = v
+    for k, shape, dt in (("u", (m, N, d), torch.complex128), ("p", (m, P), torch.complex128),
+                         ("ut", (N_T, N, d), torch.float64), ("pt", (N_T, P), torch.float64)):
+        t = torch.empty(shape, dtype=dt, pin_memory=True)
+        keep.append(t)
+        arrs[k] = t.numpy()
+    arrs["mesh"] = dict(mesh, xyz=arrs["xyz"], conn=arrs["conn"], tag=arrs["tag"])
+    arrs["_keep"] = keep
+    return arrs
+
+
+def step_host(scvs, ctx, wl, m, N, P, d, hb):
+    """One step through the host-array API: inputs from and results to pinned host memory."""
     scvs.scvs_clear_meshes(ctx)
-    mid = scvs.scvs_set_mesh(ctx, mesh)
+    mid = scvs.scvs_set_mesh(ctx, hb["mesh"])
     scvs.scvs_set_physics(ctx, mid, wl["rho"], wl["mu"])
-    scvs.scvs_set_modes(ctx, mid, wl["omegas"], wl["g"])
+    scvs.scvs_set_modes(ctx, mid, wl["omegas"], hb["g"])
     rep = scvs.scvs_solve(ctx, mid, m)
-    u, p = scvs.scvs_get_modal(ctx, mid, m, N, d, P)
-    ut, pt = scvs.scvs_reconstruct(ctx, mid, N_T, wl["period"], N, d, P)
-    nb_in = mesh["xyz"].nbytes + mesh["conn"].nbytes + mesh["tag"].nbytes + wl["g"].nbytes + wl["omegas"].nbytes
-    nb_out = u.nbytes + p.nbytes + ut.nbytes + pt.nbytes
+    scvs.scvs_get_modal(ctx, mid, m, N, d, P, out_u=hb["u"], out_p=hb["p"])
+    scvs.scvs_reconstruct(ctx, mid, N_T, wl["period"], N, d, P, out_u=hb["ut"], out_p=hb["pt"])
+    nb_in = sum(hb[k].nbytes for k in ("xyz", "conn", "tag", "g")) + wl["omegas"].nbytes
+    nb_out = sum(hb[k].nbytes for k in ("u", "p", "ut", "pt"))
     return rep, int(nb_in), int(nb_out)
 
 

@@ -305,17 +305,19 @@ int scvs_mlp_adam_step(scvs_ctx *ctx, double lr);
  * Optional CUDA-event timers around every kernel launch, recorded on the
  * context's stream, grouped in classes:
  *   0 all-modes SpMM FP32, 1 all-modes SpMM FP64 (lift, true residual),
- *   2 block preconditioner except its fine velocity sweeps, 3 Arnoldi
- *   orthogonalisation + Hessenberg, 4 elementwise vector kernels,
- *   5 pattern/assembly, 6 reconstruction, 7 matrix-free apply,
- *   8 fine velocity Chebyshev sweeps and residual of the preconditioner.
+ *   2 block preconditioner: step 0, right-hand side of the triangular form,
+ *   prolongation, 3 Arnoldi orthogonalisation + Hessenberg, 4 elementwise
+ *   vector kernels, 5 pattern/assembly, 6 reconstruction, 7 matrix-free
+ *   apply, 8 fine velocity Chebyshev sweeps and residual of the
+ *   preconditioner, 9 pressure Schur solve (persistent), 10 coarse velocity
+ *   solve (persistent).
  * Each class also sums the algorithmic bytes of its launches (the data the
  * kernel must read and write at minimum: matrix values and indices once,
  * every vector operand once).  scvs_kernel_timers(ctx, 1) clears and enables,
  * (ctx, 0) clears and disables.  scvs_kernel_times fills up to n_classes
  * entries of ms (summed device time), bytes and launches (any may be NULL)
  * and returns the number of classes. */
-#define SCVS_KC_COUNT 9
+#define SCVS_KC_COUNT 11
 int scvs_kernel_timers(scvs_ctx *ctx, int32_t enable);
 int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *bytes, int64_t *launches);
 

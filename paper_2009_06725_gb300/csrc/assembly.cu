@@ -343,6 +343,9 @@ __global__ void k_diag_f32(const double *__restrict__ a, float *__restrict__ b, 
   if (i < n) b[i] = (float)a[i];
 }
 
+// End vertices of every edge node.  All elements sharing an edge write its
+// entry; each writes the pair in ascending order, so the concurrent writes
+// carry identical values whatever the orientation of the edge in an element.
 __global__ void k_edge_ends(const int32_t *__restrict__ conn, int64_t E, int nl, int dim, int64_t P, int32_t *ends) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= E) return;
@@ -350,8 +353,9 @@ __global__ void k_edge_ends(const int32_t *__restrict__ conn, int64_t E, int nl,
   const int32_t *c = conn + e * nl;
   for (int k = 0; k < nl - nv; ++k) {
     const int64_t i = (int64_t)c[nv + k] - P;
-    ends[2 * i] = c[c_edge_pairs[k][0]];
-    ends[2 * i + 1] = c[c_edge_pairs[k][1]];
+    const int32_t a = c[c_edge_pairs[k][0]], b = c[c_edge_pairs[k][1]];
+    ends[2 * i] = min(a, b);
+    ends[2 * i + 1] = max(a, b);
   }
 }
 

@@ -520,8 +520,8 @@ __device__ __forceinline__ void pressure_row_step(const PcArgs &a, const ChebCoe
     for (int q = 0; q < cnt; ++q) {
       const int32_t Bc = gshfl<L>(gm, col, q);
       const T mq = gshfl<L>(gm, mv, q), lq = gshfl<L>(gm, lv, q);
-      if (cc.do_m) { CV<T, MPL> v; ldv<T, MPL>(v, zM + (int64_t)Bc * ld + koff); axpy(aMp, mq, v); }
-      if (cc.do_l) { CV<T, MPL> v; ldv<T, MPL>(v, zL + (int64_t)Bc * ld + koff); axpy(aLp, lq, v); }
+      if (cc.do_m) { CV<T, MPL> v; ldv_co<T, MPL>(v, zM + (int64_t)Bc * ld + koff); axpy(aMp, mq, v); }
+      if (cc.do_l) { CV<T, MPL> v; ldv_co<T, MPL>(v, zL + (int64_t)Bc * ld + koff); axpy(aLp, lq, v); }
     }
   }
   const int64_t rf = ((int64_t)DIM * a.N + B) * ld;
@@ -531,17 +531,17 @@ __device__ __forceinline__ void pressure_row_step(const PcArgs &a, const ChebCoe
   for (int i = 0; i < MPL; ++i) {
     const int k = koff + i;
     const int64_t pf = B * ld + k;
-    const C rv = r[rf + k];
+    const C rv = ld1co(r + rf + k);
     if (cc.do_m) {
-      const C z = zM[pf];
-      const C zp = cc.prev_zero_m ? mk<T>(0, 0) : zM_prev[pf];
+      const C z = ld1co(zM + pf);
+      const C zp = cc.prev_zero_m ? mk<T>(0, 0) : ld1co(zM_prev + pf);
       const T al = (T)cc.alpha_m, be = (T)cc.beta_m;
       zM_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dm * (rv.x - aMp.re[i]),
                           z.y + al * (z.y - zp.y) + be * dm * (rv.y - aMp.im[i]));
     }
     if (cc.do_l) {
-      const C z = zL[pf];
-      const C zp = cc.prev_zero_l ? mk<T>(0, 0) : zL_prev[pf];
+      const C z = ld1co(zL + pf);
+      const C zp = cc.prev_zero_l ? mk<T>(0, 0) : ld1co(zL_prev + pf);
       const T al = (T)cc.alpha_l, be = (T)cc.beta_l;
       const T rr = out ? T(0) : rv.x, ri = out ? T(0) : rv.y;
       zL_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dl * (rr - aLp.re[i]),
@@ -784,7 +784,7 @@ __device__ __forceinline__ void coarse_row_step(const PcArgs &a, const double *_
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         CV<T, MPL> xv;
-        ldv<T, MPL>(xv, zc + ((int64_t)B * DIM + c) * ld + koff);
+        ldv_co<T, MPL>(xv, zc + ((int64_t)B * DIM + c) * ld + koff);
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
           const T cf = kq + cr[i] * mq;
@@ -802,8 +802,8 @@ __device__ __forceinline__ void coarse_row_step(const PcArgs &a, const double *_
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const int64_t f = (v * DIM + c) * ld + k;
-      const C rv = rc[f], zv = zc[f];
-      const C zp = prev_zero ? mk<T>(0, 0) : zc_prev[f];
+      const C rv = ld1co(rc + f), zv = ld1co(zc + f);
+      const C zp = prev_zero ? mk<T>(0, 0) : ld1co(zc_prev + f);
       zc_prev[f] = mk<T>(zv.x + al * (zv.x - zp.x) + be * d * (rv.x - acc[c].re[i]),
                          zv.y + al * (zv.y - zp.y) + be * d * (rv.y - acc[c].im[i]));
     }
@@ -861,14 +861,14 @@ __device__ __forceinline__ void pressure_row_cached(const PcArgs &a, const ChebC
     if constexpr (DO_M) {
       CV<T, MPL> x[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ldv<T, MPL>(x[u], zM + (int64_t)__float_as_int(e[u].x) * ld + koff);
+      for (int u = 0; u < 4; ++u) ldv_co<T, MPL>(x[u], zM + (int64_t)__float_as_int(e[u].x) * ld + koff);
 #pragma unroll
       for (int u = 0; u < 4; ++u) axpy(aM, (T)e[u].y, x[u]);
     }
     if constexpr (DO_L) {
       CV<T, MPL> x[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ldv<T, MPL>(x[u], zL + (int64_t)__float_as_int(e[u].x) * ld + koff);
+      for (int u = 0; u < 4; ++u) ldv_co<T, MPL>(x[u], zL + (int64_t)__float_as_int(e[u].x) * ld + koff);
 #pragma unroll
       for (int u = 0; u < 4; ++u) axpy(aL, (T)e[u].z, x[u]);
     }
@@ -876,15 +876,15 @@ __device__ __forceinline__ void pressure_row_cached(const PcArgs &a, const ChebC
   for (; q < len; ++q) {
     const float4 e = ent[q];
     const int64_t Bc = __float_as_int(e.x);
-    if constexpr (DO_M) { CV<T, MPL> x; ldv<T, MPL>(x, zM + Bc * ld + koff); axpy(aM, (T)e.y, x); }
-    if constexpr (DO_L) { CV<T, MPL> x; ldv<T, MPL>(x, zL + Bc * ld + koff); axpy(aL, (T)e.z, x); }
+    if constexpr (DO_M) { CV<T, MPL> x; ldv_co<T, MPL>(x, zM + Bc * ld + koff); axpy(aM, (T)e.y, x); }
+    if constexpr (DO_L) { CV<T, MPL> x; ldv_co<T, MPL>(x, zL + Bc * ld + koff); axpy(aL, (T)e.z, x); }
   }
   CV<T, MPL> rv;
-  ldv<T, MPL>(rv, r + ((int64_t)DIM * a.N + B) * ld + koff);
+  ldv_co<T, MPL>(rv, r + ((int64_t)DIM * a.N + B) * ld + koff);
   if constexpr (DO_M) {
     CV<T, MPL> z, zp, o;
-    ldv<T, MPL>(z, zM + pf);
-    if (cc.prev_zero_m) zp.zero(); else ldv<T, MPL>(zp, zM_prev + pf);
+    ldv_co<T, MPL>(z, zM + pf);
+    if (cc.prev_zero_m) zp.zero(); else ldv_co<T, MPL>(zp, zM_prev + pf);
     const T al = (T)cc.alpha_m, be = (T)cc.beta_m, dm = (T)mt.x;
 #pragma unroll
     for (int i = 0; i < MPL; ++i) {
@@ -895,8 +895,8 @@ __device__ __forceinline__ void pressure_row_cached(const PcArgs &a, const ChebC
   }
   if constexpr (DO_L) {
     CV<T, MPL> z, zp, o;
-    ldv<T, MPL>(z, zL + pf);
-    if (cc.prev_zero_l) zp.zero(); else ldv<T, MPL>(zp, zL_prev + pf);
+    ldv_co<T, MPL>(z, zL + pf);
+    if (cc.prev_zero_l) zp.zero(); else ldv_co<T, MPL>(zp, zL_prev + pf);
     const T al = (T)cc.alpha_l, be = (T)cc.beta_l, dl = (T)mt.y;
     const bool out = mt.z != 0.f;
 #pragma unroll
@@ -953,8 +953,8 @@ __device__ __forceinline__ void coarse_row_cached(const PcArgs &a, const double 
     const int64_t b0 = (int64_t)__float_as_int(e0.x) * DIM, b1 = (int64_t)__float_as_int(e1.x) * DIM;
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
-      ldv<T, MPL>(x0[c], zc + (b0 + c) * ld + koff);
-      ldv<T, MPL>(x1[c], zc + (b1 + c) * ld + koff);
+      ldv_co<T, MPL>(x0[c], zc + (b0 + c) * ld + koff);
+      ldv_co<T, MPL>(x1[c], zc + (b1 + c) * ld + koff);
     }
     fma_row(e0, x0);
     fma_row(e1, x1);
@@ -964,16 +964,16 @@ __device__ __forceinline__ void coarse_row_cached(const PcArgs &a, const double 
     CV<T, MPL> x0[DIM];
     const int64_t b0 = (int64_t)__float_as_int(e0.x) * DIM;
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) ldv<T, MPL>(x0[c], zc + (b0 + c) * ld + koff);
+    for (int c = 0; c < DIM; ++c) ldv_co<T, MPL>(x0[c], zc + (b0 + c) * ld + koff);
     fma_row(e0, x0);
   }
 #pragma unroll
   for (int c = 0; c < DIM; ++c) {
     const int64_t f = (v * DIM + c) * ld + koff;
     CV<T, MPL> rv, zv, zp, o;
-    ldv<T, MPL>(rv, rc + f);
-    ldv<T, MPL>(zv, zc + f);
-    if (prev_zero) zp.zero(); else ldv<T, MPL>(zp, zc_prev + f);
+    ldv_co<T, MPL>(rv, rc + f);
+    ldv_co<T, MPL>(zv, zc + f);
+    if (prev_zero) zp.zero(); else ldv_co<T, MPL>(zp, zc_prev + f);
 #pragma unroll
     for (int i = 0; i < MPL; ++i) {
       const int k = koff + i;
@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(256, 3) k_coarse_solve(const PcArgs a, const C
     const int k = (int)(f % a.ld);
     if (row_idle(a.dof_comp, a.comp_active, v * DIM)) continue;
     const T sc = a.dirmask[v] ? T(0) : coarse_dinv<T>(a, v, k) * (T)q.inv_theta[k];
-    const auto r = q.rc[f];
+    const auto r = ld1co(q.rc + f);
     q.zc0[f] = mk<T>(sc * r.x, sc * r.y);
   }
   const int gpb = blockDim.x / L;
@@ -1145,7 +1145,7 @@ __global__ void __launch_bounds__(256, 3) k_pressure_solve(const PcArgs a, const
     const int k = (int)(e % ld);
     if (row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + e / ld)) continue;
     const T wr = p.sign * ((const T *)a.wrho)[k];
-    const C m_ = mc[e], l_ = lc[e];
+    const C m_ = ld1co(mc + e), l_ = ld1co(lc + e);
     p.z[fp + e] = mk<T>(mu * m_.x - wr * l_.y, mu * m_.y + wr * l_.x);
   }
 }
@@ -1369,7 +1369,7 @@ static void pressure_solve(Ctx &c, const Mesh &m, const PcArgs &a, const PcTable
     const int np = (ip < t.s_m) + (ip < t.s_l);
     by += (double)m.q_nnz * (4 + np * sizeof(T)) + (double)(m.P + 1) * 8 + pb + np * pb * (ip == 1 ? 2 : 3);
   }
-  KScope ks(c, KC_PRECOND, by);
+  KScope ks(c, KC_PRESSURE, by);
   PressureArgs<T> p{r, rscale, t.inv_theta_m, t.inv_theta_l, t.am_d, t.bm_d, t.al_d, t.bl_d, t.s_m, t.s_l,
                     pM[0], pM[1], pL[0], pL[1], z, sign, 0, c.gsync};
   PcArgs aa = a;
@@ -1393,7 +1393,7 @@ static typename cpx<T>::t *coarse_solve(Ctx &c, const Mesh &m, const PcArgs &a, 
               + 2 * cbk + (double)m.P * 2 * sizeof(T);                                                  // step 0
   for (int i = 1; i < t.s_c; ++i)
     by += (double)m.q_nnz * (4 + 2 * sizeof(T)) + (double)(m.P + 1) * 8 + cbk * (i == 1 ? 3 : 4);
-  KScope ks(c, KC_PRECOND, by);
+  KScope ks(c, KC_COARSE, by);
   CoarseArgs<T> q{rr, rc, zc[0], zc[1], t.inv_theta_c, t.alpha_c, t.beta_c, t.s_c, 0, c.gsync};
   PcArgs aa = a;
   SCVS_DISPATCH_LD(T, m.ld, {
@@ -1648,9 +1648,13 @@ k_jacobi_op(const PcArgs a, const typename cpx<T>::t *__restrict__ v, typename c
 
 // Per-mode 2-norms of a block of `rows` rows (free rows only where dirm != null,
 // rows indexed as velocity dofs), accumulated in double into out2[ld] (atomic).
+// Squared norm of every mode column of a block, deterministic: block b writes
+// its partial sums to part[b][ld]; k_block_norm2_finish adds them in block
+// order (the power-method bounds, and with them the Chebyshev intervals, are
+// then bitwise reproducible).
 template <typename T>
 __global__ void k_block_norm2(const typename cpx<T>::t *__restrict__ v, int64_t rows, int ld, int dim,
-                              const uint8_t *__restrict__ dirm, double *out2) {
+                              const uint8_t *__restrict__ dirm, double *part) {
   __shared__ double s[256];
   double acc = 0.0;
   const int64_t total = rows * ld;
@@ -1665,7 +1669,15 @@ __global__ void k_block_norm2(const typename cpx<T>::t *__restrict__ v, int64_t 
     if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < ld) atomicAdd(&out2[threadIdx.x], s[threadIdx.x]);
+  if (threadIdx.x < ld) part[(int64_t)blockIdx.x * ld + threadIdx.x] = s[threadIdx.x];
+}
+
+__global__ void k_block_norm2_finish(const double *__restrict__ part, int nblocks, int ld, double *out2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ld) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblocks; ++b) acc += part[(int64_t)b * ld + k];
+  out2[k] = acc;
 }
 
 __global__ void k_init_random(float2 *v, int64_t n) {
@@ -1687,7 +1699,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   const int64_t total = m.n_dof * ld;
   float2 *v = nullptr, *y = nullptr, *vM = nullptr, *yM = nullptr, *vL = nullptr, *yL = nullptr;
   float2 *vC = nullptr, *yC = nullptr;
-  double *n2 = nullptr;
+  double *n2 = nullptr, *part = nullptr;
   SCVS_CUDA(ctx_malloc(c, &v, total * sizeof(float2), c.stream));
   SCVS_CUDA(ctx_malloc(c, &y, total * sizeof(float2), c.stream));
   SCVS_CUDA(ctx_malloc(c, &vM, np * sizeof(float2), c.stream));
@@ -1704,6 +1716,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   c.launches.n += 4;
   const PcArgs a = pc_args<float>(m);
   const unsigned nbn = (unsigned)std::min<int64_t>(ceil_div(total, 256), 4 * c.num_sms);
+  SCVS_CUDA(ctx_malloc(c, &part, (size_t)4 * nbn * ld * sizeof(double), c.stream));  // per-block partial norms
   std::vector<double> h(4 * ld, 0.0);
   const int iters = 40;
   for (int it = 0; it < iters; ++it) {
@@ -1718,12 +1731,15 @@ void spectral_bounds(Ctx &c, Mesh &m) {
       else
         k_jacobi_op<float, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, v, y, vM, yM, vL, yL, vC, yC, vn2);
     });
-    SCVS_CUDA(cudaMemsetAsync(yn2, 0, 4 * ld * sizeof(double), c.stream));
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(y, (int64_t)m.dim * m.N, ld, m.dim, m.dirmask, yn2);
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yM, m.P, ld, 1, nullptr, yn2 + ld);
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yL, m.P, ld, 1, nullptr, yn2 + 2 * ld);
-    k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(yC, m.P, ld, 1, nullptr, yn2 + 3 * ld);
-    c.launches.n += 5;
+    const float2 *blocks[4] = {y, yM, yL, yC};
+    for (int q = 0; q < 4; ++q) {
+      const int64_t rows = q == 0 ? (int64_t)m.dim * m.N : m.P;
+      k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(blocks[q], rows, ld, q == 0 ? m.dim : 1,
+                                                      q == 0 ? m.dirmask : nullptr, part + (size_t)q * nbn * ld);
+      k_block_norm2_finish<<<ceil_div(ld, 128), 128, 0, c.stream>>>(part + (size_t)q * nbn * ld, (int)nbn, ld,
+                                                                   yn2 + q * ld);
+    }
+    c.launches.n += 9;
     if (it == iters - 1) {
       // the input had unit norm: ||y|| is the Rayleigh-type estimate
       SCVS_CUDA(cudaMemcpyAsync(h.data(), yn2, 4 * ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
@@ -1744,6 +1760,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   for (int k = 0; k < ld; ++k) m.lam_c[k] = std::sqrt(h[3 * ld + k]);
   for (float2 *p : {v, y, vM, yM, vL, yL, vC, yC}) SCVS_CUDA(cudaFreeAsync(p, c.stream));
   SCVS_CUDA(cudaFreeAsync(n2, c.stream));
+  SCVS_CUDA(cudaFreeAsync(part, c.stream));
 }
 
 // Residual of the current FP64 iterate: r = b - A_hat x (FP64 SpMM) and the

@@ -45,7 +45,7 @@ struct Launches { int64_t n = 0; };
 // Kernel classes timed by the optional event timers (scvs_kernel_timers).
 enum KClass : int {
   KC_SPMM32 = 0, KC_SPMM64, KC_PRECOND, KC_ARNOLDI, KC_VECTOR, KC_ASSEMBLY, KC_RECON, KC_MATFREE, KC_CHEB_FINE,
-  KC_COUNT
+  KC_PRESSURE, KC_COARSE, KC_COUNT
 };
 
 // CUDA-event timing of kernel launches on the launching stream: a start and a

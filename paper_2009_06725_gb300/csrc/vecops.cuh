@@ -45,6 +45,29 @@ __device__ __forceinline__ void ldv_cg<float, 2>(CV<float, 2> &v, const float2 *
   v.re[0] = f.x; v.im[0] = f.y; v.re[1] = f.z; v.im[1] = f.w;
 }
 
+// Coherent loads (ld.global.ca, never the read-only path) for data a
+// persistent kernel itself wrote before a grid barrier: the read-only path is
+// only valid for data that stays unchanged for the whole launch.
+__device__ __forceinline__ float2 ld1co(const float2 *p) { return __ldca(p); }
+__device__ __forceinline__ double2 ld1co(const double2 *p) { return __ldca(p); }
+template <typename T, int MPL>
+__device__ __forceinline__ void ldv_co(CV<T, MPL> &v, const typename cpx<T>::t *p) {
+#pragma unroll
+  for (int i = 0; i < MPL; ++i) { auto z = ld1co(p + i); v.re[i] = z.x; v.im[i] = z.y; }
+}
+template <>
+__device__ __forceinline__ void ldv_co<float, 2>(CV<float, 2> &v, const float2 *p) {
+  float4 f = __ldca(reinterpret_cast<const float4 *>(p));
+  v.re[0] = f.x; v.im[0] = f.y; v.re[1] = f.z; v.im[1] = f.w;
+}
+template <>
+__device__ __forceinline__ void ldv_co<float, 4>(CV<float, 4> &v, const float2 *p) {
+  float4 f = __ldca(reinterpret_cast<const float4 *>(p));
+  float4 g = __ldca(reinterpret_cast<const float4 *>(p) + 1);
+  v.re[0] = f.x; v.im[0] = f.y; v.re[1] = f.z; v.im[1] = f.w;
+  v.re[2] = g.x; v.im[2] = g.y; v.re[3] = g.z; v.im[3] = g.w;
+}
+
 template <typename T, int MPL>
 __device__ __forceinline__ void stv(typename cpx<T>::t *p, const CV<T, MPL> &v) {
 #pragma unroll

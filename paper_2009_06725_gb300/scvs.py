@@ -25,7 +25,7 @@ SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
 SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG = 0, 1, 2, 3
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
-SCVS_KC_COUNT = 9
+SCVS_KC_COUNT = 11
 SCVS_RECON_STATIC_MAX = 8192
 SCVS_TUNE_TILES = 5
 TUNE_TILES = (1, 2, 4, 8, 16)
@@ -107,7 +107,7 @@ SIGNATURES = {
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
 }
 KERNEL_CLASSES = ["spmm_fp32", "spmm_fp64", "precond", "arnoldi", "vector", "assembly", "reconstruct", "matfree",
-                  "cheb_fine"]
+                  "cheb_fine", "pressure", "coarse"]
 
 
 def lib():
@@ -216,9 +216,18 @@ def scvs_solve(ctx, mesh_id=-1, n_reports=0):
                  guess_used=r.guess_used, res0=r.res0) for r in rep[:n_reports]]
 
 
-def scvs_get_modal(ctx, mesh_id, n_modes, n_nodes, dim, n_vertices):
-    u = np.empty((n_modes, n_nodes, dim), dtype=np.complex128)
-    p = np.empty((n_modes, n_vertices), dtype=np.complex128)
+def _out(shape, dtype, out):
+    """Caller-provided output array (e.g. a pinned-memory view), checked, or a new one."""
+    if out is None:
+        return np.empty(shape, dtype=dtype)
+    if out.shape != tuple(shape) or out.dtype != dtype or not out.flags.c_contiguous or not out.flags.writeable:
+        raise ValueError(f"output array must be a writeable C-contiguous {np.dtype(dtype).name} array of shape {shape}")
+    return out
+
+
+def scvs_get_modal(ctx, mesh_id, n_modes, n_nodes, dim, n_vertices, out_u=None, out_p=None):
+    u = _out((n_modes, n_nodes, dim), np.complex128, out_u)
+    p = _out((n_modes, n_vertices), np.complex128, out_p)
     _check(ctx, lib().scvs_get_modal(ctx, mesh_id, _ptr(u), _ptr(p)))
     return u, p
 
@@ -231,9 +240,9 @@ def scvs_modal_dev(ctx, mesh_id):
     return x.value, n.value, ld.value
 
 
-def scvs_reconstruct(ctx, mesh_id, n_t, period, n_nodes, dim, n_vertices):
-    u = np.empty((n_t, n_nodes, dim), dtype=np.float64)
-    p = np.empty((n_t, n_vertices), dtype=np.float64)
+def scvs_reconstruct(ctx, mesh_id, n_t, period, n_nodes, dim, n_vertices, out_u=None, out_p=None):
+    u = _out((n_t, n_nodes, dim), np.float64, out_u)
+    p = _out((n_t, n_vertices), np.float64, out_p)
     _check(ctx, lib().scvs_reconstruct(ctx, mesh_id, n_t, period, _ptr(u), _ptr(p)))
     return u, p
 

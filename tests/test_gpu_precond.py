@@ -104,3 +104,17 @@ def test_triangular_needs_fewer_iterations(pipe):
         s.close()
         its[precond] = np.mean([r["iterations"] for r in rep])
     assert its[scvs.SCVS_PC_TRI_PMG] < 0.6 * its[scvs.SCVS_PC_BLOCK_PMG], its
+
+
+def test_precond_bitwise_reproducible_across_contexts(pipe):
+    """Two contexts that each build the mesh from scratch apply a bitwise
+    identical preconditioner (mesh tables, spectral bounds and every kernel
+    of the cycle are deterministic)."""
+    wl, mats = pipe
+    R = workloads.random_block(fem.dof_count(mats), M, seed=9)
+    outs = []
+    for _ in range(3):
+        s, mid = open_workload(wl, autotune=0)
+        with s:
+            outs.append(_apply(s, mid, R))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
