@@ -165,23 +165,6 @@ inline bool shape_valid(int ld, int mpl) { return mpl >= 1 && mpl <= 4 && ld % m
     }                                                                          \
   } while (0)
 
-// Wider row groups for the small L2-resident P1 solves: 4 FP32 modes per
-// lane from ld = 16 on, so each shuffled nonzero feeds twice the FMAs.
-#define SCVS_DISPATCH_LD_WIDE(T, ld, ...)                                      \
-  do {                                                                         \
-    if constexpr (sizeof(T) == 4) {                                            \
-      switch (ld) {                                                            \
-        SCVS_LD_CASE(2, 2, __VA_ARGS__) SCVS_LD_CASE(4, 2, __VA_ARGS__)        \
-        SCVS_LD_CASE(8, 2, __VA_ARGS__) SCVS_LD_CASE(16, 4, __VA_ARGS__)       \
-        SCVS_LD_CASE(32, 4, __VA_ARGS__) SCVS_LD_CASE(64, 4, __VA_ARGS__)      \
-        SCVS_LD_CASE(128, 4, __VA_ARGS__)                                      \
-        default: throw (int)SCVS_ERR_ARG;                                      \
-      }                                                                        \
-    } else {                                                                   \
-      SCVS_DISPATCH_LD(T, ld, __VA_ARGS__);                                    \
-    }                                                                          \
-  } while (0)
-
 // Row scheduling of the gather kernels.  Rows [lo, hi) are cut into tiles of
 // gpb * tile consecutive rows; block b takes tiles b, b + gridDim.x, ... and
 // its row groups walk a tile's rows in order.  Consecutive rows of a mesh
