@@ -1672,12 +1672,20 @@ __global__ void k_block_norm2(const typename cpx<T>::t *__restrict__ v, int64_t 
   if (threadIdx.x < ld) part[(int64_t)blockIdx.x * ld + threadIdx.x] = s[threadIdx.x];
 }
 
+// One block of 256 threads per mode column: strided partial sums, then a
+// shared-memory tree, both in a fixed order.
 __global__ void k_block_norm2_finish(const double *__restrict__ part, int nblocks, int ld, double *out2) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= ld) return;
+  __shared__ double s[256];
+  const int k = blockIdx.x;
   double acc = 0.0;
-  for (int b = 0; b < nblocks; ++b) acc += part[(int64_t)b * ld + k];
-  out2[k] = acc;
+  for (int b = threadIdx.x; b < nblocks; b += 256) acc += part[(int64_t)b * ld + k];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out2[k] = s[0];
 }
 
 __global__ void k_init_random(float2 *v, int64_t n) {
@@ -1739,8 +1747,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
       const int64_t rows = q == 0 ? (int64_t)m.dim * m.N : m.P;
       k_block_norm2<float><<<nbn, 256, 0, c.stream>>>(blocks[q], rows, ld, q == 0 ? m.dim : 1,
                                                       q == 0 ? m.dirmask : nullptr, part + (size_t)q * nbn * ld);
-      k_block_norm2_finish<<<ceil_div(ld, 128), 128, 0, c.stream>>>(part + (size_t)q * nbn * ld, (int)nbn, ld,
-                                                                   yn2 + q * ld);
+      k_block_norm2_finish<<<ld, 256, 0, c.stream>>>(part + (size_t)q * nbn * ld, (int)nbn, ld, yn2 + q * ld);
     }
     c.launches.n += 9;
     if (it == iters - 1) {
