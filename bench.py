@@ -46,6 +46,28 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def reduce_over_ranks(elapsed, count, device=None):
+    """Whole-job figures of a multi-rank run: the slowest rank's time and the
+    units all ranks completed (the only collectives of the path; a no-op for
+    one rank).  Works with any torch.distributed backend (NCCL with device
+    tensors, gloo with CPU tensors)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed), float(count)
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c)
+    return float(t.item()), float(c.item())
+
+
+def shard(items, rank, world):
+    """Independent units (meshes of a batch) dealt round-robin to the ranks:
+    every unit on exactly one rank, no exchange between ranks."""
+    return list(items)[rank::world]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -260,15 +282,7 @@ def run_gpu(args):
     conv = sum(1 for rr in reps for r in rr if r["status"] == scvs.SCVS_CONVERGED)
     tuned = scvs.scvs_tuned_shapes(ctx, 0)
     phase_ms = phases()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        c = torch.tensor([float(conv)], device=dev)
-        dist.all_reduce(c)
-        elapsed, conv_total = float(t.item()), float(c.item())
-    else:
-        conv_total = float(conv)
+    elapsed, conv_total = reduce_over_ranks(elapsed, conv, dev)
     value = conv_total / elapsed
 
     # ---- end to end through the host-pointer entry points
@@ -288,13 +302,7 @@ def run_gpu(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         te = max(ev0.elapsed_time(ev1) / 1e3, time.perf_counter() - t0)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            c = torch.tensor([float(conv_e)], device=dev)
-            dist.all_reduce(c)
-            te, conv_e = float(t.item()), float(c.item())
+        te, conv_e = reduce_over_ranks(te, conv_e, dev)
         e2e = {"value": conv_e / te, "unit": "mode-solves/s", "h2d_bytes_per_step": nb_in, "d2h_bytes_per_step": nb_out}
 
     if rank != 0:
@@ -374,12 +382,17 @@ def run_batch(args):
     modes each = 768 independent systems, solved as one mesh of independent
     components (one launch per kernel for all meshes)."""
     import torch
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     from paper_2009_06725_gb300 import build as pkg_build
     pkg_build.build()
     from paper_2009_06725_gb300 import scvs
-    parts = workloads.uneven_pipes(n_meshes=args.batch_meshes, n_modes=16, seed=0, scale=args.batch_scale)
+    all_parts = workloads.uneven_pipes(n_meshes=args.batch_meshes, n_modes=16, seed=0, scale=args.batch_scale)
+    parts = shard(all_parts, rank, world)  # each rank solves its own meshes; no exchange
     U = workloads.union_workload(parts)
     mesh = U["mesh"]
     N, P, E, d = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["conn"].shape[0], 3
@@ -404,29 +417,41 @@ def run_batch(args):
         scvs.scvs_reconstruct_dev(ctx, mid, N_T, U["period"], u_t.data_ptr(), p_t.data_ptr())
         return rep
 
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    barrier()
     scvs.scvs_kernel_timers(ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     reps = [step() for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
+    barrier()
     el = ev0.elapsed_time(ev1) / 1e3
     kt = scvs.scvs_kernel_times(ctx)
     conv = sum(1 for rr in reps for r in rr if r["status"] == scvs.SCVS_CONVERGED)
-    sizes = [p["mesh"]["xyz"].shape[0] for p in parts]
+    el, conv = reduce_over_ranks(el, conv, dev)
+    if rank != 0:
+        solver.close()
+        return
+    sizes = [p["mesh"]["xyz"].shape[0] for p in all_parts]
     out = {"metric": "converged mode-solves/s at 1e-8 rel. residual", "value": conv / el, "unit": "mode-solves/s",
-           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
            "impl": "batch",
-           "config": {"workload": (f"uneven batch: {len(parts)} stenosed pipes (R 0.5-1.5, L 5-20, s 0-0.5), "
-                                   f"{min(sizes)}-{max(sizes)} P2 nodes (total {N}), 16 modes each = "
-                                   f"{len(parts) * 16} systems, one mesh of independent components"),
-                      "systems": len(parts) * 16, "nodes_total": N},
+           "config": {"workload": (f"uneven batch: {len(all_parts)} stenosed pipes (R 0.5-1.5, L 5-20, s 0-0.5), "
+                                   f"{min(sizes)}-{max(sizes)} P2 nodes (rank 0: {len(parts)} meshes, {N} nodes), "
+                                   f"16 modes each = {len(all_parts) * 16} systems, one mesh of independent "
+                                   f"components per rank, meshes dealt round-robin to {world} rank(s)"),
+                      "systems": len(all_parts) * 16, "nodes_rank0": N},
            "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
-           "solve": {"converged": conv, "systems_per_step": len(parts) * 16,
+           "solve": {"converged": conv, "systems_per_step": len(all_parts) * 16,
                      "iterations_max": max(r["iterations"] for r in reps[-1]),
                      "iterations_mean": float(np.mean([r["iterations"] for r in reps[-1]])),
                      "rel_res_max": max(r["rel_res"] for r in reps[-1])}}
