@@ -435,17 +435,16 @@ __device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, int k) {
   return T(1) / ((T)a.mu * ((const T *)a.ksd)[A] + ((const T *)a.wabs)[k] * ((const T *)a.msd)[A]);
 }
 
-// Step 0 of every polynomial (elementwise): optionally rescale r by rscale[k]
-// (and write it back); z_u = r / (diag A_r theta_u[k]); pressure: zM = r/(diag M_p theta_M),
-// zL = r/(diag L_p theta_L) with r zeroed at outlet vertices.  Block-diagonal
-// mode: z_u = r / diag A_r, z_p = (mu/diag M_p + j omega rho/diag L_p) r.
-// The pass covers elements [0, f1) of the block (f1 = DIM N ld: velocity rows only).
+// Step 0 of the velocity polynomial (elementwise over elements [0, f1) of the
+// block), optionally rescaling r by rscale[k] first (written back: lazy
+// normalisation of the Krylov vector): z_u = r / (diag A_r theta_u[k]),
+// Dirichlet rows z_u = r.  The block-diagonal DIAG kind covers the whole block
+// (f1 = n_dof ld) with the diagonal blocks only: z_u = r / diag A_r and
+// z_p = (mu / diag M_p + j omega rho / diag L_p) r.  (The pressure polynomials
+// of the other kinds start inside k_pressure_solve.)
 template <typename T, int DIM, bool DIAG>
 __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *__restrict__ rscale,
-                           const int32_t *__restrict__ dof_comp,
-                           const double *__restrict__ inv_theta_u, double inv_theta_m, double inv_theta_l,
-                           typename cpx<T>::t *__restrict__ zu, typename cpx<T>::t *__restrict__ zM,
-                           typename cpx<T>::t *__restrict__ zL, int64_t f1) {
+                           const double *__restrict__ inv_theta_u, typename cpx<T>::t *__restrict__ zu, int64_t f1) {
   using C = typename cpx<T>::t;
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= f1) return;
@@ -454,7 +453,7 @@ __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *
   if (row_idle(a.dof_comp, a.comp_active, dof)) return;
   C v = r[f];
   if (rscale) {
-    T s = (T)rscale[(dof_comp ? dof_comp[dof] * a.ld : 0) + k];
+    T s = (T)rscale[(a.dof_comp ? a.dof_comp[dof] * a.ld : 0) + k];
     v.x *= s; v.y *= s;
     r[f] = v;
   }
@@ -463,29 +462,22 @@ __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *
     if (a.dirmask[A]) { zu[f] = v; return; }
     const T s = vel_dinv<T>(a, A, k) * (DIAG ? T(1) : (T)inv_theta_u[k]);
     zu[f] = mk<T>(s * v.x, s * v.y);
-  } else {
+  } else if (DIAG) {
     const int64_t B = dof - (int64_t)DIM * a.N;
-    const int64_t pf = B * a.ld + k;
     const bool out = a.outmask[B];
-    if (DIAG) {
-      double w = a.omega[k] * a.rho;
-      T cm = (T)(a.mu / a.mp_diag[B]);
-      T cl = out ? T(0) : (T)(w / a.lp_diag[B]);
-      // (cm + j cl) * v
-      zu[f] = mk<T>(cm * v.x - cl * v.y, cm * v.y + cl * v.x);
-    } else {
-      T sm = (T)inv_theta_m / ((const T *)a.mpd)[B];
-      zM[pf] = mk<T>(v.x * sm, v.y * sm);
-      T sl = out ? T(0) : (T)inv_theta_l / ((const T *)a.lpd)[B];
-      zL[pf] = mk<T>(v.x * sl, v.y * sl);
-    }
+    const double w = a.omega[k] * a.rho;
+    const T cm = (T)(a.mu / a.mp_diag[B]);
+    const T cl = out ? T(0) : (T)(w / a.lp_diag[B]);
+    zu[f] = mk<T>(cm * v.x - cl * v.y, cm * v.y + cl * v.x);  // (cm + j cl) v
   }
 }
 
-// Chebyshev step i >= 1 for the velocity rows (rows [0, N)) and the pressure
-// rows (rows [N, N+P), both polynomials):
-//   z_next = z + alpha (z - z_prev) + beta D^-1 (r - A z)
-// z_prev is overwritten by z_next (each row reads its own z_prev first).
+// Coefficients of one Chebyshev step i >= 1,
+//   z_next = z + alpha (z - z_prev) + beta D^-1 (r - A z),
+// of the velocity polynomial (k_pc_cheb: per-mode alpha_u, beta_u) or of the
+// two pressure polynomials (P1 mass and P1 Laplacian, stepped together by
+// k_pressure_solve).  z_prev is overwritten by z_next (each row reads its own
+// z_prev first).
 struct ChebCoef {
   const double *alpha_u, *beta_u;  // [ld] per mode (velocity)
   double alpha_m, beta_m, alpha_l, beta_l;
@@ -1423,9 +1415,9 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
     KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, total);
+      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, z, total);
     else
-      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, nullptr, 0, 0, z, nullptr, nullptr, total);
+      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, z, total);
     count_launch(c);
     return;
   }
@@ -1475,11 +1467,9 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     const int64_t fu = (int64_t)m.dim * m.N * m.ld;
     KScope ks0(c, KC_PRECOND, vb * (rscale ? 3 : 2) + (double)m.N * 17);
     if (m.dim == 2)
-      k_pc_step0<T, 2, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, 0, 0, uA,
-                                                                     nullptr, nullptr, fu);
+      k_pc_step0<T, 2, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, uA, fu);
     else
-      k_pc_step0<T, 3, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, m.dof_comp, t.inv_theta_u, 0, 0, uA,
-                                                                     nullptr, nullptr, fu);
+      k_pc_step0<T, 3, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, uA, fu);
     count_launch(c);
   }
   C *ucur = uA, *uprev = uB;

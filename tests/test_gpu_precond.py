@@ -118,3 +118,28 @@ def test_precond_bitwise_reproducible_across_contexts(pipe):
         with s:
             outs.append(_apply(s, mid, R))
     assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_diag_kind_against_definition(pipe):
+    """BLOCK_DIAG: z_u = r / diag(mu K_s + |omega| rho M_s) on free velocity rows,
+    z_u = r on Dirichlet rows, z_p = (mu / diag M_p + j omega rho / diag L_p) r_p
+    with the Laplacian term dropped on outlet vertices (p = 0 there)."""
+    wl, mats = pipe
+    N, P, d = mats["N"], mats["P"], 3
+    R = workloads.random_block(fem.dof_count(mats), M, seed=11)
+    s, mid = open_workload(wl, precond=scvs.SCVS_PC_BLOCK_DIAG)
+    with s:
+        Z = _apply(s, mid, R)
+    ks, ms = mats["Ks"].diagonal(), mats["Ms"].diagonal()
+    mp, lp = fem.p1_diagonals(wl["mesh"])
+    dirn = np.zeros(N, dtype=bool)
+    dirn[wl["dir_nodes"]] = True
+    out = (wl["mesh"]["tag"][:P] & 4) != 0
+    ref = np.empty_like(R)
+    for k in range(M):
+        w = wl["omegas"][k]
+        du = np.repeat(wl["mu"] * ks + abs(w) * wl["rho"] * ms, d)
+        ref[: d * N, k] = np.where(np.repeat(dirn, d), R[: d * N, k], R[: d * N, k] / du)
+        cp = wl["mu"] / mp + 1j * np.where(out, 0.0, w * wl["rho"] / lp)
+        ref[d * N:, k] = cp * R[d * N:, k]
+    _cols_close(Z, ref, 1e-6)
