@@ -526,6 +526,59 @@ def run_bifurcation(args):
     solver.close()
 
 
+def run_spmm(args):
+    """All-modes operator y_k = A_hat(omega_k) x_k on the benchmark pipe (32
+    modes): CSR SpMM and matrix-free apply, FP32 and FP64, each launch timed on
+    the library's stream after an L2 flush (a 512 MB write), algorithmic bytes
+    from the library's accounting (every matrix array and the geometry once, x
+    read once, y written once)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2009_06725_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2009_06725_gb300 import scvs
+    wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=PIPE["n_x"], n_modes=PIPE["n_modes"],
+                                 length=PIPE["length"])
+    peaks, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    with scvs.Solver(stream=stream.cuda_stream) as s:
+        mid = scvs.scvs_set_mesh(s.ctx, wl["mesh"])
+        scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
+        scvs.scvs_set_modes(s.ctx, mid, wl["omegas"], wl["g"])
+        n, ld = scvs.scvs_dof_count(s.ctx, mid), scvs.scvs_mode_stride(s.ctx, mid)
+        gen = torch.Generator(device=dev).manual_seed(0)
+        x64 = torch.randn((n, ld), dtype=torch.complex128, device=dev, generator=gen)
+        x32 = x64.to(torch.complex64)
+        y64, y32 = torch.empty_like(x64), torch.empty_like(x32)
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+        cases = [("csr_fp32", scvs.scvs_apply, scvs.SCVS_PREC_MIXED, x32, y32, "spmm_fp32"),
+                 ("csr_fp64", scvs.scvs_apply, scvs.SCVS_PREC_FP64, x64, y64, "spmm_fp64"),
+                 ("matfree_fp32", scvs.scvs_apply_matfree, scvs.SCVS_PREC_MIXED, x32, y32, "matfree"),
+                 ("matfree_fp64", scvs.scvs_apply_matfree, scvs.SCVS_PREC_FP64, x64, y64, "matfree")]
+        for name, fn, prec, x, y, cls in cases:
+            for _ in range(max(3, args.warmup)):
+                fn(s.ctx, mid, prec, x.data_ptr(), y.data_ptr())
+            torch.cuda.synchronize()
+            scvs.scvs_kernel_timers(s.ctx, True)
+            for _ in range(args.steps * 4):
+                flush.zero_()
+                fn(s.ctx, mid, prec, x.data_ptr(), y.data_ptr())
+            torch.cuda.synchronize()
+            ms, by, nl = scvs.scvs_kernel_times(s.ctx)[cls]
+            scvs.scvs_kernel_timers(s.ctx, False)
+            gbs = by / (ms / 1e3) / 1e9
+            out[name] = {"us_per_launch": round(ms / nl * 1e3, 1), "algorithmic_mb": round(by / nl / 1e6, 1),
+                         "gb_s": round(gbs, 1), "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 3)}
+    line = {"metric": "SpMM HBM GB/s (all-modes operator, algorithmic bytes)", "value": out["csr_fp32"]["gb_s"],
+            "unit": "GB/s", "n_gpus": 1, "higher_is_better": True, "impl": "spmm", "data": "synthetic",
+            "dtype": "c64", "peak": peaks["hbm_gbs"], "peak_source": peak_kind,
+            "config": {"workload": "151k-node pipe, 32 modes, 473,109 dofs/mode, L2 flushed before each launch"},
+            "cases": out}
+    print(json.dumps(line), flush=True)
+
+
 def run_guess(args):
     """Learned initial guess on the benchmark pipe family: train on morphs
     (R ~ U[0.5, 1.5], s ~ U[0, 0.5]) of the 151k-node pipe, then solve
@@ -699,7 +752,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")
-    ap.add_argument("--workload", default="pipe", choices=["pipe", "batch", "guess", "fp64-permode", "bifurcation"])
+    ap.add_argument("--workload", default="pipe",
+                    choices=["pipe", "batch", "guess", "fp64-permode", "bifurcation", "spmm"])
     ap.add_argument("--bif-h", type=float, default=0.038, help="voxel spacing of the bifurcation (0.038: ~6M nodes)")
     ap.add_argument("--fp64-modes", type=int, default=4)
     ap.add_argument("--batch-meshes", type=int, default=48)
@@ -716,6 +770,9 @@ def main():
         return
     if args.workload == "guess" and args.impl == "gpu":
         run_guess(args)
+        return
+    if args.workload == "spmm" and args.impl == "gpu":
+        run_spmm(args)
         return
     if args.workload == "bifurcation" and args.impl == "gpu":
         run_bifurcation(args)
