@@ -113,7 +113,7 @@ def run_reference(args):
     dt = float(np.mean(times))
     cb = cpu_baseline_obj(dt)
     out = {"metric": "converged mode-solves/s at 1e-8 rel. residual", "value": cb["value"],
-           "unit": "mode-solves/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "unit": "mode-solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt * 1e3 * PIPE["n_x"] / SAMPLE_LAYERS, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
            "impl": "reference", "config": workload_config(), "cpu_baseline": cb,

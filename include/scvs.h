@@ -132,7 +132,10 @@ typedef struct {
 void scvs_default_opts(scvs_opts *opts);
 
 /* Create a context on the current CUDA device.  opts may be NULL (defaults).
- * Owns every device buffer it allocates; released by scvs_destroy. */
+ * Owns every device buffer it allocates.  Its device memory comes from a
+ * memory pool of its own that keeps freed memory for reuse (re-creating a mesh
+ * or a Krylov workspace of a size seen before maps nothing new), so the
+ * context's footprint stays at its peak until scvs_destroy releases it. */
 int scvs_create(scvs_ctx **out, const scvs_opts *opts);
 void scvs_destroy(scvs_ctx *ctx);
 const char *scvs_last_error(const scvs_ctx *ctx);
@@ -249,15 +252,23 @@ int scvs_dof_count(scvs_ctx *ctx, int32_t mesh_id, int64_t *n_dof);
  * precision SCVS_PREC_MIXED: x, y float2 [n_dof][ld]; SCVS_PREC_FP64: double2.
  * Device pointers, caller-owned, on the context's stream. */
 int scvs_apply(scvs_ctx *ctx, int32_t mesh_id, int32_t precision, const void *x_dev, void *y_dev);
-/* Same operator evaluated element by element (matrix-free): gathers each
- * element's nodal block for all modes and contracts it with the element
- * matrices; same layouts and precisions as scvs_apply. */
+/* Same operator evaluated element by element (matrix-free): every row owner
+ * gathers the nodal blocks of its incident elements for all modes and
+ * contracts them with the element matrices (reference tables times the
+ * element's geometric factors), so no CSR values are read and no atomics are
+ * used; same layouts and precisions as scvs_apply. */
 int scvs_apply_matfree(scvs_ctx *ctx, int32_t mesh_id, int32_t precision, const void *x_dev, void *y_dev);
 /* Lifted right-hand side of every mode, FP64 double2 [n_dof][ld] (device view):
  * b_F = -A_FD g on free rows, b_D = g on Dirichlet rows. */
 int scvs_rhs_dev(scvs_ctx *ctx, int32_t mesh_id, const void **b_dev);
-/* Apply the block preconditioner P^{-1}(omega_k) of every mode:
- * z = P^{-1} r, FP32 float2 [n_dof][ld] device arrays. */
+/* Apply the block preconditioner P^{-1}(omega_k) of every mode, of the kind
+ * selected by opts.precond (default: block upper-triangular, SCVS_PC_TRI_PMG),
+ * exactly as the FP32 Krylov cycles apply it: z = P^{-1} r, FP32 float2
+ * [n_dof][ld] device arrays, r unchanged.  A linear operator in r (fixed
+ * polynomials, no inner products).  Synchronises the context's stream (to
+ * read the status of the bounded grid barriers of its persistent kernels:
+ * SCVS_ERR_TIMEOUT, z void, if one gave up).  SCVS_ERR_STATE before
+ * scvs_set_modes. */
 int scvs_apply_precond(scvs_ctx *ctx, int32_t mesh_id, const void *r_dev, void *z_dev);
 
 /* Number of kernel launches issued by this context since creation. */

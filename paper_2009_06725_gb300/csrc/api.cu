@@ -640,12 +640,22 @@ int scvs_rhs_dev(scvs_ctx *c, int32_t mesh_id, const void **b) {
 int scvs_apply_precond(scvs_ctx *c, int32_t mesh_id, const void *r, void *z) {
   return guarded(c, [&]() {
     Mesh *m = get_mesh(c, mesh_id);
-    if (!m || m->m == 0 || !r || !z) return fail(c, SCVS_ERR_ARG, "bad argument");
+    if (!m || !r || !z) return fail(c, SCVS_ERR_ARG, "bad argument");
+    if (m->m == 0) return fail(c, SCVS_ERR_STATE, "scvs_set_modes has not been called for this mesh");
     float2 *s = nullptr;
     SCVS_CUDA(ctx_malloc(*c, &s, precond_scratch_elems(*m) * sizeof(float2), c->stream));
     apply_precond<float>(*c, *m, static_cast<const float2 *>(r), static_cast<float2 *>(z), s, nullptr);
     SCVS_CUDA(cudaFreeAsync(s, c->stream));
     SCVS_CUDA(cudaGetLastError());
+    // the persistent pressure and coarse solves wait at bounded grid barriers
+    int gerr = 0;
+    SCVS_CUDA(cudaMemcpyAsync(&gerr, &c->gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    if (gerr) {
+      SCVS_CUDA(cudaMemsetAsync(c->gsync, 0, sizeof(GridSync), c->stream));
+      SCVS_CUDA(cudaStreamSynchronize(c->stream));
+      return fail(c, SCVS_ERR_TIMEOUT, "a grid barrier of the preconditioner gave up; z is void");
+    }
     return SCVS_OK;
   });
 }

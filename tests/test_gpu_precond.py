@@ -143,3 +143,16 @@ def test_diag_kind_against_definition(pipe):
         cp = wl["mu"] / mp + 1j * np.where(out, 0.0, w * wl["rho"] / lp)
         ref[d * N:, k] = cp * R[d * N:, k]
     _cols_close(Z, ref, 1e-6)
+
+
+def test_apply_precond_before_modes_is_a_state_error(pipe):
+    wl, mats = pipe
+    torch = torch_cuda()
+    n = fem.dof_count(mats)
+    with scvs.Solver() as s:
+        mid = scvs.scvs_set_mesh(s.ctx, wl["mesh"])
+        scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
+        x = torch.zeros((n, M), dtype=torch.complex64, device="cuda")
+        with pytest.raises(scvs.ScvsError) as e:
+            scvs.scvs_apply_precond(s.ctx, mid, x.data_ptr(), x.data_ptr())
+        assert e.value.code == scvs.SCVS_ERR_STATE
