@@ -559,8 +559,13 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   }
   for (auto &r : m.rep) r.guess_used = guess_on ? 1 : 0;
 
-  int *h_active = nullptr;
-  SCVS_CUDA(cudaMallocHost(&h_active, sizeof(int)));
+  // page-locked word for the per-step active-system count, freed on every exit path
+  struct PinnedInt {
+    int *p = nullptr;
+    ~PinnedInt() { if (p) cudaFreeHost(p); }
+  } pinned;
+  SCVS_CUDA(cudaMallocHost(&pinned.p, sizeof(int)));
+  int *h_active = pinned.p;
   std::vector<double> n2(S);
   std::vector<int> state(S), kd(S);
   const int max_cycles = std::max(1, c.opts.max_cycles);
@@ -649,7 +654,6 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       if (gerr) {
         SCVS_CUDA(cudaMemsetAsync(c.gsync, 0, sizeof(GridSync), c.stream));
         SCVS_CUDA(cudaStreamSynchronize(c.stream));
-        cudaFreeHost(h_active);
         return SCVS_ERR_TIMEOUT;
       }
     }
@@ -679,7 +683,6 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       }
     }
   }
-  cudaFreeHost(h_active);
   if (m.n_comp > 1) SCVS_CUDA(cudaMemsetAsync(m.comp_active, 1, m.n_comp, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
   return SCVS_OK;
