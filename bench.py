@@ -77,11 +77,11 @@ def measured_peaks():
 
 # ----------------------------------------------------------------- oracle
 
-def oracle_sample(mode=1):
-    """One mode of a 4-layer slice of the benchmark pipe: assembly + LU (FP64)."""
+def oracle_sample(mode=1, layers=SAMPLE_LAYERS):
+    """One mode of a `layers`-layer slice of the benchmark pipe: assembly + LU (FP64)."""
     from oracle import fem
-    L = PIPE["length"] * SAMPLE_LAYERS / PIPE["n_x"]
-    wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=SAMPLE_LAYERS, n_modes=mode + 1, length=L)
+    L = PIPE["length"] * layers / PIPE["n_x"]
+    wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=layers, n_modes=mode + 1, length=L)
     wl1 = dict(wl, omegas=wl["omegas"][mode:mode + 1], g=wl["g"][mode:mode + 1])
     t = time.perf_counter()
     mats = fem.assemble(wl1["mesh"])
@@ -91,13 +91,29 @@ def oracle_sample(mode=1):
     return dt, fem.dof_count(mats)
 
 
-def cpu_baseline_obj(dt):
+def growth_exponent(small, large):
+    """Measured exponent a of t ~ n_dofs^a between two slices (dt, n_dofs)."""
+    (t1, n1), (t2, n2) = small, large
+    return float(np.log(t2 / t1) / np.log(n2 / n1))
+
+
+def cpu_baseline_obj(dt, n, small=None):
+    """Oracle rate on the full pipe, from the SAMPLE_LAYERS slice scaled
+    linearly in length.  LU cost grows faster than linearly in the slice's
+    dof count (`small`, a shorter slice, measures by how much), so the
+    linear scaling is an upper bound on the oracle's full-size rate."""
     scale = PIPE["n_x"] / SAMPLE_LAYERS
-    return {"value": 1.0 / (dt * scale), "unit": "mode-solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"1 mode (k=1) of a {SAMPLE_LAYERS}-layer slice of the same pipe section "
-                       f"(assembly + SuperLU, FP64) in {dt:.2f} s, time scaled x{scale:.2f} to the "
-                       f"71-layer pipe; the LU cost grows faster than linearly with the slice "
-                       f"length, so this overstates the oracle's full-size rate")}
+    grow = ""
+    out = {"value": 1.0 / (dt * scale), "unit": "mode-solves/s", "cores": 1, "kind": "oracle"}
+    if small is not None:
+        a = growth_exponent(small, (dt, n))
+        out["growth_exponent"] = round(a, 2)
+        grow = (f"; a {SAMPLE_LAYERS // 2}-layer slice ({small[1]} dofs) took {small[0]:.2f} s, so the cost grows "
+                f"as n_dofs^{a:.1f} there")
+    out["sample"] = (f"1 mode (k=1) of a {SAMPLE_LAYERS}-layer slice ({n} dofs) of the same pipe section "
+                     f"(assembly + SuperLU, FP64) in {dt:.2f} s, time scaled x{scale:.2f} (linear in length) to "
+                     f"the 71-layer pipe{grow}; linear scaling is an upper bound on the oracle's full-size rate")
+    return out
 
 
 def run_reference(args):
@@ -108,10 +124,10 @@ def run_reference(args):
         oracle_sample()
     times = []
     for _ in range(args.steps):
-        dt, _ = oracle_sample()
+        dt, n = oracle_sample()
         times.append(dt)
     dt = float(np.mean(times))
-    cb = cpu_baseline_obj(dt)
+    cb = cpu_baseline_obj(dt, n, oracle_sample(layers=SAMPLE_LAYERS // 2))
     out = {"metric": "converged mode-solves/s at 1e-8 rel. residual", "value": cb["value"],
            "unit": "mode-solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt * 1e3 * PIPE["n_x"] / SAMPLE_LAYERS, "higher_is_better": True,
@@ -194,8 +210,9 @@ def run_gpu(args):
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, _ = oracle_sample()
-        cb = cpu_baseline_obj(dt)
+        small = oracle_sample(layers=SAMPLE_LAYERS // 2)
+        dt, n = oracle_sample()
+        cb = cpu_baseline_obj(dt, n, small)
 
     wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=PIPE["n_x"], n_modes=PIPE["n_modes"],
                                  length=PIPE["length"])
