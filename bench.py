@@ -196,6 +196,16 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- GPU
 
+def pc_opts(args):
+    """Preconditioner options given on the command line (library defaults otherwise)."""
+    o = {}
+    if args.precond is not None:
+        o["precond"] = args.precond
+    if args.schur_agg:
+        o["schur_agg"] = args.schur_agg
+    return o
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -225,8 +235,7 @@ def run_gpu(args):
     for k in ("cheb_u", "cheb_m", "cheb_l", "cheb_c", "restart"):
         if getattr(args, k):
             opts[k] = getattr(args, k)
-    if args.precond is not None:
-        opts["precond"] = args.precond
+    opts.update(pc_opts(args))
     solver = scvs.Solver(**opts)
     ctx = solver.ctx
     # device-resident inputs
@@ -415,7 +424,7 @@ def run_batch(args):
     N, P, E, d = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["conn"].shape[0], 3
     m = len(U["omegas"])
     stream = torch.cuda.current_stream(dev)
-    solver = scvs.Solver(stream=stream.cuda_stream)
+    solver = scvs.Solver(stream=stream.cuda_stream, **pc_opts(args))
     ctx = solver.ctx
     xyz_d = torch.from_numpy(mesh["xyz"]).to(dev)
     conn_d = torch.from_numpy(mesh["conn"]).to(dev)
@@ -493,7 +502,7 @@ def run_bifurcation(args):
     N, P, E, d = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["conn"].shape[0], 3
     m = len(wl["omegas"])
     stream = torch.cuda.current_stream(dev)
-    solver = scvs.Solver(stream=stream.cuda_stream, restart=20)
+    solver = scvs.Solver(stream=stream.cuda_stream, restart=20, **pc_opts(args))
     ctx = solver.ctx
     xyz_d = torch.from_numpy(mesh["xyz"]).to(dev)
     conn_d = torch.from_numpy(mesh["conn"]).to(dev)
@@ -765,7 +774,9 @@ def main():
     ap.add_argument("--cheb-l", type=int, default=0)
     ap.add_argument("--cheb-c", type=int, default=0)
     ap.add_argument("--restart", type=int, default=0)
-    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG, 3 TRI_PMG (default)")
+    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG, 3 TRI_PMG (default), "
+                    "4 TRI_PMG_CS (coarse Schur correction; pipe, batch and bifurcation workloads)")
+    ap.add_argument("--schur-agg", type=int, default=0, help="aggregates per component of TRI_PMG_CS (default 96)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")

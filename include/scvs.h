@@ -78,6 +78,13 @@ extern "C" {
 #define SCVS_PC_TRI_PMG 3      /* block upper-triangular [A_u D; 0 S~] with the Schur complement approximation
                                   S~^-1 = -(mu M_p^-1 + j omega rho L_p^-1) (pressure first), then the velocity
                                   p-multigrid cycle of BLOCK_PMG on r_u - D z_p (default) */
+#define SCVS_PC_TRI_PMG_CS 4   /* TRI_PMG with an additive coarse correction of the Schur approximation:
+                                  S~^-1 = -(mu M_p^-1 + j omega rho L_p^-1 + R_c (R_c^T D^T A~_u^-1 D R_c)^-1 R_c^T),
+                                  R_c piecewise constant on graph aggregates of the vertices (opts.schur_agg per
+                                  connected component), A~_u^-1 the velocity cycle of the preconditioner itself.
+                                  The n_c x n_c matrices (real: the cycle is real-linear) are formed and inverted
+                                  in FP64 on the first application after scvs_set_modes / scvs_set_physics /
+                                  an option change (n_c/2 velocity cycles for all modes at once) */
 
 #define SCVS_GUESS_ZERO 0
 #define SCVS_GUESS_MLP 1
@@ -103,6 +110,10 @@ typedef struct {
                         context for meshes of the same size (dim, nodes, vertices, nonzeros, mode
                         stride, components) and reused; 0: default shapes */
   void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
+  int32_t schur_agg; /* SCVS_PC_TRI_PMG_CS: aggregates per connected component of the vertex graph (1..512;
+                        0 or default: 96); aggregates are grown to ceil(vertices / schur_agg) vertices, so a
+                        component may end with somewhat more or fewer */
+  int32_t reserved;
 } scvs_opts;
 
 /* Options of scvs_train_guess (learned initial guess). */
@@ -343,6 +354,35 @@ int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *byte
  * 0 = candidate not valid for the mode stride.  Either pointer may be NULL. */
 #define SCVS_TUNE_TILES 5
 int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *shape, float *us);
+
+/* Graph aggregates of a vertex graph, the coarse space of SCVS_PC_TRI_PMG_CS
+ * (no paper counterpart: part of the preconditioner).  Host only: no context,
+ * no device work.
+ *   n_vert         number of vertices (>= 0)
+ *   row_ptr        [n_vert + 1] CSR row pointers (host, int64, non-decreasing, row_ptr[0] = 0)
+ *   col            [row_ptr[n_vert]] neighbours of every vertex (host, int32; the vertex itself may be
+ *                  listed; every entry must lie in [0, n_vert))
+ *   target         aggregates per connected component (1..512)
+ *   agg            [n_vert] out: aggregate of every vertex
+ *   n_agg, n_blk   out (may be NULL): number of aggregates and of connected components
+ * Connected components are numbered in the order of their lowest vertex; in
+ * each, aggregates are grown breadth-first (neighbours in row order) from the
+ * lowest unassigned vertex up to ceil(g * component size / target) vertices
+ * (g = 1, raised 1.5x until no component has more than min(2 target, 1024)
+ * aggregates); an aggregate below a third of that size joins the first
+ * full-size aggregate adjacent to it.  Every aggregate is connected and lies
+ * in one component; aggregates are numbered by component, then by seed.  The
+ * result depends only on the arguments.  Returns SCVS_OK or SCVS_ERR_ARG
+ * (null pointer, bad size, pointer or column out of range). */
+int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t *col, int32_t target,
+                          int32_t *agg, int32_t *n_agg, int32_t *n_blk);
+
+/* State of the coarse Schur correction of a mesh after its last setup
+ * (SCVS_PC_TRI_PMG_CS): info[4] = {aggregates, connected components, largest
+ * component's aggregates, singular (component, mode) coarse matrices, whose
+ * correction is off}; all 0 before the first application of that kind after
+ * scvs_set_modes. */
+int scvs_schur_coarse_info(scvs_ctx *ctx, int32_t mesh_id, int32_t *info);
 
 #ifdef __cplusplus
 }

@@ -246,6 +246,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->guess = SCVS_GUESS_ZERO;
   o->verbose = 0;
   o->stream = nullptr;
+  o->schur_agg = 96;
 }
 
 int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
@@ -314,7 +315,8 @@ const char *scvs_last_error(const scvs_ctx *c) { return c ? c->err.c_str() : "nu
 int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
   if (!c || !o) return SCVS_ERR_ARG;
   if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
-      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_TRI_PMG)
+      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_TRI_PMG_CS ||
+      o->schur_agg < 0 || o->schur_agg > 512)
     return fail(c, SCVS_ERR_ARG, "invalid options");
   void *old_stream = c->opts.stream;
   if (o->stream != old_stream) {
@@ -794,6 +796,40 @@ int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *shape, float *us) {
     }
     if (us)
       for (int i = 0; i < 2 * 3 * SCVS_TUNE_TILES; ++i) us[i] = i < (int)m->tune_us.size() ? m->tune_us[i] : 0.0f;
+    return SCVS_OK;
+  });
+}
+
+int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t *col, int32_t target,
+                          int32_t *agg, int32_t *n_agg, int32_t *n_blk) {
+  if (n_vert < 0 || n_vert > INT32_MAX || !row_ptr || !agg || target < 1 || target > 512) return SCVS_ERR_ARG;
+  if (row_ptr[0] != 0) return SCVS_ERR_ARG;
+  for (int64_t v = 0; v < n_vert; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return SCVS_ERR_ARG;
+  if (row_ptr[n_vert] > 0 && !col) return SCVS_ERR_ARG;
+  for (int64_t e = 0; e < row_ptr[n_vert]; ++e)
+    if (col[e] < 0 || col[e] >= n_vert) return SCVS_ERR_ARG;
+  try {
+    const AggResult r = graph_aggregates(n_vert, row_ptr, col, target);
+    std::copy(r.agg.begin(), r.agg.end(), agg);
+    if (n_agg) *n_agg = (int32_t)r.blk.size();
+    if (n_blk) *n_blk = r.n_blk;
+  } catch (...) {
+    return SCVS_ERR_OOM;
+  }
+  return SCVS_OK;
+}
+
+int scvs_schur_coarse_info(scvs_ctx *c, int32_t mesh_id, int32_t *info) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !info) return fail(c, SCVS_ERR_ARG, "bad mesh id or null info");
+    const PcTables &t = m->pc;
+    const bool built = t.cs_bytes != 0;
+    info[0] = built ? t.n_agg : 0;
+    info[1] = built ? t.n_blk : 0;
+    info[2] = built ? t.na_max : 0;
+    info[3] = built ? t.cs_singular : 0;
     return SCVS_OK;
   });
 }

@@ -1291,7 +1291,8 @@ static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   const int sc = std::max(1, c.opts.cheb_c), kind = c.opts.precond;
   if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl && t.s_c == sc && t.kind == kind) return;
   t.s_u = su; t.s_m = sm; t.s_l = sl; t.s_c = sc; t.kind = kind;
-  const bool pmg = kind == SCVS_PC_BLOCK_PMG || kind == SCVS_PC_TRI_PMG;
+  t.cs_bytes = 0;  // the coarse Schur matrices depend on the velocity cycle
+  const bool pmg = kind == SCVS_PC_BLOCK_PMG || kind == SCVS_PC_TRI_PMG || kind == SCVS_PC_TRI_PMG_CS;
   per_mode_seq(c, m, m.lam_u, pmg ? CHEB_RATIO_SMOOTH : CHEB_RATIO_U, su, &t.inv_theta_u, &t.alpha_u, &t.beta_u);
   if (pmg) per_mode_seq(c, m, m.lam_c, CHEB_RATIO_C, sc, &t.inv_theta_c, &t.alpha_c, &t.beta_c);
   t.zeros = m.mode_arena.alloc<double>(m.ld);
@@ -1399,80 +1400,408 @@ static typename cpx<T>::t *coarse_solve(Ctx &c, const Mesh &m, const PcArgs &a, 
   return zc[(t.s_c - 1) % 2];
 }
 
-// z = P^-1 r for all modes (right block preconditioner).  scratch holds
-// precond_scratch_elems(m) elements.  rscale (device, [ld], may be null): r is
-// first scaled per mode and written back (lazy normalisation of v_j).
+// ---------------------------------------- coarse Schur correction
+// Additive two-level approximation of the inverse Schur complement (the
+// triangular form's pressure block): on top of the Cahouet-Chabard term, a
+// Galerkin coarse term R_c (R_c^T D^T A~_u^-1 D R_c)^-1 R_c^T with R_c the
+// piecewise-constant functions of graph aggregates of the vertices and A~_u^-1
+// the preconditioner's own velocity cycle.  The coarse space restores the
+// smooth, domain-long pressure modes that the mass/Laplacian combination
+// misses on elongated domains (the discrete inf-sup constant shrinks with the
+// aspect ratio).  The velocity cycle applies the real shift
+// mu K_s + |omega| rho M_s with real coefficients, so it is real-linear and
+// the coarse matrices are real; a complex lane carries two coarse columns.
+
+constexpr int CS_NA_MAX = 1024;  // aggregates of one block at most
+constexpr int CS_DEFAULT_AGG = 96;
+
+// q[a][k] = sum of r_p[v][k] over the vertices v of aggregate a.  One block per
+// aggregate; thread (chunk, k) sums every (256/ld)-th vertex in ascending order
+// in FP64, and the chunk partials are added in a fixed tree order.
 template <typename T>
-void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx<T>::t *z,
-                   typename cpx<T>::t *scratch, const double *rscale) {
-  using C = typename cpx<T>::t;
-  C *r = const_cast<C *>(r_in);
-  const PcArgs a = pc_args<T>(m);
-  const int64_t total = m.n_dof * m.ld;
-  const unsigned eb = ceil_div(total, 256);
-  const double cs = 2.0 * sizeof(T), blk = (double)total * cs, pb = (double)m.P * m.ld * cs;
-  const double vb = (double)m.dim * m.N * m.ld * cs, cbk = (double)m.dim * m.P * m.ld * cs;
-  if (c.opts.precond == SCVS_PC_BLOCK_DIAG) {
-    KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
-    if (m.dim == 2)
-      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, z, total);
-    else
-      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, z, total);
-    count_launch(c);
-    return;
+__global__ void __launch_bounds__(256) k_agg_restrict(const int64_t *__restrict__ agg_ptr,
+                                                      const int32_t *__restrict__ agg_vert, int ld,
+                                                      const typename cpx<T>::t *__restrict__ rp,
+                                                      typename cpx<T>::t *__restrict__ q) {
+  __shared__ double2 part[256];
+  const int a = blockIdx.x;
+  const int k = threadIdx.x % ld, ch = threadIdx.x / ld, nch = blockDim.x / ld;
+  const int64_t v0 = agg_ptr[a], v1 = agg_ptr[a + 1];
+  double sx = 0, sy = 0;
+  for (int64_t i = v0 + ch; i < v1; i += nch) {
+    const typename cpx<T>::t v = rp[(int64_t)agg_vert[i] * ld + k];
+    sx += (double)v.x;
+    sy += (double)v.y;
   }
-  PcTables &t = m.pc;
-  pc_tables(c, m, t);
-  const bool tri = c.opts.precond == SCVS_PC_TRI_PMG;
-  const bool pmg = c.opts.precond == SCVS_PC_BLOCK_PMG || tri;
-  const int64_t pblk = m.P * m.ld, cblk = (int64_t)m.dim * m.P * m.ld;
-  C *other = scratch;  // velocity part lives in dofs [0, dim N)
-  C *pM[2] = {scratch + total, scratch + total + pblk};
-  C *pL[2] = {scratch + total + 2 * pblk, scratch + total + 3 * pblk};
-  C *rc = scratch + total + 4 * pblk;
-  C *zc[2] = {rc + cblk, rc + 2 * cblk};
-  C *rt = rc + 3 * cblk;  // velocity right-hand side of the triangular form
-  // the velocity iterate ping-pongs between z and `other`; every Chebyshev
-  // step moves it once, so the first iterate goes where the last one lands on z
-  const int moves = pmg ? (t.s_u - 1) + t.s_u : (t.s_u - 1);
-  C *uA = (moves % 2 == 0) ? z : other;
-  C *uB = (uA == z) ? other : z;
-  // 1. pressure block: z_p = -/+ (mu M_p^-1 + j omega rho L_p^-1) r_p (minus: Schur
-  //    complement of the triangular form; plus: block-diagonal form)
-  pressure_solve<T>(c, m, a, t, r, rscale, pM, pL, z, tri ? T(-1) : T(1));
-  // 2. velocity right-hand side and step 0 of the velocity polynomial
-  const C *ru = r;
-  if (tri) {
-    KScope ks(c, KC_PRECOND, vb * (rscale ? 4 : 3) + (double)m.g_nnz * (4 + m.dim * sizeof(T)) + pb +
-                                 (double)(m.N + 1) * 8 + (double)m.N * 17);
-    auto body = [&](auto mpl_c, auto l_c) {
-      constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
-      const int gpb = 256 / L;
-      const unsigned nb = row_blocks(c, m.N, gpb, a.tile);
-      const C *zp = z + (int64_t)m.dim * m.N * m.ld;
-      if (m.dim == 2)
-        k_tri_vel0<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, zp, rt, uA);
-      else
-        k_tri_vel0<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, zp, rt, uA);
-    };
-    if constexpr (sizeof(T) == 4) {
-      const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
-      SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
-    } else {
-      SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+  part[threadIdx.x] = make_double2(sx, sy);
+  __syncthreads();
+  for (int h = nch / 2; h > 0; h >>= 1) {
+    if (ch < h) {
+      const double2 o = part[threadIdx.x + h * ld];
+      part[threadIdx.x].x += o.x;
+      part[threadIdx.x].y += o.y;
     }
-    count_launch(c);
-    ru = rt;
-  } else {
-    const int64_t fu = (int64_t)m.dim * m.N * m.ld;
-    KScope ks0(c, KC_PRECOND, vb * (rscale ? 3 : 2) + (double)m.N * 17);
-    if (m.dim == 2)
-      k_pc_step0<T, 2, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, uA, fu);
-    else
-      k_pc_step0<T, 3, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, uA, fu);
-    count_launch(c);
+    __syncthreads();
   }
-  C *ucur = uA, *uprev = uB;
+  if (ch == 0) q[(int64_t)a * ld + k] = mk<T>((T)part[k].x, (T)part[k].y);
+}
+
+// Setup: pressure block of the coarse columns j (real part) and j+1 (imaginary
+// part) of every block: z_p[v][k] = [loc(v) == j] + i [loc(v) == j+1].
+template <typename T>
+__global__ void k_agg_indicator(const int32_t *__restrict__ agg, const int32_t *__restrict__ agg_loc, int64_t P,
+                                int ld, int j, typename cpx<T>::t *__restrict__ zp) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= P * ld) return;
+  const int l = agg_loc[agg[f / ld]];
+  zp[f] = mk<T>(l == j ? T(1) : T(0), l == j + 1 ? T(1) : T(0));
+}
+
+// Setup: store the restricted images q = R_c^T D^T X of columns j, j+1 (X =
+// -A~_u^-1 D R_c [e_j + i e_{j+1}]) as columns j, j+1 of the FP64 coarse matrix
+// of every (block, mode), S = R_c^T D^T A~_u^-1 D R_c.  W holds per block and
+// mode the augmented n x 2n matrix [S | I] (row-major) for the inversion.
+template <typename T>
+__global__ void k_cs_column(const int32_t *__restrict__ agg_blk, const int32_t *__restrict__ agg_loc,
+                            const int32_t *__restrict__ blk_na, const int64_t *__restrict__ blk_so, int n_agg, int ld,
+                            int j, const typename cpx<T>::t *__restrict__ q, double *__restrict__ W) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)n_agg * ld) return;
+  const int a = (int)(f / ld), k = (int)(f % ld);
+  const int b = agg_blk[a], n = blk_na[b];
+  if (j >= n) return;
+  const int i = agg_loc[a];
+  double *A = W + 2 * blk_so[b] * ld + (int64_t)k * 2 * n * n;
+  const typename cpx<T>::t v = q[f];
+  A[(int64_t)i * 2 * n + j] = -(double)v.x;
+  if (j + 1 < n) A[(int64_t)i * 2 * n + j + 1] = -(double)v.y;
+}
+
+// Setup: invert the coarse matrix of every (block, mode) by Gauss-Jordan
+// elimination with partial pivoting in FP64 (one thread block per matrix; the
+// pivot is the largest magnitude in the column, the lowest row on ties).  A
+// pivot below 1e-13 of the largest entry (or a non-finite entry) marks the
+// matrix singular: its inverse is written as zero, which switches the
+// correction off for that system, and *n_singular is incremented.  The
+// inverse is stored in T as sinv[(blk_so[b] + i n + j) ld + k].
+template <typename T>
+__global__ void __launch_bounds__(256) k_cs_invert(const int32_t *__restrict__ blk_na,
+                                                   const int64_t *__restrict__ blk_so, int ld, double *__restrict__ W,
+                                                   T *__restrict__ sinv, int *n_singular) {
+  extern __shared__ double cs_sh[];
+  const int b = blockIdx.x / ld, k = blockIdx.x % ld;
+  const int n = blk_na[b], w = 2 * n, tid = threadIdx.x, bd = blockDim.x;
+  double *A = W + 2 * blk_so[b] * ld + (int64_t)k * w * n;
+  double *f = cs_sh, *prow = cs_sh + n, *rv = cs_sh + 3 * n;
+  int *ri = reinterpret_cast<int *>(rv + bd);
+  double amax = 0;
+  for (int64_t e = tid; e < (int64_t)n * n; e += bd) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    A[(int64_t)i * w + n + c] = (i == c) ? 1.0 : 0.0;
+    const double v = fabs(A[(int64_t)i * w + c]);
+    amax = (v > amax || v != v) ? v : amax;  // NaN propagates
+  }
+  rv[tid] = amax;
+  __syncthreads();
+  for (int h = bd / 2; h > 0; h >>= 1) {
+    if (tid < h) {
+      const double o = rv[tid + h];
+      if (o > rv[tid] || o != o) rv[tid] = o;
+    }
+    __syncthreads();
+  }
+  amax = rv[0];
+  __syncthreads();
+  bool sing = !(amax > 0) || !isfinite(amax);
+  for (int p = 0; p < n && !sing; ++p) {
+    double best = -1;
+    int bi = n;
+    for (int i = p + tid; i < n; i += bd) {
+      const double v = fabs(A[(int64_t)i * w + p]);
+      if (v > best) { best = v; bi = i; }
+    }
+    rv[tid] = best;
+    ri[tid] = bi;
+    __syncthreads();
+    for (int h = bd / 2; h > 0; h >>= 1) {
+      if (tid < h) {
+        const double o = rv[tid + h];
+        const int oi = ri[tid + h];
+        if (o > rv[tid] || (o == rv[tid] && oi < ri[tid])) { rv[tid] = o; ri[tid] = oi; }
+      }
+      __syncthreads();
+    }
+    const int piv = ri[0];
+    const double pbest = rv[0];
+    if (!(pbest > 1e-13 * amax) || piv >= n) { sing = true; break; }  // uniform: read from shared memory
+    if (piv != p)
+      for (int c = p + tid; c < w; c += bd) {
+        const double x = A[(int64_t)p * w + c];
+        A[(int64_t)p * w + c] = A[(int64_t)piv * w + c];
+        A[(int64_t)piv * w + c] = x;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[(int64_t)p * w + p];
+    for (int c = p + tid; c < w; c += bd) prow[c] = A[(int64_t)p * w + c] * inv;
+    for (int i = tid; i < n; i += bd) f[i] = A[(int64_t)i * w + p];
+    __syncthreads();
+    // columns < p of the left half are unit columns already and row p is zero there
+    const int wc = w - p;
+    for (int64_t e = tid; e < (int64_t)n * wc; e += bd) {
+      const int i = (int)(e / wc), c = p + (int)(e % wc);
+      A[(int64_t)i * w + c] = (i == p) ? prow[c] : A[(int64_t)i * w + c] - f[i] * prow[c];
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)n * n; e += bd) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    sinv[(blk_so[b] + e) * ld + k] = sing ? T(0) : (T)A[(int64_t)i * w + n + c];
+  }
+  if (sing && tid == 0) atomicAdd(n_singular, 1);
+}
+
+// y[a][k] = sum_j Sinv_{b,k}[loc(a)][j] q[a0(b) + j][k]: the coarse solve of every
+// (block, mode), one thread per (aggregate, mode).
+template <typename T>
+__global__ void k_cs_product(const int32_t *__restrict__ agg_blk, const int32_t *__restrict__ agg_loc,
+                             const int32_t *__restrict__ blk_na, const int32_t *__restrict__ blk_a0,
+                             const int64_t *__restrict__ blk_so, int n_agg, int ld, const T *__restrict__ sinv,
+                             const typename cpx<T>::t *__restrict__ q, typename cpx<T>::t *__restrict__ y) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)n_agg * ld) return;
+  const int a = (int)(f / ld), k = (int)(f % ld);
+  const int b = agg_blk[a], n = blk_na[b], i = agg_loc[a];
+  const T *row = sinv + (blk_so[b] + (int64_t)i * n) * ld + k;
+  const typename cpx<T>::t *qb = q + (int64_t)blk_a0[b] * ld + k;
+  T sx = 0, sy = 0;
+  for (int j = 0; j < n; ++j) {
+    const T s = row[(int64_t)j * ld];
+    const typename cpx<T>::t v = qb[(int64_t)j * ld];
+    sx += s * v.x;
+    sy += s * v.y;
+  }
+  y[f] = mk<T>(sx, sy);
+}
+
+// z_p[v][k] -= y[agg(v)][k] (the triangular form's pressure block is -S~^-1 r_p);
+// rows of inactive components are left alone.
+template <typename T>
+__global__ void k_cs_broadcast(const PcArgs a, int dim, const int32_t *__restrict__ agg,
+                               const typename cpx<T>::t *__restrict__ y, typename cpx<T>::t *__restrict__ zp) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= a.P * a.ld) return;
+  const int64_t v = f / a.ld;
+  if (row_idle(a.dof_comp, a.comp_active, (int64_t)dim * a.N + v)) return;
+  const typename cpx<T>::t add = y[(int64_t)agg[v] * a.ld + f % a.ld];
+  typename cpx<T>::t o = zp[f];
+  o.x -= add.x;
+  o.y -= add.y;
+  zp[f] = o;
+}
+
+// Graph aggregates of the vertices (host, deterministic).  Connected
+// components become blocks (numbered by their lowest vertex); in each,
+// aggregates are grown breadth-first (neighbours in row order) from the lowest
+// unassigned vertex up to ceil(grow * vertices / target) vertices; an
+// aggregate left below a third of that size joins the first full-size
+// aggregate next to it (if any).  Aggregates are numbered by block, then by
+// seed.  grow starts at 1 and rises by 1.5x until no block has more than
+// min(2 target, CS_NA_MAX) aggregates.  Columns outside [0, P) are ignored.
+AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target) {
+  AggResult r;
+  std::vector<int32_t> comp(P, -1), queue;
+  std::vector<int64_t> csize;
+  queue.reserve(P);
+  auto valid = [&](int32_t u) { return u >= 0 && (int64_t)u < P; };
+  for (int64_t s0 = 0; s0 < P; ++s0) {
+    if (comp[s0] >= 0) continue;
+    const int32_t id = (int32_t)csize.size();
+    queue.clear();
+    queue.push_back((int32_t)s0);
+    comp[s0] = id;
+    for (size_t h = 0; h < queue.size(); ++h) {
+      const int64_t v = queue[h];
+      for (int64_t e = ptr[v]; e < ptr[v + 1]; ++e) {
+        const int32_t u = col[e];
+        if (valid(u) && comp[u] < 0) { comp[u] = id; queue.push_back(u); }
+      }
+    }
+    csize.push_back((int64_t)queue.size());
+  }
+  const int nb = (int)csize.size();
+  r.n_blk = nb;
+  r.agg.assign(P, -1);
+  r.na.assign(nb, 0);
+  r.a0.assign(nb, 0);
+  double grow = 1.0;
+  for (;;) {
+    std::vector<int64_t> size_b(nb);
+    for (int b = 0; b < nb; ++b) size_b[b] = std::max<int64_t>(1, (int64_t)std::ceil(grow * (double)csize[b] / target));
+    std::vector<int32_t> &agg = r.agg;
+    std::fill(agg.begin(), agg.end(), -1);
+    std::vector<int64_t> cnt;
+    std::vector<int32_t> seed_blk, frontier, next;
+    for (int64_t s0 = 0; s0 < P; ++s0) {
+      if (agg[s0] >= 0) continue;
+      const int32_t id = (int32_t)cnt.size();
+      const int64_t cap = size_b[comp[s0]];
+      int64_t n = 1;
+      agg[s0] = id;
+      frontier.assign(1, (int32_t)s0);
+      while (!frontier.empty() && n < cap) {
+        next.clear();
+        for (int32_t v : frontier)
+          for (int64_t e = ptr[v]; e < ptr[v + 1] && n < cap; ++e) {
+            const int32_t u = col[e];
+            if (valid(u) && agg[u] < 0) { agg[u] = id; ++n; next.push_back(u); }
+          }
+        frontier.swap(next);
+      }
+      cnt.push_back(n);
+      seed_blk.push_back(comp[s0]);
+    }
+    const int na0 = (int)cnt.size();
+    std::vector<int32_t> into(na0);
+    std::vector<char> small(na0);
+    for (int g = 0; g < na0; ++g) {
+      into[g] = g;
+      small[g] = 3 * cnt[g] < size_b[seed_blk[g]];
+    }
+    for (int64_t v = 0; v < P; ++v) {
+      const int32_t g = agg[v];
+      if (!small[g] || into[g] != g) continue;
+      for (int64_t e = ptr[v]; e < ptr[v + 1]; ++e) {
+        const int32_t u = col[e];
+        if (valid(u) && !small[agg[u]]) { into[g] = agg[u]; break; }
+      }
+    }
+    std::vector<int32_t> order;
+    for (int g = 0; g < na0; ++g)
+      if (into[g] == g) order.push_back(g);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return seed_blk[x] < seed_blk[y]; });
+    std::vector<int32_t> newid(na0, -1);
+    for (size_t i = 0; i < order.size(); ++i) newid[order[i]] = (int32_t)i;
+    for (int64_t v = 0; v < P; ++v) agg[v] = newid[into[agg[v]]];
+    const int n_agg = (int)order.size();
+    r.blk.assign(n_agg, 0);
+    r.loc.assign(n_agg, 0);
+    std::fill(r.na.begin(), r.na.end(), 0);
+    for (int i = 0; i < n_agg; ++i) {
+      const int b = seed_blk[order[i]];
+      r.blk[i] = b;
+      if (r.na[b] == 0) r.a0[b] = i;
+      r.loc[i] = r.na[b]++;
+    }
+    r.na_max = 0;
+    for (int b = 0; b < nb; ++b) r.na_max = std::max(r.na_max, r.na[b]);
+    if (r.na_max <= std::min(CS_NA_MAX, 2 * target)) break;
+    grow *= 1.5;
+  }
+  return r;
+}
+
+// Aggregates of the mesh's vertex graph (the Q pattern: the columns < P of a
+// vertex's S row) uploaded with their block tables.
+static void build_aggregates(Ctx &c, Mesh &m, PcTables &t, int target) {
+  const int64_t P = m.P;
+  std::vector<int64_t> sp(P + 1);
+  std::vector<int32_t> gl(std::max<int64_t>(P, 1));
+  SCVS_CUDA(cudaMemcpyAsync(sp.data(), m.s_ptr, (P + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(gl.data(), m.g_len, P * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<int32_t> scol(std::max<int64_t>(sp[P] - sp[0], 1));
+  SCVS_CUDA(cudaMemcpyAsync(scol.data(), m.s_col + sp[0], (sp[P] - sp[0]) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<int64_t> qp(P + 1, 0);
+  for (int64_t v = 0; v < P; ++v) qp[v + 1] = qp[v] + gl[v];
+  std::vector<int32_t> qc(std::max<int64_t>(qp[P], 1));
+  for (int64_t v = 0; v < P; ++v)
+    std::copy(scol.begin() + (sp[v] - sp[0]), scol.begin() + (sp[v] - sp[0]) + gl[v], qc.begin() + qp[v]);
+  const AggResult r = graph_aggregates(P, qp.data(), qc.data(), target);
+  const int n_agg = (int)r.blk.size(), nb = r.n_blk;
+  std::vector<int64_t> ptr(n_agg + 1, 0), so(nb);
+  std::vector<int32_t> vert(std::max<int64_t>(P, 1));
+  for (int64_t v = 0; v < P; ++v) ++ptr[r.agg[v] + 1];
+  for (int i = 0; i < n_agg; ++i) ptr[i + 1] += ptr[i];
+  {
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t v = 0; v < P; ++v) vert[fill[r.agg[v]]++] = (int32_t)v;
+  }
+  int64_t acc = 0;
+  for (int b = 0; b < nb; ++b) { so[b] = acc; acc += (int64_t)r.na[b] * r.na[b]; }
+  t.n_agg = n_agg;
+  t.n_blk = nb;
+  t.na_max = r.na_max;
+  t.so_total = acc;
+  t.cs_target = target;
+  t.agg = m.mode_arena.alloc<int32_t>(P);
+  t.agg_ptr = m.mode_arena.alloc<int64_t>(n_agg + 1);
+  t.agg_vert = m.mode_arena.alloc<int32_t>(P);
+  t.agg_blk = m.mode_arena.alloc<int32_t>(n_agg);
+  t.agg_loc = m.mode_arena.alloc<int32_t>(n_agg);
+  t.blk_na = m.mode_arena.alloc<int32_t>(nb);
+  t.blk_a0 = m.mode_arena.alloc<int32_t>(nb);
+  t.blk_so = m.mode_arena.alloc<int64_t>(nb);
+  auto up = [&](void *d, const void *h, size_t bytes) {
+    SCVS_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c.stream));
+  };
+  up(t.agg, r.agg.data(), P * sizeof(int32_t));
+  up(t.agg_ptr, ptr.data(), (n_agg + 1) * sizeof(int64_t));
+  up(t.agg_vert, vert.data(), P * sizeof(int32_t));
+  up(t.agg_blk, r.blk.data(), n_agg * sizeof(int32_t));
+  up(t.agg_loc, r.loc.data(), n_agg * sizeof(int32_t));
+  up(t.blk_na, r.na.data(), nb * sizeof(int32_t));
+  up(t.blk_a0, r.a0.data(), nb * sizeof(int32_t));
+  up(t.blk_so, so.data(), nb * sizeof(int64_t));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host vectors go out of scope
+}
+
+static int cs_target_of(const Ctx &c) { return c.opts.schur_agg > 0 ? c.opts.schur_agg : CS_DEFAULT_AGG; }
+
+// Start of the velocity solve of the triangular form (k_tri_vel0): rt = r_u - D z_p
+// and the first iterate of the velocity polynomial, written to uA.
+template <typename T>
+static void tri_vel0_launch(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t, typename cpx<T>::t *r,
+                            const double *rscale, const typename cpx<T>::t *zp, typename cpx<T>::t *rt,
+                            typename cpx<T>::t *uA) {
+  const double cs = 2.0 * sizeof(T), pb = (double)m.P * m.ld * cs, vb = (double)m.dim * m.N * m.ld * cs;
+  KScope ks(c, KC_PRECOND, vb * (rscale ? 4 : 3) + (double)m.g_nnz * (4 + m.dim * sizeof(T)) + pb +
+                               (double)(m.N + 1) * 8 + (double)m.N * 17);
+  auto body = [&](auto mpl_c, auto l_c) {
+    constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
+    const int gpb = 256 / L;
+    const unsigned nb = row_blocks(c, m.N, gpb, a.tile);
+    if (m.dim == 2)
+      k_tri_vel0<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, zp, rt, uA);
+    else
+      k_tri_vel0<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, zp, rt, uA);
+  };
+  if constexpr (sizeof(T) == 4) {
+    const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
+    SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+  } else {
+    SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+  }
+  count_launch(c);
+}
+
+// Velocity iterate moves of one application: every Chebyshev step after step
+// 0 moves the iterate between its two buffers once.
+static int vel_moves(const PcTables &t, bool pmg) { return pmg ? (t.s_u - 1) + t.s_u : (t.s_u - 1); }
+
+// Steps 1.. of the velocity solve from the first iterate in ucur (step 0 done):
+// the velocity polynomial, or for the p-multigrid kinds pre-smoothing, fine
+// residual, coarse solve, prolongation and post-smoothing.  ru is the velocity
+// right-hand side; uprev, rc and zc are scratch.  Returns the buffer holding
+// the result (ucur or uprev, after vel_moves(t, pmg) moves).
+template <typename T>
+static typename cpx<T>::t *vel_cycle(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t, bool pmg,
+                                     const typename cpx<T>::t *ru, typename cpx<T>::t *ucur,
+                                     typename cpx<T>::t *uprev, typename cpx<T>::t *rc,
+                                     typename cpx<T>::t *const *zc) {
+  using C = typename cpx<T>::t;
+  const double cs = 2.0 * sizeof(T), vb = (double)m.dim * m.N * m.ld * cs, cbk = (double)m.dim * m.P * m.ld * cs;
   auto step = [&](const double *al_u, const double *be_u, bool prev0_u) {
     ChebCoef cc{};
     cc.do_u = 1;
@@ -1482,10 +1811,10 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
     cheb_launch<T>(c, m, a, cc, ru, ucur, uprev);
     std::swap(ucur, uprev);
   };
-  // 3. velocity polynomial / pre-smoothing
+  // velocity polynomial / pre-smoothing
   for (int i = 1; i < t.s_u; ++i) step(t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, i == 1);
   if (pmg) {
-    // 4. fine residual, coarse solve (restriction + Chebyshev), prolongation
+    // fine residual, coarse solve (restriction + Chebyshev), prolongation
     {
       KScope ks(c, KC_CHEB_FINE, (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + 3 * vb);
       auto body = [&](auto mpl_c, auto l_c) {
@@ -1511,12 +1840,205 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
       k_prolong<T><<<ceil_div((int64_t)m.dim * m.N * m.ld, 256), 256, 0, c.stream>>>(a, m.dim, zres, ucur);
       count_launch(c);
     }
-    // 5. post-smoothing from the corrected iterate: first step z1 = z0 + D^-1 (r - A z0)/theta
+    // post-smoothing from the corrected iterate: first step z1 = z0 + D^-1 (r - A z0)/theta
     step(t.zeros, t.inv_theta_u, true);
     for (int i = 1; i < t.s_u; ++i) step(t.alpha_u + (size_t)i * m.ld, t.beta_u + (size_t)i * m.ld, false);
   }
-  if (ucur != z) throw (int)SCVS_ERR_STATE;  // buffer bookkeeping invariant
+  return ucur;
 }
+
+template <typename T>
+static void schur_coarse_setup(Ctx &c, Mesh &m, PcTables &t);
+template <typename T>
+static void schur_coarse_apply(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t,
+                               const typename cpx<T>::t *r, typename cpx<T>::t *z, typename cpx<T>::t *q,
+                               typename cpx<T>::t *y);
+
+// z = P^-1 r for all modes (right block preconditioner).  scratch holds
+// precond_scratch_elems(m) elements.  rscale (device, [ld], may be null): r is
+// first scaled per mode and written back (lazy normalisation of v_j).
+template <typename T>
+void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx<T>::t *z,
+                   typename cpx<T>::t *scratch, const double *rscale) {
+  using C = typename cpx<T>::t;
+  C *r = const_cast<C *>(r_in);
+  const int64_t total = m.n_dof * m.ld;
+  const unsigned eb = ceil_div(total, 256);
+  const double cs = 2.0 * sizeof(T), blk = (double)total * cs, vb = (double)m.dim * m.N * m.ld * cs;
+  const int kind = c.opts.precond;
+  if (kind == SCVS_PC_BLOCK_DIAG) {
+    const PcArgs a = pc_args<T>(m);
+    KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);
+    if (m.dim == 2)
+      k_pc_step0<T, 2, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, z, total);
+    else
+      k_pc_step0<T, 3, true><<<eb, 256, 0, c.stream>>>(a, r, rscale, nullptr, z, total);
+    count_launch(c);
+    return;
+  }
+  PcTables &t = m.pc;
+  pc_tables(c, m, t);
+  const bool cs_on = kind == SCVS_PC_TRI_PMG_CS;
+  if (cs_on && (t.cs_bytes != (int)sizeof(T) || t.cs_target != cs_target_of(c))) schur_coarse_setup<T>(c, m, t);
+  const PcArgs a = pc_args<T>(m);
+  const bool tri = kind == SCVS_PC_TRI_PMG || cs_on;
+  const bool pmg = kind == SCVS_PC_BLOCK_PMG || tri;
+  const int64_t pblk = m.P * m.ld, cblk = (int64_t)m.dim * m.P * m.ld;
+  C *other = scratch;  // velocity part lives in dofs [0, dim N)
+  C *pM[2] = {scratch + total, scratch + total + pblk};
+  C *pL[2] = {scratch + total + 2 * pblk, scratch + total + 3 * pblk};
+  C *rc = scratch + total + 4 * pblk;
+  C *zc[2] = {rc + cblk, rc + 2 * cblk};
+  C *rt = rc + 3 * cblk;  // velocity right-hand side of the triangular form
+  // the velocity iterate ping-pongs between z and `other`; the first iterate
+  // goes where the last one lands on z
+  C *uA = (vel_moves(t, pmg) % 2 == 0) ? z : other;
+  C *uB = (uA == z) ? other : z;
+  // 1. pressure block: z_p = -/+ (mu M_p^-1 + j omega rho L_p^-1) r_p (minus: Schur
+  //    complement of the triangular form; plus: block-diagonal form)
+  pressure_solve<T>(c, m, a, t, r, rscale, pM, pL, z, tri ? T(-1) : T(1));
+  // 1b. coarse Schur correction z_p -= R_c S_c^-1 R_c^T r_p (r_p already scaled
+  //     by the pressure solve); the pressure polynomials' buffers are free again
+  if (cs_on) schur_coarse_apply<T>(c, m, a, t, r, z, pM[0], pM[1]);
+  // 2. velocity right-hand side and step 0 of the velocity polynomial
+  const C *ru = r;
+  if (tri) {
+    tri_vel0_launch<T>(c, m, a, t, r, rscale, z + (int64_t)m.dim * m.N * m.ld, rt, uA);
+    ru = rt;
+  } else {
+    const int64_t fu = (int64_t)m.dim * m.N * m.ld;
+    KScope ks0(c, KC_PRECOND, vb * (rscale ? 3 : 2) + (double)m.N * 17);
+    if (m.dim == 2)
+      k_pc_step0<T, 2, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, uA, fu);
+    else
+      k_pc_step0<T, 3, false><<<ceil_div(fu, 256), 256, 0, c.stream>>>(a, r, rscale, t.inv_theta_u, uA, fu);
+    count_launch(c);
+  }
+  // 3.-5. the rest of the velocity solve
+  C *res = vel_cycle<T>(c, m, a, t, pmg, ru, uA, uB, rc, zc);
+  if (res != z) throw (int)SCVS_ERR_STATE;  // buffer bookkeeping invariant
+}
+// Stream-ordered temporaries of the coarse Schur setup, released (and the
+// components' activity flags restored) on every exit path.
+struct CsTemps {
+  Ctx &c;
+  Mesh &m;
+  std::vector<void *> p;
+  uint8_t *saved = nullptr;
+  CsTemps(Ctx &c_, Mesh &m_) : c(c_), m(m_) {}
+  ~CsTemps() {
+    if (saved) cudaMemcpyAsync(m.comp_active, saved, m.n_comp, cudaMemcpyDeviceToDevice, c.stream);
+    for (void *q : p) cudaFreeAsync(q, c.stream);
+  }
+  template <typename P> P *get(int64_t n) {
+    P *q = nullptr;
+    SCVS_CUDA(ctx_malloc(c, &q, (size_t)std::max<int64_t>(n, 1) * sizeof(P), c.stream));
+    p.push_back(q);
+    return q;
+  }
+};
+
+// Setup of the coarse Schur correction for the current modes, physics and
+// polynomial degrees: the aggregates (host, once per target), then per pair of
+// coarse columns (j, j+1) one velocity cycle for every block and mode at once,
+// X = A~_u^-1 (-D R_c [e_j + i e_{j+1}]), its image D^T X (pressure rows of the
+// saddle operator with zero pressure input), restricted to the aggregates, and
+// finally the FP64 inverses.  Every component takes part whatever its current
+// activity flag (restored afterwards).
+template <typename T>
+static void schur_coarse_setup(Ctx &c, Mesh &m, PcTables &t) {
+  using C = typename cpx<T>::t;
+  const int target = cs_target_of(c);
+  if (t.cs_target != target || !t.agg) {
+    build_aggregates(c, m, t, target);
+    t.sinv = m.mode_arena.alloc<double>(std::max<int64_t>(1, t.so_total * m.ld));  // room for either precision
+  }
+  const int64_t total = m.n_dof * m.ld, fp = (int64_t)m.dim * m.N * m.ld, pl = m.P * m.ld;
+  const int64_t pblk = pl, cblk = (int64_t)m.dim * m.P * m.ld;
+  CsTemps tmp{c, m};
+  if (m.comp_active) {
+    uint8_t *sv = tmp.get<uint8_t>(m.n_comp);
+    SCVS_CUDA(cudaMemcpyAsync(sv, m.comp_active, m.n_comp, cudaMemcpyDeviceToDevice, c.stream));
+    tmp.saved = sv;
+    SCVS_CUDA(cudaMemsetAsync(m.comp_active, 1, m.n_comp, c.stream));
+  }
+  C *Z = tmp.get<C>(total), *Y = tmp.get<C>(total), *R0 = tmp.get<C>(fp);
+  C *scr = tmp.get<C>(precond_scratch_elems(m));
+  C *q = tmp.get<C>((int64_t)t.n_agg * m.ld);
+  double *W = tmp.get<double>(2 * t.so_total * m.ld);
+  int *nsing = tmp.get<int>(1);
+  SCVS_CUDA(cudaMemsetAsync(R0, 0, fp * sizeof(C), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(W, 0, 2 * t.so_total * m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(nsing, 0, sizeof(int), c.stream));
+  const PcArgs a = pc_args<T>(m);
+  C *other = scr;
+  C *rc = scr + total + 4 * pblk;
+  C *zc[2] = {rc + cblk, rc + 2 * cblk};
+  C *rt = rc + 3 * cblk;
+  C *uA = (vel_moves(t, true) % 2 == 0) ? Z : other;
+  C *uB = (uA == Z) ? other : Z;
+  const double cs = 2.0 * sizeof(T);
+  for (int j = 0; j < t.na_max; j += 2) {
+    {
+      KScope ks(c, KC_PRECOND, pl * cs + (double)m.P * 4 + (double)t.n_agg * 4);
+      k_agg_indicator<T><<<ceil_div(pl, 256), 256, 0, c.stream>>>(t.agg, t.agg_loc, m.P, m.ld, j, Z + fp);
+      count_launch(c);
+    }
+    tri_vel0_launch<T>(c, m, a, t, R0, nullptr, Z + fp, rt, uA);
+    if (vel_cycle<T>(c, m, a, t, true, rt, uA, uB, rc, zc) != Z) throw (int)SCVS_ERR_STATE;
+    SCVS_CUDA(cudaMemsetAsync(Z + fp, 0, pl * sizeof(C), c.stream));
+    apply_saddle<T>(c, m, Z, Y);
+    {
+      KScope ks(c, KC_PRECOND, pl * cs + (double)m.P * 4 + (double)(t.n_agg + 1) * 8 + (double)t.n_agg * m.ld * cs);
+      k_agg_restrict<T><<<t.n_agg, 256, 0, c.stream>>>(t.agg_ptr, t.agg_vert, m.ld, Y + fp, q);
+      count_launch(c);
+    }
+    {
+      KScope ks(c, KC_PRECOND, (double)t.n_agg * m.ld * (cs + 16) + (double)t.n_agg * 8);
+      k_cs_column<T><<<ceil_div((int64_t)t.n_agg * m.ld, 256), 256, 0, c.stream>>>(
+          t.agg_blk, t.agg_loc, t.blk_na, t.blk_so, t.n_agg, m.ld, j, q, W);
+      count_launch(c);
+    }
+  }
+  {
+    KScope ks(c, KC_PRECOND, (double)t.so_total * m.ld * (16 + 8 + sizeof(T)));
+    const size_t smem = (size_t)(3 * t.na_max + 256) * sizeof(double) + 256 * sizeof(int);
+    k_cs_invert<T><<<t.n_blk * m.ld, 256, smem, c.stream>>>(t.blk_na, t.blk_so, m.ld, W, (T *)t.sinv, nsing);
+    count_launch(c);
+  }
+  int h_sing = 0;
+  SCVS_CUDA(cudaMemcpyAsync(&h_sing, nsing, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  t.cs_singular = h_sing;
+  t.cs_bytes = (int)sizeof(T);
+}
+
+// z_p -= R_c S_c^-1 R_c^T r_p for every active (component, mode); q and y are
+// scratch of n_agg * ld elements.
+template <typename T>
+static void schur_coarse_apply(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t,
+                               const typename cpx<T>::t *r, typename cpx<T>::t *z, typename cpx<T>::t *q,
+                               typename cpx<T>::t *y) {
+  const int64_t fp = (int64_t)m.dim * m.N * m.ld, pl = m.P * m.ld, ql = (int64_t)t.n_agg * m.ld;
+  const double cs = 2.0 * sizeof(T);
+  {
+    KScope ks(c, KC_PRECOND, pl * cs + (double)m.P * 4 + (double)(t.n_agg + 1) * 8 + ql * cs);
+    k_agg_restrict<T><<<t.n_agg, 256, 0, c.stream>>>(t.agg_ptr, t.agg_vert, m.ld, r + fp, q);
+    count_launch(c);
+  }
+  {
+    KScope ks(c, KC_PRECOND, (double)t.so_total * m.ld * sizeof(T) + 2 * ql * cs + (double)t.n_agg * 12);
+    k_cs_product<T><<<ceil_div(ql, 256), 256, 0, c.stream>>>(t.agg_blk, t.agg_loc, t.blk_na, t.blk_a0, t.blk_so,
+                                                            t.n_agg, m.ld, (const T *)t.sinv, q, y);
+    count_launch(c);
+  }
+  {
+    KScope ks(c, KC_PRECOND, 2 * pl * cs + (double)m.P * 4 + ql * cs);
+    k_cs_broadcast<T><<<ceil_div(pl, 256), 256, 0, c.stream>>>(a, m.dim, t.agg, y, z + fp);
+    count_launch(c);
+  }
+}
+
 template void apply_precond<float>(Ctx &, Mesh &, const float2 *, float2 *, float2 *, const double *);
 template void apply_precond<double>(Ctx &, Mesh &, const double2 *, double2 *, double2 *, const double *);
 

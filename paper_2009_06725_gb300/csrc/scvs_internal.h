@@ -77,6 +77,21 @@ struct PcTables {
   double inv_theta_m = 0, inv_theta_l = 0;
   int s_u = 0, s_m = 0, s_l = 0;
   bool valid = false;
+  // Coarse correction of the Schur approximation (SCVS_PC_TRI_PMG_CS): graph
+  // aggregates of the vertices, grouped by connected component ("block"), and
+  // the inverse coarse matrix of every (block, mode).
+  int cs_target = 0;                 // aggregates per block asked for
+  int n_agg = 0, n_blk = 0, na_max = 0;
+  int32_t *agg = nullptr;            // [P] aggregate of every vertex
+  int64_t *agg_ptr = nullptr;        // [n_agg+1] CSR of the aggregates' vertices (ascending ids)
+  int32_t *agg_vert = nullptr;       // [P]
+  int32_t *agg_blk = nullptr, *agg_loc = nullptr;  // [n_agg] block, index within the block
+  int32_t *blk_na = nullptr, *blk_a0 = nullptr;    // [n_blk] aggregates of the block, its first aggregate
+  int64_t *blk_so = nullptr;         // [n_blk] sum of n_a^2 over the blocks before it
+  int64_t so_total = 0;
+  void *sinv = nullptr;              // [so_total][ld] inverse coarse matrices (row-major per block), T
+  int cs_bytes = 0;                  // sizeof(T) of sinv (0: not built)
+  int cs_singular = 0;               // (block, mode) pairs whose coarse matrix was singular (correction off)
 };
 
 // One mesh and the state of its modes.
@@ -260,6 +275,14 @@ template <typename T>
 void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r, typename cpx<T>::t *z,
                    typename cpx<T>::t *scratch, const double *rscale);
 void apply_matfree(Ctx &c, const Mesh &m, int precision, const void *x, void *y);
+// Graph aggregates (host): agg [P] aggregate of every vertex, numbered by block
+// (connected component, in order of its lowest vertex) then seed; per aggregate
+// its block and index within it; per block its count and first aggregate.
+struct AggResult {
+  std::vector<int32_t> agg, blk, loc, na, a0;
+  int n_blk = 0, na_max = 0;
+};
+AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target);
 void matfree_tables(Ctx &c);  // matfree.cu
 
 // ---- krylov.cu

@@ -22,7 +22,7 @@ SCVS_ERR_OOM, SCVS_ERR_CUDA, SCVS_ERR_STATE, SCVS_ERR_TIMEOUT = -4, -5, -6, -7
 SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET = 1, 2, 4
 SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
-SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG = 0, 1, 2, 3
+SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG, SCVS_PC_TRI_PMG_CS = 0, 1, 2, 3, 4
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
 SCVS_KC_COUNT = 11
@@ -36,7 +36,8 @@ class scvs_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("precision", C.c_int32),
                 ("precond", C.c_int32), ("cheb_u", C.c_int32), ("cheb_m", C.c_int32),
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
-                ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p)]
+                ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p),
+                ("schur_agg", C.c_int32), ("reserved", C.c_int32)]
 
 
 class scvs_mode_report(C.Structure):
@@ -105,6 +106,8 @@ SIGNATURES = {
     "scvs_tuned_shapes": (_I32, [_P, _I32, _P, _P]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
+    "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
+    "scvs_schur_coarse_info": (_I32, [_P, _I32, _P]),
 }
 KERNEL_CLASSES = ["spmm_fp32", "spmm_fp64", "precond", "arnoldi", "vector", "assembly", "reconstruct", "matfree",
                   "cheb_fine", "pressure", "coarse"]
@@ -388,6 +391,27 @@ def scvs_tuned_shapes(ctx, mesh_id):
     us = us.reshape(2, 3, nt).round(1).tolist()
     return dict(mpl_spmm=int(shape[0]), tile_spmm=int(shape[1]), mpl_cheb=int(shape[2]), tile_cheb=int(shape[3]),
                 spmm_us=us[0], cheb_us=us[1])
+
+
+def scvs_graph_aggregates(row_ptr, col, target):
+    """Graph aggregates of a vertex graph given as CSR (host only).  Returns
+    (agg [n] int32, n_agg, n_blk)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = row_ptr.size - 1
+    agg = np.empty(max(n, 0), dtype=np.int32)
+    na, nb = C.c_int32(0), C.c_int32(0)
+    rc = lib().scvs_graph_aggregates(n, _ptr(row_ptr), _ptr(col), int(target), _ptr(agg), C.byref(na), C.byref(nb))
+    if rc < 0:
+        raise ScvsError(rc, "scvs_graph_aggregates: bad argument")
+    return agg, na.value, nb.value
+
+
+def scvs_schur_coarse_info(ctx, mesh_id):
+    """{n_agg, n_blk, na_max, singular} of the last coarse Schur setup (zeros before it)."""
+    info = np.zeros(4, dtype=np.int32)
+    _check(ctx, lib().scvs_schur_coarse_info(ctx, mesh_id, _ptr(info)))
+    return dict(n_agg=int(info[0]), n_blk=int(info[1]), na_max=int(info[2]), singular=int(info[3]))
 
 
 def scvs_kernel_timers(ctx, enable):

@@ -1,0 +1,166 @@
+"""SCVS_PC_TRI_PMG_CS: the triangular preconditioner with an additive coarse
+correction of the Schur approximation on graph aggregates.
+
+Pins: the correction's pressure part is piecewise constant on the aggregates
+(the library's aggregates equal those of scvs_graph_aggregates on the vertex
+graph) and satisfies the Galerkin condition R^T D^T A~_u^-1 D R y = R^T r_p,
+with D from the oracle's assembly and A~_u^-1 the velocity cycle (the
+BLOCK_PMG kind with zero pressure input); the kind is linear and
+reproducible; solves reach the oracle's solutions, one mesh or a batch of
+components; and on an elongated pipe (L/R = 40), where the Cahouet-Chabard
+approximation alone needs hundreds of Arnoldi steps, it needs a small
+fraction of them.
+
+These tests stay off until the kind's first run on a GPU
+(SCVS_RUN_CS_TESTS=1 enables them)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import fem
+from paper_2009_06725_gb300 import scvs
+from synthetic import workloads
+
+from .gpu_util import open_workload, padded_block, rel_l2, solve, stack_modal, torch_cuda
+from .test_aggregates_cpu import vertex_graph
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("SCVS_RUN_CS_TESTS") != "1",
+                                 reason="SCVS_PC_TRI_PMG_CS awaits its first validation run")]
+
+M = 8
+CS = scvs.SCVS_PC_TRI_PMG_CS
+
+
+def _apply(s, mid, X):
+    torch = torch_cuda()
+    ld = scvs.scvs_mode_stride(s.ctx, mid)
+    x = torch.from_numpy(padded_block(X, ld)).to(torch.complex64).cuda()
+    y = torch.zeros_like(x)
+    torch.cuda.synchronize()
+    scvs.scvs_apply_precond(s.ctx, mid, x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.complex128)[:, : X.shape[1]]
+
+
+@pytest.fixture(scope="module")
+def pipe():
+    wl = workloads.pipe_workload(n_c=3, n_r=2, n_x=8, n_modes=M, length=4.0)
+    return wl, fem.assemble(wl["mesh"])
+
+
+def test_correction_against_definition(pipe):
+    wl, mats = pipe
+    N, P, d = mats["N"], mats["P"], 3
+    n = fem.dof_count(mats)
+    R = workloads.random_block(n, M, seed=21)
+    target = 48
+    s_t, mid_t = open_workload(wl, precond=scvs.SCVS_PC_TRI_PMG)
+    s_c, mid_c = open_workload(wl, precond=CS, schur_agg=target)
+    s_b, mid_b = open_workload(wl, precond=scvs.SCVS_PC_BLOCK_PMG)
+    agg, n_agg, n_blk = scvs.scvs_graph_aggregates(*vertex_graph(wl["mesh"]), target)
+    with s_t, s_c, s_b:
+        Zt = _apply(s_t, mid_t, R)
+        Zc = _apply(s_c, mid_c, R)
+        info = scvs.scvs_schur_coarse_info(s_c.ctx, mid_c)
+        assert info == dict(n_agg=n_agg, n_blk=n_blk, na_max=n_agg, singular=0), info
+        dp = Zt[d * N:] - Zc[d * N:]                       # = R_c y
+        Y = np.stack([dp[agg == a].mean(axis=0) for a in range(n_agg)])
+        spread = max(np.abs(dp[agg == a] - Y[a]).max() for a in range(n_agg))
+        assert spread < 1e-4 * np.abs(Y).max(), spread
+        # Galerkin condition of the coarse solve
+        RY = Y[agg]
+        U = np.zeros((n, M), dtype=np.complex128)
+        for c in range(d):
+            U[c: d * N: d] = mats["D"][c] @ RY
+        dd = fem.dirichlet_dofs(wl["dir_nodes"], d)
+        U[dd] = 0
+        U2 = _apply(s_b, mid_b, U)[: d * N]                 # velocity cycle, zero pressure input
+        U2[dd] = 0
+        sv = sum(mats["D"][c].T @ U2[c::d] for c in range(d))
+        lhs = np.stack([sv[agg == a].sum(axis=0) for a in range(n_agg)])
+        rhs = np.stack([R[d * N:][agg == a].sum(axis=0) for a in range(n_agg)])
+        for k in range(M):
+            assert rel_l2(lhs[:, k], rhs[:, k]) < 1e-2, (k, rel_l2(lhs[:, k], rhs[:, k]))
+        # the velocity part is the same cycle on r_u - D z_p
+        Dz = np.zeros((d * N, M), dtype=np.complex128)
+        for c in range(d):
+            Dz[c::d] = mats["D"][c] @ Zc[d * N:]
+        Dz[dd] = 0
+        R2 = R.copy()
+        R2[: d * N] -= Dz
+        R2[d * N:] = 0
+        Zv = _apply(s_b, mid_b, R2)
+        for k in range(M):
+            assert rel_l2(Zv[: d * N, k], Zc[: d * N, k]) < 1e-5
+
+
+def test_linear_and_reproducible(pipe):
+    wl, mats = pipe
+    n = fem.dof_count(mats)
+    X = workloads.random_block(n, M, seed=22)
+    Y = workloads.random_block(n, M, seed=23)
+    outs = []
+    for _ in range(2):
+        s, mid = open_workload(wl, precond=CS, autotune=0)
+        with s:
+            a = _apply(s, mid, 0.5 * X + Y)
+            b = 0.5 * _apply(s, mid, X) + _apply(s, mid, Y)
+            for k in range(M):
+                assert rel_l2(a[:, k], b[:, k]) < 1e-5
+            outs.append(a)
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision", [scvs.SCVS_PREC_MIXED, scvs.SCVS_PREC_FP64])
+def test_solves_to_the_oracle(pipe, precision):
+    wl, mats = pipe
+    X = fem.solve_modes(mats, wl)
+    s, mid, rep, u, p = solve(wl, precond=CS, precision=precision, max_cycles=2000)
+    with s:
+        Xg = stack_modal(u, p)
+    for k, r in enumerate(rep):
+        assert r["status"] == scvs.SCVS_CONVERGED, (k, r)
+        assert rel_l2(Xg[k], X[k]) < 1e-6
+    assert np.all(fem.relative_residual(mats, wl, Xg) < 1.05e-8)
+
+
+def test_elongated_pipe_needs_few_iterations():
+    wl = workloads.pipe_workload(n_c=3, n_r=2, n_x=40, n_modes=2, length=20.0, radius=0.5)
+    res = {}
+    for kind in (scvs.SCVS_PC_TRI_PMG, CS):
+        s, mid, rep, u, p = solve(wl, precond=kind, max_cycles=2000)
+        with s:
+            assert all(r["status"] == scvs.SCVS_CONVERGED for r in rep), rep
+            res[kind] = ([r["iterations"] for r in rep], stack_modal(u, p))
+    it_t, it_c = res[scvs.SCVS_PC_TRI_PMG][0], res[CS][0]
+    assert it_t[0] > 300, it_t
+    assert max(it_c) < 100 and it_c[0] < 0.15 * it_t[0], (it_t, it_c)
+    for k in range(2):
+        assert rel_l2(res[CS][1][k], res[scvs.SCVS_PC_TRI_PMG][1][k]) < 1e-6
+
+
+def test_batch_of_components():
+    wls = [workloads.pipe_workload(n_c=n_c, n_r=n_r, n_x=n_x, n_modes=4, length=L, radius=Rr, seed=i)
+           for i, (n_c, n_r, n_x, L, Rr) in enumerate([(2, 1, 6, 6.0, 0.5), (3, 2, 5, 2.5, 1.2), (2, 2, 8, 8.0, 0.7)])]
+    U = workloads.union_workload(wls)
+    m = len(U["omegas"])
+    with scvs.Solver(precond=CS, schur_agg=24, max_cycles=2000) as s:
+        mid = scvs.scvs_set_mesh(s.ctx, U["mesh"])
+        scvs.scvs_set_components(s.ctx, mid, U["n_comp"], U["node_comp"])
+        scvs.scvs_set_physics(s.ctx, mid, U["rho"], U["mu"])
+        scvs.scvs_set_modes(s.ctx, mid, U["omegas"], U["g"])
+        rep = scvs.scvs_solve(s.ctx, mid, U["n_comp"] * m)
+        info = scvs.scvs_schur_coarse_info(s.ctx, mid)
+        N, P = U["mesh"]["xyz"].shape[0], U["mesh"]["n_vertices"]
+        u, p = scvs.scvs_get_modal(s.ctx, mid, m, N, 3, P)
+    assert info["n_blk"] == 3 and info["singular"] == 0 and info["na_max"] <= 48, info
+    for i, (wl, mp) in enumerate(zip(wls, U["maps"])):
+        mats = fem.assemble(wl["mesh"])
+        X = fem.solve_modes(mats, wl)
+        Pi = wl["mesh"]["n_vertices"]
+        for k in range(m):
+            assert rep[i * m + k]["status"] == scvs.SCVS_CONVERGED, (i, k, rep[i * m + k])
+            xi = np.concatenate([u[k][mp].reshape(-1), p[k][mp[:Pi]]])
+            assert rel_l2(xi, X[k]) < 1e-6, (i, k)
