@@ -201,6 +201,19 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- GPU
 
+PC_NAMES = {0: "block-chebyshev", 1: "block-diagonal", 2: "block-pmg", 3: "triangular-pmg",
+            4: "triangular-pmg + coarse Schur correction"}
+
+
+def pc_config(args):
+    """The preconditioner entry of a bench line's config (library default: triangular-pmg)."""
+    kind = 3 if args.precond is None else args.precond
+    c = {"precond": PC_NAMES.get(kind, str(kind))}
+    if kind == 4:
+        c["schur_agg"] = args.schur_agg or 96
+    return c
+
+
 def pc_opts(args):
     """Preconditioner options given on the command line (library defaults otherwise)."""
     o = {}
@@ -361,7 +374,7 @@ def run_gpu(args):
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "c128" if args.precision == "fp64" else "c64+f64", "data": "synthetic",
-           "config": workload_config(), "roofline": roof, "spmm": spmm,
+           "config": dict(workload_config(), **pc_config(args)), "roofline": roof, "spmm": spmm,
            "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
            "gpu_launches": int(launches), "clocks": clk, "e2e": e2e, "cpu_baseline": cb, "autotune": tuned,
            "phase_ms": phase_ms,
@@ -480,7 +493,7 @@ def run_batch(args):
                                    f"{min(sizes)}-{max(sizes)} P2 nodes (rank 0: {len(parts)} meshes, {N} nodes), "
                                    f"16 modes each = {len(all_parts) * 16} systems, one mesh of independent "
                                    f"components per rank, meshes dealt round-robin to {world} rank(s)"),
-                      "systems": len(all_parts) * 16, "nodes_rank0": N},
+                      "systems": len(all_parts) * 16, "nodes_rank0": N, **pc_config(args)},
            "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
            "solve": {"converged": conv, "systems_per_step": len(all_parts) * 16,
                      "iterations_max": max(r["iterations"] for r in reps[-1]),
@@ -545,7 +558,8 @@ def run_bifurcation(args):
            "config": {"workload": (f"stenosed bifurcation (parent R=1, 50% cosine stenosis, daughters R=0.7 at "
                                    f"+-45 deg), voxel mesh h={args.bif_h}: {N} P2 nodes, {P} vertices, {E} tets, "
                                    f"{3 * N + P} dofs/mode, 16 modes, GMRES(20) FP32 + FP64 refinement"),
-                      "nodes": N, "dofs_per_mode": 3 * N + P, "mesh_gen_s": round(t_gen, 1)},
+                      "nodes": N, "dofs_per_mode": 3 * N + P, "mesh_gen_s": round(t_gen, 1),
+                      **pc_config(args)},
            "device_memory_gb": round((total - free) / 1e9, 1),
            "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
            "solve": {"converged": conv, "modes_per_step": m,
