@@ -355,6 +355,32 @@ int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *byte
 #define SCVS_TUNE_TILES 5
 int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *shape, float *us);
 
+/* Spectral preprocessing of sampled periodic boundary data (Sec. 3, steps 1
+ * and 2 of the algorithm): the Fourier coefficients of Eq. SCVS_bc by the
+ * rectangle rule on n_t uniform samples t_s = s T / n_t of one period, as the
+ * solver's per-mode data, and the a priori truncation error of Eq. mode_error.
+ *   n_t      samples (>= 2)
+ *   n_pts    values per sample, e.g. n_dir * dim for Dirichlet data in the
+ *            [node][component] layout of scvs_set_modes
+ *   n_modes  modes 0..n_modes-1 (omega_i = 2 pi i / T), below the Nyquist
+ *            frequency of the samples: 2 (n_modes - 1) < n_t
+ *   g_t      device, FP64 [n_t][n_pts]: real samples (caller-owned)
+ *   w        device, FP64 [n_pts]: weights of the L2(Gamma) inner product
+ *            (e.g. nodal boundary areas), or NULL for unit weights
+ *   c        device, out, complex128 [n_modes][n_pts]: c_0 = g~_0,
+ *            c_i = 2 g~_i (i >= 1), so the field is Re sum_i c_i e^{j omega_i t};
+ *            with n_pts = n_dir * dim this is the g argument of scvs_set_modes_dev
+ *   e2       host, out, [n_modes]: e2[N] = ||g - g^_N||^2 / ||g||^2 in
+ *            L2(Gamma x T) (time by the rectangle rule, space by w) for the
+ *            series truncated after mode N, from the discrete Parseval identity
+ *            (exact on the samples); all 0 if g is zero.  The Dirichlet and
+ *            Neumann terms of Eq. mode_error are two calls whose e2 add.
+ * FP64 throughout (twiddles cos/sin(2 pi j / n_t) in FP64; fixed-order
+ * reductions, so the result is reproducible).  Runs on the context's stream
+ * and synchronises it.  Returns SCVS_OK or SCVS_ERR_ARG (sizes, null pointers). */
+int scvs_bc_spectrum(scvs_ctx *ctx, int32_t n_t, int64_t n_pts, int32_t n_modes, const double *g_t, const double *w,
+                     void *c, double *e2);
+
 /* Graph aggregates of a vertex graph, the coarse space of SCVS_PC_TRI_PMG_CS
  * (no paper counterpart: part of the preconditioner).  Host only: no context,
  * no device work.

@@ -800,6 +800,19 @@ int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *shape, float *us) {
   });
 }
 
+int scvs_bc_spectrum(scvs_ctx *c, int32_t n_t, int64_t n_pts, int32_t n_modes, const double *g_t, const double *w,
+                     void *c_out, double *e2) {
+  return guarded(c, [&]() {
+    if (n_t < 2 || n_pts < 1 || n_modes < 1 || 2 * (int64_t)(n_modes - 1) >= n_t)
+      return fail(c, SCVS_ERR_ARG, "need n_t >= 2, n_pts >= 1, 1 <= n_modes and 2 (n_modes - 1) < n_t");
+    if ((int64_t)n_t * n_pts > (int64_t)1 << 40 || (int64_t)n_modes * n_pts > (int64_t)1 << 40)
+      return fail(c, SCVS_ERR_ARG, "sizes too large");
+    if (!g_t || !c_out || !e2) return fail(c, SCVS_ERR_ARG, "null g_t, c or e2");
+    bc_spectrum(*c, n_t, n_pts, n_modes, g_t, w, static_cast<double2 *>(c_out), e2);
+    return SCVS_OK;
+  });
+}
+
 int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t *col, int32_t target,
                           int32_t *agg, int32_t *n_agg, int32_t *n_blk) {
   if (n_vert < 0 || n_vert > INT32_MAX || !row_ptr || !agg || target < 1 || target > 512) return SCVS_ERR_ARG;

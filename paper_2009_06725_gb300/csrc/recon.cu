@@ -5,6 +5,7 @@
 // its n_t samples; consecutive threads write consecutive dofs of a sample
 // (coalesced).  The twiddles e^{j omega_k t_s} are tabulated in FP64 on the
 // host; accumulation is FP64.
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -122,6 +123,106 @@ void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p
                                                               (int64_t)m.dim * m.N, u_t, p_t, m.P);
   count_launch(c);
   SCVS_CUDA(cudaFreeAsync(twd, c.stream));
+}
+
+// ---- spectral preprocessing of sampled boundary data -------------------
+// Fourier coefficients of a periodic boundary field from n_t uniform samples
+// (Eq. SCVS_bc by the rectangle rule), returned as the solver's per-mode data
+// c_0 = g~_0, c_i = 2 g~_i, and the a priori truncation error of Eq.
+// mode_error through the discrete Parseval identity: with the samples' mean
+// square E = (1/n_t) sum_s sum_p w_p g(t_s, p)^2 and mode energies
+// e_0 = sum_p w_p |g~_0|^2, e_i = 2 sum_p w_p |g~_i|^2 (modes below the Nyquist
+// frequency), the truncated series after mode N misses exactly
+// E - sum_{i <= N} e_i.
+
+// c[i][p] = (i ? 2 : 1) / n_t * sum_s g[s][p] e^{-j 2 pi i s / n_t}: one thread per
+// (mode, point), samples in ascending order, twiddle index i s mod n_t stepped
+// incrementally; consecutive threads read consecutive points of a sample.
+__global__ void k_bc_dft(const double *__restrict__ g, int64_t n_pts, int n_t, int n_modes,
+                         const double2 *__restrict__ tw, double2 *__restrict__ c) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)n_modes * n_pts) return;
+  const int i = (int)(f / n_pts);
+  const int64_t p = f % n_pts;
+  double re = 0.0, im = 0.0;
+  int idx = 0;
+  for (int s = 0; s < n_t; ++s) {
+    const double v = g[(int64_t)s * n_pts + p];
+    const double2 t = tw[idx];
+    re += v * t.x;
+    im -= v * t.y;
+    idx += i;
+    if (idx >= n_t) idx -= n_t;
+  }
+  const double sc = (i ? 2.0 : 1.0) / n_t;
+  c[f] = make_double2(re * sc, im * sc);
+}
+
+// out[i] = e_i for i < n_modes (from c: e_0 = w |c_0|^2, e_i = w |c_i|^2 / 2) and
+// out[n_modes] = E; one block per entry, threads stride in order, fixed tree.
+__global__ void __launch_bounds__(1024) k_bc_energy(const double *__restrict__ g, const double2 *__restrict__ c,
+                                                    const double *__restrict__ w, int64_t n_pts, int n_t,
+                                                    int n_modes, double *__restrict__ out) {
+  __shared__ double red[1024];
+  const int i = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  double acc = 0.0;
+  if (i < n_modes) {
+    for (int64_t p = tid; p < n_pts; p += bd) {
+      const double2 v = c[(int64_t)i * n_pts + p];
+      acc += (w ? w[p] : 1.0) * (v.x * v.x + v.y * v.y);
+    }
+    if (i) acc *= 0.5;
+  } else {
+    const int64_t n = (int64_t)n_t * n_pts;
+    for (int64_t e = tid; e < n; e += bd) {
+      const double v = g[e];
+      acc += (w ? w[e % n_pts] : 1.0) * v * v;
+    }
+    acc /= n_t;
+  }
+  red[tid] = acc;
+  __syncthreads();
+  for (int h = bd / 2; h > 0; h >>= 1) {
+    if (tid < h) red[tid] += red[tid + h];
+    __syncthreads();
+  }
+  if (tid == 0) out[i] = red[0];
+}
+
+void bc_spectrum(Ctx &c, int n_t, int64_t n_pts, int n_modes, const double *g_t, const double *w, double2 *c_out,
+                 double *e2) {
+  std::vector<double2> tw(n_t);
+  for (int j = 0; j < n_t; ++j) {
+    const double ph = 2.0 * M_PI * (double)j / (double)n_t;
+    tw[j] = make_double2(std::cos(ph), std::sin(ph));
+  }
+  double2 *twd = nullptr;
+  double *en = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &twd, (size_t)n_t * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &en, (size_t)(n_modes + 1) * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(twd, tw.data(), (size_t)n_t * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+  const int64_t nc = (int64_t)n_modes * n_pts;
+  {
+    KScope ks(c, KC_RECON, (double)n_t * n_pts * 8 + (double)nc * 16);
+    k_bc_dft<<<ceil_div(nc, 256), 256, 0, c.stream>>>(g_t, n_pts, n_t, n_modes, twd, c_out);
+    count_launch(c);
+  }
+  {
+    KScope ks(c, KC_RECON, (double)n_t * n_pts * 8 + (double)nc * 16 + (w ? (double)n_pts * 8 * (n_modes + 1) : 0.0));
+    k_bc_energy<<<n_modes + 1, 1024, 0, c.stream>>>(g_t, c_out, w, n_pts, n_t, n_modes, en);
+    count_launch(c);
+  }
+  std::vector<double> h(n_modes + 1);
+  SCVS_CUDA(cudaMemcpyAsync(h.data(), en, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(twd, c.stream));
+  SCVS_CUDA(cudaFreeAsync(en, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  const double total = h[n_modes];
+  double kept = 0.0;
+  for (int i = 0; i < n_modes; ++i) {
+    kept += h[i];
+    e2[i] = total > 0.0 ? std::max(0.0, (total - kept) / total) : 0.0;
+  }
 }
 
 }  // namespace scvs

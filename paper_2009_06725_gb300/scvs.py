@@ -106,6 +106,7 @@ SIGNATURES = {
     "scvs_tuned_shapes": (_I32, [_P, _I32, _P, _P]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
+    "scvs_bc_spectrum": (_I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
     "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "scvs_schur_coarse_info": (_I32, [_P, _I32, _P]),
 }
@@ -391,6 +392,15 @@ def scvs_tuned_shapes(ctx, mesh_id):
     us = us.reshape(2, 3, nt).round(1).tolist()
     return dict(mpl_spmm=int(shape[0]), tile_spmm=int(shape[1]), mpl_cheb=int(shape[2]), tile_cheb=int(shape[3]),
                 spmm_us=us[0], cheb_us=us[1])
+
+
+def scvs_bc_spectrum(ctx, g_t_dev, n_t, n_pts, n_modes, c_dev, w_dev=None):
+    """Per-mode data c [n_modes][n_pts] (complex128, written to device memory
+    at c_dev) of the device samples g_t_dev [n_t][n_pts] (FP64) and the
+    truncation errors e2 [n_modes] (numpy)."""
+    e2 = np.zeros(n_modes)
+    _check(ctx, lib().scvs_bc_spectrum(ctx, n_t, n_pts, n_modes, g_t_dev, w_dev, c_dev, _ptr(e2)))
+    return e2
 
 
 def scvs_graph_aggregates(row_ptr, col, target):

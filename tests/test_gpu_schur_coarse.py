@@ -12,7 +12,7 @@ approximation alone needs hundreds of Arnoldi steps, it needs a small
 fraction of them.
 
 These tests stay off until the kind's first run on a GPU
-(SCVS_RUN_CS_TESTS=1 enables them)."""
+(SCVS_RUN_PENDING=1 enables them)."""
 import os
 
 import numpy as np
@@ -26,7 +26,7 @@ from .gpu_util import open_workload, padded_block, rel_l2, solve, stack_modal, t
 from .test_aggregates_cpu import vertex_graph
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("SCVS_RUN_CS_TESTS") != "1",
+              pytest.mark.skipif(os.environ.get("SCVS_RUN_PENDING") != "1",
                                  reason="SCVS_PC_TRI_PMG_CS awaits its first validation run")]
 
 M = 8
