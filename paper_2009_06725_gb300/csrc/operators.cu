@@ -2218,7 +2218,7 @@ __global__ void k_init_random(float2 *v, int64_t n) {
 // iteration counts on the benchmark pipe at twice the cost).
 void spectral_bounds(Ctx &c, Mesh &m) {
   const int ld = m.ld;
-  const int64_t nu = (int64_t)m.dim * m.N * ld, np = m.P * ld;
+  const int64_t np = m.P * ld;
   const int64_t total = m.n_dof * ld;
   float2 *v = nullptr, *y = nullptr, *vM = nullptr, *yM = nullptr, *vL = nullptr, *yL = nullptr;
   float2 *vC = nullptr, *yC = nullptr;

@@ -98,9 +98,12 @@ __device__ __forceinline__ V gshfl(unsigned mask, V v, int q) {
 
 template <int L>
 __device__ __forceinline__ unsigned group_mask() {
-  if (L >= 32) return 0xffffffffu;
-  const unsigned base = (threadIdx.x & 31) / L * L;
-  return ((1u << L) - 1u) << base;
+  if constexpr (L >= 32) {
+    return 0xffffffffu;
+  } else {
+    const unsigned base = (threadIdx.x & 31) / L * L;
+    return ((1u << L) - 1u) << base;
+  }
 }
 
 #define SCVS_SHAPE_KEY(LDV, MPLV) ((LDV) * 8 + (MPLV))
