@@ -16,7 +16,13 @@ What it computes (arXiv 2009.06725, Sec. 3, steps 1 and 2 of the algorithm):
     g and, when present, Neumann h); the time integral is the rectangle rule
     on the same samples and the L2(Gamma) inner product a nodal quadrature
     with caller weights (unit weights: the nodal l2 norm);
-  * the smallest N_m with e_M < epsilon_m (step 2 of the algorithm).
+  * the smallest N_m with e_M < epsilon_m (step 2 of the algorithm);
+  * the a posteriori side of the same step: the L2(Omega x T) energy of every
+    solved mode's velocity field Re(u~_k e^{j omega_k t}) and the relative
+    change ||u^_N - u^_{N-1}||^2 / ||u^_N||^2 between the reconstructions
+    (Eq. sol_reconstruct) truncated after modes N-1 and N, both evaluated
+    literally from time samples of the reconstructions, the L2(Omega) norm
+    with the P2 mass matrix M_s (as in Eq. total_error).
 Each step follows the definition literally: coefficients by the sum, the
 truncation error by reconstructing the truncated series at the samples.
 """
@@ -86,3 +92,44 @@ def select_modes(fields, eps, n_max):
     e2 = truncation_errors(fields, n_max)
     ok = np.flatnonzero(e2 < eps * eps)
     return (int(ok[0]) if ok.size else None), e2
+
+
+def _l2_omega_t(Ms, u_t):
+    """int_0^T ||u||^2_{L2(Omega)} dt / T of samples u_t [n_t][N][d] (rectangle rule; M_s per component)."""
+    return float(np.mean([sum(u[:, c] @ (Ms @ u[:, c]) for c in range(u.shape[1])) for u in u_t]))
+
+
+def _series(U, omegas, period, n_t, N):
+    """Samples of Re sum_{k<=N} U_k e^{j omega_k t} (Eq. sol_reconstruct), [n_t][N][d]."""
+    t = np.arange(n_t) * (period / n_t)
+    out = np.zeros((n_t,) + U.shape[1:], dtype=np.float64)
+    for s in range(n_t):
+        acc = np.zeros(U.shape[1:], dtype=np.complex128)
+        for k in range(N + 1):
+            acc += U[k] * np.exp(1j * omegas[k] * t[s])
+        out[s] = acc.real
+    return out
+
+
+def mode_energies(Ms, U, omegas, period, n_t):
+    """E_k = mean over the period of ||Re(U_k e^{j omega_k t})||^2_{L2(Omega)}; U [m][N][d] complex."""
+    out = np.zeros(len(omegas))
+    t = np.arange(n_t) * (period / n_t)
+    for k, w in enumerate(omegas):
+        u_t = np.stack([np.real(U[k] * np.exp(1j * w * ts)) for ts in t])
+        out[k] = _l2_omega_t(Ms, u_t)
+    return out
+
+
+def a_posteriori_increments(Ms, U, omegas, period, n_t):
+    """delta_N^2 = ||u^_N - u^_{N-1}||^2 / ||u^_N||^2 in L2(Omega x T), N = 0..m-1 (u^_{-1} = 0;
+    0 where ||u^_N|| = 0), from time samples of the two truncated reconstructions."""
+    m = len(omegas)
+    out = np.zeros(m)
+    prev = np.zeros((n_t,) + U.shape[1:])
+    for N in range(m):
+        cur = _series(U, omegas, period, n_t, N)
+        den = _l2_omega_t(Ms, cur)
+        out[N] = _l2_omega_t(Ms, cur - prev) / den if den > 0 else 0.0
+        prev = cur
+    return out

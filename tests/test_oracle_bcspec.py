@@ -1,7 +1,9 @@
-"""Pins of the boundary-data spectral oracle (Eqs. SCVS_bc and mode_error)
-against closed forms and an independent library transform."""
+"""Pins of the boundary-data spectral oracle (Eqs. SCVS_bc and mode_error) and
+of its a posteriori side (mode energies, reconstruction increments) against
+closed forms and an independent library transform."""
 import numpy as np
 import pytest
+import scipy.sparse as spm
 
 from oracle import bcspec
 
@@ -82,3 +84,44 @@ def test_select_modes():
     assert bcspec.select_modes([(g, np.ones(1))], 1e-20, 4)[0] is None
     with pytest.raises(ValueError):
         bcspec.truncation_errors([(g, np.ones(1))], 33)
+
+
+def _mass(n, seed):
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((n, n))
+    return spm.csr_matrix(B @ B.T + n * np.eye(n))
+
+
+def test_mode_energies_closed_form():
+    # time averages over one period of harmonics: ||Re U_0||^2 for omega_0 = 0 and
+    # (1/2) U_k^H M U_k for omega_k = 2 pi k / T (the e^{2 j omega t} term averages out)
+    N, d, m, T = 9, 3, 5, 2.0
+    Ms = _mass(N, 3)
+    rng = np.random.default_rng(4)
+    U = rng.standard_normal((m, N, d)) + 1j * rng.standard_normal((m, N, d))
+    om = 2 * np.pi * np.arange(m) / T
+    E = bcspec.mode_energies(Ms, U, om, T, 32)
+    M = Ms.toarray()
+    assert E[0] == pytest.approx(sum(U[0, :, c].real @ M @ U[0, :, c].real for c in range(d)), rel=1e-12)
+    for k in range(1, m):
+        ref = 0.5 * sum(np.real(np.conj(U[k, :, c]) @ M @ U[k, :, c]) for c in range(d))
+        assert E[k] == pytest.approx(ref, rel=1e-12)
+
+
+def test_increments_closed_form_and_orthogonality():
+    N, d, m, T = 7, 2, 6, 1.0
+    Ms = _mass(N, 5)
+    rng = np.random.default_rng(6)
+    U = rng.standard_normal((m, N, d)) + 1j * rng.standard_normal((m, N, d))
+    U[0] = U[0].real  # real steady mode
+    om = 2 * np.pi * np.arange(m) / T
+    E = bcspec.mode_energies(Ms, U, om, T, 32)
+    inc = bcspec.a_posteriori_increments(Ms, U, om, T, 32)
+    # distinct harmonics are orthogonal in L2(Omega x T): the truncated series'
+    # energy is the sum of the modes' energies and the change is mode N alone
+    assert np.allclose(inc, E / np.cumsum(E), rtol=1e-11)
+    assert inc[0] == pytest.approx(1.0)
+    # a zero mode changes nothing
+    U[3] = 0
+    inc = bcspec.a_posteriori_increments(Ms, U, om, T, 32)
+    assert abs(inc[3]) < 1e-28
