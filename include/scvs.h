@@ -381,6 +381,22 @@ int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *shape, float *us)
 int scvs_bc_spectrum(scvs_ctx *ctx, int32_t n_t, int64_t n_pts, int32_t n_modes, const double *g_t, const double *w,
                      void *c, double *e2);
 
+/* A posteriori mode energies of a solved mesh (Sec. 3: the change of the
+ * reconstruction of Eq. sol_reconstruct when mode N is added decides whether
+ * more modes are needed).  For every component and mode (index comp * n_modes + k):
+ *   E[.]      (host, out) time average over the period of
+ *             ||Re(u~_k e^{j omega_k t})||^2_{L2(Omega)} of the velocity, with the P2
+ *             mass matrix: ||Re u~_k||^2 for omega_k = 0, (1/2) u~_k^H M u~_k otherwise
+ *   incr2[.]  (host, out, may be NULL) delta_N^2 = E_N / sum_{k <= N} E_k, the squared
+ *             L2(Omega x T) change of the series truncated after mode N relative to
+ *             its norm (modes in the order given to scvs_set_modes; exact for distinct
+ *             harmonic frequencies omega_k = 2 pi k / T, which are orthogonal over the
+ *             period); 0 where the series is zero
+ * n_out must be at least n_components * n_modes.  FP64, fixed-order
+ * reductions.  Runs on the context's stream and synchronises it.  Returns
+ * SCVS_ERR_STATE before scvs_solve, SCVS_ERR_ARG for a bad id or size. */
+int scvs_mode_energies(scvs_ctx *ctx, int32_t mesh_id, int64_t n_out, double *E, double *incr2);
+
 /* Graph aggregates of a vertex graph, the coarse space of SCVS_PC_TRI_PMG_CS
  * (no paper counterpart: part of the preconditioner).  Host only: no context,
  * no device work.

@@ -813,6 +813,18 @@ int scvs_bc_spectrum(scvs_ctx *c, int32_t n_t, int64_t n_pts, int32_t n_modes, c
   });
 }
 
+int scvs_mode_energies(scvs_ctx *c, int32_t mesh_id, int64_t n_out, double *E, double *incr2) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    if (!m->solved) return fail(c, SCVS_ERR_STATE, "no solution: call scvs_solve first");
+    if (!E || n_out < (int64_t)m->n_comp * m->m)
+      return fail(c, SCVS_ERR_ARG, "E needs n_components * n_modes entries");
+    mode_energies(*c, *m, E, incr2);
+    return SCVS_OK;
+  });
+}
+
 int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t *col, int32_t target,
                           int32_t *agg, int32_t *n_agg, int32_t *n_blk) {
   if (n_vert < 0 || n_vert > INT32_MAX || !row_ptr || !agg || target < 1 || target > 512) return SCVS_ERR_ARG;

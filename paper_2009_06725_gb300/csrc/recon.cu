@@ -225,4 +225,110 @@ void bc_spectrum(Ctx &c, int n_t, int64_t n_pts, int n_modes, const double *g_t,
   }
 }
 
+// ---- a posteriori mode energies ------------------------------------------
+// E_k = time average over the period of ||Re(u~_k e^{j omega_k t})||^2_{L2(Omega)}
+// for the velocity of every solved (component, mode): ||Re u~_k||^2_{M_s} for
+// omega_k = 0 and (1/2) u~_k^H (I_d (x) M_s) u~_k otherwise (harmonic frequencies,
+// whose e^{2 j omega t} term averages out).  Distinct harmonics are orthogonal
+// in L2(Omega x T), so the reconstruction truncated after mode N changes by
+// delta_N^2 = E_N / sum_{k <= N} E_k relative to itself (Sec. 3, a posteriori
+// choice of the number of modes).
+
+// q[dof][k] = weight_k Re(conj(x_{A,c,k}) (M_s x_{.,c,k})_A) for the velocity dof
+// A dim + c (one thread per (dof, mode), S row of A in pattern order; weight 1
+// with the real part only for omega_k = 0, else 1/2 with the complex modulus).
+__global__ void k_mass_quad(const double2 *__restrict__ x, const int64_t *__restrict__ s_ptr,
+                            const int32_t *__restrict__ s_col, const double *__restrict__ Ms,
+                            const double *__restrict__ omega, int64_t N, int dim, int ld, int m,
+                            double *__restrict__ q) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)dim * N * ld) return;
+  const int k = (int)(f % ld);
+  if (k >= m) { q[f] = 0.0; return; }
+  const int64_t dof = f / ld, A = dof / dim;
+  const int c = (int)(dof % dim);
+  double sx = 0.0, sy = 0.0;
+  for (int64_t t = s_ptr[A]; t < s_ptr[A + 1]; ++t) {
+    const double2 v = x[((int64_t)s_col[t] * dim + c) * ld + k];
+    const double mv = Ms[t];
+    sx += mv * v.x;
+    sy += mv * v.y;
+  }
+  const double2 u = x[f];
+  q[f] = omega[k] == 0.0 ? u.x * sx : 0.5 * (u.x * sx + u.y * sy);
+}
+
+// Per row chunk and mode: sum of q over the chunk's rows (rows at or beyond
+// n_q hold no value), strided in order and reduced by a fixed tree.
+constexpr int ENERGY_T = 256;
+__global__ void k_chunk_sum(const double *__restrict__ q, int64_t n_q, int ld, int64_t n_chunk,
+                            const int64_t *__restrict__ row0, const int32_t *__restrict__ rows,
+                            double *__restrict__ part) {
+  __shared__ double s[ENERGY_T];
+  for (int64_t ch = blockIdx.x; ch < n_chunk; ch += gridDim.x) {
+    const int64_t f0 = row0[ch] * ld, f1 = min((row0[ch] + rows[ch]) * ld, n_q * ld);
+    double acc = 0.0;
+    for (int64_t f = f0 + threadIdx.x; f < f1; f += ENERGY_T) acc += q[f];  // stride is a multiple of ld
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = ENERGY_T / 2; w >= ld; w >>= 1) {
+      if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x < ld) part[ch * ld + threadIdx.x] = s[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// out[comp][k] = sum of the component's chunk partials in chunk order.
+__global__ void k_sys_sum(const double *__restrict__ part, const int32_t *__restrict__ comp_chunk, int n_comp, int ld,
+                          double *__restrict__ out) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= n_comp * ld) return;
+  const int comp = sys / ld, k = sys % ld;
+  double acc = 0.0;
+  for (int ch = comp_chunk[comp]; ch < comp_chunk[comp + 1]; ++ch) acc += part[(int64_t)ch * ld + k];
+  out[sys] = acc;
+}
+
+void mode_energies(Ctx &c, Mesh &m, double *E, double *incr2) {
+  const int64_t nq = (int64_t)m.dim * m.N;
+  double *q = nullptr, *part = nullptr, *out = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &q, (size_t)nq * m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &part, (size_t)m.n_chunk * m.ld * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &out, (size_t)m.n_sys() * sizeof(double), c.stream));
+  {
+    KScope ks(c, KC_RECON, (double)m.s_nnz * 12 * m.dim * m.m + (double)nq * m.ld * 24);
+    k_mass_quad<<<ceil_div(nq * m.ld, 256), 256, 0, c.stream>>>(m.x, m.s_ptr, m.s_col, m.Ms, m.omega_d, m.N, m.dim,
+                                                                m.ld, m.m, q);
+    count_launch(c);
+  }
+  {
+    KScope ks(c, KC_RECON, (double)nq * m.ld * 8 + (double)m.n_chunk * m.ld * 8);
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(m.n_chunk, 8 * c.num_sms));
+    k_chunk_sum<<<nb, ENERGY_T, 0, c.stream>>>(q, nq, m.ld, m.n_chunk, m.chunk_row0, m.chunk_rows, part);
+    count_launch(c);
+  }
+  {
+    KScope ks(c, KC_RECON, (double)m.n_chunk * m.ld * 8 + (double)m.n_sys() * 8);
+    k_sys_sum<<<ceil_div(m.n_sys(), 128), 128, 0, c.stream>>>(part, m.comp_chunk, m.n_comp, m.ld, out);
+    count_launch(c);
+  }
+  std::vector<double> h(m.n_sys());
+  SCVS_CUDA(cudaMemcpyAsync(h.data(), out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(q, c.stream));
+  SCVS_CUDA(cudaFreeAsync(part, c.stream));
+  SCVS_CUDA(cudaFreeAsync(out, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  for (int comp = 0; comp < m.n_comp; ++comp) {
+    double tot = 0.0;
+    for (int k = 0; k < m.m; ++k) {
+      const double e = h[(size_t)comp * m.ld + k];
+      tot += e;
+      E[(size_t)comp * m.m + k] = e;
+      if (incr2) incr2[(size_t)comp * m.m + k] = tot > 0.0 ? e / tot : 0.0;
+    }
+  }
+}
+
 }  // namespace scvs

@@ -303,6 +303,7 @@ void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p
 void reconstruct_static(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);
 void bc_spectrum(Ctx &c, int n_t, int64_t n_pts, int n_modes, const double *g_t, const double *w, double2 *c_out,
                  double *e2);
+void mode_energies(Ctx &c, Mesh &m, double *E, double *incr2);
 
 int dev_error(Ctx &c);  // reads and clears the device error word
 inline void count_launch(Ctx &c) { c.launches.n++; }

@@ -107,6 +107,7 @@ SIGNATURES = {
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
     "scvs_bc_spectrum": (_I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
+    "scvs_mode_energies": (_I32, [_P, _I32, _I64, _P, _P]),
     "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "scvs_schur_coarse_info": (_I32, [_P, _I32, _P]),
 }
@@ -401,6 +402,15 @@ def scvs_bc_spectrum(ctx, g_t_dev, n_t, n_pts, n_modes, c_dev, w_dev=None):
     e2 = np.zeros(n_modes)
     _check(ctx, lib().scvs_bc_spectrum(ctx, n_t, n_pts, n_modes, g_t_dev, w_dev, c_dev, _ptr(e2)))
     return e2
+
+
+def scvs_mode_energies(ctx, mesh_id, n_out):
+    """(E, incr2), each [n_out] = [n_components * n_modes]: time-averaged L2 energy of every
+    solved mode's velocity and the a posteriori increments of the truncated reconstruction."""
+    E = np.zeros(n_out)
+    inc = np.zeros(n_out)
+    _check(ctx, lib().scvs_mode_energies(ctx, mesh_id, n_out, _ptr(E), _ptr(inc)))
+    return E, inc
 
 
 def scvs_graph_aggregates(row_ptr, col, target):

@@ -1,6 +1,7 @@
 """Spectral preprocessing of sampled boundary data on the GPU (Eqs. SCVS_bc,
-mode_error) against the FP64 oracle, and its output used as the solver's
-per-mode Dirichlet data (steps 1-3 of the algorithm of Sec. 3).
+mode_error) against the FP64 oracle, its output used as the solver's per-mode
+Dirichlet data (steps 1-3 of the algorithm of Sec. 3), and the a posteriori
+mode energies of a solved mesh.
 
 These tests stay off until the kernels' first run on a GPU
 (SCVS_RUN_PENDING=1 enables them)."""
@@ -94,3 +95,33 @@ def test_bad_sizes():
             with pytest.raises(scvs.ScvsError) as e:
                 scvs.scvs_bc_spectrum(s.ctx, gd.data_ptr(), n_t, 3, m, cd.data_ptr())
             assert e.value.code == scvs.SCVS_ERR_ARG
+
+
+def test_mode_energies_match_oracle():
+    """Energies and a posteriori increments of a solved mesh and of a batch of two
+    components, against the oracle's literal time-domain evaluation on the GPU's
+    own modal solution."""
+    wls = [workloads.pipe_workload(n_c=3, n_r=2, n_x=5, n_modes=6, length=2.5, seed=0),
+           workloads.pipe_workload(n_c=2, n_r=1, n_x=4, n_modes=6, length=2.0, radius=0.8, seed=1)]
+    U = workloads.union_workload(wls)
+    m = len(U["omegas"])
+    with scvs.Solver(tol=1e-12, max_cycles=2000) as s:
+        mid = scvs.scvs_set_mesh(s.ctx, U["mesh"])
+        scvs.scvs_set_components(s.ctx, mid, U["n_comp"], U["node_comp"])
+        scvs.scvs_set_physics(s.ctx, mid, U["rho"], U["mu"])
+        with pytest.raises(scvs.ScvsError) as e:
+            scvs.scvs_mode_energies(s.ctx, mid, 2 * m)
+        assert e.value.code == scvs.SCVS_ERR_STATE
+        scvs.scvs_set_modes(s.ctx, mid, U["omegas"], U["g"])
+        rep = scvs.scvs_solve(s.ctx, mid, 2 * m)
+        assert all(r["status"] == scvs.SCVS_CONVERGED for r in rep)
+        E, inc = scvs.scvs_mode_energies(s.ctx, mid, 2 * m)
+        N = U["mesh"]["xyz"].shape[0]
+        u, _ = scvs.scvs_get_modal(s.ctx, mid, m, N, 3, U["mesh"]["n_vertices"])
+    for i, (wl, mp) in enumerate(zip(wls, U["maps"])):
+        Ms = fem.assemble(wl["mesh"])["Ms"]
+        Ui = u[:, mp]
+        ref_E = bcspec.mode_energies(Ms, Ui, U["omegas"], U["period"], 32)
+        ref_inc = bcspec.a_posteriori_increments(Ms, Ui, U["omegas"], U["period"], 32)
+        assert np.allclose(E[i * m:(i + 1) * m], ref_E, rtol=1e-11, atol=0), (i, E, ref_E)
+        assert np.allclose(inc[i * m:(i + 1) * m], ref_inc, rtol=1e-10, atol=1e-15), (i, inc, ref_inc)
