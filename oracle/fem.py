@@ -16,7 +16,9 @@ What it computes (arXiv 2009.06725):
     symmetric),
   * Dirichlet lifting (Eq. shape_fun / dir_dis): velocity dofs of Dirichlet nodes
     are prescribed, their columns moved to the right-hand side of both the
-    momentum rows and the continuity rows,
+    momentum rows and the continuity rows; an optional Neumann load (the
+    boundary integral of Eq. LS_construction, oracle/boundary.py) is added to
+    the momentum rows,
   * an exact sparse direct solve per mode (SuperLU, complex128),
   * reconstruction in time (Eq. sol_reconstruct) and the relative L2 error
     (Eq. total_error) with the L2(Omega) norm evaluated with M_s.
@@ -277,10 +279,21 @@ def solve_modes(mats, wl):
         A = saddle_matrix(mats, w, wl["rho"], wl["mu"])
         g = wl["g"][k].reshape(-1)
         A_FF, b_F, free = lifted_system(A, dd, g)
+        b_F = b_F + _load(mats, wl, k)[free]
         X[k, dd] = g
         if np.any(b_F != 0):
             X[k, free] = direct_solve(A_FF, b_F)
     return X
+
+
+def _load(mats, wl, k):
+    """Full-length momentum load of mode k: the Neumann term int_{Gamma_h} M_A h_c
+    (wl["load"] [m][N][d], e.g. from oracle.boundary.neumann_load), zero if absent."""
+    n = dof_count(mats)
+    out = np.zeros(n, dtype=np.complex128)
+    if wl.get("load") is not None:
+        out[: mats["dim"] * mats["N"]] = np.asarray(wl["load"][k]).reshape(-1)
+    return out
 
 
 def masked_apply(mats, omegas, rho, mu, dir_nodes, Xblock):
@@ -314,7 +327,7 @@ def rhs_block(mats, wl):
         g = wl["g"][k].reshape(-1)
         gfull = np.zeros(n, dtype=np.complex128)
         gfull[dd] = g
-        b = -(A @ gfull)
+        b = -(A @ gfull) + _load(mats, wl, k)
         b[dd] = g
         B[:, k] = b
     return B
@@ -330,6 +343,7 @@ def relative_residual(mats, wl, X):
         A = saddle_matrix(mats, w, wl["rho"], wl["mu"])
         g = wl["g"][k].reshape(-1)
         A_FF, b_F, free = lifted_system(A, dd, g)
+        b_F = b_F + _load(mats, wl, k)[free]
         r = b_F - A_FF @ X[k, free]
         nb = np.linalg.norm(b_F)
         out.append(np.linalg.norm(r) / nb if nb > 0 else np.linalg.norm(r))

@@ -1,0 +1,101 @@
+"""Pins of the Neumann (traction) boundary term of the oracle: face tables,
+P2 face mass matrices against closed forms, and the paper's channel case with
+a traction inlet (Sec. 4.1) against its analytic solution (Eq. channel_ana):
+exact at omega = 0 (the parabola lies in P2), third-order convergent at
+W = 2 pi."""
+import numpy as np
+import pytest
+
+from oracle import boundary, fem
+from synthetic import meshes, workloads
+
+
+def test_face_tables_are_faces():
+    # every local face's edge nodes are the midpoints of its vertex pairs (affine P2)
+    for mesh in (meshes.channel2d(4, 2), workloads.pipe_workload(n_c=3, n_r=2, n_x=3, n_modes=1)["mesh"]):
+        xyz, conn = mesh["xyz"], mesh["conn"]
+        local = boundary.FACES_2D if mesh["dim"] == 2 else boundary.FACES_3D
+        nv = mesh["dim"]
+        pairs = ((0, 1),) if nv == 2 else ((0, 1), (1, 2), (2, 0))
+        for f in local:
+            for j, (a, b) in enumerate(pairs):
+                mid = 0.5 * (xyz[conn[:, f[a]]] + xyz[conn[:, f[b]]])
+                assert np.allclose(xyz[conn[:, f[nv + j]]], mid, atol=1e-12)
+
+
+def test_face_mass_row_sums_closed_form():
+    # int over a P2 face of each basis function: segment L/6, L/6, 2L/3;
+    # triangle 0 at the vertices and |F|/3 at the edge nodes
+    seg = boundary.face_mass_reference(1)
+    assert np.allclose(seg.sum(axis=1), [1 / 6, 1 / 6, 2 / 3], atol=1e-15)
+    tri = boundary.face_mass_reference(2)
+    assert np.allclose(tri.sum(axis=1), [0, 0, 0, 1 / 6, 1 / 6, 1 / 6], atol=1e-15)
+    for M in (seg, tri):
+        assert np.allclose(M, M.T) and np.all(np.linalg.eigvalsh(M) > 0)
+
+
+def test_inlet_faces_and_total_measure():
+    mesh = meshes.channel2d(8, 4)
+    faces = boundary.boundary_faces(mesh, meshes.INLET)
+    assert faces.shape == (4, 3)  # one triangle edge per inlet cell
+    assert np.allclose(mesh["xyz"][faces.ravel(), 0], 0.0)
+    Mg = boundary.face_mass(mesh, faces)
+    assert Mg.sum() == pytest.approx(2 * mesh["half_height"], rel=1e-14)
+    # with every node tagged only faces of one element count: the whole boundary
+    every = dict(mesh, tag=mesh["tag"] | 8)
+    allf = boundary.boundary_faces(every, 8)
+    assert allf.shape[0] == 2 * (8 + 4)
+    assert boundary.face_mass(every, allf).sum() == pytest.approx(2 * (4.0 + 2 * mesh["half_height"]), rel=1e-14)
+    wl = workloads.pipe_workload(n_c=6, n_r=4, n_x=3, n_modes=1)
+    faces3 = boundary.boundary_faces(wl["mesh"], meshes.INLET)
+    assert np.allclose(wl["mesh"]["xyz"][faces3.ravel(), 0], 0.0)
+    area = boundary.face_measures(wl["mesh"], faces3).sum()
+    assert boundary.face_mass(wl["mesh"], faces3).sum() == pytest.approx(area, rel=1e-13)
+    assert abs(area - np.pi) < 0.05 * np.pi  # polygonal unit disk
+    # no outlet face is taken for the inlet and vice versa
+    out = boundary.boundary_faces(wl["mesh"], meshes.OUTLET)
+    assert out.shape[0] == faces3.shape[0]
+    assert not set(map(tuple, np.sort(out, axis=1))) & set(map(tuple, np.sort(faces3, axis=1)))
+
+
+def _traction_channel(nx, ny, omegas, hx=1.0, rho=1.0, mu=0.01, L=4.0, H=0.5):
+    mesh = meshes.channel2d(nx, ny, length=L, half_height=H)
+    walls = np.flatnonzero((mesh["tag"] & meshes.WALL) != 0)
+    faces = boundary.boundary_faces(mesh, meshes.INLET)
+    h = np.zeros((mesh["xyz"].shape[0], 2))
+    h[:, 0] = hx
+    b = boundary.neumann_load(mesh, faces, h)
+    wl = dict(mesh=mesh, omegas=np.asarray(omegas, dtype=np.float64), rho=rho, mu=mu, dir_nodes=walls,
+              g=np.zeros((len(omegas), walls.size, 2), dtype=np.complex128),
+              load=np.stack([b.astype(np.complex128)] * len(omegas)))
+    mats = fem.assemble(mesh)
+    return mesh, mats, wl, fem.solve_modes(mats, wl)
+
+
+def test_traction_channel_steady_is_exact():
+    hx, mu, L, H = 1.0, 0.01, 4.0, 0.5
+    mesh, mats, wl, X = _traction_channel(8, 4, [0.0], hx=hx, mu=mu, L=L, H=H)
+    u, p = fem.split_fields(mats, X[0])
+    y = mesh["xyz"][:, 1]
+    ux = hx / (2 * mu * L) * (H - y) * (H + y)
+    assert np.abs(u[:, 0] - ux).max() < 1e-10 * ux.max()
+    assert np.abs(u[:, 1]).max() < 1e-10 * ux.max()
+    x = mesh["xyz"][: mats["P"], 0]
+    assert np.abs(p - hx * (L - x) / L).max() < 1e-10 * hx
+    assert np.all(fem.relative_residual(mats, wl, X) < 1e-12)
+
+
+def test_traction_channel_oscillatory_converges_to_cosh_profile():
+    hx, rho, mu, L, H = 1.0, 1.0, 0.01, 4.0, 0.5
+    W = 2 * np.pi
+    w = W * (mu / rho) / H ** 2
+    lam = np.sqrt(1j * W)
+    errs = []
+    for nx, ny in ((8, 4), (16, 8)):
+        mesh, mats, wl, X = _traction_channel(nx, ny, [w], hx=hx, rho=rho, mu=mu, L=L, H=H)
+        u, _ = fem.split_fields(mats, X[0])
+        y = mesh["xyz"][:, 1]
+        ux = -1j * hx / (rho * L * w) * (1 - np.cosh(lam * y / H) / np.cosh(lam))
+        ref = np.stack([ux, np.zeros_like(ux)], axis=1)
+        errs.append(fem.relative_l2_error(mats["Ms"], ref, u))
+    assert errs[0] < 1e-2 and errs[0] / errs[1] > 6.0, errs  # measured 2.5e-3, ratio 11.5
