@@ -27,9 +27,10 @@
  *    VTK quadratic-simplex order (vertices, then edge nodes (0,1),(1,2),(2,0)
  *    [, (0,3),(1,3),(2,3)]); vertex nodes are numbered first, so node ids
  *    0..n_vertices-1 are the P1 pressure dofs; tag uint8 [n_nodes] with bits
- *    SCVS_TAG_WALL / _INLET / _OUTLET.  A node tagged WALL or INLET is a
- *    Dirichlet node (all velocity components prescribed); the remaining
- *    boundary is traction-free (Eq. steady_stokes with h = 0).
+ *    SCVS_TAG_WALL / _INLET / _OUTLET / _NEUMANN.  A node tagged WALL or INLET
+ *    is a Dirichlet node (all velocity components prescribed); the remaining
+ *    boundary is traction-free (Eq. steady_stokes with h = 0) unless
+ *    scvs_set_neumann gives a traction on faces tagged NEUMANN.
  *  - Dof ordering of one mode: velocity dof (node*dim + c), then the pressure
  *    dof of every vertex.  Device vectors hold every mode of a mesh
  *    interleaved: element (dof, k) at dof*ld + k with ld = scvs_mode_stride().
@@ -58,6 +59,7 @@ extern "C" {
 #define SCVS_TAG_WALL 1
 #define SCVS_TAG_INLET 2
 #define SCVS_TAG_OUTLET 4
+#define SCVS_TAG_NEUMANN 8 /* traction boundary of scvs_set_neumann (not Dirichlet unless also WALL or INLET) */
 
 /* ---- per-mode solve status (scvs_mode_report.status) -------------------- */
 #define SCVS_CONVERGED 0  /* FP64 ||b - A x|| / ||b|| <= tol */
@@ -354,6 +356,21 @@ int scvs_kernel_times(scvs_ctx *ctx, int32_t n_classes, double *ms, double *byte
  * 0 = candidate not valid for the mode stride.  Either pointer may be NULL. */
 #define SCVS_TUNE_TILES 5
 int scvs_tuned_shapes(scvs_ctx *ctx, int32_t mesh_id, int32_t *shape, float *us);
+
+/* Neumann (traction) data of every mode (Eq. steady_stokes, boundary term of
+ * Eq. LS_construction): the momentum right-hand side gains
+ * b_u[A, c] = int_{Gamma_h} M_A h_c dGamma, with h interpolated from nodal values
+ * by the P2 trace basis (b_u = M_Gamma h, M_Gamma the P2 boundary mass matrix of
+ * straight-sided faces).  Gamma_h is the set of element faces whose nodes all
+ * carry SCVS_TAG_NEUMANN and that belong to one element only.  Rows of
+ * Dirichlet nodes keep their prescribed values.
+ *   h        host, complex [n_modes][n_nodes][dim]: nodal traction of every mode
+ *            (only nodes of Gamma_h are read; caller-owned, copied)
+ *   n_faces  out (may be NULL): number of faces of Gamma_h
+ * Call after scvs_set_modes (which clears the Neumann data); the data persist
+ * across scvs_set_physics.  Returns SCVS_ERR_STATE before scvs_set_modes,
+ * SCVS_ERR_ARG for a bad id or a null h. */
+int scvs_set_neumann(scvs_ctx *ctx, int32_t mesh_id, const scvs_c64 *h, int64_t *n_faces);
 
 /* Spectral preprocessing of sampled periodic boundary data (Sec. 3, steps 1
  * and 2 of the algorithm): the Fourier coefficients of Eq. SCVS_bc by the

@@ -183,6 +183,7 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
   if (n_modes < 1 || n_modes > 128) return fail(c, SCVS_ERR_ARG, "n_modes must be in [1, 128]");
   if (!omega || (!g && m->n_dir > 0)) return fail(c, SCVS_ERR_ARG, "null omega or g");
   m->mode_arena.release();
+  m->neu = nullptr;
   m->pc = PcTables{};
   m->mpl_spmm = m->mpl_cheb = 0;
   m->tile_spmm = m->tile_cheb = 0;
@@ -796,6 +797,19 @@ int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *shape, float *us) {
     }
     if (us)
       for (int i = 0; i < 2 * 3 * SCVS_TUNE_TILES; ++i) us[i] = i < (int)m->tune_us.size() ? m->tune_us[i] : 0.0f;
+    return SCVS_OK;
+  });
+}
+
+int scvs_set_neumann(scvs_ctx *c, int32_t mesh_id, const scvs_c64 *h, int64_t *n_faces) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !h) return fail(c, SCVS_ERR_ARG, "bad mesh id or null h");
+    if (m->m == 0) return fail(c, SCVS_ERR_STATE, "call scvs_set_modes first");
+    const int64_t nf = set_neumann(*c, *m, reinterpret_cast<const double2 *>(h));
+    m->solved = false;
+    lift_rhs(*c, *m);
+    if (n_faces) *n_faces = nf;
     return SCVS_OK;
   });
 }

@@ -11,7 +11,10 @@
 //      entry is summed in the same order on every run (deterministic)
 //   5. Dirichlet masking, FP32 copies and diagonals
 #include <algorithm>
+#include <array>
 #include <climits>
+#include <cmath>
+#include <map>
 #include "scvs_internal.h"
 
 namespace scvs {
@@ -594,6 +597,150 @@ void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, c
   c.launches.n += 4;
   SCVS_CUDA(cudaStreamSynchronize(s));
   SCVS_CUDA(cudaGetLastError());
+}
+
+// ---- Neumann (traction) load ---------------------------------------------
+// b_u[A, c] = int_{Gamma_h} M_A h_c dGamma (the boundary term of Eq.
+// LS_construction) for a traction given by nodal values and interpolated with
+// the P2 trace basis: b_u = M_Gamma h.  Gamma_h is the set of element faces
+// whose nodes all carry SCVS_TAG_NEUMANN and that belong to one element only
+// (found on the host; the count runs over the tagged faces, which include
+// every face with the same nodes).  Straight-sided faces: M_F = |F| times the
+// reference matrix of the P2 segment or triangle (closed forms, per unit
+// measure).  The load is gathered per node over its incident faces in face
+// order (no atomics: deterministic).
+
+// local P2 faces of an element, each in the face's VTK order
+static const int FACES2[3][3] = {{0, 1, 3}, {1, 2, 4}, {2, 0, 5}};
+static const int FACES3[4][6] = {{0, 1, 2, 4, 5, 6}, {0, 1, 3, 4, 8, 7}, {1, 2, 3, 5, 9, 8}, {2, 0, 3, 6, 7, 9}};
+// P2 face mass matrices per unit measure: segment (v0, v1, mid) and triangle
+// (v0, v1, v2, e01, e12, e20)
+static const double SEG_M[3][3] = {{4. / 30, -1. / 30, 2. / 30}, {-1. / 30, 4. / 30, 2. / 30}, {2. / 30, 2. / 30, 16. / 30}};
+static const double TRI_M[6][6] = {{6. / 180, -1. / 180, -1. / 180, 0, -4. / 180, 0},
+                                   {-1. / 180, 6. / 180, -1. / 180, 0, 0, -4. / 180},
+                                   {-1. / 180, -1. / 180, 6. / 180, -4. / 180, 0, 0},
+                                   {0, 0, -4. / 180, 32. / 180, 16. / 180, 16. / 180},
+                                   {-4. / 180, 0, 0, 16. / 180, 32. / 180, 16. / 180},
+                                   {0, -4. / 180, 0, 16. / 180, 16. / 180, 32. / 180}};
+
+// neu[(A dim + c) ld + k] = sum over the faces of A (incidence order) of
+// sum_b M_F[a][b] h[k][B_b][c]; one thread per (node, component, mode slot).
+__global__ void k_neumann_load(const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
+                               const int32_t *__restrict__ fnodes, const double *__restrict__ fmass, int nfl,
+                               const double2 *__restrict__ h, int64_t N, int dim, int m, int ld,
+                               double2 *__restrict__ neu) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= (int64_t)dim * N * ld) return;
+  const int k = (int)(f % ld);
+  const int64_t dof = f / ld, A = dof / dim;
+  const int c = (int)(dof % dim);
+  double sx = 0.0, sy = 0.0;
+  if (k < m)
+    for (int64_t t = inc_ptr[A]; t < inc_ptr[A + 1]; ++t) {
+      const int fc = inc[2 * t], a = inc[2 * t + 1];
+      const double *Mrow = fmass + ((int64_t)fc * nfl + a) * nfl;
+      for (int b = 0; b < nfl; ++b) {
+        const double2 v = h[((int64_t)k * N + fnodes[(int64_t)fc * nfl + b]) * dim + c];
+        sx += Mrow[b] * v.x;
+        sy += Mrow[b] * v.y;
+      }
+    }
+  neu[f] = make_double2(sx, sy);
+}
+
+int64_t set_neumann(Ctx &c, Mesh &m, const double2 *h_host) {
+  const int dim = m.dim, nl = m.nl, nfl = dim == 2 ? 3 : 6, nf_el = dim == 2 ? 3 : 4;
+  const int64_t N = m.N, E = m.E;
+  std::vector<int32_t> conn((size_t)E * nl);
+  std::vector<uint8_t> tag(N);
+  std::vector<double> xyz((size_t)N * dim);
+  SCVS_CUDA(cudaMemcpyAsync(conn.data(), m.conn, conn.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(tag.data(), m.tag, N, cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(xyz.data(), m.xyz, xyz.size() * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  // tagged faces, keyed by their sorted vertices
+  std::vector<std::array<int32_t, 6>> cand;
+  std::map<std::array<int32_t, 3>, int> count;
+  for (int64_t e = 0; e < E; ++e)
+    for (int lf = 0; lf < nf_el; ++lf) {
+      std::array<int32_t, 6> nodes{};
+      bool all = true;
+      for (int a = 0; a < nfl; ++a) {
+        nodes[a] = conn[(size_t)e * nl + (dim == 2 ? FACES2[lf][a] : FACES3[lf][a])];
+        all = all && (tag[nodes[a]] & SCVS_TAG_NEUMANN);
+      }
+      if (!all) continue;
+      std::array<int32_t, 3> key{nodes[0], nodes[1], dim == 2 ? -1 : nodes[2]};
+      std::sort(key.begin(), key.begin() + dim);
+      ++count[key];
+      cand.push_back(nodes);
+    }
+  std::vector<int32_t> fnodes;
+  std::vector<double> fmass;
+  for (const auto &nodes : cand) {
+    std::array<int32_t, 3> key{nodes[0], nodes[1], dim == 2 ? -1 : nodes[2]};
+    std::sort(key.begin(), key.begin() + dim);
+    if (count[key] != 1) continue;  // shared by two elements: interior
+    double meas;
+    const double *p0 = &xyz[(size_t)nodes[0] * dim], *p1 = &xyz[(size_t)nodes[1] * dim];
+    if (dim == 2) {
+      meas = std::hypot(p1[0] - p0[0], p1[1] - p0[1]);
+    } else {
+      const double *p2 = &xyz[(size_t)nodes[2] * dim];
+      const double u[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+      const double v[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+      const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+      meas = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    }
+    for (int a = 0; a < nfl; ++a) fnodes.push_back(nodes[a]);
+    for (int a = 0; a < nfl; ++a)
+      for (int b = 0; b < nfl; ++b) fmass.push_back(meas * (dim == 2 ? SEG_M[a][b] : TRI_M[a][b]));
+  }
+  const int64_t nf = (int64_t)fnodes.size() / nfl;
+  // node -> (face, local index) incidence, by node then face
+  std::vector<int64_t> inc_ptr(N + 1, 0);
+  for (int64_t f = 0; f < nf; ++f)
+    for (int a = 0; a < nfl; ++a) ++inc_ptr[fnodes[(size_t)f * nfl + a] + 1];
+  for (int64_t i = 0; i < N; ++i) inc_ptr[i + 1] += inc_ptr[i];
+  std::vector<int32_t> inc(2 * std::max<int64_t>(inc_ptr[N], 1));
+  {
+    std::vector<int64_t> fill(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int64_t f = 0; f < nf; ++f)
+      for (int a = 0; a < nfl; ++a) {
+        const int64_t t = fill[fnodes[(size_t)f * nfl + a]]++;
+        inc[2 * t] = (int32_t)f;
+        inc[2 * t + 1] = a;
+      }
+  }
+  const int64_t nh = (int64_t)m.m * N * dim;
+  int64_t *d_ptr = nullptr;
+  int32_t *d_inc = nullptr, *d_fn = nullptr;
+  double *d_fm = nullptr;
+  double2 *d_h = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &d_ptr, (N + 1) * sizeof(int64_t), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &d_inc, inc.size() * sizeof(int32_t), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &d_fn, std::max<size_t>(fnodes.size(), 1) * sizeof(int32_t), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &d_fm, std::max<size_t>(fmass.size(), 1) * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &d_h, nh * sizeof(double2), c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(d_ptr, inc_ptr.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(d_inc, inc.data(), inc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+  if (nf) {
+    SCVS_CUDA(cudaMemcpyAsync(d_fn, fnodes.data(), fnodes.size() * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+    SCVS_CUDA(cudaMemcpyAsync(d_fm, fmass.data(), fmass.size() * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  }
+  SCVS_CUDA(cudaMemcpyAsync(d_h, h_host, nh * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+  const int64_t nu = (int64_t)dim * N * m.ld;
+  m.neu = m.mode_arena.alloc<double2>(nu);
+  {
+    KScope ks(c, KC_ASSEMBLY, (double)nu * 16 + (double)nf * nfl * (4 + 8 * nfl) + (double)nh * 16);
+    k_neumann_load<<<ceil_div(nu, 256), 256, 0, c.stream>>>(d_ptr, d_inc, d_fn, d_fm, nfl, d_h, N, dim, m.m, m.ld,
+                                                            m.neu);
+    count_launch(c);
+  }
+  for (void *p : {(void *)d_ptr, (void *)d_inc, (void *)d_fn, (void *)d_fm, (void *)d_h})
+    SCVS_CUDA(cudaFreeAsync(p, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  return nf;
 }
 
 }  // namespace scvs

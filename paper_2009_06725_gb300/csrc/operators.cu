@@ -237,16 +237,18 @@ __global__ void k_scatter_dirichlet(const double2 *__restrict__ g, const int64_t
   gfull[(dir_nodes[i] * dim + c) * ld + k] = g[t];
 }
 
-// b = -y on free rows, b = gfull on Dirichlet velocity rows
+// b = -y (+ the Neumann load on velocity rows) on free rows, b = gfull on
+// Dirichlet velocity rows
 __global__ void k_lift_finish(const double2 *__restrict__ y, const double2 *__restrict__ gfull,
                               const uint8_t *__restrict__ dirm, int64_t N, int dim, int64_t n_dof, int ld,
-                              double2 *__restrict__ b) {
+                              const double2 *__restrict__ neu, double2 *__restrict__ b) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= n_dof * ld) return;
   int64_t dof = f / ld;
   bool dir = dof < N * dim && dirm[dof / dim];
   double2 v = y[f];
-  b[f] = dir ? gfull[f] : make_double2(-v.x, -v.y);
+  double2 l = (neu && dof < N * dim) ? neu[f] : make_double2(0.0, 0.0);
+  b[f] = dir ? gfull[f] : make_double2(l.x - v.x, l.y - v.y);
 }
 
 // Deterministic per-system squared norms over the free rows: one block per
@@ -363,7 +365,8 @@ void lift_rhs(Ctx &c, Mesh &m) {
   launch_saddle<double>(c, m, saddle_args<double>(c, m, false), gfull, y);
   {
     KScope ks(c, KC_VECTOR, (double)total * 48);
-    k_lift_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(y, gfull, m.dirmask, m.N, m.dim, m.n_dof, m.ld, m.b);
+    k_lift_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(y, gfull, m.dirmask, m.N, m.dim, m.n_dof, m.ld, m.neu,
+                                                              m.b);
     count_launch(c);
   }
   norms2_sys(c, m, m.b, nrm);

@@ -164,6 +164,7 @@ struct Mesh {
   double2 *g = nullptr;          // [m][n_dir][dim]
   double2 *b = nullptr;          // [n_dof][ld] lifted RHS (b_D = g)
   double2 *x = nullptr;          // [n_dof][ld] FP64 solution
+  double2 *neu = nullptr;        // [dim N][ld] Neumann load of the modes (null: traction-free)
   std::vector<double> bnorm;     // [n_comp * ld] ||b_F|| per system
   std::vector<double> lam_u;     // [ld] spectral radius estimate of D_r^-1 A_r per mode (velocity)
   std::vector<double> lam_c;     // [ld] same for the P1 coarse velocity operator
@@ -258,6 +259,7 @@ struct KScope {
 
 // ---- assembly.cu
 void build_mesh(Ctx &c, Mesh &m, const double *xyz_dev, const int32_t *conn_dev, const uint8_t *tag_dev);
+int64_t set_neumann(Ctx &c, Mesh &m, const double2 *h_host);  // returns the number of Neumann faces
 void scan_exclusive(Ctx &c, const int32_t *in, int64_t *out, int64_t n);
 
 // ---- operators.cu

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libscvs.so")
 SCVS_OK = 0
 SCVS_ERR_ARG, SCVS_ERR_MESH, SCVS_ERR_PRESSURE_NULLSPACE = -1, -2, -3
 SCVS_ERR_OOM, SCVS_ERR_CUDA, SCVS_ERR_STATE, SCVS_ERR_TIMEOUT = -4, -5, -6, -7
-SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET = 1, 2, 4
+SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET, SCVS_TAG_NEUMANN = 1, 2, 4, 8
 SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
 SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG, SCVS_PC_TRI_PMG_CS = 0, 1, 2, 3, 4
@@ -106,6 +106,7 @@ SIGNATURES = {
     "scvs_tuned_shapes": (_I32, [_P, _I32, _P, _P]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
+    "scvs_set_neumann": (_I32, [_P, _I32, _P, C.POINTER(_I64)]),
     "scvs_bc_spectrum": (_I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
     "scvs_mode_energies": (_I32, [_P, _I32, _I64, _P, _P]),
     "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
@@ -393,6 +394,15 @@ def scvs_tuned_shapes(ctx, mesh_id):
     us = us.reshape(2, 3, nt).round(1).tolist()
     return dict(mpl_spmm=int(shape[0]), tile_spmm=int(shape[1]), mpl_cheb=int(shape[2]), tile_cheb=int(shape[3]),
                 spmm_us=us[0], cheb_us=us[1])
+
+
+def scvs_set_neumann(ctx, mesh_id, h):
+    """Nodal tractions h [n_modes][n_nodes][dim] (complex) on the faces tagged
+    SCVS_TAG_NEUMANN; returns the number of such faces."""
+    hh = np.ascontiguousarray(h, dtype=np.complex128)
+    nf = C.c_int64(0)
+    _check(ctx, lib().scvs_set_neumann(ctx, mesh_id, _ptr(hh), C.byref(nf)))
+    return nf.value
 
 
 def scvs_bc_spectrum(ctx, g_t_dev, n_t, n_pts, n_modes, c_dev, w_dev=None):
