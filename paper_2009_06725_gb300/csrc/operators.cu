@@ -247,8 +247,14 @@ __global__ void k_lift_finish(const double2 *__restrict__ y, const double2 *__re
   int64_t dof = f / ld;
   bool dir = dof < N * dim && dirm[dof / dim];
   double2 v = y[f];
-  double2 l = (neu && dof < N * dim) ? neu[f] : make_double2(0.0, 0.0);
-  b[f] = dir ? gfull[f] : make_double2(l.x - v.x, l.y - v.y);
+  if (dir) {
+    b[f] = gfull[f];
+  } else if (neu && dof < N * dim) {
+    const double2 l = neu[f];
+    b[f] = make_double2(l.x - v.x, l.y - v.y);
+  } else {
+    b[f] = make_double2(-v.x, -v.y);
+  }
 }
 
 // Deterministic per-system squared norms over the free rows: one block per
