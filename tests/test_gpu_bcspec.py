@@ -1,12 +1,7 @@
 """Spectral preprocessing of sampled boundary data on the GPU (Eqs. SCVS_bc,
 mode_error) against the FP64 oracle, its output used as the solver's per-mode
 Dirichlet data (steps 1-3 of the algorithm of Sec. 3), and the a posteriori
-mode energies of a solved mesh.
-
-These tests stay off until the kernels' first run on a GPU
-(SCVS_RUN_PENDING=1 enables them)."""
-import os
-
+mode energies of a solved mesh."""
 import numpy as np
 import pytest
 
@@ -16,9 +11,7 @@ from synthetic import workloads
 
 from .gpu_util import rel_l2, stack_modal, torch_cuda
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("SCVS_RUN_PENDING") != "1",
-                                 reason="scvs_bc_spectrum awaits its first validation run")]
+pytestmark = pytest.mark.gpu
 
 
 def _samples(wl, n_t, seed=0):

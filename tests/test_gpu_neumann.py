@@ -1,12 +1,7 @@
 """Neumann (traction) inlets on the GPU (scvs_set_neumann) against the oracle:
 the lifted right-hand side with the boundary term element by element, the
 solutions of the paper's channel with a traction inlet (Sec. 4.1; exact
-parabola at omega = 0, Eq. channel_ana) and of a pipe with a traction inlet.
-
-These tests stay off until the kernel's first run on a GPU
-(SCVS_RUN_PENDING=1 enables them)."""
-import os
-
+parabola at omega = 0, Eq. channel_ana) and of a pipe with a traction inlet."""
 import numpy as np
 import pytest
 
@@ -17,9 +12,7 @@ from synthetic import meshes, workloads
 from .gpu_util import rel_err, rel_l2, stack_modal
 from .test_gpu_parity import _device_view
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("SCVS_RUN_PENDING") != "1",
-                                 reason="scvs_set_neumann awaits its first validation run")]
+pytestmark = pytest.mark.gpu
 
 
 def _traction_case(mesh, omegas, hx, rho=1.0, mu=0.01):
