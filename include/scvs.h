@@ -90,6 +90,8 @@ extern "C" {
 
 #define SCVS_GUESS_ZERO 0
 #define SCVS_GUESS_MLP 1
+#define SCVS_GUESS_CURRENT 2 /* start every mode from the solution the mesh holds (the last solve's, or the one
+                                given by scvs_set_solution), its Dirichlet rows reset to g: warm start / resume */
 
 typedef struct scvs_ctx scvs_ctx;
 typedef struct { double re, im; } scvs_c64;
@@ -135,7 +137,8 @@ typedef struct {
   int32_t status;     /* SCVS_CONVERGED / MAX_ITER / STAGNATED / NON_FINITE */
   int32_t iterations; /* Arnoldi steps spent on this mode */
   int32_t cycles;     /* restart cycles (= FP64 refinement steps) */
-  int32_t guess_used; /* 1 if the learned initial guess was kept (its residual was below ||b||) */
+  int32_t guess_used; /* 1 if the learned initial guess was kept (its residual was below ||b||), or with
+                         SCVS_GUESS_CURRENT */
   double rel_res;     /* final FP64 ||b_F - A_FF x_F - A_FD g|| / ||b_F|| (Eq. ls_error) */
   double res0;        /* the same relative residual at the start point: 1 for the zero start (x_F = 0),
                          below 1 where the learned guess was kept */
@@ -413,6 +416,43 @@ int scvs_bc_spectrum(scvs_ctx *ctx, int32_t n_t, int64_t n_pts, int32_t n_modes,
  * reductions.  Runs on the context's stream and synchronises it.  Returns
  * SCVS_ERR_STATE before scvs_solve, SCVS_ERR_ARG for a bad id or size. */
 int scvs_mode_energies(scvs_ctx *ctx, int32_t mesh_id, int64_t n_out, double *E, double *incr2);
+
+/* ---- checkpoint / resume --------------------------------------------------
+ * Every mode is an independent problem, so the modal solution is the
+ * checkpoint: a file holds the converged modes of one mesh with their omega_k,
+ * status and residual, and a resumed run starts matching modes from it
+ * (scvs_set_solution + opts.guess = SCVS_GUESS_CURRENT), so that they converge
+ * at the first true-residual check.  No paper counterpart. */
+
+/* Initial solution of every mode (layout of scvs_get_modal): u host complex
+ * [n_modes][n_nodes][dim], p host complex [n_modes][n_vertices] (copied).  The
+ * next scvs_solve with opts.guess = SCVS_GUESS_CURRENT starts from it.
+ * SCVS_ERR_STATE before scvs_set_modes; SCVS_ERR_ARG for a bad id or null arrays. */
+int scvs_set_solution(scvs_ctx *ctx, int32_t mesh_id, const scvs_c64 *u, const scvs_c64 *p);
+
+typedef struct {
+  int32_t dim, n_modes;
+  int64_t n_nodes, n_vertices;
+  uint64_t mesh_hash; /* scvs_mesh_hash of the mesh the modes belong to */
+  double tol;         /* relative residual the modes were solved to */
+} scvs_ckpt_header;
+
+/* FNV-1a 64 hash of a mesh's arrays (host pointers, the layout of
+ * scvs_set_mesh): sizes, xyz, conn and tag bytes.  Host only. */
+int scvs_mesh_hash(int32_t dim, int64_t n_nodes, int64_t n_vertices, const double *xyz, int64_t n_elem,
+                   const int32_t *conn, const uint8_t *tag, uint64_t *hash);
+
+/* Write / read a checkpoint file (host only; little-endian machine format):
+ * magic "SCVSCKP1", the header, omega [n_modes], status [n_modes] (SCVS_CONVERGED
+ * ...), rel_res [n_modes], u [n_modes][n_nodes][dim], p [n_modes][n_vertices]
+ * (complex), then an FNV-1a 64 checksum of everything before it.  Read checks
+ * magic, sizes and checksum and returns SCVS_ERR_ARG on any mismatch (nothing
+ * written to the outputs); each output array may be NULL (skipped), so a first
+ * call with NULL arrays reads the header to size them. */
+int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *header, const double *omega,
+                          const int32_t *status, const double *rel_res, const scvs_c64 *u, const scvs_c64 *p);
+int scvs_checkpoint_read(const char *path, scvs_ckpt_header *header, double *omega, int32_t *status,
+                         double *rel_res, scvs_c64 *u, scvs_c64 *p);
 
 /* Graph aggregates of a vertex graph, the coarse space of SCVS_PC_TRI_PMG_CS
  * (no paper counterpart: part of the preconditioner).  Host only: no context,

@@ -3,6 +3,7 @@
 // operators.cu, krylov.cu and recon.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -467,6 +468,30 @@ int scvs_get_modal(scvs_ctx *c, int32_t mesh_id, scvs_c64 *u, scvs_c64 *p) {
   });
 }
 
+int scvs_set_solution(scvs_ctx *c, int32_t mesh_id, const scvs_c64 *u, const scvs_c64 *p) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !u || !p) return fail(c, SCVS_ERR_ARG, "bad mesh id or null u / p");
+    if (m->m == 0) return fail(c, SCVS_ERR_STATE, "call scvs_set_modes first");
+    std::vector<double2> h((size_t)m->n_dof * m->ld, make_double2(0.0, 0.0));
+    const int64_t nu = (int64_t)m->dim * m->N;
+    for (int k = 0; k < m->m; ++k) {
+      for (int64_t d = 0; d < nu; ++d) {
+        const scvs_c64 v = u[(size_t)k * nu + d];
+        h[(size_t)d * m->ld + k] = make_double2(v.re, v.im);
+      }
+      for (int64_t v = 0; v < m->P; ++v) {
+        const scvs_c64 z = p[(size_t)k * m->P + v];
+        h[(size_t)(nu + v) * m->ld + k] = make_double2(z.re, z.im);
+      }
+    }
+    SCVS_CUDA(cudaMemcpyAsync(m->x, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    m->solved = false;
+    return SCVS_OK;
+  });
+}
+
 int scvs_modal_dev(scvs_ctx *c, int32_t mesh_id, const void **x, int64_t *n_dof, int32_t *ld) {
   return guarded(c, [&]() {
     Mesh *m = get_mesh(c, mesh_id);
@@ -837,6 +862,103 @@ int scvs_mode_energies(scvs_ctx *c, int32_t mesh_id, int64_t n_out, double *E, d
     mode_energies(*c, *m, E, incr2);
     return SCVS_OK;
   });
+}
+
+// ---- checkpoint files (host only) -----------------------------------------
+// FNV-1a 64-bit hash (Fowler, Noll, Vo): h = (h xor byte) * 1099511628211 from
+// 14695981039346656037.
+static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+static const uint64_t FNV_OFFSET = 14695981039346656037ULL;
+static const char CKPT_MAGIC[8] = {'S', 'C', 'V', 'S', 'C', 'K', 'P', '1'};
+
+int scvs_mesh_hash(int32_t dim, int64_t N, int64_t P, const double *xyz, int64_t E, const int32_t *conn,
+                   const uint8_t *tag, uint64_t *hash) {
+  if ((dim != 2 && dim != 3) || N <= 0 || P <= 0 || E <= 0 || !xyz || !conn || !tag || !hash) return SCVS_ERR_ARG;
+  const int64_t sizes[4] = {dim, N, P, E};
+  uint64_t h = fnv1a(FNV_OFFSET, sizes, sizeof(sizes));
+  h = fnv1a(h, xyz, (size_t)N * dim * sizeof(double));
+  h = fnv1a(h, conn, (size_t)E * (dim == 2 ? 6 : 10) * sizeof(int32_t));
+  h = fnv1a(h, tag, (size_t)N);
+  *hash = h;
+  return SCVS_OK;
+}
+
+static int64_t ckpt_payload(const scvs_ckpt_header &h) {
+  const int64_t m = h.n_modes;
+  return m * (8 + 4 + 8) + m * h.n_nodes * h.dim * 16 + m * h.n_vertices * 16;
+}
+
+static bool ckpt_header_ok(const scvs_ckpt_header &h) {
+  return (h.dim == 2 || h.dim == 3) && h.n_modes >= 1 && h.n_modes <= 128 && h.n_nodes > 0 && h.n_vertices > 0 &&
+         h.n_vertices <= h.n_nodes && h.n_nodes < INT32_MAX;
+}
+
+int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *hd, const double *omega, const int32_t *status,
+                          const double *rel_res, const scvs_c64 *u, const scvs_c64 *p) {
+  if (!path || !hd || !omega || !status || !rel_res || !u || !p || !ckpt_header_ok(*hd)) return SCVS_ERR_ARG;
+  const scvs_ckpt_header &h = *hd;
+  const int64_t m = h.n_modes, nu = (int64_t)h.n_nodes * h.dim;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return SCVS_ERR_ARG;
+  uint64_t sum = FNV_OFFSET;
+  bool ok = true;
+  auto put = [&](const void *d, size_t n) {
+    if (!ok) return;
+    ok = std::fwrite(d, 1, n, f) == n;
+    sum = fnv1a(sum, d, n);
+  };
+  put(CKPT_MAGIC, sizeof(CKPT_MAGIC));
+  put(&h, sizeof(h));
+  put(omega, m * sizeof(double));
+  put(status, m * sizeof(int32_t));
+  put(rel_res, m * sizeof(double));
+  put(u, (size_t)m * nu * sizeof(scvs_c64));
+  put(p, (size_t)m * h.n_vertices * sizeof(scvs_c64));
+  if (ok) ok = std::fwrite(&sum, 1, sizeof(sum), f) == sizeof(sum);
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SCVS_OK : SCVS_ERR_ARG;
+}
+
+int scvs_checkpoint_read(const char *path, scvs_ckpt_header *hd, double *omega, int32_t *status, double *rel_res,
+                         scvs_c64 *u, scvs_c64 *p) {
+  if (!path || !hd) return SCVS_ERR_ARG;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return SCVS_ERR_ARG;
+  std::vector<char> buf;
+  char chunk[1 << 16];
+  size_t n;
+  while ((n = std::fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + n);
+  std::fclose(f);
+  scvs_ckpt_header h{};
+  const size_t head = sizeof(CKPT_MAGIC) + sizeof(h);
+  if (buf.size() < head + sizeof(uint64_t) || std::memcmp(buf.data(), CKPT_MAGIC, sizeof(CKPT_MAGIC)) != 0)
+    return SCVS_ERR_ARG;
+  std::memcpy(&h, buf.data() + sizeof(CKPT_MAGIC), sizeof(h));
+  if (!ckpt_header_ok(h) || (int64_t)buf.size() != (int64_t)head + ckpt_payload(h) + (int64_t)sizeof(uint64_t))
+    return SCVS_ERR_ARG;
+  uint64_t stored = 0;
+  std::memcpy(&stored, buf.data() + buf.size() - sizeof(stored), sizeof(stored));
+  if (fnv1a(FNV_OFFSET, buf.data(), buf.size() - sizeof(stored)) != stored) return SCVS_ERR_ARG;
+  *hd = h;
+  const int64_t m = h.n_modes, nu = (int64_t)h.n_nodes * h.dim;
+  const char *q = buf.data() + head;
+  auto take = [&](void *dst, size_t bytes) {
+    if (dst) std::memcpy(dst, q, bytes);
+    q += bytes;
+  };
+  take(omega, m * sizeof(double));
+  take(status, m * sizeof(int32_t));
+  take(rel_res, m * sizeof(double));
+  take(u, (size_t)m * nu * sizeof(scvs_c64));
+  take(p, (size_t)m * h.n_vertices * sizeof(scvs_c64));
+  return SCVS_OK;
 }
 
 int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t *col, int32_t target,

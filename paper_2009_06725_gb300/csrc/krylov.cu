@@ -437,6 +437,15 @@ __global__ void k_init_x(const double2 *__restrict__ b, const uint8_t *__restric
   x[f] = dir ? b[f] : make_double2(0.0, 0.0);
 }
 
+// Warm start: keep x on free rows, x = b (= g) on Dirichlet velocity rows.
+__global__ void k_warm_x(const double2 *__restrict__ b, const uint8_t *__restrict__ dirm, int64_t N, int dim,
+                         int64_t total, int ld, double2 *__restrict__ x) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= total) return;
+  const int64_t dof = f / ld;
+  if (dof < N * dim && dirm[dof / dim]) x[f] = b[f];
+}
+
 template <typename T>
 struct Work {
   using C = typename cpx<T>::t;
@@ -552,12 +561,17 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   }
 
   const int64_t eb = ceil_div(total, 256);
-  bool guess_on = c.opts.guess == SCVS_GUESS_MLP && m.n_comp == 1 && guess_initial(c, m);
-  if (!guess_on) {
+  const bool warm = c.opts.guess == SCVS_GUESS_CURRENT;
+  const bool guess_on = !warm && c.opts.guess == SCVS_GUESS_MLP && m.n_comp == 1 && guess_initial(c, m);
+  if (warm) {
+    k_warm_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x);
+    count_launch(c);
+  } else if (!guess_on) {
     k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, nullptr, m.dof_comp);
     count_launch(c);
   }
-  for (auto &r : m.rep) r.guess_used = guess_on ? 1 : 0;
+  for (auto &r : m.rep) r.guess_used = (guess_on || warm) ? 1 : 0;
+  bool check_guess = guess_on || warm;  // drop a start no better than zero, once
 
   // page-locked word for the per-step active-system count, freed on every exit path
   struct PinnedInt {
@@ -577,7 +591,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       residual_fp64(c, m, nullptr, wk.V, wk.norm2);
     SCVS_CUDA(cudaMemcpyAsync(n2.data(), wk.norm2, S * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     SCVS_CUDA(cudaStreamSynchronize(c.stream));
-    if (cyc == 0 && guess_on) {
+    if (cyc == 0 && check_guess) {
       // a guess no better than zero is dropped for that mode (zero-start fallback)
       std::vector<int> reset(S, 0);
       int n_reset = 0;
@@ -586,7 +600,7 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
         const double r = std::sqrt(std::max(n2[s], 0.0));
         if (!(r < m.bnorm[s])) { reset[s] = 1; ++n_reset; rep(s).guess_used = 0; }
       }
-      guess_on = false;
+      check_guess = false;
       if (n_reset > 0) {
         SCVS_CUDA(cudaMemcpyAsync(wk.upd, reset.data(), S * sizeof(int), cudaMemcpyHostToDevice, c.stream));
         k_init_x<<<(unsigned)eb, 256, 0, c.stream>>>(m.b, m.dirmask, m.N, m.dim, total, ld, m.x, wk.upd, m.dof_comp);

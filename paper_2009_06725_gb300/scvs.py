@@ -23,13 +23,18 @@ SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET, SCVS_TAG_NEUMANN = 1, 2, 4, 8
 SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
 SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG, SCVS_PC_TRI_PMG_CS = 0, 1, 2, 3, 4
-SCVS_GUESS_ZERO, SCVS_GUESS_MLP = 0, 1
+SCVS_GUESS_ZERO, SCVS_GUESS_MLP, SCVS_GUESS_CURRENT = 0, 1, 2
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
 SCVS_KC_COUNT = 11
 SCVS_RECON_STATIC_MAX = 8192
 SCVS_TUNE_TILES = 5
 TUNE_TILES = (1, 2, 4, 8, 16)
 STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "stagnated", 3: "non_finite"}
+
+
+class scvs_ckpt_header(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_modes", C.c_int32), ("n_nodes", C.c_int64), ("n_vertices", C.c_int64),
+                ("mesh_hash", C.c_uint64), ("tol", C.c_double)]
 
 
 class scvs_opts(C.Structure):
@@ -109,6 +114,10 @@ SIGNATURES = {
     "scvs_set_neumann": (_I32, [_P, _I32, _P, C.POINTER(_I64)]),
     "scvs_bc_spectrum": (_I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
     "scvs_mode_energies": (_I32, [_P, _I32, _I64, _P, _P]),
+    "scvs_set_solution": (_I32, [_P, _I32, _P, _P]),
+    "scvs_mesh_hash": (_I32, [_I32, _I64, _I64, _P, _I64, _P, _P, C.POINTER(C.c_uint64)]),
+    "scvs_checkpoint_write": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P]),
+    "scvs_checkpoint_read": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P]),
     "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "scvs_schur_coarse_info": (_I32, [_P, _I32, _P]),
 }
@@ -421,6 +430,101 @@ def scvs_mode_energies(ctx, mesh_id, n_out):
     inc = np.zeros(n_out)
     _check(ctx, lib().scvs_mode_energies(ctx, mesh_id, n_out, _ptr(E), _ptr(inc)))
     return E, inc
+
+
+def scvs_set_solution(ctx, mesh_id, u, p):
+    """Initial solution [n_modes][N][d], [n_modes][P] (complex) for opts.guess = SCVS_GUESS_CURRENT."""
+    uu = np.ascontiguousarray(u, dtype=np.complex128)
+    pp = np.ascontiguousarray(p, dtype=np.complex128)
+    return _check(ctx, lib().scvs_set_solution(ctx, mesh_id, _ptr(uu), _ptr(pp)))
+
+
+def scvs_mesh_hash(mesh):
+    """FNV-1a 64 hash of a mesh dict's arrays (host only)."""
+    xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
+    conn = np.ascontiguousarray(mesh["conn"], dtype=np.int32)
+    tag = np.ascontiguousarray(mesh["tag"], dtype=np.uint8)
+    h = C.c_uint64(0)
+    rc = lib().scvs_mesh_hash(mesh["dim"], xyz.shape[0], mesh["n_vertices"], _ptr(xyz), conn.shape[0], _ptr(conn),
+                              _ptr(tag), C.byref(h))
+    if rc < 0:
+        raise ScvsError(rc, "scvs_mesh_hash: bad mesh")
+    return h.value
+
+
+def scvs_checkpoint_write(path, header, omega, status, rel_res, u, p):
+    arrs = [np.ascontiguousarray(omega, dtype=np.float64), np.ascontiguousarray(status, dtype=np.int32),
+            np.ascontiguousarray(rel_res, dtype=np.float64), np.ascontiguousarray(u, dtype=np.complex128),
+            np.ascontiguousarray(p, dtype=np.complex128)]
+    m = header.n_modes
+    shapes = [(m,), (m,), (m,), (m, header.n_nodes, header.dim), (m, header.n_vertices)]
+    for a, sh in zip(arrs, shapes):
+        if a.size != int(np.prod(sh)):
+            raise ScvsError(SCVS_ERR_ARG, "scvs_checkpoint_write: array size does not match the header")
+    rc = lib().scvs_checkpoint_write(os.fsencode(path), C.byref(header), *[_ptr(a) for a in arrs])
+    if rc < 0:
+        raise ScvsError(rc, f"scvs_checkpoint_write: cannot write {path}")
+
+
+def scvs_checkpoint_read(path):
+    """(header, omega, status, rel_res, u [m][N][d], p [m][P]); raises ScvsError on a bad file."""
+    h = scvs_ckpt_header()
+    rc = lib().scvs_checkpoint_read(os.fsencode(path), C.byref(h), None, None, None, None, None)
+    if rc < 0:
+        raise ScvsError(rc, f"scvs_checkpoint_read: bad checkpoint {path}")
+    m = h.n_modes
+    om, st, rr = np.zeros(m), np.zeros(m, dtype=np.int32), np.zeros(m)
+    u = np.zeros((m, h.n_nodes, h.dim), dtype=np.complex128)
+    p = np.zeros((m, h.n_vertices), dtype=np.complex128)
+    rc = lib().scvs_checkpoint_read(os.fsencode(path), C.byref(h), _ptr(om), _ptr(st), _ptr(rr), _ptr(u), _ptr(p))
+    if rc < 0:
+        raise ScvsError(rc, f"scvs_checkpoint_read: bad checkpoint {path}")
+    return h, om, st, rr, u, p
+
+
+def save_checkpoint(ctx, mesh_id, mesh, omegas, reports, tol, path):
+    """Write the modal solution of a solved mesh with its per-mode status: a mode counts as
+    converged when every component's system of that mode converged."""
+    m = len(omegas)
+    N, P, d = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["dim"]
+    u, p = scvs_get_modal(ctx, mesh_id, m, N, d, P)
+    n_comp = max(1, len(reports) // m)
+    status = np.array([SCVS_CONVERGED if all(reports[c * m + k]["status"] == SCVS_CONVERGED for c in range(n_comp))
+                       else SCVS_MAX_ITER for k in range(m)], dtype=np.int32)
+    rel = np.array([max(reports[c * m + k]["rel_res"] for c in range(n_comp)) for k in range(m)])
+    hdr = scvs_ckpt_header(d, m, N, P, scvs_mesh_hash(mesh), float(tol))
+    scvs_checkpoint_write(path, hdr, omegas, status, rel, u, p)
+
+
+def resumable_modes(header, f_omega, f_status, omegas, tol, mesh_hash):
+    """For every current mode k, the checkpoint mode j with the same omega (exact) that converged
+    to a tolerance at least as tight on the same mesh, else -1."""
+    out = np.full(len(omegas), -1, dtype=np.int64)
+    if header.mesh_hash != mesh_hash or header.tol > tol:
+        return out
+    for k, w in enumerate(omegas):
+        for j in range(header.n_modes):
+            if f_omega[j] == w and f_status[j] == SCVS_CONVERGED:
+                out[k] = j
+                break
+    return out
+
+
+def resume_from_checkpoint(ctx, mesh_id, mesh, omegas, tol, path):
+    """Load the matching modes of a checkpoint as the initial solution (the others start
+    from zero); solve next with opts.guess = SCVS_GUESS_CURRENT.  Returns the map of
+    resumable_modes."""
+    h, om, st, _, u, p = scvs_checkpoint_read(path)
+    if h.n_nodes != mesh["xyz"].shape[0] or h.n_vertices != mesh["n_vertices"] or h.dim != mesh["dim"]:
+        return np.full(len(omegas), -1, dtype=np.int64)
+    idx = resumable_modes(h, om, st, omegas, tol, scvs_mesh_hash(mesh))
+    u0 = np.zeros((len(omegas), h.n_nodes, h.dim), dtype=np.complex128)
+    p0 = np.zeros((len(omegas), h.n_vertices), dtype=np.complex128)
+    for k, j in enumerate(idx):
+        if j >= 0:
+            u0[k], p0[k] = u[j], p[j]
+    scvs_set_solution(ctx, mesh_id, u0, p0)
+    return idx
 
 
 def scvs_graph_aggregates(row_ptr, col, target):
