@@ -165,3 +165,37 @@ def test_bad_arguments():
 def test_default_aggregate_count():
     o = scvs.scvs_default_opts()
     assert o.schur_agg == 96 and o.precond == scvs.SCVS_PC_TRI_PMG
+
+
+def _random_graph(n, n_comp, extra, seed):
+    """n vertices in n_comp components: a random spanning tree per component plus
+    extra random edges inside components; vertex ids shuffled across components."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(n)
+    parts = np.array_split(perm, n_comp)
+    edges = []
+    for part in parts:
+        for i in range(1, part.size):
+            edges.append((int(part[i]), int(part[rng.integers(0, i)])))
+        for _ in range(extra if part.size > 1 else 0):
+            a, b = rng.choice(part, 2, replace=False)
+            edges.append((int(a), int(b)))
+    return csr_from_edges(n, edges)
+
+
+def test_random_graphs_property():
+    hypothesis = pytest.importorskip("hypothesis")
+    st = hypothesis.strategies
+
+    @hypothesis.settings(max_examples=40, deadline=None)
+    @hypothesis.given(n=st.integers(1, 300), n_comp=st.integers(1, 6), extra=st.integers(0, 200),
+                      target=st.integers(1, 64), seed=st.integers(0, 2**31 - 1))
+    def prop(n, n_comp, extra, target, seed):
+        n_comp = min(n_comp, n)
+        ptr, col = _random_graph(n, n_comp, extra, seed)
+        agg, n_agg, n_blk = scvs.scvs_graph_aggregates(ptr, col, target)
+        assert n_blk == n_comp
+        check_partition(ptr, col, agg, n_agg, n_blk, target)
+        assert np.array_equal(agg, scvs.scvs_graph_aggregates(ptr, col, target)[0])
+
+    prop()
