@@ -3,8 +3,6 @@
 import os
 import re
 
-import pytest
-
 from paper_2009_06725_gb300 import build, scvs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

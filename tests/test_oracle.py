@@ -8,7 +8,6 @@ import os
 
 import numpy as np
 import pytest
-import scipy.sparse as spm
 
 from oracle import fem
 from synthetic import meshes, workloads
