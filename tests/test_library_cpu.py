@@ -39,3 +39,20 @@ def test_header_constants_match_binding():
     src = open(os.path.join(ROOT, "include", "scvs.h")).read()
     for name, val in re.findall(r"#define (SCVS_[A-Z0-9_]+) \(?(-?\d+)\)?", src):
         assert getattr(scvs, name) == int(val), name
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/scvs.h compiles on its own as C99 (no C++ or torch types in the ABI)."""
+    import shutil
+    import subprocess
+
+    import pytest
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "scvs.h"\nint main(void) { scvs_opts o; scvs_ckpt_header h; scvs_mode_report r;'
+                   ' (void)o; (void)h; (void)r; return 0; }\n')
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
