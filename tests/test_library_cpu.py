@@ -2,6 +2,10 @@
 (no GPU needed; no compute call is made)."""
 import os
 import re
+import shutil
+import subprocess
+
+import pytest
 
 from paper_2009_06725_gb300 import build, scvs
 
@@ -43,10 +47,6 @@ def test_header_constants_match_binding():
 
 def test_header_is_plain_c(tmp_path):
     """include/scvs.h compiles on its own as C99 (no C++ or torch types in the ABI)."""
-    import shutil
-    import subprocess
-
-    import pytest
     gcc = shutil.which("gcc")
     if gcc is None:
         pytest.skip("no C compiler")
