@@ -527,6 +527,17 @@ def resume_from_checkpoint(ctx, mesh_id, mesh, omegas, tol, path):
     return idx
 
 
+def modes_to_keep(incr2, eps):
+    """A posteriori choice of the number of modes (Sec. 3): modes are added in
+    order while the reconstruction still changes by at least eps in relative
+    L2(Omega x T) norm; returns the count of modes kept (the first N with
+    sqrt(incr2[N]) < eps; all of them if none)."""
+    inc = np.sqrt(np.maximum(np.asarray(incr2, dtype=np.float64), 0.0))
+    small = np.flatnonzero(inc < eps)
+    small = small[small > 0]  # mode 0 alone is the whole series
+    return int(small[0]) if small.size else int(inc.size)
+
+
 def scvs_graph_aggregates(row_ptr, col, target):
     """Graph aggregates of a vertex graph given as CSR (host only).  Returns
     (agg [n] int32, n_agg, n_blk)."""

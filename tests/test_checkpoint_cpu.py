@@ -77,3 +77,14 @@ def test_write_checks_sizes(tmp_path):
     bad = scvs.scvs_ckpt_header(4, hdr.n_modes, hdr.n_nodes, hdr.n_vertices, hdr.mesh_hash, hdr.tol)
     with pytest.raises(scvs.ScvsError):
         scvs.scvs_checkpoint_write(tmp_path / "y.ckpt", bad, om, st, rr, u, p)
+
+
+def test_modes_to_keep_rule():
+    # increments of a k^-2 spectrum: delta_N^2 = E_N / sum_{k<=N} E_k
+    E = np.array([1.0] + [0.5 * k ** -4.0 for k in range(1, 10)])
+    inc = E / np.cumsum(E)
+    for eps in (1e-1, 3e-2, 1e-2):  # reached at N = 3, 5, 8
+        n = scvs.modes_to_keep(inc, eps)
+        assert np.sqrt(inc[n]) < eps and all(np.sqrt(inc[1:n]) >= eps)
+    assert scvs.modes_to_keep(inc, 1e-12) == 10  # none small enough: keep all
+    assert scvs.modes_to_keep([1.0, 0.0, 0.3], 1e-3) == 1  # a zero mode stops the series
