@@ -214,6 +214,31 @@ def p1_diagonals(mesh):
 
 # ------------------------------------------------------------ the system
 
+def p1_mass(mesh):
+    """Full P1 (vertex) mass matrix int N_A N_B over the simplices of the mesh
+    (the L2(Omega) inner product of the pressure space, Sec. 2.3), summed
+    element by element from the reference integrals."""
+    xyz, conn, dim, P = mesh["xyz"], mesh["conn"].astype(np.int64), mesh["dim"], mesh["n_vertices"]
+    vc = conn[:, :dim + 1]
+    M1, _ = p1_reference_integrals(dim)
+    _, det, _ = element_maps(xyz, vc, dim)
+    vals = det[:, None, None] * M1[None, :, :]
+    nv = dim + 1
+    rows = np.repeat(vc, nv, axis=1).ravel()
+    cols = np.tile(vc, (1, nv)).ravel()
+    return _coo_to_csr(rows, cols, vals.ravel(), (P, P))
+
+
+def block_weights(mats, mesh):
+    """L2(Omega) inner products of the two field blocks of a modal vector in
+    the solver's dof order (velocity dof = node * d + c, then the vertices):
+    W_u = M_s (x) I_d on the velocity block, W_p = the P1 mass on the pressure
+    block."""
+    d = mats["dim"]
+    Wu = spm.kron(mats["Ms"], spm.identity(d), format="csr")
+    return Wu, p1_mass(mesh)
+
+
 def dof_count(mats):
     return mats["dim"] * mats["N"] + mats["P"]
 

@@ -1,11 +1,6 @@
 """The accessor entry points no other test calls: scvs_dirichlet_count,
 scvs_modal_dev (the device block of the solution), scvs_mlp_num_params and
-scvs_guess_reset.
-
-These tests stay off until their first run on a GPU (SCVS_RUN_PENDING=1
-enables them)."""
-import os
-
+scvs_guess_reset."""
 import numpy as np
 import pytest
 
@@ -15,9 +10,7 @@ from synthetic import workloads
 from .gpu_util import solve, stack_modal
 from .test_gpu_parity import _device_view
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("SCVS_RUN_PENDING") != "1",
-                                 reason="the accessor tests await their first validation run")]
+pytestmark = pytest.mark.gpu
 
 
 def test_dirichlet_count_and_device_solution():

@@ -16,9 +16,7 @@ from synthetic import workloads
 
 from .gpu_util import solve
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("SCVS_RUN_PENDING") != "1",
-                                 reason="the warm start awaits its first validation run")]
+pytestmark = pytest.mark.gpu
 
 
 def _open(wl, omegas, g, **opts):

@@ -379,3 +379,48 @@ def test_bifurcation_generator_is_conforming_and_tagged():
     assert np.array_equal(on_b, tag != 0)
     assert (tag & meshes.INLET).any() and (tag & meshes.WALL).any()
     assert ((tag & meshes.OUTLET) != 0).sum() > 0 and (((tag & meshes.OUTLET) != 0) & ((tag & meshes.WALL) == 0)).any()
+
+
+# -------------------------------------------------- L2 norm and P1 mass
+
+def test_l2_norm_closed_forms_on_the_channel():
+    """On [0,4] x [-0.5,0.5]: ||1|| = 2, ||x||^2 = 64/3, ||x^2||^2 = 4^5/5,
+    ||(1, y)||^2 = 4 + 1/3 (P2 reproduces polynomials of degree 2 exactly and
+    M_s integrates their products exactly); relative errors scale linearly."""
+    m = meshes.channel2d(8, 4)
+    mats = fem.assemble(m)
+    x, y = m["xyz"][:, 0], m["xyz"][:, 1]
+    one = np.ones_like(x)
+    assert abs(fem.l2_norm(mats["Ms"], one) - 2.0) < 1e-13
+    assert abs(fem.l2_norm(mats["Ms"], x) - math.sqrt(64.0 / 3.0)) < 1e-12
+    assert abs(fem.l2_norm(mats["Ms"], x * x) - math.sqrt(4.0 ** 5 / 5.0)) < 1e-11
+    assert abs(fem.l2_norm(mats["Ms"], np.stack([one, y], axis=1)) - math.sqrt(4.0 + 1.0 / 3.0)) < 1e-12
+    assert abs(fem.relative_l2_error(mats["Ms"], x, 0.75 * x) - 0.25) < 1e-14
+    # complex fields: ||(1 + 2j) x|| = sqrt(5) ||x||
+    assert abs(fem.l2_norm(mats["Ms"], (1 + 2j) * x) - math.sqrt(5.0 * 64.0 / 3.0)) < 1e-11
+
+
+def test_p1_mass_closed_forms():
+    """Full P1 mass matrix: 1^T M 1 = |Omega|, x^T M 1 = int x, x^T M x = int x^2
+    (the P1 interpolant of a linear function is exact), symmetric, and the
+    element matrix |T|/12 [2 1 1; 1 2 1; 1 1 2] on a single triangle."""
+    m = meshes.channel2d(8, 4)
+    Mp = fem.p1_mass(m).toarray()
+    P = m["n_vertices"]
+    x = m["xyz"][:P, 0]
+    one = np.ones(P)
+    assert np.allclose(Mp, Mp.T, atol=0)
+    assert abs(one @ Mp @ one - 4.0) < 1e-13
+    assert abs(x @ Mp @ one - 8.0) < 1e-12
+    assert abs(x @ Mp @ x - 64.0 / 3.0) < 1e-12
+    tri = dict(xyz=np.array([[0.0, 0.0], [2.0, 0.0], [0.0, 1.0], [1.0, 0.0], [1.0, 0.5], [0.0, 0.5]]),
+               conn=np.array([[0, 1, 2, 3, 4, 5]], dtype=np.int32), dim=2, n_vertices=3)
+    ref = (1.0 / 12.0) * np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]])
+    assert np.allclose(fem.p1_mass(tri).toarray(), ref, atol=1e-15)
+    # 3D: 1^T M 1 is the discrete volume
+    pm = meshes.pipe3d(n_c=2, n_r=1, n_x=3, length=1.0, jitter=0.0)
+    M3 = fem.p1_mass(pm)
+    vol = fem.assemble(pm)["Ms"].sum()
+    assert abs(M3.sum() - vol) < 1e-12 * vol
+    Wu, Wp = fem.block_weights(fem.assemble(m), m)
+    assert Wu.shape == (2 * m["xyz"].shape[0],) * 2 and Wp.shape == (P, P)
