@@ -235,9 +235,9 @@ int scvs_reconstruct_dev(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double per
  *  - the first call on a device looks up the table's device address
  *    (cudaGetSymbolAddress) for that device; make that first call before any
  *    stream capture;
- *  - every call overwrites the whole table, so nothing carries over between
- *    calls, but calls that overlap on the GPU (e.g. on two streams) race on
- *    the table: serialise them.
+ *  - every call writes the table entries it reads, so nothing carries over
+ *    between calls, but calls that overlap on the GPU (e.g. on two streams or
+ *    from two contexts) race on the table: serialise them.
  * Output layout and accuracy are those of scvs_reconstruct_dev. */
 #define SCVS_RECON_STATIC_MAX 8192
 int scvs_reconstruct_dev_static(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
@@ -287,8 +287,27 @@ int scvs_rhs_dev(scvs_ctx *ctx, int32_t mesh_id, const void **b_dev);
  * scvs_set_modes. */
 int scvs_apply_precond(scvs_ctx *ctx, int32_t mesh_id, const void *r_dev, void *z_dev);
 
+/* Failure detection of the persistent kernels' grid barrier (no paper
+ * counterpart).  One cooperative launch of n_blocks blocks (1..SMs) in which
+ * every block except absent_block (-1: none) passes two bounded grid barriers
+ * with the given poll limit (1..2^24; the solver's kernels use 2^24, a few
+ * seconds); absent_block returns without arriving, so the other blocks' wait
+ * runs out: they record the time-out in the barrier's error word and return
+ * instead of hanging.  Returns SCVS_OK if every barrier completed,
+ * SCVS_ERR_TIMEOUT if a wait ran out (the barrier state is then reset, and the
+ * context stays usable); *blocks_passed (may be NULL) = blocks that passed
+ * both barriers.  Synchronises the context's stream. */
+int scvs_barrier_selftest(scvs_ctx *ctx, int64_t spin_limit, int32_t n_blocks, int32_t absent_block,
+                          int32_t *blocks_passed);
+
 /* Number of kernel launches issued by this context since creation. */
 int64_t scvs_launch_count(const scvs_ctx *ctx);
+/* Device memory of the context's stream-ordered pool (every mesh, mode set and
+ * Krylov workspace is taken from it), after synchronising the context's stream:
+ * bytes in use, the high-water mark of bytes in use, and bytes reserved
+ * (mapped; freed blocks stay reserved for reuse).  reset_high != 0 then
+ * resets the high-water mark to the current use.  Any output may be NULL. */
+int scvs_pool_usage(scvs_ctx *ctx, int32_t reset_high, int64_t *used, int64_t *used_high, int64_t *reserved);
 
 /* ---- learned initial guess ----------------------------------------------
  * The modes of one geometry family share a node set; a converged mode x_k
@@ -300,7 +319,21 @@ int64_t scvs_launch_count(const scvs_ctx *ctx);
  * set for a mesh, scvs_solve starts every mode from x0 = c_k Phi a(f) (and g
  * on the Dirichlet rows); a mode whose x0 has a residual >= ||b|| starts from
  * zero instead.  The paper solves every mode from scratch; this is an
- * addition. features: host double [n_modes][5]. */
+ * addition. features: host double [n_modes][5].
+ *
+ * POD: per field block (velocity rows, pressure rows) in the block's L2(Omega)
+ * inner product <x, y> = x^H W y, W = M_s per velocity component and the P1
+ * mass for the pressure, both of the mesh that gave the first snapshot (the
+ * reference geometry; every snapshot shares its connectivity).  The Gram
+ * matrix of the first max_pod_snapshots snapshots is formed on the GPU (FP32
+ * data, FP64 accumulation), its eigenpairs on the host (FP64 Jacobi); every
+ * eigenvector is scaled by a unit complex number that makes its
+ * largest-magnitude entry real positive (this fixes each basis vector's
+ * phase), Phi = X V Lambda^{-1/2} (Phi^H W Phi = I, stored FP32) with rank
+ * r = min(n_pod, #eigenvalues > 1e-10 lambda_1), the same in both blocks;
+ * the training targets are a_s = Phi^H W x_s.  Features and targets are
+ * standardised by their means and population deviations (a deviation
+ * below 1e-12 counts as 1). */
 void scvs_default_train_opts(scvs_train_opts *opts);
 /* Append the converged modes of a solved mesh to the training set. */
 int scvs_guess_add_snapshots(scvs_ctx *ctx, int32_t mesh_id, const double *features);
@@ -312,12 +345,32 @@ int scvs_guess_set_features(scvs_ctx *ctx, int32_t mesh_id, const double *featur
 int scvs_guess_info(scvs_ctx *ctx, int64_t *n_snapshots, int32_t *n_pod, int32_t *trained);
 /* Drop snapshots and model. */
 int scvs_guess_reset(scvs_ctx *ctx);
+/* POD basis of a trained model: block 0 velocity (n_rows = dim N, row = node *
+ * dim + component), 1 pressure (n_rows = P); phi host [n_rows][n_pod].
+ * SCVS_ERR_STATE without a trained model, SCVS_ERR_ARG on a size mismatch. */
+int scvs_guess_basis(scvs_ctx *ctx, int32_t block, int64_t n_rows, int32_t n_pod, scvs_c64 *phi);
+/* POD coefficients a_s = Phi^H W x_s of every training snapshot (the training
+ * targets before standardisation): a host [n_snapshots][n_pod]. */
+int scvs_guess_coefficients(scvs_ctx *ctx, int32_t block, int64_t n_snapshots, int32_t n_pod, scvs_c64 *a);
+/* The learned start of every mode of the mesh, without solving (features
+ * set, model trained): x0 = c_k [Phi_u a_u; Phi_p a_p] with g on the
+ * Dirichlet rows, its FP64 relative residual res0[k] = ||b - A x0|| / ||b||
+ * (host [n_modes]) and kept[k] = 1 if scvs_solve with SCVS_GUESS_MLP would
+ * start mode k from it (res0 < 1; otherwise that mode starts from zero).  x0,
+ * kept or not, becomes the mesh's held solution (scvs_get_modal reads it).
+ * SCVS_ERR_STATE if the model cannot serve the mesh (untrained, another node
+ * set, no features, several components). */
+int scvs_guess_initial(scvs_ctx *ctx, int32_t mesh_id, int64_t n_modes, double *res0, int32_t *kept);
 
 /* Raw MLP (no feature/target scaling), for gradient checks and checkpoints.
  * Parameters are one flat FP32 array: for layer l = 0..3, W_l [in][out]
  * row-major then b_l [out], sizes n_in -> hidden -> hidden -> hidden -> n_out.
  * The kernels use the BF16 rounding of W and b and accumulate in FP32. */
 int scvs_mlp_init(scvs_ctx *ctx, int32_t n_in, int32_t hidden, int32_t n_out, const float *params);
+/* Overwrite the weights of the current MLP (same flat layout and size as
+ * scvs_mlp_init) and keep everything else: a trained model keeps its POD
+ * bases and standardisation.  SCVS_ERR_STATE without an MLP. */
+int scvs_mlp_set_params(scvs_ctx *ctx, const float *params);
 int scvs_mlp_num_params(scvs_ctx *ctx, int64_t *n);
 int scvs_mlp_get_params(scvs_ctx *ctx, float *params);
 /* y_dev[B][n_out] = MLP(x_dev[B][n_in]) (device pointers). */
@@ -416,6 +469,17 @@ int scvs_bc_spectrum(scvs_ctx *ctx, int32_t n_t, int64_t n_pts, int32_t n_modes,
  * reductions.  Runs on the context's stream and synchronises it.  Returns
  * SCVS_ERR_STATE before scvs_solve, SCVS_ERR_ARG for a bad id or size. */
 int scvs_mode_energies(scvs_ctx *ctx, int32_t mesh_id, int64_t n_out, double *E, double *incr2);
+
+/* A posteriori number of modes (Sec. 3, the remark after step 4: after each
+ * mode, compare the reconstructions with N - 1 and N modes and go on while the
+ * difference exceeds a tolerance).  incr2[0..n): the squared relative changes
+ * of scvs_mode_energies for one system, modes in order.  *n_keep = the
+ * smallest N >= 1 such that the changes of modes N, N+1, ..., N+patience-1 all
+ * exist and are below eps (their square root); n if there is none.  patience
+ * = 1 is the literal rule; a larger patience keeps going across a missing
+ * harmonic (a zero change followed by energetic modes).  Host only.
+ * SCVS_ERR_ARG if n < 1, patience < 1, eps <= 0 or a pointer is NULL. */
+int scvs_modes_to_keep(const double *incr2, int64_t n, double eps, int32_t patience, int64_t *n_keep);
 
 /* ---- checkpoint / resume --------------------------------------------------
  * Every mode is an independent problem, so the modal solution is the

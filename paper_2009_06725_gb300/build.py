@@ -63,7 +63,7 @@ def build(force=False, verbose_ptxas=False, jobs=None):
             objs.append(o)
             logs.append(log)
     tmp = OUT + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-lcublas"]
+    cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

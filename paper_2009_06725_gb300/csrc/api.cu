@@ -690,6 +690,24 @@ int scvs_apply_precond(scvs_ctx *c, int32_t mesh_id, const void *r, void *z) {
 
 int64_t scvs_launch_count(const scvs_ctx *c) { return c ? c->launches.n : -1; }
 
+int scvs_pool_usage(scvs_ctx *c, int32_t reset_high, int64_t *used, int64_t *used_high, int64_t *reserved) {
+  return guarded(c, [&]() {
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    unsigned long long u = 0, h = 0, r = 0;  // the runtime reports these attributes as 64-bit counts
+    SCVS_CUDA(cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    SCVS_CUDA(cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemHigh, &h));
+    SCVS_CUDA(cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    if (used) *used = (int64_t)u;
+    if (used_high) *used_high = (int64_t)h;
+    if (reserved) *reserved = (int64_t)r;
+    if (reset_high) {
+      unsigned long long z = 0;
+      SCVS_CUDA(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrUsedMemHigh, &z));
+    }
+    return SCVS_OK;
+  });
+}
+
 void scvs_default_train_opts(scvs_train_opts *o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
@@ -761,6 +779,59 @@ int scvs_mlp_init(scvs_ctx *c, int32_t n_in, int32_t hidden, int32_t n_out, cons
     SCVS_CUDA(cudaMemcpy(g.Wf, params, g.n_params * sizeof(float), cudaMemcpyHostToDevice));
     mlp_refresh_bf16(*c, g);
     SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    return SCVS_OK;
+  });
+}
+
+int scvs_mlp_set_params(scvs_ctx *c, const float *params) {
+  return guarded(c, [&]() {
+    GuessModel &g = c->guess;
+    if (!params) return fail(c, SCVS_ERR_ARG, "null parameters");
+    if (g.n_params == 0) return fail(c, SCVS_ERR_STATE, "no MLP (scvs_mlp_init or scvs_train_guess first)");
+    SCVS_CUDA(cudaMemcpy(g.Wf, params, g.n_params * sizeof(float), cudaMemcpyHostToDevice));
+    mlp_refresh_bf16(*c, g);
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
+    return SCVS_OK;
+  });
+}
+
+int scvs_guess_basis(scvs_ctx *c, int32_t block, int64_t n_rows, int32_t n_pod, scvs_c64 *phi) {
+  return guarded(c, [&]() {
+    GuessModel &g = c->guess;
+    if (!g.trained || !g.Phi_u) return fail(c, SCVS_ERR_STATE, "no trained guess");
+    if (block != 0 && block != 1) return fail(c, SCVS_ERR_ARG, "block must be 0 (velocity) or 1 (pressure)");
+    const int64_t nr = block == 0 ? g.n_u : g.n_dof - g.n_u;
+    if (!phi || n_rows != nr || n_pod != g.n_pod) return fail(c, SCVS_ERR_ARG, "basis size mismatch");
+    std::vector<float2> h((size_t)nr * g.n_pod);
+    SCVS_CUDA(cudaMemcpy(h.data(), block == 0 ? g.Phi_u : g.Phi_p, h.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < h.size(); ++i) phi[i] = scvs_c64{h[i].x, h[i].y};
+    return SCVS_OK;
+  });
+}
+
+int scvs_guess_coefficients(scvs_ctx *c, int32_t block, int64_t n_snap, int32_t n_pod, scvs_c64 *a) {
+  return guarded(c, [&]() {
+    GuessModel &g = c->guess;
+    if (!g.trained || g.coef_u.empty()) return fail(c, SCVS_ERR_STATE, "no trained guess");
+    if (block != 0 && block != 1) return fail(c, SCVS_ERR_ARG, "block must be 0 (velocity) or 1 (pressure)");
+    if (!a || n_snap != g.n_snap || n_pod != g.n_pod) return fail(c, SCVS_ERR_ARG, "coefficient size mismatch");
+    const auto &src = block == 0 ? g.coef_u : g.coef_p;
+    for (size_t i = 0; i < src.size(); ++i) a[i] = scvs_c64{src[i].real(), src[i].imag()};
+    return SCVS_OK;
+  });
+}
+
+int scvs_guess_initial(scvs_ctx *c, int32_t mesh_id, int64_t n_modes, double *res0, int32_t *kept) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
+    if (!res0 || !kept || n_modes != m->m) return fail(c, SCVS_ERR_ARG, "res0/kept must hold one entry per mode");
+    std::vector<int> k(m->m, 0);
+    if (!guess_probe(*c, *m, res0, k.data()))
+      return fail(c, SCVS_ERR_STATE,
+                  "the learned guess cannot serve this mesh (untrained model, another node set, no features, or "
+                  "several components)");
+    for (int i = 0; i < m->m; ++i) kept[i] = k[i];
     return SCVS_OK;
   });
 }
@@ -877,6 +948,31 @@ static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
 }
 static const uint64_t FNV_OFFSET = 14695981039346656037ULL;
 static const char CKPT_MAGIC[8] = {'S', 'C', 'V', 'S', 'C', 'K', 'P', '1'};
+
+int scvs_barrier_selftest(scvs_ctx *c, int64_t spin_limit, int32_t n_blocks, int32_t absent_block,
+                          int32_t *blocks_passed) {
+  return guarded(c, [&]() {
+    if (spin_limit < 1 || spin_limit > SPIN_LIMIT || n_blocks < 1 || n_blocks > c->num_sms ||
+        absent_block < -1 || absent_block >= n_blocks)
+      return fail(c, SCVS_ERR_ARG, "spin_limit in [1, 2^24], 1 <= n_blocks <= SMs, -1 <= absent_block < n_blocks");
+    int passed = 0;
+    const int r = barrier_selftest(*c, (long long)spin_limit, n_blocks, absent_block, &passed);
+    if (blocks_passed) *blocks_passed = passed;
+    if (r == SCVS_ERR_TIMEOUT) return fail(c, r, "a device grid barrier timed out (self-test)");
+    return r;
+  });
+}
+
+int scvs_modes_to_keep(const double *incr2, int64_t n, double eps, int32_t patience, int64_t *n_keep) {
+  if (!incr2 || !n_keep || n < 1 || patience < 1 || !(eps > 0)) return SCVS_ERR_ARG;
+  *n_keep = n;
+  for (int64_t N = 1; N + patience <= n; ++N) {
+    bool small = true;
+    for (int32_t q = 0; q < patience && small; ++q) small = std::sqrt(std::max(incr2[N + q], 0.0)) < eps;
+    if (small) { *n_keep = N; break; }
+  }
+  return SCVS_OK;
+}
 
 int scvs_mesh_hash(int32_t dim, int64_t N, int64_t P, const double *xyz, int64_t E, const int32_t *conn,
                    const uint8_t *tag, uint64_t *hash) {

@@ -43,8 +43,8 @@ template <typename T> __host__ __device__ __forceinline__ typename cpx<T>::t mk(
 // ----------------------------------------------------------- grid barrier
 // Bounded sense-counting barrier for cooperative launches: every block of the
 // grid must be resident (the host launches with cudaLaunchCooperativeKernel).
-// A block that waits more than SPIN_LIMIT polls sets the error word and
-// returns false; every caller then exits the kernel.
+// A block that waits more than spin_limit polls (default SPIN_LIMIT) sets the
+// error word and returns false; every caller then exits the kernel.
 struct GridSync {
   unsigned int count;
   unsigned int gen;
@@ -55,7 +55,7 @@ struct GridSync {
 constexpr long long SPIN_LIMIT = 1ll << 24;  // ~2-4 s with the back-off below
 
 #ifdef __CUDACC__
-__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned int nblocks, long long spin_limit = SPIN_LIMIT) {
   __shared__ int s_ok;
   __threadfence();
   __syncthreads();
@@ -74,7 +74,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned int nblocks) {
       long long spins = 0;
       while (*vgen == g) {
         if (*verr) { ok = 0; break; }
-        if (++spins > SPIN_LIMIT) { atomicExch(&gs->err, 1); ok = 0; break; }
+        if (++spins > spin_limit) { atomicExch(&gs->err, 1); ok = 0; break; }
         if (spins > 4096) __nanosleep(100);  // poll tightly first: most waits are a few microseconds
       }
     }

@@ -4,30 +4,26 @@
 // mode's boundary coefficient c_k (the problem is linear in c_k), stored as
 // complex FP32 columns of length n_dof together with the mode features
 // f = (omega_k, Re c_k, Im c_k, R, s).
-// POD (method of snapshots, per field block u / p): Gram matrix X^H X by a
-// complex GEMM, its leading eigenpairs on the host (cyclic Jacobi), basis
-// Phi = X V Lambda^{-1/2}; training targets a = Phi^H x.
+// POD (method of snapshots, per field block u / p) in the block's L2(Omega)
+// inner product: Gram matrix X^H W X (W the reference mesh's mass matrix of the
+// block) by the project's own FP64-accumulating Gram kernel, its leading
+// eigenpairs on the host (cyclic Jacobi), basis Phi = X V Lambda^{-1/2} with a
+// fixed phase per vector; training targets a = Phi^H W x.
 // MLP 5 -> H -> H -> H -> 4 n_pod with exact GELU on the hidden layers; the
 // weights used by the forward/backward kernels are BF16 (FP32 master copies
 // updated by Adam), every product is accumulated in FP32.
 // Inference: x0 = c_k [Phi_u a_u; Phi_p a_p] on the free rows, g on the
 // Dirichlet rows.
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <random>
+#include <type_traits>
 #include <vector>
 #include "scvs_internal.h"
 
 namespace scvs {
-
-#define SCVS_CUBLAS(call)                                                                \
-  do {                                                                                  \
-    cublasStatus_t _s = (call);                                                         \
-    if (_s != CUBLAS_STATUS_SUCCESS) throw CudaError{cudaErrorUnknown, std::string(#call) + " (cuBLAS)"}; \
-  } while (0)
 
 // ------------------------------------------------------------ MLP kernels
 constexpr int MLP_TB = 16;  // samples per block
@@ -369,6 +365,20 @@ void guess_add_snapshots(Ctx &c, Mesh &m, const double *features) {
   if (g.n_dof == 0) {
     g.n_dof = m.n_dof;
     g.n_u = (int64_t)m.dim * m.N;
+    // the first mesh's mass matrices define the POD inner products
+    GuessModel::RefMass &w = g.wref;
+    w.dim = m.dim; w.N = m.N; w.P = m.P;
+    auto dup = [&](auto *&dst, const auto *src, int64_t n) {
+      using E = std::remove_cv_t<std::remove_pointer_t<std::remove_reference_t<decltype(dst)>>>;
+      SCVS_CUDA(cudaMalloc(&dst, (size_t)std::max<int64_t>(n, 1) * sizeof(E)));
+      SCVS_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * sizeof(E), cudaMemcpyDeviceToDevice, c.stream));
+    };
+    dup(w.s_ptr, m.s_ptr, m.N + 1);
+    dup(w.g_ptr, m.g_ptr, m.N + 1);
+    dup(w.s_col, m.s_col, m.s_nnz);
+    dup(w.g_len, m.g_len, m.N);
+    dup(w.Ms, m.Ms, m.s_nnz);
+    dup(w.Mp, m.Mp, m.q_nnz);
   } else if (g.n_dof != m.n_dof || g.n_u != (int64_t)m.dim * m.N) {
     throw (int)SCVS_ERR_ARG;  // snapshots must share the node set
   }
@@ -398,27 +408,216 @@ void guess_add_snapshots(Ctx &c, Mesh &m, const double *features) {
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
 }
 
-// POD of one block (rows [r0, r0 + nr) of the snapshots) -> Phi [nr][n_pod]
-// row-major complex FP32; also the coefficients a [n_snap][n_pod].
-static void pod_block(Ctx &c, GuessModel &g, cublasHandle_t h, int64_t r0, int64_t nr, int n_pod_req, int n_basis,
-                      float2 **Phi_out, std::vector<std::complex<float>> &coef, int &n_pod_out) {
+// ---------------------------------------------------------------- POD
+// Mass weighting of snapshot-layout vectors of one field block: y_s = W x_s for
+// s < ns, with W = M_s (x) I_d on the velocity block and the P1 mass on the
+// pressure block, both of the reference mesh (the one that gave the first
+// snapshot; morphs share its connectivity).  x_s at x + s * ldx, block row i
+// at x_s[i]; FP64 accumulation of FP32 inputs, FP32 result.
+__global__ void k_pod_weight_u(const GuessModel::RefMass w, const float2 *__restrict__ x, int64_t ldx, int ns,
+                               float2 *__restrict__ y, int64_t ldy) {
+  const int64_t n_u = (int64_t)w.dim * w.N;
+  const int64_t t = blockIdx.x * 256ll + threadIdx.x;
+  const int s = blockIdx.y;
+  if (t >= n_u || s >= ns) return;
+  const int64_t A = t / w.dim;
+  const int c = (int)(t % w.dim);
+  const float2 *xs = x + (int64_t)s * ldx;
+  double re = 0.0, im = 0.0;
+  for (int64_t q = w.s_ptr[A]; q < w.s_ptr[A + 1]; ++q) {
+    const double mv = w.Ms[q];
+    const float2 v = xs[(int64_t)w.s_col[q] * w.dim + c];
+    re = fma(mv, (double)v.x, re);
+    im = fma(mv, (double)v.y, im);
+  }
+  y[(int64_t)s * ldy + t] = make_float2((float)re, (float)im);
+}
+
+__global__ void k_pod_weight_p(const GuessModel::RefMass w, const float2 *__restrict__ x, int64_t ldx, int ns,
+                               float2 *__restrict__ y, int64_t ldy) {
+  const int64_t v = blockIdx.x * 256ll + threadIdx.x;
+  const int s = blockIdx.y;
+  if (v >= w.P || s >= ns) return;
+  const float2 *xs = x + (int64_t)s * ldx;
+  const int64_t q0 = w.g_ptr[v], c0 = w.s_ptr[v];
+  double re = 0.0, im = 0.0;
+  for (int t = 0; t < w.g_len[v]; ++t) {
+    const double mv = w.Mp[q0 + t];
+    const float2 e = xs[w.s_col[c0 + t]];
+    re = fma(mv, (double)e.x, re);
+    im = fma(mv, (double)e.y, im);
+  }
+  y[(int64_t)s * ldy + v] = make_float2((float)re, (float)im);
+}
+
+// Complex Gram products with FP64 accumulation of FP32 inputs:
+// part[kc][i][j] = sum over rows r of chunk kc of conj(A_i[r]) B_j[r], with
+// A_i at A + i * lda and B_j at B + j * ldb (i < na, j < nb, r < rows).  One
+// 32 x 32 output tile per block of 256 threads (2 x 2 outputs per thread),
+// rows staged 32 at a time in shared memory.
+constexpr int GT = 32;
+__global__ void __launch_bounds__(256) k_cgram(const float2 *__restrict__ A, int64_t lda, int na,
+                                               const float2 *__restrict__ B, int64_t ldb, int nb, int64_t rows,
+                                               int64_t chunk, double2 *__restrict__ part) {
+  __shared__ float2 As[GT][GT + 1], Bs[GT][GT + 1];
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  const int64_t r_begin = (int64_t)blockIdx.z * chunk, r_end = min(rows, r_begin + chunk);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2][2] = {};
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += GT) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = threadIdx.x + 256 * q;
+      const int a = idx / GT, rr = idx % GT;
+      const int64_t r = r0 + rr;
+      const bool in_r = r < r_end;
+      As[rr][a] = (in_r && i0 + a < na) ? A[(int64_t)(i0 + a) * lda + r] : make_float2(0.f, 0.f);
+      Bs[rr][a] = (in_r && j0 + a < nb) ? B[(int64_t)(j0 + a) * ldb + r] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < GT; ++rr) {
+      const float2 a0 = As[rr][2 * ty], a1 = As[rr][2 * ty + 1];
+      const float2 b0 = Bs[rr][2 * tx], b1 = Bs[rr][2 * tx + 1];
+      const float2 av[2] = {a0, a1}, bv[2] = {b0, b1};
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          const double ar = av[u].x, ai = av[u].y, br = bv[v].x, bi = bv[v].y;
+          acc[u][v][0] = fma(ar, br, fma(ai, bi, acc[u][v][0]));
+          acc[u][v][1] = fma(ar, bi, fma(-ai, br, acc[u][v][1]));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = i0 + 2 * ty + u, j = j0 + 2 * tx + v;
+      if (i < na && j < nb)
+        part[((int64_t)blockIdx.z * na + i) * nb + j] = make_double2(acc[u][v][0], acc[u][v][1]);
+    }
+}
+
+// out[i][j] = sum_kc part[kc][i][j], chunks in order.
+__global__ void k_cgram_sum(const double2 *__restrict__ part, int nkc, int64_t n, double2 *__restrict__ out) {
+  const int64_t t = blockIdx.x * 256ll + threadIdx.x;
+  if (t >= n) return;
+  double re = 0.0, im = 0.0;
+  for (int k = 0; k < nkc; ++k) {
+    const double2 v = part[(int64_t)k * n + t];
+    re += v.x;
+    im += v.y;
+  }
+  out[t] = make_double2(re, im);
+}
+
+// Phi[i][j] = sum_{s < ns} X_s[i] Wm[s][j] (rows i < nr of the block, j < r),
+// FP64 accumulation; writes Phi row-major [nr][r] and transposed Phit [r][nr].
+// Block: 256 rows x 16 columns (grid.y tiles the columns); Wm staged 32
+// snapshots at a time.
+__global__ void __launch_bounds__(256) k_pod_basis(const float2 *__restrict__ X, int64_t ldx, int ns, int64_t nr,
+                                                   const double2 *__restrict__ Wm, int r, float2 *__restrict__ Phi,
+                                                   float2 *__restrict__ Phit) {
+  __shared__ double2 ws[32][16];
+  const int64_t i = blockIdx.x * 256ll + threadIdx.x;
+  const int j0 = blockIdx.y * 16;
+  double acc[16][2] = {};
+  for (int s0 = 0; s0 < ns; s0 += 32) {
+    for (int t = threadIdx.x; t < 32 * 16; t += 256) {
+      const int ss = t / 16, jj = t % 16;
+      ws[ss][jj] = (s0 + ss < ns && j0 + jj < r) ? Wm[(int64_t)(s0 + ss) * r + j0 + jj] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (i < nr) {
+      const int sn = min(32, ns - s0);
+      for (int ss = 0; ss < sn; ++ss) {
+        const float2 xv = X[(int64_t)(s0 + ss) * ldx + i];
+        const double xr = xv.x, xi = xv.y;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const double2 w = ws[ss][jj];
+          acc[jj][0] = fma(xr, w.x, fma(-xi, w.y, acc[jj][0]));
+          acc[jj][1] = fma(xr, w.y, fma(xi, w.x, acc[jj][1]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (i >= nr) return;
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) {
+    const int j = j0 + jj;
+    if (j >= r) break;
+    const float2 v = make_float2((float)acc[jj][0], (float)acc[jj][1]);
+    Phi[i * r + j] = v;
+    Phit[(int64_t)j * nr + i] = v;
+  }
+}
+
+// Gram products conj(A)^T B of snapshot-layout operands over `rows` rows, on
+// the device: returns out [na][nb] (device, FP64 complex, from the pool).
+static double2 *cgram(Ctx &c, const float2 *A, int64_t lda, int na, const float2 *B, int64_t ldb, int nb,
+                      int64_t rows) {
+  const int ti = (int)ceil_div(na, GT), tj = (int)ceil_div(nb, GT);
+  const int64_t want = std::max<int64_t>(1, (4 * (int64_t)c.num_sms + ti * tj - 1) / ((int64_t)ti * tj));
+  const int64_t chunk = std::max<int64_t>(GT, ceil_div(ceil_div(rows, want), GT) * GT);
+  const int nkc = (int)ceil_div(rows, chunk);
+  const int64_t n = (int64_t)na * nb;
+  double2 *part = nullptr, *out = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &part, (size_t)nkc * n * sizeof(double2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &out, (size_t)n * sizeof(double2), c.stream));
+  k_cgram<<<dim3(tj, ti, nkc), 256, 0, c.stream>>>(A, lda, na, B, ldb, nb, rows, chunk, part);
+  count_launch(c);
+  k_cgram_sum<<<(unsigned)ceil_div(n, 256), 256, 0, c.stream>>>(part, nkc, n, out);
+  count_launch(c);
+  SCVS_CUDA(cudaFreeAsync(part, c.stream));
+  return out;
+}
+
+// y_s = W x_s (s < ns) for the field block `blk` (0: velocity, 1: pressure).
+static void pod_weight(Ctx &c, const GuessModel &g, int blk, const float2 *x, int64_t ldx, int ns, float2 *y,
+                       int64_t ldy) {
+  const int64_t nr = blk == 0 ? g.n_u : g.n_dof - g.n_u;
+  for (int s0 = 0; s0 < ns; s0 += 65535) {
+    const int sn = std::min(65535, ns - s0);
+    dim3 grid((unsigned)ceil_div(nr, 256), (unsigned)sn);
+    if (blk == 0)
+      k_pod_weight_u<<<grid, 256, 0, c.stream>>>(g.wref, x + (int64_t)s0 * ldx, ldx, sn, y + (int64_t)s0 * ldy, ldy);
+    else
+      k_pod_weight_p<<<grid, 256, 0, c.stream>>>(g.wref, x + (int64_t)s0 * ldx, ldx, sn, y + (int64_t)s0 * ldy, ldy);
+    count_launch(c);
+  }
+}
+
+// POD of one field block (rows [r0, r0 + nr) of the snapshots) in the block's
+// L2(Omega) inner product: G = X_b^H W X_b over the first n_basis snapshots,
+// its eigenpairs (host cyclic Jacobi, FP64), every eigenvector's phase fixed
+// so that its largest-magnitude entry is real positive, Phi = X_b V_r
+// Lambda_r^{-1/2} (W-orthonormal), and the coefficients a_s = Phi^H W x_s of
+// every snapshot.  Phi is row-major [nr][r] on the device; coef is [n_snap][r].
+static void pod_block(Ctx &c, GuessModel &g, int blk, int n_pod_req, int n_basis, float2 **Phi_out,
+                      std::vector<std::complex<double>> &coef, std::vector<double> &lam_out, int &n_pod_out) {
+  const int64_t r0 = blk == 0 ? 0 : g.n_u, nr = blk == 0 ? g.n_u : g.n_dof - g.n_u;
   const int S = (int)g.n_snap, Sb = std::min<int>(S, n_basis);
-  const cuComplex one = make_cuComplex(1, 0), zero = make_cuComplex(0, 0);
-  const cuComplex *X = reinterpret_cast<const cuComplex *>(g.snap + r0);  // column-major nr x S, lda = n_dof
-  cuComplex *G = nullptr;
-  SCVS_CUDA(cudaMalloc(&G, (size_t)Sb * Sb * sizeof(cuComplex)));
-  SCVS_CUBLAS(cublasCgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, Sb, Sb, (int)nr, &one, X, (int)g.n_dof, X, (int)g.n_dof, &zero,
-                          G, Sb));
-  std::vector<std::complex<float>> hg((size_t)Sb * Sb);
-  SCVS_CUDA(cudaMemcpyAsync(hg.data(), G, hg.size() * sizeof(cuComplex), cudaMemcpyDeviceToHost, c.stream));
+  const float2 *X = g.snap + r0;  // snapshot s, block row i at X[s * n_dof + i]
+  float2 *WX = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &WX, (size_t)Sb * nr * sizeof(float2), c.stream));
+  pod_weight(c, g, blk, X, g.n_dof, Sb, WX, nr);
+  double2 *Gd = cgram(c, X, g.n_dof, Sb, WX, nr, Sb, nr);  // G[i][j] = x_i^H W x_j
+  std::vector<double2> hg((size_t)Sb * Sb);
+  SCVS_CUDA(cudaMemcpyAsync(hg.data(), Gd, hg.size() * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(Gd, c.stream));
+  SCVS_CUDA(cudaFreeAsync(WX, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
-  std::vector<std::complex<double>> A(hg.size());
-  for (size_t i = 0; i < hg.size(); ++i) A[i] = std::complex<double>(hg[i].real(), hg[i].imag());
-  for (int i = 0; i < Sb; ++i)  // exact Hermitian symmetry
-    for (int j = i + 1; j < Sb; ++j) {
-      const auto v = 0.5 * (A[(size_t)j * Sb + i] + std::conj(A[(size_t)i * Sb + j]));
-      A[(size_t)j * Sb + i] = v;
-      A[(size_t)i * Sb + j] = std::conj(v);
+  // column-major Hermitian matrix for the eigensolver, made exactly Hermitian
+  std::vector<std::complex<double>> A((size_t)Sb * Sb);
+  for (int i = 0; i < Sb; ++i)
+    for (int j = 0; j < Sb; ++j) {
+      const double2 a = hg[(size_t)i * Sb + j], b = hg[(size_t)j * Sb + i];
+      A[(size_t)j * Sb + i] = 0.5 * (std::complex<double>(a.x, a.y) + std::conj(std::complex<double>(b.x, b.y)));
     }
   std::vector<double> lam;
   std::vector<std::complex<double>> V;
@@ -426,93 +625,83 @@ static void pod_block(Ctx &c, GuessModel &g, cublasHandle_t h, int64_t r0, int64
   int r = 0;
   while (r < std::min(n_pod_req, Sb) && lam[r] > 1e-10 * lam[0]) ++r;
   n_pod_out = r;
-  // W = V_r Lambda_r^{-1/2}  (Sb x r), Phi = X_b W  (nr x r, column-major)
-  std::vector<cuComplex> Wh((size_t)Sb * r);
-  for (int j = 0; j < r; ++j)
+  lam_out = lam;
+  // Wm = V_r Lambda_r^{-1/2} with each column's phase fixed, [Sb][r] row-major
+  std::vector<double2> Wm((size_t)Sb * r);
+  for (int j = 0; j < r; ++j) {
+    const std::complex<double> *vj = V.data() + (size_t)j * Sb;
+    int imax = 0;
+    for (int i = 1; i < Sb; ++i)
+      if (std::abs(vj[i]) > std::abs(vj[imax])) imax = i;
+    const std::complex<double> ph = std::conj(vj[imax]) / std::abs(vj[imax]);
+    const double sc = 1.0 / std::sqrt(lam[j]);
     for (int i = 0; i < Sb; ++i) {
-      const auto v = V[(size_t)j * Sb + i] / std::sqrt(lam[j]);
-      Wh[(size_t)j * Sb + i] = make_cuComplex((float)v.real(), (float)v.imag());
+      const std::complex<double> v = vj[i] * ph * sc;
+      Wm[(size_t)i * r + j] = make_double2(v.real(), v.imag());
     }
-  cuComplex *Wd = nullptr, *Pc = nullptr, *Cd = nullptr;
-  SCVS_CUDA(cudaMalloc(&Wd, Wh.size() * sizeof(cuComplex)));
-  SCVS_CUDA(cudaMalloc(&Pc, (size_t)nr * r * sizeof(cuComplex)));
-  SCVS_CUDA(cudaMalloc(&Cd, (size_t)r * S * sizeof(cuComplex)));
-  SCVS_CUDA(cudaMemcpyAsync(Wd, Wh.data(), Wh.size() * sizeof(cuComplex), cudaMemcpyHostToDevice, c.stream));
-  SCVS_CUBLAS(cublasCgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, (int)nr, r, Sb, &one, X, (int)g.n_dof, Wd, Sb, &zero, Pc, (int)nr));
-  // coefficients of every snapshot: C = Phi^H X  (r x S)
-  SCVS_CUBLAS(cublasCgemm(h, CUBLAS_OP_C, CUBLAS_OP_N, r, S, (int)nr, &one, Pc, (int)nr, X, (int)g.n_dof, &zero, Cd, r));
-  coef.resize((size_t)r * S);
-  SCVS_CUDA(cudaMemcpyAsync(coef.data(), Cd, coef.size() * sizeof(cuComplex), cudaMemcpyDeviceToHost, c.stream));
-  // Phi stored row-major [nr][r] for the expansion kernel: transpose via GEMM-free copy on host
-  std::vector<cuComplex> pc((size_t)nr * r), pr((size_t)nr * r);
-  SCVS_CUDA(cudaMemcpyAsync(pc.data(), Pc, pc.size() * sizeof(cuComplex), cudaMemcpyDeviceToHost, c.stream));
+  }
+  double2 *Wmd = nullptr;
+  float2 *Phi = nullptr, *Phit = nullptr, *WPhit = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &Wmd, Wm.size() * sizeof(double2), c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(Wmd, Wm.data(), Wm.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMalloc(&Phi, (size_t)nr * r * sizeof(float2)));
+  SCVS_CUDA(ctx_malloc(c, &Phit, (size_t)nr * r * sizeof(float2), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &WPhit, (size_t)nr * r * sizeof(float2), c.stream));
+  k_pod_basis<<<dim3((unsigned)ceil_div(nr, 256), (unsigned)ceil_div(r, 16)), 256, 0, c.stream>>>(X, g.n_dof, Sb, nr,
+                                                                                                 Wmd, r, Phi, Phit);
+  count_launch(c);
+  // coefficients: C[j][s] = (W phi_j)^H x_s = phi_j^H W x_s (W is real symmetric)
+  pod_weight(c, g, blk, Phit, nr, r, WPhit, nr);
+  double2 *Cd = cgram(c, WPhit, nr, r, X, g.n_dof, S, nr);
+  std::vector<double2> hc((size_t)r * S);
+  SCVS_CUDA(cudaMemcpyAsync(hc.data(), Cd, hc.size() * sizeof(double2), cudaMemcpyDeviceToHost, c.stream));
+  for (void *p : {(void *)Wmd, (void *)Phit, (void *)WPhit, (void *)Cd}) SCVS_CUDA(cudaFreeAsync(p, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
-  for (int j = 0; j < r; ++j)
-    for (int64_t i = 0; i < nr; ++i) pr[(size_t)i * r + j] = pc[(size_t)j * nr + i];
-  float2 *Phi = nullptr;
-  SCVS_CUDA(cudaMalloc(&Phi, pr.size() * sizeof(float2)));
-  SCVS_CUDA(cudaMemcpyAsync(Phi, pr.data(), pr.size() * sizeof(float2), cudaMemcpyHostToDevice, c.stream));
-  SCVS_CUDA(cudaStreamSynchronize(c.stream));
-  cudaFree(G); cudaFree(Wd); cudaFree(Pc); cudaFree(Cd);
+  coef.resize((size_t)S * r);
+  for (int s = 0; s < S; ++s)
+    for (int j = 0; j < r; ++j) coef[(size_t)s * r + j] = std::complex<double>(hc[(size_t)j * S + s].x, hc[(size_t)j * S + s].y);
   *Phi_out = Phi;
+}
+
+// Keep the first r columns of a row-major [n][r_old] device basis and of the
+// [S][r_old] coefficients.
+static void truncate_basis(Ctx &c, float2 *&Phi, int64_t n, int r_old, int r, std::vector<std::complex<double>> &coef,
+                           int64_t S) {
+  std::vector<float2> tmp((size_t)n * r_old), nt((size_t)n * r);
+  SCVS_CUDA(cudaMemcpy(tmp.data(), Phi, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < r; ++j) nt[(size_t)i * r + j] = tmp[(size_t)i * r_old + j];
+  SCVS_CUDA(cudaMemcpy(Phi, nt.data(), nt.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  std::vector<std::complex<double>> c2((size_t)S * r);
+  for (int64_t s = 0; s < S; ++s)
+    for (int j = 0; j < r; ++j) c2[(size_t)s * r + j] = coef[(size_t)s * r_old + j];
+  coef.swap(c2);
+  (void)c;
 }
 
 // Train: POD of both blocks, targets, feature/target standardisation, Adam.
 double guess_train(Ctx &c, const scvs_train_opts &o) {
   GuessModel &g = c.guess;
   if (g.n_snap < 4) throw (int)SCVS_ERR_STATE;
-  cublasHandle_t h;
-  SCVS_CUBLAS(cublasCreate(&h));
-  SCVS_CUBLAS(cublasSetStream(h, c.stream));
   if (g.Phi_u) cudaFree(g.Phi_u);
   if (g.Phi_p) cudaFree(g.Phi_p);
   g.Phi_u = g.Phi_p = nullptr;
-  std::vector<std::complex<float>> cu, cp;
+  std::vector<std::complex<double>> &cu = g.coef_u, &cp = g.coef_p;
   int ru = 0, rp = 0;
-  try {
-    pod_block(c, g, h, 0, g.n_u, o.n_pod, o.max_pod_snapshots, &g.Phi_u, cu, ru);
-    pod_block(c, g, h, g.n_u, g.n_dof - g.n_u, o.n_pod, o.max_pod_snapshots, &g.Phi_p, cp, rp);
-  } catch (...) {
-    cublasDestroy(h);
-    throw;
-  }
-  cublasDestroy(h);
-  if (ru != rp) {  // keep both blocks at the same rank
-    const int r = std::min(ru, rp);
-    if (ru > r) {  // truncate u
-      std::vector<float2> tmp((size_t)g.n_u * ru), nt((size_t)g.n_u * r);
-      SCVS_CUDA(cudaMemcpy(tmp.data(), g.Phi_u, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
-      for (int64_t i = 0; i < g.n_u; ++i)
-        for (int j = 0; j < r; ++j) nt[(size_t)i * r + j] = tmp[(size_t)i * ru + j];
-      SCVS_CUDA(cudaMemcpy(g.Phi_u, nt.data(), nt.size() * sizeof(float2), cudaMemcpyHostToDevice));
-      std::vector<std::complex<float>> c2((size_t)r * g.n_snap);
-      for (int64_t s = 0; s < g.n_snap; ++s)
-        for (int j = 0; j < r; ++j) c2[(size_t)s * r + j] = cu[(size_t)s * ru + j];
-      cu.swap(c2);
-      ru = r;
-    } else {
-      std::vector<float2> tmp((size_t)(g.n_dof - g.n_u) * rp), nt((size_t)(g.n_dof - g.n_u) * r);
-      SCVS_CUDA(cudaMemcpy(tmp.data(), g.Phi_p, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost));
-      for (int64_t i = 0; i < g.n_dof - g.n_u; ++i)
-        for (int j = 0; j < r; ++j) nt[(size_t)i * r + j] = tmp[(size_t)i * rp + j];
-      SCVS_CUDA(cudaMemcpy(g.Phi_p, nt.data(), nt.size() * sizeof(float2), cudaMemcpyHostToDevice));
-      std::vector<std::complex<float>> c2((size_t)r * g.n_snap);
-      for (int64_t s = 0; s < g.n_snap; ++s)
-        for (int j = 0; j < r; ++j) c2[(size_t)s * r + j] = cp[(size_t)s * rp + j];
-      cp.swap(c2);
-      rp = r;
-    }
-  }
+  pod_block(c, g, 0, o.n_pod, o.max_pod_snapshots, &g.Phi_u, cu, g.lam_u, ru);
+  pod_block(c, g, 1, o.n_pod, o.max_pod_snapshots, &g.Phi_p, cp, g.lam_p, rp);
+  if (ru > rp) { truncate_basis(c, g.Phi_u, g.n_u, ru, rp, cu, g.n_snap); ru = rp; }  // same rank in both blocks
+  if (rp > ru) { truncate_basis(c, g.Phi_p, g.n_dof - g.n_u, rp, ru, cp, g.n_snap); rp = ru; }
   g.n_pod = ru;
   const int S = (int)g.n_snap, n_out = 4 * g.n_pod;
   // targets [S][n_out]: (Re a_u, Im a_u) then (Re a_p, Im a_p)
   std::vector<float> T((size_t)S * n_out), F((size_t)S * 5);
   for (int s = 0; s < S; ++s) {
     for (int j = 0; j < g.n_pod; ++j) {
-      T[(size_t)s * n_out + 2 * j] = cu[(size_t)s * g.n_pod + j].real();
-      T[(size_t)s * n_out + 2 * j + 1] = cu[(size_t)s * g.n_pod + j].imag();
-      T[(size_t)s * n_out + 2 * g.n_pod + 2 * j] = cp[(size_t)s * g.n_pod + j].real();
-      T[(size_t)s * n_out + 2 * g.n_pod + 2 * j + 1] = cp[(size_t)s * g.n_pod + j].imag();
+      T[(size_t)s * n_out + 2 * j] = (float)cu[(size_t)s * g.n_pod + j].real();
+      T[(size_t)s * n_out + 2 * j + 1] = (float)cu[(size_t)s * g.n_pod + j].imag();
+      T[(size_t)s * n_out + 2 * g.n_pod + 2 * j] = (float)cp[(size_t)s * g.n_pod + j].real();
+      T[(size_t)s * n_out + 2 * g.n_pod + 2 * j + 1] = (float)cp[(size_t)s * g.n_pod + j].imag();
     }
     for (int q = 0; q < 5; ++q) F[(size_t)s * 5 + q] = (float)g.feat[(size_t)s * 5 + q];
   }
@@ -533,7 +722,7 @@ double guess_train(Ctx &c, const scvs_train_opts &o) {
     mu /= S;
     for (int s = 0; s < S; ++s) s2 += (T[(size_t)s * n_out + j] - mu) * (T[(size_t)s * n_out + j] - mu);
     g.tmean[j] = mu;
-    g.tstd[j] = std::sqrt(s2 / S) > 1e-30 ? std::sqrt(s2 / S) : 1.0;
+    g.tstd[j] = std::sqrt(s2 / S) > 1e-12 ? std::sqrt(s2 / S) : 1.0;
   }
   for (int s = 0; s < S; ++s) {
     for (int q = 0; q < 5; ++q) F[(size_t)s * 5 + q] = (float)((F[(size_t)s * 5 + q] - g.fmean[q]) / g.fstd[q]);

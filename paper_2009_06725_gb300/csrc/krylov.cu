@@ -707,4 +707,59 @@ int solve_mesh(Ctx &c, Mesh &m) {
   return solve_mesh_t<float>(c, m);
 }
 
+// Self-test of the bounded grid barrier: every block except `absent` (-1: none)
+// passes two barriers with the given poll limit; `absent` returns at once, so
+// the others' first wait runs out, they set the error word and return.
+__global__ void k_barrier_selftest(GridSync *gs, long long spin_limit, int absent, int *passed) {
+  if ((int)blockIdx.x == absent) return;
+  for (int round = 0; round < 2; ++round)
+    if (!grid_sync(gs, gridDim.x, spin_limit)) return;
+  if (threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
+int barrier_selftest(Ctx &c, long long spin_limit, int n_blocks, int absent, int *passed_out) {
+  int *passed = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &passed, sizeof(int), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(passed, 0, sizeof(int), c.stream));
+  void *args[] = {(void *)&c.gsync, (void *)&spin_limit, (void *)&absent, (void *)&passed};
+  SCVS_CUDA(cudaLaunchCooperativeKernel((void *)k_barrier_selftest, dim3(n_blocks), dim3(64), args, 0, c.stream));
+  count_launch(c);
+  int gerr = 0, np = 0;
+  SCVS_CUDA(cudaMemcpyAsync(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(&np, passed, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(passed, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  *passed_out = np;
+  if (gerr) {  // the barrier's count is left mid-round: reset it for the next cooperative kernel
+    SCVS_CUDA(cudaMemsetAsync(c.gsync, 0, sizeof(GridSync), c.stream));
+    SCVS_CUDA(cudaStreamSynchronize(c.stream));
+    return SCVS_ERR_TIMEOUT;
+  }
+  return SCVS_OK;
+}
+
+// The learned start of every mode of a mesh, without solving: x0 from the MLP
+// and the POD bases (Dirichlet rows = g), its FP64 relative residual
+// ||b - A x0|| / ||b|| per mode, and whether solve_mesh_t would keep it
+// (residual below ||b||; otherwise it starts that mode from zero).  x0 is left
+// as the mesh's held solution as it is, kept or not.  Returns false if the
+// model cannot serve the mesh.
+bool guess_probe(Ctx &c, Mesh &m, double *res0, int *kept) {
+  if (m.n_comp != 1 || !guess_initial(c, m)) return false;
+  const int ld = m.ld;
+  double *n2d = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &n2d, ld * sizeof(double), c.stream));
+  residual_fp64(c, m, nullptr, nullptr, n2d);
+  std::vector<double> n2(ld);
+  SCVS_CUDA(cudaMemcpyAsync(n2.data(), n2d, ld * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(n2d, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  for (int k = 0; k < m.m; ++k) {
+    const double r = std::sqrt(std::max(n2[k], 0.0)), bn = m.bnorm[k];
+    res0[k] = bn > 0.0 ? r / bn : r;
+    kept[k] = (bn > 0.0 && r < bn) ? 1 : 0;
+  }
+  return true;
+}
+
 }  // namespace scvs

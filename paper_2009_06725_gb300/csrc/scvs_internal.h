@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <complex>
 #include <map>
 #include <string>
 #include <vector>
@@ -183,8 +184,21 @@ struct GuessModel {
   int64_t n_dof = 0, n_u = 0, n_snap = 0, snap_cap = 0;
   float2 *snap = nullptr;           // [n_snap][n_dof] solutions divided by c_k
   std::vector<double> feat;         // [n_snap][5]
+  // Mass matrices of the reference mesh (the one that gave the first
+  // snapshot): the POD's inner products.  Device copies of the S pattern, the
+  // G row offsets/lengths (the P1 mass lives on the vertex G rows), M_s and
+  // the P1 mass.
+  struct RefMass {
+    int dim = 0;
+    int64_t N = 0, P = 0;
+    int64_t *s_ptr = nullptr, *g_ptr = nullptr;
+    int32_t *s_col = nullptr, *g_len = nullptr;
+    double *Ms = nullptr, *Mp = nullptr;
+  } wref;
   int n_pod = 0;
   float2 *Phi_u = nullptr, *Phi_p = nullptr;  // [n_u][n_pod], [n_p][n_pod]
+  std::vector<std::complex<double>> coef_u, coef_p;  // [n_snap][n_pod] POD coefficients of the snapshots
+  std::vector<double> lam_u, lam_p;                   // Gram eigenvalues, descending
   std::vector<double> fmean, fstd, tmean, tstd;
   int hidden = 0, n_out = 0, dims[5] = {0, 0, 0, 0, 0};
   int64_t woff[4] = {0}, boff[4] = {0}, n_params = 0;
@@ -216,11 +230,15 @@ struct GuessModel {
   }
   void release() {
     release_mlp();
-    for (void *p : {(void *)snap, (void *)Phi_u, (void *)Phi_p})
+    for (void *p : {(void *)snap, (void *)Phi_u, (void *)Phi_p, (void *)wref.s_ptr, (void *)wref.g_ptr,
+                    (void *)wref.s_col, (void *)wref.g_len, (void *)wref.Ms, (void *)wref.Mp})
       if (p) cudaFree(p);
     snap = nullptr; Phi_u = Phi_p = nullptr;
+    wref = RefMass{};
     n_snap = snap_cap = n_dof = n_u = 0;
+    n_pod = 0;
     feat.clear();
+    coef_u.clear(); coef_p.clear(); lam_u.clear(); lam_p.clear();
   }
 };
 
@@ -289,6 +307,8 @@ void matfree_tables(Ctx &c);  // matfree.cu
 
 // ---- krylov.cu
 int solve_mesh(Ctx &c, Mesh &m);
+bool guess_probe(Ctx &c, Mesh &m, double *res0, int *kept);
+int barrier_selftest(Ctx &c, long long spin_limit, int n_blocks, int absent, int *passed);
 
 // ---- guess.cu
 void guess_add_snapshots(Ctx &c, Mesh &m, const double *features);

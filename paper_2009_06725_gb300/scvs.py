@@ -96,6 +96,8 @@ SIGNATURES = {
     "scvs_rhs_dev": (_I32, [_P, _I32, C.POINTER(_P)]),
     "scvs_apply_precond": (_I32, [_P, _I32, _P, _P]),
     "scvs_launch_count": (_I64, [_P]),
+    "scvs_barrier_selftest": (_I32, [_P, _I64, _I32, _I32, C.POINTER(_I32)]),
+    "scvs_pool_usage": (_I32, [_P, _I32, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
     "scvs_default_train_opts": (None, [C.POINTER(scvs_train_opts)]),
     "scvs_guess_add_snapshots": (_I32, [_P, _I32, _P]),
     "scvs_train_guess": (_I32, [_P, C.POINTER(scvs_train_opts), C.POINTER(_D)]),
@@ -103,6 +105,10 @@ SIGNATURES = {
     "scvs_guess_info": (_I32, [_P, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32)]),
     "scvs_guess_reset": (_I32, [_P]),
     "scvs_mlp_init": (_I32, [_P, _I32, _I32, _I32, _P]),
+    "scvs_mlp_set_params": (_I32, [_P, _P]),
+    "scvs_guess_basis": (_I32, [_P, _I32, _I64, _I32, _P]),
+    "scvs_guess_coefficients": (_I32, [_P, _I32, _I64, _I32, _P]),
+    "scvs_guess_initial": (_I32, [_P, _I32, _I64, _P, _P]),
     "scvs_mlp_num_params": (_I32, [_P, C.POINTER(_I64)]),
     "scvs_mlp_get_params": (_I32, [_P, _P]),
     "scvs_mlp_forward_dev": (_I32, [_P, _P, _I64, _P]),
@@ -114,6 +120,7 @@ SIGNATURES = {
     "scvs_set_neumann": (_I32, [_P, _I32, _P, C.POINTER(_I64)]),
     "scvs_bc_spectrum": (_I32, [_P, _I32, _I64, _I32, _P, _P, _P, _P]),
     "scvs_mode_energies": (_I32, [_P, _I32, _I64, _P, _P]),
+    "scvs_modes_to_keep": (_I32, [_P, _I64, _D, _I32, C.POINTER(_I64)]),
     "scvs_set_solution": (_I32, [_P, _I32, _P, _P]),
     "scvs_mesh_hash": (_I32, [_I32, _I64, _I64, _P, _I64, _P, _P, C.POINTER(C.c_uint64)]),
     "scvs_checkpoint_write": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P]),
@@ -327,6 +334,24 @@ def scvs_launch_count(ctx):
     return lib().scvs_launch_count(ctx)
 
 
+def scvs_barrier_selftest(ctx, spin_limit, n_blocks, absent_block):
+    """Bounded grid-barrier self-test: returns (status code, blocks passed);
+    SCVS_ERR_TIMEOUT is returned, not raised."""
+    n = C.c_int32(0)
+    rc = lib().scvs_barrier_selftest(ctx, int(spin_limit), int(n_blocks), int(absent_block), C.byref(n))
+    if rc < 0 and rc != SCVS_ERR_TIMEOUT:
+        _check(ctx, rc)
+    return rc, n.value
+
+
+def scvs_pool_usage(ctx, reset_high=False):
+    """(used, used_high, reserved) bytes of the context's device memory pool;
+    reset_high then resets the high-water mark to the current use."""
+    u, h, r = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(ctx, lib().scvs_pool_usage(ctx, 1 if reset_high else 0, C.byref(u), C.byref(h), C.byref(r)))
+    return u.value, h.value, r.value
+
+
 def scvs_default_train_opts(**overrides):
     o = scvs_train_opts()
     lib().scvs_default_train_opts(C.byref(o))
@@ -364,6 +389,36 @@ def scvs_guess_reset(ctx):
 def scvs_mlp_init(ctx, n_in, hidden, n_out, params):
     p = np.ascontiguousarray(params, dtype=np.float32)
     return _check(ctx, lib().scvs_mlp_init(ctx, n_in, hidden, n_out, _ptr(p)))
+
+
+def scvs_mlp_set_params(ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(ctx, lib().scvs_mlp_set_params(ctx, _ptr(p)))
+
+
+def scvs_guess_basis(ctx, block, n_rows):
+    """POD basis of block 0 (velocity) or 1 (pressure): complex [n_rows][n_pod]."""
+    r = scvs_guess_info(ctx)["n_pod"]
+    out = np.empty((n_rows, r), dtype=np.complex128)
+    _check(ctx, lib().scvs_guess_basis(ctx, block, n_rows, r, _ptr(out)))
+    return out
+
+
+def scvs_guess_coefficients(ctx, block):
+    """POD coefficients of the training snapshots: complex [n_snapshots][n_pod]."""
+    info = scvs_guess_info(ctx)
+    out = np.empty((info["n_snapshots"], info["n_pod"]), dtype=np.complex128)
+    _check(ctx, lib().scvs_guess_coefficients(ctx, block, info["n_snapshots"], info["n_pod"], _ptr(out)))
+    return out
+
+
+def scvs_guess_initial(ctx, mesh_id, n_modes):
+    """Learned start of every mode without solving: (res0 [m], kept [m] bool);
+    x0 is left as the mesh's solution (read it with scvs_get_modal)."""
+    res0 = np.empty(n_modes, dtype=np.float64)
+    kept = np.empty(n_modes, dtype=np.int32)
+    _check(ctx, lib().scvs_guess_initial(ctx, mesh_id, n_modes, _ptr(res0), _ptr(kept)))
+    return res0, kept.astype(bool)
 
 
 def scvs_mlp_num_params(ctx):
@@ -527,15 +582,16 @@ def resume_from_checkpoint(ctx, mesh_id, mesh, omegas, tol, path):
     return idx
 
 
-def modes_to_keep(incr2, eps):
-    """A posteriori choice of the number of modes (Sec. 3): modes are added in
-    order while the reconstruction still changes by at least eps in relative
-    L2(Omega x T) norm; returns the count of modes kept (the first N with
-    sqrt(incr2[N]) < eps; all of them if none)."""
-    inc = np.sqrt(np.maximum(np.asarray(incr2, dtype=np.float64), 0.0))
-    small = np.flatnonzero(inc < eps)
-    small = small[small > 0]  # mode 0 alone is the whole series
-    return int(small[0]) if small.size else int(inc.size)
+def scvs_modes_to_keep(incr2, eps, patience=2):
+    """A posteriori number of modes (Sec. 3): the smallest N >= 1 whose next
+    `patience` reconstruction changes (sqrt of incr2) are all below eps; all
+    modes if none."""
+    inc = np.ascontiguousarray(incr2, dtype=np.float64)
+    n = C.c_int64(0)
+    rc = lib().scvs_modes_to_keep(_ptr(inc), inc.size, float(eps), int(patience), C.byref(n))
+    if rc < 0:
+        raise ScvsError(rc, "scvs_modes_to_keep: bad argument")
+    return n.value
 
 
 def scvs_graph_aggregates(row_ptr, col, target):

@@ -80,11 +80,24 @@ def test_write_checks_sizes(tmp_path):
 
 
 def test_modes_to_keep_rule():
-    # increments of a k^-2 spectrum: delta_N^2 = E_N / sum_{k<=N} E_k
+    """The a posteriori mode count through the C ABI (host only)."""
+    # increments of a k^-2 spectrum: delta_N^2 = E_N / sum_{k<=N} E_k, decreasing
     E = np.array([1.0] + [0.5 * k ** -4.0 for k in range(1, 10)])
     inc = E / np.cumsum(E)
-    for eps in (1e-1, 3e-2, 1e-2):  # reached at N = 3, 5, 8
-        n = scvs.modes_to_keep(inc, eps)
+    for eps in (1e-1, 3e-2, 1e-2):  # first reached at N = 3, 5, 8
+        n = scvs.scvs_modes_to_keep(inc, eps, patience=1)
         assert np.sqrt(inc[n]) < eps and all(np.sqrt(inc[1:n]) >= eps)
-    assert scvs.modes_to_keep(inc, 1e-12) == 10  # none small enough: keep all
-    assert scvs.modes_to_keep([1.0, 0.0, 0.3], 1e-3) == 1  # a zero mode stops the series
+        # with monotone increments a longer patience stops at the same mode
+        assert scvs.scvs_modes_to_keep(inc, eps, patience=2) == n
+    assert scvs.scvs_modes_to_keep(inc, 1e-12) == 10  # none small enough: keep all
+    # a missing harmonic (zero change) followed by an energetic mode
+    assert scvs.scvs_modes_to_keep([1.0, 0.0, 0.3], 1e-3, patience=1) == 1
+    assert scvs.scvs_modes_to_keep([1.0, 0.0, 0.3], 1e-3) == 3
+    assert scvs.scvs_modes_to_keep([1.0, 0.0, 0.3, 0.0, 0.0, 0.2], 1e-3) == 3
+    # the last change alone cannot be confirmed by a second one: keep every mode
+    assert scvs.scvs_modes_to_keep([1.0, 0.5, 1e-9], 1e-3) == 3
+    assert scvs.scvs_modes_to_keep([1.0], 1e-3) == 1
+    with pytest.raises(scvs.ScvsError):
+        scvs.scvs_modes_to_keep([1.0, 0.1], 0.0)
+    with pytest.raises(scvs.ScvsError):
+        scvs.scvs_modes_to_keep([1.0, 0.1], 1e-3, patience=0)

@@ -96,6 +96,23 @@ def test_every_kind_solves_to_the_oracle(pipe, precond):
     assert np.all(fem.relative_residual(mats, wl, Xg) < 1.05e-8)
 
 
+@pytest.mark.parametrize("precond", [scvs.SCVS_PC_BLOCK_CHEB, scvs.SCVS_PC_BLOCK_PMG, scvs.SCVS_PC_TRI_PMG,
+                                     scvs.SCVS_PC_TRI_PMG_CS])
+@pytest.mark.parametrize("precision,solve_tol,err_tol", [(scvs.SCVS_PREC_FP64, 1e-13, 1e-10),
+                                                         (scvs.SCVS_PREC_MIXED, 1e-12, 1e-8)])
+def test_every_kind_at_the_parity_tolerance(pipe, precond, precision, solve_tol, err_tol):
+    """Solved to a 1e-13 (FP64) / 1e-12 (mixed) residual, every kind reaches
+    the oracle's solution within 1e-10 / 1e-8 relative L2 per mode."""
+    wl, mats = pipe
+    X = fem.solve_modes(mats, wl)
+    s, mid, rep, u, p = solve(wl, precond=precond, precision=precision, tol=solve_tol, max_cycles=4000)
+    with s:
+        Xg = stack_modal(u, p)
+    for k, r in enumerate(rep):
+        assert r["status"] == scvs.SCVS_CONVERGED and r["rel_res"] <= solve_tol, (k, r)
+        assert rel_l2(Xg[k], X[k]) < err_tol, (k, rel_l2(Xg[k], X[k]))
+
+
 def test_triangular_needs_fewer_iterations(pipe):
     wl, _ = pipe
     its = {}

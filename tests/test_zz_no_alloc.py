@@ -46,3 +46,34 @@ def test_static_reconstruction_matches_allocating_entry_point():
             scvs.scvs_reconstruct_dev_static(s.ctx, mid, too_many, 1.0, big_u.data_ptr(), big_u.data_ptr())
         assert e.value.code == scvs.SCVS_ERR_ARG
         assert "SCVS_RECON_STATIC_MAX" in str(e.value)
+
+
+def test_static_reconstruction_allocates_nothing():
+    """A warm call leaves the context pool's high-water mark, its reservation
+    and the device's free memory unchanged and launches exactly its two
+    kernels; the allocating entry point, timed the same way, raises the
+    high-water mark (so the probe can see an allocation)."""
+    torch = torch_cuda()
+    wl = workloads.channel_workload(16, 4, n_modes=8)
+    s, mid, rep, u, p = solve(wl, precision=scvs.SCVS_PREC_FP64, tol=1e-12)
+    N, P = u.shape[1], p.shape[1]
+    n_t = 32
+    with s:
+        out_u = torch.zeros((n_t, N, 2), dtype=torch.float64, device="cuda")
+        out_p = torch.zeros((n_t, P), dtype=torch.float64, device="cuda")
+        scvs.scvs_reconstruct_dev_static(s.ctx, mid, n_t, 1.0, out_u.data_ptr(), out_p.data_ptr())  # set-up call
+        torch.cuda.synchronize()
+        used0, _, res0 = scvs.scvs_pool_usage(s.ctx, reset_high=True)
+        free0 = torch.cuda.mem_get_info()[0]
+        n0 = scvs.scvs_launch_count(s.ctx)
+        scvs.scvs_reconstruct_dev_static(s.ctx, mid, n_t, 1.0, out_u.data_ptr(), out_p.data_ptr())
+        torch.cuda.synchronize()
+        used1, high1, res1 = scvs.scvs_pool_usage(s.ctx, reset_high=True)
+        free1 = torch.cuda.mem_get_info()[0]
+        assert scvs.scvs_launch_count(s.ctx) == n0 + 2
+        assert (used1, high1, res1) == (used0, used0, res0)
+        assert free1 == free0
+        # the same probe around the allocating entry point sees its scratch
+        scvs.scvs_reconstruct_dev(s.ctx, mid, n_t, 1.0, out_u.data_ptr(), out_p.data_ptr())
+        used2, high2, _ = scvs.scvs_pool_usage(s.ctx)
+        assert used2 == used0 and high2 > used0
