@@ -11,11 +11,14 @@ def test_growth_exponent_and_extrapolation():
     n4 = 30000
     cb = bench.cpu_baseline_obj(2.0, n4, small=(0.25, n4 // 2))
     assert cb["growth_exponent"] == pytest.approx(3.0)
-    assert cb["value"] == pytest.approx(1.0 / (2.0 * bench.PIPE["n_x"] / bench.SAMPLE_LAYERS))
+    # value is what was measured: the slice's own rate
+    assert cb["value"] == pytest.approx(0.5) and cb["measured_on"] == "slice" and cb["slice_dofs"] == n4
+    assert cb["value_linear_upper_bound"] == pytest.approx(1.0 / (2.0 * bench.PIPE["n_x"] / bench.SAMPLE_LAYERS))
     assert cb["value_extrapolated"] == pytest.approx(1.0 / (2.0 * (bench.FULL_DOFS / n4) ** 3.0))
-    # an exponent above 1 makes the extrapolated rate the lower of the two
-    assert cb["value_extrapolated"] < cb["value"]
-    assert "extrapolated" in cb["sample"] and cb["cores"] == 1 and cb["kind"] == "oracle"
+    # an exponent above 1 makes the extrapolated rate the lower of the two full-size figures
+    assert cb["value_extrapolated"] < cb["value_linear_upper_bound"] < cb["value"]
+    assert "extrapolated" in cb["sample"] and "upper bound" in cb["sample"]
+    assert cb["cores"] == 1 and cb["kind"] == "oracle"
     plain = bench.cpu_baseline_obj(2.0, n4)
     assert "value_extrapolated" not in plain
 

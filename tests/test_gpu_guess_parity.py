@@ -90,8 +90,11 @@ def test_pod_basis_and_coefficients_match_oracle(family):
     # element by element, phases included (both sides fix them the same way)
     assert _col_err(Gu, family["Pu"]) < 2e-3
     assert _col_err(Gp, family["Pp"]) < 2e-3
-    assert _col_err(cu, family["au"]) < 2e-3
-    assert _col_err(cp, family["ap"]) < 2e-3
+    # coefficients against the size of the snapshot's whole coefficient vector (the error of the
+    # reconstruction Phi a): a weak vector's own coefficients are ill-conditioned, because FP32
+    # snapshots tilt it towards the dominant directions by ~eps_32 sigma_1 / sigma_j
+    for A, B in ((cu, family["au"]), (cp, family["ap"])):
+        assert (np.abs(A - B).max(axis=1) / np.abs(B).max(axis=1)).max() < 1e-4
     # the leading vectors, whose eigenvalues stand well apart, agree closely
     assert _col_err(Gu[:, :3], family["Pu"][:, :3]) < 1e-4
     assert _col_err(cu[:, :3], family["au"][:, :3]) < 1e-4
