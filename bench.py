@@ -214,14 +214,20 @@ def pc_config(args):
     """The preconditioner entry of a bench line's config (library default: triangular-pmg)."""
     kind = 3 if args.precond is None else args.precond
     c = {"precond": PC_NAMES.get(kind, str(kind))}
+    if getattr(args, "krylov", "fgmres") == "cocr":
+        c["krylov"] = "cocr"
     if kind == 4:
         c["schur_agg"] = args.schur_agg or 96
     return c
 
 
 def pc_opts(args):
-    """Preconditioner options given on the command line (library defaults otherwise)."""
+    """Preconditioner and staging options given on the command line (library defaults otherwise)."""
     o = {}
+    if getattr(args, "stage", None) is not None:
+        o["stage"] = args.stage
+    if getattr(args, "krylov", "fgmres") == "cocr":
+        o["krylov"] = 1
     if args.precond is not None:
         o["precond"] = args.precond
     if args.schur_agg:
@@ -330,6 +336,7 @@ def run_gpu(args):
     scvs.scvs_kernel_timers(ctx, False)
     conv = sum(1 for rr in reps for r in rr if r["status"] == scvs.SCVS_CONVERGED)
     tuned = scvs.scvs_tuned_shapes(ctx, 0)
+    tuned["staged"] = scvs.scvs_staged_info(ctx, 0)
     phase_ms = phases()
     elapsed, conv_total = reduce_over_ranks(elapsed, conv, dev)
     value = conv_total / elapsed
@@ -645,10 +652,11 @@ def run_spmm(args):
     peaks, peak_kind = measured_peaks()
     stream = torch.cuda.current_stream(dev)
     out = {}
-    with scvs.Solver(stream=stream.cuda_stream) as s:
+    with scvs.Solver(stream=stream.cuda_stream, **pc_opts(args)) as s:
         mid = scvs.scvs_set_mesh(s.ctx, wl["mesh"])
         scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
         scvs.scvs_set_modes(s.ctx, mid, wl["omegas"], wl["g"])
+        staged = scvs.scvs_staged_info(s.ctx, mid)
         n, ld = scvs.scvs_dof_count(s.ctx, mid), scvs.scvs_mode_stride(s.ctx, mid)
         gen = torch.Generator(device=dev).manual_seed(0)
         x64 = torch.randn((n, ld), dtype=torch.complex128, device=dev, generator=gen)
@@ -677,7 +685,7 @@ def run_spmm(args):
             "unit": "GB/s", "n_gpus": 1, "higher_is_better": True, "impl": "spmm", "data": "synthetic",
             "dtype": "c64", "peak": peaks["hbm_gbs"], "peak_source": peak_kind,
             "config": {"workload": "151k-node pipe, 32 modes, 473,109 dofs/mode, L2 flushed before each launch"},
-            "cases": out}
+            "cases": out, "staged": staged}
     print(json.dumps(line), flush=True)
 
 
@@ -771,6 +779,104 @@ def run_fp64_permode(args):
     print(json.dumps(out), flush=True)
 
 
+def run_validation(args):
+    """The paper's validation cases on the GPU path (traction inlets, analytic
+    solutions): the channel of Sec. 3.2 on the paper's mesh (Table
+    channel_err: e(T/4), e(T/2) at W = 0, 2 pi, 10 pi, 20 pi) and the pipe of
+    Sec. 3.4 (L/R = 15) on meshes of the QM1-QM4 node counts: e(T/2) at W = 8 pi
+    per mesh (Fig. cylinder_msh_elesize) and e(T/2) at W = 0, 8 pi, ..., 80 pi on
+    the finest (Fig. cylinder_msh_freq).  The errors use the assembled M_s of
+    the library (scvs_get_values) and the time samples of its reconstruction."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2009_06725_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2009_06725_gb300 import scvs
+    import scipy.sparse as sp
+    from synthetic.womersley import channel_profile, pipe_profile
+
+    def solve(wl, tol):
+        mesh = wl["mesh"]
+        N, P, d, m = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["dim"], len(wl["omegas"])
+        with scvs.Solver(tol=tol, max_cycles=2000) as s:
+            mid = scvs.scvs_set_mesh(s.ctx, mesh)
+            scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
+            scvs.scvs_set_modes(s.ctx, mid, wl["omegas"], wl["g"])
+            scvs.scvs_set_neumann(s.ctx, mid, wl["h"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = scvs.scvs_solve(s.ctx, mid, m)
+            dt = time.perf_counter() - t0
+            u, _ = scvs.scvs_get_modal(s.ctx, mid, m, N, d, P)
+            rp, col = scvs.scvs_get_csr(s.ctx, mid, scvs.SCVS_CSR_S)
+            vals = scvs.scvs_get_values(s.ctx, mid, scvs.SCVS_CSR_S, d)
+        Ms = sp.csr_matrix((vals[0], col, rp), shape=(N, N))
+        return u, Ms, rep, dt
+
+    def err_t(Ms, uh, ue, w, t):
+        ph = np.exp(1j * w * t)
+        a, b = np.real(ue * ph), np.real(uh * ph)
+        e, f = a - b, a
+        ne = sum(float(e[:, c] @ (Ms @ e[:, c])) for c in range(e.shape[1]))
+        nf = sum(float(f[:, c] @ (Ms @ f[:, c])) for c in range(f.shape[1]))
+        return float(np.sqrt(ne / nf))
+
+    out = {"metric": "relative L2 error e(t) against the analytic solution (Eq. total_error)", "impl": "validation",
+           "n_gpus": 1, "data": "synthetic", "dtype": "c64+f64", "unit": "1", "tol": args.val_tol}
+    # channel
+    rho, mu, H, L = 1.0, 0.01, 0.5, 5.0
+    Ws = [0.0, 2 * np.pi, 10 * np.pi, 20 * np.pi]
+    wl = workloads.paper_channel(np.array(Ws) * (mu / rho) / H ** 2, rho=rho, mu=mu, neumann_tag=scvs.SCVS_TAG_NEUMANN)
+    u, Ms, rep, dt = solve(wl, args.val_tol)
+    y = wl["mesh"]["xyz"][:, 1]
+    rows = []
+    for k, W in enumerate(Ws):
+        w = wl["omegas"][k]
+        ex = np.zeros_like(u[k])
+        ex[:, 0] = channel_profile(y, w, H, rho, mu, G=1.0 / L)
+        T = 2 * np.pi / w if w > 0 else 1.0
+        rows.append({"W_over_pi": W / np.pi, "e_T4": err_t(Ms, u[k], ex, w, 0.25 * T),
+                     "e_T2": err_t(Ms, u[k], ex, w, 0.5 * T), "iterations": rep[k]["iterations"]})
+    out["channel"] = {"mesh": "49 x 9 quads of [0,5] x [-0.5,0.5] in P2 triangles: 882 elements, 1,881 nodes, "
+                              "4,262 dofs (the paper's mesh)", "rows": rows, "solve_s": dt,
+                      "paper_scvs_percent": {"0": "1.3e-3 (at eps_L 1e-6)", "2pi": [0.01, 0.031],
+                                             "10pi": [0.12, 0.46], "20pi": [0.29, 1.8]}}
+    # pipe
+    rho, mu = 1.0, 1.0
+    conv = []
+    for name, target in (("QM1", 37469), ("QM2", 70872), ("QM3", 133645), ("QM4", 225610)):
+        wl = workloads.paper_pipe(target, np.array([8 * np.pi * mu / rho]), rho=rho, mu=mu,
+                                  neumann_tag=scvs.SCVS_TAG_NEUMANN)
+        u, Ms, rep, dt = solve(wl, args.val_tol)
+        xyz = wl["mesh"]["xyz"]
+        r = np.hypot(xyz[:, 1], xyz[:, 2])
+        ex = np.zeros_like(u[0])
+        w = wl["omegas"][0]
+        ex[:, 0] = pipe_profile(r, w, 1.0, rho, mu, G=1.0 / 15.0)
+        n_el = wl["mesh"]["conn"].shape[0]
+        h = (np.pi * 15.0 / n_el * 6.0 * np.sqrt(2.0)) ** (1.0 / 3.0)  # edge of a regular tet of the mean volume
+        conv.append({"mesh": name + "-sized", "nodes": int(xyz.shape[0]), "elements": int(n_el), "h_over_R": h,
+                     "e_T2": err_t(Ms, u[0], ex, w, np.pi / w), "iterations": rep[0]["iterations"], "solve_s": dt})
+    Ws = np.arange(11) * 8 * np.pi
+    wl = workloads.paper_pipe(225610, Ws * mu / rho, rho=rho, mu=mu, neumann_tag=scvs.SCVS_TAG_NEUMANN)
+    u, Ms, rep, dt = solve(wl, args.val_tol)
+    xyz = wl["mesh"]["xyz"]
+    r = np.hypot(xyz[:, 1], xyz[:, 2])
+    freq = []
+    for k, W in enumerate(Ws):
+        w = wl["omegas"][k]
+        ex = np.zeros_like(u[k])
+        ex[:, 0] = pipe_profile(r, w, 1.0, rho, mu, G=1.0 / 15.0)
+        T = 2 * np.pi / w if w > 0 else 1.0
+        freq.append({"W_over_pi": float(W / np.pi), "e_T2": err_t(Ms, u[k], ex, w, 0.5 * T),
+                     "iterations": rep[k]["iterations"]})
+    out["pipe"] = {"geometry": "L/R = 15, R = 1, traction inlet, no-slip wall, traction-free outlet, O-grid tets",
+                   "convergence_W8pi": conv, "frequency_QM4": freq, "frequency_solve_s": dt,
+                   "paper": "QM1-QM4: 37,469-225,610 nodes; e(T/2) at W = 8 pi and its growth with W in "
+                            "Figs. cylinder_msh_elesize and cylinder_msh_freq (context only)"}
+    print(json.dumps(out), flush=True)
+
+
 def pinned_host_buffers(torch, wl, m, N, P, d):
     """Inputs copied once into page-locked host memory and page-locked output
     arrays, so the end-to-end step moves its bytes by DMA (set up outside the
@@ -839,12 +945,17 @@ def main():
     ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG, 3 TRI_PMG (default), "
                     "4 TRI_PMG_CS (coarse Schur correction; pipe, batch and bifurcation workloads)")
     ap.add_argument("--schur-agg", type=int, default=0, help="aggregates per component of TRI_PMG_CS (default 96)")
+    ap.add_argument("--krylov", default="fgmres", choices=["fgmres", "cocr"],
+                    help="cocr: short-recurrence COCR (with a symmetric, block-diagonal --precond 0/1/2)")
+    ap.add_argument("--stage", type=int, default=None, help="staged gathers: 0 autotuned (default), -1 never, "
+                    "4/8/16/32 forced mode chunk")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true", help="skip the per-mode FP64 error and comparison")
     ap.add_argument("--kernel-case", action="store_true", help="short kernel sequence for profiler captures")
     ap.add_argument("--workload", default="pipe",
-                    choices=["pipe", "batch", "guess", "fp64-permode", "bifurcation", "spmm"])
+                    choices=["pipe", "batch", "guess", "fp64-permode", "bifurcation", "spmm", "validation"])
+    ap.add_argument("--val-tol", type=float, default=1e-10, help="residual tolerance of the validation solves")
     ap.add_argument("--bif-h", type=float, default=0.038, help="voxel spacing of the bifurcation (0.038: ~6M nodes)")
     ap.add_argument("--fp64-modes", type=int, default=4)
     ap.add_argument("--batch-meshes", type=int, default=48)
@@ -867,6 +978,9 @@ def main():
         return
     if args.workload == "bifurcation" and args.impl == "gpu":
         run_bifurcation(args)
+        return
+    if args.workload == "validation" and args.impl == "gpu":
+        run_validation(args)
         return
     if args.workload == "fp64-permode" and args.impl == "gpu":
         run_fp64_permode(args)

@@ -93,6 +93,9 @@ extern "C" {
 #define SCVS_GUESS_CURRENT 2 /* start every mode from the solution the mesh holds (the last solve's, or the one
                                 given by scvs_set_solution), its Dirichlet rows reset to g: warm start / resume */
 
+#define SCVS_KRYLOV_FGMRES 0
+#define SCVS_KRYLOV_COCR 1
+
 typedef struct scvs_ctx scvs_ctx;
 typedef struct { double re, im; } scvs_c64;
 
@@ -117,7 +120,15 @@ typedef struct {
   int32_t schur_agg; /* SCVS_PC_TRI_PMG_CS: aggregates per connected component of the vertex graph (1..512;
                         0 or default: 96); aggregates are grown to ceil(vertices / schur_agg) vertices, so a
                         component may end with somewhat more or fewer */
-  int32_t reserved;
+  int32_t stage;     /* staged gathers of the FP32 SpMM and fine Chebyshev kernels (row blocks of compact
+                        footprint, the footprint copied into shared memory by TMA bulk copies): 0 (default):
+                        the autotuner times them beside the unstaged shapes and keeps the fastest; -1: never
+                        (no row blocks are built); 4, 8, 16 or 32: always, with that many modes per block
+                        (where the footprint fits shared memory) */
+  int32_t krylov;    /* SCVS_KRYLOV_FGMRES (default): restarted flexible GMRES(restart); SCVS_KRYLOV_COCR:
+                        preconditioned COCR, a short recurrence for complex symmetric systems (7 work vectors
+                        per system), valid with the symmetric block-diagonal preconditioner kinds */
+  int32_t inner_max; /* COCR iterations per FP64 refinement cycle (default 400) */
 } scvs_opts;
 
 /* Options of scvs_train_guess (learned initial guess). */
@@ -242,6 +253,23 @@ int scvs_reconstruct_dev(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double per
 #define SCVS_RECON_STATIC_MAX 8192
 int scvs_reconstruct_dev_static(scvs_ctx *ctx, int32_t mesh_id, int32_t n_t, double period,
                                 double *u_t_dev, double *p_t_dev);
+
+/* Staged gathers of a mesh: info[10] = {row blocks built (1/0), blocks, nonzero
+ * budget per block, largest footprint, largest vertex prefix of a footprint,
+ * footprint entries in total, staged mode chunk of the SpMM and of the fine
+ * Chebyshev kernels (0: unstaged), 1 if that SpMM / Chebyshev choice fits
+ * shared memory (otherwise the unstaged kernel runs)}; us[8] (may be NULL) = autotuner times of
+ * the staged SpMM and Chebyshev step with mode chunks 4, 8, 16, 32 (0: not
+ * timed). */
+int scvs_staged_info(scvs_ctx *ctx, int32_t mesh_id, int64_t *info, float *us);
+/* The row blocks themselves (host copies; any pointer may be NULL): perm[N]
+ * (rows in locality order), row0[n_blk+1] (block b = perm[row0[b]..row0[b+1])),
+ * fp_ptr[n_blk+1] and fp_col[footprint total] (every block's ascending
+ * distinct columns), fv_len[n_blk] (columns < n_vertices at the head of each
+ * footprint), lcol[S nonzeros] (each nonzero's index in its row's block
+ * footprint, S pattern order).  SCVS_ERR_STATE if none were built. */
+int scvs_staged_blocks(scvs_ctx *ctx, int32_t mesh_id, int32_t *perm, int64_t *row0, int64_t *fp_ptr, int32_t *fp_col,
+                       int32_t *fv_len, uint16_t *lcol);
 
 /* ---- parity / inspection ------------------------------------------------ */
 #define SCVS_CSR_S 0  /* P2 x P2 scalar pattern (values M_s, K_s) */

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 SOURCES = ["api.cu", "assembly.cu", "operators.cu", "krylov.cu", "recon.cu", "matfree.cu", "guess.cu",
-           "refmats.cpp"]
+           "blocks.cu", "refmats.cpp"]
 
 
 def nvcc():

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 #include "scvs_internal.h"
+#include "opargs.cuh"
 
 using namespace scvs;
 
@@ -216,14 +217,19 @@ int set_modes(scvs_ctx *c, int mesh_id, int n_modes, const double *omega, const 
     auto it = c->tune_cache.find(key);
     if (it == c->tune_cache.end()) {
       autotune_shapes(*c, *m);
-      c->tune_cache[key] = Ctx::TuneRec{m->mpl_spmm, m->tile_spmm, m->mpl_cheb, m->tile_cheb, m->tune_us};
+      c->tune_cache[key] =
+          Ctx::TuneRec{m->mpl_spmm, m->tile_spmm, m->mpl_cheb, m->tile_cheb, m->st_spmm, m->st_cheb, m->tune_us};
     } else {
       m->mpl_spmm = it->second.mpl_spmm;
       m->tile_spmm = it->second.tile_spmm;
       m->mpl_cheb = it->second.mpl_cheb;
       m->tile_cheb = it->second.tile_cheb;
+      m->st_spmm = it->second.st_spmm;
+      m->st_cheb = it->second.st_cheb;
       m->tune_us = it->second.us;
     }
+  } else {
+    m->st_spmm = m->st_cheb = c->opts.stage > 0 ? c->opts.stage : 0;
   }
   return SCVS_OK;
 }
@@ -249,6 +255,8 @@ void scvs_default_opts(scvs_opts *o) {
   o->verbose = 0;
   o->stream = nullptr;
   o->schur_agg = 96;
+  o->krylov = SCVS_KRYLOV_FGMRES;
+  o->inner_max = 400;
 }
 
 int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
@@ -258,6 +266,12 @@ int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
   if (!c) return SCVS_ERR_OOM;
   if (opts) c->opts = *opts; else scvs_default_opts(&c->opts);
   if (c->opts.cheb_c < 1) c->opts.cheb_c = 20;
+  const int st = c->opts.stage;
+  if (!(st == -1 || st == 0 || st == 4 || st == 8 || st == 16 || st == 32) ||
+      (c->opts.krylov != SCVS_KRYLOV_FGMRES && c->opts.krylov != SCVS_KRYLOV_COCR) || c->opts.inner_max < 1) {
+    delete c;
+    return SCVS_ERR_ARG;
+  }
   int r = guarded(c, [&]() {
     SCVS_CUDA(cudaGetDevice(&c->device));
     SCVS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -318,7 +332,9 @@ int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
   if (!c || !o) return SCVS_ERR_ARG;
   if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
       o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_TRI_PMG_CS ||
-      o->schur_agg < 0 || o->schur_agg > 512)
+      o->schur_agg < 0 || o->schur_agg > 512 ||
+      !(o->stage == -1 || o->stage == 0 || o->stage == 4 || o->stage == 8 || o->stage == 16 || o->stage == 32) ||
+      (o->krylov != SCVS_KRYLOV_FGMRES && o->krylov != SCVS_KRYLOV_COCR) || o->inner_max < 1)
     return fail(c, SCVS_ERR_ARG, "invalid options");
   void *old_stream = c->opts.stream;
   if (o->stream != old_stream) {
@@ -893,6 +909,47 @@ int scvs_tuned_shapes(scvs_ctx *c, int32_t mesh_id, int32_t *shape, float *us) {
     }
     if (us)
       for (int i = 0; i < 2 * 3 * SCVS_TUNE_TILES; ++i) us[i] = i < (int)m->tune_us.size() ? m->tune_us[i] : 0.0f;
+    return SCVS_OK;
+  });
+}
+
+int scvs_staged_info(scvs_ctx *c, int32_t mesh_id, int64_t *info, float *us) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    const RowBlocks &rb = m->rb;
+    if (info) {
+      const void *aligned = reinterpret_cast<const void *>(256);  // any 16-byte aligned vector
+      const int64_t v[10] = {rb.valid ? 1 : 0, rb.n_blk, rb.budget, rb.fp_max, rb.fv_max, rb.fp_total, m->st_spmm,
+                             m->st_cheb, staged_ok(*c, *m, m->st_spmm, true, aligned) ? 1 : 0,
+                             staged_ok(*c, *m, m->st_cheb, false, aligned) ? 1 : 0};
+      for (int i = 0; i < 10; ++i) info[i] = v[i];
+    }
+    if (us) {
+      const size_t st0 = (size_t)2 * 3 * SCVS_TUNE_TILES;
+      for (int i = 0; i < 8; ++i) us[i] = st0 + i < m->tune_us.size() ? m->tune_us[st0 + i] : 0.0f;
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_staged_blocks(scvs_ctx *c, int32_t mesh_id, int32_t *perm, int64_t *row0, int64_t *fp_ptr, int32_t *fp_col,
+                       int32_t *fv_len, uint16_t *lcol) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m) return fail(c, SCVS_ERR_ARG, "bad mesh id");
+    const RowBlocks &rb = m->rb;
+    if (!rb.valid) return fail(c, SCVS_ERR_STATE, "the mesh has no row blocks");
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+      if (dst) SCVS_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    };
+    cp(perm, rb.perm, m->N * sizeof(int32_t));
+    cp(row0, rb.row0, (rb.n_blk + 1) * sizeof(int64_t));
+    cp(fp_ptr, rb.fp_ptr, (rb.n_blk + 1) * sizeof(int64_t));
+    cp(fp_col, rb.fp_col, rb.fp_total * sizeof(int32_t));
+    cp(fv_len, rb.fv_len, rb.n_blk * sizeof(int32_t));
+    cp(lcol, rb.lcol, m->s_nnz * sizeof(uint16_t));
+    SCVS_CUDA(cudaStreamSynchronize(c->stream));
     return SCVS_OK;
   });
 }

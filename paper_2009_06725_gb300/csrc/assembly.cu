@@ -597,6 +597,8 @@ void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, c
   c.launches.n += 4;
   SCVS_CUDA(cudaStreamSynchronize(s));
   SCVS_CUDA(cudaGetLastError());
+  // row blocks of the staged FP32 gather kernels (locality order, footprints)
+  if (c.opts.stage >= 0) build_row_blocks(c, m, 0);
 }
 
 // ---- Neumann (traction) load ---------------------------------------------

@@ -499,17 +499,277 @@ static void arnoldi_config(Ctx &c, int ld, int m_r, int &grid, int &block, size_
   grid = per_sm * c.num_sms;
 }
 
+// ----------------------------------------------------------------- COCR
+// Preconditioned COCR (conjugate orthogonal conjugate residual, Sogabe and
+// Zhang 2007): the conjugate-residual recurrence with the bilinear form
+// x^T y in place of the Hermitian product, valid for a complex symmetric
+// operator (A_hat^T = A_hat, reading C1 of the continuity row) and a complex
+// symmetric preconditioner M ~ A_hat^-1 (the block-diagonal kinds).  Paper
+// Sec. 2.3 remarks that the left-hand side is symmetric; a short recurrence
+// keeps 7 work vectors per system instead of a restart basis.  Per iteration,
+// for every active system s:
+//   q = M Ap,  mu = Ap^T q,  alpha = rho / mu
+//   d += alpha p,  r -= alpha Ap,  z -= alpha q
+//   Az = A_hat z,  rho' = z^T Az,  beta = rho' / rho
+//   p = z + beta p,  Ap = Az + beta Ap
+// with r the (FP32) residual of the correction equation A_hat d = r_0 of the
+// refinement cycle, stopped when ||r|| reaches the cycle's target.
+struct CocrState {
+  double2 *part;      // [n_chunk][2][ld] chunk partials
+  double2 *rho;       // [S] z^T Az
+  double2 *alpha;     // [S]
+  double2 *beta;      // [S]
+  double *target2;    // [S] squared residual target of the cycle
+  int *state;         // [S] 1 = iterating
+  int *iters;         // [S] iterations of the cycle
+  int *n_active;      // [1]
+};
+
+// Chunk partials of (a^T b) (bilinear) in slot 0 and, with NORM, ||c||^2 in
+// slot 1 (.x), for every mode; one thread per (row group, mode).
+template <typename T, bool NORM>
+__global__ void __launch_bounds__(256) k_cocr_dot(const typename cpx<T>::t *__restrict__ a,
+                                                  const typename cpx<T>::t *__restrict__ b,
+                                                  const typename cpx<T>::t *__restrict__ cvec, int ld,
+                                                  int64_t n_chunk, const int64_t *__restrict__ chunk_row0,
+                                                  const int32_t *__restrict__ chunk_rows,
+                                                  const int32_t *__restrict__ chunk_comp,
+                                                  const uint8_t *__restrict__ comp_active, double2 *__restrict__ part) {
+  __shared__ double sh[3][256];
+  const int k = threadIdx.x % ld, rg = threadIdx.x / ld, RG = blockDim.x / ld;
+  for (int64_t ch = blockIdx.x; ch < n_chunk; ch += gridDim.x) {
+    if (!comp_active[chunk_comp[ch]]) continue;  // block-uniform
+    const int64_t r0 = chunk_row0[ch], r1 = r0 + chunk_rows[ch];
+    double sr = 0.0, si = 0.0, sn = 0.0;
+    if (rg < RG)
+      for (int64_t r = r0 + rg; r < r1; r += RG) {
+        const auto x = a[r * ld + k], y = b[r * ld + k];
+        sr = fma((double)x.x, (double)y.x, fma(-(double)x.y, (double)y.y, sr));
+        si = fma((double)x.x, (double)y.y, fma((double)x.y, (double)y.x, si));
+        if (NORM) {
+          const auto z = cvec[r * ld + k];
+          sn = fma((double)z.x, (double)z.x, fma((double)z.y, (double)z.y, sn));
+        }
+      }
+    sh[0][threadIdx.x] = sr;
+    sh[1][threadIdx.x] = si;
+    sh[2][threadIdx.x] = sn;
+    __syncthreads();
+    if (rg == 0) {
+      double tr = 0.0, ti = 0.0, tn = 0.0;
+      for (int g = 0; g < RG; ++g) {  // fixed order
+        tr += sh[0][g * ld + k];
+        ti += sh[1][g * ld + k];
+        tn += sh[2][g * ld + k];
+      }
+      part[(ch * 2 + 0) * ld + k] = make_double2(tr, ti);
+      if (NORM) part[(ch * 2 + 1) * ld + k] = make_double2(tn, 0.0);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double2 sum_chunks(const double2 *__restrict__ part, const int32_t *__restrict__ comp_chunk,
+                                              int comp, int slot, int ld, int k) {
+  double2 v = make_double2(0.0, 0.0);
+  for (int ch = comp_chunk[comp]; ch < comp_chunk[comp + 1]; ++ch) {
+    const double2 p = part[((int64_t)ch * 2 + slot) * ld + k];
+    v.x += p.x;
+    v.y += p.y;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// rho = z^T Az of the cycle's start (one thread per system).
+__global__ void k_cocr_init(CocrState st, const int32_t *__restrict__ comp_chunk, int S, int ld) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  st.iters[s] = 0;
+  if (!st.state[s]) { st.rho[s] = make_double2(0.0, 0.0); return; }
+  st.rho[s] = sum_chunks(st.part, comp_chunk, s / ld, 0, ld, s % ld);
+}
+
+// alpha = rho / (Ap^T q); a vanishing or non-finite denominator stops the system.
+__global__ void k_cocr_alpha(CocrState st, const int32_t *__restrict__ comp_chunk, int S, int ld) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  double2 al = make_double2(0.0, 0.0);
+  if (st.state[s]) {
+    const double2 mu = sum_chunks(st.part, comp_chunk, s / ld, 0, ld, s % ld);
+    al = cdiv(st.rho[s], mu);
+    if (!(isfinite(al.x) && isfinite(al.y)) || (mu.x == 0.0 && mu.y == 0.0)) {
+      st.state[s] = 0;
+      al = make_double2(0.0, 0.0);
+    } else {
+      st.iters[s] += 1;
+    }
+  }
+  st.alpha[s] = al;
+}
+
+// beta = rho' / rho and the convergence test ||r||^2 <= target^2.
+__global__ void k_cocr_beta(CocrState st, const int32_t *__restrict__ comp_chunk, int S, int ld, int last) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  double2 be = make_double2(0.0, 0.0);
+  if (st.state[s]) {
+    const double2 rn = sum_chunks(st.part, comp_chunk, s / ld, 0, ld, s % ld);
+    const double r2 = sum_chunks(st.part, comp_chunk, s / ld, 1, ld, s % ld).x;
+    be = cdiv(rn, st.rho[s]);
+    const bool ok = isfinite(be.x) && isfinite(be.y) && isfinite(r2);
+    if (!ok || r2 <= st.target2[s] || last) {
+      st.state[s] = 0;
+      be = make_double2(0.0, 0.0);
+    } else {
+      st.rho[s] = rn;
+      atomicAdd(st.n_active, 1);
+    }
+  }
+  st.beta[s] = be;
+}
+
+// d += alpha p; r -= alpha Ap; z -= alpha q
+template <typename T>
+__global__ void k_cocr_update1(const double2 *__restrict__ alpha, const int32_t *__restrict__ dof_comp, int ld,
+                               int64_t total, const typename cpx<T>::t *__restrict__ p,
+                               const typename cpx<T>::t *__restrict__ Ap, const typename cpx<T>::t *__restrict__ q,
+                               typename cpx<T>::t *__restrict__ d, typename cpx<T>::t *__restrict__ r,
+                               typename cpx<T>::t *__restrict__ z) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= total) return;
+  const double2 a = alpha[(dof_comp ? dof_comp[f / ld] * ld : 0) + f % ld];
+  if (a.x == 0.0 && a.y == 0.0) return;
+  const T ar = (T)a.x, ai = (T)a.y;
+  const auto pv = p[f], av = Ap[f], qv = q[f];
+  auto dv = d[f], rv = r[f], zv = z[f];
+  dv.x += ar * pv.x - ai * pv.y;  dv.y += ar * pv.y + ai * pv.x;
+  rv.x -= ar * av.x - ai * av.y;  rv.y -= ar * av.y + ai * av.x;
+  zv.x -= ar * qv.x - ai * qv.y;  zv.y -= ar * qv.y + ai * qv.x;
+  d[f] = dv;
+  r[f] = rv;
+  z[f] = zv;
+}
+
+// p = z + beta p; Ap = Az + beta Ap (systems still iterating)
+template <typename T>
+__global__ void k_cocr_update2(const double2 *__restrict__ beta, const int *__restrict__ state,
+                               const int32_t *__restrict__ dof_comp, int ld, int64_t total,
+                               const typename cpx<T>::t *__restrict__ z, const typename cpx<T>::t *__restrict__ Az,
+                               typename cpx<T>::t *__restrict__ p, typename cpx<T>::t *__restrict__ Ap) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= total) return;
+  const int sys = (dof_comp ? dof_comp[f / ld] * ld : 0) + (int)(f % ld);
+  if (!state[sys]) return;
+  const double2 b = beta[sys];
+  const T br = (T)b.x, bi = (T)b.y;
+  const auto zv = z[f], azv = Az[f];
+  auto pv = p[f], av = Ap[f];
+  p[f] = mk<T>(zv.x + br * pv.x - bi * pv.y, zv.y + br * pv.y + bi * pv.x);
+  Ap[f] = mk<T>(azv.x + br * av.x - bi * av.y, azv.y + br * av.y + bi * av.x);
+}
+
+// One refinement cycle of COCR for every system with state[s] = 1: the
+// correction equation A_hat d = r (r = the FP32/FP64 residual in V[0]) is
+// iterated until ||r|| <= max(0.5 tol ||b||, tau_in ||r_0||) or inner_max
+// iterations, then x += d in FP64.  Returns SCVS_OK or SCVS_ERR_TIMEOUT (a
+// grid barrier of the preconditioner gave up).
+template <typename T>
+static int cocr_cycle(Ctx &c, Mesh &m, typename cpx<T>::t *V, typename cpx<T>::t *S_scratch, double2 *part,
+                      int *upd, CocrState cs, const std::vector<int> &state, const std::vector<double> &n2, double tol,
+                      int *h_active, std::vector<int> &iters) {
+  using C = typename cpx<T>::t;
+  const int ld = m.ld, S = m.n_sys();
+  const int64_t total = m.n_dof * ld;
+  const unsigned eb = ceil_div(total, 256), sb = ceil_div(S, 128);
+  C *r = V, *d = r + total, *z = d + total, *Az = z + total, *p = Az + total, *Ap = p + total, *q = Ap + total;
+  const double tau_in = sizeof(T) == 4 ? 1e-5 : 1e-12;
+  std::vector<double> tg2(S, 0.0);
+  for (int s = 0; s < S; ++s)
+    if (state[s]) {
+      const double t = std::max(0.5 * tol * m.bnorm[s], tau_in * std::sqrt(std::max(n2[s], 0.0)));
+      tg2[s] = t * t;
+    }
+  SCVS_CUDA(cudaMemcpyAsync(cs.state, state.data(), S * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(upd, state.data(), S * sizeof(int), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(cs.target2, tg2.data(), S * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaMemsetAsync(d, 0, total * sizeof(C), c.stream));
+  const unsigned db = (unsigned)std::min<int64_t>(m.n_chunk, (int64_t)c.num_sms * 8);
+  const double vb = (double)total * sizeof(C);
+  auto dot = [&](const C *a, const C *b, const C *nv) {
+    KScope ks(c, KC_ARNOLDI, (nv ? 3 : 2) * vb);
+    if (nv)
+      k_cocr_dot<T, true><<<db, 256, 0, c.stream>>>(a, b, nv, ld, m.n_chunk, m.chunk_row0, m.chunk_rows, m.chunk_comp,
+                                                    m.comp_active, part);
+    else
+      k_cocr_dot<T, false><<<db, 256, 0, c.stream>>>(a, b, nullptr, ld, m.n_chunk, m.chunk_row0, m.chunk_rows,
+                                                     m.chunk_comp, m.comp_active, part);
+    count_launch(c);
+  };
+  apply_precond<T>(c, m, r, z, S_scratch, nullptr);
+  apply_saddle<T>(c, m, z, Az);
+  SCVS_CUDA(cudaMemcpyAsync(p, z, total * sizeof(C), cudaMemcpyDeviceToDevice, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(Ap, Az, total * sizeof(C), cudaMemcpyDeviceToDevice, c.stream));
+  dot(z, Az, nullptr);
+  k_cocr_init<<<sb, 128, 0, c.stream>>>(cs, m.comp_chunk, S, ld);
+  count_launch(c);
+  const int inner_max = std::max(1, c.opts.inner_max);
+  for (int it = 0; it < inner_max; ++it) {
+    apply_precond<T>(c, m, Ap, q, S_scratch, nullptr);
+    dot(Ap, q, nullptr);
+    k_cocr_alpha<<<sb, 128, 0, c.stream>>>(cs, m.comp_chunk, S, ld);
+    {
+      KScope ks(c, KC_ARNOLDI, 9 * vb);
+      k_cocr_update1<T><<<eb, 256, 0, c.stream>>>(cs.alpha, m.dof_comp, ld, total, p, Ap, q, d, r, z);
+    }
+    c.launches.n += 2;
+    apply_saddle<T>(c, m, z, Az);
+    dot(z, Az, r);
+    SCVS_CUDA(cudaMemsetAsync(cs.n_active, 0, sizeof(int), c.stream));
+    k_cocr_beta<<<sb, 128, 0, c.stream>>>(cs, m.comp_chunk, S, ld, it + 1 == inner_max ? 1 : 0);
+    {
+      KScope ks(c, KC_ARNOLDI, 6 * vb);
+      k_cocr_update2<T><<<eb, 256, 0, c.stream>>>(cs.beta, cs.state, m.dof_comp, ld, total, z, Az, p, Ap);
+    }
+    c.launches.n += 2;
+    SCVS_CUDA(cudaMemcpyAsync(h_active, cs.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    SCVS_CUDA(cudaStreamSynchronize(c.stream));
+    if (*h_active == 0) break;
+  }
+  int gerr = 0;
+  SCVS_CUDA(cudaMemcpyAsync(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(iters.data(), cs.iters, S * sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  if (gerr) {
+    SCVS_CUDA(cudaMemsetAsync(c.gsync, 0, sizeof(GridSync), c.stream));
+    SCVS_CUDA(cudaStreamSynchronize(c.stream));
+    return SCVS_ERR_TIMEOUT;
+  }
+  {
+    KScope ks(c, KC_VECTOR, (double)total * (32 + sizeof(C)));
+    k_add_to_x<T><<<eb, 256, 0, c.stream>>>(d, upd, ld, m.dof_comp, total, m.x);
+    count_launch(c);
+  }
+  return SCVS_OK;
+}
+
 template <typename T>
 static int solve_mesh_t(Ctx &c, Mesh &m) {
   using C = typename cpx<T>::t;
   const int ld = m.ld, m_r = std::max(1, std::min(64, c.opts.restart));
   const int S = m.n_sys(), nm = m.m;
   const int64_t total = m.n_dof * ld;
+  const bool cocr = c.opts.krylov == SCVS_KRYLOV_COCR;
   Work<T> wk;
   wk.s = c.stream;
   wk.pool = c.pool;
-  wk.V = wk.template get<C>((size_t)(m_r + 1) * total);
-  wk.Z = wk.template get<C>((size_t)m_r * total);  // flexible GMRES: z_j = P^-1 v_j kept
+  // COCR: 7 work vectors (r, d, z, Az, p, Ap, q); flexible GMRES: the basis V and z_j = P^-1 v_j
+  wk.V = wk.template get<C>((size_t)(cocr ? 7 : m_r + 1) * total);
+  wk.Z = cocr ? nullptr : wk.template get<C>((size_t)m_r * total);
   wk.W = wk.template get<C>(total);
   wk.S = wk.template get<C>(precond_scratch_elems(m));
   int grid, block;
@@ -530,6 +790,17 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   wk.kdim = wk.template get<int>(S);
   wk.upd = wk.template get<int>(S);
   wk.n_active = wk.template get<int>(1);
+  CocrState cst{};
+  if (cocr) {
+    cst.part = wk.part;
+    cst.rho = wk.template get<double2>(S);
+    cst.alpha = wk.template get<double2>(S);
+    cst.beta = wk.template get<double2>(S);
+    cst.target2 = wk.template get<double>(S);
+    cst.state = wk.state;
+    cst.iters = wk.kdim;
+    cst.n_active = wk.n_active;
+  }
 
   ArnArgs<T> aa{};
   aa.rows = m.n_dof; aa.ld = ld; aa.m_r = m_r; aa.n_comp = m.n_comp; aa.V = wk.V; aa.w = wk.W; aa.vstride = total;
@@ -630,6 +901,15 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       for (int s = 0; s < S; ++s)
         if (!done[s]) ca[s / ld] = 1;
       SCVS_CUDA(cudaMemcpyAsync(m.comp_active, ca.data(), m.n_comp, cudaMemcpyHostToDevice, c.stream));
+    }
+    if (cocr) {  // short-recurrence correction of every active system, then the next true residual
+      for (int s = 0; s < S; ++s) state[s] = done[s] ? 0 : 1;
+      std::vector<int> its(S, 0);
+      const int rc = cocr_cycle<T>(c, m, wk.V, wk.S, wk.part, wk.upd, cst, state, n2, tol, h_active, its);
+      if (rc != SCVS_OK) return rc;
+      for (int s = 0; s < S; ++s)
+        if (state[s]) { rep(s).iterations += its[s]; rep(s).cycles += 1; }
+      continue;
     }
     // 2. cycle set-up: active systems, targets, first scale, Hessenberg reset
     std::vector<double> tgt(S, 0.0), rs(S, 0.0);

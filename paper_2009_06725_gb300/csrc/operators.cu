@@ -20,30 +20,11 @@
 #include <type_traits>
 #include "scvs_internal.h"
 #include "vecops.cuh"
+#include "opargs.cuh"
 
 namespace scvs {
 
-template <typename T> struct SaddleArgs {
-  int64_t N, P;
-  int ld;
-  const int64_t *s_ptr;
-  const int32_t *s_col;
-  const int32_t *g_len;
-  const int64_t *g_ptr;
-  const T *Kv, *Mv, *Dv, *DTv;
-  int64_t g_nnz, gt_nnz;
-  const uint8_t *dirmask;  // null: no identity rows
-  const double *omega;
-  double rho, mu;
-  const int32_t *dof_comp;      // null: one component
-  const uint8_t *comp_active;   // rows of inactive components are skipped
-  int tile;                     // row tile (SCVS_ROW_LOOP)
-};
 
-// true if the row's component has no active system (multi-component meshes)
-__device__ __forceinline__ bool row_idle(const int32_t *dof_comp, const uint8_t *comp_active, int64_t dof) {
-  return dof_comp && !comp_active[dof_comp[dof]];
-}
 
 template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
@@ -195,6 +176,10 @@ void launch_saddle(Ctx &c, const Mesh &m, const SaddleArgs<T> &a, const typename
                    typename cpx<T>::t *y) {
   KScope ks(c, sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM64, saddle_bytes(m, sizeof(T)));
   if constexpr (sizeof(T) == 4) {
+    if (m.st_spmm && a.dirmask && staged_ok(c, m, m.st_spmm, true, x)) {
+      launch_saddle_staged(c, m, a, x, y, m.st_spmm);
+      return;
+    }
     const int mpl = m.mpl_spmm ? m.mpl_spmm : default_mpl<T>(m.ld);
     SCVS_DISPATCH_SHAPE(m.ld, mpl, {
       const int gpb = 256 / L;
@@ -405,44 +390,7 @@ __global__ void k_residual_finish(const double2 *__restrict__ b, const double2 *
 }
 
 // ----------------------------------------------------- preconditioner
-struct PcArgs {
-  int64_t N, P;
-  int ld;
-  const int64_t *s_ptr;
-  const int32_t *s_col;
-  const int32_t *g_len;
-  const int64_t *g_ptr;
-  const void *Kv, *Mv;         // masked velocity-block values (T)
-  const void *Mpv, *Lpv;       // P1 mass, Laplacian (outlet rows identity) values (T), Q pattern
-  const double *ms_diag, *ks_diag, *mp_diag, *lp_diag;
-  const uint8_t *dirmask, *outmask;
-  const double *omega;
-  double rho, mu;
-  // coarse (P1) velocity level
-  const void *Kcv, *Mcv;       // masked P1 stiffness / mass (T), Q pattern
-  const double *k1_diag;
-  const int32_t *edge_ends;
-  const int64_t *v2e_ptr;
-  const int32_t *v2e;
-  // diagonals and per-mode scalars in the kernel's precision T
-  const void *ksd, *msd, *mpd, *lpd, *k1d;
-  const void *wabs, *wrho;   // [ld] |omega_k| rho, omega_k rho
-  const int32_t *dof_comp;   // null: one component
-  const uint8_t *comp_active;
-  int tile;                  // row tile of the gather kernels (SCVS_ROW_LOOP)
-  const void *Dv;            // G block values (T), [dim][g_nnz] (block-triangular form)
-  int64_t g_nnz;
-};
 
-// The velocity block of mode k, A_u = mu K_s + j omega rho M_s, is preconditioned
-// through the real SPD shift A_r = mu K_s + |omega| rho M_s: the spectrum of
-// A_r^-1 A_u lies on the arc from j to 1 (|z| >= 1/sqrt 2) for every omega, and
-// A_r has a real positive Jacobi-scaled spectrum on which a Chebyshev
-// polynomial on a real interval is effective.  vel_dinv is 1 / diag(A_r).
-template <typename T>
-__device__ __forceinline__ T vel_dinv(const PcArgs &a, int64_t A, int k) {
-  return T(1) / ((T)a.mu * ((const T *)a.ksd)[A] + ((const T *)a.wabs)[k] * ((const T *)a.msd)[A]);
-}
 
 // Step 0 of the velocity polynomial (elementwise over elements [0, f1) of the
 // block), optionally rescaling r by rscale[k] first (written back: lazy
@@ -481,18 +429,6 @@ __global__ void k_pc_step0(const PcArgs a, typename cpx<T>::t *r, const double *
   }
 }
 
-// Coefficients of one Chebyshev step i >= 1,
-//   z_next = z + alpha (z - z_prev) + beta D^-1 (r - A z),
-// of the velocity polynomial (k_pc_cheb: per-mode alpha_u, beta_u) or of the
-// two pressure polynomials (P1 mass and P1 Laplacian, stepped together by
-// k_pressure_solve).  z_prev is overwritten by z_next (each row reads its own
-// z_prev first).
-struct ChebCoef {
-  const double *alpha_u, *beta_u;  // [ld] per mode (velocity)
-  double alpha_m, beta_m, alpha_l, beta_l;
-  int do_u, do_m, do_l;
-  int prev_zero_u, prev_zero_m, prev_zero_l;
-};
 
 // One Chebyshev step of both pressure polynomials (P1 mass, P1 Laplacian with
 // p = 0 on the outlet) on pressure row B, for the lane's modes.
@@ -1259,7 +1195,7 @@ constexpr double CHEB_RATIO_U = 30.0, CHEB_RATIO_SMOOTH = 12.0, CHEB_RATIO_C = 3
                  CHEB_RATIO_L = 3000.0, CHEB_TOP = 1.10;
 
 template <typename T>
-static PcArgs pc_args(const Mesh &m) {
+PcArgs pc_args(const Mesh &m) {
   const bool f = sizeof(T) == 4;
   return PcArgs{m.N, m.P, m.ld, m.s_ptr, m.s_col, m.g_len, m.g_ptr,
                 f ? (const void *)m.Ks_f : (const void *)m.Ks_m, f ? (const void *)m.Ms_f : (const void *)m.Ms_m,
@@ -1334,6 +1270,12 @@ static void cheb_launch(Ctx &c, const Mesh &m, const PcArgs &a, const ChebCoef &
   const double cs = 2.0 * sizeof(T), vb = (double)m.dim * m.N * m.ld * cs;
   KScope ksc(c, KC_CHEB_FINE,
              (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + vb * (cc.prev_zero_u ? 3 : 4));
+  if constexpr (sizeof(T) == 4) {
+    if (m.st_cheb && staged_ok(c, m, m.st_cheb, false, ucur)) {
+      launch_cheb_staged(c, m, a, cc, r, ucur, uprev, m.st_cheb);
+      return;
+    }
+  }
   auto body = [&](auto mpl_c, auto l_c) {
     constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
     const int gpb = 256 / L;
@@ -1826,6 +1768,13 @@ static typename cpx<T>::t *vel_cycle(Ctx &c, const Mesh &m, const PcArgs &a, con
     // fine residual, coarse solve (restriction + Chebyshev), prolongation
     {
       KScope ks(c, KC_CHEB_FINE, (double)m.s_nnz * (4 + 2 * sizeof(T)) + (double)(m.N + 1) * 8 + m.N + 3 * vb);
+      bool staged = false;
+      if constexpr (sizeof(T) == 4) {
+        if (m.st_cheb && staged_ok(c, m, m.st_cheb, false, ucur)) {
+          launch_vel_residual_staged(c, m, a, ru, ucur, uprev, m.st_cheb);
+          staged = true;
+        }
+      }
       auto body = [&](auto mpl_c, auto l_c) {
         constexpr int MPL = decltype(mpl_c)::value, L = decltype(l_c)::value;
         const int gpb = 256 / L;
@@ -1835,13 +1784,15 @@ static typename cpx<T>::t *vel_cycle(Ctx &c, const Mesh &m, const PcArgs &a, con
         else
           k_vel_residual<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, ru, ucur, uprev);
       };
-      if constexpr (sizeof(T) == 4) {
-        const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
-        SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
-      } else {
-        SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+      if (!staged) {
+        if constexpr (sizeof(T) == 4) {
+          const int mpl = m.mpl_cheb ? m.mpl_cheb : default_mpl<T>(m.ld);
+          SCVS_DISPATCH_SHAPE(m.ld, mpl, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+        } else {
+          SCVS_DISPATCH_LD(T, m.ld, body(std::integral_constant<int, MPL>{}, std::integral_constant<int, L>{}));
+        }
+        count_launch(c);
       }
-      count_launch(c);
     }
     C *zres = coarse_solve<T>(c, m, a, t, uprev, rc, zc);
     {
@@ -2355,6 +2306,7 @@ void autotune_shapes(Ctx &c, Mesh &m) {
   cc.prev_zero_u = 1;
   int best_s[2] = {0, 0}, best_c[2] = {0, 0};
   float tb_s = 1e30f, tb_c = 1e30f;
+  m.st_spmm = m.st_cheb = 0;
   for (int mi = 0; mi < 3; ++mi) {
     const int mpl = 1 << mi;
     if (!shape_valid(m.ld, mpl)) continue;
@@ -2376,6 +2328,32 @@ void autotune_shapes(Ctx &c, Mesh &m) {
   m.tile_spmm = best_s[1];
   m.mpl_cheb = best_c[0];
   m.tile_cheb = best_c[1];
+  // staged (shared-memory) variants: mode chunks 4, 8, 16, 32 of the row blocks
+  int st_s = 0, st_c = 0;
+  m.tune_us.resize(m.tune_us.size() + 8, 0.0f);
+  const size_t st0 = (size_t)2 * 3 * NT;
+  if (c.opts.stage >= 0) {
+    for (int qi = 0; qi < 4; ++qi) {
+      const int mc = 4 << qi;
+      if (mc > m.ld) break;
+      if (staged_ok(c, m, mc, true, x)) {
+        m.st_spmm = mc;
+        const float ts = time_it([&]() { apply_saddle<float>(c, m, x, y); });
+        m.tune_us[st0 + qi] = ts;
+        if (ts < tb_s) { tb_s = ts; st_s = mc; }
+      }
+      if (staged_ok(c, m, mc, false, x)) {
+        m.st_cheb = mc;
+        const PcArgs pa = pc_args<float>(m);
+        const float tc = time_it([&]() { cheb_launch<float>(c, m, pa, cc, x, x, y); });
+        m.tune_us[st0 + 4 + qi] = tc;
+        if (tc < tb_c) { tb_c = tc; st_c = mc; }
+      }
+    }
+  }
+  m.st_spmm = st_s;
+  m.st_cheb = st_c;
+  if (c.opts.stage > 0) m.st_spmm = m.st_cheb = c.opts.stage;  // forced mode chunk
   c.timers.on = timers_on;
   SCVS_CUDA(cudaEventDestroy(e0));
   SCVS_CUDA(cudaEventDestroy(e1));

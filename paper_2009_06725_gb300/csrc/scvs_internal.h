@@ -95,6 +95,25 @@ struct PcTables {
   int cs_singular = 0;               // (block, mode) pairs whose coarse matrix was singular (correction off)
 };
 
+// Row blocks of a mesh for the staged gather kernels (blocks.cu): rows in a
+// locality order cut into blocks of about `budget` nonzeros, the distinct
+// columns ("footprint") of every block and every nonzero's index in it.
+constexpr int RB_DEFAULT_BUDGET = 768;
+constexpr size_t STAGE_SMEM_MAX = 200 * 1024;
+struct RowBlocks {
+  bool valid = false;
+  int budget = 0, fp_max = 0, fv_max = 0;
+  int64_t n_blk = 0, fp_total = 0;
+  int32_t *perm = nullptr;     // [N]
+  int64_t *row0 = nullptr;     // [n_blk + 1]
+  int64_t *fp_ptr = nullptr;   // [n_blk + 1]
+  int32_t *fp_col = nullptr;   // [fp_total]
+  int32_t *fv_len = nullptr;   // [n_blk]
+  uint16_t *lcol = nullptr;    // [s_nnz]
+  // the arrays live in the mesh arena (released with the mesh)
+  void release(cudaStream_t) { *this = RowBlocks{}; }
+};
+
 // One mesh and the state of its modes.
 //
 // Patterns: S (P2 x P2) is stored once; because vertex nodes carry the
@@ -171,6 +190,8 @@ struct Mesh {
   std::vector<double> lam_c;     // [ld] same for the P1 coarse velocity operator
   double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
   PcTables pc;
+  RowBlocks rb;                          // staged-gather row blocks (FP32 path)
+  int st_spmm = 0, st_cheb = 0;          // staged mode chunk of the SpMM / fine Chebyshev kernels (0: unstaged)
   int mpl_spmm = 0, mpl_cheb = 0;       // autotuned row-group shapes (0: default)
   int tile_spmm = 0, tile_cheb = 0;     // autotuned row tiles (0: default)
   std::vector<float> tune_us;            // measured candidates: [spmm mpl=1,2,4, cheb mpl=1,2,4] (us, 0 = n/a)
@@ -258,7 +279,7 @@ struct Ctx {
   GuessModel guess;
   // autotuned launch shapes by mesh size (dim, N, P, S nonzeros, G nonzeros,
   // mode stride, components): the timings depend on the pattern's size, not its values
-  struct TuneRec { int mpl_spmm, tile_spmm, mpl_cheb, tile_cheb; std::vector<float> us; };
+  struct TuneRec { int mpl_spmm, tile_spmm, mpl_cheb, tile_cheb, st_spmm, st_cheb; std::vector<float> us; };
   std::map<std::vector<int64_t>, TuneRec> tune_cache;
   cudaMemPool_t pool = nullptr;  // every stream-ordered allocation of the context
 };
@@ -279,6 +300,7 @@ struct KScope {
 void build_mesh(Ctx &c, Mesh &m, const double *xyz_dev, const int32_t *conn_dev, const uint8_t *tag_dev);
 int64_t set_neumann(Ctx &c, Mesh &m, const double2 *h_host);  // returns the number of Neumann faces
 void scan_exclusive(Ctx &c, const int32_t *in, int64_t *out, int64_t n);
+void build_row_blocks(Ctx &c, Mesh &m, int budget);  // blocks.cu
 
 // ---- operators.cu
 template <typename T>

@@ -24,6 +24,7 @@ SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
 SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG, SCVS_PC_TRI_PMG_CS = 0, 1, 2, 3, 4
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP, SCVS_GUESS_CURRENT = 0, 1, 2
+SCVS_KRYLOV_FGMRES, SCVS_KRYLOV_COCR = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3
 SCVS_KC_COUNT = 11
 SCVS_RECON_STATIC_MAX = 8192
@@ -42,7 +43,8 @@ class scvs_opts(C.Structure):
                 ("precond", C.c_int32), ("cheb_u", C.c_int32), ("cheb_m", C.c_int32),
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
                 ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p),
-                ("schur_agg", C.c_int32), ("reserved", C.c_int32)]
+                ("schur_agg", C.c_int32), ("stage", C.c_int32), ("krylov", C.c_int32),
+                ("inner_max", C.c_int32)]
 
 
 class scvs_mode_report(C.Structure):
@@ -115,6 +117,8 @@ SIGNATURES = {
     "scvs_mlp_gradient_dev": (_I32, [_P, _P, _P, _I64, _P, C.POINTER(_D)]),
     "scvs_mlp_adam_step": (_I32, [_P, _D]),
     "scvs_tuned_shapes": (_I32, [_P, _I32, _P, _P]),
+    "scvs_staged_info": (_I32, [_P, _I32, _P, _P]),
+    "scvs_staged_blocks": (_I32, [_P, _I32, _P, _P, _P, _P, _P, _P]),
     "scvs_kernel_timers": (_I32, [_P, _I32]),
     "scvs_kernel_times": (_I32, [_P, _I32, _P, _P, _P]),
     "scvs_set_neumann": (_I32, [_P, _I32, _P, C.POINTER(_I64)]),
@@ -446,6 +450,36 @@ def scvs_mlp_gradient_dev(ctx, x_dev, t_dev, batch):
 
 def scvs_mlp_adam_step(ctx, lr):
     return _check(ctx, lib().scvs_mlp_adam_step(ctx, lr))
+
+
+def scvs_staged_info(ctx, mesh_id):
+    """Row blocks and staged-gather choice of a mesh (see include/scvs.h)."""
+    info = np.zeros(10, dtype=np.int64)
+    us = np.zeros(8, dtype=np.float32)
+    _check(ctx, lib().scvs_staged_info(ctx, mesh_id, _ptr(info), _ptr(us)))
+    keys = ("valid", "n_blk", "budget", "fp_max", "fv_max", "fp_total", "st_spmm", "st_cheb", "runs_spmm",
+            "runs_cheb")
+    out = {k: int(v) for k, v in zip(keys, info)}
+    for k in ("valid", "runs_spmm", "runs_cheb"):
+        out[k] = bool(out[k])
+    out["spmm_us"] = [float(v) for v in us[:4]]
+    out["cheb_us"] = [float(v) for v in us[4:]]
+    return out
+
+
+def scvs_staged_blocks(ctx, mesh_id, n_nodes, s_nnz):
+    """Host copies of the row blocks: perm, row0, fp_ptr, fp_col, fv_len, lcol."""
+    info = scvs_staged_info(ctx, mesh_id)
+    nb = info["n_blk"]
+    perm = np.empty(n_nodes, dtype=np.int32)
+    row0 = np.empty(nb + 1, dtype=np.int64)
+    fp_ptr = np.empty(nb + 1, dtype=np.int64)
+    fp_col = np.empty(max(info["fp_total"], 1), dtype=np.int32)
+    fv_len = np.empty(nb, dtype=np.int32)
+    lcol = np.empty(s_nnz, dtype=np.uint16)
+    _check(ctx, lib().scvs_staged_blocks(ctx, mesh_id, _ptr(perm), _ptr(row0), _ptr(fp_ptr), _ptr(fp_col),
+                                         _ptr(fv_len), _ptr(lcol)))
+    return dict(perm=perm, row0=row0, fp_ptr=fp_ptr, fp_col=fp_col[:info["fp_total"]], fv_len=fv_len, lcol=lcol)
 
 
 def scvs_tuned_shapes(ctx, mesh_id):

@@ -169,3 +169,41 @@ def uneven_pipes(n_meshes=48, n_modes=16, seed=0, n_min=20_000, n_max=400_000, s
                            seed=seed + 1 + i)
         out.append(wl)
     return out
+
+
+def traction_inlet(mesh, omegas, hx, rho, mu, neumann_tag):
+    """The paper's validation setting (Sec. 3.2 channel, Sec. 3.4 pipe): the
+    inlet carries a uniform streamwise traction h = (hx, 0[, 0]) for every mode
+    (a cosine in time for omega > 0) instead of a velocity, the walls are
+    no-slip and the outlet traction-free.  Inlet nodes are retagged with
+    `neumann_tag` (wall nodes stay Dirichlet); returns the workload with zero
+    Dirichlet data and the nodal tractions h [m][N][d] (input data only: the
+    boundary integral is the solver's or the oracle's business)."""
+    tag = mesh["tag"].copy()
+    inl = (tag & meshes.INLET) != 0
+    tag[inl] = (tag[inl] & ~np.uint8(meshes.INLET)) | np.uint8(neumann_tag)
+    mesh = dict(mesh, tag=tag)
+    d = mesh["dim"]
+    walls = np.flatnonzero((tag & meshes.WALL) != 0)
+    N = mesh["xyz"].shape[0]
+    m = len(omegas)
+    h = np.zeros((m, N, d), dtype=np.complex128)
+    h[:, :, 0] = hx
+    return dict(mesh=mesh, omegas=np.asarray(omegas, dtype=np.float64), rho=rho, mu=mu, dir_nodes=walls,
+                g=np.zeros((m, walls.size, d), dtype=np.complex128), h=h, hx=hx)
+
+
+def paper_channel(omegas, rho=1.0, mu=0.01, hx=1.0, neumann_tag=8):
+    """The paper's 2D channel (Sec. 3.2): aspect ratio 5, 882 P2 triangles,
+    1,881 nodes and 4,262 dofs, i.e. 49 x 9 quads of [0, 5] x [-0.5, 0.5]
+    split in two; traction inlet."""
+    mesh = meshes.channel2d(49, 9, length=5.0, half_height=0.5)
+    return traction_inlet(mesh, omegas, hx, rho, mu, neumann_tag)
+
+
+def paper_pipe(target_nodes, omegas, rho=1.0, mu=1.0, hx=1.0, neumann_tag=8, seed=0):
+    """The paper's pipe (Sec. 3.4): L/R = 15, R = 1, traction inlet, on an
+    O-grid mesh of about target_nodes P2 nodes (QM1-QM4: 37,469 / 70,872 /
+    133,645 / 225,610 nodes), no jitter."""
+    mesh = meshes.pipe_for_nodes(target_nodes, radius=1.0, length=15.0, jitter=0.0, seed=seed)
+    return traction_inlet(mesh, omegas, hx, rho, mu, neumann_tag)
