@@ -121,10 +121,11 @@ typedef struct {
                         0 or default: 96); aggregates are grown to ceil(vertices / schur_agg) vertices, so a
                         component may end with somewhat more or fewer */
   int32_t stage;     /* staged gathers of the FP32 SpMM and fine Chebyshev kernels (row blocks of compact
-                        footprint, the footprint copied into shared memory by TMA bulk copies): 0 (default):
-                        the autotuner times them beside the unstaged shapes and keeps the fastest; -1: never
-                        (no row blocks are built); 4, 8, 16 or 32: always, with that many modes per block
-                        (where the footprint fits shared memory) */
+                        footprint, the footprint copied into shared memory by TMA bulk copies or cp.async):
+                        -1 (default): never (no row blocks are built; on the benchmark pipe the staged kernels
+                        measured 3-5x slower than the L1-cached gathers); 0: the autotuner times them beside
+                        the unstaged shapes and keeps the fastest; 4, 8, 16 or 32: always, with that many
+                        modes per block (where the footprint fits shared memory) */
   int32_t krylov;    /* SCVS_KRYLOV_FGMRES (default): restarted flexible GMRES(restart); SCVS_KRYLOV_COCR:
                         preconditioned COCR, a short recurrence for complex symmetric systems (7 work vectors
                         per system), valid with the symmetric block-diagonal preconditioner kinds */

@@ -257,6 +257,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->schur_agg = 96;
   o->krylov = SCVS_KRYLOV_FGMRES;
   o->inner_max = 400;
+  o->stage = -1;
 }
 
 int scvs_create(scvs_ctx **out, const scvs_opts *opts) {

@@ -39,7 +39,7 @@ def test_row_blocks_match_their_definition(case):
     name, wl = case
     mesh = wl["mesh"]
     N, P = mesh["xyz"].shape[0], mesh["n_vertices"]
-    s, mid = open_workload(wl)
+    s, mid = open_workload(wl, stage=0)
     with s:
         info = scvs.scvs_staged_info(s.ctx, mid)
         assert info["valid"] and info["n_blk"] >= 2
@@ -123,7 +123,7 @@ def test_staged_solve_matches_oracle(stage):
 
 def test_autotuner_times_the_staged_variants():
     wl = _cases()["pipe"]
-    s, mid = open_workload(wl)
+    s, mid = open_workload(wl, stage=0)
     with s:
         info = scvs.scvs_staged_info(s.ctx, mid)
     assert info["valid"]

@@ -37,6 +37,7 @@ def test_default_options():
     o = scvs.scvs_default_opts()
     assert o.tol == 1e-8 and o.restart == 30 and o.precision == scvs.SCVS_PREC_MIXED
     assert o.cheb_u >= 1 and o.max_cycles >= 1
+    assert o.stage == -1 and o.krylov == scvs.SCVS_KRYLOV_FGMRES and o.inner_max == 400
 
 
 def test_header_constants_match_binding():
