@@ -144,6 +144,46 @@ def element_matrices(xyz, conn, dim):
     return Me, Ke, De
 
 
+def curved_elements(xyz, conn, dim, rtol=1e-12):
+    """Elements whose edge nodes are not at their edge midpoints (curved,
+    isoparametric P2 geometry; the paper projects boundary edge nodes onto
+    the curved wall, Sec. 3.1)."""
+    nv = dim + 1
+    out = np.zeros(conn.shape[0], dtype=bool)
+    for j, (a, b) in enumerate(_edges(dim)):
+        xa, xb, xm = xyz[conn[:, a]], xyz[conn[:, b]], xyz[conn[:, nv + j]]
+        dev = np.linalg.norm(xm - 0.5 * (xa + xb), axis=1)
+        out |= dev > rtol * np.linalg.norm(xb - xa, axis=1)
+    return out
+
+
+ISO_QUAD = 6  # points per direction of the collapsed rule on curved elements
+
+
+def element_matrices_iso(xyz, conn, dim, n=ISO_QUAD):
+    """Element matrices of isoparametric P2 elements (x(xi) = sum_a x_a phi_a(xi)):
+    at every quadrature point J = sum_a x_a grad_xi phi_a^T, physical gradients
+    grad_x phi_a = J^-T grad_xi phi_a, and
+    M_e[a,b] = sum_q w_q |J| phi_a phi_b,  K_e[a,b] = sum_q w_q |J| grad_x phi_a . grad_x phi_b,
+    D_e[c,a,b] = -sum_q w_q |J| d_c phi_a psi_b  (psi the P1 basis of the reference
+    simplex, mapped with the element).  Rejects non-positive |J| at a point."""
+    pts, w = simplex_rule(dim, n)
+    phi, dphi = p2_basis(dim, pts)            # [Q][nl], [Q][nl][dim]
+    psi, _ = p1_basis(dim, pts)               # [Q][nv]
+    X = xyz[conn]                             # [E][nl][dim]
+    J = np.einsum("ear,qai->eqri", X, dphi)   # [E][Q][dim][dim]: dx_r / dxi_i
+    det = np.linalg.det(J)
+    if np.any(det <= 0.0):
+        raise ValueError("element with non-positive Jacobian at a quadrature point")
+    Jinv = np.linalg.inv(J)                   # [E][Q][i][r]
+    G = np.einsum("qai,eqic->eqac", dphi, Jinv)  # grad_x phi_a: sum_i dphi/dxi_i (J^-1)_ic
+    wd = det * w[None, :]                     # [E][Q]
+    Me = np.einsum("eq,qa,qb->eab", wd, phi, phi)
+    Ke = np.einsum("eq,eqac,eqbc->eab", wd, G, G)
+    De = -np.einsum("eq,eqac,qb->ecab", wd, G, psi)
+    return Me, Ke, De
+
+
 # --------------------------------------------------------------- assembly
 
 def patterns(n_nodes, n_vertices, conn, dim):
@@ -179,10 +219,22 @@ def assemble(mesh):
     """Global real matrices: Ms, Ks (N x N), D = [D_x, D_y(, D_z)] (N x P each).
 
     Sums element contributions over elements (Eq. LS_construction); explicit
-    zeros are kept so every matrix has exactly the structural pattern."""
+    zeros are kept so every matrix has exactly the structural pattern.
+    Straight-sided elements use the exact reference integrals; elements with
+    displaced edge nodes (curved boundaries, Sec. 3.1) the isoparametric map
+    and quadrature (element_matrices_iso)."""
     xyz, conn, dim, P = mesh["xyz"], mesh["conn"].astype(np.int64), mesh["dim"], mesh["n_vertices"]
     N = xyz.shape[0]
-    Me, Ke, De = element_matrices(xyz, conn, dim)
+    curved = curved_elements(xyz, conn, dim)
+    if curved.any():  # isoparametric elements where the geometry is curved
+        Me, Ke, De = element_matrices(xyz, conn, dim) if not curved.all() else (None, None, None)
+        Mi, Ki, Di = element_matrices_iso(xyz, conn[curved], dim)
+        if Me is None:
+            Me, Ke, De = Mi, Ki, Di
+        else:
+            Me[curved], Ke[curved], De[curved] = Mi, Ki, Di
+    else:
+        Me, Ke, De = element_matrices(xyz, conn, dim)
     nl = conn.shape[1]
     nv = dim + 1
     rows = np.repeat(conn, nl, axis=1).ravel()

@@ -108,6 +108,110 @@ def channel2d(nx=32, ny=8, length=4.0, half_height=0.5):
                 name=f"channel {nx}x{ny}", length=length, half_height=H)
 
 
+def _structured_2d(vxyz, nx, ny):
+    """Triangles of an (nx+1) x (ny+1) vertex lattice (x-fastest ids), every
+    quad cut along its (i,j)->(i+1,j+1) diagonal, positively oriented."""
+    vid = lambda i, j: j * (nx + 1) + i
+    tris = []
+    for j in range(ny):
+        for i in range(nx):
+            v00, v10, v11, v01 = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            tris.append((v00, v10, v11))
+            tris.append((v00, v11, v01))
+    return _orient_positive(vxyz, np.array(tris, dtype=np.int64))
+
+
+def _lattice_key(nx):
+    def key(lo, hi, mid):
+        # edge nodes numbered by their lattice position (i + i', j + j'), x-fastest
+        i = lo % (nx + 1) + hi % (nx + 1)
+        j = lo // (nx + 1) + hi // (nx + 1)
+        return (i, j)
+    return key
+
+
+def annulus2d(n_r=4, n_t=16, r1=1.0, r2=2.0, theta=0.5 * np.pi, curved=True):
+    """Annular sector r1 <= r <= r2, 0 <= t <= theta (a curved channel):
+    vertices on the polar lattice, straight-sided P2 edge nodes at edge
+    midpoints except, with ``curved``, those of edges on the circles r = r1 and
+    r = r2, projected radially onto the circle (isoparametric boundary, the
+    paper's Sec. 3.1 node projection).  Walls r = r1, r2; inlet t = 0; outlet
+    t = theta."""
+    rr = np.linspace(r1, r2, n_r + 1)
+    tt = np.linspace(0.0, theta, n_t + 1)
+    R, T = np.meshgrid(rr, tt, indexing="ij")  # [radius j][angle i]: ids angle-fastest
+    R, T = R.ravel(), T.ravel()
+    vxyz = np.stack([R * np.cos(T), R * np.sin(T)], axis=1)
+    simp = _structured_2d(vxyz, n_t, n_r)
+    xyz, conn, ends = _add_p2_nodes(vxyz, simp, _lattice_key(n_t))
+    P = vxyz.shape[0]
+    vr = np.hypot(vxyz[:, 0], vxyz[:, 1])
+    vt = np.arctan2(vxyz[:, 1], vxyz[:, 0])
+    eps = 1e-9
+    vtag = np.zeros(P, dtype=np.uint8)
+    vtag[(np.abs(vr - r1) < eps) | (np.abs(vr - r2) < eps)] |= WALL
+    vtag[np.abs(vt) < eps] |= INLET
+    vtag[np.abs(vt - theta) < eps] |= OUTLET
+    tag = np.zeros(xyz.shape[0], dtype=np.uint8)
+    tag[:P] = vtag
+    ra, rb = vr[ends[:, 0]], vr[ends[:, 1]]
+    same_circle = (np.abs(ra - rb) < eps) & ((np.abs(ra - r1) < eps) | (np.abs(ra - r2) < eps))
+    same_ray = np.abs(vt[ends[:, 0]] - vt[ends[:, 1]]) < eps
+    etag = np.zeros(ends.shape[0], dtype=np.uint8)
+    etag[same_circle] |= WALL
+    etag[same_ray] |= vtag[ends[same_ray, 0]] & vtag[ends[same_ray, 1]] & (INLET | OUTLET)
+    tag[P:] = etag
+    if curved:
+        e = np.flatnonzero(same_circle) + P
+        m = xyz[e]
+        xyz[e] = m * (ra[same_circle] / np.hypot(m[:, 0], m[:, 1]))[:, None]
+    return dict(dim=2, xyz=xyz, conn=conn, tag=tag, n_vertices=P, name=f"annulus {n_r}x{n_t}",
+                r1=r1, r2=r2, theta=theta)
+
+
+def nozzle_half_height(x, h_in=1.0, ratio=2.0, x1=2.0, x2=6.0):
+    """Wall of the diverging nozzle: h_in up to x1, a cosine ramp to ratio * h_in at x2, then constant."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.clip((x - x1) / (x2 - x1), 0.0, 1.0)
+    return h_in * (1.0 + (ratio - 1.0) * 0.5 * (1.0 - np.cos(np.pi * s)))
+
+
+def nozzle2d(nx=30, ny=10, length=10.0, h_in=1.0, ratio=2.0, x1=2.0, x2=6.0):
+    """2D diverging nozzle of expansion ratio 2 (the paper's Sec. 3.3): walls
+    y = +-h(x), h from nozzle_half_height; vertices (x_i, eta_j h(x_i)) on an
+    (nx+1) x (ny+1) lattice; P2 edge nodes at edge midpoints except the wall
+    edge nodes, placed on the wall at the midpoint abscissa (the paper
+    projects inserted boundary nodes onto the curved wall).  nx = 30, ny = 10
+    gives the paper's 600 quadratic triangles and 1,281 nodes.  Inlet x = 0,
+    outlet x = length."""
+    xs = np.linspace(0.0, length, nx + 1)
+    eta = np.linspace(-1.0, 1.0, ny + 1)
+    X, E = np.meshgrid(xs, eta)  # rows: eta (j), columns: x (i) -> x-fastest
+    H = nozzle_half_height(X, h_in, ratio, x1, x2)
+    vxyz = np.stack([X.ravel(), (E * H).ravel()], axis=1)
+    simp = _structured_2d(vxyz, nx, ny)
+    xyz, conn, ends = _add_p2_nodes(vxyz, simp, _lattice_key(nx))
+    P = vxyz.shape[0]
+    vj = np.arange(P) // (nx + 1)
+    vi = np.arange(P) % (nx + 1)
+    vtag = np.zeros(P, dtype=np.uint8)
+    vtag[(vj == 0) | (vj == ny)] |= WALL
+    vtag[vi == 0] |= INLET
+    vtag[vi == nx] |= OUTLET
+    tag = np.zeros(xyz.shape[0], dtype=np.uint8)
+    tag[:P] = vtag
+    a, b = ends[:, 0], ends[:, 1]
+    wall_e = ((vj[a] == 0) & (vj[b] == 0)) | ((vj[a] == ny) & (vj[b] == ny))
+    end_e = ((vi[a] == 0) & (vi[b] == 0)) | ((vi[a] == nx) & (vi[b] == nx))
+    tag[P:][wall_e] |= WALL
+    tag[P:][end_e] |= vtag[a[end_e]] & vtag[b[end_e]] & (INLET | OUTLET)
+    e = np.flatnonzero(wall_e) + P
+    xm = xyz[e, 0]
+    xyz[e, 1] = np.sign(xyz[e, 1]) * nozzle_half_height(xm, h_in, ratio, x1, x2)
+    return dict(dim=2, xyz=xyz, conn=conn, tag=tag, n_vertices=P, name=f"nozzle {nx}x{ny}", length=length,
+                h_in=h_in, ratio=ratio)
+
+
 def _ogrid_section(n_c, n_r, radius, core=0.5):
     """5-block O-grid of the disk: a core square of half-width core*R and a
     ring of 4*n_c x n_r quads blending the square perimeter to the circle.
@@ -177,7 +281,7 @@ def stenosis_radius(x, radius, s, x_c, ell):
 
 
 def pipe3d(radius=1.0, length=10.0, n_c=8, n_r=6, n_x=71, jitter=0.05, seed=0,
-           stenosis=0.0, core=0.5):
+           stenosis=0.0, core=0.5, curved=False):
     """Straight (optionally stenosed) round pipe along x, inlet x=0, outlet x=L.
 
     Cross-section: 5-block O-grid, each quad cut into 2 triangles; extruded in
@@ -191,7 +295,10 @@ def pipe3d(radius=1.0, length=10.0, n_c=8, n_r=6, n_x=71, jitter=0.05, seed=0,
     stay on the (stenosed) circle, inlet/outlet vertices in their planes.
     A stenosis s > 0 scales each layer radially by R(x)/R0 (centre L/2,
     extent 4R0).  Node count N = (V2 + E2) (2 n_x + 1) with V2/E2 the 2D
-    vertex/edge counts.
+    vertex/edge counts.  With ``curved`` the edge nodes of wall edges are
+    projected radially onto the (stenosed) wall, so boundary elements are
+    isoparametric (the paper's Sec. 3.1 node projection); otherwise every
+    edge node is an edge midpoint.
     """
     vxy, quads, on_circle = _ogrid_section(n_c, n_r, radius, core)
     tris = _split_quads(quads)
@@ -249,6 +356,11 @@ def pipe3d(radius=1.0, length=10.0, n_c=8, n_r=6, n_x=71, jitter=0.05, seed=0,
     # O-grid no interior edge joins two wall vertices (n_r >= 1) and no edge
     # joins two vertices of an end plane except in that plane
     tag[P:] = vtag[ends[:, 0]] & vtag[ends[:, 1]]
+    if curved:
+        e = np.flatnonzero(tag[P:] & WALL) + P
+        rw = radius if stenosis <= 0.0 else stenosis_radius(xyz[e, 0], radius, stenosis, 0.5 * length, 4.0 * radius)
+        rr = np.hypot(xyz[e, 1], xyz[e, 2])
+        xyz[e, 1:] *= (rw / rr)[:, None]
     assert n_layers >= 2
     return dict(dim=3, xyz=xyz, conn=conn, tag=tag, n_vertices=P,
                 name=f"pipe R={radius} L={length} n_c={n_c} n_r={n_r} n_x={n_x} s={stenosis}",
