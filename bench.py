@@ -844,9 +844,10 @@ def run_validation(args):
     # pipe
     rho, mu = 1.0, 1.0
     conv = []
-    for name, target in (("QM1", 37469), ("QM2", 70872), ("QM3", 133645), ("QM4", 225610)):
+    for (name, target), curved in [(q, cv) for cv in (True, False) for q in
+                                   (("QM1", 37469), ("QM2", 70872), ("QM3", 133645), ("QM4", 225610))]:
         wl = workloads.paper_pipe(target, np.array([8 * np.pi * mu / rho]), rho=rho, mu=mu,
-                                  neumann_tag=scvs.SCVS_TAG_NEUMANN)
+                                  neumann_tag=scvs.SCVS_TAG_NEUMANN, curved=curved)
         u, Ms, rep, dt = solve(wl, args.val_tol)
         xyz = wl["mesh"]["xyz"]
         r = np.hypot(xyz[:, 1], xyz[:, 2])
@@ -855,7 +856,8 @@ def run_validation(args):
         ex[:, 0] = pipe_profile(r, w, 1.0, rho, mu, G=1.0 / 15.0)
         n_el = wl["mesh"]["conn"].shape[0]
         h = (np.pi * 15.0 / n_el * 6.0 * np.sqrt(2.0)) ** (1.0 / 3.0)  # edge of a regular tet of the mean volume
-        conv.append({"mesh": name + "-sized", "nodes": int(xyz.shape[0]), "elements": int(n_el), "h_over_R": h,
+        conv.append({"mesh": name + "-sized", "wall": "curved" if curved else "straight",
+                     "nodes": int(xyz.shape[0]), "elements": int(n_el), "h_over_R": h,
                      "e_T2": err_t(Ms, u[0], ex, w, np.pi / w), "iterations": rep[0]["iterations"], "solve_s": dt})
     Ws = np.arange(11) * 8 * np.pi
     wl = workloads.paper_pipe(225610, Ws * mu / rho, rho=rho, mu=mu, neumann_tag=scvs.SCVS_TAG_NEUMANN)
@@ -870,7 +872,8 @@ def run_validation(args):
         T = 2 * np.pi / w if w > 0 else 1.0
         freq.append({"W_over_pi": float(W / np.pi), "e_T2": err_t(Ms, u[k], ex, w, 0.5 * T),
                      "iterations": rep[k]["iterations"]})
-    out["pipe"] = {"geometry": "L/R = 15, R = 1, traction inlet, no-slip wall, traction-free outlet, O-grid tets",
+    out["pipe"] = {"geometry": ("L/R = 15, R = 1, traction inlet, no-slip wall, traction-free outlet, O-grid tets; "
+                                "wall edge nodes on the cylinder (curved, isoparametric) or at chord midpoints"),
                    "convergence_W8pi": conv, "frequency_QM4": freq, "frequency_solve_s": dt,
                    "paper": "QM1-QM4: 37,469-225,610 nodes; e(T/2) at W = 8 pi and its growth with W in "
                             "Figs. cylinder_msh_elesize and cylinder_msh_freq (context only)"}

@@ -292,6 +292,8 @@ int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
     SCVS_CUDA(cudaMemset(c->gsync, 0, sizeof(GridSync)));
     reference_tables(2, &c->ref2);
     reference_tables(3, &c->ref3);
+    quad_tables(2, ISO_QUAD, &c->quad2);
+    quad_tables(3, ISO_QUAD, &c->quad3);
     matfree_tables(*c);
     return SCVS_OK;
   });

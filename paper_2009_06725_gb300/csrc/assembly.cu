@@ -76,6 +76,144 @@ __global__ void k_geom(const double *__restrict__ xyz, const int32_t *__restrict
     }
 }
 
+// ------------------------------------------------------ curved elements
+// An element is curved (isoparametric) if one of its edge nodes is not at its
+// edge's midpoint (relative tolerance 1e-12 of the edge length): the paper
+// projects inserted boundary nodes onto curved walls (Sec. 3.1).
+__global__ void k_curved_flag(const double *__restrict__ xyz, const int32_t *__restrict__ conn, int64_t E, int nl,
+                              int dim, int32_t *__restrict__ flag) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int32_t *c = conn + e * nl;
+  const int ne = dim == 2 ? 3 : 6;
+  const int EA[6] = {0, 1, 2, 0, 1, 2}, EB[6] = {1, 2, 0, 3, 3, 3};
+  int curved = 0;
+  for (int j = 0; j < ne; ++j) {
+    const double *xa = xyz + (int64_t)c[EA[j]] * dim, *xb = xyz + (int64_t)c[EB[j]] * dim;
+    const double *xm = xyz + (int64_t)c[dim + 1 + j] * dim;
+    double dev = 0.0, len = 0.0;
+    for (int r = 0; r < dim; ++r) {
+      const double d = xm[r] - 0.5 * (xa[r] + xb[r]), l = xb[r] - xa[r];
+      dev += d * d;
+      len += l * l;
+    }
+    if (dev > 1e-24 * len) curved = 1;
+  }
+  flag[e] = curved;
+}
+
+__global__ void k_curved_slot(const int32_t *__restrict__ flag, const int64_t *__restrict__ scan, int64_t E,
+                              int32_t *__restrict__ slot) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < E) slot[e] = flag[e] ? (int32_t)scan[e] : -1;
+}
+
+// Element matrices of the curved elements by quadrature of the isoparametric
+// map x(xi) = sum_a x_a phi_a(xi): at every point J = sum_a x_a grad_xi phi_a^T,
+// grad_x phi_a = J^-T grad_xi phi_a, and
+//   CM[a][b] += w |J| phi_a phi_b,  CK[a][b] += w |J| grad_x phi_a . grad_x phi_b,
+//   CD[c][a][b] += -w |J| d_c phi_a psi_b.
+// One warp per element, lanes over the (a, b) pairs.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_curved_mats(const double *__restrict__ xyz, const int32_t *__restrict__ conn,
+                                                     const int32_t *__restrict__ slot, int64_t E,
+                                                     const QuadTables *__restrict__ qt, double *__restrict__ CM,
+                                                     double *__restrict__ CK, double *__restrict__ CD, int *err) {
+  constexpr int NL = DIM == 2 ? 6 : 10, NV = DIM + 1, PPL = (NL * NL + 31) / 32;
+  __shared__ double X[4][NL][DIM];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t e = (int64_t)blockIdx.x * 4 + warp; e < E; e += (int64_t)gridDim.x * 4) {
+    const int s = slot[e];
+    if (s < 0) continue;  // warp-uniform
+    if (lane < NL)
+      for (int r = 0; r < DIM; ++r) X[warp][lane][r] = xyz[(int64_t)conn[e * NL + lane] * DIM + r];
+    __syncwarp();
+    double am[PPL], ak[PPL], ad[PPL][DIM];
+#pragma unroll
+    for (int u = 0; u < PPL; ++u) {
+      am[u] = ak[u] = 0.0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) ad[u][c] = 0.0;
+    }
+    bool bad = false;
+    for (int q = 0; q < qt->nq; ++q) {
+      double J[DIM][DIM];
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          double v = 0.0;
+#pragma unroll
+          for (int a = 0; a < NL; ++a) v += X[warp][a][r] * __ldg(&qt->dphi[q][a][i]);
+          J[r][i] = v;
+        }
+      double det, Ji[DIM][DIM];  // Ji[i][r] = (J^-1)_{i r}
+      if (DIM == 2) {
+        det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        Ji[0][0] = J[1][1] / det; Ji[0][1] = -J[0][1] / det;
+        Ji[1][0] = -J[1][0] / det; Ji[1][1] = J[0][0] / det;
+      } else {
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        Ji[0][0] = c00 / det;
+        Ji[1][0] = c01 / det;
+        Ji[2][0] = c02 / det;
+        Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+      }
+      if (!(det > 0.0)) bad = true;
+      const double wd = __ldg(&qt->w[q]) * det;
+#pragma unroll
+      for (int u = 0; u < PPL; ++u) {
+        const int pr = lane + 32 * u;
+        if (pr >= NL * NL) break;
+        const int a = pr / NL, b = pr % NL;
+        double ga[DIM], gb[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          double va = 0.0, vb = 0.0;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            va += __ldg(&qt->dphi[q][a][i]) * Ji[i][c];
+            vb += __ldg(&qt->dphi[q][b][i]) * Ji[i][c];
+          }
+          ga[c] = va;
+          gb[c] = vb;
+        }
+        am[u] += wd * __ldg(&qt->phi[q][a]) * __ldg(&qt->phi[q][b]);
+        double kd = 0.0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) kd += ga[c] * gb[c];
+        ak[u] += wd * kd;
+        if (b < NV) {
+          const double pb = __ldg(&qt->psi[q][b]);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) ad[u][c] -= wd * ga[c] * pb;
+        }
+      }
+    }
+    if (bad && lane == 0) atomicOr(err, DEVERR_JACOBIAN);
+#pragma unroll
+    for (int u = 0; u < PPL; ++u) {
+      const int pr = lane + 32 * u;
+      if (pr >= NL * NL) break;
+      const int a = pr / NL, b = pr % NL;
+      CM[(int64_t)s * NL * NL + pr] = am[u];
+      CK[(int64_t)s * NL * NL + pr] = ak[u];
+      if (b < NV)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) CD[((int64_t)s * DIM + c) * NL * NV + a * NV + b] = ad[u][c];
+    }
+    __syncwarp();
+  }
+}
+
 // -------------------------------------------------------------- incidence
 __global__ void k_count_incidence(const int32_t *__restrict__ conn, int64_t total, int32_t *cnt) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -186,7 +324,8 @@ k_assemble_rows(const int64_t *__restrict__ n2e_ptr, const int32_t *__restrict__
                 const int32_t *__restrict__ g_len, const int64_t *__restrict__ g_ptr, int cap,
                 int64_t g_nnz, int64_t gt_nnz, double *__restrict__ Ms, double *__restrict__ Ks,
                 double *__restrict__ Dv, double *__restrict__ DTv, double *__restrict__ Mp,
-                double *__restrict__ Lp, int *err) {
+                double *__restrict__ Lp, const int32_t *__restrict__ cslot, const double *__restrict__ CM,
+                const double *__restrict__ CK, const double *__restrict__ CD, int *err) {
   extern __shared__ double smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // per warp: acc[10][cap] doubles, cols[cap] ints
@@ -226,8 +365,24 @@ k_assemble_rows(const int64_t *__restrict__ n2e_ptr, const int32_t *__restrict__
           if (cv == myc) { pos = mid; break; }
           if (cv < myc) lo = mid + 1; else hi = mid - 1;
         }
+        const int cs = cslot ? cslot[e] : -1;  // curved element: stored isoparametric matrices
         if (pos < 0) {
           atomicOr(err, DEVERR_BAD_NODE);
+        } else if (cs >= 0) {
+          acc[0 * cap + pos] += CM[((int64_t)cs * nl + a) * nl + b];
+          acc[1 * cap + pos] += CK[((int64_t)cs * nl + a) * nl + b];
+          if (b < nv)
+            for (int cc = 0; cc < dim; ++cc) acc[(2 + cc) * cap + pos] += CD[(((int64_t)cs * dim + cc) * nl + a) * nv + b];
+          if (is_vertex) {
+            for (int cc = 0; cc < dim; ++cc) acc[(5 + cc) * cap + pos] += CD[(((int64_t)cs * dim + cc) * nl + b) * nv + a];
+            if (b < nv) {  // the preconditioner's P1 operators keep the straight simplex of the vertices
+              const double det = g[0];
+              acc[8 * cap + pos] += det * c_ref.m1[a][b];
+              double lv = 0.0;
+              for (int p = 0; p < npair; ++p) lv += g[10 + p] * c_ref.k1sym[p][a][b];
+              acc[9 * cap + pos] += lv;
+            }
+          }
         } else {
           const double det = g[0];
           acc[0 * cap + pos] += det * c_ref.mref[a][b];
@@ -475,6 +630,36 @@ void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, c
   int derr = dev_error(c);
   if (derr) throw derr;
 
+  // curved (isoparametric) elements: flags, slots, element matrices by quadrature
+  {
+    int32_t *flag = m.arena.alloc<int32_t>(E);
+    int64_t *scan = m.arena.alloc<int64_t>(E + 1);
+    k_curved_flag<<<ceil_div(E, 256), 256, 0, s>>>(m.xyz, m.conn, E, nl, dim, flag);
+    count_launch(c);
+    scan_exclusive(c, flag, scan, E);
+    SCVS_CUDA(cudaMemcpyAsync(&m.n_curved, scan + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SCVS_CUDA(cudaStreamSynchronize(s));
+    if (m.n_curved > 0) {
+      m.cslot = m.arena.alloc<int32_t>(E);
+      k_curved_slot<<<ceil_div(E, 256), 256, 0, s>>>(flag, scan, E, m.cslot);
+      count_launch(c);
+      m.CM = m.arena.alloc<double>(m.n_curved * nl * nl);
+      m.CK = m.arena.alloc<double>(m.n_curved * nl * nl);
+      m.CD = m.arena.alloc<double>(m.n_curved * dim * nl * m.nv);
+      const QuadTables &qh = dim == 2 ? c.quad2 : c.quad3;
+      QuadTables *qd = m.arena.alloc<QuadTables>(1);
+      SCVS_CUDA(cudaMemcpyAsync(qd, &qh, sizeof(QuadTables), cudaMemcpyHostToDevice, s));
+      const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(E, 4), (int64_t)c.num_sms * 16);
+      if (dim == 2)
+        k_curved_mats<2><<<nb, 128, 0, s>>>(m.xyz, m.conn, m.cslot, E, qd, m.CM, m.CK, m.CD, c.dev_err);
+      else
+        k_curved_mats<3><<<nb, 128, 0, s>>>(m.xyz, m.conn, m.cslot, E, qd, m.CM, m.CK, m.CD, c.dev_err);
+      count_launch(c);
+      derr = dev_error(c);
+      if (derr) throw derr;
+    }
+  }
+
   // node -> element incidence
   int32_t *cnt = m.arena.alloc<int32_t>(N);
   SCVS_CUDA(cudaMemsetAsync(cnt, 0, N * sizeof(int32_t), s));
@@ -533,7 +718,7 @@ void build_mesh(Ctx &c, Mesh &m, const double *xyz_in, const int32_t *conn_in, c
   const unsigned asm_blocks = std::min<int64_t>(ceil_div(N, ASM_WARPS), (int64_t)c.num_sms * 32);
   k_assemble_rows<<<asm_blocks, ASM_WARPS * 32, smem, s>>>(
       m.n2e_ptr, m.n2e, m.conn, m.geom, nl, dim, N, P, m.s_ptr, m.s_col, m.g_len, m.g_ptr, cap, m.g_nnz,
-      m.gt_nnz, m.Ms, m.Ks, m.Dv, m.DTv, m.Mp, m.Lp, c.dev_err);
+      m.gt_nnz, m.Ms, m.Ks, m.Dv, m.DTv, m.Mp, m.Lp, m.cslot, m.CM, m.CK, m.CD, c.dev_err);
   count_launch(c);
   derr = dev_error(c);
   if (derr) throw derr;

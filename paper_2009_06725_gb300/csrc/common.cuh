@@ -108,6 +108,20 @@ struct RefTables {
 
 void reference_tables(int dim, RefTables *out);  // refmats.cpp
 
+// Quadrature of curved (isoparametric) elements: points of the collapsed
+// Gauss-Legendre rule with ISO_QUAD points per direction, weights, the P2
+// basis, its reference gradients and the P1 basis at every point.
+constexpr int ISO_QUAD = 6;
+constexpr int ISO_QMAX = ISO_QUAD * ISO_QUAD * ISO_QUAD;
+struct QuadTables {
+  int dim, nq;
+  double w[ISO_QMAX];
+  double phi[ISO_QMAX][MAX_NL];
+  double dphi[ISO_QMAX][MAX_NL][3];
+  double psi[ISO_QMAX][MAX_NV];
+};
+void quad_tables(int dim, int n, QuadTables *out);  // refmats.cpp
+
 inline unsigned int ceil_div(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
 
 }  // namespace scvs

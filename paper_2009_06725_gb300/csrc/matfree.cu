@@ -33,6 +33,8 @@ template <typename T> struct MfArgs {
   const int32_t *n2e;
   const int32_t *conn;
   const double *geom;
+  const int32_t *cslot;        // curved elements: stored matrices (null: none)
+  const double *CM, *CK, *CD;
   const uint8_t *dirmask;
   const double *omega;
   double rho, mu;
@@ -75,6 +77,7 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
         if (cn[b] == (int32_t)node) loc = b;
       }
       const double *g = a.geom + e * GEOM_STRIDE;
+      const int cs = a.cslot ? __ldg(a.cslot + e) : -1;
       const T det = (T)__ldg(g);
       T ji[DIM][DIM], ga[NP];
 #pragma unroll
@@ -88,10 +91,15 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
 #pragma unroll
         for (int b = 0; b < NL; ++b) {
           if (a.dirmask[cn[b]]) continue;  // Dirichlet columns are removed
-          T kc = 0;
+          T kc = 0, mc;
+          if (cs >= 0) {
+            kc = (T)__ldg(a.CK + ((int64_t)cs * NL + aa) * NL + b);
+            mc = (T)__ldg(a.CM + ((int64_t)cs * NL + aa) * NL + b);
+          } else {
 #pragma unroll
-          for (int p = 0; p < NP; ++p) kc += ga[p] * (T)c_mf[DIM - 2].ksym[p][aa][b];
-          const T mc = det * (T)c_mf[DIM - 2].mref[aa][b];
+            for (int p = 0; p < NP; ++p) kc += ga[p] * (T)c_mf[DIM - 2].ksym[p][aa][b];
+            mc = det * (T)c_mf[DIM - 2].mref[aa][b];
+          }
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {
             CV<T, MPL> xv;
@@ -106,10 +114,16 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
           ldv<T, MPL>(xq, xp_base + (int64_t)cn[b] * ld);
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {
-            T s = 0;
+            T dc;
+            if (cs >= 0) {
+              dc = (T)__ldg(a.CD + (((int64_t)cs * DIM + c) * NL + aa) * NV + b);
+            } else {
+              T s = 0;
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) s += ji[i][c] * (T)c_mf[DIM - 2].eref[i][aa][b];
-            axpy(aD[c], -det * s, xq);
+              for (int i = 0; i < DIM; ++i) s += ji[i][c] * (T)c_mf[DIM - 2].eref[i][aa][b];
+              dc = -det * s;
+            }
+            axpy(aD[c], dc, xq);
           }
         }
       } else {
@@ -119,12 +133,18 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
           if (a.dirmask[cn[b]]) continue;
 #pragma unroll
           for (int c = 0; c < DIM; ++c) {
-            T s = 0;
+            T dc;
+            if (cs >= 0) {
+              dc = (T)__ldg(a.CD + (((int64_t)cs * DIM + c) * NL + b) * NV + beta);
+            } else {
+              T s = 0;
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) s += ji[i][c] * (T)c_mf[DIM - 2].eref[i][b][beta];
+              for (int i = 0; i < DIM; ++i) s += ji[i][c] * (T)c_mf[DIM - 2].eref[i][b][beta];
+              dc = -det * s;
+            }
             CV<T, MPL> xv;
             ldv<T, MPL>(xv, x + ((int64_t)cn[b] * DIM + c) * ld + koff);
-            axpy(aD[0], -det * s, xv);
+            axpy(aD[0], dc, xv);
           }
         }
       }
@@ -149,7 +169,8 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
 template <typename T>
 static void launch_matfree(Ctx &c, const Mesh &m, const void *x, void *y) {
   using C = typename cpx<T>::t;
-  MfArgs<T> a{m.N, m.P, m.ld, m.nl, m.n2e_ptr, m.n2e, m.conn, m.geom, m.dirmask, m.omega_d, m.rho, m.mu};
+  MfArgs<T> a{m.N, m.P, m.ld, m.nl, m.n2e_ptr, m.n2e, m.conn, m.geom, m.cslot, m.CM, m.CK, m.CD,
+              m.dirmask, m.omega_d, m.rho, m.mu};
   // algorithmic bytes: connectivity, geometry and incidence once, x read once, y written once
   KScope ks(c, KC_MATFREE, (double)m.E * (m.nl * 4 + GEOM_STRIDE * 8) + (double)m.E * m.nl * 4 + (double)(m.N + 1) * 8 +
                                2.0 * m.n_dof * m.ld * 2 * sizeof(T));

@@ -7,6 +7,7 @@
 //     int_ref lam_0^a0 ... lam_d^ad dxi = a0! ... ad! / (a0 + ... + ad + d)!
 // so the tables carry no quadrature error.  A derivative d/dxi_i of a
 // barycentric polynomial is d/dlam_i - d/dlam_0 (chain rule).
+#include <cmath>
 #include <map>
 #include <array>
 #include <vector>
@@ -80,7 +81,79 @@ void bases(int dim, std::vector<Poly> &p2, std::vector<Poly> &p1) {
   }
 }
 
+double evaluate(const Poly &a, const double *lam) {
+  double s = 0;
+  for (auto &kv : a) {
+    double t = kv.second;
+    for (int i = 0; i < 4; ++i)
+      for (int q = 0; q < kv.first[i]; ++q) t *= lam[i];
+    s += t;
+  }
+  return s;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n
+// (three-term recurrence), started from the Tricomi-type estimate
+// cos(pi (i - 1/4) / (n + 1/2)).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
 }  // namespace
+
+// Quadrature of curved (isoparametric) elements: the collapsed (Duffy)
+// product Gauss-Legendre rule with n points per direction on the reference
+// simplex (triangle: xi = u, eta = v (1 - u), weight (1 - u); tet: zeta = t (1
+// - u)(1 - v), weight (1 - u)^2 (1 - v)), with the P2 basis, its reference
+// gradients and the P1 basis at every point.
+void quad_tables(int dim, int n, QuadTables *out) {
+  std::vector<double> g, wg;
+  gauss_legendre(n, g, wg);
+  for (int i = 0; i < n; ++i) { g[i] = 0.5 * (g[i] + 1.0); wg[i] *= 0.5; }
+  std::vector<Poly> p2, p1;
+  bases(dim, p2, p1);
+  const int nl = (int)p2.size(), nv = (int)p1.size();
+  std::vector<std::vector<Poly>> d2(nl);
+  for (int a = 0; a < nl; ++a)
+    for (int i = 0; i < dim; ++i) d2[a].push_back(dxi(p2[a], i));
+  out->dim = dim;
+  out->nq = 0;
+  const int n3 = dim == 3 ? n : 1;
+  for (int iu = 0; iu < n; ++iu)
+    for (int iv = 0; iv < n; ++iv)
+      for (int it = 0; it < n3; ++it) {
+        const double u = g[iu], v = g[iv], t = dim == 3 ? g[it] : 0.0;
+        double xi[3] = {u, v * (1.0 - u), dim == 3 ? t * (1.0 - u) * (1.0 - v) : 0.0};
+        double w = wg[iu] * wg[iv] * (dim == 3 ? wg[it] * (1.0 - u) * (1.0 - u) * (1.0 - v) : (1.0 - u));
+        double lm[4] = {1.0 - xi[0] - xi[1] - xi[2], xi[0], xi[1], xi[2]};
+        const int q = out->nq++;
+        out->w[q] = w;
+        for (int a = 0; a < nl; ++a) {
+          out->phi[q][a] = evaluate(p2[a], lm);
+          for (int i = 0; i < dim; ++i) out->dphi[q][a][i] = evaluate(d2[a][i], lm);
+        }
+        for (int b = 0; b < nv; ++b) out->psi[q][b] = evaluate(p1[b], lm);
+      }
+}
 
 void reference_tables(int dim, RefTables *t) {
   std::memset(t, 0, sizeof(*t));

@@ -128,6 +128,11 @@ struct Mesh {
   int32_t *conn = nullptr;
   uint8_t *tag = nullptr;
   double *geom = nullptr;           // [E][GEOM_STRIDE]
+  // curved (isoparametric) elements: slot of every element (-1: straight) and
+  // their element matrices by quadrature, CM/CK [n_curved][nl][nl], CD [n_curved][dim][nl][nv]
+  int64_t n_curved = 0;
+  int32_t *cslot = nullptr;
+  double *CM = nullptr, *CK = nullptr, *CD = nullptr;
   int64_t *n2e_ptr = nullptr;       // [N+1] node -> incident elements
   int32_t *n2e = nullptr;           // ascending element ids per node
   int64_t *s_ptr = nullptr;         // [N+1]
@@ -275,6 +280,7 @@ struct Ctx {
   int *dev_err = nullptr;   // device error word (DevErr bits)
   GridSync *gsync = nullptr;
   RefTables ref2, ref3;
+  QuadTables quad2, quad3;
   KTimers timers;
   GuessModel guess;
   // autotuned launch shapes by mesh size (dim, N, P, S nonzeros, G nonzeros,

@@ -66,10 +66,11 @@ PIPE_MU = 2.0 * np.pi * 31.0 / 20.0
 
 
 def pipe_workload(n_c=8, n_r=6, n_x=71, n_modes=32, radius=1.0, length=10.0, rho=1.0,
-                  mu=PIPE_MU, period=1.0, G=1.0, jitter=0.05, seed=0, stenosis=0.0):
-    """Jittered O-grid pipe; c_k = k^-2 exp(j phi_k) with seeded phases."""
+                  mu=PIPE_MU, period=1.0, G=1.0, jitter=0.05, seed=0, stenosis=0.0, curved=False):
+    """Jittered O-grid pipe; c_k = k^-2 exp(j phi_k) with seeded phases
+    (``curved``: wall edge nodes projected onto the wall)."""
     mesh = meshes.pipe3d(radius=radius, length=length, n_c=n_c, n_r=n_r, n_x=n_x,
-                         jitter=jitter, seed=seed, stenosis=stenosis)
+                         jitter=jitter, seed=seed, stenosis=stenosis, curved=curved)
     omegas = 2.0 * np.pi * np.arange(n_modes) / period
     coeffs = phases(n_modes, seed)
     dn, g = _inlet_values(mesh, omegas, coeffs, rho, mu, G)
@@ -201,9 +202,40 @@ def paper_channel(omegas, rho=1.0, mu=0.01, hx=1.0, neumann_tag=8):
     return traction_inlet(mesh, omegas, hx, rho, mu, neumann_tag)
 
 
-def paper_pipe(target_nodes, omegas, rho=1.0, mu=1.0, hx=1.0, neumann_tag=8, seed=0):
+def paper_pipe(target_nodes, omegas, rho=1.0, mu=1.0, hx=1.0, neumann_tag=8, seed=0, curved=True):
     """The paper's pipe (Sec. 3.4): L/R = 15, R = 1, traction inlet, on an
     O-grid mesh of about target_nodes P2 nodes (QM1-QM4: 37,469 / 70,872 /
-    133,645 / 225,610 nodes), no jitter."""
-    mesh = meshes.pipe_for_nodes(target_nodes, radius=1.0, length=15.0, jitter=0.0, seed=seed)
+    133,645 / 225,610 nodes), no jitter; wall edge nodes on the cylinder
+    (``curved``, the paper's node projection) or at chord midpoints."""
+    mesh = meshes.pipe_for_nodes(target_nodes, radius=1.0, length=15.0, jitter=0.0, seed=seed, curved=curved)
     return traction_inlet(mesh, omegas, hx, rho, mu, neumann_tag)
+
+
+def curved_channel(n_r, n_t, curved=True, mu=1.0, K=1.0, r1=1.0, r2=2.0, theta=0.5 * np.pi, neumann_tag=8):
+    """Steady Stokes flow in the annular sector r1 <= r <= r2, 0 <= t <= theta
+    (meshes.annulus2d) driven by the azimuthal pressure p = K (theta - t):
+    u = u_t(r) e_t with u_t = A r + B / r - K / (2 mu) r ln r, u_t(r1) = u_t(r2) = 0.
+    Dirichlet data on the inlet and the walls; the outlet nodes also carry
+    ``neumann_tag`` with the exact pseudo-traction (-p I + mu grad u) n =
+    -mu u_t / r e_r there.  Returns the workload, the nodal tractions h [1][N][2]
+    and the exact nodal velocity."""
+    m = meshes.annulus2d(n_r=n_r, n_t=n_t, r1=r1, r2=r2, theta=theta, curved=curved)
+    c = K / (2.0 * mu)
+    A = c * (r2 * np.log(r2) - r1 * r1 / r2 * np.log(r1)) / (r2 - r1 * r1 / r2)
+    B = c * r1 * r1 * np.log(r1) - A * r1 * r1
+    xyz = m["xyz"]
+    r = np.hypot(xyz[:, 0], xyz[:, 1])
+    t = np.arctan2(xyz[:, 1], xyz[:, 0])
+    ut = A * r + B / r - c * r * np.log(r)
+    uex = np.stack([-np.sin(t) * ut, np.cos(t) * ut], axis=1)
+    tag = m["tag"].copy()
+    out = (tag & meshes.OUTLET) != 0
+    tag[out] |= np.uint8(neumann_tag)
+    m = dict(m, tag=tag)
+    dn = dirichlet_nodes(tag)
+    h = np.zeros((1,) + xyz.shape, dtype=np.complex128)
+    h[0, :, 0] = -mu * ut / r * np.cos(theta)
+    h[0, :, 1] = -mu * ut / r * np.sin(theta)
+    wl = dict(mesh=m, omegas=np.array([0.0]), rho=1.0, mu=mu, dir_nodes=dn,
+              g=uex[dn][None].astype(np.complex128), h=h, name=f"curved channel {n_r}x{n_t}")
+    return wl, uex
