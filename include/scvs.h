@@ -130,6 +130,11 @@ typedef struct {
                         preconditioned COCR, a short recurrence for complex symmetric systems (7 work vectors
                         per system), valid with the symmetric block-diagonal preconditioner kinds */
   int32_t inner_max; /* COCR iterations per FP64 refinement cycle (default 400) */
+  int32_t graphs;    /* 1: replay every FGMRES Arnoldi step (preconditioner, SpMM, Arnoldi kernel) from a CUDA graph
+                        captured on its first use after the first restart cycle of a solve; 0 (default): plain
+                        launches.  Off while the kernel timers run.  A capture the runtime refuses falls back to
+                        plain launches for the rest of the solve */
+  int32_t reserved;
 } scvs_opts;
 
 /* Options of scvs_train_guess (learned initial guess). */
@@ -528,7 +533,13 @@ typedef struct {
   int64_t n_nodes, n_vertices;
   uint64_t mesh_hash; /* scvs_mesh_hash of the mesh the modes belong to */
   double tol;         /* relative residual the modes were solved to */
+  double rho, mu;     /* the physics the modes were solved with */
 } scvs_ckpt_header;
+
+/* FNV-1a 64 hash of one mode's boundary data: the Dirichlet values g (n_g
+ * complex entries) and, when not NULL, the nodal tractions h (n_h entries).  A
+ * stored mode is reused only for identical data.  Host only. */
+int scvs_data_hash(const scvs_c64 *g, int64_t n_g, const scvs_c64 *h, int64_t n_h, uint64_t *hash);
 
 /* FNV-1a 64 hash of a mesh's arrays (host pointers, the layout of
  * scvs_set_mesh): sizes, xyz, conn and tag bytes.  Host only. */
@@ -536,16 +547,20 @@ int scvs_mesh_hash(int32_t dim, int64_t n_nodes, int64_t n_vertices, const doubl
                    const int32_t *conn, const uint8_t *tag, uint64_t *hash);
 
 /* Write / read a checkpoint file (host only; little-endian machine format):
- * magic "SCVSCKP1", the header, omega [n_modes], status [n_modes] (SCVS_CONVERGED
- * ...), rel_res [n_modes], u [n_modes][n_nodes][dim], p [n_modes][n_vertices]
- * (complex), then an FNV-1a 64 checksum of everything before it.  Read checks
- * magic, sizes and checksum and returns SCVS_ERR_ARG on any mismatch (nothing
- * written to the outputs); each output array may be NULL (skipped), so a first
- * call with NULL arrays reads the header to size them. */
+ * magic "SCVSCKP2", the header, omega [n_modes], data_hash [n_modes]
+ * (scvs_data_hash of every mode's boundary data), status [n_modes]
+ * (SCVS_CONVERGED ...), rel_res [n_modes], u [n_modes][n_nodes][dim], p
+ * [n_modes][n_vertices] (complex), then an FNV-1a 64 checksum of everything
+ * before it.  Read checks magic, sizes and checksum and returns SCVS_ERR_ARG on
+ * any mismatch (nothing written to the outputs).  With every output array NULL
+ * it only reads the header (to size the arrays); with any array given, *header
+ * is also an input: the file's dim, n_modes, n_nodes and n_vertices must equal
+ * it (the arrays are sized for it), else SCVS_ERR_ARG before any copy. */
 int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *header, const double *omega,
-                          const int32_t *status, const double *rel_res, const scvs_c64 *u, const scvs_c64 *p);
-int scvs_checkpoint_read(const char *path, scvs_ckpt_header *header, double *omega, int32_t *status,
-                         double *rel_res, scvs_c64 *u, scvs_c64 *p);
+                          const uint64_t *data_hash, const int32_t *status, const double *rel_res, const scvs_c64 *u,
+                          const scvs_c64 *p);
+int scvs_checkpoint_read(const char *path, scvs_ckpt_header *header, double *omega, uint64_t *data_hash,
+                         int32_t *status, double *rel_res, scvs_c64 *u, scvs_c64 *p);
 
 /* Graph aggregates of a vertex graph, the coarse space of SCVS_PC_TRI_PMG_CS
  * (no paper counterpart: part of the preconditioner).  Host only: no context,

@@ -1007,7 +1007,7 @@ static uint64_t fnv1a(uint64_t h, const void *data, size_t n) {
   return h;
 }
 static const uint64_t FNV_OFFSET = 14695981039346656037ULL;
-static const char CKPT_MAGIC[8] = {'S', 'C', 'V', 'S', 'C', 'K', 'P', '1'};
+static const char CKPT_MAGIC[8] = {'S', 'C', 'V', 'S', 'C', 'K', 'P', '2'};
 
 int scvs_barrier_selftest(scvs_ctx *c, int64_t spin_limit, int32_t n_blocks, int32_t absent_block,
                           int32_t *blocks_passed) {
@@ -1048,7 +1048,17 @@ int scvs_mesh_hash(int32_t dim, int64_t N, int64_t P, const double *xyz, int64_t
 
 static int64_t ckpt_payload(const scvs_ckpt_header &h) {
   const int64_t m = h.n_modes;
-  return m * (8 + 4 + 8) + m * h.n_nodes * h.dim * 16 + m * h.n_vertices * 16;
+  return m * (8 + 8 + 4 + 8) + m * h.n_nodes * h.dim * 16 + m * h.n_vertices * 16;
+}
+
+int scvs_data_hash(const scvs_c64 *g, int64_t n_g, const scvs_c64 *h, int64_t n_h, uint64_t *hash) {
+  if (!hash || n_g < 0 || n_h < 0 || (n_g > 0 && !g) || (h && n_h < 0)) return SCVS_ERR_ARG;
+  const int64_t sizes[2] = {n_g, h ? n_h : -1};
+  uint64_t v = fnv1a(FNV_OFFSET, sizes, sizeof(sizes));
+  if (n_g > 0) v = fnv1a(v, g, (size_t)n_g * sizeof(scvs_c64));
+  if (h && n_h > 0) v = fnv1a(v, h, (size_t)n_h * sizeof(scvs_c64));
+  *hash = v;
+  return SCVS_OK;
 }
 
 static bool ckpt_header_ok(const scvs_ckpt_header &h) {
@@ -1056,9 +1066,10 @@ static bool ckpt_header_ok(const scvs_ckpt_header &h) {
          h.n_vertices <= h.n_nodes && h.n_nodes < INT32_MAX;
 }
 
-int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *hd, const double *omega, const int32_t *status,
-                          const double *rel_res, const scvs_c64 *u, const scvs_c64 *p) {
-  if (!path || !hd || !omega || !status || !rel_res || !u || !p || !ckpt_header_ok(*hd)) return SCVS_ERR_ARG;
+int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *hd, const double *omega, const uint64_t *data_hash,
+                          const int32_t *status, const double *rel_res, const scvs_c64 *u, const scvs_c64 *p) {
+  if (!path || !hd || !omega || !data_hash || !status || !rel_res || !u || !p || !ckpt_header_ok(*hd))
+    return SCVS_ERR_ARG;
   const scvs_ckpt_header &h = *hd;
   const int64_t m = h.n_modes, nu = (int64_t)h.n_nodes * h.dim;
   FILE *f = std::fopen(path, "wb");
@@ -1073,6 +1084,7 @@ int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *hd, const do
   put(CKPT_MAGIC, sizeof(CKPT_MAGIC));
   put(&h, sizeof(h));
   put(omega, m * sizeof(double));
+  put(data_hash, m * sizeof(uint64_t));
   put(status, m * sizeof(int32_t));
   put(rel_res, m * sizeof(double));
   put(u, (size_t)m * nu * sizeof(scvs_c64));
@@ -1082,9 +1094,11 @@ int scvs_checkpoint_write(const char *path, const scvs_ckpt_header *hd, const do
   return ok ? SCVS_OK : SCVS_ERR_ARG;
 }
 
-int scvs_checkpoint_read(const char *path, scvs_ckpt_header *hd, double *omega, int32_t *status, double *rel_res,
-                         scvs_c64 *u, scvs_c64 *p) {
+int scvs_checkpoint_read(const char *path, scvs_ckpt_header *hd, double *omega, uint64_t *data_hash, int32_t *status,
+                         double *rel_res, scvs_c64 *u, scvs_c64 *p) {
   if (!path || !hd) return SCVS_ERR_ARG;
+  const bool fill = omega || data_hash || status || rel_res || u || p;
+  const scvs_ckpt_header expect = *hd;  // the arrays' sizes when filling
   FILE *f = std::fopen(path, "rb");
   if (!f) return SCVS_ERR_ARG;
   std::vector<char> buf;
@@ -1102,6 +1116,9 @@ int scvs_checkpoint_read(const char *path, scvs_ckpt_header *hd, double *omega, 
   uint64_t stored = 0;
   std::memcpy(&stored, buf.data() + buf.size() - sizeof(stored), sizeof(stored));
   if (fnv1a(FNV_OFFSET, buf.data(), buf.size() - sizeof(stored)) != stored) return SCVS_ERR_ARG;
+  if (fill && (h.dim != expect.dim || h.n_modes != expect.n_modes || h.n_nodes != expect.n_nodes ||
+               h.n_vertices != expect.n_vertices))
+    return SCVS_ERR_ARG;  // the file no longer matches the header the caller sized its arrays for
   *hd = h;
   const int64_t m = h.n_modes, nu = (int64_t)h.n_nodes * h.dim;
   const char *q = buf.data() + head;
@@ -1110,6 +1127,7 @@ int scvs_checkpoint_read(const char *path, scvs_ckpt_header *hd, double *omega, 
     q += bytes;
   };
   take(omega, m * sizeof(double));
+  take(data_hash, m * sizeof(uint64_t));
   take(status, m * sizeof(int32_t));
   take(rel_res, m * sizeof(double));
   take(u, (size_t)m * nu * sizeof(scvs_c64));

@@ -446,6 +446,63 @@ __global__ void k_warm_x(const double2 *__restrict__ b, const uint8_t *__restric
   if (dof < N * dim && dirm[dof / dim]) x[f] = b[f];
 }
 
+// One CUDA graph per Arnoldi step j of a solve: the step's launches (block
+// preconditioner, all-modes SpMM, the persistent Arnoldi kernel and the copy
+// of the active-system count) are captured once, on an internal stream (the
+// caller's stream may be the legacy default stream, which cannot capture),
+// and replayed on the context's stream.  Launch counts advance as for plain
+// launches.  A capture the runtime refuses switches graphs off for the solve.
+struct StepGraphs {
+  bool on;
+  std::vector<cudaGraphExec_t> exec;
+  std::vector<int64_t> launches;  // kernel launches per replay of step j
+  cudaStream_t cap = nullptr;
+  StepGraphs(int m_r, bool enable) : on(enable), exec(m_r, nullptr), launches(m_r, 0) {
+    if (on && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) { on = false; cap = nullptr; }
+  }
+  ~StepGraphs() {
+    for (auto &e : exec) if (e) cudaGraphExecDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
+  }
+  template <typename F> bool capture(Ctx &c, int j, F &&body) {
+    SCVS_CUDA(cudaStreamSynchronize(c.stream));
+    cudaStream_t user = c.stream;
+    const int64_t n0 = c.launches.n;
+    c.stream = cap;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        body();
+      } catch (...) {
+        cudaStreamEndCapture(cap, &g);
+        if (g) cudaGraphDestroy(g);
+        c.stream = user;
+        (void)cudaGetLastError();
+        on = false;
+        c.launches.n = n0;
+        return false;
+      }
+      ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && g;
+    }
+    c.stream = user;
+    launches[j] = c.launches.n - n0;
+    c.launches.n = n0;
+    if (ok) ok = cudaGraphInstantiate(&exec[j], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      (void)cudaGetLastError();
+      exec[j] = nullptr;
+      on = false;
+    }
+    return ok;
+  }
+  void launch(Ctx &c, int j) {
+    SCVS_CUDA(cudaGraphLaunch(exec[j], c.stream));
+    c.launches.n += launches[j];
+  }
+};
+
 template <typename T>
 struct Work {
   using C = typename cpx<T>::t;
@@ -844,6 +901,9 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   for (auto &r : m.rep) r.guess_used = (guess_on || warm) ? 1 : 0;
   bool check_guess = guess_on || warm;  // drop a start no better than zero, once
 
+  // CUDA graphs of the Arnoldi steps (opts.graphs; off while the kernel
+  // timers run, which record events around every launch)
+  StepGraphs graphs(m_r, c.opts.graphs != 0 && !c.timers.on);
   // page-locked word for the per-step active-system count, freed on every exit path
   struct PinnedInt {
     int *p = nullptr;
@@ -928,14 +988,23 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
     SCVS_CUDA(cudaMemcpyAsync(wk.rscale, rs.data(), S * sizeof(double), cudaMemcpyHostToDevice, c.stream));
     SCVS_CUDA(cudaMemcpyAsync(wk.gv, g0.data(), g0.size() * sizeof(double2), cudaMemcpyHostToDevice, c.stream));
     SCVS_CUDA(cudaMemsetAsync(wk.kdim, 0, S * sizeof(int), c.stream));
-    // 3. Arnoldi steps
+    // 3. Arnoldi steps (each step's launches replayed from a CUDA graph when
+    //    graphs are on: captured on the step's first use after the first cycle)
     for (int j = 0; j < m_r; ++j) {
       C *Vj = wk.V + (int64_t)j * total, *Zj = wk.Z + (int64_t)j * total;
-      apply_precond<T>(c, m, Vj, Zj, wk.S, wk.rscale);  // normalizes v_j in place
-      apply_saddle<T>(c, m, Zj, wk.W);
-      SCVS_CUDA(cudaMemsetAsync(wk.n_active, 0, sizeof(int), c.stream));
-      launch_arnoldi<T>(c, aa, j, grid, block, smem);
-      SCVS_CUDA(cudaMemcpyAsync(h_active, wk.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+      auto body = [&]() {
+        apply_precond<T>(c, m, Vj, Zj, wk.S, wk.rscale);  // normalizes v_j in place
+        apply_saddle<T>(c, m, Zj, wk.W);
+        SCVS_CUDA(cudaMemsetAsync(wk.n_active, 0, sizeof(int), c.stream));
+        launch_arnoldi<T>(c, aa, j, grid, block, smem);
+        SCVS_CUDA(cudaMemcpyAsync(h_active, wk.n_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+      };
+      if (graphs.on && cyc > 0) {
+        if (!graphs.exec[j] && !graphs.capture(c, j, body)) body();  // capture refused: plain launches from now
+        if (graphs.exec[j]) graphs.launch(c, j);
+      } else {
+        body();
+      }
       SCVS_CUDA(cudaStreamSynchronize(c.stream));
       if (*h_active == 0) break;
     }

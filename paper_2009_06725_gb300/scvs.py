@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "converged", 1: "max_iter", 2: "stagnated", 3: "non_finite"}
 
 class scvs_ckpt_header(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_modes", C.c_int32), ("n_nodes", C.c_int64), ("n_vertices", C.c_int64),
-                ("mesh_hash", C.c_uint64), ("tol", C.c_double)]
+                ("mesh_hash", C.c_uint64), ("tol", C.c_double), ("rho", C.c_double), ("mu", C.c_double)]
 
 
 class scvs_opts(C.Structure):
@@ -44,7 +44,7 @@ class scvs_opts(C.Structure):
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
                 ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p),
                 ("schur_agg", C.c_int32), ("stage", C.c_int32), ("krylov", C.c_int32),
-                ("inner_max", C.c_int32)]
+                ("inner_max", C.c_int32), ("graphs", C.c_int32), ("reserved", C.c_int32)]
 
 
 class scvs_mode_report(C.Structure):
@@ -127,8 +127,9 @@ SIGNATURES = {
     "scvs_modes_to_keep": (_I32, [_P, _I64, _D, _I32, C.POINTER(_I64)]),
     "scvs_set_solution": (_I32, [_P, _I32, _P, _P]),
     "scvs_mesh_hash": (_I32, [_I32, _I64, _I64, _P, _I64, _P, _P, C.POINTER(C.c_uint64)]),
-    "scvs_checkpoint_write": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P]),
-    "scvs_checkpoint_read": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P]),
+    "scvs_checkpoint_write": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P, _P]),
+    "scvs_checkpoint_read": (_I32, [C.c_char_p, C.POINTER(scvs_ckpt_header), _P, _P, _P, _P, _P, _P]),
+    "scvs_data_hash": (_I32, [_P, _I64, _P, _I64, C.POINTER(C.c_uint64)]),
     "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "scvs_schur_coarse_info": (_I32, [_P, _I32, _P]),
 }
@@ -541,12 +542,23 @@ def scvs_mesh_hash(mesh):
     return h.value
 
 
-def scvs_checkpoint_write(path, header, omega, status, rel_res, u, p):
-    arrs = [np.ascontiguousarray(omega, dtype=np.float64), np.ascontiguousarray(status, dtype=np.int32),
-            np.ascontiguousarray(rel_res, dtype=np.float64), np.ascontiguousarray(u, dtype=np.complex128),
-            np.ascontiguousarray(p, dtype=np.complex128)]
+def scvs_data_hash(g, h=None):
+    """FNV-1a 64 hash of one mode's boundary data (Dirichlet values, optional tractions)."""
+    ga = np.ascontiguousarray(g, dtype=np.complex128).ravel()
+    ha = None if h is None else np.ascontiguousarray(h, dtype=np.complex128).ravel()
+    out = C.c_uint64()
+    rc = lib().scvs_data_hash(_ptr(ga), ga.size, _ptr(ha), 0 if ha is None else ha.size, C.byref(out))
+    if rc < 0:
+        raise ScvsError(rc, "scvs_data_hash: bad argument")
+    return out.value
+
+
+def scvs_checkpoint_write(path, header, omega, data_hash, status, rel_res, u, p):
+    arrs = [np.ascontiguousarray(omega, dtype=np.float64), np.ascontiguousarray(data_hash, dtype=np.uint64),
+            np.ascontiguousarray(status, dtype=np.int32), np.ascontiguousarray(rel_res, dtype=np.float64),
+            np.ascontiguousarray(u, dtype=np.complex128), np.ascontiguousarray(p, dtype=np.complex128)]
     m = header.n_modes
-    shapes = [(m,), (m,), (m,), (m, header.n_nodes, header.dim), (m, header.n_vertices)]
+    shapes = [(m,), (m,), (m,), (m,), (m, header.n_nodes, header.dim), (m, header.n_vertices)]
     for a, sh in zip(arrs, shapes):
         if a.size != int(np.prod(sh)):
             raise ScvsError(SCVS_ERR_ARG, "scvs_checkpoint_write: array size does not match the header")
@@ -556,24 +568,32 @@ def scvs_checkpoint_write(path, header, omega, status, rel_res, u, p):
 
 
 def scvs_checkpoint_read(path):
-    """(header, omega, status, rel_res, u [m][N][d], p [m][P]); raises ScvsError on a bad file."""
+    """(header, omega, data_hash, status, rel_res, u [m][N][d], p [m][P]); raises ScvsError on
+    a bad file, or if the file changed between the header read and the array read."""
     h = scvs_ckpt_header()
-    rc = lib().scvs_checkpoint_read(os.fsencode(path), C.byref(h), None, None, None, None, None)
+    rc = lib().scvs_checkpoint_read(os.fsencode(path), C.byref(h), None, None, None, None, None, None)
     if rc < 0:
         raise ScvsError(rc, f"scvs_checkpoint_read: bad checkpoint {path}")
     m = h.n_modes
-    om, st, rr = np.zeros(m), np.zeros(m, dtype=np.int32), np.zeros(m)
+    om, dh, st, rr = np.zeros(m), np.zeros(m, dtype=np.uint64), np.zeros(m, dtype=np.int32), np.zeros(m)
     u = np.zeros((m, h.n_nodes, h.dim), dtype=np.complex128)
     p = np.zeros((m, h.n_vertices), dtype=np.complex128)
-    rc = lib().scvs_checkpoint_read(os.fsencode(path), C.byref(h), _ptr(om), _ptr(st), _ptr(rr), _ptr(u), _ptr(p))
+    rc = lib().scvs_checkpoint_read(os.fsencode(path), C.byref(h), _ptr(om), _ptr(dh), _ptr(st), _ptr(rr), _ptr(u),
+                                    _ptr(p))
     if rc < 0:
         raise ScvsError(rc, f"scvs_checkpoint_read: bad checkpoint {path}")
-    return h, om, st, rr, u, p
+    return h, om, dh, st, rr, u, p
 
 
-def save_checkpoint(ctx, mesh_id, mesh, omegas, reports, tol, path):
-    """Write the modal solution of a solved mesh with its per-mode status: a mode counts as
-    converged when every component's system of that mode converged."""
+def mode_data_hashes(g, h=None):
+    """Per-mode boundary-data hashes: g [m][n_dir][d], h [m][N][d] or None."""
+    return np.array([scvs_data_hash(g[k], None if h is None else h[k]) for k in range(len(g))], dtype=np.uint64)
+
+
+def save_checkpoint(ctx, mesh_id, mesh, omegas, reports, tol, path, rho, mu, g, h=None):
+    """Write the modal solution of a solved mesh with its per-mode status (a mode counts as
+    converged when every component's system of that mode converged), the physics and the
+    hash of every mode's boundary data."""
     m = len(omegas)
     N, P, d = mesh["xyz"].shape[0], mesh["n_vertices"], mesh["dim"]
     u, p = scvs_get_modal(ctx, mesh_id, m, N, d, P)
@@ -581,34 +601,35 @@ def save_checkpoint(ctx, mesh_id, mesh, omegas, reports, tol, path):
     status = np.array([SCVS_CONVERGED if all(reports[c * m + k]["status"] == SCVS_CONVERGED for c in range(n_comp))
                        else SCVS_MAX_ITER for k in range(m)], dtype=np.int32)
     rel = np.array([max(reports[c * m + k]["rel_res"] for c in range(n_comp)) for k in range(m)])
-    hdr = scvs_ckpt_header(d, m, N, P, scvs_mesh_hash(mesh), float(tol))
-    scvs_checkpoint_write(path, hdr, omegas, status, rel, u, p)
+    hdr = scvs_ckpt_header(d, m, N, P, scvs_mesh_hash(mesh), float(tol), float(rho), float(mu))
+    scvs_checkpoint_write(path, hdr, omegas, mode_data_hashes(g, h), status, rel, u, p)
 
 
-def resumable_modes(header, f_omega, f_status, omegas, tol, mesh_hash):
-    """For every current mode k, the checkpoint mode j with the same omega (exact) that converged
-    to a tolerance at least as tight on the same mesh, else -1."""
+def resumable_modes(header, f_omega, f_hash, f_status, omegas, data_hash, tol, mesh_hash, rho, mu):
+    """For every current mode k, the checkpoint mode j with the same omega and the same
+    boundary-data hash (exact) that converged to a tolerance at least as tight on the same
+    mesh with the same physics, else -1."""
     out = np.full(len(omegas), -1, dtype=np.int64)
-    if header.mesh_hash != mesh_hash or header.tol > tol:
+    if header.mesh_hash != mesh_hash or header.tol > tol or header.rho != rho or header.mu != mu:
         return out
     for k, w in enumerate(omegas):
         for j in range(header.n_modes):
-            if f_omega[j] == w and f_status[j] == SCVS_CONVERGED:
+            if f_omega[j] == w and int(f_hash[j]) == int(data_hash[k]) and f_status[j] == SCVS_CONVERGED:
                 out[k] = j
                 break
     return out
 
 
-def resume_from_checkpoint(ctx, mesh_id, mesh, omegas, tol, path):
+def resume_from_checkpoint(ctx, mesh_id, mesh, omegas, tol, path, rho, mu, g, h=None):
     """Load the matching modes of a checkpoint as the initial solution (the others start
     from zero); solve next with opts.guess = SCVS_GUESS_CURRENT.  Returns the map of
     resumable_modes."""
-    h, om, st, _, u, p = scvs_checkpoint_read(path)
-    if h.n_nodes != mesh["xyz"].shape[0] or h.n_vertices != mesh["n_vertices"] or h.dim != mesh["dim"]:
+    hd, om, dh, st, _, u, p = scvs_checkpoint_read(path)
+    if hd.n_nodes != mesh["xyz"].shape[0] or hd.n_vertices != mesh["n_vertices"] or hd.dim != mesh["dim"]:
         return np.full(len(omegas), -1, dtype=np.int64)
-    idx = resumable_modes(h, om, st, omegas, tol, scvs_mesh_hash(mesh))
-    u0 = np.zeros((len(omegas), h.n_nodes, h.dim), dtype=np.complex128)
-    p0 = np.zeros((len(omegas), h.n_vertices), dtype=np.complex128)
+    idx = resumable_modes(hd, om, dh, st, omegas, mode_data_hashes(g, h), tol, scvs_mesh_hash(mesh), rho, mu)
+    u0 = np.zeros((len(omegas), hd.n_nodes, hd.dim), dtype=np.complex128)
+    p0 = np.zeros((len(omegas), hd.n_vertices), dtype=np.complex128)
     for k, j in enumerate(idx):
         if j >= 0:
             u0[k], p0[k] = u[j], p[j]

@@ -1,6 +1,7 @@
 """Checkpoint files and the resume rule (host code of the library and the
 binding; no GPU needed): round trip, rejection of corrupted, truncated or
-foreign files, the mesh hash, and which modes a resumed run may reuse."""
+foreign files and of a file replaced between the header read and the array
+read, the mesh and data hashes, and which modes a resumed run may reuse."""
 import numpy as np
 import pytest
 
@@ -17,23 +18,42 @@ def _case(tmp_path, m=3, seed=0):
     om = 2 * np.pi * np.arange(m)
     st = np.array([scvs.SCVS_CONVERGED, scvs.SCVS_MAX_ITER, scvs.SCVS_CONVERGED][:m], dtype=np.int32)
     rr = np.array([3e-9, 2e-3, 7e-9][:m])
-    hdr = scvs.scvs_ckpt_header(d, m, N, P, scvs.scvs_mesh_hash(mesh), 1e-8)
+    g = rng.standard_normal((m, 6, d)) + 1j * rng.standard_normal((m, 6, d))
+    dh = scvs.mode_data_hashes(g)
+    hdr = scvs.scvs_ckpt_header(d, m, N, P, scvs.scvs_mesh_hash(mesh), 1e-8, 1.0, 0.01)
     path = tmp_path / "modes.ckpt"
-    scvs.scvs_checkpoint_write(path, hdr, om, st, rr, u, p)
-    return mesh, hdr, om, st, rr, u, p, path
+    scvs.scvs_checkpoint_write(path, hdr, om, dh, st, rr, u, p)
+    return mesh, hdr, om, st, rr, u, p, path, g, dh
 
 
 def test_round_trip(tmp_path):
-    mesh, hdr, om, st, rr, u, p, path = _case(tmp_path)
-    h, om2, st2, rr2, u2, p2 = scvs.scvs_checkpoint_read(path)
-    assert (h.dim, h.n_modes, h.n_nodes, h.n_vertices, h.mesh_hash, h.tol) == \
-        (hdr.dim, hdr.n_modes, hdr.n_nodes, hdr.n_vertices, hdr.mesh_hash, hdr.tol)
-    for a, b in ((om, om2), (st, st2), (rr, rr2), (u, u2), (p, p2)):
+    mesh, hdr, om, st, rr, u, p, path, g, dh = _case(tmp_path)
+    h, om2, dh2, st2, rr2, u2, p2 = scvs.scvs_checkpoint_read(path)
+    assert (h.dim, h.n_modes, h.n_nodes, h.n_vertices, h.mesh_hash, h.tol, h.rho, h.mu) == \
+        (hdr.dim, hdr.n_modes, hdr.n_nodes, hdr.n_vertices, hdr.mesh_hash, hdr.tol, hdr.rho, hdr.mu)
+    for a, b in ((om, om2), (dh, dh2), (st, st2), (rr, rr2), (u, u2), (p, p2)):
         assert np.array_equal(a, b)
 
 
+def test_file_replaced_between_reads_is_rejected(tmp_path):
+    """The array read checks the file against the header the arrays were sized
+    for: a larger file swapped in after the header read is refused, not copied."""
+    mesh, hdr, om, st, rr, u, p, path, g, dh = _case(tmp_path, m=2)
+    h = scvs.scvs_ckpt_header()
+    assert scvs.lib().scvs_checkpoint_read(bytes(path), scvs.C.byref(h), None, None, None, None, None, None) == 0
+    _case(tmp_path, m=3)  # the same path now holds three modes
+    m = h.n_modes
+    om2, dh2 = np.zeros(m), np.zeros(m, dtype=np.uint64)
+    st2, rr2 = np.zeros(m, dtype=np.int32), np.zeros(m)
+    u2 = np.zeros((m, h.n_nodes, h.dim), dtype=np.complex128)
+    p2 = np.zeros((m, h.n_vertices), dtype=np.complex128)
+    rc = scvs.lib().scvs_checkpoint_read(bytes(path), scvs.C.byref(h), scvs._ptr(om2), scvs._ptr(dh2), scvs._ptr(st2),
+                                         scvs._ptr(rr2), scvs._ptr(u2), scvs._ptr(p2))
+    assert rc == scvs.SCVS_ERR_ARG and h.n_modes == 2 and not u2.any()
+
+
 def test_corrupted_truncated_and_foreign_files_are_rejected(tmp_path):
-    _, _, _, _, _, _, _, path = _case(tmp_path)
+    path = _case(tmp_path)[7]
     raw = bytearray(path.read_bytes())
     bad = tmp_path / "bad.ckpt"
     flipped = bytearray(raw)
@@ -59,24 +79,43 @@ def test_mesh_hash_is_deterministic_and_sensitive():
 
 
 def test_resumable_modes_rule(tmp_path):
-    mesh, hdr, om, st, rr, u, p, path = _case(tmp_path)
-    h, om2, st2, _, _, _ = scvs.scvs_checkpoint_read(path)
+    mesh, hdr, om, st, rr, u, p, path, g, dh = _case(tmp_path)
+    h, om2, dh2, st2, _, _, _ = scvs.scvs_checkpoint_read(path)
     hsh = scvs.scvs_mesh_hash(mesh)
     # same omegas, reordered and with one new mode; mode 1 of the file did not converge
     cur = np.array([om[2], om[1], 5.0, om[0]])
-    assert scvs.resumable_modes(h, om2, st2, cur, 1e-8, hsh).tolist() == [2, -1, -1, 0]
-    # a looser tolerance than requested, or another mesh: nothing is reused
-    assert scvs.resumable_modes(h, om2, st2, cur, 1e-10, hsh).tolist() == [-1] * 4
-    assert scvs.resumable_modes(h, om2, st2, cur, 1e-8, hsh ^ 1).tolist() == [-1] * 4
+    cdh = np.array([dh[2], dh[1], 7, dh[0]], dtype=np.uint64)
+    assert scvs.resumable_modes(h, om2, dh2, st2, cur, cdh, 1e-8, hsh, 1.0, 0.01).tolist() == [2, -1, -1, 0]
+    # a looser tolerance than requested, another mesh or other physics: nothing is reused
+    assert scvs.resumable_modes(h, om2, dh2, st2, cur, cdh, 1e-10, hsh, 1.0, 0.01).tolist() == [-1] * 4
+    assert scvs.resumable_modes(h, om2, dh2, st2, cur, cdh, 1e-8, hsh ^ 1, 1.0, 0.01).tolist() == [-1] * 4
+    assert scvs.resumable_modes(h, om2, dh2, st2, cur, cdh, 1e-8, hsh, 1.0, 0.02).tolist() == [-1] * 4
+    assert scvs.resumable_modes(h, om2, dh2, st2, cur, cdh, 1e-8, hsh, 2.0, 0.01).tolist() == [-1] * 4
+    # other boundary data for mode 0 (same omega): that mode starts afresh
+    g2 = g.copy()
+    g2[0, 1, 0] += 1e-9
+    cdh2 = scvs.mode_data_hashes(g2)[[2, 1, 1, 0]]
+    assert scvs.resumable_modes(h, om2, dh2, st2, cur, cdh2, 1e-8, hsh, 1.0, 0.01).tolist() == [2, -1, -1, -1]
+
+
+def test_data_hash_sees_dirichlet_and_traction_data():
+    g = np.arange(12, dtype=np.complex128).reshape(6, 2)
+    h = np.ones((5, 2), dtype=np.complex128)
+    base = scvs.scvs_data_hash(g)
+    assert scvs.scvs_data_hash(g.copy()) == base
+    assert scvs.scvs_data_hash(g, h) != base
+    h2 = h.copy()
+    h2[3, 1] = 1j
+    assert scvs.scvs_data_hash(g, h2) != scvs.scvs_data_hash(g, h)
 
 
 def test_write_checks_sizes(tmp_path):
-    mesh, hdr, om, st, rr, u, p, _ = _case(tmp_path)
+    mesh, hdr, om, st, rr, u, p, _, g, dh = _case(tmp_path)
     with pytest.raises(scvs.ScvsError):
-        scvs.scvs_checkpoint_write(tmp_path / "x.ckpt", hdr, om, st, rr, u[:, :-1], p)
-    bad = scvs.scvs_ckpt_header(4, hdr.n_modes, hdr.n_nodes, hdr.n_vertices, hdr.mesh_hash, hdr.tol)
+        scvs.scvs_checkpoint_write(tmp_path / "x.ckpt", hdr, om, dh, st, rr, u[:, :-1], p)
+    bad = scvs.scvs_ckpt_header(4, hdr.n_modes, hdr.n_nodes, hdr.n_vertices, hdr.mesh_hash, hdr.tol, 1.0, 0.01)
     with pytest.raises(scvs.ScvsError):
-        scvs.scvs_checkpoint_write(tmp_path / "y.ckpt", bad, om, st, rr, u, p)
+        scvs.scvs_checkpoint_write(tmp_path / "y.ckpt", bad, om, dh, st, rr, u, p)
 
 
 def test_modes_to_keep_rule():

@@ -38,12 +38,19 @@ def test_resume_reuses_converged_modes(tmp_path):
         rep = scvs.scvs_solve(s.ctx, mid, 4)
         assert all(r["status"] == scvs.SCVS_CONVERGED for r in rep)
         u_ref, p_ref = scvs.scvs_get_modal(s.ctx, mid, 4, N, 3, P)
-        scvs.save_checkpoint(s.ctx, mid, mesh, wl["omegas"][:4], rep, s.opts.tol, path)
+        scvs.save_checkpoint(s.ctx, mid, mesh, wl["omegas"][:4], rep, s.opts.tol, path, wl["rho"], wl["mu"],
+                             wl["g"][:4])
     # resumed run: all five modes, the first four from the checkpoint
     s, mid = _open(wl, wl["omegas"], wl["g"], guess=scvs.SCVS_GUESS_CURRENT)
     with s:
-        idx = scvs.resume_from_checkpoint(s.ctx, mid, mesh, wl["omegas"], s.opts.tol, path)
+        idx = scvs.resume_from_checkpoint(s.ctx, mid, mesh, wl["omegas"], s.opts.tol, path, wl["rho"], wl["mu"],
+                                          wl["g"])
         assert idx.tolist() == [0, 1, 2, 3, -1]
+        # other physics: nothing is reused
+        assert scvs.resume_from_checkpoint(s.ctx, mid, mesh, wl["omegas"], s.opts.tol, path, wl["rho"],
+                                           2 * wl["mu"], wl["g"]).tolist() == [-1] * 5
+        idx = scvs.resume_from_checkpoint(s.ctx, mid, mesh, wl["omegas"], s.opts.tol, path, wl["rho"], wl["mu"],
+                                          wl["g"])
         rep = scvs.scvs_solve(s.ctx, mid, 5)
         u, p = scvs.scvs_get_modal(s.ctx, mid, 5, N, 3, P)
     assert all(r["status"] == scvs.SCVS_CONVERGED for r in rep)
