@@ -6,10 +6,13 @@ What it computes (arXiv 2009.06725, Sec. 2.3): the boundary integral of the
 weak form, b_u[A, c] = int_{Gamma_h} M_A h_c dGamma (Eq. LS_construction), for a
 traction h given by its nodal values and interpolated with the P2 trace
 basis, i.e. b_u = M_Gamma h with M_Gamma the boundary mass matrix of the P2
-faces on Gamma_h (segments with 3 nodes in 2D, triangles with 6 nodes in 3D,
-straight-sided).  Gamma_h is the set of element faces whose nodes all carry a
-given tag bit and that belong to one element only.  Face matrices are
-|F| / |F_ref| times reference matrices integrated by Gauss quadrature.
+faces on Gamma_h (segments with 3 nodes in 2D, triangles with 6 nodes in 3D).
+Gamma_h is the set of element faces whose nodes all carry a given tag bit and
+that belong to one element only.  Straight faces: |F| / |F_ref| times the
+reference matrix; curved faces (an edge node off its edge midpoint, the
+paper's projected boundary nodes, Sec. 3.1): the isoparametric face map
+x(xi) = sum_a x_a phi_a(xi) and its surface Jacobian at every point of a
+6-point-per-direction Gauss rule.
 """
 from __future__ import annotations
 
@@ -40,6 +43,47 @@ def _face_rule(fdim, n=4):
     u, v = np.meshgrid(g, g, indexing="ij")
     wu, wv = np.meshgrid(wg, wg, indexing="ij")
     return np.stack([u.ravel(), (v * (1 - u)).ravel()], axis=1), (wu * wv * (1 - u)).ravel()
+
+
+def _p2_trace_grads(fdim, pts):
+    """Reference derivatives [Q][nl][fdim] of the P2 trace basis."""
+    lam = np.concatenate([1.0 - pts.sum(axis=1, keepdims=True), pts], axis=1)
+    dlam = np.zeros((fdim + 1, fdim))
+    dlam[0, :] = -1.0
+    dlam[1:, :] = np.eye(fdim)
+    g = [(4 * lam[:, a] - 1)[:, None] * dlam[a][None, :] for a in range(fdim + 1)]
+    edges = ((0, 1),) if fdim == 1 else ((0, 1), (1, 2), (2, 0))
+    g += [4 * (lam[:, a][:, None] * dlam[b][None, :] + lam[:, b][:, None] * dlam[a][None, :]) for a, b in edges]
+    return np.stack(g, axis=1)
+
+
+def curved_faces(mesh, faces, rtol=1e-12):
+    """Faces whose edge nodes are not at their edge midpoints."""
+    xyz = mesh["xyz"]
+    fdim = mesh["dim"] - 1
+    edges = ((0, 1),) if fdim == 1 else ((0, 1), (1, 2), (2, 0))
+    out = np.zeros(faces.shape[0], dtype=bool)
+    for j, (a, b) in enumerate(edges):
+        xa, xb, xm = xyz[faces[:, a]], xyz[faces[:, b]], xyz[faces[:, fdim + 1 + j]]
+        out |= np.linalg.norm(xm - 0.5 * (xa + xb), axis=1) > rtol * np.linalg.norm(xb - xa, axis=1)
+    return out
+
+
+def face_mass_iso(mesh, faces, n=6):
+    """Face mass matrices [n_f][nl][nl] of the isoparametric P2 faces:
+    sum_q w_q J_s(xi_q) phi_a phi_b with J_s = |dx/dxi| (segment) or
+    |dx/dxi_1 x dx/dxi_2| (triangle)."""
+    fdim = mesh["dim"] - 1
+    pts, w = _face_rule(fdim, n)
+    phi = _p2_trace_basis(fdim, pts)
+    dphi = _p2_trace_grads(fdim, pts)
+    X = mesh["xyz"][faces]                            # [F][nl][d]
+    T = np.einsum("far,qai->fqir", X, dphi)           # tangents [F][Q][fdim][d]
+    if fdim == 1:
+        Js = np.linalg.norm(T[:, :, 0, :], axis=2)
+    else:
+        Js = np.linalg.norm(np.cross(T[:, :, 0, :], T[:, :, 1, :]), axis=2)
+    return np.einsum("fq,q,qa,qb->fab", Js, w, phi, phi)
 
 
 def face_mass_reference(fdim):
@@ -85,7 +129,11 @@ def face_mass(mesh, faces):
     nl = faces.shape[1]
     rows = np.repeat(faces, nl, axis=1).ravel()
     cols = np.tile(faces, (1, nl)).ravel()
-    vals = (meas[:, None, None] / ref_measure * Mref[None]).ravel()
+    Mf = meas[:, None, None] / ref_measure * Mref[None]
+    cv = curved_faces(mesh, faces)
+    if cv.any():
+        Mf[cv] = face_mass_iso(mesh, faces[cv])
+    vals = Mf.ravel()
     return spm.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
 
 

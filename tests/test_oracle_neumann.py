@@ -146,3 +146,34 @@ def test_spectral_algorithm_end_to_end_channel():
     ref_t = fem.reconstruct(ref, omegas, n_t, T)
     errs = [fem.relative_l2_error(mats["Ms"], ref_t[s], u_t[s]) for s in range(n_t)]
     assert max(errs) < 1e-4, max(errs)  # measured 1.5e-5 on the 32x16 mesh (harmonics at W = 50 pi, 100 pi)
+
+
+def test_curved_face_mass_closed_forms():
+    """A P2 segment whose midpoint is displaced by delta: sum M_F = arc length of
+    x(t) = t L + 4 delta t (1 - t) n, i.e. (1/(4 delta)) [s/2 sqrt(L^2+s^2) + L^2/2 ln(s + sqrt(L^2+s^2))]
+    from 0 to 4 delta (closed form); a planar triangle face with one curved edge:
+    area |T| + (2/3) |chord| delta; straight faces keep the reference matrices."""
+    import math
+    L, delta = 2.0, 0.3
+    xyz = np.array([[0.0, 0.0], [L, 0.0], [0.5 * L, delta]])
+    m2 = dict(xyz=xyz, dim=2)
+    faces = np.array([[0, 1, 2]])
+    assert boundary.curved_faces(m2, faces).all()
+    s4 = 4 * delta
+    F = lambda s: 0.5 * s * math.sqrt(L * L + s * s) + 0.5 * L * L * math.log(s + math.sqrt(L * L + s * s))
+    arc = (F(s4) - F(0.0)) / (4 * delta)
+    Mf = boundary.face_mass_iso(m2, faces)[0]
+    assert abs(Mf.sum() - arc) < 1e-7 * arc       # sqrt integrand: 6.9e-9 quadrature error at delta / L = 0.15
+    assert np.allclose(Mf, Mf.T, atol=1e-15)
+    # planar face in 3D (z = 0) with the edge node of edge (0,1) displaced in-plane
+    x3 = np.array([[0, 0, 0], [2, 0, 0], [0, 1, 0], [1, -delta, 0], [1, 0.5, 0], [0, 0.5, 0]], dtype=float)
+    f3 = np.array([[0, 1, 2, 3, 4, 5]])
+    m3 = dict(xyz=x3, dim=3)
+    assert abs(boundary.face_mass_iso(m3, f3)[0].sum() - (1.0 + (2.0 / 3.0) * 2.0 * delta)) < 1e-13
+    # straight faces: the isoparametric rule gives the closed-form matrices
+    x3s = x3.copy()
+    x3s[3] = [1, 0, 0]
+    ms = dict(xyz=x3s, dim=3)
+    assert not boundary.curved_faces(ms, f3).any()
+    ref = boundary.face_measures(ms, f3)[0] / 0.5 * boundary.face_mass_reference(2)
+    assert np.abs(boundary.face_mass_iso(ms, f3)[0] - ref).max() < 1e-15
