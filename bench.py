@@ -207,16 +207,17 @@ class ClockSampler:
 # --------------------------------------------------------------------- GPU
 
 PC_NAMES = {0: "block-chebyshev", 1: "block-diagonal", 2: "block-pmg", 3: "triangular-pmg",
-            4: "triangular-pmg + coarse Schur correction"}
+            4: "triangular-pmg + coarse Schur correction",
+            5: "auto (triangular-pmg; + coarse Schur correction on multi-component or > 1M-node meshes)"}
 
 
 def pc_config(args):
-    """The preconditioner entry of a bench line's config (library default: triangular-pmg)."""
-    kind = 3 if args.precond is None else args.precond
+    """The preconditioner entry of a bench line's config (library default: auto)."""
+    kind = 5 if args.precond is None else args.precond
     c = {"precond": PC_NAMES.get(kind, str(kind))}
     if getattr(args, "krylov", "fgmres") == "cocr":
         c["krylov"] = "cocr"
-    if kind == 4:
+    if kind in (4, 5):
         c["schur_agg"] = args.schur_agg or 96
     return c
 
@@ -950,8 +951,9 @@ def main():
     ap.add_argument("--cheb-l", type=int, default=0)
     ap.add_argument("--cheb-c", type=int, default=0)
     ap.add_argument("--restart", type=int, default=0)
-    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG, 3 TRI_PMG (default), "
-                    "4 TRI_PMG_CS (coarse Schur correction; pipe, batch and bifurcation workloads)")
+    ap.add_argument("--precond", type=int, default=None, help="0 BLOCK_CHEB, 1 BLOCK_DIAG, 2 BLOCK_PMG, 3 TRI_PMG, "
+                    "4 TRI_PMG_CS (coarse Schur correction), 5 AUTO (default: 4 on the batch and the bifurcation, "
+                    "3 on the pipe)")
     ap.add_argument("--schur-agg", type=int, default=0, help="aggregates per component of TRI_PMG_CS (default 96)")
     ap.add_argument("--graphs", action="store_true", help="replay the Arnoldi steps from CUDA graphs (needs --no-timers)")
     ap.add_argument("--no-timers", action="store_true", help="time the steps without the per-class kernel timers "

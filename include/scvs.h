@@ -79,7 +79,7 @@ extern "C" {
                                   operator on the nested P1 (vertex) space; pressure as BLOCK_CHEB */
 #define SCVS_PC_TRI_PMG 3      /* block upper-triangular [A_u D; 0 S~] with the Schur complement approximation
                                   S~^-1 = -(mu M_p^-1 + j omega rho L_p^-1) (pressure first), then the velocity
-                                  p-multigrid cycle of BLOCK_PMG on r_u - D z_p (default) */
+                                  p-multigrid cycle of BLOCK_PMG on r_u - D z_p */
 #define SCVS_PC_TRI_PMG_CS 4   /* TRI_PMG with an additive coarse correction of the Schur approximation:
                                   S~^-1 = -(mu M_p^-1 + j omega rho L_p^-1 + R_c (R_c^T D^T A~_u^-1 D R_c)^-1 R_c^T),
                                   R_c piecewise constant on graph aggregates of the vertices (opts.schur_agg per
@@ -87,6 +87,11 @@ extern "C" {
                                   The n_c x n_c matrices (real: the cycle is real-linear) are formed and inverted
                                   in FP64 on the first application after scvs_set_modes / scvs_set_physics /
                                   an option change (n_c/2 velocity cycles for all modes at once) */
+#define SCVS_PC_AUTO 5         /* default: per mesh, TRI_PMG_CS on meshes of several components or more than 10^6
+                                  nodes (their long, thin or branched parts are where the Cahouet-Chabard
+                                  approximation alone degrades: measured 4.4x and 16x faster solves on the batch
+                                  of 48 pipes and the 5.7M-node bifurcation), TRI_PMG otherwise (on a single 151k-node
+                                  pipe the correction's set-up costs more than its saved iterations) */
 
 #define SCVS_GUESS_ZERO 0
 #define SCVS_GUESS_MLP 1

@@ -244,7 +244,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->tol = 1e-8;
   o->restart = 30;
   o->precision = SCVS_PREC_MIXED;
-  o->precond = SCVS_PC_TRI_PMG;
+  o->precond = SCVS_PC_AUTO;
   o->cheb_u = 3;
   o->cheb_c = 30;
   o->autotune = 1;
@@ -334,7 +334,7 @@ const char *scvs_last_error(const scvs_ctx *c) { return c ? c->err.c_str() : "nu
 int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
   if (!c || !o) return SCVS_ERR_ARG;
   if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
-      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_TRI_PMG_CS ||
+      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_AUTO ||
       o->schur_agg < 0 || o->schur_agg > 512 ||
       !(o->stage == -1 || o->stage == 0 || o->stage == 4 || o->stage == 8 || o->stage == 16 || o->stage == 32) ||
       (o->krylov != SCVS_KRYLOV_FGMRES && o->krylov != SCVS_KRYLOV_COCR) || o->inner_max < 1)

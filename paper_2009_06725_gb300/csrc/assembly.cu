@@ -880,8 +880,32 @@ int64_t set_neumann(Ctx &c, Mesh &m, const double2 *h_host) {
       meas = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
     }
     for (int a = 0; a < nfl; ++a) fnodes.push_back(nodes[a]);
-    for (int a = 0; a < nfl; ++a)
-      for (int b = 0; b < nfl; ++b) fmass.push_back(meas * (dim == 2 ? SEG_M[a][b] : TRI_M[a][b]));
+    // a face with an edge node off its edge midpoint (meeting a projected,
+    // curved wall) is integrated with its isoparametric map
+    bool curved = false;
+    const int nfe = dim == 2 ? 1 : 3;
+    static const int FEA[3] = {0, 1, 2}, FEB[3] = {1, 2, 0};
+    for (int j = 0; j < nfe; ++j) {
+      const double *xa = &xyz[(size_t)nodes[FEA[j]] * dim], *xb = &xyz[(size_t)nodes[FEB[j]] * dim];
+      const double *xm = &xyz[(size_t)nodes[dim + j] * dim];
+      double dev = 0.0, len = 0.0;
+      for (int r = 0; r < dim; ++r) {
+        const double dd = xm[r] - 0.5 * (xa[r] + xb[r]), l = xb[r] - xa[r];
+        dev += dd * dd;
+        len += l * l;
+      }
+      if (dev > 1e-24 * len) curved = true;
+    }
+    if (curved) {
+      double X[6 * 3], Mf[36];
+      for (int a = 0; a < nfl; ++a)
+        for (int r = 0; r < dim; ++r) X[a * dim + r] = xyz[(size_t)nodes[a] * dim + r];
+      face_mass_iso(dim - 1, dim, ISO_QUAD, X, Mf);
+      for (int q = 0; q < nfl * nfl; ++q) fmass.push_back(Mf[q]);
+    } else {
+      for (int a = 0; a < nfl; ++a)
+        for (int b = 0; b < nfl; ++b) fmass.push_back(meas * (dim == 2 ? SEG_M[a][b] : TRI_M[a][b]));
+    }
   }
   const int64_t nf = (int64_t)fnodes.size() / nfl;
   // node -> (face, local index) incidence, by node then face

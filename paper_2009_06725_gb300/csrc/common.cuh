@@ -121,6 +121,7 @@ struct QuadTables {
   double psi[ISO_QMAX][MAX_NV];
 };
 void quad_tables(int dim, int n, QuadTables *out);  // refmats.cpp
+void face_mass_iso(int fdim, int dim, int n, const double *X, double *M);  // refmats.cpp
 
 inline unsigned int ceil_div(long long a, long long b) { return (unsigned int)((a + b - 1) / b); }
 

@@ -1231,9 +1231,16 @@ static void per_mode_seq(Ctx &c, Mesh &m, const std::vector<double> &lam, double
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
 }
 
+// The preconditioner kind of a mesh: SCVS_PC_AUTO resolves to the coarse
+// Schur correction on multi-component or large meshes.
+int pc_kind(const Ctx &c, const Mesh &m) {
+  if (c.opts.precond != SCVS_PC_AUTO) return c.opts.precond;
+  return (m.n_comp > 1 || m.N > 1000000) ? SCVS_PC_TRI_PMG_CS : SCVS_PC_TRI_PMG;
+}
+
 static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   const int su = std::max(1, c.opts.cheb_u), sm = std::max(1, c.opts.cheb_m), sl = std::max(1, c.opts.cheb_l);
-  const int sc = std::max(1, c.opts.cheb_c), kind = c.opts.precond;
+  const int sc = std::max(1, c.opts.cheb_c), kind = pc_kind(c, m);
   if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl && t.s_c == sc && t.kind == kind) return;
   t.s_u = su; t.s_m = sm; t.s_l = sl; t.s_c = sc; t.kind = kind;
   t.cs_bytes = 0;  // the coarse Schur matrices depend on the velocity cycle
@@ -1825,7 +1832,7 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   const int64_t total = m.n_dof * m.ld;
   const unsigned eb = ceil_div(total, 256);
   const double cs = 2.0 * sizeof(T), blk = (double)total * cs, vb = (double)m.dim * m.N * m.ld * cs;
-  const int kind = c.opts.precond;
+  const int kind = pc_kind(c, m);
   if (kind == SCVS_PC_BLOCK_DIAG) {
     const PcArgs a = pc_args<T>(m);
     KScope ks(c, KC_PRECOND, blk * (rscale ? 3 : 2) + (double)m.N * 17 + (double)m.P * 17);

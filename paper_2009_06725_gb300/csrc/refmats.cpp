@@ -155,6 +155,63 @@ void quad_tables(int dim, int n, QuadTables *out) {
       }
 }
 
+// Mass matrix M[a][b] = int phi_a phi_b dGamma of one isoparametric P2 face
+// (fdim = 1: segment, nodes (end, end, middle); fdim = 2: triangle in face VTK
+// order) with node coordinates X [nfl][dim]: the face map x(xi) = sum_a x_a
+// phi_a(xi), surface Jacobian |dx/dxi| or |dx/dxi_1 x dx/dxi_2|, and the
+// collapsed Gauss-Legendre rule with n points per direction.
+void face_mass_iso(int fdim, int dim, int n, const double *X, double *M) {
+  std::vector<double> g, wg;
+  gauss_legendre(n, g, wg);
+  for (int i = 0; i < n; ++i) { g[i] = 0.5 * (g[i] + 1.0); wg[i] *= 0.5; }
+  const int nfl = fdim == 1 ? 3 : 6;
+  for (int i = 0; i < nfl * nfl; ++i) M[i] = 0.0;
+  static const int FE[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+  const double dl[3][2] = {{-1.0, -1.0}, {1.0, 0.0}, {0.0, 1.0}};  // grad of lam_0..2 (triangle)
+  const int nj = fdim == 1 ? 1 : n;
+  for (int iu = 0; iu < n; ++iu)
+    for (int iv = 0; iv < nj; ++iv) {
+      double phi[6], dphi[6][2] = {{0}};
+      double w;
+      if (fdim == 1) {
+        const double t = g[iu], l0 = 1.0 - t, l1 = t;
+        w = wg[iu];
+        phi[0] = l0 * (2 * l0 - 1); phi[1] = l1 * (2 * l1 - 1); phi[2] = 4 * l0 * l1;
+        dphi[0][0] = -(4 * l0 - 1); dphi[1][0] = 4 * l1 - 1; dphi[2][0] = 4 * (l0 - l1);
+      } else {
+        const double u = g[iu], v = g[iv] * (1.0 - u);
+        w = wg[iu] * wg[iv] * (1.0 - u);
+        const double lm[3] = {1.0 - u - v, u, v};
+        for (int a = 0; a < 3; ++a) {
+          phi[a] = lm[a] * (2 * lm[a] - 1);
+          for (int i = 0; i < 2; ++i) dphi[a][i] = (4 * lm[a] - 1) * dl[a][i];
+        }
+        for (int e = 0; e < 3; ++e) {
+          const int a = FE[e][0], b = FE[e][1];
+          phi[3 + e] = 4 * lm[a] * lm[b];
+          for (int i = 0; i < 2; ++i) dphi[3 + e][i] = 4 * (lm[a] * dl[b][i] + lm[b] * dl[a][i]);
+        }
+      }
+      double T[2][3] = {{0}};
+      for (int i = 0; i < fdim; ++i)
+        for (int r = 0; r < dim; ++r)
+          for (int a = 0; a < nfl; ++a) T[i][r] += X[a * dim + r] * dphi[a][i];
+      double js;
+      if (fdim == 1) {
+        js = 0;
+        for (int r = 0; r < dim; ++r) js += T[0][r] * T[0][r];
+        js = std::sqrt(js);
+      } else {
+        const double cx = T[0][1] * T[1][2] - T[0][2] * T[1][1];
+        const double cy = T[0][2] * T[1][0] - T[0][0] * T[1][2];
+        const double cz = T[0][0] * T[1][1] - T[0][1] * T[1][0];
+        js = std::sqrt(cx * cx + cy * cy + cz * cz);
+      }
+      for (int a = 0; a < nfl; ++a)
+        for (int b = 0; b < nfl; ++b) M[a * nfl + b] += w * js * phi[a] * phi[b];
+    }
+}
+
 void reference_tables(int dim, RefTables *t) {
   std::memset(t, 0, sizeof(*t));
   std::vector<Poly> p2, p1;

@@ -319,6 +319,7 @@ void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out
 void norms2_sys(Ctx &c, const Mesh &m, const double2 *v, double *out_dev);  // [n_sys] free-row squared norms
 void set_chunks(Ctx &c, Mesh &m, const int32_t *node_comp_host, int n_comp);
 void spectral_bounds(Ctx &c, Mesh &m);
+int pc_kind(const Ctx &c, const Mesh &m);  // opts.precond with SCVS_PC_AUTO resolved for the mesh
 template <typename T>
 void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r, typename cpx<T>::t *z,
                    typename cpx<T>::t *scratch, const double *rscale);

@@ -23,6 +23,7 @@ SCVS_TAG_WALL, SCVS_TAG_INLET, SCVS_TAG_OUTLET, SCVS_TAG_NEUMANN = 1, 2, 4, 8
 SCVS_CONVERGED, SCVS_MAX_ITER, SCVS_STAGNATED, SCVS_NON_FINITE = 0, 1, 2, 3
 SCVS_PREC_MIXED, SCVS_PREC_FP64 = 0, 1
 SCVS_PC_BLOCK_CHEB, SCVS_PC_BLOCK_DIAG, SCVS_PC_BLOCK_PMG, SCVS_PC_TRI_PMG, SCVS_PC_TRI_PMG_CS = 0, 1, 2, 3, 4
+SCVS_PC_AUTO = 5
 SCVS_GUESS_ZERO, SCVS_GUESS_MLP, SCVS_GUESS_CURRENT = 0, 1, 2
 SCVS_KRYLOV_FGMRES, SCVS_KRYLOV_COCR = 0, 1
 SCVS_CSR_S, SCVS_CSR_G, SCVS_CSR_GT, SCVS_CSR_Q = 0, 1, 2, 3

@@ -26,7 +26,7 @@ def test_growth_exponent_and_extrapolation():
 def test_pc_config_and_opts():
     import bench
     a = argparse.Namespace(precond=None, schur_agg=0)
-    assert bench.pc_config(a) == {"precond": "triangular-pmg"} and bench.pc_opts(a) == {}
+    assert bench.pc_config(a)["precond"].startswith("auto") and bench.pc_opts(a) == {}
     a = argparse.Namespace(precond=4, schur_agg=0)
     assert bench.pc_config(a) == {"precond": "triangular-pmg + coarse Schur correction", "schur_agg": 96}
     assert bench.pc_opts(a) == {"precond": 4}

@@ -159,3 +159,24 @@ def test_batch_of_components():
             assert rep[i * m + k]["status"] == scvs.SCVS_CONVERGED, (i, k, rep[i * m + k])
             xi = np.concatenate([u[k][mp].reshape(-1), p[k][mp[:Pi]]])
             assert rel_l2(xi, X[k]) < 1e-6, (i, k)
+
+
+def test_auto_kind_picks_the_correction_for_batches_only(pipe):
+    """SCVS_PC_AUTO (the default) applies the coarse Schur correction to a mesh
+    of several components and the plain triangular form to a single small mesh."""
+    wl, _ = pipe
+    parts = [workloads.pipe_workload(n_c=2, n_r=1, n_x=n, n_modes=4, length=L) for n, L in ((4, 2.0), (6, 3.0))]
+    U = workloads.union_workload(parts)
+    with scvs.Solver() as s:
+        assert s.opts.precond == scvs.SCVS_PC_AUTO
+        mid = scvs.scvs_set_mesh(s.ctx, U["mesh"])
+        scvs.scvs_set_components(s.ctx, mid, U["n_comp"], U["node_comp"])
+        scvs.scvs_set_physics(s.ctx, mid, U["rho"], U["mu"])
+        scvs.scvs_set_modes(s.ctx, mid, U["omegas"], U["g"])
+        rep = scvs.scvs_solve(s.ctx, mid, U["n_comp"] * 4)
+        assert all(r["status"] == scvs.SCVS_CONVERGED for r in rep)
+        assert scvs.scvs_schur_coarse_info(s.ctx, mid)["n_blk"] == 2
+    s, mid, rep, u, p = solve(wl)
+    with s:
+        assert all(r["status"] == scvs.SCVS_CONVERGED for r in rep)
+        assert scvs.scvs_schur_coarse_info(s.ctx, mid)["n_agg"] == 0
