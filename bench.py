@@ -472,7 +472,7 @@ def run_kernel_case(args):
     wl = workloads.pipe_workload(n_c=PIPE["n_c"], n_r=PIPE["n_r"], n_x=PIPE["n_x"], n_modes=PIPE["n_modes"],
                                  length=PIPE["length"])
     mesh = wl["mesh"]
-    with scvs.Solver(restart=4, max_cycles=1) as s:
+    with scvs.Solver(restart=4, max_cycles=1, **pc_opts(args)) as s:
         mid = scvs.scvs_set_mesh(s.ctx, mesh)
         scvs.scvs_set_physics(s.ctx, mid, wl["rho"], wl["mu"])
         scvs.scvs_set_modes(s.ctx, mid, wl["omegas"], wl["g"])

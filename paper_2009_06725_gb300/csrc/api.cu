@@ -467,22 +467,18 @@ int scvs_get_modal(scvs_ctx *c, int32_t mesh_id, scvs_c64 *u, scvs_c64 *p) {
   return guarded(c, [&]() {
     Mesh *m = get_mesh(c, mesh_id);
     if (!m || m->m == 0) return fail(c, SCVS_ERR_ARG, "bad mesh id or no modes");
-    std::vector<double2> h((size_t)m->n_dof * m->ld);
-    SCVS_CUDA(cudaMemcpyAsync(h.data(), m->x, h.size() * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    // transpose on the device into the caller's mode-major layout, then one
+    // copy per field straight into the caller's arrays (DMA when they are pinned)
+    const int64_t nu = (int64_t)m->dim * m->N, np = m->P;
+    double2 *U = nullptr, *Pm = nullptr;
+    SCVS_CUDA(ctx_malloc(*c, &U, (size_t)m->m * nu * sizeof(double2), c->stream));
+    SCVS_CUDA(ctx_malloc(*c, &Pm, (size_t)m->m * np * sizeof(double2), c->stream));
+    modal_split(*c, *m, U, Pm);
+    if (u) SCVS_CUDA(cudaMemcpyAsync(u, U, (size_t)m->m * nu * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    if (p) SCVS_CUDA(cudaMemcpyAsync(p, Pm, (size_t)m->m * np * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    SCVS_CUDA(cudaFreeAsync(U, c->stream));
+    SCVS_CUDA(cudaFreeAsync(Pm, c->stream));
     SCVS_CUDA(cudaStreamSynchronize(c->stream));
-    const int64_t nu = (int64_t)m->dim * m->N;
-    for (int k = 0; k < m->m; ++k) {
-      if (u)
-        for (int64_t d = 0; d < nu; ++d) {
-          double2 v = h[(size_t)d * m->ld + k];
-          u[(size_t)k * nu + d] = scvs_c64{v.x, v.y};
-        }
-      if (p)
-        for (int64_t v = 0; v < m->P; ++v) {
-          double2 z = h[(size_t)(nu + v) * m->ld + k];
-          p[(size_t)k * m->P + v] = scvs_c64{z.x, z.y};
-        }
-    }
     return SCVS_OK;
   });
 }

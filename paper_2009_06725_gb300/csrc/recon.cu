@@ -102,6 +102,39 @@ void reconstruct_static(Ctx &c, Mesh &m, int n_t, double period, double *u_t, do
   SCVS_CUDA(cudaGetLastError());
 }
 
+// Mode-major copies of the modal solution: U[k][i] = x[i][k] for the velocity
+// dofs i < n_u, Pm[k][v] = x[n_u + v][k] for the pressure dofs; 32 x 32 tiles
+// of (dof, mode) transposed through shared memory (coalesced reads of the
+// interleaved block and coalesced writes of the mode-major arrays).
+__global__ void k_modal_split(const double2 *__restrict__ x, int64_t n_dof, int ld, int m, int64_t n_u,
+                              double2 *__restrict__ U, double2 *__restrict__ Pm) {
+  __shared__ double2 t[32][33];
+  const int64_t d0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t d = d0 + r;
+    const int k = k0 + threadIdx.x;
+    t[r][threadIdx.x] = (d < n_dof && k < m) ? x[d * ld + k] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r;
+    const int64_t d = d0 + threadIdx.x;
+    if (k >= m || d >= n_dof) continue;
+    const double2 v = t[threadIdx.x][r];
+    if (d < n_u) U[(int64_t)k * n_u + d] = v;
+    else Pm[(int64_t)k * (n_dof - n_u) + (d - n_u)] = v;
+  }
+}
+
+void modal_split(Ctx &c, Mesh &m, double2 *U, double2 *Pm) {
+  const int64_t n_u = (int64_t)m.dim * m.N;
+  dim3 grid((unsigned)ceil_div(m.n_dof, 32), (unsigned)ceil_div(m.m, 32));
+  KScope ks(c, KC_VECTOR, (double)m.n_dof * m.m * 32);
+  k_modal_split<<<grid, dim3(32, 8), 0, c.stream>>>(m.x, m.n_dof, m.ld, m.m, n_u, U, Pm);
+  count_launch(c);
+}
+
 void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t) {
   std::vector<double2> tw((size_t)n_t * m.m);
   for (int s = 0; s < n_t; ++s) {

@@ -352,6 +352,7 @@ void mlp_adam(Ctx &c, GuessModel &g, float lr);
 // ---- recon.cu
 void reconstruct(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);
 void reconstruct_static(Ctx &c, Mesh &m, int n_t, double period, double *u_t, double *p_t);
+void modal_split(Ctx &c, Mesh &m, double2 *U, double2 *Pm);  // mode-major velocity / pressure copies
 void bc_spectrum(Ctx &c, int n_t, int64_t n_pts, int n_modes, const double *g_t, const double *w, double2 *c_out,
                  double *e2);
 void mode_energies(Ctx &c, Mesh &m, double *E, double *incr2);
