@@ -108,11 +108,11 @@ typedef struct {
   double tol;        /* relative residual target per mode (default 1e-8) */
   int32_t restart;   /* GMRES restart length m_r (default 30, max 64) */
   int32_t precision; /* SCVS_PREC_* (default MIXED) */
-  int32_t precond;   /* SCVS_PC_* (default TRI_PMG) */
+  int32_t precond;   /* SCVS_PC_* (default AUTO) */
   int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with the p-multigrid kinds the degree of each
                         of the pre- and post-smoothers (default 3) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
-  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian (default 75) */
+  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian, when lap_agg = -1 (default 75) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
@@ -139,6 +139,13 @@ typedef struct {
                         captured on its first use after the first restart cycle of a solve; 0 (default): plain
                         launches.  Off while the kernel timers run.  A capture the runtime refuses falls back to
                         plain launches for the rest of the solve */
+  int32_t lap_agg;   /* pressure Laplacian L_p^-1 of the Schur approximation: 0 (default) or 1..224: a symmetric
+                        two-level cycle, S + coarse + S with S the lap_smooth-step Chebyshev-Jacobi polynomial on
+                        [lambda/30, 1.1 lambda] and a Galerkin coarse level R (R^T L_p R)^-1 R^T on graph
+                        aggregates of the vertices off the outlet (this many per connected component; 0: 200);
+                        -1: one Chebyshev polynomial of degree cheb_l on [lambda/3000, 1.1 lambda].  Meshes with a
+                        component that no outlet vertex reaches keep the polynomial (scvs_lap_info) */
+  int32_t lap_smooth;/* Chebyshev degree of each smoother of that cycle (1..64; 0 or default: 8) */
   int32_t reserved;
 } scvs_opts;
 
@@ -169,7 +176,9 @@ typedef struct {
 /* Fill *opts with the defaults listed above. */
 void scvs_default_opts(scvs_opts *opts);
 
-/* Create a context on the current CUDA device.  opts may be NULL (defaults).
+/* Create a context on the current CUDA device.  opts may be NULL (defaults);
+ * options outside the documented ranges return SCVS_ERR_ARG before any device
+ * call (scvs_set_opts checks the same ranges).
  * Owns every device buffer it allocates.  Its device memory comes from a
  * memory pool of its own that keeps freed memory for reuse (re-creating a mesh
  * or a Krylov workspace of a size seen before maps nothing new), so the
@@ -595,6 +604,25 @@ int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t 
  * correction is off}; all 0 before the first application of that kind after
  * scvs_set_modes. */
 int scvs_schur_coarse_info(scvs_ctx *ctx, int32_t mesh_id, int32_t *info);
+
+/* Coarse level of the two-level pressure Laplacian of a mesh (opts.lap_agg >= 0; built on the first
+ * preconditioner application with that option and kept for the mesh's lifetime): info[6] = {1 if the
+ * cycle is in use, else 0 (the plain polynomial), aggregates, connected components of the vertex graph
+ * without the outlet vertices, largest component's aggregates, components whose coarse matrix was
+ * singular (coarse correction off there), components no outlet vertex reaches (any: the plain
+ * polynomial)}; all 0 before it is built.  agg (may be NULL, else [n_vertices]): every vertex's
+ * aggregate, -1 on the outlet (all -1 while the cycle is not in use).  SCVS_ERR_ARG for a bad mesh id
+ * or a null info. */
+int scvs_lap_info(scvs_ctx *ctx, int32_t mesh_id, int32_t *info, int32_t *agg);
+
+/* Spectral bounds behind the preconditioner's Chebyshev intervals (a 20-step power method on the
+ * Jacobi-scaled operators, run by scvs_set_modes and scvs_set_physics): out[0] = lambda_max of
+ * D^-1 M_p, out[1] of D^-1 L_p (outlet rows and columns removed), out[2 + k] of D^-1 A_r with the
+ * velocity shift A_r = mu K + |omega_k| rho M of mode k (P2, Dirichlet rows removed) and
+ * out[2 + n_modes + k] of its P1 (vertex) coarse operator; 2 + 2 n_modes doubles (host).
+ * SCVS_ERR_ARG for a bad mesh id, a null out or n_modes other than the mesh's; SCVS_ERR_STATE before
+ * scvs_set_modes. */
+int scvs_pc_bounds(scvs_ctx *ctx, int32_t mesh_id, int32_t n_modes, double *out);
 
 #ifdef __cplusplus
 }

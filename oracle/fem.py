@@ -281,6 +281,22 @@ def p1_mass(mesh):
     return _coo_to_csr(rows, cols, vals.ravel(), (P, P))
 
 
+def p1_stiffness(mesh):
+    """Full P1 (vertex) stiffness matrix int grad N_A . grad N_B over the
+    simplices of the mesh: the Laplacian L_p of the Cahouet-Chabard Schur
+    approximation (Sec. 2.3), before any boundary condition is imposed."""
+    xyz, conn, dim, P = mesh["xyz"], mesh["conn"].astype(np.int64), mesh["dim"], mesh["n_vertices"]
+    vc = conn[:, :dim + 1]
+    _, K1 = p1_reference_integrals(dim)
+    _, det, Jinv = element_maps(xyz, vc, dim)
+    gamma = np.einsum("eic,ejc->eij", Jinv, Jinv) * det[:, None, None]
+    vals = np.einsum("eij,ijab->eab", gamma, K1)
+    nv = dim + 1
+    rows = np.repeat(vc, nv, axis=1).ravel()
+    cols = np.tile(vc, (1, nv)).ravel()
+    return _coo_to_csr(rows, cols, vals.ravel(), (P, P))
+
+
 def block_weights(mats, mesh):
     """L2(Omega) inner products of the two field blocks of a modal vector in
     the solver's dof order (velocity dof = node * d + c, then the vertices):

@@ -258,21 +258,29 @@ void scvs_default_opts(scvs_opts *o) {
   o->krylov = SCVS_KRYLOV_FGMRES;
   o->inner_max = 400;
   o->stage = -1;
+  o->lap_agg = 0;
+  o->lap_smooth = 0;
+}
+
+// The option ranges documented in the header (scvs_create and scvs_set_opts).
+static bool opts_valid(const scvs_opts *o) {
+  return o->tol > 0 && o->restart >= 1 && o->restart <= 64 && o->cheb_u >= 1 && o->cheb_m >= 1 && o->cheb_l >= 1 &&
+         o->cheb_c >= 1 && o->max_cycles >= 1 && o->precond >= 0 && o->precond <= SCVS_PC_AUTO &&
+         o->schur_agg >= 0 && o->schur_agg <= 512 &&
+         (o->stage == -1 || o->stage == 0 || o->stage == 4 || o->stage == 8 || o->stage == 16 || o->stage == 32) &&
+         (o->krylov == SCVS_KRYLOV_FGMRES || o->krylov == SCVS_KRYLOV_COCR) && o->inner_max >= 1 &&
+         o->lap_agg >= -1 && o->lap_agg <= LAP_NA_MAX && o->lap_smooth >= 0 && o->lap_smooth <= 64;
 }
 
 int scvs_create(scvs_ctx **out, const scvs_opts *opts) {
   if (!out) return SCVS_ERR_ARG;
   *out = nullptr;
+  scvs_opts o;
+  if (opts) o = *opts; else scvs_default_opts(&o);
+  if (!opts_valid(&o)) return SCVS_ERR_ARG;
   scvs_ctx *c = new (std::nothrow) scvs_ctx();
   if (!c) return SCVS_ERR_OOM;
-  if (opts) c->opts = *opts; else scvs_default_opts(&c->opts);
-  if (c->opts.cheb_c < 1) c->opts.cheb_c = 20;
-  const int st = c->opts.stage;
-  if (!(st == -1 || st == 0 || st == 4 || st == 8 || st == 16 || st == 32) ||
-      (c->opts.krylov != SCVS_KRYLOV_FGMRES && c->opts.krylov != SCVS_KRYLOV_COCR) || c->opts.inner_max < 1) {
-    delete c;
-    return SCVS_ERR_ARG;
-  }
+  c->opts = o;
   int r = guarded(c, [&]() {
     SCVS_CUDA(cudaGetDevice(&c->device));
     SCVS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
@@ -333,12 +341,7 @@ const char *scvs_last_error(const scvs_ctx *c) { return c ? c->err.c_str() : "nu
 
 int scvs_set_opts(scvs_ctx *c, const scvs_opts *o) {
   if (!c || !o) return SCVS_ERR_ARG;
-  if (!(o->tol > 0) || o->restart < 1 || o->restart > 64 || o->cheb_u < 1 || o->cheb_m < 1 || o->cheb_l < 1 ||
-      o->cheb_c < 1 || o->max_cycles < 1 || o->precond < 0 || o->precond > SCVS_PC_AUTO ||
-      o->schur_agg < 0 || o->schur_agg > 512 ||
-      !(o->stage == -1 || o->stage == 0 || o->stage == 4 || o->stage == 8 || o->stage == 16 || o->stage == 32) ||
-      (o->krylov != SCVS_KRYLOV_FGMRES && o->krylov != SCVS_KRYLOV_COCR) || o->inner_max < 1)
-    return fail(c, SCVS_ERR_ARG, "invalid options");
+  if (!opts_valid(o)) return fail(c, SCVS_ERR_ARG, "invalid options");
   void *old_stream = c->opts.stream;
   if (o->stream != old_stream) {
     // work queued on the old stream finishes before the arenas follow the new one
@@ -1161,6 +1164,45 @@ int scvs_schur_coarse_info(scvs_ctx *c, int32_t mesh_id, int32_t *info) {
     info[1] = built ? t.n_blk : 0;
     info[2] = built ? t.na_max : 0;
     info[3] = built ? t.cs_singular : 0;
+    return SCVS_OK;
+  });
+}
+
+int scvs_lap_info(scvs_ctx *c, int32_t mesh_id, int32_t *info, int32_t *agg) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !info) return fail(c, SCVS_ERR_ARG, "bad mesh id or null info");
+    const LapCoarse &L = m->lap;
+    info[0] = L.on ? 1 : 0;
+    info[1] = L.target ? L.n_agg : 0;
+    info[2] = L.target ? L.n_blk : 0;
+    info[3] = L.target ? L.na_max : 0;
+    info[4] = L.target ? L.singular : 0;
+    info[5] = L.target ? L.unanchored : 0;
+    if (agg) {
+      if (L.on) {
+        SCVS_CUDA(cudaMemcpyAsync(agg, L.agg, m->P * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        SCVS_CUDA(cudaStreamSynchronize(c->stream));
+      } else {
+        std::fill(agg, agg + m->P, -1);
+      }
+    }
+    return SCVS_OK;
+  });
+}
+
+int scvs_pc_bounds(scvs_ctx *c, int32_t mesh_id, int32_t n_modes, double *out) {
+  return guarded(c, [&]() {
+    Mesh *m = get_mesh(c, mesh_id);
+    if (!m || !out) return fail(c, SCVS_ERR_ARG, "bad mesh id or null out");
+    if (m->m < 1 || (int)m->lam_u.size() < m->m) return fail(c, SCVS_ERR_STATE, "no modes set");
+    if (n_modes != m->m) return fail(c, SCVS_ERR_ARG, "n_modes differs from the mesh's");
+    out[0] = m->lam_m;
+    out[1] = m->lam_l;
+    for (int k = 0; k < n_modes; ++k) {
+      out[2 + k] = m->lam_u[k];
+      out[2 + n_modes + k] = m->lam_c[k];
+    }
     return SCVS_OK;
   });
 }

@@ -78,6 +78,7 @@ struct ChebCoef {
   double alpha_m, beta_m, alpha_l, beta_l;
   int do_u, do_m, do_l;
   int prev_zero_u, prev_zero_m, prev_zero_l;
+  int resid_l;  // pressure Laplacian: write the residual r - L_p z (0 on the outlet) instead of a step
 };
 
 // Row blocks of a mesh for the staged kernels (blocks.cu).

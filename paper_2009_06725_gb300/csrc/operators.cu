@@ -477,12 +477,16 @@ __device__ __forceinline__ void pressure_row_step(const PcArgs &a, const ChebCoe
                           z.y + al * (z.y - zp.y) + be * dm * (rv.y - aMp.im[i]));
     }
     if (cc.do_l) {
-      const C z = ld1co(zL + pf);
-      const C zp = cc.prev_zero_l ? mk<T>(0, 0) : ld1co(zL_prev + pf);
-      const T al = (T)cc.alpha_l, be = (T)cc.beta_l;
       const T rr = out ? T(0) : rv.x, ri = out ? T(0) : rv.y;
-      zL_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dl * (rr - aLp.re[i]),
-                          z.y + al * (z.y - zp.y) + be * dl * (ri - aLp.im[i]));
+      if (cc.resid_l) {
+        zL_prev[pf] = out ? mk<T>(0, 0) : mk<T>(rr - aLp.re[i], ri - aLp.im[i]);
+      } else {
+        const C z = ld1co(zL + pf);
+        const C zp = cc.prev_zero_l ? mk<T>(0, 0) : ld1co(zL_prev + pf);
+        const T al = (T)cc.alpha_l, be = (T)cc.beta_l;
+        zL_prev[pf] = mk<T>(z.x + al * (z.x - zp.x) + be * dl * (rr - aLp.re[i]),
+                            z.y + al * (z.y - zp.y) + be * dl * (ri - aLp.im[i]));
+      }
     }
   }
 }
@@ -831,16 +835,25 @@ __device__ __forceinline__ void pressure_row_cached(const PcArgs &a, const ChebC
     stv<T, MPL>(zM_prev + pf, o);
   }
   if constexpr (DO_L) {
-    CV<T, MPL> z, zp, o;
-    ldv_co<T, MPL>(z, zL + pf);
-    if (cc.prev_zero_l) zp.zero(); else ldv_co<T, MPL>(zp, zL_prev + pf);
-    const T al = (T)cc.alpha_l, be = (T)cc.beta_l, dl = (T)mt.y;
+    CV<T, MPL> o;
     const bool out = mt.z != 0.f;
+    if (cc.resid_l) {
 #pragma unroll
-    for (int i = 0; i < MPL; ++i) {
-      const T rr = out ? T(0) : rv.re[i], ri = out ? T(0) : rv.im[i];
-      o.re[i] = z.re[i] + al * (z.re[i] - zp.re[i]) + be * dl * (rr - aL.re[i]);
-      o.im[i] = z.im[i] + al * (z.im[i] - zp.im[i]) + be * dl * (ri - aL.im[i]);
+      for (int i = 0; i < MPL; ++i) {
+        o.re[i] = out ? T(0) : rv.re[i] - aL.re[i];
+        o.im[i] = out ? T(0) : rv.im[i] - aL.im[i];
+      }
+    } else {
+      CV<T, MPL> z, zp;
+      ldv_co<T, MPL>(z, zL + pf);
+      if (cc.prev_zero_l) zp.zero(); else ldv_co<T, MPL>(zp, zL_prev + pf);
+      const T al = (T)cc.alpha_l, be = (T)cc.beta_l, dl = (T)mt.y;
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) {
+        const T rr = out ? T(0) : rv.re[i], ri = out ? T(0) : rv.im[i];
+        o.re[i] = z.re[i] + al * (z.re[i] - zp.re[i]) + be * dl * (rr - aL.re[i]);
+        o.im[i] = z.im[i] + al * (z.im[i] - zp.im[i]) + be * dl * (ri - aL.im[i]);
+      }
     }
     stv<T, MPL>(zL_prev + pf, o);
   }
@@ -996,6 +1009,15 @@ __global__ void __launch_bounds__(256, 3) k_coarse_solve(const PcArgs a, const C
 // Laplacian polynomials (r_p first scaled in place by rscale, if given), their
 // Chebyshev steps with a bounded grid barrier between steps, and
 // z_p = sign (mu zM + j omega rho zL) written to the pressure rows of z.
+//
+// With lap_s > 0 the Laplacian part is the symmetric two-level cycle
+//   x1 = S r,  x2 = x1 + R A_c^-1 R^T (r - L_p x1),  x3 = x2 + S (r - L_p x2),
+// S the lap_s-step Chebyshev-Jacobi polynomial (al, bl, inv_theta_l), R the
+// indicator of the vertex aggregates (0 on the outlet) and A_c^-1 the inverse
+// Galerkin matrix R^T L_p R of every block: the residual pass, the restriction
+// (one thread block per aggregate, FP64 sums in a fixed order), the coarse
+// product and the prolongation each end at a grid barrier; the post-smoother
+// repeats the recurrence from x2 (its first step has alpha = 0).
 template <typename T> struct PressureArgs {
   typename cpx<T>::t *r;   // the full block; only its pressure rows are read (and scaled)
   const double *rscale;    // [n_comp][ld] or null
@@ -1007,6 +1029,12 @@ template <typename T> struct PressureArgs {
   T sign;
   int kmax;  // rows cached per row group (the dynamic shared memory holds gpb * kmax rows)
   GridSync *gs;
+  // two-level Laplacian (lap_s > 0; then s_l == lap_s)
+  int lap_s, n_lagg;
+  const int32_t *lagg, *lagg_vert, *lagg_blk, *lagg_loc, *lblk_na, *lblk_a0;
+  const int64_t *lagg_ptr, *lblk_so;
+  const T *linv;
+  typename cpx<T>::t *q, *y;  // [n_lagg][ld] scratch
 };
 
 template <typename T, int MPL, int L, int DIM>
@@ -1048,14 +1076,8 @@ __global__ void __launch_bounds__(256, 3) k_pressure_solve(const PcArgs a, const
   }
   if (!grid_sync(p.gs, gridDim.x)) return;  // also orders the cache fill before its use
   C *mc = p.zM0, *mn = p.zM1, *lc = p.zL0, *ln = p.zL1;  // current / next iterates
-  const int steps = max(p.s_m, p.s_l);
-  for (int ip = 1; ip < steps; ++ip) {
-    ChebCoef cc{};
-    cc.do_m = ip < p.s_m;
-    cc.do_l = ip < p.s_l;
-    cc.alpha_m = cc.do_m ? p.am[ip] : 0.0; cc.beta_m = cc.do_m ? p.bm[ip] : 0.0;
-    cc.alpha_l = cc.do_l ? p.al[ip] : 0.0; cc.beta_l = cc.do_l ? p.bl[ip] : 0.0;
-    cc.prev_zero_m = cc.prev_zero_l = (ip == 1);
+  // one pass over the pressure rows of this group: the steps cc selects
+  auto pass = [&](const ChebCoef &cc) {
     int kk = 0;
     for (int64_t B = g; B < a.P; B += G, ++kk) {
       if (row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + B)) continue;
@@ -1073,8 +1095,88 @@ __global__ void __launch_bounds__(256, 3) k_pressure_solve(const PcArgs a, const
       }
       pressure_row_step<T, MPL, L, DIM>(a, cc, B, p.r, mc, mn, lc, ln, lane, gm);
     }
+  };
+  // steps 1 .. s_pre-1 of the polynomials; with the two-level Laplacian then the
+  // residual pass (step s_pre), the coarse correction and lap_s post-smoothing steps
+  const int s_pre = max(p.s_m, p.s_l), n_steps = s_pre + (p.lap_s > 0 ? p.lap_s + 1 : 0);
+  for (int st = 1; st < n_steps; ++st) {
+    ChebCoef cc{};
+    if (st < s_pre) {
+      cc.do_m = st < p.s_m;
+      cc.do_l = st < p.s_l;
+      cc.alpha_m = cc.do_m ? p.am[st] : 0.0; cc.beta_m = cc.do_m ? p.bm[st] : 0.0;
+      cc.alpha_l = cc.do_l ? p.al[st] : 0.0; cc.beta_l = cc.do_l ? p.bl[st] : 0.0;
+      cc.prev_zero_m = cc.prev_zero_l = (st == 1);
+    } else if (st == s_pre) {
+      cc.do_l = 1;
+      cc.resid_l = 1;  // r - L_p x1 into ln
+    } else {           // the same recurrence started from x2: its first step has alpha = 0
+      const int ip = st - s_pre - 1;
+      cc.do_l = 1;
+      cc.alpha_l = ip ? p.al[ip] : 0.0;
+      cc.beta_l = ip ? p.bl[ip] : p.inv_theta_l;
+      cc.prev_zero_l = (ip == 0);
+    }
+    pass(cc);
     if (cc.do_m) { C *t = mc; mc = mn; mn = t; }
-    if (cc.do_l) { C *t = lc; lc = ln; ln = t; }
+    if (cc.do_l && !cc.resid_l) { C *t = lc; lc = ln; ln = t; }
+    if (!grid_sync(p.gs, gridDim.x)) return;
+    if (st != s_pre || p.lap_s == 0) continue;
+    // restriction q[a][k] = sum over the aggregate's vertices (ascending) of the residual
+    __shared__ double2 part[256];
+    {
+      const int k = threadIdx.x % ld, ch = threadIdx.x / ld, nch = blockDim.x / ld;
+      for (int ag = blockIdx.x; ag < p.n_lagg; ag += gridDim.x) {
+        double sx = 0, sy = 0;
+        for (int64_t i = p.lagg_ptr[ag] + ch; i < p.lagg_ptr[ag + 1]; i += nch) {
+          const int64_t v = p.lagg_vert[i];
+          if (row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + v)) continue;
+          const C rv = ld1co(ln + v * ld + k);
+          sx += (double)rv.x;
+          sy += (double)rv.y;
+        }
+        part[threadIdx.x] = make_double2(sx, sy);
+        __syncthreads();
+        for (int h = nch / 2; h > 0; h >>= 1) {
+          if (ch < h) {
+            const double2 o = part[threadIdx.x + h * ld];
+            part[threadIdx.x].x += o.x;
+            part[threadIdx.x].y += o.y;
+          }
+          __syncthreads();
+        }
+        if (ch == 0) p.q[(int64_t)ag * ld + k] = mk<T>((T)part[k].x, (T)part[k].y);
+        __syncthreads();  // part is reused by the block's next aggregate
+      }
+    }
+    if (!grid_sync(p.gs, gridDim.x)) return;
+    // coarse solve y = A_c^-1 q of every block, one thread per (aggregate, mode)
+    for (int64_t f = tid; f < (int64_t)p.n_lagg * ld; f += nth) {
+      const int ag = (int)(f / ld), k = (int)(f % ld);
+      const int b = p.lagg_blk[ag], n = p.lblk_na[b];
+      const T *row = p.linv + p.lblk_so[b] + (int64_t)p.lagg_loc[ag] * n;
+      const C *qb = p.q + (int64_t)p.lblk_a0[b] * ld + k;
+      T sx = 0, sy = 0;
+      for (int j = 0; j < n; ++j) {
+        const T w = row[j];
+        const C v = ld1co(qb + (int64_t)j * ld);
+        sx = fma(w, v.x, sx);
+        sy = fma(w, v.y, sy);
+      }
+      p.y[f] = mk<T>(sx, sy);
+    }
+    if (!grid_sync(p.gs, gridDim.x)) return;
+    // prolongation x2 = x1 + R y
+    for (int64_t e = tid; e < np; e += nth) {
+      const int64_t B = e / ld;
+      const int ag = p.lagg[B];
+      if (ag < 0 || row_idle(a.dof_comp, a.comp_active, (int64_t)DIM * a.N + B)) continue;
+      const C add = ld1co(p.y + (int64_t)ag * ld + e % ld);
+      C o = ld1co(lc + e);
+      o.x += add.x;
+      o.y += add.y;
+      lc[e] = o;
+    }
     if (!grid_sync(p.gs, gridDim.x)) return;
   }
   const T mu = p.sign * (T)a.mu;
@@ -1193,6 +1295,20 @@ static ChebSeq cheb_seq(double lo, double hi, int s) {
 // P1 mass and P1 Laplacian.
 constexpr double CHEB_RATIO_U = 30.0, CHEB_RATIO_SMOOTH = 12.0, CHEB_RATIO_C = 30.0, CHEB_RATIO_M = 6.0,
                  CHEB_RATIO_L = 3000.0, CHEB_TOP = 1.10;
+// Smoother of the two-level pressure Laplacian: damps [lambda/30, 1.1 lambda]
+// and leaves the smooth end to the coarse level.
+constexpr double CHEB_RATIO_LAP = 30.0;
+
+static void lap_build(Ctx &c, Mesh &m, int target);
+static int lap_target_of(const Ctx &c) { return c.opts.lap_agg > 0 ? c.opts.lap_agg : LAP_DEFAULT_AGG; }
+// Smoothing degree of the two-level pressure Laplacian of a mesh, 0 where the
+// plain polynomial is used (option off, or no coarse level on this mesh).
+static int lap_smooth_of(Ctx &c, Mesh &m) {
+  if (c.opts.lap_agg < 0) return 0;
+  const int target = lap_target_of(c);
+  if (m.lap.target != target) lap_build(c, m, target);
+  return m.lap.on ? (c.opts.lap_smooth > 0 ? c.opts.lap_smooth : LAP_DEFAULT_SMOOTH) : 0;
+}
 
 template <typename T>
 PcArgs pc_args(const Mesh &m) {
@@ -1241,8 +1357,10 @@ int pc_kind(const Ctx &c, const Mesh &m) {
 static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   const int su = std::max(1, c.opts.cheb_u), sm = std::max(1, c.opts.cheb_m), sl = std::max(1, c.opts.cheb_l);
   const int sc = std::max(1, c.opts.cheb_c), kind = pc_kind(c, m);
-  if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl && t.s_c == sc && t.kind == kind) return;
-  t.s_u = su; t.s_m = sm; t.s_l = sl; t.s_c = sc; t.kind = kind;
+  const int lap = lap_smooth_of(c, m), sl_eff = lap ? lap : sl;
+  if (t.valid && t.s_u == su && t.s_m == sm && t.s_l == sl_eff && t.lap_s == lap && t.s_c == sc && t.kind == kind)
+    return;
+  t.s_u = su; t.s_m = sm; t.s_l = sl_eff; t.lap_s = lap; t.s_c = sc; t.kind = kind;
   t.cs_bytes = 0;  // the coarse Schur matrices depend on the velocity cycle
   const bool pmg = kind == SCVS_PC_BLOCK_PMG || kind == SCVS_PC_TRI_PMG || kind == SCVS_PC_TRI_PMG_CS;
   per_mode_seq(c, m, m.lam_u, pmg ? CHEB_RATIO_SMOOTH : CHEB_RATIO_U, su, &t.inv_theta_u, &t.alpha_u, &t.beta_u);
@@ -1250,7 +1368,8 @@ static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
   t.zeros = m.mode_arena.alloc<double>(m.ld);
   SCVS_CUDA(cudaMemsetAsync(t.zeros, 0, m.ld * sizeof(double), c.stream));
   ChebSeq qm = cheb_seq(m.lam_m / CHEB_RATIO_M, CHEB_TOP * m.lam_m, sm);
-  ChebSeq ql = cheb_seq(m.lam_l / CHEB_RATIO_L, CHEB_TOP * m.lam_l, sl);
+  ChebSeq ql = lap ? cheb_seq(m.lam_l / CHEB_RATIO_LAP, CHEB_TOP * m.lam_l, lap)
+                  : cheb_seq(m.lam_l / CHEB_RATIO_L, CHEB_TOP * m.lam_l, sl);
   t.inv_theta_m = qm.inv_theta; t.am = qm.alpha; t.bm = qm.beta;
   t.inv_theta_l = ql.inv_theta; t.al = ql.alpha; t.bl = ql.beta;
   double **dst[4] = {&t.am_d, &t.bm_d, &t.al_d, &t.bl_d};
@@ -1313,16 +1432,35 @@ static int coop_grid(Ctx &c, const void *kfn, size_t smem) {
 template <typename T>
 static void pressure_solve(Ctx &c, const Mesh &m, const PcArgs &a, const PcTables &t, typename cpx<T>::t *r,
                            const double *rscale, typename cpx<T>::t *const *pM, typename cpx<T>::t *const *pL,
-                           typename cpx<T>::t *z, T sign) {
+                           typename cpx<T>::t *z, T sign, typename cpx<T>::t *lq, typename cpx<T>::t *ly) {
   const double cs = 2.0 * sizeof(T), pb = (double)m.P * m.ld * cs;
   double by = pb * (rscale ? 4 : 3) + (double)m.P * 2 * sizeof(T) + 3 * pb;  // step 0 and the combination
+  const double lstep = (double)m.q_nnz * (4 + sizeof(T)) + (double)(m.P + 1) * 8;  // one pass over the L_p rows
   for (int ip = 1; ip < std::max(t.s_m, t.s_l); ++ip) {
     const int np = (ip < t.s_m) + (ip < t.s_l);
     by += (double)m.q_nnz * (4 + np * sizeof(T)) + (double)(m.P + 1) * 8 + pb + np * pb * (ip == 1 ? 2 : 3);
   }
+  const LapCoarse &lap = m.lap;
+  if (t.lap_s > 0) {
+    const double qb = (double)lap.n_agg * m.ld * cs;
+    by += lstep + 2 * pb;                                                   // residual
+    by += pb + (double)m.P * 4 + (double)(lap.n_agg + 1) * 8 + qb;            // restriction
+    by += (double)lap.so_total * sizeof(T) + (double)lap.n_agg * 12 + 2 * qb;  // coarse product (each row once)
+    by += 2 * pb + (double)m.P * 4 + qb;                                    // prolongation
+    by += t.lap_s * (lstep + 3 * pb) + pb;                                  // post-smoothing
+  }
   KScope ks(c, KC_PRESSURE, by);
   PressureArgs<T> p{r, rscale, t.inv_theta_m, t.inv_theta_l, t.am_d, t.bm_d, t.al_d, t.bl_d, t.s_m, t.s_l,
                     pM[0], pM[1], pL[0], pL[1], z, sign, 0, c.gsync};
+  if (t.lap_s > 0) {
+    p.lap_s = t.lap_s;
+    p.n_lagg = lap.n_agg;
+    p.lagg = lap.agg; p.lagg_vert = lap.agg_vert; p.lagg_blk = lap.agg_blk; p.lagg_loc = lap.agg_loc;
+    p.lblk_na = lap.blk_na; p.lblk_a0 = lap.blk_a0; p.lagg_ptr = lap.agg_ptr; p.lblk_so = lap.blk_so;
+    p.linv = sizeof(T) == 4 ? (const T *)(const void *)lap.inv_f : (const T *)(const void *)lap.inv_d;
+    p.q = lq;
+    p.y = ly;
+  }
   PcArgs aa = a;
   SCVS_DISPATCH_LD(T, m.ld, {
     const void *kfn = m.dim == 2 ? (const void *)k_pressure_solve<T, MPL, L, 2> : (const void *)k_pressure_solve<T, MPL, L, 3>;
@@ -1564,8 +1702,9 @@ __global__ void k_cs_broadcast(const PcArgs a, int dim, const int32_t *__restric
 // aggregate left below a third of that size joins the first full-size
 // aggregate next to it (if any).  Aggregates are numbered by block, then by
 // seed.  grow starts at 1 and rises by 1.5x until no block has more than
-// min(2 target, CS_NA_MAX) aggregates.  Columns outside [0, P) are ignored.
-AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target) {
+// min(2 target, CS_NA_MAX) aggregates (na_cap instead, if positive).  Columns
+// outside [0, P) are ignored.
+AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target, int na_cap) {
   AggResult r;
   std::vector<int32_t> comp(P, -1), queue;
   std::vector<int64_t> csize;
@@ -1652,7 +1791,7 @@ AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, in
     }
     r.na_max = 0;
     for (int b = 0; b < nb; ++b) r.na_max = std::max(r.na_max, r.na[b]);
-    if (r.na_max <= std::min(CS_NA_MAX, 2 * target)) break;
+    if (r.na_max <= (na_cap > 0 ? na_cap : std::min(CS_NA_MAX, 2 * target))) break;
     grow *= 1.5;
   }
   return r;
@@ -1713,6 +1852,207 @@ static void build_aggregates(Ctx &c, Mesh &m, PcTables &t, int target) {
   up(t.blk_a0, r.a0.data(), nb * sizeof(int32_t));
   up(t.blk_so, so.data(), nb * sizeof(int64_t));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host vectors go out of scope
+}
+
+// ---------------------------------------- two-level pressure Laplacian: set-up
+// Galerkin matrix of the Laplacian's coarse level, row a of its block b:
+// W[so_b + loc(a) n_b + loc(agg(u))] = sum of L_p[v][u] over the vertices v of
+// aggregate a and their neighbours u off the outlet.  One thread block per
+// aggregate; thread c owns column c (n_b <= LAP_NA_MAX < 256) and visits the
+// nonzeros in storage order, so the sums are reproducible.
+__global__ void __launch_bounds__(256) k_lap_galerkin(const int64_t *__restrict__ agg_ptr,
+                                                      const int32_t *__restrict__ agg_vert,
+                                                      const int32_t *__restrict__ agg, const int32_t *__restrict__ agg_blk,
+                                                      const int32_t *__restrict__ agg_loc,
+                                                      const int32_t *__restrict__ blk_na,
+                                                      const int64_t *__restrict__ blk_so, const int64_t *__restrict__ g_ptr,
+                                                      const int64_t *__restrict__ s_ptr, const int32_t *__restrict__ s_col,
+                                                      const double *__restrict__ Lp, double *__restrict__ W) {
+  const int a = blockIdx.x, b = agg_blk[a], n = blk_na[b], c = threadIdx.x;
+  double acc = 0;
+  for (int64_t i = agg_ptr[a]; i < agg_ptr[a + 1]; ++i) {
+    const int64_t v = agg_vert[i];
+    const int64_t r0 = g_ptr[v], r1 = g_ptr[v + 1], s0 = s_ptr[v];
+    for (int64_t t = r0; t < r1; ++t) {
+      const int32_t au = agg[s_col[s0 + (t - r0)]];
+      if (au >= 0 && agg_loc[au] == c) acc += Lp[t];
+    }
+  }
+  if (c < n) W[blk_so[b] + (int64_t)agg_loc[a] * n + c] = acc;
+}
+
+// Inverse of every block's Galerkin matrix (symmetric positive definite when
+// an outlet vertex anchors the block) by the in-place Gauss-Jordan sweep in
+// FP32 shared memory, one thread block per block: for each pivot k, row k is
+// divided by a_kk, a_ij -= a_ik a_kj off row and column k, column k becomes
+// -a_ik / a_kk and a_kk its reciprocal.  A pivot at or below 1e-6 of the
+// largest diagonal entry (or not finite) marks the block singular: its inverse
+// is written as zero (coarse correction off there) and *n_singular counts it.
+__global__ void __launch_bounds__(1024) k_lap_invert(const int32_t *__restrict__ blk_na,
+                                                     const int64_t *__restrict__ blk_so, const double *__restrict__ W,
+                                                     float *__restrict__ inv_f, double *__restrict__ inv_d,
+                                                     int *n_singular) {
+  extern __shared__ float lap_sh[];
+  __shared__ float s_piv;
+  __shared__ int s_bad;
+  const int b = blockIdx.x, n = blk_na[b], tid = threadIdx.x, bd = blockDim.x;
+  const int64_t so = blk_so[b];
+  float *A = lap_sh, *colk = lap_sh + n * n;
+  for (int e = tid; e < n * n; e += bd) A[e] = (float)W[so + e];
+  __syncthreads();
+  if (tid == 0) {
+    float dmax = 0;
+    for (int i = 0; i < n; ++i) dmax = fmaxf(dmax, fabsf(A[i * n + i]));
+    s_piv = dmax;  // reused below for the pivot
+    s_bad = !(dmax > 0) || !isfinite(dmax);
+  }
+  __syncthreads();
+  const float dmax = s_piv;
+  __syncthreads();
+  for (int k = 0; k < n && !s_bad; ++k) {
+    if (tid == 0) {
+      const float pv = A[k * n + k];
+      if (!(pv > 1e-6f * dmax) || !isfinite(pv)) s_bad = 1;
+      s_piv = pv;
+    }
+    __syncthreads();
+    if (s_bad) break;  // uniform: read from shared memory after the barrier
+    const float ip = 1.f / s_piv;
+    for (int i = tid; i < n; i += bd) colk[i] = A[i * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += bd)
+      if (j != k) A[k * n + j] *= ip;
+    __syncthreads();
+    for (int e = tid; e < n * n; e += bd) {
+      const int i = e / n, j = e % n;
+      if (i != k && j != k) A[e] = fmaf(-colk[i], A[k * n + j], A[e]);
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += bd) A[i * n + k] = (i == k) ? ip : -colk[i] * ip;
+    __syncthreads();
+  }
+  const bool bad = s_bad;
+  for (int e = tid; e < n * n; e += bd) {
+    const float v = bad ? 0.f : A[e];
+    inv_f[so + e] = v;
+    inv_d[so + e] = (double)v;
+  }
+  if (bad && tid == 0) atomicAdd(n_singular, 1);
+}
+
+// Coarse level of the pressure Laplacian (host aggregation, device Galerkin
+// matrices and inverses), kept in the mesh arena for the mesh's lifetime.  The
+// graph is the vertex graph with the outlet vertices (p = 0 there) removed;
+// every connected component of it must touch the outlet, else the mesh keeps
+// the plain polynomial.
+static void lap_build(Ctx &c, Mesh &m, int target) {
+  LapCoarse &L = m.lap;
+  L = LapCoarse{};
+  L.target = target;
+  const int64_t P = m.P;
+  std::vector<int64_t> sp(P + 1);
+  std::vector<int32_t> gl(std::max<int64_t>(P, 1));
+  std::vector<uint8_t> om(std::max<int64_t>(P, 1));
+  SCVS_CUDA(cudaMemcpyAsync(sp.data(), m.s_ptr, (P + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(gl.data(), m.g_len, P * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(om.data(), m.outmask, P, cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<int32_t> scol(std::max<int64_t>(sp[P] - sp[0], 1));
+  SCVS_CUDA(cudaMemcpyAsync(scol.data(), m.s_col + sp[0], (sp[P] - sp[0]) * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  std::vector<int32_t> id(std::max<int64_t>(P, 1), -1);
+  int64_t n = 0;
+  for (int64_t v = 0; v < P; ++v)
+    if (!om[v]) id[v] = (int32_t)n++;
+  if (n == 0) { L.unanchored = 1; return; }
+  std::vector<int64_t> cp(n + 1, 0);
+  std::vector<int32_t> cc;
+  std::vector<char> touch(n, 0);
+  cc.reserve(sp[P] - sp[0]);
+  for (int64_t v = 0; v < P; ++v) {
+    if (om[v]) continue;
+    const int64_t i = id[v];
+    for (int64_t e = sp[v] - sp[0]; e < sp[v] - sp[0] + gl[v]; ++e) {
+      const int32_t u = scol[e];
+      if (om[u]) touch[i] = 1;
+      else cc.push_back(id[u]);
+    }
+    cp[i + 1] = (int64_t)cc.size();
+  }
+  const AggResult r = graph_aggregates(n, cp.data(), cc.empty() ? nullptr : cc.data(), target, LAP_NA_MAX);
+  const int n_agg = (int)r.blk.size(), nb = r.n_blk;
+  std::vector<char> anch(nb, 0);
+  for (int64_t i = 0; i < n; ++i)
+    if (touch[i]) anch[r.blk[r.agg[i]]] = 1;
+  for (int b = 0; b < nb; ++b) L.unanchored += !anch[b];
+  L.n_agg = n_agg;
+  L.n_blk = nb;
+  L.na_max = r.na_max;
+  if (L.unanchored > 0 || r.na_max > LAP_NA_MAX) return;
+  std::vector<int32_t> agg(P);
+  std::vector<int64_t> ptr(n_agg + 1, 0), so(nb);
+  std::vector<int32_t> vert(n);
+  for (int64_t v = 0; v < P; ++v) {
+    agg[v] = om[v] ? -1 : r.agg[id[v]];
+    if (agg[v] >= 0) ++ptr[agg[v] + 1];
+  }
+  for (int i = 0; i < n_agg; ++i) ptr[i + 1] += ptr[i];
+  {
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t v = 0; v < P; ++v)
+      if (agg[v] >= 0) vert[fill[agg[v]]++] = (int32_t)v;
+  }
+  int64_t acc = 0;
+  for (int b = 0; b < nb; ++b) { so[b] = acc; acc += (int64_t)r.na[b] * r.na[b]; }
+  L.so_total = acc;
+  L.agg = m.arena.alloc<int32_t>(P);
+  L.agg_ptr = m.arena.alloc<int64_t>(n_agg + 1);
+  L.agg_vert = m.arena.alloc<int32_t>(n);
+  L.agg_blk = m.arena.alloc<int32_t>(n_agg);
+  L.agg_loc = m.arena.alloc<int32_t>(n_agg);
+  L.blk_na = m.arena.alloc<int32_t>(nb);
+  L.blk_a0 = m.arena.alloc<int32_t>(nb);
+  L.blk_so = m.arena.alloc<int64_t>(nb);
+  L.inv_f = m.arena.alloc<float>(acc);
+  L.inv_d = m.arena.alloc<double>(acc);
+  auto up = [&](void *d, const void *h, size_t bytes) {
+    SCVS_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c.stream));
+  };
+  up(L.agg, agg.data(), P * sizeof(int32_t));
+  up(L.agg_ptr, ptr.data(), (n_agg + 1) * sizeof(int64_t));
+  up(L.agg_vert, vert.data(), n * sizeof(int32_t));
+  up(L.agg_blk, r.blk.data(), n_agg * sizeof(int32_t));
+  up(L.agg_loc, r.loc.data(), n_agg * sizeof(int32_t));
+  up(L.blk_na, r.na.data(), nb * sizeof(int32_t));
+  up(L.blk_a0, r.a0.data(), nb * sizeof(int32_t));
+  up(L.blk_so, so.data(), nb * sizeof(int64_t));
+  double *W = nullptr;
+  int *nsing = nullptr;
+  SCVS_CUDA(ctx_malloc(c, &W, (size_t)acc * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &nsing, sizeof(int), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(W, 0, (size_t)acc * sizeof(double), c.stream));
+  SCVS_CUDA(cudaMemsetAsync(nsing, 0, sizeof(int), c.stream));
+  {
+    KScope ks(c, KC_PRECOND, (double)n * 4 + (double)m.q_nnz * 28 + (double)acc * 8);
+    k_lap_galerkin<<<n_agg, 256, 0, c.stream>>>(L.agg_ptr, L.agg_vert, L.agg, L.agg_blk, L.agg_loc, L.blk_na,
+                                                L.blk_so, m.g_ptr, m.s_ptr, m.s_col, m.Lp, W);
+    count_launch(c);
+  }
+  {
+    KScope ks(c, KC_PRECOND, (double)acc * 20);
+    const size_t smem = (size_t)(r.na_max * r.na_max + r.na_max) * sizeof(float);
+    SCVS_CUDA(cudaFuncSetAttribute(k_lap_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lap_invert<<<nb, 1024, smem, c.stream>>>(L.blk_na, L.blk_so, W, L.inv_f, L.inv_d, nsing);
+    count_launch(c);
+  }
+  int h_sing = 0;
+  SCVS_CUDA(cudaMemcpyAsync(&h_sing, nsing, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaFreeAsync(W, c.stream));
+  SCVS_CUDA(cudaFreeAsync(nsing, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host vectors go out of scope
+  L.singular = h_sing;
+  L.on = true;
 }
 
 static int cs_target_of(const Ctx &c) { return c.opts.schur_agg > 0 ? c.opts.schur_agg : CS_DEFAULT_AGG; }
@@ -1863,7 +2203,7 @@ void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r_in, typename cpx
   C *uB = (uA == z) ? other : z;
   // 1. pressure block: z_p = -/+ (mu M_p^-1 + j omega rho L_p^-1) r_p (minus: Schur
   //    complement of the triangular form; plus: block-diagonal form)
-  pressure_solve<T>(c, m, a, t, r, rscale, pM, pL, z, tri ? T(-1) : T(1));
+  pressure_solve<T>(c, m, a, t, r, rscale, pM, pL, z, tri ? T(-1) : T(1), rc, zc[0]);
   // 1b. coarse Schur correction z_p -= R_c S_c^-1 R_c^T r_p (r_p already scaled
   //     by the pressure solve); the pressure polynomials' buffers are free again
   if (cs_on) schur_coarse_apply<T>(c, m, a, t, r, z, pM[0], pM[1]);

@@ -77,6 +77,7 @@ struct PcTables {
   double *am_d = nullptr, *bm_d = nullptr, *al_d = nullptr, *bl_d = nullptr;  // device copies
   double inv_theta_m = 0, inv_theta_l = 0;
   int s_u = 0, s_m = 0, s_l = 0;
+  int lap_s = 0;  // > 0: two-level Laplacian with lap_s pre- and post-smoothing steps (al/bl, inv_theta_l)
   bool valid = false;
   // Coarse correction of the Schur approximation (SCVS_PC_TRI_PMG_CS): graph
   // aggregates of the vertices, grouped by connected component ("block"), and
@@ -93,6 +94,31 @@ struct PcTables {
   void *sinv = nullptr;              // [so_total][ld] inverse coarse matrices (row-major per block), T
   int cs_bytes = 0;                  // sizeof(T) of sinv (0: not built)
   int cs_singular = 0;               // (block, mode) pairs whose coarse matrix was singular (correction off)
+};
+
+// Coarse level of the two-level pressure Laplacian solve (opts.lap_agg >= 0):
+// graph aggregates of the vertices off the outlet (where the Laplacian has
+// p = 0), grouped by connected component of that graph ("block"), and the
+// inverse of every block's Galerkin matrix R^T L_p R (R the piecewise-constant
+// indicator of the aggregates).  Mode independent: built once per mesh and
+// target.  Blocks not reached by an outlet vertex make L_p singular there;
+// such a mesh keeps the plain Chebyshev polynomial (on = false).
+constexpr int LAP_NA_MAX = 224;  // aggregates of one block at most (its inverse is formed in shared memory)
+constexpr int LAP_DEFAULT_AGG = 200;
+constexpr int LAP_DEFAULT_SMOOTH = 8;
+struct LapCoarse {
+  int target = 0;                    // aggregates per block asked for (0: not built)
+  bool on = false;
+  int n_agg = 0, n_blk = 0, na_max = 0, singular = 0, unanchored = 0;
+  int32_t *agg = nullptr;            // [P] aggregate of every vertex, -1 on the outlet
+  int64_t *agg_ptr = nullptr;        // [n_agg+1] CSR of the aggregates' vertices (ascending ids)
+  int32_t *agg_vert = nullptr;       // [P - outlet vertices]
+  int32_t *agg_blk = nullptr, *agg_loc = nullptr;  // [n_agg]
+  int32_t *blk_na = nullptr, *blk_a0 = nullptr;    // [n_blk]
+  int64_t *blk_so = nullptr;         // [n_blk] sum of n_a^2 over the blocks before it
+  int64_t so_total = 0;
+  float *inv_f = nullptr;            // [so_total] inverse Galerkin matrices (row-major per block)
+  double *inv_d = nullptr;           // the same values widened for the FP64 path
 };
 
 // Row blocks of a mesh for the staged gather kernels (blocks.cu): rows in a
@@ -195,6 +221,7 @@ struct Mesh {
   std::vector<double> lam_c;     // [ld] same for the P1 coarse velocity operator
   double lam_m = 0, lam_l = 0;   // same for the P1 mass / Laplacian
   PcTables pc;
+  LapCoarse lap;                         // two-level pressure Laplacian (mesh arena)
   RowBlocks rb;                          // staged-gather row blocks (FP32 path)
   int st_spmm = 0, st_cheb = 0;          // staged mode chunk of the SpMM / fine Chebyshev kernels (0: unstaged)
   int mpl_spmm = 0, mpl_cheb = 0;       // autotuned row-group shapes (0: default)
@@ -331,7 +358,7 @@ struct AggResult {
   std::vector<int32_t> agg, blk, loc, na, a0;
   int n_blk = 0, na_max = 0;
 };
-AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target);
+AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target, int na_cap = 0);
 void matfree_tables(Ctx &c);  // matfree.cu
 
 // ---- krylov.cu

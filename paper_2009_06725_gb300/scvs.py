@@ -45,7 +45,8 @@ class scvs_opts(C.Structure):
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
                 ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p),
                 ("schur_agg", C.c_int32), ("stage", C.c_int32), ("krylov", C.c_int32),
-                ("inner_max", C.c_int32), ("graphs", C.c_int32), ("reserved", C.c_int32)]
+                ("inner_max", C.c_int32), ("graphs", C.c_int32), ("lap_agg", C.c_int32), ("lap_smooth", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class scvs_mode_report(C.Structure):
@@ -133,6 +134,8 @@ SIGNATURES = {
     "scvs_data_hash": (_I32, [_P, _I64, _P, _I64, C.POINTER(C.c_uint64)]),
     "scvs_graph_aggregates": (_I32, [_I64, _P, _P, _I32, _P, C.POINTER(_I32), C.POINTER(_I32)]),
     "scvs_schur_coarse_info": (_I32, [_P, _I32, _P]),
+    "scvs_lap_info": (_I32, [_P, _I32, _P, _P]),
+    "scvs_pc_bounds": (_I32, [_P, _I32, _I32, _P]),
 }
 KERNEL_CLASSES = ["spmm_fp32", "spmm_fp64", "precond", "arnoldi", "vector", "assembly", "reconstruct", "matfree",
                   "cheb_fine", "pressure", "coarse"]
@@ -669,6 +672,28 @@ def scvs_schur_coarse_info(ctx, mesh_id):
     info = np.zeros(4, dtype=np.int32)
     _check(ctx, lib().scvs_schur_coarse_info(ctx, mesh_id, _ptr(info)))
     return dict(n_agg=int(info[0]), n_blk=int(info[1]), na_max=int(info[2]), singular=int(info[3]))
+
+
+def scvs_lap_info(ctx, mesh_id, n_vertices=None):
+    """{on, n_agg, n_blk, na_max, singular, unanchored} of the two-level pressure
+    Laplacian's coarse level, plus 'agg' ([n_vertices] int32, -1 on the outlet)
+    when n_vertices is given."""
+    info = np.zeros(6, dtype=np.int32)
+    agg = None if n_vertices is None else np.empty(int(n_vertices), dtype=np.int32)
+    _check(ctx, lib().scvs_lap_info(ctx, mesh_id, _ptr(info), None if agg is None else _ptr(agg)))
+    out = dict(on=int(info[0]), n_agg=int(info[1]), n_blk=int(info[2]), na_max=int(info[3]),
+               singular=int(info[4]), unanchored=int(info[5]))
+    if agg is not None:
+        out["agg"] = agg
+    return out
+
+
+def scvs_pc_bounds(ctx, mesh_id, n_modes):
+    """(lam_m, lam_l, lam_u [n_modes], lam_c [n_modes]): the power-method
+    estimates behind the preconditioner's Chebyshev intervals."""
+    out = np.empty(2 + 2 * n_modes, dtype=np.float64)
+    _check(ctx, lib().scvs_pc_bounds(ctx, mesh_id, int(n_modes), _ptr(out)))
+    return float(out[0]), float(out[1]), out[2:2 + n_modes].copy(), out[2 + n_modes:].copy()
 
 
 def scvs_kernel_timers(ctx, enable):

@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every declared entry point
 (no GPU needed; no compute call is made)."""
+import ctypes
 import os
 import re
 import shutil
@@ -38,6 +39,37 @@ def test_default_options():
     assert o.tol == 1e-8 and o.restart == 30 and o.precision == scvs.SCVS_PREC_MIXED
     assert o.cheb_u >= 1 and o.max_cycles >= 1
     assert o.stage == -1 and o.krylov == scvs.SCVS_KRYLOV_FGMRES and o.inner_max == 400
+    assert o.lap_agg == 0 and o.lap_smooth == 0
+
+
+@pytest.mark.parametrize("field,value", [("lap_agg", -2), ("lap_agg", 225), ("lap_smooth", -1), ("lap_smooth", 65),
+                                         ("stage", 3), ("schur_agg", 513)])
+def test_invalid_options_are_refused_before_any_device_call(field, value):
+    o = scvs.scvs_default_opts()
+    setattr(o, field, value)
+    with pytest.raises(scvs.ScvsError) as e:
+        scvs.scvs_create(o)
+    assert e.value.code == scvs.SCVS_ERR_ARG
+
+
+def test_option_struct_layout_matches_the_header(tmp_path):
+    """sizeof and field offsets of scvs_opts as the C compiler lays them out equal the binding's."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in scvs.scvs_opts._fields_]
+    body = "".join(f'printf("%s %zu\\n", "{f}", offsetof(scvs_opts, {f}));' for f in fields)
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "scvs.h"\nint main(void) { '
+                   + body + ' printf("sizeof %zu\\n", sizeof(scvs_opts)); return 0; }\n')
+    exe = tmp_path / "layout"
+    r = subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for f in fields:
+        assert int(out[f]) == getattr(scvs.scvs_opts, f).offset, f
+    assert int(out["sizeof"]) == ctypes.sizeof(scvs.scvs_opts)
 
 
 def test_header_constants_match_binding():

@@ -424,3 +424,34 @@ def test_p1_mass_closed_forms():
     assert abs(M3.sum() - vol) < 1e-12 * vol
     Wu, Wp = fem.block_weights(fem.assemble(m), m)
     assert Wu.shape == (2 * m["xyz"].shape[0],) * 2 and Wp.shape == (P, P)
+
+
+def test_p1_stiffness_closed_forms():
+    """Full P1 stiffness matrix: K 1 = 0 (constants have no gradient), the energy of
+    a linear function is int |grad u|^2 = |a|^2 |Omega| (x^T K x = 4 and
+    (x + 2y)^T K (x + 2y) = 20 on the 4 x 1 channel), symmetric positive
+    semidefinite, its diagonal is the one p1_diagonals gives, and on one
+    right triangle with legs 2 and 1 it is the textbook element matrix."""
+    m = meshes.channel2d(8, 4)
+    K = fem.p1_stiffness(m).toarray()
+    P = m["n_vertices"]
+    x, y = m["xyz"][:P, 0], m["xyz"][:P, 1]
+    assert np.allclose(K, K.T, atol=0)
+    assert np.abs(K @ np.ones(P)).max() < 1e-12
+    assert abs(x @ K @ x - 4.0) < 1e-12
+    assert abs((x + 2 * y) @ K @ (x + 2 * y) - 20.0) < 1e-11
+    assert np.linalg.eigvalsh(K).min() > -1e-12
+    _, Ld = fem.p1_diagonals(m)
+    assert np.allclose(np.diag(K), Ld, rtol=1e-13)
+    tri = dict(xyz=np.array([[0.0, 0.0], [2.0, 0.0], [0.0, 1.0], [1.0, 0.0], [1.0, 0.5], [0.0, 0.5]]),
+               conn=np.array([[0, 1, 2, 3, 4, 5]], dtype=np.int32), dim=2, n_vertices=3)
+    # grad l_1 = (1/2, 0), grad l_2 = (0, 1), grad l_0 = (-1/2, -1); area 1
+    g = np.array([[-0.5, -1.0], [0.5, 0.0], [0.0, 1.0]])
+    assert np.allclose(fem.p1_stiffness(tri).toarray(), g @ g.T, atol=1e-15)
+    # 3D pipe: K 1 = 0 and x^T K x = |Omega| (the discrete volume)
+    pm = meshes.pipe3d(n_c=2, n_r=1, n_x=3, length=1.0, jitter=0.0)
+    K3 = fem.p1_stiffness(pm)
+    x3 = pm["xyz"][:pm["n_vertices"], 0]
+    vol = fem.assemble(pm)["Ms"].sum()
+    assert np.abs(K3 @ np.ones(pm["n_vertices"])).max() < 1e-12
+    assert abs(x3 @ K3 @ x3 - vol) < 1e-12 * vol
