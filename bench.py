@@ -220,10 +220,10 @@ def pc_config(args):
     if kind in (4, 5):
         c["schur_agg"] = args.schur_agg or 96
     if kind != 1:
-        lap = getattr(args, "lap_agg", 0) or 0
+        lap = getattr(args, "lap_size", 0) or 0
+        sm = getattr(args, "lap_smooth", 0) or 8
         c["pressure_laplacian"] = ("chebyshev degree %d" % (getattr(args, "cheb_l", 0) or 75) if lap < 0 else
-                                   "two-level: %d aggregates per component, %d + %d smoothing steps"
-                                   % (lap or 200, getattr(args, "lap_smooth", 0) or 8, getattr(args, "lap_smooth", 0) or 8))
+                                   "two-level: aggregates of %d vertices, %d + %d smoothing steps" % (lap or 48, sm, sm))
     return c
 
 
@@ -240,8 +240,8 @@ def pc_opts(args):
         o["precond"] = args.precond
     if args.schur_agg:
         o["schur_agg"] = args.schur_agg
-    if getattr(args, "lap_agg", 0):
-        o["lap_agg"] = args.lap_agg
+    if getattr(args, "lap_size", 0):
+        o["lap_size"] = args.lap_size
     if getattr(args, "lap_smooth", 0):
         o["lap_smooth"] = args.lap_smooth
     return o
@@ -964,8 +964,8 @@ def main():
                     "4 TRI_PMG_CS (coarse Schur correction), 5 AUTO (default: 4 on the batch and the bifurcation, "
                     "3 on the pipe)")
     ap.add_argument("--schur-agg", type=int, default=0, help="aggregates per component of TRI_PMG_CS (default 96)")
-    ap.add_argument("--lap-agg", type=int, default=0, help="pressure Laplacian: -1 plain Chebyshev polynomial "
-                    "(degree --cheb-l), else aggregates per component of its two-level cycle (default 200)")
+    ap.add_argument("--lap-size", type=int, default=0, help="pressure Laplacian: -1 plain Chebyshev polynomial "
+                    "(degree --cheb-l), else vertices per aggregate of its two-level cycle (default 48)")
     ap.add_argument("--lap-smooth", type=int, default=0, help="smoothing steps of the two-level pressure "
                     "Laplacian, each side (default 8)")
     ap.add_argument("--graphs", action="store_true", help="replay the Arnoldi steps from CUDA graphs (needs --no-timers)")

@@ -112,7 +112,7 @@ typedef struct {
   int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with the p-multigrid kinds the degree of each
                         of the pre- and post-smoothers (default 3) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
-  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian, when lap_agg = -1 (default 75) */
+  int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian, when lap_size = -1 (default 75) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
@@ -139,12 +139,13 @@ typedef struct {
                         captured on its first use after the first restart cycle of a solve; 0 (default): plain
                         launches.  Off while the kernel timers run.  A capture the runtime refuses falls back to
                         plain launches for the rest of the solve */
-  int32_t lap_agg;   /* pressure Laplacian L_p^-1 of the Schur approximation: 0 (default) or 1..224: a symmetric
+  int32_t lap_size;  /* pressure Laplacian L_p^-1 of the Schur approximation: 0 (default) or 1..4096: a symmetric
                         two-level cycle, S + coarse + S with S the lap_smooth-step Chebyshev-Jacobi polynomial on
-                        [lambda/30, 1.1 lambda] and a Galerkin coarse level R (R^T L_p R)^-1 R^T on graph
-                        aggregates of the vertices off the outlet (this many per connected component; 0: 200);
-                        -1: one Chebyshev polynomial of degree cheb_l on [lambda/3000, 1.1 lambda].  Meshes with a
-                        component that no outlet vertex reaches keep the polynomial (scvs_lap_info) */
+                        [lambda/120, 1.1 lambda] and a Galerkin coarse level R (R^T L_p R)^-1 R^T on graph
+                        aggregates of about this many vertices off the outlet (0: 48; at most 1024 aggregates
+                        per connected component, larger components get larger aggregates); -1: one Chebyshev
+                        polynomial of degree cheb_l on [lambda/3000, 1.1 lambda].  Meshes with a component
+                        that no outlet vertex reaches keep the polynomial (scvs_lap_info) */
   int32_t lap_smooth;/* Chebyshev degree of each smoother of that cycle (1..64; 0 or default: 8) */
   int32_t reserved;
 } scvs_opts;
@@ -605,7 +606,7 @@ int scvs_graph_aggregates(int64_t n_vert, const int64_t *row_ptr, const int32_t 
  * scvs_set_modes. */
 int scvs_schur_coarse_info(scvs_ctx *ctx, int32_t mesh_id, int32_t *info);
 
-/* Coarse level of the two-level pressure Laplacian of a mesh (opts.lap_agg >= 0; built on the first
+/* Coarse level of the two-level pressure Laplacian of a mesh (opts.lap_size >= 0; built on the first
  * preconditioner application with that option and kept for the mesh's lifetime): info[6] = {1 if the
  * cycle is in use, else 0 (the plain polynomial), aggregates, connected components of the vertex graph
  * without the outlet vertices, largest component's aggregates, components whose coarse matrix was

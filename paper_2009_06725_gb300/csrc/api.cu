@@ -258,7 +258,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->krylov = SCVS_KRYLOV_FGMRES;
   o->inner_max = 400;
   o->stage = -1;
-  o->lap_agg = 0;
+  o->lap_size = 0;
   o->lap_smooth = 0;
 }
 
@@ -269,7 +269,7 @@ static bool opts_valid(const scvs_opts *o) {
          o->schur_agg >= 0 && o->schur_agg <= 512 &&
          (o->stage == -1 || o->stage == 0 || o->stage == 4 || o->stage == 8 || o->stage == 16 || o->stage == 32) &&
          (o->krylov == SCVS_KRYLOV_FGMRES || o->krylov == SCVS_KRYLOV_COCR) && o->inner_max >= 1 &&
-         o->lap_agg >= -1 && o->lap_agg <= LAP_NA_MAX && o->lap_smooth >= 0 && o->lap_smooth <= 64;
+         o->lap_size >= -1 && o->lap_size <= 4096 && o->lap_smooth >= 0 && o->lap_smooth <= 64;
 }
 
 int scvs_create(scvs_ctx **out, const scvs_opts *opts) {

@@ -1295,18 +1295,19 @@ static ChebSeq cheb_seq(double lo, double hi, int s) {
 // P1 mass and P1 Laplacian.
 constexpr double CHEB_RATIO_U = 30.0, CHEB_RATIO_SMOOTH = 12.0, CHEB_RATIO_C = 30.0, CHEB_RATIO_M = 6.0,
                  CHEB_RATIO_L = 3000.0, CHEB_TOP = 1.10;
-// Smoother of the two-level pressure Laplacian: damps [lambda/30, 1.1 lambda]
-// and leaves the smooth end to the coarse level.
-constexpr double CHEB_RATIO_LAP = 30.0;
+// Smoother of the two-level pressure Laplacian: damps [lambda/120, 1.1 lambda]
+// and leaves the smooth end to the coarse level (on the benchmark pipe a wider
+// interval than a plain smoother's beat [lambda/30] and [lambda/60]).
+constexpr double CHEB_RATIO_LAP = 120.0;
 
-static void lap_build(Ctx &c, Mesh &m, int target);
-static int lap_target_of(const Ctx &c) { return c.opts.lap_agg > 0 ? c.opts.lap_agg : LAP_DEFAULT_AGG; }
+static void lap_build(Ctx &c, Mesh &m, int size);
+static int lap_size_of(const Ctx &c) { return c.opts.lap_size > 0 ? c.opts.lap_size : LAP_DEFAULT_SIZE; }
 // Smoothing degree of the two-level pressure Laplacian of a mesh, 0 where the
 // plain polynomial is used (option off, or no coarse level on this mesh).
 static int lap_smooth_of(Ctx &c, Mesh &m) {
-  if (c.opts.lap_agg < 0) return 0;
-  const int target = lap_target_of(c);
-  if (m.lap.target != target) lap_build(c, m, target);
+  if (c.opts.lap_size < 0) return 0;
+  const int size = lap_size_of(c);
+  if (m.lap.target != size) lap_build(c, m, size);
   return m.lap.on ? (c.opts.lap_smooth > 0 ? c.opts.lap_smooth : LAP_DEFAULT_SMOOTH) : 0;
 }
 
@@ -1702,9 +1703,11 @@ __global__ void k_cs_broadcast(const PcArgs a, int dim, const int32_t *__restric
 // aggregate left below a third of that size joins the first full-size
 // aggregate next to it (if any).  Aggregates are numbered by block, then by
 // seed.  grow starts at 1 and rises by 1.5x until no block has more than
-// min(2 target, CS_NA_MAX) aggregates (na_cap instead, if positive).  Columns
-// outside [0, P) are ignored.
-AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target, int na_cap) {
+// min(2 target, CS_NA_MAX) aggregates (na_cap instead, if positive).  With
+// size > 0 every block's aggregates are grown to `size` vertices instead (times
+// grow), whatever the block's size; target is then unused.  Columns outside
+// [0, P) are ignored.
+AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target, int na_cap, int size) {
   AggResult r;
   std::vector<int32_t> comp(P, -1), queue;
   std::vector<int64_t> csize;
@@ -1733,7 +1736,8 @@ AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, in
   double grow = 1.0;
   for (;;) {
     std::vector<int64_t> size_b(nb);
-    for (int b = 0; b < nb; ++b) size_b[b] = std::max<int64_t>(1, (int64_t)std::ceil(grow * (double)csize[b] / target));
+    for (int b = 0; b < nb; ++b)
+      size_b[b] = std::max<int64_t>(1, (int64_t)std::ceil(size > 0 ? grow * size : grow * (double)csize[b] / target));
     std::vector<int32_t> &agg = r.agg;
     std::fill(agg.begin(), agg.end(), -1);
     std::vector<int64_t> cnt;
@@ -1858,8 +1862,9 @@ static void build_aggregates(Ctx &c, Mesh &m, PcTables &t, int target) {
 // Galerkin matrix of the Laplacian's coarse level, row a of its block b:
 // W[so_b + loc(a) n_b + loc(agg(u))] = sum of L_p[v][u] over the vertices v of
 // aggregate a and their neighbours u off the outlet.  One thread block per
-// aggregate; thread c owns column c (n_b <= LAP_NA_MAX < 256) and visits the
-// nonzeros in storage order, so the sums are reproducible.
+// aggregate; thread t owns the columns t, t + 256, t + 512, t + 768 (n_b <=
+// LAP_NA_MAX) and visits the nonzeros in storage order, so the sums are
+// reproducible.
 __global__ void __launch_bounds__(256) k_lap_galerkin(const int64_t *__restrict__ agg_ptr,
                                                       const int32_t *__restrict__ agg_vert,
                                                       const int32_t *__restrict__ agg, const int32_t *__restrict__ agg_blk,
@@ -1868,76 +1873,94 @@ __global__ void __launch_bounds__(256) k_lap_galerkin(const int64_t *__restrict_
                                                       const int64_t *__restrict__ blk_so, const int64_t *__restrict__ g_ptr,
                                                       const int64_t *__restrict__ s_ptr, const int32_t *__restrict__ s_col,
                                                       const double *__restrict__ Lp, double *__restrict__ W) {
-  const int a = blockIdx.x, b = agg_blk[a], n = blk_na[b], c = threadIdx.x;
-  double acc = 0;
+  constexpr int NC = LAP_NA_MAX / 256;
+  const int a = blockIdx.x, b = agg_blk[a], n = blk_na[b], t = threadIdx.x;
+  double acc[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) acc[i] = 0;
   for (int64_t i = agg_ptr[a]; i < agg_ptr[a + 1]; ++i) {
     const int64_t v = agg_vert[i];
     const int64_t r0 = g_ptr[v], r1 = g_ptr[v + 1], s0 = s_ptr[v];
-    for (int64_t t = r0; t < r1; ++t) {
-      const int32_t au = agg[s_col[s0 + (t - r0)]];
-      if (au >= 0 && agg_loc[au] == c) acc += Lp[t];
+    for (int64_t e = r0; e < r1; ++e) {
+      const int32_t au = agg[s_col[s0 + (e - r0)]];
+      if (au < 0) continue;
+      const int c = agg_loc[au];
+      if ((c & 255) == t) acc[c >> 8] += Lp[e];
     }
   }
-  if (c < n) W[blk_so[b] + (int64_t)agg_loc[a] * n + c] = acc;
+#pragma unroll
+  for (int i = 0; i < NC; ++i)
+    if (t + 256 * i < n) W[blk_so[b] + (int64_t)agg_loc[a] * n + t + 256 * i] = acc[i];
 }
 
 // Inverse of every block's Galerkin matrix (symmetric positive definite when
-// an outlet vertex anchors the block) by the in-place Gauss-Jordan sweep in
-// FP32 shared memory, one thread block per block: for each pivot k, row k is
-// divided by a_kk, a_ij -= a_ik a_kj off row and column k, column k becomes
-// -a_ik / a_kk and a_kk its reciprocal.  A pivot at or below 1e-6 of the
-// largest diagonal entry (or not finite) marks the block singular: its inverse
-// is written as zero (coarse correction off there) and *n_singular counts it.
-__global__ void __launch_bounds__(1024) k_lap_invert(const int32_t *__restrict__ blk_na,
-                                                     const int64_t *__restrict__ blk_so, const double *__restrict__ W,
-                                                     float *__restrict__ inv_f, double *__restrict__ inv_d,
-                                                     int *n_singular) {
-  extern __shared__ float lap_sh[];
-  __shared__ float s_piv;
-  __shared__ int s_bad;
-  const int b = blockIdx.x, n = blk_na[b], tid = threadIdx.x, bd = blockDim.x;
-  const int64_t so = blk_so[b];
-  float *A = lap_sh, *colk = lap_sh + n * n;
-  for (int e = tid; e < n * n; e += bd) A[e] = (float)W[so + e];
-  __syncthreads();
-  if (tid == 0) {
-    float dmax = 0;
-    for (int i = 0; i < n; ++i) dmax = fmaxf(dmax, fabsf(A[i * n + i]));
-    s_piv = dmax;  // reused below for the pivot
-    s_bad = !(dmax > 0) || !isfinite(dmax);
+// an outlet vertex anchors the block) by the Gauss-Jordan sweep in FP32, all
+// blocks at once in one cooperative launch: at pivot k every entry of every
+// block with n_b > k is rewritten from the previous sweep's matrix (a_kk ->
+// 1/a_kk, row k -> a_kj/a_kk, column k -> -a_ik/a_kk, the rest a_ij -
+// a_ik a_kj/a_kk) into the other buffer, one bounded grid barrier per pivot.
+// A pivot at or below 1e-6 of the block's largest diagonal entry (or not
+// finite) marks the block singular: its inverse is written as zero (coarse
+// correction off there) and counted in *n_singular.  dmax[b] and bad[b] are
+// scratch; A0 holds the matrices on entry, A1 the other buffer.
+__global__ void __launch_bounds__(256) k_lap_invert(const int32_t *__restrict__ blk_na,
+                                                    const int64_t *__restrict__ blk_so, int n_blk, int na_max,
+                                                    const double *__restrict__ W, float *A0, float *A1, float *dmax,
+                                                    int *bad, float *__restrict__ inv_f, double *__restrict__ inv_d,
+                                                    int *n_singular, GridSync *gs) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const int64_t total = blk_so[n_blk - 1] + (int64_t)blk_na[n_blk - 1] * blk_na[n_blk - 1];
+  for (int64_t e = tid; e < total; e += nth) A0[e] = (float)W[e];
+  for (int64_t b = tid; b < n_blk; b += nth) {
+    const int n = blk_na[b];
+    float m = 0;
+    for (int i = 0; i < n; ++i) m = fmaxf(m, fabsf((float)W[blk_so[b] + (int64_t)i * n + i]));
+    dmax[b] = m;
+    bad[b] = !(m > 0) || !isfinite(m);
   }
-  __syncthreads();
-  const float dmax = s_piv;
-  __syncthreads();
-  for (int k = 0; k < n && !s_bad; ++k) {
-    if (tid == 0) {
-      const float pv = A[k * n + k];
-      if (!(pv > 1e-6f * dmax) || !isfinite(pv)) s_bad = 1;
-      s_piv = pv;
+  if (!grid_sync(gs, gridDim.x)) return;
+  float *cur = A0, *nxt = A1;
+  for (int k = 0; k < na_max; ++k) {
+    for (int64_t e = tid; e < total; e += nth) {
+      int lo = 0, hi = n_blk - 1;  // block of entry e: the last b with blk_so[b] <= e
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_so[mid] <= e) lo = mid; else hi = mid - 1;
+      }
+      const int b = lo, n = blk_na[b];
+      const int64_t so = blk_so[b];
+      const int i = (int)((e - so) / n), j = (int)((e - so) % n);
+      const float v = ld1co(cur + e);
+      if (k >= n || ld1co(bad + b)) { nxt[e] = v; continue; }
+      const float pv = ld1co(cur + so + (int64_t)k * n + k);
+      if (!(pv > 1e-6f * ld1co(dmax + b)) || !isfinite(pv)) {
+        nxt[e] = v;
+        if (i == 0 && j == 0) bad[b] = 1;  // read by every thread only after the next barrier
+        continue;
+      }
+      const float ip = 1.f / pv;
+      float o;
+      if (i == k && j == k) o = ip;
+      else if (i == k) o = v * ip;
+      else if (j == k) o = -v * ip;
+      else o = fmaf(-ld1co(cur + so + (int64_t)i * n + k) * ip, ld1co(cur + so + (int64_t)k * n + j), v);
+      nxt[e] = o;
     }
-    __syncthreads();
-    if (s_bad) break;  // uniform: read from shared memory after the barrier
-    const float ip = 1.f / s_piv;
-    for (int i = tid; i < n; i += bd) colk[i] = A[i * n + k];
-    __syncthreads();
-    for (int j = tid; j < n; j += bd)
-      if (j != k) A[k * n + j] *= ip;
-    __syncthreads();
-    for (int e = tid; e < n * n; e += bd) {
-      const int i = e / n, j = e % n;
-      if (i != k && j != k) A[e] = fmaf(-colk[i], A[k * n + j], A[e]);
+    if (!grid_sync(gs, gridDim.x)) return;
+    float *t = cur; cur = nxt; nxt = t;
+  }
+  for (int64_t e = tid; e < total; e += nth) {
+    int lo = 0, hi = n_blk - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (blk_so[mid] <= e) lo = mid; else hi = mid - 1;
     }
-    __syncthreads();
-    for (int i = tid; i < n; i += bd) A[i * n + k] = (i == k) ? ip : -colk[i] * ip;
-    __syncthreads();
+    const float v = ld1co(bad + lo) ? 0.f : ld1co(cur + e);
+    inv_f[e] = v;
+    inv_d[e] = (double)v;
   }
-  const bool bad = s_bad;
-  for (int e = tid; e < n * n; e += bd) {
-    const float v = bad ? 0.f : A[e];
-    inv_f[so + e] = v;
-    inv_d[so + e] = (double)v;
-  }
-  if (bad && tid == 0) atomicAdd(n_singular, 1);
+  for (int64_t b = tid; b < n_blk; b += nth)
+    if (ld1co(bad + b)) atomicAdd(n_singular, 1);
 }
 
 // Coarse level of the pressure Laplacian (host aggregation, device Galerkin
@@ -1945,10 +1968,10 @@ __global__ void __launch_bounds__(1024) k_lap_invert(const int32_t *__restrict__
 // graph is the vertex graph with the outlet vertices (p = 0 there) removed;
 // every connected component of it must touch the outlet, else the mesh keeps
 // the plain polynomial.
-static void lap_build(Ctx &c, Mesh &m, int target) {
+static void lap_build(Ctx &c, Mesh &m, int size) {
   LapCoarse &L = m.lap;
   L = LapCoarse{};
-  L.target = target;
+  L.target = size;
   const int64_t P = m.P;
   std::vector<int64_t> sp(P + 1);
   std::vector<int32_t> gl(std::max<int64_t>(P, 1));
@@ -1980,7 +2003,7 @@ static void lap_build(Ctx &c, Mesh &m, int target) {
     }
     cp[i + 1] = (int64_t)cc.size();
   }
-  const AggResult r = graph_aggregates(n, cp.data(), cc.empty() ? nullptr : cc.data(), target, LAP_NA_MAX);
+  const AggResult r = graph_aggregates(n, cp.data(), cc.empty() ? nullptr : cc.data(), 1, LAP_NA_MAX, size);
   const int n_agg = (int)r.blk.size(), nb = r.n_blk;
   std::vector<char> anch(nb, 0);
   for (int64_t i = 0; i < n; ++i)
@@ -2028,8 +2051,13 @@ static void lap_build(Ctx &c, Mesh &m, int target) {
   up(L.blk_a0, r.a0.data(), nb * sizeof(int32_t));
   up(L.blk_so, so.data(), nb * sizeof(int64_t));
   double *W = nullptr;
-  int *nsing = nullptr;
+  float *A0 = nullptr, *A1 = nullptr, *dmax = nullptr;
+  int *nsing = nullptr, *bad = nullptr;
   SCVS_CUDA(ctx_malloc(c, &W, (size_t)acc * sizeof(double), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &A0, (size_t)acc * sizeof(float), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &A1, (size_t)acc * sizeof(float), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &dmax, (size_t)nb * sizeof(float), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &bad, (size_t)nb * sizeof(int), c.stream));
   SCVS_CUDA(ctx_malloc(c, &nsing, sizeof(int), c.stream));
   SCVS_CUDA(cudaMemsetAsync(W, 0, (size_t)acc * sizeof(double), c.stream));
   SCVS_CUDA(cudaMemsetAsync(nsing, 0, sizeof(int), c.stream));
@@ -2040,17 +2068,26 @@ static void lap_build(Ctx &c, Mesh &m, int target) {
     count_launch(c);
   }
   {
-    KScope ks(c, KC_PRECOND, (double)acc * 20);
-    const size_t smem = (size_t)(r.na_max * r.na_max + r.na_max) * sizeof(float);
-    SCVS_CUDA(cudaFuncSetAttribute(k_lap_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lap_invert<<<nb, 1024, smem, c.stream>>>(L.blk_na, L.blk_so, W, L.inv_f, L.inv_d, nsing);
+    KScope ks(c, KC_PRECOND, (double)acc * 20 + (double)r.na_max * acc * 12);
+    const void *kfn = (const void *)k_lap_invert;
+    int n_blk = nb, na_max = r.na_max;
+    GridSync *gs = c.gsync;
+    void *args[] = {(void *)&L.blk_na, (void *)&L.blk_so, (void *)&n_blk, (void *)&na_max, (void *)&W, (void *)&A0,
+                    (void *)&A1, (void *)&dmax, (void *)&bad, (void *)&L.inv_f, (void *)&L.inv_d, (void *)&nsing,
+                    (void *)&gs};
+    SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn, 0)), dim3(256), args, 0, c.stream));
     count_launch(c);
   }
-  int h_sing = 0;
+  int h_sing = 0, gerr = 0;
   SCVS_CUDA(cudaMemcpyAsync(&h_sing, nsing, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  SCVS_CUDA(cudaFreeAsync(W, c.stream));
-  SCVS_CUDA(cudaFreeAsync(nsing, c.stream));
+  SCVS_CUDA(cudaMemcpyAsync(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  for (void *q : {(void *)W, (void *)A0, (void *)A1, (void *)dmax, (void *)bad, (void *)nsing})
+    SCVS_CUDA(cudaFreeAsync(q, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host vectors go out of scope
+  if (gerr) {  // a barrier wait gave up: the inverses are incomplete
+    SCVS_CUDA(cudaMemsetAsync(c.gsync, 0, sizeof(GridSync), c.stream));
+    throw (int)SCVS_ERR_TIMEOUT;
+  }
   L.singular = h_sing;
   L.on = true;
 }

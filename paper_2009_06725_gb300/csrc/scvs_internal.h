@@ -96,18 +96,20 @@ struct PcTables {
   int cs_singular = 0;               // (block, mode) pairs whose coarse matrix was singular (correction off)
 };
 
-// Coarse level of the two-level pressure Laplacian solve (opts.lap_agg >= 0):
+// Coarse level of the two-level pressure Laplacian solve (opts.lap_size >= 0):
 // graph aggregates of the vertices off the outlet (where the Laplacian has
-// p = 0), grouped by connected component of that graph ("block"), and the
-// inverse of every block's Galerkin matrix R^T L_p R (R the piecewise-constant
-// indicator of the aggregates).  Mode independent: built once per mesh and
-// target.  Blocks not reached by an outlet vertex make L_p singular there;
-// such a mesh keeps the plain Chebyshev polynomial (on = false).
-constexpr int LAP_NA_MAX = 224;  // aggregates of one block at most (its inverse is formed in shared memory)
-constexpr int LAP_DEFAULT_AGG = 200;
+// p = 0) of about lap_size vertices each (a fixed aggregate diameter keeps the
+// two-level convergence independent of the mesh size), grouped by connected
+// component of that graph ("block"), and the inverse of every block's Galerkin
+// matrix R^T L_p R (R the piecewise-constant indicator of the aggregates).
+// Mode independent: built once per mesh and size.  Blocks not reached by an
+// outlet vertex make L_p singular there; such a mesh keeps the plain
+// Chebyshev polynomial (on = false).
+constexpr int LAP_NA_MAX = 1024;  // aggregates of one block at most (larger blocks get larger aggregates)
+constexpr int LAP_DEFAULT_SIZE = 48;
 constexpr int LAP_DEFAULT_SMOOTH = 8;
 struct LapCoarse {
-  int target = 0;                    // aggregates per block asked for (0: not built)
+  int target = 0;                    // aggregate size asked for (0: not built)
   bool on = false;
   int n_agg = 0, n_blk = 0, na_max = 0, singular = 0, unanchored = 0;
   int32_t *agg = nullptr;            // [P] aggregate of every vertex, -1 on the outlet
@@ -358,7 +360,8 @@ struct AggResult {
   std::vector<int32_t> agg, blk, loc, na, a0;
   int n_blk = 0, na_max = 0;
 };
-AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target, int na_cap = 0);
+AggResult graph_aggregates(int64_t P, const int64_t *ptr, const int32_t *col, int target, int na_cap = 0,
+                           int size = 0);
 void matfree_tables(Ctx &c);  // matfree.cu
 
 // ---- krylov.cu

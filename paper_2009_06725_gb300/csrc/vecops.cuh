@@ -48,6 +48,8 @@ __device__ __forceinline__ void ldv_cg<float, 2>(CV<float, 2> &v, const float2 *
 // Coherent loads (ld.global.ca, never the read-only path) for data a
 // persistent kernel itself wrote before a grid barrier: the read-only path is
 // only valid for data that stays unchanged for the whole launch.
+__device__ __forceinline__ float ld1co(const float *p) { return __ldca(p); }
+__device__ __forceinline__ int ld1co(const int *p) { return __ldca(p); }
 __device__ __forceinline__ float2 ld1co(const float2 *p) { return __ldca(p); }
 __device__ __forceinline__ double2 ld1co(const double2 *p) { return __ldca(p); }
 template <typename T, int MPL>

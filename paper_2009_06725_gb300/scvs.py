@@ -45,7 +45,7 @@ class scvs_opts(C.Structure):
                 ("cheb_l", C.c_int32), ("max_cycles", C.c_int32), ("guess", C.c_int32),
                 ("verbose", C.c_int32), ("cheb_c", C.c_int32), ("autotune", C.c_int32), ("stream", C.c_void_p),
                 ("schur_agg", C.c_int32), ("stage", C.c_int32), ("krylov", C.c_int32),
-                ("inner_max", C.c_int32), ("graphs", C.c_int32), ("lap_agg", C.c_int32), ("lap_smooth", C.c_int32),
+                ("inner_max", C.c_int32), ("graphs", C.c_int32), ("lap_size", C.c_int32), ("lap_smooth", C.c_int32),
                 ("reserved", C.c_int32)]
 
 

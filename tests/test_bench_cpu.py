@@ -29,13 +29,13 @@ def test_pc_config_and_opts():
     assert bench.pc_config(a)["precond"].startswith("auto") and bench.pc_opts(a) == {}
     a = argparse.Namespace(precond=4, schur_agg=0)
     assert bench.pc_config(a) == {"precond": "triangular-pmg + coarse Schur correction", "schur_agg": 96,
-                                  "pressure_laplacian": "two-level: 200 aggregates per component, 8 + 8 smoothing steps"}
+                                  "pressure_laplacian": "two-level: aggregates of 48 vertices, 8 + 8 smoothing steps"}
     assert bench.pc_opts(a) == {"precond": 4}
     a = argparse.Namespace(precond=4, schur_agg=64)
     assert bench.pc_opts(a) == {"precond": 4, "schur_agg": 64} and bench.pc_config(a)["schur_agg"] == 64
-    a = argparse.Namespace(precond=None, schur_agg=0, lap_agg=-1, lap_smooth=0, cheb_l=60)
-    assert bench.pc_opts(a) == {"lap_agg": -1}
+    a = argparse.Namespace(precond=None, schur_agg=0, lap_size=-1, lap_smooth=0, cheb_l=60)
+    assert bench.pc_opts(a) == {"lap_size": -1}
     assert bench.pc_config(a)["pressure_laplacian"] == "chebyshev degree 60"
-    a = argparse.Namespace(precond=1, schur_agg=0, lap_agg=32, lap_smooth=4)
-    assert bench.pc_opts(a) == {"precond": 1, "lap_agg": 32, "lap_smooth": 4}
+    a = argparse.Namespace(precond=1, schur_agg=0, lap_size=32, lap_smooth=4)
+    assert bench.pc_opts(a) == {"precond": 1, "lap_size": 32, "lap_smooth": 4}
     assert "pressure_laplacian" not in bench.pc_config(a)

@@ -39,10 +39,10 @@ def test_default_options():
     assert o.tol == 1e-8 and o.restart == 30 and o.precision == scvs.SCVS_PREC_MIXED
     assert o.cheb_u >= 1 and o.max_cycles >= 1
     assert o.stage == -1 and o.krylov == scvs.SCVS_KRYLOV_FGMRES and o.inner_max == 400
-    assert o.lap_agg == 0 and o.lap_smooth == 0
+    assert o.lap_size == 0 and o.lap_smooth == 0
 
 
-@pytest.mark.parametrize("field,value", [("lap_agg", -2), ("lap_agg", 225), ("lap_smooth", -1), ("lap_smooth", 65),
+@pytest.mark.parametrize("field,value", [("lap_size", -2), ("lap_size", 4097), ("lap_smooth", -1), ("lap_smooth", 65),
                                          ("stage", 3), ("schur_agg", 513)])
 def test_invalid_options_are_refused_before_any_device_call(field, value):
     o = scvs.scvs_default_opts()
