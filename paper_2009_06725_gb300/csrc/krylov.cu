@@ -915,11 +915,13 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
   std::vector<int> state(S), kd(S);
   const int max_cycles = std::max(1, c.opts.max_cycles);
   for (int cyc = 0; cyc <= max_cycles; ++cyc) {
-    // 1. FP64 true residual; r goes to V_0 (unnormalized)
+    // 1. FP64 true residual; r goes to V_0 (unnormalized).  From the zero start
+    //    it is the right-hand side itself (no product needed).
+    const bool zero_start = cyc == 0 && !warm && !guess_on;
     if constexpr (sizeof(T) == 4)
-      residual_fp64(c, m, wk.V, nullptr, wk.norm2);
+      residual_fp64(c, m, wk.V, nullptr, wk.norm2, zero_start);
     else
-      residual_fp64(c, m, nullptr, wk.V, wk.norm2);
+      residual_fp64(c, m, nullptr, wk.V, wk.norm2, zero_start);
     SCVS_CUDA(cudaMemcpyAsync(n2.data(), wk.norm2, S * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     SCVS_CUDA(cudaStreamSynchronize(c.stream));
     if (cyc == 0 && check_guess) {

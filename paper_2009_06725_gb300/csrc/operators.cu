@@ -383,7 +383,7 @@ __global__ void k_residual_finish(const double2 *__restrict__ b, const double2 *
   int64_t dof = f / ld;
   if (row_idle(dof_comp, comp_active, dof)) return;
   bool dir = dof < N * dim && dirm[dof / dim];
-  double2 bb = b[f], a = ax[f];
+  double2 bb = b[f], a = ax ? ax[f] : make_double2(0.0, 0.0);
   double2 r = dir ? make_double2(0.0, 0.0) : make_double2(bb.x - a.x, bb.y - a.y);
   if (r32) r32[f] = make_float2((float)r.x, (float)r.y);
   if (r64) r64[f] = r;
@@ -2630,9 +2630,22 @@ void spectral_bounds(Ctx &c, Mesh &m) {
 }
 
 // Residual of the current FP64 iterate: r = b - A_hat x (FP64 SpMM) and the
-// per-mode squared free-row norms into norm2_out_dev[ld].
-void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev) {
+// per-mode squared free-row norms into norm2_out_dev[ld].  zero_start: x is
+// the zero start (g on the Dirichlet rows, 0 elsewhere), whose product with the
+// masked operator A_hat is exactly zero (every Dirichlet column is masked), so
+// r = b on the free rows bit for bit and the FP64 product is skipped.
+void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev, bool zero_start) {
   const int64_t total = m.n_dof * m.ld;
+  if (zero_start) {
+    if (r32 || r64) {
+      KScope ks(c, KC_VECTOR, (double)total * (16 + (r64 ? 16 : 0) + (r32 ? 8 : 0)));
+      k_residual_finish<<<ceil_div(total, 256), 256, 0, c.stream>>>(m.b, nullptr, m.dirmask, m.N, m.dim, total, m.ld,
+                                                                    r32, r64, m.dof_comp, m.comp_active);
+      count_launch(c);
+    }
+    norms2_sys(c, m, r64 ? r64 : m.b, norm2_out_dev);  // the free rows of r and b hold the same values
+    return;
+  }
   double2 *ax = nullptr;
   SCVS_CUDA(ctx_malloc(c, &ax, total * sizeof(double2), c.stream));
   launch_saddle<double>(c, m, saddle_args<double>(c, m, true), m.x, ax);

@@ -344,7 +344,7 @@ void lift_rhs(Ctx &c, Mesh &m);
 double saddle_bytes(const Mesh &m, int value_size);
 int64_t precond_scratch_elems(const Mesh &m);
 void autotune_shapes(Ctx &c, Mesh &m);
-void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev);
+void residual_fp64(Ctx &c, Mesh &m, float2 *r32, double2 *r64, double *norm2_out_dev, bool zero_start = false);
 void norms2_sys(Ctx &c, const Mesh &m, const double2 *v, double *out_dev);  // [n_sys] free-row squared norms
 void set_chunks(Ctx &c, Mesh &m, const int32_t *node_comp_host, int n_comp);
 void spectral_bounds(Ctx &c, Mesh &m);
