@@ -223,7 +223,7 @@ def pc_config(args):
         lap = getattr(args, "lap_size", 0) or 0
         sm = getattr(args, "lap_smooth", 0) or 8
         c["pressure_laplacian"] = ("chebyshev degree %d" % (getattr(args, "cheb_l", 0) or 75) if lap < 0 else
-                                   "two-level: aggregates of %d vertices, %d + %d smoothing steps" % (lap or 48, sm, sm))
+                                   "two-level: aggregates of %d vertices, %d + %d smoothing steps" % (lap or 32, sm, sm))
     return c
 
 
@@ -965,7 +965,7 @@ def main():
                     "3 on the pipe)")
     ap.add_argument("--schur-agg", type=int, default=0, help="aggregates per component of TRI_PMG_CS (default 96)")
     ap.add_argument("--lap-size", type=int, default=0, help="pressure Laplacian: -1 plain Chebyshev polynomial "
-                    "(degree --cheb-l), else vertices per aggregate of its two-level cycle (default 48)")
+                    "(degree --cheb-l), else vertices per aggregate of its two-level cycle (default 32)")
     ap.add_argument("--lap-smooth", type=int, default=0, help="smoothing steps of the two-level pressure "
                     "Laplacian, each side (default 8)")
     ap.add_argument("--graphs", action="store_true", help="replay the Arnoldi steps from CUDA graphs (needs --no-timers)")

@@ -142,7 +142,7 @@ typedef struct {
   int32_t lap_size;  /* pressure Laplacian L_p^-1 of the Schur approximation: 0 (default) or 1..4096: a symmetric
                         two-level cycle, S + coarse + S with S the lap_smooth-step Chebyshev-Jacobi polynomial on
                         [lambda/120, 1.1 lambda] and a Galerkin coarse level R (R^T L_p R)^-1 R^T on graph
-                        aggregates of about this many vertices off the outlet (0: 48; at most 1024 aggregates
+                        aggregates of about this many vertices off the outlet (0: 32; at most 1024 aggregates
                         per connected component, larger components get larger aggregates); -1: one Chebyshev
                         polynomial of degree cheb_l on [lambda/3000, 1.1 lambda].  Meshes with a component
                         that no outlet vertex reaches keep the polynomial (scvs_lap_info) */

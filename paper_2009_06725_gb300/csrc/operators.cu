@@ -1894,20 +1894,41 @@ __global__ void __launch_bounds__(256) k_lap_galerkin(const int64_t *__restrict_
 }
 
 // Inverse of every block's Galerkin matrix (symmetric positive definite when
-// an outlet vertex anchors the block) by the Gauss-Jordan sweep in FP32, all
-// blocks at once in one cooperative launch: at pivot k every entry of every
-// block with n_b > k is rewritten from the previous sweep's matrix (a_kk ->
-// 1/a_kk, row k -> a_kj/a_kk, column k -> -a_ik/a_kk, the rest a_ij -
-// a_ik a_kj/a_kk) into the other buffer, one bounded grid barrier per pivot.
-// A pivot at or below 1e-6 of the block's largest diagonal entry (or not
-// finite) marks the block singular: its inverse is written as zero (coarse
-// correction off there) and counted in *n_singular.  dmax[b] and bad[b] are
+// an outlet vertex anchors the block) by the blocked Gauss-Jordan sweep in
+// FP32, all blocks at once in one cooperative launch.  For each group K of
+// LAP_BS pivots (k0 .. k0+bs-1) of every block with n_b > k0, from the matrix
+// A of the previous sweep into the other buffer A':
+//   1. D = A[K,K]^-1 (one thread block per block, in shared memory),
+//   2. A'[K,K] = D, A'[K,j] = D A[K,j] and A'[i,K] = -A[i,K] D (i, j outside K),
+//   3. A'[i,j] = A[i,j] - A[i,K] A'[K,j] (i, j outside K; 32 x 32 tiles with both
+//      factors staged in shared memory),
+// each phase ending at a bounded grid barrier (three per pivot group instead
+// of one per pivot).  A pivot at or below 1e-6 of the block's largest
+// diagonal entry (or not finite) marks the block singular: its inverse is
+// written as zero (coarse correction off there) and counted in *n_singular.
+// tile0 / pan0 [n_blk+1] are the offsets of every block's 32 x 32 tiles and
+// panel entries (2 LAP_BS n_b); dmax, bad and Dinv (n_blk LAP_BS^2) are
 // scratch; A0 holds the matrices on entry, A1 the other buffer.
+constexpr int LAP_BS = 32;
+__device__ __forceinline__ int lap_find(const int64_t *__restrict__ off, int n, int64_t e) {
+  int lo = 0, hi = n - 1;  // the last b with off[b] <= e
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(256) k_lap_invert(const int32_t *__restrict__ blk_na,
-                                                    const int64_t *__restrict__ blk_so, int n_blk, int na_max,
+                                                    const int64_t *__restrict__ blk_so,
+                                                    const int64_t *__restrict__ tile0,
+                                                    const int64_t *__restrict__ pan0, int n_blk, int na_max,
                                                     const double *__restrict__ W, float *A0, float *A1, float *dmax,
-                                                    int *bad, float *__restrict__ inv_f, double *__restrict__ inv_d,
-                                                    int *n_singular, GridSync *gs) {
+                                                    int *bad, float *Dinv, float *__restrict__ inv_f,
+                                                    double *__restrict__ inv_d, int *n_singular, GridSync *gs) {
+  __shared__ float sA[LAP_BS][LAP_BS + 1], sB[LAP_BS][LAP_BS + 1];
+  __shared__ float s_piv;
+  __shared__ int s_bad;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   const int64_t total = blk_so[n_blk - 1] + (int64_t)blk_na[n_blk - 1] * blk_na[n_blk - 1];
   for (int64_t e = tid; e < total; e += nth) A0[e] = (float)W[e];
@@ -1920,42 +1941,116 @@ __global__ void __launch_bounds__(256) k_lap_invert(const int32_t *__restrict__ 
   }
   if (!grid_sync(gs, gridDim.x)) return;
   float *cur = A0, *nxt = A1;
-  for (int k = 0; k < na_max; ++k) {
-    for (int64_t e = tid; e < total; e += nth) {
-      int lo = 0, hi = n_blk - 1;  // block of entry e: the last b with blk_so[b] <= e
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (blk_so[mid] <= e) lo = mid; else hi = mid - 1;
+  const int t = threadIdx.x;
+  for (int k0 = 0; k0 < na_max; k0 += LAP_BS) {
+    // 1. D = A[K,K]^-1 per block (in-place Gauss-Jordan sweep in shared memory)
+    for (int b = blockIdx.x; b < n_blk; b += gridDim.x) {
+      const int n = blk_na[b];
+      if (n <= k0 || ld1co(bad + b)) continue;  // block-uniform
+      const int bs = min(LAP_BS, n - k0);
+      const float *A = cur + blk_so[b];
+      for (int e = t; e < bs * bs; e += blockDim.x)
+        sA[e / bs][e % bs] = ld1co(A + (int64_t)(k0 + e / bs) * n + k0 + e % bs);
+      if (t == 0) s_bad = 0;
+      __syncthreads();
+      const float dm = ld1co(dmax + b);
+      for (int k = 0; k < bs; ++k) {
+        if (t == 0) {
+          const float pv = sA[k][k];
+          if (!(pv > 1e-6f * dm) || !isfinite(pv)) s_bad = 1;
+          s_piv = pv;
+        }
+        __syncthreads();
+        if (s_bad) break;  // uniform: read from shared memory after the barrier
+        const float ip = 1.f / s_piv;
+        if (t < bs) sB[0][t] = sA[t][k];  // column k before the sweep
+        __syncthreads();
+        if (t < bs && t != k) sA[k][t] *= ip;
+        __syncthreads();
+        for (int e = t; e < bs * bs; e += blockDim.x) {
+          const int i = e / bs, j = e % bs;
+          if (i != k && j != k) sA[i][j] = fmaf(-sB[0][i], sA[k][j], sA[i][j]);
+        }
+        __syncthreads();
+        if (t < bs) sA[t][k] = (t == k) ? ip : -sB[0][t] * ip;
+        __syncthreads();
       }
-      const int b = lo, n = blk_na[b];
-      const int64_t so = blk_so[b];
-      const int i = (int)((e - so) / n), j = (int)((e - so) % n);
-      const float v = ld1co(cur + e);
-      if (k >= n || ld1co(bad + b)) { nxt[e] = v; continue; }
-      const float pv = ld1co(cur + so + (int64_t)k * n + k);
-      if (!(pv > 1e-6f * ld1co(dmax + b)) || !isfinite(pv)) {
-        nxt[e] = v;
-        if (i == 0 && j == 0) bad[b] = 1;  // read by every thread only after the next barrier
-        continue;
+      if (s_bad) {
+        if (t == 0) bad[b] = 1;
+      } else {
+        for (int e = t; e < bs * bs; e += blockDim.x) Dinv[(int64_t)b * LAP_BS * LAP_BS + e] = sA[e / bs][e % bs];
       }
-      const float ip = 1.f / pv;
-      float o;
-      if (i == k && j == k) o = ip;
-      else if (i == k) o = v * ip;
-      else if (j == k) o = -v * ip;
-      else o = fmaf(-ld1co(cur + so + (int64_t)i * n + k) * ip, ld1co(cur + so + (int64_t)k * n + j), v);
-      nxt[e] = o;
+      __syncthreads();
     }
     if (!grid_sync(gs, gridDim.x)) return;
-    float *t = cur; cur = nxt; nxt = t;
+    // 2. the pivot rows and columns: A'[K,j] = D A[K,j] (with A'[K,K] = D), A'[i,K] = -A[i,K] D
+    for (int64_t e = tid; e < pan0[n_blk]; e += nth) {
+      const int b = lap_find(pan0, n_blk, e);
+      const int n = blk_na[b];
+      if (n <= k0 || ld1co(bad + b)) continue;
+      const int bs = min(LAP_BS, n - k0);
+      const int64_t q = e - pan0[b];
+      const float *A = cur + blk_so[b];
+      float *O = nxt + blk_so[b];
+      const float *D = Dinv + (int64_t)b * LAP_BS * LAP_BS;
+      if (q < (int64_t)LAP_BS * n) {  // row panel entry (k0 + r, j)
+        const int r = (int)(q / n), j = (int)(q % n);
+        if (r >= bs) continue;
+        float o;
+        if (j >= k0 && j < k0 + bs) {
+          o = ld1co(D + r * bs + (j - k0));
+        } else {
+          o = 0.f;
+          for (int u = 0; u < bs; ++u) o = fmaf(ld1co(D + r * bs + u), ld1co(A + (int64_t)(k0 + u) * n + j), o);
+        }
+        O[(int64_t)(k0 + r) * n + j] = o;
+      } else {  // column panel entry (i, k0 + c), i outside K
+        const int64_t q2 = q - (int64_t)LAP_BS * n;
+        const int c = (int)(q2 / n), i = (int)(q2 % n);
+        if (c >= bs || (i >= k0 && i < k0 + bs)) continue;
+        float o = 0.f;
+        for (int u = 0; u < bs; ++u) o = fmaf(ld1co(A + (int64_t)i * n + k0 + u), ld1co(D + u * bs + c), o);
+        O[(int64_t)i * n + k0 + c] = -o;
+      }
+    }
+    if (!grid_sync(gs, gridDim.x)) return;
+    // 3. the rest: A'[i,j] = A[i,j] - A[i,K] A'[K,j], by 32 x 32 tiles (finished or
+    //    singular blocks are carried over unchanged)
+    for (int64_t tl = blockIdx.x; tl < tile0[n_blk]; tl += gridDim.x) {
+      const int b = lap_find(tile0, n_blk, tl);
+      const int n = blk_na[b], nt = (n + LAP_BS - 1) / LAP_BS;
+      const int64_t q = tl - tile0[b];
+      const int i0 = (int)(q / nt) * LAP_BS, j0 = (int)(q % nt) * LAP_BS;
+      const float *A = cur + blk_so[b];
+      float *O = nxt + blk_so[b];
+      const bool active = n > k0 && !ld1co(bad + b);  // block-uniform
+      const int bs = active ? min(LAP_BS, n - k0) : 0;
+      if (active) {
+        for (int e = t; e < LAP_BS * LAP_BS; e += blockDim.x) {
+          const int r = e / LAP_BS, cc = e % LAP_BS;
+          sA[r][cc] = (i0 + r < n && cc < bs) ? ld1co(A + (int64_t)(i0 + r) * n + k0 + cc) : 0.f;
+          sB[r][cc] = (r < bs && j0 + cc < n) ? ld1co(O + (int64_t)(k0 + r) * n + j0 + cc) : 0.f;
+        }
+      }
+      __syncthreads();
+      for (int e = t; e < LAP_BS * LAP_BS; e += blockDim.x) {
+        const int i = i0 + e / LAP_BS, j = j0 + e % LAP_BS;
+        if (i >= n || j >= n) continue;
+        const int64_t f = (int64_t)i * n + j;
+        if (!active) { O[f] = ld1co(A + f); continue; }
+        if ((i >= k0 && i < k0 + bs) || (j >= k0 && j < k0 + bs)) continue;  // written in phase 2
+        float o = ld1co(A + f);
+        for (int u = 0; u < bs; ++u) o = fmaf(-sA[e / LAP_BS][u], sB[u][e % LAP_BS], o);
+        O[f] = o;
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(gs, gridDim.x)) return;
+    float *tmp = cur; cur = nxt; nxt = tmp;
   }
   for (int64_t e = tid; e < total; e += nth) {
-    int lo = 0, hi = n_blk - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (blk_so[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    const float v = ld1co(bad + lo) ? 0.f : ld1co(cur + e);
+    const int b = lap_find(blk_so, n_blk, e);
+    const float v = ld1co(bad + b) ? 0.f : ld1co(cur + e);
     inv_f[e] = v;
     inv_d[e] = (double)v;
   }
@@ -2050,15 +2145,27 @@ static void lap_build(Ctx &c, Mesh &m, int size) {
   up(L.blk_na, r.na.data(), nb * sizeof(int32_t));
   up(L.blk_a0, r.a0.data(), nb * sizeof(int32_t));
   up(L.blk_so, so.data(), nb * sizeof(int64_t));
+  std::vector<int64_t> tile0(nb + 1, 0), pan0(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t nt = (r.na[b] + LAP_BS - 1) / LAP_BS;
+    tile0[b + 1] = tile0[b] + nt * nt;
+    pan0[b + 1] = pan0[b] + 2 * (int64_t)LAP_BS * r.na[b];
+  }
   double *W = nullptr;
-  float *A0 = nullptr, *A1 = nullptr, *dmax = nullptr;
+  float *A0 = nullptr, *A1 = nullptr, *dmax = nullptr, *Dinv = nullptr;
   int *nsing = nullptr, *bad = nullptr;
+  int64_t *tile0_d = nullptr, *pan0_d = nullptr;
   SCVS_CUDA(ctx_malloc(c, &W, (size_t)acc * sizeof(double), c.stream));
   SCVS_CUDA(ctx_malloc(c, &A0, (size_t)acc * sizeof(float), c.stream));
   SCVS_CUDA(ctx_malloc(c, &A1, (size_t)acc * sizeof(float), c.stream));
   SCVS_CUDA(ctx_malloc(c, &dmax, (size_t)nb * sizeof(float), c.stream));
   SCVS_CUDA(ctx_malloc(c, &bad, (size_t)nb * sizeof(int), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &Dinv, (size_t)nb * LAP_BS * LAP_BS * sizeof(float), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &tile0_d, (size_t)(nb + 1) * sizeof(int64_t), c.stream));
+  SCVS_CUDA(ctx_malloc(c, &pan0_d, (size_t)(nb + 1) * sizeof(int64_t), c.stream));
   SCVS_CUDA(ctx_malloc(c, &nsing, sizeof(int), c.stream));
+  up(tile0_d, tile0.data(), (nb + 1) * sizeof(int64_t));
+  up(pan0_d, pan0.data(), (nb + 1) * sizeof(int64_t));
   SCVS_CUDA(cudaMemsetAsync(W, 0, (size_t)acc * sizeof(double), c.stream));
   SCVS_CUDA(cudaMemsetAsync(nsing, 0, sizeof(int), c.stream));
   {
@@ -2068,20 +2175,21 @@ static void lap_build(Ctx &c, Mesh &m, int size) {
     count_launch(c);
   }
   {
-    KScope ks(c, KC_PRECOND, (double)acc * 20 + (double)r.na_max * acc * 12);
+    KScope ks(c, KC_PRECOND, (double)acc * 20 + (double)((r.na_max + LAP_BS - 1) / LAP_BS) * acc * 12);
     const void *kfn = (const void *)k_lap_invert;
     int n_blk = nb, na_max = r.na_max;
     GridSync *gs = c.gsync;
-    void *args[] = {(void *)&L.blk_na, (void *)&L.blk_so, (void *)&n_blk, (void *)&na_max, (void *)&W, (void *)&A0,
-                    (void *)&A1, (void *)&dmax, (void *)&bad, (void *)&L.inv_f, (void *)&L.inv_d, (void *)&nsing,
-                    (void *)&gs};
+    void *args[] = {(void *)&L.blk_na, (void *)&L.blk_so, (void *)&tile0_d, (void *)&pan0_d, (void *)&n_blk,
+                    (void *)&na_max, (void *)&W, (void *)&A0, (void *)&A1, (void *)&dmax, (void *)&bad,
+                    (void *)&Dinv, (void *)&L.inv_f, (void *)&L.inv_d, (void *)&nsing, (void *)&gs};
     SCVS_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(coop_grid(c, kfn, 0)), dim3(256), args, 0, c.stream));
     count_launch(c);
   }
   int h_sing = 0, gerr = 0;
   SCVS_CUDA(cudaMemcpyAsync(&h_sing, nsing, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   SCVS_CUDA(cudaMemcpyAsync(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  for (void *q : {(void *)W, (void *)A0, (void *)A1, (void *)dmax, (void *)bad, (void *)nsing})
+  for (void *q : {(void *)W, (void *)A0, (void *)A1, (void *)dmax, (void *)bad, (void *)Dinv, (void *)tile0_d,
+                  (void *)pan0_d, (void *)nsing})
     SCVS_CUDA(cudaFreeAsync(q, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host vectors go out of scope
   if (gerr) {  // a barrier wait gave up: the inverses are incomplete

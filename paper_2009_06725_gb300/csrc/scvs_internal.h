@@ -106,7 +106,7 @@ struct PcTables {
 // outlet vertex make L_p singular there; such a mesh keeps the plain
 // Chebyshev polynomial (on = false).
 constexpr int LAP_NA_MAX = 1024;  // aggregates of one block at most (larger blocks get larger aggregates)
-constexpr int LAP_DEFAULT_SIZE = 48;
+constexpr int LAP_DEFAULT_SIZE = 32;
 constexpr int LAP_DEFAULT_SMOOTH = 8;
 struct LapCoarse {
   int target = 0;                    // aggregate size asked for (0: not built)

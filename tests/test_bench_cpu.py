@@ -29,7 +29,7 @@ def test_pc_config_and_opts():
     assert bench.pc_config(a)["precond"].startswith("auto") and bench.pc_opts(a) == {}
     a = argparse.Namespace(precond=4, schur_agg=0)
     assert bench.pc_config(a) == {"precond": "triangular-pmg + coarse Schur correction", "schur_agg": 96,
-                                  "pressure_laplacian": "two-level: aggregates of 48 vertices, 8 + 8 smoothing steps"}
+                                  "pressure_laplacian": "two-level: aggregates of 32 vertices, 8 + 8 smoothing steps"}
     assert bench.pc_opts(a) == {"precond": 4}
     a = argparse.Namespace(precond=4, schur_agg=64)
     assert bench.pc_opts(a) == {"precond": 4, "schur_agg": 64} and bench.pc_config(a)["schur_agg"] == 64
