@@ -735,7 +735,7 @@ def run_guess(args):
         rep = scvs.scvs_solve(s.ctx, mid, len(f))
         return mid, rep, time.perf_counter() - t
 
-    with scvs.Solver() as s:
+    with scvs.Solver(**pc_opts(args)) as s:
         t0 = time.perf_counter()
         for i in range(args.guess_train):
             wl, f = morph(i)
@@ -765,7 +765,8 @@ def run_guess(args):
            "n_gpus": 1, "higher_is_better": True, "impl": "learned-guess", "data": "synthetic", "dtype": "c64+f64",
            "config": {"workload": (f"learned initial guess: {args.guess_train} training morphs x 32 modes of the "
                                    f"151k-node pipe (R 0.5-1.5, s 0-0.5), {args.guess_test} held-out morphs"),
-                      "snapshots": info["n_snapshots"], "n_pod": info["n_pod"], "mlp": "5-256-256-256-128 GELU BF16"},
+                      "snapshots": info["n_snapshots"], "n_pod": info["n_pod"], "mlp": "5-256-256-256-128 GELU BF16",
+                      **pc_config(args)},
            "without_guess": {"value": n / t0s, "iterations_mean": float(np.mean(it0)), "iterations_max": int(max(it0)),
                              "solve_s": t0s},
            "with_guess": {"value": conv1 / t1s, "iterations_mean": float(np.mean(it1)), "iterations_max": int(max(it1)),
