@@ -208,7 +208,7 @@ class ClockSampler:
 
 PC_NAMES = {0: "block-chebyshev", 1: "block-diagonal", 2: "block-pmg", 3: "triangular-pmg",
             4: "triangular-pmg + coarse Schur correction",
-            5: "auto (triangular-pmg; + coarse Schur correction on multi-component or > 1M-node meshes)"}
+            5: "auto (triangular-pmg + coarse Schur correction)"}
 
 
 def pc_config(args):
@@ -218,7 +218,7 @@ def pc_config(args):
     if getattr(args, "krylov", "fgmres") == "cocr":
         c["krylov"] = "cocr"
     if kind in (4, 5):
-        c["schur_agg"] = args.schur_agg or 96
+        c["schur_agg"] = args.schur_agg or 16
     if kind != 1:
         lap = getattr(args, "lap_size", 0) or 0
         sm = getattr(args, "lap_smooth", 0) or 8

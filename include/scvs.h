@@ -87,11 +87,10 @@ extern "C" {
                                   The n_c x n_c matrices (real: the cycle is real-linear) are formed and inverted
                                   in FP64 on the first application after scvs_set_modes / scvs_set_physics /
                                   an option change (n_c/2 velocity cycles for all modes at once) */
-#define SCVS_PC_AUTO 5         /* default: per mesh, TRI_PMG_CS on meshes of several components or more than 10^6
-                                  nodes (their long, thin or branched parts are where the Cahouet-Chabard
-                                  approximation alone degrades: measured 4.4x and 16x faster solves on the batch
-                                  of 48 pipes and the 5.7M-node bifurcation), TRI_PMG otherwise (on a single 151k-node
-                                  pipe the correction's set-up costs more than its saved iterations) */
+#define SCVS_PC_AUTO 5         /* default: TRI_PMG_CS (with the default 16 aggregates per component the correction
+                                  removes the iteration tails of long, thin, stenosed or branched domains, where the
+                                  Cahouet-Chabard approximation alone degrades, and its set-up of 8 velocity cycles
+                                  costs less than the iterations it saves even on the single 151k-node pipe) */
 
 #define SCVS_GUESS_ZERO 0
 #define SCVS_GUESS_MLP 1
@@ -123,7 +122,7 @@ typedef struct {
                         stride, components) and reused; 0: default shapes */
   void *stream;      /* cudaStream_t to run on; NULL = the legacy default stream */
   int32_t schur_agg; /* SCVS_PC_TRI_PMG_CS: aggregates per connected component of the vertex graph (1..512;
-                        0 or default: 96); aggregates are grown to ceil(vertices / schur_agg) vertices, so a
+                        0 or default: 16); aggregates are grown to ceil(vertices / schur_agg) vertices, so a
                         component may end with somewhat more or fewer */
   int32_t stage;     /* staged gathers of the FP32 SpMM and fine Chebyshev kernels (row blocks of compact
                         footprint, the footprint copied into shared memory by TMA bulk copies or cp.async):

@@ -254,7 +254,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->guess = SCVS_GUESS_ZERO;
   o->verbose = 0;
   o->stream = nullptr;
-  o->schur_agg = 96;
+  o->schur_agg = 16;
   o->krylov = SCVS_KRYLOV_FGMRES;
   o->inner_max = 400;
   o->stage = -1;

@@ -1348,11 +1348,14 @@ static void per_mode_seq(Ctx &c, Mesh &m, const std::vector<double> &lam, double
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
 }
 
-// The preconditioner kind of a mesh: SCVS_PC_AUTO resolves to the coarse
-// Schur correction on multi-component or large meshes.
+// The preconditioner kind of a mesh: SCVS_PC_AUTO resolves to the triangular
+// form with the coarse Schur correction (with 16 aggregates per component it
+// was the fastest kind on every workload measured, the single 151k-node pipe
+// included).
 int pc_kind(const Ctx &c, const Mesh &m) {
+  (void)m;
   if (c.opts.precond != SCVS_PC_AUTO) return c.opts.precond;
-  return (m.n_comp > 1 || m.N > 1000000) ? SCVS_PC_TRI_PMG_CS : SCVS_PC_TRI_PMG;
+  return SCVS_PC_TRI_PMG_CS;
 }
 
 static void pc_tables(Ctx &c, Mesh &m, PcTables &t) {
@@ -1510,7 +1513,7 @@ static typename cpx<T>::t *coarse_solve(Ctx &c, const Mesh &m, const PcArgs &a, 
 // the coarse matrices are real; a complex lane carries two coarse columns.
 
 constexpr int CS_NA_MAX = 1024;  // aggregates of one block at most
-constexpr int CS_DEFAULT_AGG = 96;
+constexpr int CS_DEFAULT_AGG = 16;
 
 // q[a][k] = sum of r_p[v][k] over the vertices v of aggregate a.  One block per
 // aggregate; thread (chunk, k) sums every (256/ld)-th vertex in ascending order

@@ -164,7 +164,7 @@ def test_bad_arguments():
 
 def test_default_aggregate_count():
     o = scvs.scvs_default_opts()
-    assert o.schur_agg == 96 and o.precond == scvs.SCVS_PC_AUTO
+    assert o.schur_agg == 16 and o.precond == scvs.SCVS_PC_AUTO
 
 
 def _random_graph(n, n_comp, extra, seed):

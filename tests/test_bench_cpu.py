@@ -28,7 +28,7 @@ def test_pc_config_and_opts():
     a = argparse.Namespace(precond=None, schur_agg=0)
     assert bench.pc_config(a)["precond"].startswith("auto") and bench.pc_opts(a) == {}
     a = argparse.Namespace(precond=4, schur_agg=0)
-    assert bench.pc_config(a) == {"precond": "triangular-pmg + coarse Schur correction", "schur_agg": 96,
+    assert bench.pc_config(a) == {"precond": "triangular-pmg + coarse Schur correction", "schur_agg": 16,
                                   "pressure_laplacian": "two-level: aggregates of 32 vertices, 8 + 8 smoothing steps"}
     assert bench.pc_opts(a) == {"precond": 4}
     a = argparse.Namespace(precond=4, schur_agg=64)
