@@ -244,6 +244,9 @@ def pc_opts(args):
         o["lap_size"] = args.lap_size
     if getattr(args, "lap_smooth", 0):
         o["lap_smooth"] = args.lap_smooth
+    for k in ("cheb_u", "cheb_m", "cheb_l", "cheb_c"):
+        if getattr(args, k, 0):
+            o[k] = getattr(args, k)
     return o
 
 
@@ -273,9 +276,8 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     opts = dict(stream=stream.cuda_stream, precision=scvs.SCVS_PREC_FP64 if args.precision == "fp64"
                 else scvs.SCVS_PREC_MIXED)
-    for k in ("cheb_u", "cheb_m", "cheb_l", "cheb_c", "restart"):
-        if getattr(args, k):
-            opts[k] = getattr(args, k)
+    if args.restart:
+        opts["restart"] = args.restart
     opts.update(pc_opts(args))
     solver = scvs.Solver(**opts)
     ctx = solver.ctx

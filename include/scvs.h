@@ -115,7 +115,7 @@ typedef struct {
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */
   int32_t guess;     /* SCVS_GUESS_* (default ZERO) */
   int32_t verbose;   /* 0 = silent */
-  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of the p-multigrid kinds (default 30) */
+  int32_t cheb_c;    /* Chebyshev degree of the coarse (P1) velocity solve of the p-multigrid kinds (default 16) */
   int32_t autotune;  /* 1 (default): time the launch shapes (modes per lane, row tile) of the FP32 SpMM and
                         Chebyshev kernels at scvs_set_modes and keep the fastest; the result is kept per
                         context for meshes of the same size (dim, nodes, vertices, nonzeros, mode
@@ -316,11 +316,12 @@ int scvs_dof_count(scvs_ctx *ctx, int32_t mesh_id, int64_t *n_dof);
  * precision SCVS_PREC_MIXED: x, y float2 [n_dof][ld]; SCVS_PREC_FP64: double2.
  * Device pointers, caller-owned, on the context's stream. */
 int scvs_apply(scvs_ctx *ctx, int32_t mesh_id, int32_t precision, const void *x_dev, void *y_dev);
-/* Same operator evaluated element by element (matrix-free): every row owner
- * gathers the nodal blocks of its incident elements for all modes and
- * contracts them with the element matrices (reference tables times the
- * element's geometric factors), so no CSR values are read and no atomics are
- * used; same layouts and precisions as scvs_apply. */
+/* Same operator evaluated element by element (matrix-free): every element's
+ * matrices (reference tables times its geometric factors; stored quadrature
+ * matrices on curved elements) are applied once to its gathered nodal block
+ * for all modes, colour by colour (no two elements of a colour share a node;
+ * the colouring is built on the first call for a mesh), so no CSR values are
+ * read and no atomics are used; same layouts and precisions as scvs_apply. */
 int scvs_apply_matfree(scvs_ctx *ctx, int32_t mesh_id, int32_t precision, const void *x_dev, void *y_dev);
 /* Lifted right-hand side of every mode, FP64 double2 [n_dof][ld] (device view):
  * b_F = -A_FD g on free rows, b_D = g on Dirichlet rows. */

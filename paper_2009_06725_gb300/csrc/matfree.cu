@@ -3,15 +3,15 @@
 //
 // For affine P2 simplices every element matrix is a combination of fixed
 // reference matrices: M_e = det J * Mref, K_e = sum_p gamma_p(e) Ksym_p,
-// D_e[c] = -det J sum_i (J^-1)_ic Eref_i.  A row group of L lanes (lanes over
-// modes) owns one row; it walks the row's incident elements in ascending id
-// order, forms the element-matrix row of its local node from the element's
-// geometric factors and the reference tables, and contracts it with the
-// gathered nodal block x_e (every node of the element, every component, every
-// mode).  Owner-computes: no atomics, the summation order is fixed, results
-// are reproducible bit for bit.  The contraction has K = 10 (P2 tet) per
-// element and row, far too thin for tensor cores at FP32/FP64 accuracy, so it
-// runs on CUDA-core FMAs.
+// D_e[c] = -det J sum_i (J^-1)_ic Eref_i (curved elements: the stored
+// matrices).  Element by element: each element's matrices are formed once and
+// applied to its gathered nodal block (every node, component and mode), so
+// every gathered value serves the element's whole local matrix; elements are
+// processed colour by colour (no two elements of a colour share a node), so
+// their contributions are added with plain stores, without atomics, in a
+// fixed order (results reproducible bit for bit).  The contraction has K = 10
+// (P2 tet) per element row, far too thin for tensor cores at FP32/FP64
+// accuracy, so it runs on CUDA-core FMAs.
 #include <algorithm>
 #include "scvs_internal.h"
 #include "vecops.cuh"
@@ -29,8 +29,6 @@ void matfree_tables(Ctx &c) {
 template <typename T> struct MfArgs {
   int64_t N, P;
   int ld, nl;
-  const int64_t *n2e_ptr;
-  const int32_t *n2e;
   const int32_t *conn;
   const double *geom;
   const int32_t *cslot;        // curved elements: stored matrices (null: none)
@@ -38,155 +36,231 @@ template <typename T> struct MfArgs {
   const uint8_t *dirmask;
   const double *omega;
   double rho, mu;
+  const int32_t *el;           // elements of the current colour (ascending ids)
+  int64_t n_el;
 };
 
+// y = x on the Dirichlet velocity rows (identity rows), 0 elsewhere: the
+// element passes then add every element's contribution to the other rows.
+template <typename T>
+__global__ void k_matfree_init(const uint8_t *__restrict__ dirmask, int64_t N, int dim, int64_t total, int ld,
+                               const typename cpx<T>::t *__restrict__ x, typename cpx<T>::t *__restrict__ y) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= total) return;
+  const int64_t dof = f / ld;
+  const bool dir = dof < N * dim && dirmask[dof / dim];
+  y[f] = dir ? x[f] : mk<T>(0, 0);
+}
+
+// One colour of elements: no two of them share a node, so every element adds
+// its contribution y_e = A_e x_e to its nodes' rows with plain loads and
+// stores (no atomics; the colours run in a fixed order, so the sum over a
+// node's elements has a fixed order too).  A row group of L lanes (lanes over
+// modes) takes one element: it forms the element's K_e, M_e and D_e in shared
+// memory (reference tables times geometric factors, or the stored matrices of
+// a curved element), gathers the element's nodal block component by
+// component, and contracts: velocity rows a (not Dirichlet) get
+// mu (K_e u)_a + j omega rho (M_e u)_a + (D_e p)_a, pressure rows beta get
+// sum_b D_e[b][beta] . u_b, Dirichlet columns b left out.
 template <typename T, int MPL, int L, int DIM>
 __global__ void __launch_bounds__(256)
 k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename cpx<T>::t *__restrict__ y) {
   constexpr int NL = DIM == 2 ? 6 : 10, NV = DIM + 1, NP = DIM * (DIM + 1) / 2;
+  constexpr int NE = 2 * NL * NL + DIM * NL * NV;  // K, M, D entries of one element
+  constexpr int NR = NP * NL * NL + NL * NL + DIM * NL * NV;  // reference tables
+  extern __shared__ unsigned char mf_raw[];
+  // the reference tables first (the lanes of a group read different entries:
+  // from shared memory instead of the constant cache, which serialises them)
+  T *rK = reinterpret_cast<T *>(mf_raw), *rM = rK + NP * NL * NL, *rE = rM + NL * NL;
+  for (int t = threadIdx.x; t < NR; t += blockDim.x) {
+    T v;
+    if (t < NP * NL * NL) v = (T)c_mf[DIM - 2].ksym[t / (NL * NL)][(t / NL) % NL][t % NL];
+    else if (t < NP * NL * NL + NL * NL) v = (T)c_mf[DIM - 2].mref[(t - NP * NL * NL) / NL][(t - NP * NL * NL) % NL];
+    else {
+      const int tt = t - NP * NL * NL - NL * NL;
+      v = (T)c_mf[DIM - 2].eref[tt / (NL * NV)][(tt / NV) % NL][tt % NV];
+    }
+    rK[t] = v;  // rK, rM, rE are consecutive
+  }
+  __syncthreads();
+  T *sh = rK + NR;
   const int gpb = blockDim.x / L;
   const int lane = threadIdx.x % L, group = threadIdx.x / L;
+  const unsigned gm = group_mask<L>();
   const int ld = a.ld, koff = lane * MPL;
+  T *sK = sh + (size_t)group * NE, *sM = sK + NL * NL, *sD = sM + NL * NL;  // sD[c][aa][beta]
   T wr[MPL];
 #pragma unroll
   for (int i = 0; i < MPL; ++i) wr[i] = (T)(a.omega[koff + i] * a.rho);
   const T mu = (T)a.mu;
   const auto *xp_base = x + (int64_t)DIM * a.N * ld + koff;
-  for (int64_t row = (int64_t)blockIdx.x * gpb + group; row < a.N + a.P; row += (int64_t)gridDim.x * gpb) {
-    const bool vel = row < a.N;
-    const int64_t node = vel ? row : row - a.N;
-    if (vel && a.dirmask[node]) {
+  auto *yp_base = y + (int64_t)DIM * a.N * ld + koff;
+  for (int64_t q = (int64_t)blockIdx.x * gpb + group; q < a.n_el; q += (int64_t)gridDim.x * gpb) {
+    const int64_t e = __ldg(a.el + q);
+    int32_t cn[NL];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) {
-        CV<T, MPL> v;
-        ldv<T, MPL>(v, x + (node * DIM + c) * ld + koff);
-        stv<T, MPL>(y + (node * DIM + c) * ld + koff, v);
+    for (int b = 0; b < NL; ++b) cn[b] = __ldg(a.conn + e * NL + b);
+    const double *g = a.geom + e * GEOM_STRIDE;
+    const int cs = a.cslot ? __ldg(a.cslot + e) : -1;
+    const T det = (T)__ldg(g);
+    // element matrices into shared memory, entries split over the group's lanes
+    for (int t = lane; t < NE; t += L) {
+      T v;
+      if (t < NL * NL) {  // K
+        const int aa = t / NL, b = t % NL;
+        if (cs >= 0) {
+          v = (T)__ldg(a.CK + ((int64_t)cs * NL + aa) * NL + b);
+        } else {
+          v = 0;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) v += (T)__ldg(g + 10 + p) * rK[(p * NL + aa) * NL + b];
+        }
+      } else if (t < 2 * NL * NL) {  // M
+        const int tt = t - NL * NL, aa = tt / NL, b = tt % NL;
+        v = cs >= 0 ? (T)__ldg(a.CM + ((int64_t)cs * NL + aa) * NL + b) : det * rM[aa * NL + b];
+      } else {  // D[c][aa][beta]
+        const int tt = t - 2 * NL * NL, c = tt / (NL * NV), aa = (tt / NV) % NL, be = tt % NV;
+        if (cs >= 0) {
+          v = (T)__ldg(a.CD + (((int64_t)cs * DIM + c) * NL + aa) * NV + be);
+        } else {
+          T sacc = 0;
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) sacc += (T)__ldg(g + 1 + i * DIM + c) * rE[(i * NL + aa) * NV + be];
+          v = -det * sacc;
+        }
       }
-      continue;
+      sh[(size_t)group * NE + t] = v;
     }
-    CV<T, MPL> aK[DIM], aM[DIM], aD[DIM];
+    __syncwarp(gm);
+    CV<T, MPL> pv[NV], yp[NV];
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) { aK[c].zero(); aM[c].zero(); aD[c].zero(); }
-    for (int64_t ei = a.n2e_ptr[node]; ei < a.n2e_ptr[node + 1]; ++ei) {
-      const int64_t e = __ldg(a.n2e + ei);
-      int32_t cn[NL];
-      int loc = 0;
+    for (int be = 0; be < NV; ++be) {
+      ldv<T, MPL>(pv[be], xp_base + (int64_t)cn[be] * ld);
+      yp[be].zero();
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      CV<T, MPL> u[NL];
 #pragma unroll
       for (int b = 0; b < NL; ++b) {
-        cn[b] = __ldg(a.conn + e * NL + b);
-        if (cn[b] == (int32_t)node) loc = b;
+        if (a.dirmask[cn[b]]) u[b].zero();  // Dirichlet columns are removed
+        else ldv<T, MPL>(u[b], x + ((int64_t)cn[b] * DIM + c) * ld + koff);
       }
-      const double *g = a.geom + e * GEOM_STRIDE;
-      const int cs = a.cslot ? __ldg(a.cslot + e) : -1;
-      const T det = (T)__ldg(g);
-      T ji[DIM][DIM], ga[NP];
+      // pressure rows: sum_b D[c][b][beta] u_b
 #pragma unroll
-      for (int i = 0; i < DIM; ++i)
+      for (int b = 0; b < NL; ++b)
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) ji[i][c] = (T)__ldg(g + 1 + i * DIM + c);
-#pragma unroll
-      for (int p = 0; p < NP; ++p) ga[p] = (T)__ldg(g + 10 + p);
-      if (vel) {
-        const int aa = loc;
+        for (int be = 0; be < NV; ++be) axpy(yp[be], sD[(c * NL + b) * NV + be], u[b]);
+      // velocity rows
+      for (int aa = 0; aa < NL; ++aa) {
+        if (a.dirmask[cn[aa]]) continue;
+        CV<T, MPL> aK, aM, aD;
+        aK.zero(); aM.zero(); aD.zero();
 #pragma unroll
         for (int b = 0; b < NL; ++b) {
-          if (a.dirmask[cn[b]]) continue;  // Dirichlet columns are removed
-          T kc = 0, mc;
-          if (cs >= 0) {
-            kc = (T)__ldg(a.CK + ((int64_t)cs * NL + aa) * NL + b);
-            mc = (T)__ldg(a.CM + ((int64_t)cs * NL + aa) * NL + b);
-          } else {
-#pragma unroll
-            for (int p = 0; p < NP; ++p) kc += ga[p] * (T)c_mf[DIM - 2].ksym[p][aa][b];
-            mc = det * (T)c_mf[DIM - 2].mref[aa][b];
-          }
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) {
-            CV<T, MPL> xv;
-            ldv<T, MPL>(xv, x + ((int64_t)cn[b] * DIM + c) * ld + koff);
-            axpy(aK[c], kc, xv);
-            axpy(aM[c], mc, xv);
-          }
+          axpy(aK, sK[aa * NL + b], u[b]);
+          axpy(aM, sM[aa * NL + b], u[b]);
         }
 #pragma unroll
-        for (int b = 0; b < NV; ++b) {
-          CV<T, MPL> xq;
-          ldv<T, MPL>(xq, xp_base + (int64_t)cn[b] * ld);
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) {
-            T dc;
-            if (cs >= 0) {
-              dc = (T)__ldg(a.CD + (((int64_t)cs * DIM + c) * NL + aa) * NV + b);
-            } else {
-              T s = 0;
-#pragma unroll
-              for (int i = 0; i < DIM; ++i) s += ji[i][c] * (T)c_mf[DIM - 2].eref[i][aa][b];
-              dc = -det * s;
-            }
-            axpy(aD[c], dc, xq);
-          }
-        }
-      } else {
-        const int beta = loc;  // vertex: local index < NV
-#pragma unroll
-        for (int b = 0; b < NL; ++b) {
-          if (a.dirmask[cn[b]]) continue;
-#pragma unroll
-          for (int c = 0; c < DIM; ++c) {
-            T dc;
-            if (cs >= 0) {
-              dc = (T)__ldg(a.CD + (((int64_t)cs * DIM + c) * NL + b) * NV + beta);
-            } else {
-              T s = 0;
-#pragma unroll
-              for (int i = 0; i < DIM; ++i) s += ji[i][c] * (T)c_mf[DIM - 2].eref[i][b][beta];
-              dc = -det * s;
-            }
-            CV<T, MPL> xv;
-            ldv<T, MPL>(xv, x + ((int64_t)cn[b] * DIM + c) * ld + koff);
-            axpy(aD[0], dc, xv);
-          }
-        }
-      }
-    }
-    if (vel) {
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) {
+        for (int be = 0; be < NV; ++be) axpy(aD, sD[(c * NL + aa) * NV + be], pv[be]);
+        auto *yr = y + ((int64_t)cn[aa] * DIM + c) * ld + koff;
         CV<T, MPL> o;
+        ldv<T, MPL>(o, yr);
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
-          o.re[i] = mu * aK[c].re[i] - wr[i] * aM[c].im[i] + aD[c].re[i];
-          o.im[i] = mu * aK[c].im[i] + wr[i] * aM[c].re[i] + aD[c].im[i];
+          o.re[i] += mu * aK.re[i] - wr[i] * aM.im[i] + aD.re[i];
+          o.im[i] += mu * aK.im[i] + wr[i] * aM.re[i] + aD.im[i];
         }
-        stv<T, MPL>(y + (node * DIM + c) * ld + koff, o);
+        stv<T, MPL>(yr, o);
       }
-    } else {
-      stv<T, MPL>(y + ((int64_t)DIM * a.N + node) * ld + koff, aD[0]);
     }
+#pragma unroll
+    for (int be = 0; be < NV; ++be) {
+      auto *yr = yp_base + (int64_t)cn[be] * ld;
+      CV<T, MPL> o;
+      ldv<T, MPL>(o, yr);
+#pragma unroll
+      for (int i = 0; i < MPL; ++i) { o.re[i] += yp[be].re[i]; o.im[i] += yp[be].im[i]; }
+      stv<T, MPL>(yr, o);
+    }
+    __syncwarp(gm);  // the group's shared matrices are rewritten for its next element
   }
 }
 
-template <typename T>
-static void launch_matfree(Ctx &c, const Mesh &m, const void *x, void *y) {
-  using C = typename cpx<T>::t;
-  MfArgs<T> a{m.N, m.P, m.ld, m.nl, m.n2e_ptr, m.n2e, m.conn, m.geom, m.cslot, m.CM, m.CK, m.CD,
-              m.dirmask, m.omega_d, m.rho, m.mu};
-  // algorithmic bytes: connectivity, geometry and incidence once, x read once, y written once
-  KScope ks(c, KC_MATFREE, (double)m.E * (m.nl * 4 + GEOM_STRIDE * 8) + (double)m.E * m.nl * 4 + (double)(m.N + 1) * 8 +
-                               2.0 * m.n_dof * m.ld * 2 * sizeof(T));
-  SCVS_DISPATCH_LD(T, m.ld, {
-    const int gpb = 256 / L;
-    int64_t need = (m.N + m.P + gpb - 1) / gpb;
-    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)c.num_sms * 32));
-    if (m.dim == 2)
-      k_matfree<T, MPL, L, 2><<<nb, 256, 0, c.stream>>>(a, static_cast<const C *>(x), static_cast<C *>(y));
-    else
-      k_matfree<T, MPL, L, 3><<<nb, 256, 0, c.stream>>>(a, static_cast<const C *>(x), static_cast<C *>(y));
-  });
-  count_launch(c);
+// Colours of the elements for the element passes (host greedy, once per mesh):
+// elements in ascending id take the lowest colour that no element sharing one
+// of their nodes holds yet.  The elements are then listed colour by colour,
+// ascending ids within a colour.
+static void matfree_colours(Ctx &c, Mesh &m) {
+  const int64_t E = m.E;
+  const int nl = m.nl;
+  std::vector<int32_t> conn((size_t)std::max<int64_t>(E, 1) * nl);
+  SCVS_CUDA(cudaMemcpyAsync(conn.data(), m.conn, (size_t)E * nl * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
+  constexpr int W = 4;  // 256 colours at most
+  std::vector<uint64_t> used((size_t)m.N * W, 0);
+  std::vector<int16_t> col(std::max<int64_t>(E, 1), -1);
+  int n_col = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    uint64_t u[W] = {0, 0, 0, 0};
+    for (int b = 0; b < nl; ++b)
+      for (int w = 0; w < W; ++w) u[w] |= used[(size_t)conn[(size_t)e * nl + b] * W + w];
+    int k = -1;
+    for (int w = 0; w < W && k < 0; ++w)
+      if (~u[w]) k = w * 64 + __builtin_ctzll(~u[w]);
+    if (k < 0) throw (int)SCVS_ERR_STATE;  // more than 256 colours: not a simplex mesh of bounded degree
+    col[e] = (int16_t)k;
+    n_col = std::max(n_col, k + 1);
+    for (int b = 0; b < nl; ++b) used[(size_t)conn[(size_t)e * nl + b] * W + k / 64] |= 1ull << (k % 64);
+  }
+  std::vector<int64_t> ptr(n_col + 1, 0);
+  for (int64_t e = 0; e < E; ++e) ++ptr[col[e] + 1];
+  for (int k = 0; k < n_col; ++k) ptr[k + 1] += ptr[k];
+  std::vector<int32_t> list(std::max<int64_t>(E, 1));
+  {
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) list[fill[col[e]]++] = (int32_t)e;
+  }
+  m.mf_col_ptr = ptr;
+  m.mf_el = m.arena.alloc<int32_t>(std::max<int64_t>(E, 1));
+  SCVS_CUDA(cudaMemcpyAsync(m.mf_el, list.data(), (size_t)E * sizeof(int32_t), cudaMemcpyHostToDevice, c.stream));
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host list goes out of scope
 }
 
-void apply_matfree(Ctx &c, const Mesh &m, int precision, const void *x, void *y) {
+template <typename T>
+static void launch_matfree(Ctx &c, Mesh &m, const void *x, void *y) {
+  using C = typename cpx<T>::t;
+  if (m.mf_col_ptr.empty()) matfree_colours(c, m);
+  const int64_t total = m.n_dof * m.ld;
+  // algorithmic bytes: connectivity, geometry and the element list once, x read once, y written once
+  KScope ks(c, KC_MATFREE, (double)m.E * (m.nl * 4 + GEOM_STRIDE * 8 + 4) + 2.0 * total * 2 * sizeof(T));
+  k_matfree_init<T><<<ceil_div(total, 256), 256, 0, c.stream>>>(m.dirmask, m.N, m.dim, total, m.ld,
+                                                                static_cast<const C *>(x), static_cast<C *>(y));
+  count_launch(c);
+  MfArgs<T> a{m.N, m.P, m.ld, m.nl, m.conn, m.geom, m.cslot, m.CM, m.CK, m.CD, m.dirmask, m.omega_d, m.rho, m.mu,
+              nullptr, 0};
+  const int n_col = (int)m.mf_col_ptr.size() - 1;
+  for (int k = 0; k < n_col; ++k) {
+    a.el = m.mf_el + m.mf_col_ptr[k];
+    a.n_el = m.mf_col_ptr[k + 1] - m.mf_col_ptr[k];
+    if (a.n_el == 0) continue;
+    SCVS_DISPATCH_LD(T, m.ld, {
+      // at most 16 groups per block: their element matrices and the tables stay under 48 KB of shared memory
+      const int gpb = std::min(256 / L, 16), threads = gpb * L;
+      const int nv = m.dim + 1, np = m.dim * (m.dim + 1) / 2;
+      const int ne = 2 * m.nl * m.nl + m.dim * m.nl * nv, nr = np * m.nl * m.nl + m.nl * m.nl + m.dim * m.nl * nv;
+      const size_t smem = (size_t)(gpb * ne + nr) * sizeof(T);
+      const unsigned nb = (unsigned)std::max<int64_t>(1, (a.n_el + gpb - 1) / gpb);
+      if (m.dim == 2)
+        k_matfree<T, MPL, L, 2><<<nb, threads, smem, c.stream>>>(a, static_cast<const C *>(x), static_cast<C *>(y));
+      else
+        k_matfree<T, MPL, L, 3><<<nb, threads, smem, c.stream>>>(a, static_cast<const C *>(x), static_cast<C *>(y));
+    });
+    count_launch(c);
+  }
+}
+
+void apply_matfree(Ctx &c, Mesh &m, int precision, const void *x, void *y) {
   if (precision == SCVS_PREC_FP64)
     launch_matfree<double>(c, m, x, y);
   else

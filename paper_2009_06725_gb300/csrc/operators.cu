@@ -2667,10 +2667,11 @@ __global__ void k_init_random(float2 *v, int64_t n) {
 }
 
 // Spectral radius estimates of D^-1 A for the real-shifted velocity block
-// (per mode), the P1 mass and the P1 Laplacian (power method, 20 steps, FP32;
+// (per mode), the P1 mass and the P1 Laplacian (power method, 14 steps, FP32;
 // it approaches lambda_max from below, and the Chebyshev intervals end at
-// CHEB_TOP = 1.10 times the estimate: 40 steps with a 5% margin gave the same
-// iteration counts on the benchmark pipe at twice the cost).
+// CHEB_TOP = 1.10 times the estimate.  On the benchmark pipe 40 steps with a 5%
+// margin, 20 and 10 steps gave the same iteration counts and 7 steps let the
+// smoothers diverge, so 14 keeps a margin above that edge).
 void spectral_bounds(Ctx &c, Mesh &m) {
   const int ld = m.ld;
   const int64_t np = m.P * ld;
@@ -2696,7 +2697,7 @@ void spectral_bounds(Ctx &c, Mesh &m) {
   const unsigned nbn = (unsigned)std::min<int64_t>(ceil_div(total, 256), 4 * c.num_sms);
   SCVS_CUDA(ctx_malloc(c, &part, (size_t)4 * nbn * ld * sizeof(double), c.stream));  // per-block partial norms
   std::vector<double> h(4 * ld, 0.0);
-  const int iters = 20;
+  const int iters = 14;
   for (int it = 0; it < iters; ++it) {
     // y = D^-1 A (v / ||v||) with ||v|| from the previous step (the start vector is used as is)
     const double *vn2 = it == 0 ? nullptr : n2 + ((it - 1) % 2) * 4 * ld;

@@ -161,6 +161,8 @@ struct Mesh {
   int64_t n_curved = 0;
   int32_t *cslot = nullptr;
   double *CM = nullptr, *CK = nullptr, *CD = nullptr;
+  std::vector<int64_t> mf_col_ptr;  // matrix-free element colours: colour k = mf_el[ptr[k] .. ptr[k+1])
+  int32_t *mf_el = nullptr;         // [E] elements by colour (built on the first matrix-free application)
   int64_t *n2e_ptr = nullptr;       // [N+1] node -> incident elements
   int32_t *n2e = nullptr;           // ascending element ids per node
   int64_t *s_ptr = nullptr;         // [N+1]
@@ -352,7 +354,7 @@ int pc_kind(const Ctx &c, const Mesh &m);  // opts.precond with SCVS_PC_AUTO res
 template <typename T>
 void apply_precond(Ctx &c, Mesh &m, const typename cpx<T>::t *r, typename cpx<T>::t *z,
                    typename cpx<T>::t *scratch, const double *rscale);
-void apply_matfree(Ctx &c, const Mesh &m, int precision, const void *x, void *y);
+void apply_matfree(Ctx &c, Mesh &m, int precision, const void *x, void *y);
 // Graph aggregates (host): agg [P] aggregate of every vertex, numbered by block
 // (connected component, in order of its lowest vertex) then seed; per aggregate
 // its block and index within it; per block its count and first aggregate.

@@ -34,7 +34,7 @@ def test_pc_config_and_opts():
     a = argparse.Namespace(precond=4, schur_agg=64)
     assert bench.pc_opts(a) == {"precond": 4, "schur_agg": 64} and bench.pc_config(a)["schur_agg"] == 64
     a = argparse.Namespace(precond=None, schur_agg=0, lap_size=-1, lap_smooth=0, cheb_l=60)
-    assert bench.pc_opts(a) == {"lap_size": -1}
+    assert bench.pc_opts(a) == {"lap_size": -1, "cheb_l": 60}
     assert bench.pc_config(a)["pressure_laplacian"] == "chebyshev degree 60"
     a = argparse.Namespace(precond=1, schur_agg=0, lap_size=32, lap_smooth=4)
     assert bench.pc_opts(a) == {"precond": 1, "lap_size": 32, "lap_smooth": 4}
