@@ -63,7 +63,7 @@ __global__ void k_matfree_init(const uint8_t *__restrict__ dirmask, int64_t N, i
 // mu (K_e u)_a + j omega rho (M_e u)_a + (D_e p)_a, pressure rows beta get
 // sum_b D_e[b][beta] . u_b, Dirichlet columns b left out.
 template <typename T, int MPL, int L, int DIM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1)
 k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename cpx<T>::t *__restrict__ y) {
   constexpr int NL = DIM == 2 ? 6 : 10, NV = DIM + 1, NP = DIM * (DIM + 1) / 2;
   constexpr int NE = 2 * NL * NL + DIM * NL * NV;  // K, M, D entries of one element
@@ -98,8 +98,11 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
   for (int64_t q = (int64_t)blockIdx.x * gpb + group; q < a.n_el; q += (int64_t)gridDim.x * gpb) {
     const int64_t e = __ldg(a.el + q);
     int32_t cn[NL];
+    bool dir[NL];
 #pragma unroll
     for (int b = 0; b < NL; ++b) cn[b] = __ldg(a.conn + e * NL + b);
+#pragma unroll
+    for (int b = 0; b < NL; ++b) dir[b] = a.dirmask[cn[b]] != 0;
     const double *g = a.geom + e * GEOM_STRIDE;
     const int cs = a.cslot ? __ldg(a.cslot + e) : -1;
     const T det = (T)__ldg(g);
@@ -138,12 +141,12 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
       ldv<T, MPL>(pv[be], xp_base + (int64_t)cn[be] * ld);
       yp[be].zero();
     }
-#pragma unroll
-    for (int c = 0; c < DIM; ++c) {
+#pragma unroll 1
+    for (int c = 0; c < DIM; ++c) {  // one component at a time keeps the nodal block in registers
       CV<T, MPL> u[NL];
 #pragma unroll
       for (int b = 0; b < NL; ++b) {
-        if (a.dirmask[cn[b]]) u[b].zero();  // Dirichlet columns are removed
+        if (dir[b]) u[b].zero();  // Dirichlet columns are removed
         else ldv<T, MPL>(u[b], x + ((int64_t)cn[b] * DIM + c) * ld + koff);
       }
       // pressure rows: sum_b D[c][b][beta] u_b
@@ -151,9 +154,14 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
       for (int b = 0; b < NL; ++b)
 #pragma unroll
         for (int be = 0; be < NV; ++be) axpy(yp[be], sD[(c * NL + b) * NV + be], u[b]);
-      // velocity rows
+      // velocity rows: the rows' current sums are loaded together (one round trip), then updated
+      CV<T, MPL> yv[NL];
+#pragma unroll
+      for (int aa = 0; aa < NL; ++aa)
+        if (!dir[aa]) ldv<T, MPL>(yv[aa], y + ((int64_t)cn[aa] * DIM + c) * ld + koff);
+#pragma unroll
       for (int aa = 0; aa < NL; ++aa) {
-        if (a.dirmask[cn[aa]]) continue;
+        if (dir[aa]) continue;
         CV<T, MPL> aK, aM, aD;
         aK.zero(); aM.zero(); aD.zero();
 #pragma unroll
@@ -163,25 +171,22 @@ k_matfree(const MfArgs<T> a, const typename cpx<T>::t *__restrict__ x, typename 
         }
 #pragma unroll
         for (int be = 0; be < NV; ++be) axpy(aD, sD[(c * NL + aa) * NV + be], pv[be]);
-        auto *yr = y + ((int64_t)cn[aa] * DIM + c) * ld + koff;
-        CV<T, MPL> o;
-        ldv<T, MPL>(o, yr);
 #pragma unroll
         for (int i = 0; i < MPL; ++i) {
-          o.re[i] += mu * aK.re[i] - wr[i] * aM.im[i] + aD.re[i];
-          o.im[i] += mu * aK.im[i] + wr[i] * aM.re[i] + aD.im[i];
+          yv[aa].re[i] += mu * aK.re[i] - wr[i] * aM.im[i] + aD.re[i];
+          yv[aa].im[i] += mu * aK.im[i] + wr[i] * aM.re[i] + aD.im[i];
         }
-        stv<T, MPL>(yr, o);
+        stv<T, MPL>(y + ((int64_t)cn[aa] * DIM + c) * ld + koff, yv[aa]);
       }
     }
+    CV<T, MPL> po[NV];
+#pragma unroll
+    for (int be = 0; be < NV; ++be) ldv<T, MPL>(po[be], yp_base + (int64_t)cn[be] * ld);
 #pragma unroll
     for (int be = 0; be < NV; ++be) {
-      auto *yr = yp_base + (int64_t)cn[be] * ld;
-      CV<T, MPL> o;
-      ldv<T, MPL>(o, yr);
 #pragma unroll
-      for (int i = 0; i < MPL; ++i) { o.re[i] += yp[be].re[i]; o.im[i] += yp[be].im[i]; }
-      stv<T, MPL>(yr, o);
+      for (int i = 0; i < MPL; ++i) { po[be].re[i] += yp[be].re[i]; po[be].im[i] += yp[be].im[i]; }
+      stv<T, MPL>(yp_base + (int64_t)cn[be] * ld, po[be]);
     }
     __syncwarp(gm);  // the group's shared matrices are rewritten for its next element
   }
@@ -227,6 +232,17 @@ static void matfree_colours(Ctx &c, Mesh &m) {
   SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host list goes out of scope
 }
 
+#define SCVS_MF_DISPATCH(ld, ...)                                                        \
+  do {                                                                                   \
+    switch (ld) {                                                                        \
+      SCVS_LD_CASE(2, 1, __VA_ARGS__) SCVS_LD_CASE(4, 1, __VA_ARGS__)                   \
+      SCVS_LD_CASE(8, 1, __VA_ARGS__) SCVS_LD_CASE(16, 1, __VA_ARGS__)                  \
+      SCVS_LD_CASE(32, 1, __VA_ARGS__) SCVS_LD_CASE(64, 2, __VA_ARGS__)                 \
+      SCVS_LD_CASE(128, 4, __VA_ARGS__)                                                  \
+      default: throw (int)SCVS_ERR_ARG;                                                  \
+    }                                                                                    \
+  } while (0)
+
 template <typename T>
 static void launch_matfree(Ctx &c, Mesh &m, const void *x, void *y) {
   using C = typename cpx<T>::t;
@@ -244,8 +260,10 @@ static void launch_matfree(Ctx &c, Mesh &m, const void *x, void *y) {
     a.el = m.mf_el + m.mf_col_ptr[k];
     a.n_el = m.mf_col_ptr[k + 1] - m.mf_col_ptr[k];
     if (a.n_el == 0) continue;
-    SCVS_DISPATCH_LD(T, m.ld, {
-      // at most 16 groups per block: their element matrices and the tables stay under 48 KB of shared memory
+    // one mode per lane up to 32 modes (the element's nodal block of one
+    // component then takes 20 registers per lane), at most 16 groups per
+    // block (their element matrices and the tables stay under 48 KB)
+    SCVS_MF_DISPATCH(m.ld, {
       const int gpb = std::min(256 / L, 16), threads = gpb * L;
       const int nv = m.dim + 1, np = m.dim * (m.dim + 1) / 2;
       const int ne = 2 * m.nl * m.nl + m.dim * m.nl * nv, nr = np * m.nl * m.nl + m.nl * m.nl + m.dim * m.nl * nv;
