@@ -109,7 +109,7 @@ typedef struct {
   int32_t precision; /* SCVS_PREC_* (default MIXED) */
   int32_t precond;   /* SCVS_PC_* (default AUTO) */
   int32_t cheb_u;    /* Chebyshev degree of the velocity polynomial; with the p-multigrid kinds the degree of each
-                        of the pre- and post-smoothers (default 3) */
+                        of the pre- and post-smoothers (default 2) */
   int32_t cheb_m;    /* Chebyshev degree, pressure mass (default 4) */
   int32_t cheb_l;    /* Chebyshev degree, pressure Laplacian, when lap_size = -1 (default 75) */
   int32_t max_cycles;/* cap on restart cycles; each cycle ends with an FP64 true residual (default 400) */

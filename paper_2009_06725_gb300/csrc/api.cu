@@ -245,7 +245,7 @@ void scvs_default_opts(scvs_opts *o) {
   o->restart = 30;
   o->precision = SCVS_PREC_MIXED;
   o->precond = SCVS_PC_AUTO;
-  o->cheb_u = 3;
+  o->cheb_u = 2;
   o->cheb_c = 16;
   o->autotune = 1;
   o->cheb_m = 4;

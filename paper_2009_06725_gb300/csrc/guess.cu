@@ -360,7 +360,7 @@ void mlp_forward(Ctx &c, GuessModel &g, const float *x, int64_t B, float *y) {
 }
 
 // Gradients of the MSE against targets t for a batch; returns into g.grad.
-float mlp_gradient(Ctx &c, GuessModel &g, const float *x, const float *t, int64_t B) {
+float mlp_gradient(Ctx &c, GuessModel &g, const float *x, const float *t, int64_t B, bool read_loss) {
   g.ensure(B);
   float *y = g.ybuf();
   mlp_forward(c, g, x, B, y);
@@ -384,10 +384,20 @@ float mlp_gradient(Ctx &c, GuessModel &g, const float *x, const float *t, int64_
       std::swap(dcur, dprev);
     }
   }
+  if (!read_loss) return 0.0f;  // the training loop reads only its last step's loss
   float h = 0;
   SCVS_CUDA(cudaMemcpyAsync(&h, loss, sizeof(float), cudaMemcpyDeviceToHost, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));
   return h;
+}
+
+// Minibatch of the training loop: rows idx[0..B) of the device-resident
+// standardised features F [S][5] and targets T [S][n_out].
+__global__ void k_gather_batch(const int32_t *__restrict__ idx, int64_t B, const float *__restrict__ F,
+                               const float *__restrict__ T, int n_out, float *__restrict__ X, float *__restrict__ Y) {
+  const int64_t i = blockIdx.x * 256ll + threadIdx.x;
+  if (i < B * 5) X[i] = F[(int64_t)idx[i / 5] * 5 + i % 5];
+  if (i < B * n_out) Y[i] = T[(int64_t)idx[i / n_out] * n_out + i % n_out];
 }
 
 void mlp_refresh_bf16(Ctx &c, GuessModel &g) {
@@ -818,32 +828,48 @@ double guess_train(Ctx &c, const scvs_train_opts &o) {
   }
   SCVS_CUDA(cudaMemcpy(g.Wf, w0.data(), w0.size() * sizeof(float), cudaMemcpyHostToDevice));
   mlp_refresh_bf16(c, g);
-  // minibatch Adam
+  // minibatch Adam: the standardised data stay on the device, every step's
+  // minibatch indices (seeded shuffles, drawn on the host up front) are
+  // uploaded once, a kernel gathers each minibatch, and the host reads back
+  // only the last step's loss, so the steps run back to back on the stream
   const int B = std::min<int>(o.batch, S);
-  float *Xd = nullptr, *Td = nullptr;
+  std::vector<int32_t> idx((size_t)std::max(o.steps, 0) * B);
+  {
+    std::vector<int> perm(S);
+    for (int i = 0; i < S; ++i) perm[i] = i;
+    int pos = S;
+    for (int step = 0; step < o.steps; ++step) {
+      if (pos + B > S) { std::shuffle(perm.begin(), perm.end(), rng); pos = 0; }
+      for (int b = 0; b < B; ++b) idx[(size_t)step * B + b] = perm[pos + b];
+      pos += B;
+    }
+  }
+  float *Xd = nullptr, *Td = nullptr, *Fall = nullptr, *Tall = nullptr;
+  int32_t *idx_d = nullptr;
   SCVS_CUDA(cudaMalloc(&Xd, (size_t)B * 5 * sizeof(float)));
   SCVS_CUDA(cudaMalloc(&Td, (size_t)B * n_out * sizeof(float)));
-  std::vector<int> perm(S);
-  for (int i = 0; i < S; ++i) perm[i] = i;
-  std::vector<float> xb((size_t)B * 5), tb((size_t)B * n_out);
-  int pos = S;
+  SCVS_CUDA(cudaMalloc(&Fall, F.size() * sizeof(float)));
+  SCVS_CUDA(cudaMalloc(&Tall, T.size() * sizeof(float)));
+  SCVS_CUDA(cudaMalloc(&idx_d, std::max<size_t>(idx.size(), 1) * sizeof(int32_t)));
+  SCVS_CUDA(cudaMemcpy(Fall, F.data(), F.size() * sizeof(float), cudaMemcpyHostToDevice));
+  SCVS_CUDA(cudaMemcpy(Tall, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice));
+  SCVS_CUDA(cudaMemcpy(idx_d, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   double last = 0;
   for (int step = 0; step < o.steps; ++step) {
-    if (pos + B > S) { std::shuffle(perm.begin(), perm.end(), rng); pos = 0; }
-    for (int b = 0; b < B; ++b) {
-      const int s = perm[pos + b];
-      std::copy(F.begin() + (size_t)s * 5, F.begin() + (size_t)s * 5 + 5, xb.begin() + (size_t)b * 5);
-      std::copy(T.begin() + (size_t)s * n_out, T.begin() + (size_t)(s + 1) * n_out, tb.begin() + (size_t)b * n_out);
-    }
-    pos += B;
-    SCVS_CUDA(cudaMemcpyAsync(Xd, xb.data(), xb.size() * sizeof(float), cudaMemcpyHostToDevice, c.stream));
-    SCVS_CUDA(cudaMemcpyAsync(Td, tb.data(), tb.size() * sizeof(float), cudaMemcpyHostToDevice, c.stream));
+    k_gather_batch<<<grid1((int64_t)B * std::max(5, n_out)), 256, 0, c.stream>>>(idx_d + (size_t)step * B, B, Fall,
+                                                                                Tall, n_out, Xd, Td);
+    count_launch(c);
     const float lr = (float)(o.lr * (step < o.steps / 2 ? 1.0 : (step < 3 * o.steps / 4 ? 0.3 : 0.1)));
-    last = mlp_gradient(c, g, Xd, Td, B);
+    const float l = mlp_gradient(c, g, Xd, Td, B, step == o.steps - 1);
+    if (step == o.steps - 1) last = l;
     mlp_adam(c, g, lr);
   }
+  SCVS_CUDA(cudaStreamSynchronize(c.stream));
   cudaFree(Xd);
   cudaFree(Td);
+  cudaFree(Fall);
+  cudaFree(Tall);
+  cudaFree(idx_d);
   g.trained = true;
   return last;
 }

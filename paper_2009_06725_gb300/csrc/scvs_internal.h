@@ -378,7 +378,7 @@ bool guess_initial(Ctx &c, Mesh &m);
 void mlp_alloc(GuessModel &g, int n_in, int hidden, int n_out);
 void mlp_refresh_bf16(Ctx &c, GuessModel &g);
 void mlp_forward(Ctx &c, GuessModel &g, const float *x, int64_t B, float *y);
-float mlp_gradient(Ctx &c, GuessModel &g, const float *x, const float *t, int64_t B);
+float mlp_gradient(Ctx &c, GuessModel &g, const float *x, const float *t, int64_t B, bool read_loss = true);
 void mlp_adam(Ctx &c, GuessModel &g, float lr);
 
 // ---- recon.cu
