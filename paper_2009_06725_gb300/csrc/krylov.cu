@@ -370,45 +370,68 @@ __global__ void k_lsq(const double2 *__restrict__ H, const double2 *__restrict__
   }
 }
 
-// u = sum_{i<nv} y_i v_i (per mode)
+// x += sum_{i<nv} y_i v_i (per mode), in one pass: per element four FP32
+// partial sums (term i into sum i mod 4; a zero coefficient, a system past its
+// Krylov dimension, contributes nothing, so stale vectors never propagate),
+// combined as (s0 + s1) + (s2 + s3) and added to the FP64 iterate.  Two adjacent elements per thread, so every
+// thread keeps eight basis loads in flight.
 template <typename T>
-__global__ void k_combine(const typename cpx<T>::t *__restrict__ V, int64_t vstride, const double2 *__restrict__ y,
-                          int nv, int ld, int S, const int32_t *__restrict__ dof_comp, const int *__restrict__ upd,
-                          int64_t total, typename cpx<T>::t *__restrict__ u) {
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= total) return;
-  const int sys = (dof_comp ? dof_comp[f / ld] * ld : 0) + (int)(f % ld);
-  if (!upd[sys]) return;  // system not updated in this cycle
-  // steps beyond this system's Krylov dimension have y = 0; their term is
-  // selected away (not multiplied by 0) so stale vectors never propagate.
-  // Four independent accumulators keep several basis loads in flight.
-  T re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+__global__ void __launch_bounds__(256) k_combine_add(const typename cpx<T>::t *__restrict__ V, int64_t vstride,
+                                                     const double2 *__restrict__ y, int nv, int ld, int S,
+                                                     const int32_t *__restrict__ dof_comp,
+                                                     const int *__restrict__ upd, int64_t total,
+                                                     double2 *__restrict__ x) {
+  const int64_t f0 = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+  if (f0 >= total) return;
+  int sys[2];
+  bool on[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int64_t f = f0 + e;
+    sys[e] = f < total ? (dof_comp ? dof_comp[f / ld] * ld : 0) + (int)(f % ld) : 0;
+    on[e] = f < total && upd[sys[e]];
+  }
+  if (!on[0] && !on[1]) return;
+  T re[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}}, im[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
   int i = 0;
   for (; i + 4 <= nv; i += 4) {
-    typename cpx<T>::t v[4];
-    double2 yy[4];
+    typename cpx<T>::t v[4][2];
+    double2 yy[4][2];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      yy[u] = y[(int64_t)(i + u) * S + sys];
-      v[u] = V[(int64_t)(i + u) * vstride + f];
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        yy[u][e] = y[(int64_t)(i + u) * S + sys[e]];
+        v[u][e] = (f0 + e < total) ? V[(int64_t)(i + u) * vstride + f0 + e] : mk<T>(0, 0);
+      }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const bool z = yy[u][e].x == 0.0 && yy[u][e].y == 0.0;
+        const T a = (T)yy[u][e].x, b = (T)yy[u][e].y;
+        re[e][u] += z ? T(0) : a * v[u][e].x - b * v[u][e].y;
+        im[e][u] += z ? T(0) : a * v[u][e].y + b * v[u][e].x;
+      }
+  }
+  for (; i < nv; ++i)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const double2 yy = y[(int64_t)i * S + sys[e]];
+      const auto v = (f0 + e < total) ? V[(int64_t)i * vstride + f0 + e] : mk<T>(0, 0);
+      const bool z = yy.x == 0.0 && yy.y == 0.0;
+      re[e][0] += z ? T(0) : (T)yy.x * v.x - (T)yy.y * v.y;
+      im[e][0] += z ? T(0) : (T)yy.x * v.y + (T)yy.y * v.x;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const bool z = yy[u].x == 0.0 && yy[u].y == 0.0;
-      const T a = (T)yy[u].x, b = (T)yy[u].y;
-      re[u] += z ? T(0) : a * v[u].x - b * v[u].y;
-      im[u] += z ? T(0) : a * v[u].y + b * v[u].x;
-    }
+  for (int e = 0; e < 2; ++e) {
+    if (!on[e]) continue;
+    const T rs = (re[e][0] + re[e][1]) + (re[e][2] + re[e][3]), is = (im[e][0] + im[e][1]) + (im[e][2] + im[e][3]);
+    double2 xv = x[f0 + e];
+    xv.x += (double)rs;
+    xv.y += (double)is;
+    x[f0 + e] = xv;
   }
-  for (; i < nv; ++i) {
-    const double2 yy = y[(int64_t)i * S + sys];
-    const auto v = V[(int64_t)i * vstride + f];
-    const bool z = yy.x == 0.0 && yy.y == 0.0;
-    re[0] += z ? T(0) : (T)yy.x * v.x - (T)yy.y * v.y;
-    im[0] += z ? T(0) : (T)yy.x * v.y + (T)yy.y * v.x;
-  }
-  const T rs = (re[0] + re[1]) + (re[2] + re[3]), is = (im[0] + im[1]) + (im[2] + im[3]);
-  u[f] = mk<T>(rs, is);
 }
 
 template <typename T>
@@ -1035,17 +1058,10 @@ static int solve_mesh_t(Ctx &c, Mesh &m) {
       rep(s).cycles += 1;
     }
     if (nvmax > 0) {
-      {
-        KScope ks(c, KC_VECTOR, (double)(nvmax + 1) * total * 2 * sizeof(T));
-        k_combine<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.Z, total, wk.y, nvmax, ld, S, m.dof_comp, wk.upd, total,
-                                                         wk.W);
-        count_launch(c);
-      }
-      {
-        KScope ks(c, KC_VECTOR, (double)total * (32 + 2 * sizeof(T)));
-        k_add_to_x<T><<<(unsigned)eb, 256, 0, c.stream>>>(wk.W, wk.upd, ld, m.dof_comp, total, m.x);
-        count_launch(c);
-      }
+      KScope ks(c, KC_VECTOR, (double)nvmax * total * 2 * sizeof(T) + (double)total * 32);
+      k_combine_add<T><<<(unsigned)ceil_div(total, 512), 256, 0, c.stream>>>(wk.Z, total, wk.y, nvmax, ld, S,
+                                                                             m.dof_comp, wk.upd, total, m.x);
+      count_launch(c);
     }
   }
   if (m.n_comp > 1) SCVS_CUDA(cudaMemsetAsync(m.comp_active, 1, m.n_comp, c.stream));
