@@ -616,7 +616,7 @@ int scvs_schur_coarse_info(scvs_ctx *ctx, int32_t mesh_id, int32_t *info);
  * or a null info. */
 int scvs_lap_info(scvs_ctx *ctx, int32_t mesh_id, int32_t *info, int32_t *agg);
 
-/* Spectral bounds behind the preconditioner's Chebyshev intervals (a 20-step power method on the
+/* Spectral bounds behind the preconditioner's Chebyshev intervals (a 14-step power method on the
  * Jacobi-scaled operators, run by scvs_set_modes and scvs_set_physics): out[0] = lambda_max of
  * D^-1 M_p, out[1] of D^-1 L_p (outlet rows and columns removed), out[2 + k] of D^-1 A_r with the
  * velocity shift A_r = mu K + |omega_k| rho M of mode k (P2, Dirichlet rows removed) and
