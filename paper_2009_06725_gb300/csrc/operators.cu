@@ -1515,15 +1515,18 @@ static typename cpx<T>::t *coarse_solve(Ctx &c, const Mesh &m, const PcArgs &a, 
 constexpr int CS_NA_MAX = 1024;  // aggregates of one block at most
 constexpr int CS_DEFAULT_AGG = 16;
 
-// q[a][k] = sum of r_p[v][k] over the vertices v of aggregate a.  One block per
-// aggregate; thread (chunk, k) sums every (256/ld)-th vertex in ascending order
-// in FP64, and the chunk partials are added in a fixed tree order.
+// q[a][k] = sum of r_p[v][k] over the vertices v of aggregate a.  One block of
+// AGG_RT threads per aggregate (a few large aggregates: the whole block's width
+// keeps loads in flight); thread (chunk, k) sums every (AGG_RT/ld)-th vertex
+// in ascending order in FP64, and the chunk partials are added in a fixed
+// tree order.
+constexpr int AGG_RT = 1024;
 template <typename T>
-__global__ void __launch_bounds__(256) k_agg_restrict(const int64_t *__restrict__ agg_ptr,
-                                                      const int32_t *__restrict__ agg_vert, int ld,
-                                                      const typename cpx<T>::t *__restrict__ rp,
-                                                      typename cpx<T>::t *__restrict__ q) {
-  __shared__ double2 part[256];
+__global__ void __launch_bounds__(AGG_RT) k_agg_restrict(const int64_t *__restrict__ agg_ptr,
+                                                         const int32_t *__restrict__ agg_vert, int ld,
+                                                         const typename cpx<T>::t *__restrict__ rp,
+                                                         typename cpx<T>::t *__restrict__ q) {
+  __shared__ double2 part[AGG_RT];
   const int a = blockIdx.x;
   const int k = threadIdx.x % ld, ch = threadIdx.x / ld, nch = blockDim.x / ld;
   const int64_t v0 = agg_ptr[a], v1 = agg_ptr[a + 1];
@@ -2445,7 +2448,7 @@ static void schur_coarse_setup(Ctx &c, Mesh &m, PcTables &t) {
     apply_saddle<T>(c, m, Z, Y);
     {
       KScope ks(c, KC_PRECOND, pl * cs + (double)m.P * 4 + (double)(t.n_agg + 1) * 8 + (double)t.n_agg * m.ld * cs);
-      k_agg_restrict<T><<<t.n_agg, 256, 0, c.stream>>>(t.agg_ptr, t.agg_vert, m.ld, Y + fp, q);
+      k_agg_restrict<T><<<t.n_agg, AGG_RT, 0, c.stream>>>(t.agg_ptr, t.agg_vert, m.ld, Y + fp, q);
       count_launch(c);
     }
     {
@@ -2478,7 +2481,7 @@ static void schur_coarse_apply(Ctx &c, const Mesh &m, const PcArgs &a, const PcT
   const double cs = 2.0 * sizeof(T);
   {
     KScope ks(c, KC_PRECOND, pl * cs + (double)m.P * 4 + (double)(t.n_agg + 1) * 8 + ql * cs);
-    k_agg_restrict<T><<<t.n_agg, 256, 0, c.stream>>>(t.agg_ptr, t.agg_vert, m.ld, r + fp, q);
+    k_agg_restrict<T><<<t.n_agg, AGG_RT, 0, c.stream>>>(t.agg_ptr, t.agg_vert, m.ld, r + fp, q);
     count_launch(c);
   }
   {
