@@ -638,24 +638,31 @@ k_vel_residual(const PcArgs a, const typename cpx<T>::t *__restrict__ r, const t
 template <typename T>
 __global__ void k_prolong(const PcArgs a, int dim, const typename cpx<T>::t *__restrict__ zc,
                           typename cpx<T>::t *__restrict__ z) {
-  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // two consecutive elements (modes k, k+1 of one node and component) per
+  // thread: dim * ld is even, so both belong to the same node
+  const int64_t f = 2 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
   const int64_t per = (int64_t)dim * a.ld;
   if (f >= a.N * per) return;
   const int64_t n = f / per, rem = f % per;
   if (a.dirmask[n] || row_idle(a.dof_comp, a.comp_active, n * dim)) return;
-  T cr, ci;
+  CV<T, 2> c0, o;
   if (n < a.P) {
-    const auto c0 = zc[n * per + rem];
-    cr = c0.x; ci = c0.y;
+    ldv<T, 2>(c0, zc + n * per + rem);
   } else {
     const int64_t i = n - a.P;
-    const auto c0 = zc[(int64_t)a.edge_ends[2 * i] * per + rem];
-    const auto c1 = zc[(int64_t)a.edge_ends[2 * i + 1] * per + rem];
-    cr = T(0.5) * (c0.x + c1.x);
-    ci = T(0.5) * (c0.y + c1.y);
+    CV<T, 2> c1;
+    ldv<T, 2>(c0, zc + (int64_t)a.edge_ends[2 * i] * per + rem);
+    ldv<T, 2>(c1, zc + (int64_t)a.edge_ends[2 * i + 1] * per + rem);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      c0.re[q] = T(0.5) * (c0.re[q] + c1.re[q]);
+      c0.im[q] = T(0.5) * (c0.im[q] + c1.im[q]);
+    }
   }
-  auto o = z[f];
-  z[f] = mk<T>(o.x + cr, o.y + ci);
+  ldv<T, 2>(o, z + f);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) { o.re[q] += c0.re[q]; o.im[q] += c0.im[q]; }
+  stv<T, 2>(z + f, o);
 }
 
 // Coarse operator A_c = mu K_1 + |omega| rho M_1 (P1, Dirichlet vertices removed);
@@ -2295,7 +2302,7 @@ static typename cpx<T>::t *vel_cycle(Ctx &c, const Mesh &m, const PcArgs &a, con
     C *zres = coarse_solve<T>(c, m, a, t, uprev, rc, zc);
     {
       KScope ks(c, KC_PRECOND, 2 * vb + cbk + (double)(m.N - m.P) * 8 + m.N);
-      k_prolong<T><<<ceil_div((int64_t)m.dim * m.N * m.ld, 256), 256, 0, c.stream>>>(a, m.dim, zres, ucur);
+      k_prolong<T><<<ceil_div((int64_t)m.dim * m.N * m.ld, 512), 256, 0, c.stream>>>(a, m.dim, zres, ucur);
       count_launch(c);
     }
     // post-smoothing from the corrected iterate: first step z1 = z0 + D^-1 (r - A z0)/theta
