@@ -1248,6 +1248,7 @@ k_tri_vel0(const PcArgs a, typename cpx<T>::t *__restrict__ r, const double *__r
         for (int c = 0; c < DIM; ++c) dv[c] = __ldg(Dv + c * a.g_nnz + t + goff);
       }
       const int cnt = (int)min((int64_t)L, g1 - base);
+#pragma unroll 4
       for (int q = 0; q < cnt; ++q) {
         const int32_t B = gshfl<L>(gm, col, q);
         CV<T, MPL> xq;
