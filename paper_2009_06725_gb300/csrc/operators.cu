@@ -2072,6 +2072,22 @@ __global__ void __launch_bounds__(256) k_lap_invert(const int32_t *__restrict__ 
     if (ld1co(bad + b)) atomicAdd(n_singular, 1);
 }
 
+// Stream-ordered device temporaries of a set-up step, released when the
+// owner goes out of scope (also when a CUDA error unwinds the step).
+struct LapTemps {
+  Ctx &c;
+  std::vector<void *> p;
+  ~LapTemps() {
+    for (void *q : p) cudaFreeAsync(q, c.stream);
+  }
+  template <typename P> P *get(int64_t n) {
+    P *q = nullptr;
+    SCVS_CUDA(ctx_malloc(c, &q, (size_t)std::max<int64_t>(n, 1) * sizeof(P), c.stream));
+    p.push_back(q);
+    return q;
+  }
+};
+
 // Coarse level of the pressure Laplacian (host aggregation, device Galerkin
 // matrices and inverses), kept in the mesh arena for the mesh's lifetime.  The
 // graph is the vertex graph with the outlet vertices (p = 0 there) removed;
@@ -2165,19 +2181,12 @@ static void lap_build(Ctx &c, Mesh &m, int size) {
     tile0[b + 1] = tile0[b] + nt * nt;
     pan0[b + 1] = pan0[b] + 2 * (int64_t)LAP_BS * r.na[b];
   }
-  double *W = nullptr;
-  float *A0 = nullptr, *A1 = nullptr, *dmax = nullptr, *Dinv = nullptr;
-  int *nsing = nullptr, *bad = nullptr;
-  int64_t *tile0_d = nullptr, *pan0_d = nullptr;
-  SCVS_CUDA(ctx_malloc(c, &W, (size_t)acc * sizeof(double), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &A0, (size_t)acc * sizeof(float), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &A1, (size_t)acc * sizeof(float), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &dmax, (size_t)nb * sizeof(float), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &bad, (size_t)nb * sizeof(int), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &Dinv, (size_t)nb * LAP_BS * LAP_BS * sizeof(float), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &tile0_d, (size_t)(nb + 1) * sizeof(int64_t), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &pan0_d, (size_t)(nb + 1) * sizeof(int64_t), c.stream));
-  SCVS_CUDA(ctx_malloc(c, &nsing, sizeof(int), c.stream));
+  LapTemps tmp{c, {}};  // stream-ordered temporaries, released on every exit path
+  double *W = tmp.get<double>(acc);
+  float *A0 = tmp.get<float>(acc), *A1 = tmp.get<float>(acc), *dmax = tmp.get<float>(nb);
+  float *Dinv = tmp.get<float>((int64_t)nb * LAP_BS * LAP_BS);
+  int *bad = tmp.get<int>(nb), *nsing = tmp.get<int>(1);
+  int64_t *tile0_d = tmp.get<int64_t>(nb + 1), *pan0_d = tmp.get<int64_t>(nb + 1);
   up(tile0_d, tile0.data(), (nb + 1) * sizeof(int64_t));
   up(pan0_d, pan0.data(), (nb + 1) * sizeof(int64_t));
   SCVS_CUDA(cudaMemsetAsync(W, 0, (size_t)acc * sizeof(double), c.stream));
@@ -2202,9 +2211,6 @@ static void lap_build(Ctx &c, Mesh &m, int size) {
   int h_sing = 0, gerr = 0;
   SCVS_CUDA(cudaMemcpyAsync(&h_sing, nsing, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
   SCVS_CUDA(cudaMemcpyAsync(&gerr, &c.gsync->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  for (void *q : {(void *)W, (void *)A0, (void *)A1, (void *)dmax, (void *)bad, (void *)Dinv, (void *)tile0_d,
-                  (void *)pan0_d, (void *)nsing})
-    SCVS_CUDA(cudaFreeAsync(q, c.stream));
   SCVS_CUDA(cudaStreamSynchronize(c.stream));  // the host vectors go out of scope
   if (gerr) {  // a barrier wait gave up: the inverses are incomplete
     SCVS_CUDA(cudaMemsetAsync(c.gsync, 0, sizeof(GridSync), c.stream));
